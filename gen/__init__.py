@@ -1,0 +1,21 @@
+"""Seeded synthetic inputs for the MINRES-CG solver.
+
+This package only builds test problems (sparse matrices, eigenpairs of the
+negative invariant subspace, right-hand sides).  It holds none of the solver's
+arithmetic and is shared by the CPU oracle, the CUDA path's tests and the
+benchmark.
+"""
+from .problems import (  # noqa: F401
+    Problem,
+    laplacian_csr,
+    laplacian_smallest_eigs,
+    laplacian_eigvecs,
+    shift_for_negatives,
+    shifted_laplacian_problem,
+    random_indefinite_dense,
+    dense_to_csr,
+    config1,
+    config2,
+    small_3d,
+    CONFIGS,
+)

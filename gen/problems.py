@@ -1,0 +1,218 @@
+"""Seeded test problems with few negative eigenvalues.
+
+The solver targets sparse, full-rank, symmetric indefinite A with k << n
+negative eigenvalues (Sec. 1, Eq. 1).  The synthetic stand-ins are shifted
+Dirichlet Laplacians A = L - sigma*I whose eigenpairs are known in closed form,
+so the negative invariant subspace V_hat and its eigenvalues Lambda_hat
+(Sec. 2, definition of M_mr) are exact up to rounding.
+
+Recipe (one function per workload):
+  * L: unscaled Dirichlet 5-point (2D) / 7-point (3D) stencil, row index
+    p + m1*(q + m2*r) (x fastest); diagonal 2*d, off-diagonals -1.
+  * eigenvalue of mode (i1, .., id): sum_d 2 - 2 cos(i_d pi / (m_d + 1)),
+    eigenvector prod_d sqrt(2/(m_d+1)) sin(i_d pi (p_d+1) / (m_d+1)).
+  * sigma midway between the k-th and (k+1)-th smallest eigenvalue; if they
+    coincide (symmetric grids have degenerate clusters) k is raised to the end
+    of its cluster so that A stays nonsingular.
+  * x* = default_rng(seed).uniform(-1, 1, n); b = A x* (scipy CSR product).
+"""
+from __future__ import annotations
+
+import itertools
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.sparse as sp
+
+
+@dataclass
+class Problem:
+    """One symmetric indefinite system with its negative eigenpairs.
+
+    rowptr int64[n+1], colind int32[nnz], val float64[nnz]: full symmetric CSR
+    with sorted column indices.  V float64[n, k] (C order, i.e. row-major; use
+    V.T for the column-major n x k block the C-ABI takes), lam float64[k] < 0.
+    """
+
+    name: str
+    n: int
+    rowptr: np.ndarray
+    colind: np.ndarray
+    val: np.ndarray
+    k: int
+    V: np.ndarray
+    lam: np.ndarray
+    xstar: np.ndarray
+    b: np.ndarray
+    sigma: float = 0.0
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.rowptr[-1])
+
+    def scipy(self) -> sp.csr_matrix:
+        return sp.csr_matrix((self.val, self.colind, self.rowptr), shape=(self.n, self.n))
+
+    def dense(self) -> np.ndarray:
+        return self.scipy().toarray()
+
+    def V_colmajor(self) -> np.ndarray:
+        """V as one contiguous column-major n x k block (column j at offset j*n)."""
+        return np.ascontiguousarray(self.V.T)
+
+
+def laplacian_csr(dims, sigma: float = 0.0):
+    """CSR of the Dirichlet Laplacian on a len(dims)-D grid, minus sigma*I."""
+    dims = tuple(int(m) for m in dims)
+    d = len(dims)
+    n = int(np.prod(dims))
+    idx = np.arange(n, dtype=np.int64)
+    coords = []
+    rem = idx.copy()
+    for m in dims:
+        coords.append(rem % m)
+        rem //= m
+    strides = [1]
+    for m in dims[:-1]:
+        strides.append(strides[-1] * m)
+    rows = [idx]
+    cols = [idx]
+    vals = [np.full(n, 2.0 * d - sigma)]
+    for ax, (m, st) in enumerate(zip(dims, strides)):
+        lo = coords[ax] > 0
+        rows.append(idx[lo]); cols.append(idx[lo] - st); vals.append(np.full(int(lo.sum()), -1.0))
+        hi = coords[ax] < m - 1
+        rows.append(idx[hi]); cols.append(idx[hi] + st); vals.append(np.full(int(hi.sum()), -1.0))
+    r = np.concatenate(rows); c = np.concatenate(cols); v = np.concatenate(vals)
+    order = np.lexsort((c, r))
+    r, c, v = r[order], c[order], v[order]
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rowptr, r + 1, 1)
+    rowptr = np.cumsum(rowptr)
+    return rowptr, c.astype(np.int32), v.astype(np.float64)
+
+
+def _mode_value(dims, modes):
+    # sum of the per-axis values in sorted order, so that permuted modes of a
+    # symmetric grid give bit-identical eigenvalues
+    parts = sorted(2.0 - 2.0 * np.cos(i * np.pi / (m + 1)) for i, m in zip(modes, dims))
+    s = 0.0
+    for p in parts:
+        s += p
+    return s
+
+
+def laplacian_smallest_eigs(dims, count: int):
+    """The `count` smallest Laplacian eigenvalues with their mode tuples.
+
+    Returned ascending with multiplicity; ties broken by the mode tuple.
+    """
+    dims = tuple(int(m) for m in dims)
+    reach = 1
+    while True:
+        ranges = [range(1, min(m, reach) + 1) for m in dims]
+        cand = [(_mode_value(dims, md), md) for md in itertools.product(*ranges)]
+        cand.sort()
+        if len(cand) > count:
+            # every mode outside the box has some index > reach, so its value
+            # exceeds the smallest value with that index: enlarge until the
+            # count-th value is below that bound
+            bound = min(_mode_value(dims, tuple(min(reach + 1, m) if a == ax else 1
+                                                for a, m in enumerate(dims)))
+                        for ax in range(len(dims)) if dims[ax] > reach) if any(m > reach for m in dims) else np.inf
+            if cand[count][0] < bound:
+                return cand[: count + 1]
+        if all(m <= reach for m in dims):
+            return cand
+        reach += 2
+
+
+def laplacian_eigvecs(dims, modes) -> np.ndarray:
+    """Orthonormal eigenvectors (rows of the returned [len(modes), n] array)."""
+    dims = tuple(int(m) for m in dims)
+    out = np.empty((len(modes), int(np.prod(dims))))
+    for t, md in enumerate(modes):
+        vec = np.ones(1)
+        for i, m in zip(modes[t], dims):
+            axis = np.sqrt(2.0 / (m + 1)) * np.sin(i * np.pi * np.arange(1, m + 1) / (m + 1))
+            vec = np.kron(axis, vec)  # x fastest
+        out[t] = vec
+    return out
+
+
+def shift_for_negatives(dims, k_wanted: int, rel_tie: float = 1e-10):
+    """sigma midway between eigenvalues k and k+1, with k raised past ties.
+
+    Returns (sigma, k_eff, eigs[0:k_eff+1] as (value, mode)).
+    """
+    k = int(k_wanted)
+    while True:
+        ev = laplacian_smallest_eigs(dims, k + 1)
+        lk, lk1 = ev[k - 1][0], ev[k][0]
+        if abs(lk1 - lk) <= rel_tie * lk1:
+            k += 1
+            continue
+        return 0.5 * (lk + lk1), k, ev[: k + 1]
+
+
+def shifted_laplacian_problem(name, dims, k_wanted, seed, xstar=None) -> Problem:
+    sigma, k, ev = shift_for_negatives(dims, k_wanted)
+    rowptr, colind, val = laplacian_csr(dims, sigma)
+    n = int(np.prod(dims))
+    modes = [m for _, m in ev[:k]]
+    V = laplacian_eigvecs(dims, modes).T.copy()  # n x k, row-major
+    lam = np.array([v for v, _ in ev[:k]]) - sigma
+    if xstar is None:
+        xstar = np.random.default_rng(seed).uniform(-1.0, 1.0, n)
+    A = sp.csr_matrix((val, colind, rowptr), shape=(n, n))
+    b = A @ xstar
+    gap = min(abs(ev[k - 1][0] - sigma), abs(ev[k][0] - sigma))
+    lam_max = sum(2.0 - 2.0 * np.cos(m * np.pi / (m + 1)) for m in dims) - sigma
+    meta = {"dims": list(dims), "k_wanted": int(k_wanted), "k": k, "sigma": sigma,
+            "min_abs_eig": gap, "max_abs_eig": lam_max, "cond": lam_max / gap, "seed": seed}
+    return Problem(name, n, rowptr, colind, val, k, V, lam, xstar, b, sigma, meta)
+
+
+def config1() -> Problem:
+    """2D 5-point Laplacian 64x64 (n=4096), 4 negative eigenvalues, seed 0."""
+    return shifted_laplacian_problem("lap2d_64x64_k4", (64, 64), 4, seed=0)
+
+
+def config2() -> Problem:
+    """3D 7-point Laplacian 128^3 (n=2,097,152), 10 negative eigenvalues, seed 1."""
+    return shifted_laplacian_problem("lap3d_128^3_k10", (128, 128, 128), 10, seed=1)
+
+
+def small_3d(m=(12, 11, 10), k=5, seed=7) -> Problem:
+    """Small 3D analogue used by the parity tests (ragged in every dimension)."""
+    return shifted_laplacian_problem(f"lap3d_{m[0]}x{m[1]}x{m[2]}_k{k}", m, k, seed=seed)
+
+
+def random_indefinite_dense(n: int, k: int, seed: int, spread=(0.5, 4.0)):
+    """Dense Q diag(d) Q^T with exactly k negative eigenvalues.
+
+    Returns (A, V_neg[n,k], lam_neg[k], eigvals, Q).  Used only for tiny
+    dense checks of the oracle.
+    """
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    mags = rng.uniform(spread[0], spread[1], n)
+    d = mags.copy()
+    d[:k] = -mags[:k]
+    A = (Q * d) @ Q.T
+    A = 0.5 * (A + A.T)
+    return A, Q[:, :k].copy(), d[:k].copy(), d, Q
+
+
+def dense_to_csr(A: np.ndarray):
+    """CSR (int64 rowptr, int32 colind, float64 values) of the nonzeros of A."""
+    M = sp.csr_matrix(A)
+    M.sort_indices()
+    return M.indptr.astype(np.int64), M.indices.astype(np.int32), M.data.astype(np.float64)
+
+
+CONFIGS = {
+    "lap2d_64x64_k4": config1,
+    "lap3d_128^3_k10": config2,
+}

@@ -1,0 +1,298 @@
+/* Plain FP64 CPU oracle for MINRES-CG.
+ *
+ * TEST INFRASTRUCTURE ONLY: serial, unblocked, unfused, written to be checked
+ * against the paper by eye.  Each function cites the passage it follows.
+ * Nothing here is shared with, or called by, the CUDA library.
+ */
+#include "mrcg_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+static double dot(int64_t n, const double* a, const double* b) {
+  double s = 0.0;
+  for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
+  return s;
+}
+
+static double nrm2(int64_t n, const double* a) { return sqrt(dot(n, a, a)); }
+
+/* Alg. 1: products with the sparse coefficient matrix A. */
+void orc_csr_spmv(const orc_system* s, const double* x, double* y) {
+  for (int64_t i = 0; i < s->n; ++i) {
+    double acc = 0.0;
+    for (int64_t p = s->rowptr[i]; p < s->rowptr[i + 1]; ++p) acc += s->val[p] * x[s->colind[p]];
+    y[i] = acc;
+  }
+}
+
+/* Sec. 2: M_mr u = A u + 2 (V (|Lambda| (V^T u))), cost O(nnz + kn).
+ * Steps in the paper's order: t = V^T u; t <- 2|Lambda| t; out = A u + V t. */
+void orc_mmr_apply(const orc_system* s, const double* u, double* out, double* t, int64_t* flops) {
+  const int64_t n = s->n;
+  const int32_t k = s->k;
+  for (int32_t j = 0; j < k; ++j) t[j] = dot(n, s->V + (int64_t)j * n, u); /* 2n flops each */
+  for (int32_t j = 0; j < k; ++j) t[j] *= 2.0 * fabs(s->lam[j]);           /* 1 flop each: the factor 2|lam| is data */
+  for (int64_t i = 0; i < n; ++i) {
+    double acc = 0.0;
+    for (int64_t p = s->rowptr[i]; p < s->rowptr[i + 1]; ++p) acc += s->val[p] * u[s->colind[p]];
+    for (int32_t j = 0; j < k; ++j) acc += s->V[(int64_t)j * n + i] * t[j];
+    out[i] = acc;
+  }
+  if (flops) *flops += 2 * s->rowptr[n] + 4 * (int64_t)k * n + k;
+}
+
+void orc_mmr_diag(const orc_system* s, double* d) {
+  for (int64_t i = 0; i < s->n; ++i) {
+    double a = 0.0;
+    for (int64_t p = s->rowptr[i]; p < s->rowptr[i + 1]; ++p)
+      if (s->colind[p] == i) a += s->val[p];
+    for (int32_t j = 0; j < s->k; ++j) {
+      double v = s->V[(int64_t)j * s->n + i];
+      a += 2.0 * fabs(s->lam[j]) * v * v;
+    }
+    d[i] = a;
+  }
+}
+
+/* Preconditioned CG (Hestenes-Stiefel) on the SPD system M_mr z = y, Eq. 2,
+ * with M_cg = I or Jacobi.  Start z = 0, stop when ||r|| <= tol ||y||. */
+int orc_cg(const orc_system* s, int mcg, const double* y, double* z, double tol, int64_t maxit,
+           int64_t* iters, double* work) {
+  const int64_t n = s->n;
+  double* r = work;
+  double* p = work + n;
+  double* q = work + 2 * n;
+  double* sv = work + 3 * n; /* M_cg^{-1} r */
+  double* dinv = work + 4 * n;
+  double* t = work + 5 * n;
+  *iters = 0;
+  if (mcg == ORC_MCG_JACOBI) {
+    orc_mmr_diag(s, dinv);
+    for (int64_t i = 0; i < n; ++i) dinv[i] = 1.0 / dinv[i];
+  } else {
+    for (int64_t i = 0; i < n; ++i) dinv[i] = 1.0;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    z[i] = 0.0;
+    r[i] = y[i];
+    sv[i] = dinv[i] * r[i];
+    p[i] = sv[i];
+  }
+  const double ynorm = nrm2(n, y);
+  if (!isfinite(ynorm)) return ORC_ERR_NONFINITE;
+  if (ynorm == 0.0) return ORC_OK;
+  double rho = dot(n, r, sv);
+  for (int64_t it = 0; it < maxit; ++it) {
+    orc_mmr_apply(s, p, q, t, NULL);
+    const double kappa = dot(n, p, q);
+    if (!isfinite(kappa)) return ORC_ERR_NONFINITE;
+    if (kappa <= 0.0) return ORC_ERR_NOT_SPD;
+    const double alpha = rho / kappa;
+    for (int64_t i = 0; i < n; ++i) {
+      z[i] += alpha * p[i];
+      r[i] -= alpha * q[i];
+    }
+    *iters = it + 1;
+    const double rnorm = nrm2(n, r);
+    if (!isfinite(rnorm)) return ORC_ERR_NONFINITE;
+    if (rnorm <= tol * ynorm) return ORC_OK;
+    for (int64_t i = 0; i < n; ++i) sv[i] = dinv[i] * r[i];
+    const double rho_new = dot(n, r, sv);
+    const double beta = rho_new / rho;
+    rho = rho_new;
+    for (int64_t i = 0; i < n; ++i) p[i] = sv[i] + beta * p[i];
+  }
+  return ORC_ERR_MAXITER;
+}
+
+double orc_true_relres(const orc_system* s, const double* b, const double* x, double* work) {
+  orc_csr_spmv(s, x, work);
+  for (int64_t i = 0; i < s->n; ++i) work[i] = b[i] - work[i];
+  const double bn = nrm2(s->n, b);
+  return bn == 0.0 ? nrm2(s->n, work) : nrm2(s->n, work) / bn;
+}
+
+/* Preconditioned MINRES [PaiS75], the outer iteration of Alg. 1.  Lanczos in
+ * the P^{-1} inner product with unnormalised vectors v (z = P^{-1} v,
+ * gamma = sqrt(z^T v)), QR of the tridiagonal by Givens rotations, and the
+ * short recurrence for the search directions w.  Stopping test: the true
+ * relative residual (Sec. 4.2: "stop when the true relative residual is less
+ * than the tolerance"). */
+int orc_minres(const orc_system* s, const double* b, double* x, orc_prec_fn prec, void* prec_ctx,
+               double outer_tol, int32_t max_outer, int64_t max_inner_total, double restart_factor,
+               double* hist_relres, double* hist_eta, int32_t hist_cap, orc_info* info) {
+  const int64_t n = s->n;
+  memset(info, 0, sizeof(*info));
+  double* mem = (double*)calloc((size_t)(9 * n + 1), sizeof(double));
+  if (!mem) return ORC_ERR_INVALID;
+  double* v_old = mem;
+  double* v = mem + n;
+  double* v_new = mem + 2 * n;
+  double* z = mem + 3 * n;
+  double* z_new = mem + 4 * n;
+  double* w_old = mem + 5 * n;
+  double* w = mem + 6 * n;
+  double* az = mem + 7 * n; /* also used as the residual */
+  double* w_new = mem + 8 * n;
+
+  int status = ORC_ERR_MAXITER;
+  const double bnorm = nrm2(n, b);
+  if (!isfinite(bnorm)) { free(mem); info->status = ORC_ERR_NONFINITE; return ORC_ERR_NONFINITE; }
+  if (bnorm == 0.0) {
+    for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+    free(mem);
+    info->status = ORC_OK;
+    return ORC_OK;
+  }
+  /* residual of the start vector */
+  orc_csr_spmv(s, x, az);
+  for (int64_t i = 0; i < n; ++i) az[i] = b[i] - az[i];
+  double relres = nrm2(n, az) / bnorm;
+  info->true_relres = relres;
+  if (relres <= outer_tol) { free(mem); info->status = ORC_OK; return ORC_OK; }
+
+  int32_t hist_n = 0;
+  for (;;) { /* one restart cycle */
+    double cyc_relres[4096];
+    int32_t cyc_n = 0;
+    /* v_1 = b - A x0, z_1 = P^{-1} v_1, gamma_1 = sqrt(z_1^T v_1) */
+    for (int64_t i = 0; i < n; ++i) { v[i] = az[i]; v_old[i] = 0.0; w[i] = 0.0; w_old[i] = 0.0; }
+    int64_t used = 0;
+    int rc = prec(prec_ctx, n, v, z, max_inner_total - info->inner_iters_total, &used);
+    info->inner_iters_total += used;
+    info->prec_calls += 1;
+    if (rc != ORC_OK) { status = rc; goto done; }
+    double gamma2 = dot(n, z, v);
+    if (!isfinite(gamma2)) { status = ORC_ERR_NONFINITE; goto done; }
+    if (gamma2 <= 0.0) { status = ORC_ERR_BREAKDOWN; goto done; }
+    double gamma = sqrt(gamma2), gamma_old = 1.0;
+    double eta = gamma;
+    double s_old = 0.0, s_cur = 0.0, c_old = 1.0, c_cur = 1.0;
+    int restart = 0;
+    while (!restart) {
+      if (info->outer_iters >= max_outer) { status = ORC_ERR_MAXITER; goto done; }
+      /* Lanczos step */
+      for (int64_t i = 0; i < n; ++i) z[i] /= gamma;
+      orc_csr_spmv(s, z, az);
+      const double delta = dot(n, z, az);
+      for (int64_t i = 0; i < n; ++i)
+        v_new[i] = az[i] - (delta / gamma) * v[i] - (gamma / gamma_old) * v_old[i];
+      rc = prec(prec_ctx, n, v_new, z_new, max_inner_total - info->inner_iters_total, &used);
+      info->inner_iters_total += used;
+      info->prec_calls += 1;
+      if (rc != ORC_OK) { status = rc; goto done; }
+      const double gamma_new2 = dot(n, z_new, v_new);
+      if (!isfinite(gamma_new2)) { status = ORC_ERR_NONFINITE; goto done; }
+      if (gamma_new2 < 0.0) { status = ORC_ERR_BREAKDOWN; goto done; }
+      const double gamma_new = sqrt(gamma_new2);
+      /* Givens rotations on the new column of the tridiagonal */
+      const double a0 = c_cur * delta - c_old * s_cur * gamma;
+      const double a1 = sqrt(a0 * a0 + gamma_new * gamma_new);
+      const double a2 = s_cur * delta + c_old * c_cur * gamma;
+      const double a3 = s_old * gamma;
+      if (!(a1 > 0.0)) { status = ORC_ERR_BREAKDOWN; goto done; }
+      const double c_new = a0 / a1;
+      const double s_new = gamma_new / a1;
+      /* direction and solution update */
+      for (int64_t i = 0; i < n; ++i) {
+        w_new[i] = (z[i] - a3 * w_old[i] - a2 * w[i]) / a1;
+        x[i] += c_new * eta * w_new[i];
+      }
+      eta = -s_new * eta;
+      info->outer_iters += 1;
+      /* true relative residual */
+      orc_csr_spmv(s, x, az);
+      for (int64_t i = 0; i < n; ++i) az[i] = b[i] - az[i];
+      relres = nrm2(n, az) / bnorm;
+      info->true_relres = relres;
+      if (hist_n < hist_cap) {
+        if (hist_relres) hist_relres[hist_n] = relres;
+        if (hist_eta) hist_eta[hist_n] = fabs(eta);
+      }
+      hist_n++;
+      if (!isfinite(relres)) { status = ORC_ERR_NONFINITE; goto done; }
+      if (relres <= outer_tol) { status = ORC_OK; goto done; }
+      if (cyc_n < 4096) cyc_relres[cyc_n] = relres;
+      cyc_n++;
+      if (restart_factor > 0.0 && cyc_n >= 4 && cyc_n <= 4096 &&
+          relres > restart_factor * cyc_relres[cyc_n - 4])
+        restart = 1;
+      if (gamma_new == 0.0) restart = 1;
+      /* shift the recurrences */
+      double* tp;
+      tp = v_old; v_old = v; v = v_new; v_new = tp;
+      tp = z; z = z_new; z_new = tp;
+      tp = w_old; w_old = w; w = w_new; w_new = tp;
+      gamma_old = gamma; gamma = gamma_new;
+      c_old = c_cur; c_cur = c_new;
+      s_old = s_cur; s_cur = s_new;
+    }
+    info->restarts += 1; /* az holds b - A x: the next cycle starts from it */
+  }
+done:
+  info->history_len = hist_n < hist_cap ? hist_n : hist_cap;
+  info->status = status;
+  free(mem);
+  return status;
+}
+
+typedef struct {
+  const orc_system* s;
+  int mcg;
+  double tol;
+  double* work;
+} cg_ctx;
+
+static int cg_prec(void* ctx, int64_t n, const double* v, double* z, int64_t budget, int64_t* iters) {
+  (void)n;
+  cg_ctx* c = (cg_ctx*)ctx;
+  if (budget <= 0) { *iters = 0; return ORC_ERR_MAXITER; }
+  return orc_cg(c->s, c->mcg, v, z, c->tol, budget, iters, c->work);
+}
+
+/* Alg. 1: MINRES on A x = b with preconditioner M_mr, each application of
+ * M_mr^{-1} done approximately by the inner CG. */
+int orc_minres_cg(const orc_system* s, int mcg, const double* b, double* x, double outer_tol,
+                  double inner_tol, int64_t max_iters, int32_t max_outer, double restart_factor,
+                  double* hist_relres, double* hist_eta, int32_t hist_cap, orc_info* info) {
+  cg_ctx c;
+  c.s = s;
+  c.mcg = mcg;
+  c.tol = inner_tol;
+  c.work = (double*)malloc(sizeof(double) * (size_t)(5 * s->n + s->k + 1));
+  if (!c.work) return ORC_ERR_INVALID;
+  int rc = orc_minres(s, b, x, cg_prec, &c, outer_tol, max_outer, max_iters, restart_factor,
+                      hist_relres, hist_eta, hist_cap, info);
+  free(c.work);
+  return rc;
+}
+
+/* Sec. 1, 2x2 pivot blocks of the Bunch-Parlett factor: spectral
+ * decomposition with the reflector R = [[c, s], [s, -c]] and replacement of
+ * the eigenvalues by their absolute values. */
+void orc_abs_2x2(double a, double b, double c, double* out, double* eig, double* rot) {
+  double cs, sn, l1, l2;
+  if (b == 0.0) {
+    cs = 1.0; sn = 0.0; l1 = a; l2 = c;
+  } else {
+    const double mid = 0.5 * (a + c);
+    const double rad = hypot(0.5 * (a - c), b);
+    l1 = mid + rad;
+    l2 = mid - rad;
+    /* eigenvector of l1: the larger of the two row-based candidates */
+    double x1 = b, y1 = l1 - a;   /* from row 1: (a-l1) x + b y = 0 */
+    double x2 = l1 - c, y2 = b;   /* from row 2: b x + (c-l1) y = 0 */
+    double n1 = hypot(x1, y1), n2 = hypot(x2, y2);
+    if (n1 >= n2) { cs = x1 / n1; sn = y1 / n1; }
+    else { cs = x2 / n2; sn = y2 / n2; }
+  }
+  const double m1 = fabs(l1), m2 = fabs(l2);
+  /* R diag(m1, m2) R, R = [[cs, sn], [sn, -cs]] */
+  out[0] = cs * cs * m1 + sn * sn * m2;
+  out[1] = cs * sn * m1 - sn * cs * m2;
+  out[2] = sn * sn * m1 + cs * cs * m2;
+  if (eig) { eig[0] = l1; eig[1] = l2; }
+  if (rot) { rot[0] = cs; rot[1] = sn; }
+}

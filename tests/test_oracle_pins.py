@@ -1,0 +1,359 @@
+"""Pins for the FP64 CPU oracle: checks against mathematics the paper fixes.
+
+Each test pins one oracle function to something other than itself: a closed
+form, an identity from the paper, a textbook property of CG / MINRES, dense
+numpy linear algebra, or hand-derived fixtures under tests/golden/.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from gen import (config1, dense_to_csr, laplacian_csr, laplacian_smallest_eigs, random_indefinite_dense,
+                 shifted_laplacian_problem)
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def dense_system(n=40, k=3, seed=0):
+    A, Vn, lam, d, Q = random_indefinite_dense(n, k, seed)
+    rp, ci, va = dense_to_csr(A)
+    return A, Vn, lam, d, Q, O.System(rp, ci, va, Vn, lam)
+
+
+def dense_op(apply, n):
+    return np.column_stack([apply(np.eye(n)[:, i]) for i in range(n)])
+
+
+def absA(A):
+    w, Q = np.linalg.eigh(A)
+    return (Q * np.abs(w)) @ Q.T
+
+
+# ---------------------------------------------------------------- M_mr (Sec. 2)
+
+@pytest.mark.parametrize("k,seed", [(1, 1), (2, 2), (5, 3)])
+def test_mmr_equals_abs_A_for_exact_subspace(k, seed):
+    """Exact V_hat: M_mr = A + 2 V|L|V^T equals |A| = V|Lambda|V^T (Sec. 1-2)."""
+    A, Vn, lam, d, Q, s = dense_system(40, k, seed)
+    M = dense_op(s.mmr_apply, 40)
+    assert np.allclose(M, absA(A), rtol=0, atol=1e-12 * np.abs(A).max())
+    assert np.all(np.linalg.eigvalsh(0.5 * (M + M.T)) > 0)
+
+
+def test_mmr_laplacian_spectrum_is_abs():
+    """On a shifted 2D Laplacian with analytic eigenvectors, eig(M_mr) = |eig(A)|."""
+    p = shifted_laplacian_problem("t", (7, 5), 3, seed=0)
+    s = O.System.from_problem(p)
+    M = dense_op(s.mmr_apply, p.n)
+    wA = np.sort(np.abs(np.linalg.eigvalsh(p.dense())))
+    wM = np.sort(np.linalg.eigvalsh(0.5 * (M + M.T)))
+    assert np.allclose(wA, wM, atol=1e-12)
+
+
+def test_mmr_smw_inverse():
+    """Sec. 2.1: M_mr^{-1} = A^{-1} - 2 V Lambda^{-1} V^T, so M_mr applied to it is I."""
+    A, Vn, lam, d, Q, s = dense_system(30, 4, 11)
+    Minv = np.linalg.inv(A) - 2.0 * (Vn / lam) @ Vn.T
+    rng = np.random.default_rng(0)
+    for _ in range(3):
+        u = rng.standard_normal(30)
+        assert np.allclose(s.mmr_apply(Minv @ u), u, atol=1e-11)
+
+
+def test_mmr_preconditioned_spectrum_pm1():
+    """Sec. 1-2: eig(M_mr^{-1} A) are +1 and -1 only, with -1 of multiplicity k."""
+    A, Vn, lam, d, Q, s = dense_system(36, 5, 5)
+    M = dense_op(s.mmr_apply, 36)
+    ev = np.linalg.eigvals(np.linalg.solve(M, A))
+    assert np.allclose(np.abs(ev.imag), 0, atol=1e-9)
+    ev = np.sort(ev.real)
+    assert np.allclose(ev[:5], -1, atol=1e-9) and np.allclose(ev[5:], 1, atol=1e-9)
+
+
+def test_mmr_flop_count():
+    """Sec. 2: one M_mr product costs O(nnz + kn): exactly 2nnz + 4kn + k here."""
+    p = shifted_laplacian_problem("t", (9, 8), 4, seed=1)
+    s = O.System.from_problem(p)
+    _, fl = s.mmr_apply(np.ones(p.n), count_flops=True)
+    assert fl == 2 * p.nnz + 4 * p.k * p.n + p.k
+
+
+def test_mmr_diag():
+    A, Vn, lam, d, Q, s = dense_system(25, 3, 8)
+    M = dense_op(s.mmr_apply, 25)
+    assert np.allclose(s.mmr_diag(), np.diag(M), atol=1e-12)
+
+
+def test_csr_spmv_matches_dense():
+    p = shifted_laplacian_problem("t", (6, 5, 4), 2, seed=3)
+    s = O.System.from_problem(p)
+    x = np.random.default_rng(1).standard_normal(p.n)
+    assert np.allclose(s.spmv(x), p.dense() @ x, rtol=0, atol=1e-13)
+
+
+# ---------------------------------------------------------------- inner CG (Eq. 2)
+
+def _krylov_galerkin(M, y, m, Dinv=None):
+    """Textbook CG iterate: z_m in K_m(D^-1 M, D^-1 y) with M-orthogonal residual."""
+    n = len(y)
+    D = np.eye(n) if Dinv is None else np.diag(Dinv)
+    vecs = [D @ y]
+    for _ in range(m - 1):
+        vecs.append(D @ (M @ vecs[-1]))
+    K, _ = np.linalg.qr(np.column_stack(vecs))
+    c = np.linalg.solve(K.T @ M @ K, K.T @ y)
+    return K @ c
+
+
+@pytest.mark.parametrize("mcg", [O.MCG_IDENTITY, O.MCG_JACOBI])
+def test_cg_iterates_are_galerkin(mcg):
+    """Each CG iterate is the energy-norm best approximation from the Krylov space (Sec. 2)."""
+    A, Vn, lam, d, Q, s = dense_system(24, 2, 21)
+    # make diag(M_mr) non-constant so Jacobi differs from identity
+    Dsc = np.diag(np.linspace(0.5, 2.0, 24))
+    A = Dsc @ A @ Dsc
+    w, Qa = np.linalg.eigh(A)
+    Vn, lam = Qa[:, :2], w[:2]
+    assert np.all(lam < 0) and w[2] > 0
+    rp, ci, va = dense_to_csr(A)
+    s = O.System(rp, ci, va, Vn, lam)
+    M = dense_op(s.mmr_apply, 24)
+    y = np.random.default_rng(2).standard_normal(24)
+    Dinv = 1.0 / np.diag(M) if mcg == O.MCG_JACOBI else None
+    for m in range(1, 7):
+        z, it, st = s.cg(y, 1e-300, m, mcg)
+        assert it == m and st == O.ERR_MAXITER
+        zg = _krylov_galerkin(M, y, m, Dinv)
+        assert np.allclose(z, zg, rtol=0, atol=1e-9 * np.linalg.norm(zg))
+
+
+def test_cg_energy_error_monotone_and_finite_termination():
+    """Energy-norm error decreases monotonically (Sec. 2); exact after <= n steps."""
+    rp, ci, va = laplacian_csr((4, 4))  # SPD, k = 0 so M_mr = A
+    s = O.System(rp, ci, va)
+    M = dense_op(s.mmr_apply, 16)
+    y = np.random.default_rng(3).standard_normal(16)
+    zs = np.linalg.solve(M, y)
+    errs = []
+    for m in range(1, 17):
+        z, it, st = s.cg(y, 1e-300, m)
+        e = z - zs
+        errs.append(np.sqrt(e @ M @ e))
+    assert all(b <= a * (1 + 1e-12) + 1e-14 for a, b in zip(errs, errs[1:]))
+    z, it, st = s.cg(y, 1e-12, 16)
+    assert st == O.OK and it <= 16
+    assert np.linalg.norm(z - zs) <= 1e-10 * np.linalg.norm(zs)
+
+
+def test_cg_stopping_rule():
+    p = shifted_laplacian_problem("t", (10, 9), 3, seed=4)
+    s = O.System.from_problem(p)
+    y = np.random.default_rng(5).standard_normal(p.n)
+    for tol in (1e-2, 1e-6):
+        z, it, st = s.cg(y, tol, 10000)
+        assert st == O.OK
+        M = dense_op(s.mmr_apply, p.n)
+        # recursive residual drift is tiny at this size: the true residual obeys the test
+        assert np.linalg.norm(y - M @ z) <= tol * np.linalg.norm(y) * 1.01
+        z1, it1, _ = s.cg(y, tol, it - 1)
+        assert np.linalg.norm(y - M @ z1) > tol * np.linalg.norm(y)
+
+
+def test_cg_indefinite_reports_not_spd():
+    A = np.diag([-1.0, 1.0, 2.0, 3.0])
+    rp, ci, va = dense_to_csr(A)
+    s = O.System(rp, ci, va)  # k = 0: M_mr = A is indefinite
+    z, it, st = s.cg(np.array([1.0, 0, 0, 0]), 1e-8, 10)
+    assert st == O.ERR_NOT_SPD
+
+
+def test_cg_zero_rhs():
+    p = shifted_laplacian_problem("t", (5, 5), 1, seed=0)
+    s = O.System.from_problem(p)
+    z, it, st = s.cg(np.zeros(p.n), 1e-8, 10)
+    assert st == O.OK and it == 0 and not z.any()
+
+
+# ---------------------------------------------------------------- outer MINRES
+
+def test_minres_identity_prec_matches_residual_norm():
+    """P = I: MINRES minimises ||r||_2, so |eta_j| = ||b - A x_j|| and is monotone."""
+    A, Vn, lam, d, Q, s = dense_system(30, 4, 13)
+    b = np.random.default_rng(4).standard_normal(30)
+    r = O.minres(s, b, lambda v: v, outer_tol=1e-13, restart_factor=0.0)  # no restarts
+    assert r.status == O.OK and r.restarts == 0
+    bn = np.linalg.norm(b)
+    assert np.allclose(r.eta_history / bn, r.relres_history, rtol=1e-6, atol=1e-14)
+    assert np.all(np.diff(r.eta_history) <= 1e-14)
+    assert np.allclose(r.x, np.linalg.solve(A, b), atol=1e-10)
+    assert r.outer_iters <= 30 + 2
+
+
+def test_minres_spd_prec_minimises_prec_norm():
+    """SPD P: |eta_j| = ||r_j||_{P^{-1}}, and it is non-increasing."""
+    A, Vn, lam, d, Q, s = dense_system(20, 3, 17)
+    rng = np.random.default_rng(6)
+    G = rng.standard_normal((20, 20))
+    P = G @ G.T + 20 * np.eye(20)
+    b = rng.standard_normal(20)
+    Pinv = np.linalg.inv(P)
+    etas = []
+    for j in range(1, 9):
+        r = O.minres(s, b, lambda v: np.linalg.solve(P, v), outer_tol=1e-300, max_outer=j, restart_factor=0.0)
+        assert r.outer_iters == j
+        res = b - A @ r.x
+        etas.append(r.eta_history[-1])
+        assert np.isclose(r.eta_history[-1], np.sqrt(res @ Pinv @ res), rtol=1e-8)
+    assert all(b <= a * (1 + 1e-12) for a, b in zip(etas, etas[1:]))
+
+
+def test_minres_exact_mmr_converges_in_two_steps():
+    """Sec. 1-2: with the exact M_mr, M_mr^{-1}A has eigenvalues +-1: <= 2 iterations."""
+    A, Vn, lam, d, Q, s = dense_system(50, 6, 23)
+    M = dense_op(s.mmr_apply, 50)
+    L = np.linalg.cholesky(0.5 * (M + M.T))
+    prec = lambda v: np.linalg.solve(L.T, np.linalg.solve(L, v))
+    b = np.random.default_rng(7).standard_normal(50)
+    r = O.minres(s, b, prec, outer_tol=1e-12, restart_factor=0.0)
+    assert r.status == O.OK and r.outer_iters <= 2
+    assert np.allclose(r.x, np.linalg.solve(A, b), atol=1e-10)
+
+
+def test_minres_cg_dense_solution():
+    """Alg. 1 end to end on a tiny dense problem: x equals the LU solution."""
+    A, Vn, lam, d, Q, s = dense_system(60, 5, 29)
+    b = np.random.default_rng(8).standard_normal(60)
+    r = O.minres_cg(s, b, outer_tol=1e-13, inner_tol=1e-3)
+    assert r.status == O.OK
+    xs = np.linalg.solve(A, b)
+    assert np.linalg.norm(r.x - xs) <= 1e-10 * np.linalg.norm(xs)
+    assert r.true_relres <= 1e-13
+    assert np.isclose(r.true_relres, np.linalg.norm(b - A @ r.x) / np.linalg.norm(b), rtol=1e-6)
+
+
+def test_minres_cg_config1_matches_xstar():
+    """64x64 shifted Laplacian (4 negatives): x* is recovered to kappa * tol."""
+    p = config1()
+    s = O.System.from_problem(p)
+    r = O.minres_cg(s, p.b, outer_tol=1e-12, inner_tol=1e-3)
+    assert r.status == O.OK and r.true_relres <= 1e-12
+    err = np.linalg.norm(r.x - p.xstar) / np.linalg.norm(p.xstar)
+    assert err <= 1e-8
+    assert np.isclose(s.true_relres(p.b, r.x), r.true_relres, rtol=1e-9)
+    assert r.inner_iters_total > 0 and r.prec_calls == r.outer_iters + 1 + r.restarts
+
+
+def test_minres_cg_jacobi_and_k0():
+    p = shifted_laplacian_problem("t", (9, 7), 3, seed=9)
+    s = O.System.from_problem(p)
+    r = O.minres_cg(s, p.b, outer_tol=1e-12, inner_tol=1e-3, mcg=O.MCG_JACOBI)
+    assert r.status == O.OK and np.allclose(r.x, p.xstar, atol=1e-8)
+    rp, ci, va = laplacian_csr((9, 7))  # SPD, no negative eigenvalues: M_mr = A
+    s0 = O.System(rp, ci, va)
+    b = np.random.default_rng(3).standard_normal(63)
+    r0 = O.minres_cg(s0, b, outer_tol=1e-12, inner_tol=1e-3)
+    assert r0.status == O.OK
+    assert np.allclose(r0.x, np.linalg.solve(s0_dense(rp, ci, va, 63), b), atol=1e-9)
+
+
+def s0_dense(rp, ci, va, n):
+    import scipy.sparse as sp
+    return sp.csr_matrix((va, ci, rp), shape=(n, n)).toarray()
+
+
+def test_minres_cg_degenerate_inputs():
+    p = shifted_laplacian_problem("t", (8, 8), 4, seed=2)
+    s = O.System.from_problem(p)
+    r = O.minres_cg(s, np.zeros(p.n))
+    assert r.status == O.OK and not r.x.any() and r.outer_iters == 0
+    r = O.minres_cg(s, p.b, x0=p.xstar, outer_tol=1e-10)
+    assert r.status == O.OK and r.outer_iters == 0
+    r = O.minres_cg(s, p.b, outer_tol=1e-12, max_iters=5)
+    assert r.status == O.ERR_MAXITER and r.inner_iters_total <= 5
+    b = p.b.copy(); b[3] = np.nan
+    assert O.minres_cg(s, b).status == O.ERR_NONFINITE
+
+
+def test_inexact_preconditioned_spectrum_clusters():
+    """Sec. 4.2 (eigenvalue figures): P_inexact A clusters at +-1 and tightens with the inner tolerance."""
+    A, Vn, lam, d, Q, s = dense_system(40, 3, 31)
+    dist = []
+    for tol in (1e-2, 1e-4, 1e-6):
+        T = np.column_stack([s.cg(A[:, i], tol, 10000)[0] for i in range(40)])
+        ev = np.linalg.eigvals(T)
+        dd = np.minimum(np.abs(ev - 1), np.abs(ev + 1))
+        dist.append(dd.max())
+        assert np.sum(ev.real < 0) == 3
+    assert dist[0] > dist[1] > dist[2] and dist[2] < 1e-3
+
+
+# ---------------------------------------------------------------- 2x2 replacement (Sec. 1)
+
+def _golden_2x2():
+    rows = []
+    with open(os.path.join(GOLDEN, "abs_2x2.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                a, e, o = (np.array(part.split(), dtype=float) for part in line.split("|"))
+                rows.append((a, e, o))
+    return rows
+
+
+@pytest.mark.parametrize("case", _golden_2x2())
+def test_abs_2x2_golden(case):
+    (a, b, c), eig, out = case
+    B, (l1, l2), (cs, sn) = O.abs_2x2(a, b, c)
+    assert np.allclose(sorted([l1, l2]), sorted(eig), atol=1e-14)
+    assert np.allclose(B, [[out[0], out[1]], [out[1], out[2]]], atol=1e-14)
+
+
+def test_abs_2x2_closed_form_and_reflector():
+    rng = np.random.default_rng(9)
+    for _ in range(200):
+        a, b, c = rng.standard_normal(3) * rng.choice([1e-3, 1, 1e3])
+        Bt, (l1, l2), (cs, sn) = O.abs_2x2(a, b, c)
+        B = np.array([[a, b], [b, c]])
+        R = np.array([[cs, sn], [sn, -cs]])
+        assert np.isclose(cs * cs + sn * sn, 1.0)
+        assert np.allclose(R @ np.diag([l1, l2]) @ R, B, atol=1e-12 * np.abs(B).max())
+        closed = (B @ B + abs(np.linalg.det(B)) * np.eye(2)) / (abs(l1) + abs(l2))
+        assert np.allclose(Bt, closed, atol=1e-12 * np.abs(B).max())
+        # n = 2 case of the deflation: B + 2 |l_-| v_- v_-^T
+        w, Q = np.linalg.eigh(B)
+        D = B.copy()
+        for i in range(2):
+            if w[i] < 0:
+                D += 2 * abs(w[i]) * np.outer(Q[:, i], Q[:, i])
+        assert np.allclose(Bt, D, atol=1e-12 * np.abs(B).max())
+
+
+# ---------------------------------------------------------------- generators
+
+@pytest.mark.parametrize("dims,k", [((64, 64), 4), ((7, 5), 3), ((6, 5, 4), 2), ((5, 5, 5), 2), ((8, 8), 2)])
+def test_generator_inertia_and_eigenpairs(dims, k):
+    """Negative count equals k (raised past ties); V, Lambda are eigenpairs of A."""
+    p = shifted_laplacian_problem("t", dims, k, seed=0)
+    A = p.dense()
+    w = np.linalg.eigvalsh(A)
+    assert int(np.sum(w < 0)) == p.k >= k
+    assert np.allclose(np.sort(p.lam), w[: p.k], atol=1e-12)
+    assert np.abs(A @ p.V - p.V * p.lam).max() <= 1e-12
+    assert np.abs(p.V.T @ p.V - np.eye(p.k)).max() <= 1e-12
+    assert np.allclose(A @ p.xstar, p.b, atol=1e-13)
+
+
+def test_generator_tie_rounding():
+    # cube: eigenvalues come in clusters (2,1,1)x3 etc.: k = 2 must round up to 4
+    p = shifted_laplacian_problem("t", (5, 5, 5), 2, seed=0)
+    assert p.k == 4
+    ev = laplacian_smallest_eigs((64, 64), 6)
+    assert np.isclose(ev[0][0], 2 * (2 - 2 * np.cos(np.pi / 65)))
+    assert np.isclose(p.sigma, 0.5 * (laplacian_smallest_eigs((5, 5, 5), 5)[3][0] +
+                                      laplacian_smallest_eigs((5, 5, 5), 5)[4][0]))
+
+
+def test_generator_is_reproducible():
+    a, b = config1(), config1()
+    assert np.array_equal(a.b, b.b) and np.array_equal(a.V, b.V) and a.sigma == b.sigma
