@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""MINRES-CG throughput on one GB300: solves/s at true relative residual 1e-10.
+
+Workload: 3D 7-point Dirichlet Laplacian on a 128^3 grid (n = 2,097,152,
+nnz = 14,581,760) shifted midway between its 10th and 11th eigenvalues
+(k = 10 negative eigenvalues), x* = uniform[-1, 1] (seed 1), b = A x*.
+One step = one full solve from x0 = 0: outer FP64 MINRES, inner CG on
+M_mr = A + 2 V|Lambda|V^T with inner_tol 1e-3, stopping at FP64 true relative
+residual <= 1e-10.  The headline is the mixed-precision solver (FP32 inner CG,
+FP64 outer); the plain FP64 solver is measured in the same run.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs an independent replica (no data-path
+collective); value = solves of all ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "solves/s & SpMV HBM GB/s at true rel. residual 1e-10, mixed vs FP64, 1xGB300"
+WORKLOAD = "lap3d_128^3_k10: 3D 7-pt Laplacian 128^3 (n=2,097,152) shifted to 10 negative eigenvalues, 1 RHS"
+OUTER_TOL, INNER_TOL = 1e-10, 1e-3
+CPU_SAMPLE_ITERS = 120  # inner iterations of the oracle's solve timed for the CPU baseline
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws, dev):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, ws, dev):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0])); mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def full_solve_inner_iters(name):
+    path = os.path.join(ROOT, "oracle", "full_solve_counts.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        return int(rec[f"{name}|outer={OUTER_TOL:g}|inner={INNER_TOL:g}"]["inner_iters_total"])
+    except Exception:
+        return None
+
+
+def cpu_baseline(p, n_full_fallback):
+    """The oracle as it stands (serial C, FP64) on the first CPU_SAMPLE_ITERS
+    inner iterations of this workload's solve, scaled to one full solve."""
+    import oracle as O
+    s = O.System.from_problem(p)
+    t = time.perf_counter()
+    r = O.minres_cg(s, p.b, outer_tol=OUTER_TOL, inner_tol=INNER_TOL, max_iters=CPU_SAMPLE_ITERS)
+    dt = time.perf_counter() - t
+    n_full = full_solve_inner_iters(p.name) or n_full_fallback
+    frac = r.inner_iters_total / n_full
+    return {"value": frac / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {r.inner_iters_total} inner CG iterations of the FP64 oracle solve ({dt:.1f} s), "
+                      f"scaled by the {n_full} inner iterations of a full oracle solve",
+            "seconds": round(dt, 2)}
+
+
+# ------------------------------------------------------------------ reference arm (the oracle)
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    from gen import config2
+    p = config2()
+    vals = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(p, 2303)
+        if i >= args.warmup:
+            vals.append(cb["value"])
+    v = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "outer_tol": OUTER_TOL, "inner_tol": INNER_TOL,
+                       "parallelism": "rank 0 only (CPU oracle)"},
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": cb["sample"]},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    import torch
+
+    from gen import config2
+    from paper_1805_12417_gb300 import build as _b
+    _b.build()
+    import paper_1805_12417_gb300 as m
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    p = config2()
+    b_dev = torch.from_numpy(p.b).to(dev)
+    x_dev = torch.zeros(p.n, dtype=torch.float64, device=dev)
+    solvers = {prec: m.Solver.from_problem(p, precision=prec, stream=stream.cuda_stream, validate=False)
+               for prec in (m.MIXED_FP32, m.FP64)}
+
+    def run(prec, steps, warmup, clocks=False):
+        s = solvers[prec]
+        for _ in range(warmup):
+            x_dev.zero_()
+            s.solve(b_dev, x_dev, outer_tol=OUTER_TOL, inner_tol=INNER_TOL)
+        barrier(ws)
+        torch.cuda.synchronize(dev)
+        infos = []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ck = Clocks(local) if clocks else None
+        if ck:
+            ck.__enter__()
+        e0.record(stream)
+        for _ in range(steps):
+            x_dev.zero_()
+            _, info = s.solve(b_dev, x_dev, outer_tol=OUTER_TOL, inner_tol=INNER_TOL)
+            infos.append(info)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(ws)
+        if ck:
+            ck.__exit__(None, None, None)
+        ms = e0.elapsed_time(e1)
+        ms = max_over_ranks(ms, ws, dev)
+        ok = sum(1 for i in infos if i.status == m.OK and i.true_relres <= OUTER_TOL)
+        ok = sum_over_ranks(ok, ws, dev)
+        return ms, ok, infos, (ck.summary() if ck else None)
+
+    # mixed precision (headline) and plain FP64
+    ms_mx, ok_mx, inf_mx, clocks = run(m.MIXED_FP32, args.steps, args.warmup, clocks=(rank == 0))
+    ms_64, ok_64, inf_64, _ = run(m.FP64, args.steps, max(1, args.warmup))
+    value = ok_mx / (ms_mx / 1000.0)
+    fp64_value = ok_64 / (ms_64 / 1000.0)
+
+    # errors against x* (FP64 check on the host)
+    x_last = x_dev.cpu().numpy()
+    err64 = float(np.linalg.norm(x_last - p.xstar) / np.linalg.norm(p.xstar))
+    x_dev.zero_()
+    solvers[m.MIXED_FP32].solve(b_dev, x_dev, outer_tol=OUTER_TOL, inner_tol=INNER_TOL)
+    xm = x_dev.cpu().numpy()
+    errmx = float(np.linalg.norm(xm - p.xstar) / np.linalg.norm(p.xstar))
+    rr_mx = float(np.linalg.norm(p.b - p.scipy() @ xm) / np.linalg.norm(p.b))
+
+    # end to end through the C ABI with pinned host buffers (copies inside the call)
+    b_h = torch.from_numpy(p.b.copy()).pin_memory()
+    x_h = torch.zeros(p.n, dtype=torch.float64).pin_memory()
+    sm = solvers[m.MIXED_FP32]
+    x_h.zero_()
+    sm.solve(b_h, x_h, outer_tol=OUTER_TOL, inner_tol=INNER_TOL)
+    barrier(ws)
+    t0 = time.perf_counter()
+    ok_e2e = 0
+    for _ in range(args.steps):
+        x_h.zero_()
+        _, info = sm.solve(b_h, x_h, outer_tol=OUTER_TOL, inner_tol=INNER_TOL)
+        ok_e2e += int(info.status == m.OK and info.true_relres <= OUTER_TOL)
+    t_e2e = time.perf_counter() - t0
+    t_e2e = max_over_ranks(t_e2e, ws, dev)
+    ok_e2e = sum_over_ranks(ok_e2e, ws, dev)
+
+    # dominant kernel: inner-CG step a (SpMV + low-rank term + direction update + dot)
+    ta_mx, tb_mx = m.time_inner_kernels(solvers[m.MIXED_FP32].h, 50)
+    ta_64, tb_64 = m.time_inner_kernels(solvers[m.FP64].h, 50)
+    n, nnz, k = p.n, p.nnz, p.k
+
+    def bytes_a(w):  # A values + int32 indices, s and p_old read, V read, q and p_new written
+        return nnz * (w + 4) + 2 * n * w + k * n * w + 2 * n * w
+
+    def bytes_b(w):  # p, q, z, r read; z, r written; V read
+        return 6 * n * w + k * n * w
+
+    peak, peak_kind = measured_peak_gbs()
+    ach_a = bytes_a(4) / (ta_mx * 1e-3) / 1e9
+    roof = {"kernel": "cg_step_a_kernel<float,16>", "bound": "hbm", "achieved": round(ach_a, 1), "peak": peak,
+            "unit": "GB/s", "frac": round(ach_a / peak, 4), "traffic": None,
+            "peak_kind": f"{peak_kind} copy bandwidth (burst: kernel timed alone)",
+            "bytes_per_launch": bytes_a(4), "avg_ms": round(ta_mx, 5)}
+
+    kernels = {
+        "mixed": {"step_a_ms": ta_mx, "step_b_ms": tb_mx, "step_a_gbs": bytes_a(4) / (ta_mx * 1e-3) / 1e9,
+                  "step_b_gbs": bytes_b(4) / (tb_mx * 1e-3) / 1e9},
+        "fp64": {"step_a_ms": ta_64, "step_b_ms": tb_64, "step_a_gbs": bytes_a(8) / (ta_64 * 1e-3) / 1e9,
+                 "step_b_gbs": bytes_b(8) / (tb_64 * 1e-3) / 1e9},
+    }
+    launches = sum(i.kernel_launches for i in inf_mx)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(p, inf_64[-1].inner_iters_total)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_mx / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 inner CG + f64 outer MINRES", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "nnz": nnz, "k": k, "outer_tol": OUTER_TOL,
+                       "inner_tol": INNER_TOL, "precision": "mixed: FP32 inner CG, FP64 outer MINRES",
+                       "l2": "inputs larger than L2 (FP32 A 117 MB + V 84 MB + vectors per inner iteration)",
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "roofline": roof,
+            "spmv_hbm_gbs": {"mixed_step_a": round(kernels["mixed"]["step_a_gbs"], 1),
+                             "fp64_step_a": round(kernels["fp64"]["step_a_gbs"], 1), "peak": peak},
+            "kernels": {kk: {a: round(b, 5) for a, b in v.items()} for kk, v in kernels.items()},
+            "fp64": {"value": fp64_value, "unit": "solves/s", "ms_per_step": ms_64 / args.steps,
+                     "outer_iters": inf_64[-1].outer_iters, "inner_iters_total": inf_64[-1].inner_iters_total,
+                     "true_relres": inf_64[-1].true_relres, "rel_err_vs_xstar": err64},
+            "mixed": {"outer_iters": inf_mx[-1].outer_iters, "inner_iters_total": inf_mx[-1].inner_iters_total,
+                      "restarts": inf_mx[-1].restarts, "true_relres": inf_mx[-1].true_relres,
+                      "true_relres_host_fp64": rr_mx, "rel_err_vs_xstar": errmx},
+            "mixed_vs_fp64_speedup": value / fp64_value if fp64_value > 0 else None,
+            "e2e": {"value": ok_e2e / t_e2e, "unit": "solves/s", "h2d_bytes_per_step": 2 * n * 8,
+                    "d2h_bytes_per_step": n * 8},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    for s in solvers.values():
+        s.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -14,6 +14,7 @@ from .problems import (  # noqa: F401
     shifted_laplacian_problem,
     random_indefinite_dense,
     dense_to_csr,
+    random_sparse_symmetric,
     config1,
     config2,
     small_3d,

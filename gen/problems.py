@@ -216,3 +216,37 @@ CONFIGS = {
     "lap2d_64x64_k4": config1,
     "lap3d_128^3_k10": config2,
 }
+
+
+def random_sparse_symmetric(n: int, seed: int, density_rows=(0, 70), diag_shift: float = 0.0,
+                            empty_rows: int = 2):
+    """Random symmetric CSR with ragged row lengths (including empty rows).
+
+    Off-diagonal pairs are drawn per row with a row-dependent count so that
+    row lengths span density_rows; values uniform[-1, 1]; the diagonal is
+    diag_shift plus uniform[-1, 1] except on `empty_rows` rows that keep no
+    entry at all.  Used for the SpMV / M_mr product tests.
+    """
+    rng = np.random.default_rng(seed)
+    lo, hi = density_rows
+    rows, cols = [], []
+    for i in range(n):
+        cnt = int(rng.integers(lo, hi + 1)) // 2
+        if cnt:
+            js = rng.integers(0, n, cnt)
+            rows.append(np.full(cnt, i)); cols.append(js)
+    r = np.concatenate(rows) if rows else np.zeros(0, dtype=np.int64)
+    c = np.concatenate(cols) if cols else np.zeros(0, dtype=np.int64)
+    v = rng.uniform(-1, 1, len(r))
+    M = sp.coo_matrix((v, (r, c)), shape=(n, n)).tocsr()
+    M = M + M.T
+    M = M + sp.diags(diag_shift + rng.uniform(-1, 1, n))
+    M = M.tolil()
+    empties = rng.choice(n, size=min(empty_rows, n), replace=False)
+    for e in empties:
+        M[e, :] = 0
+        M[:, e] = 0
+    M = M.tocsr()
+    M.eliminate_zeros()
+    M.sort_indices()
+    return M.indptr.astype(np.int64), M.indices.astype(np.int32), M.data.astype(np.float64)

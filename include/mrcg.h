@@ -1,0 +1,151 @@
+/* mrcg.h -- C ABI of the GB300 (sm_103a) MINRES-CG solver.
+ *
+ * Method: Manguoglu & Mehrmann, "A robust iterative scheme for symmetric
+ * indefinite systems" (arXiv 1805.12417).  A x = b with A sparse, symmetric,
+ * indefinite, full rank and k << n negative eigenvalues (Sec. 1, Eq. 1) is
+ * solved by an outer preconditioned MINRES iteration whose preconditioner
+ *     M_mr = A + 2 V_hat |Lambda_hat| V_hat^T                  (Sec. 2)
+ * (V_hat: n x k basis of the negative invariant subspace, Lambda_hat: its k
+ * negative eigenvalues) is applied approximately by an inner CG solve of
+ * M_mr z = y (Eq. 2, Algorithm 1).  The solve stage is the third of the
+ * paper's three stages (Sec. 2, "In summary ..."): the caller supplies the
+ * eigenpairs (stage two); the inner preconditioner M_cg is the identity or
+ * Jacobi (stage one, see mrcg_inner_prec).
+ *
+ * Conventions for every entry point:
+ *  - Status codes are returned; nothing is thrown across the ABI.
+ *  - Vector pointers (b, x, u, y, z, ...) may be host or device memory; the
+ *    library detects which with cudaPointerGetAttributes.  Device pointers must
+ *    be on the handle's device.  Host pointers are staged through the handle's
+ *    own device buffers (copies are inside the call).
+ *  - Every call is ordered on the handle's CUDA stream and returns only when
+ *    its results are complete (host-visible status and info).
+ *  - A handle is used by one host thread at a time.
+ *  - CSR inputs: full symmetric storage, int64 row pointers (rowptr[0] = 0),
+ *    int32 column indices in [0, n), float64 values.
+ */
+#ifndef MRCG_H
+#define MRCG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mrcg_solver* mrcg_handle; /* opaque */
+
+typedef enum {
+  MRCG_OK = 0,
+  MRCG_ERR_INVALID = 1,    /* malformed arguments or inputs */
+  MRCG_ERR_NOT_SPD = 2,    /* inner CG met p^T M_mr p <= 0: M_mr is not SPD */
+  MRCG_ERR_BREAKDOWN = 3,  /* MINRES Lanczos/Givens breakdown */
+  MRCG_ERR_MAXITER = 4,    /* iteration budget exhausted; x = last iterate */
+  MRCG_ERR_NONFINITE = 5,  /* NaN/Inf met in the data or the recurrences */
+  MRCG_ERR_CUDA = 6,       /* a CUDA runtime call failed */
+  MRCG_ERR_OOM = 7         /* device allocation failed */
+} mrcg_status;
+
+/* Arithmetic of the inner CG.  The outer MINRES (Lanczos vectors, Givens
+ * rotations, residual norms, true-residual check) is always FP64. */
+typedef enum {
+  MRCG_FP64 = 0,       /* inner CG in FP64 */
+  MRCG_MIXED_FP32 = 1  /* inner CG with FP32 copies of A, V_hat and FP32 vectors */
+} mrcg_precision;
+
+/* Inner preconditioner M_cg of Algorithm 1 ("solve M_cg t = g"). */
+typedef enum {
+  MRCG_MCG_IDENTITY = 0, /* M_cg = I */
+  MRCG_MCG_JACOBI = 1    /* M_cg = diag(M_mr) */
+} mrcg_inner_prec;
+
+typedef struct {
+  int64_t n;              /* rows of A (n >= 1) */
+  int64_t nnz;            /* stored nonzeros (rowptr[n]) */
+  const int64_t* rowptr;  /* [n+1], host or device */
+  const int32_t* colind;  /* [nnz], sorted within each row */
+  const double* val;      /* [nnz] */
+  int32_t k;              /* columns of V_hat, 0 <= k <= 32 */
+  const double* V;        /* [n*k] column-major (column j at V + j*n); NULL iff k == 0 */
+  const double* lambda;   /* [k] eigenvalues of the columns of V_hat, all < 0 */
+  int32_t precision;      /* mrcg_precision */
+  int32_t inner_prec;     /* mrcg_inner_prec */
+  int32_t validate;       /* nonzero: check V^T V ~ I and ||A V - V Lambda|| at create */
+  int32_t max_outer;      /* cap on outer MINRES steps per solve; <= 0 selects 200 */
+  double restart_factor;  /* restart a MINRES cycle when relres_j > f * relres_{j-3}
+                             (j >= 4 within the cycle); 0 selects 0.5, < 0 disables */
+  void* stream;           /* cudaStream_t to order all work on; NULL = a stream of its own */
+} mrcg_create_args;
+
+typedef struct {
+  int32_t outer_iters;        /* outer MINRES steps, all cycles */
+  int32_t restarts;           /* cycles started after the first */
+  int64_t inner_iters_total;  /* inner CG iterations (M_mr products) in total */
+  int64_t prec_calls;         /* inner CG solves (applications of P) */
+  int64_t kernel_launches;    /* kernels of this library executed by the call */
+  double true_relres;        /* ||b - A x||_2 / ||b||_2 at exit, FP64 */
+  double solve_ms;            /* wall time of the call */
+  double* relres_history;     /* caller array or NULL: true relres after each outer step */
+  int32_t history_cap;        /* its capacity */
+  int32_t history_len;        /* entries written */
+  int32_t status;             /* mrcg_status of the solve */
+} mrcg_info;
+
+/* Create a solver for A with preconditioner M_mr = A + 2 V |Lambda| V^T
+ * (Sec. 2).  Every input array is deep-copied; the caller may free it when
+ * the call returns.  A is stored on the device in SELL-32 form (slices of 32
+ * rows, column-major within a slice) with FP64 values and, in mixed mode, an
+ * FP32 copy of A and V_hat.
+ * Errors: MRCG_ERR_INVALID (bad sizes, unsorted or out-of-range columns,
+ * lambda >= 0, a V_hat that fails validation), MRCG_ERR_OOM, MRCG_ERR_CUDA. */
+mrcg_status mrcg_solver_create(const mrcg_create_args* args, mrcg_handle* out);
+
+/* Solve A x = b by MINRES-CG (Algorithm 1).  On entry x holds x0, on exit the
+ * last iterate.  Stops when the FP64 true relative residual
+ * ||b - A x|| / ||b|| <= outer_tol (Sec. 4.2); each inner CG solve stops when
+ * its recursive residual falls to inner_tol times its right-hand side's norm.
+ * max_iters bounds the TOTAL inner CG iterations (the paper's "maximum
+ * (total) number of iterations", Sec. 4.1-4.2); <= 0 means no bound beyond
+ * 2^31.  info may be NULL.  Returns the solve status (MRCG_ERR_MAXITER keeps
+ * x and info valid). */
+mrcg_status mrcg_solve(mrcg_handle h, const double* b, double* x, double outer_tol, double inner_tol,
+                       int64_t max_iters, mrcg_info* info);
+
+/* y = A x in FP64 (Algorithm 1, "matrix-vector products with A"). */
+mrcg_status mrcg_apply_A(mrcg_handle h, const double* x, double* y);
+
+/* out = M_mr u = A u + 2 V (|Lambda| (V^T u))  (Sec. 2, the product procedure
+ * after the definition of M_mr), computed in the inner CG's precision: FP64,
+ * or FP32 data and accumulation in mixed mode (inputs rounded to FP32,
+ * output widened to FP64). */
+mrcg_status mrcg_apply_mmr(mrcg_handle h, const double* u, double* out);
+
+/* One application of the preconditioner: z ~ M_mr^{-1} y by the inner CG
+ * from z = 0 (Eq. 2), in the handle's precision, until
+ * ||y - M_mr z||_recursive <= inner_tol ||y|| or max_iters iterations.
+ * iters (may be NULL) receives the iteration count.  Returns MRCG_OK,
+ * MRCG_ERR_MAXITER, MRCG_ERR_NOT_SPD or MRCG_ERR_NONFINITE. */
+mrcg_status mrcg_inner_solve(mrcg_handle h, const double* y, double* z, double inner_tol, int64_t max_iters,
+                             int64_t* iters);
+
+/* Diagnostic timing of the two kernels of one inner CG iteration (Eq. 2):
+ *   ms[0]: step a  -- p = s + beta p fused into q = A p + V (2|Lambda| V^T p)
+ *          and the partial p^T q (the M_mr product of Sec. 2),
+ *   ms[1]: step b  -- z += alpha p, r -= alpha q, s = M_cg^{-1} r and the
+ *          partials r^T s, r^T r, V^T s.
+ * Each is launched `iters` times (1 <= iters <= 4096) on the handle's stream,
+ * outside the solver's graph, on a fixed synthetic right-hand side, and
+ * bracketed by CUDA events; ms receives the average duration in
+ * milliseconds.  Overwrites the handle's work vectors (not its matrix). */
+mrcg_status mrcg_time_inner_kernels(mrcg_handle h, int32_t iters, double* ms);
+
+/* Release every device and host resource of the handle (NULL is a no-op). */
+void mrcg_solver_destroy(mrcg_handle h);
+
+/* Static, human-readable name of a status code. */
+const char* mrcg_status_string(mrcg_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MRCG_H */

@@ -1,0 +1,261 @@
+"""GB300 (sm_103a) MINRES-CG for sparse symmetric indefinite systems.
+
+Thin ctypes binding of the C ABI in include/mrcg.h (same entry-point names
+without the ``mrcg_`` prefix).  It only marshals arguments: every step of the
+solve runs in the CUDA library ``libmrcg.so`` built from ``csrc/``.  There is
+no CPU fallback; loading fails loudly when the library is missing.
+
+Arrays may be numpy arrays (host memory) or CUDA torch tensors (device
+memory); the library detects which.  Device inputs must be complete before a
+call (the binding synchronises torch's current stream first).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmrcg.so")
+
+OK, ERR_INVALID, ERR_NOT_SPD, ERR_BREAKDOWN, ERR_MAXITER, ERR_NONFINITE, ERR_CUDA, ERR_OOM = range(8)
+FP64, MIXED_FP32 = 0, 1
+MCG_IDENTITY, MCG_JACOBI = 0, 1
+
+
+class CreateArgs(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("rowptr", C.c_void_p), ("colind", C.c_void_p),
+                ("val", C.c_void_p), ("k", C.c_int32), ("V", C.c_void_p), ("lambda_", C.c_void_p),
+                ("precision", C.c_int32), ("inner_prec", C.c_int32), ("validate", C.c_int32),
+                ("max_outer", C.c_int32), ("restart_factor", C.c_double), ("stream", C.c_void_p)]
+
+
+class Info(C.Structure):
+    _fields_ = [("outer_iters", C.c_int32), ("restarts", C.c_int32), ("inner_iters_total", C.c_int64),
+                ("prec_calls", C.c_int64), ("kernel_launches", C.c_int64), ("true_relres", C.c_double), ("solve_ms", C.c_double),
+                ("relres_history", C.c_void_p), ("history_cap", C.c_int32), ("history_len", C.c_int32),
+                ("status", C.c_int32)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libmrcg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                               "(run `python -c 'import __graft_entry__ as g; g.build()'`)")
+        L = C.CDLL(LIB_PATH)
+        P = C.c_void_p
+        L.mrcg_solver_create.argtypes = [C.POINTER(CreateArgs), C.POINTER(C.c_void_p)]
+        L.mrcg_solver_create.restype = C.c_int
+        L.mrcg_solve.argtypes = [P, P, P, C.c_double, C.c_double, C.c_int64, C.POINTER(Info)]
+        L.mrcg_solve.restype = C.c_int
+        L.mrcg_apply_A.argtypes = [P, P, P]
+        L.mrcg_apply_A.restype = C.c_int
+        L.mrcg_apply_mmr.argtypes = [P, P, P]
+        L.mrcg_apply_mmr.restype = C.c_int
+        L.mrcg_inner_solve.argtypes = [P, P, P, C.c_double, C.c_int64, C.POINTER(C.c_int64)]
+        L.mrcg_inner_solve.restype = C.c_int
+        L.mrcg_time_inner_kernels.argtypes = [P, C.c_int32, P]
+        L.mrcg_time_inner_kernels.restype = C.c_int
+        L.mrcg_solver_destroy.argtypes = [P]
+        L.mrcg_solver_destroy.restype = None
+        L.mrcg_status_string.argtypes = [C.c_int]
+        L.mrcg_status_string.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    """(pointer, keep-alive) for a numpy array or a torch tensor."""
+    if a is None:
+        return None, None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be contiguous")
+        return a.ctypes.data, a
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        if a.is_cuda:
+            import torch
+            torch.cuda.current_stream(a.device).synchronize()
+        return a.data_ptr(), a
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _check_dtype(a, dtype, name):
+    if isinstance(a, np.ndarray):
+        if a.dtype != dtype:
+            raise TypeError(f"{name} must be {np.dtype(dtype).name}, got {a.dtype}")
+    elif hasattr(a, "dtype"):
+        import torch
+        tmap = {np.float64: torch.float64, np.int64: torch.int64, np.int32: torch.int32}
+        if a.dtype != tmap[dtype]:
+            raise TypeError(f"{name} must be {np.dtype(dtype).name}, got {a.dtype}")
+
+
+def status_string(s: int) -> str:
+    return lib().mrcg_status_string(int(s)).decode()
+
+
+class MrcgError(RuntimeError):
+    def __init__(self, status, where):
+        super().__init__(f"{where}: {status_string(status)}")
+        self.status = status
+
+
+def solver_create(n, rowptr, colind, val, V=None, lam=None, precision=FP64, inner_prec=MCG_IDENTITY,
+                  validate=True, max_outer=0, restart_factor=0.0, stream=None) -> int:
+    """mrcg_solver_create.  V is n x k (row index = unknown); it is passed
+    column-major.  Returns the opaque handle (int)."""
+    _check_dtype(rowptr, np.int64, "rowptr"); _check_dtype(colind, np.int32, "colind")
+    _check_dtype(val, np.float64, "val")
+    keep = []
+    k = 0
+    Vp = lamp = None
+    if V is not None and lam is not None and len(lam) > 0:
+        if isinstance(V, np.ndarray):
+            V = np.asarray(V, dtype=np.float64).reshape(n, -1)
+            k = V.shape[1]
+            V = np.ascontiguousarray(V.T)
+        else:
+            k = V.shape[1]
+            V = V.t().contiguous()
+        lam = np.ascontiguousarray(lam, dtype=np.float64) if isinstance(lam, (np.ndarray, list)) else lam
+        Vp, kv = _ptr(V); lamp, kl = _ptr(lam); keep += [kv, kl]
+    rp, k1 = _ptr(rowptr); ci, k2 = _ptr(colind); va, k3 = _ptr(val)
+    keep += [k1, k2, k3]
+    a = CreateArgs(int(n), int(rowptr[-1]), rp, ci, va, k, Vp, lamp, int(precision), int(inner_prec),
+                   1 if validate else 0, int(max_outer), float(restart_factor), stream)
+    h = C.c_void_p()
+    st = lib().mrcg_solver_create(C.byref(a), C.byref(h))
+    if st != OK:
+        raise MrcgError(st, "mrcg_solver_create")
+    return h.value
+
+
+def solver_destroy(h) -> None:
+    lib().mrcg_solver_destroy(h)
+
+
+@dataclass
+class SolveInfo:
+    status: int
+    outer_iters: int
+    restarts: int
+    inner_iters_total: int
+    prec_calls: int
+    kernel_launches: int
+    true_relres: float
+    solve_ms: float
+    relres_history: np.ndarray = field(default_factory=lambda: np.zeros(0))
+
+    @property
+    def status_name(self):
+        return status_string(self.status)
+
+
+def solve(h, b, x, outer_tol=1e-10, inner_tol=1e-3, max_iters=0, history_cap=512) -> SolveInfo:
+    """mrcg_solve: x (in: x0, out: solution) is updated in place."""
+    _check_dtype(b, np.float64, "b"); _check_dtype(x, np.float64, "x")
+    hist = np.zeros(max(history_cap, 1))
+    info = Info()
+    info.relres_history = hist.ctypes.data
+    info.history_cap = history_cap
+    bp, kb = _ptr(b); xp, kx = _ptr(x)
+    st = lib().mrcg_solve(h, bp, xp, float(outer_tol), float(inner_tol), int(max_iters), C.byref(info))
+    if st in (ERR_INVALID, ERR_CUDA, ERR_OOM):
+        raise MrcgError(st, "mrcg_solve")
+    return SolveInfo(st, info.outer_iters, info.restarts, info.inner_iters_total, info.prec_calls,
+                     info.kernel_launches, info.true_relres, info.solve_ms, hist[: info.history_len].copy())
+
+
+def apply_A(h, x, y) -> None:
+    """mrcg_apply_A: y = A x."""
+    xp, kx = _ptr(x); yp, ky = _ptr(y)
+    st = lib().mrcg_apply_A(h, xp, yp)
+    if st != OK:
+        raise MrcgError(st, "mrcg_apply_A")
+
+
+def apply_mmr(h, u, out) -> None:
+    """mrcg_apply_mmr: out = M_mr u in the handle's inner precision."""
+    up, ku = _ptr(u); op, ko = _ptr(out)
+    st = lib().mrcg_apply_mmr(h, up, op)
+    if st != OK:
+        raise MrcgError(st, "mrcg_apply_mmr")
+
+
+def inner_solve(h, y, z, inner_tol=1e-3, max_iters=0):
+    """mrcg_inner_solve: z ~ M_mr^{-1} y by the inner CG.  Returns (status, iters)."""
+    yp, ky = _ptr(y); zp, kz = _ptr(z)
+    it = C.c_int64(0)
+    st = lib().mrcg_inner_solve(h, yp, zp, float(inner_tol), int(max_iters), C.byref(it))
+    if st in (ERR_INVALID, ERR_CUDA, ERR_OOM):
+        raise MrcgError(st, "mrcg_inner_solve")
+    return st, it.value
+
+
+def time_inner_kernels(h, iters=20):
+    """mrcg_time_inner_kernels: average ms of (step a, step b) of one inner CG iteration."""
+    ms = np.zeros(2)
+    st = lib().mrcg_time_inner_kernels(h, int(iters), ms.ctypes.data)
+    if st != OK:
+        raise MrcgError(st, "mrcg_time_inner_kernels")
+    return float(ms[0]), float(ms[1])
+
+
+class Solver:
+    """Owning wrapper of one handle."""
+
+    def __init__(self, n, rowptr, colind, val, V=None, lam=None, **kw):
+        self.n = int(n)
+        self.h = solver_create(n, rowptr, colind, val, V, lam, **kw)
+
+    @classmethod
+    def from_problem(cls, p, **kw):
+        return cls(p.n, p.rowptr, p.colind, p.val, p.V, p.lam, **kw)
+
+    def solve(self, b, x=None, **kw):
+        if x is None:
+            x = np.zeros(self.n) if isinstance(b, np.ndarray) else b.new_zeros(b.shape)
+        info = solve(self.h, b, x, **kw)
+        return x, info
+
+    def apply_A(self, x, y=None):
+        y = np.empty(self.n) if y is None else y
+        apply_A(self.h, x, y)
+        return y
+
+    def apply_mmr(self, u, out=None):
+        out = np.empty(self.n) if out is None else out
+        apply_mmr(self.h, u, out)
+        return out
+
+    def inner_solve(self, y, z=None, **kw):
+        z = np.empty(self.n) if z is None else z
+        st, it = inner_solve(self.h, y, z, **kw)
+        return z, st, it
+
+    def close(self):
+        if getattr(self, "h", None):
+            solver_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

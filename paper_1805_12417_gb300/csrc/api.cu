@@ -1,0 +1,626 @@
+// C ABI of the MINRES-CG solver: handle setup (SELL conversion, validation,
+// graph instantiation) and the host driver of the outer MINRES loop.
+//
+// The host takes part once per outer MINRES step: it launches the step's
+// kernels and the inner-CG graph, then reads back a ~1 KB state block (true
+// residual, status, Givens gamma) to apply the stopping and restart rules.
+// The inner CG loop itself runs entirely on the device.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "mrcg.h"
+
+using namespace mrcg;
+
+struct mrcg_solver {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int64_t n = 0, n_pad = 0, nnz = 0;
+  int k = 0;
+  bool fp32 = false;
+  int mcg = MRCG_MCG_IDENTITY;
+  int max_outer = 200;
+  double restart_factor = 0.5;
+  double lam2[kMaxK] = {};
+
+  Sell A;
+  int64_t* d_slice_ptr = nullptr;
+  int32_t* d_col = nullptr;
+  double* d_val64 = nullptr;
+  float* d_val32 = nullptr;
+  double* d_V64 = nullptr;
+  float* d_V32 = nullptr;
+  void* d_dinv = nullptr;
+  DevState* d_st = nullptr;
+  DevState* h_st = nullptr;    // pinned mirror (read back)
+  DevState* h_init = nullptr;  // pinned staging (upload)
+  double* d_partials = nullptr;
+
+  // FP64 vectors of the outer iteration (n_pad each)
+  double *x = nullptr, *b = nullptr, *res = nullptr, *zraw = nullptr, *zn = nullptr;
+  double* v[2] = {nullptr, nullptr};
+  double* w[2] = {nullptr, nullptr};
+  // inner-precision vectors
+  void *iz = nullptr, *ir = nullptr, *is = nullptr, *ip0 = nullptr, *ip1 = nullptr, *iq = nullptr;
+
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  int grid_spmv = 1, grid_stream = 1, unroll = 4;
+  OuterArgs oargs;
+  InnerGraphSpec spec;
+  std::vector<void*> allocations;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+#define CK(call)                                                                                 \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess) {                                                                     \
+      if (getenv("MRCG_DEBUG")) fprintf(stderr, "mrcg: %s failed: %s (%s:%d)\n", #call,          \
+                                        cudaGetErrorString(e_), __FILE__, __LINE__);             \
+      return e_ == cudaErrorMemoryAllocation ? MRCG_ERR_OOM : MRCG_ERR_CUDA;                     \
+    }                                                                                            \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+mrcg_status dalloc(mrcg_solver* h, T** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T) + 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return MRCG_ERR_OOM;
+  }
+  h->allocations.push_back(q);
+  *p = reinterpret_cast<T*>(q);
+  return MRCG_OK;
+}
+
+// copy `count` elements from a host or device array into a host vector
+template <typename T>
+mrcg_status fetch(const T* src, size_t count, std::vector<T>& dst) {
+  dst.resize(count);
+  if (count == 0) return MRCG_OK;
+  if (is_device_ptr(src)) {
+    CK(cudaMemcpy(dst.data(), src, count * sizeof(T), cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(dst.data(), src, count * sizeof(T));
+  }
+  return MRCG_OK;
+}
+
+// copy n doubles between a user array (host or device) and a device buffer
+mrcg_status stage_in(mrcg_solver* h, const double* user, double* dev) {
+  const cudaMemcpyKind kind = is_device_ptr(user) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CK(cudaMemcpyAsync(dev, user, (size_t)h->n * sizeof(double), kind, h->stream));
+  return MRCG_OK;
+}
+
+mrcg_status stage_out(mrcg_solver* h, const double* dev, double* user) {
+  const cudaMemcpyKind kind = is_device_ptr(user) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CK(cudaMemcpyAsync(user, dev, (size_t)h->n * sizeof(double), kind, h->stream));
+  return MRCG_OK;
+}
+
+void reset_state(mrcg_solver* h, double inner_tol, long long budget) {
+  DevState& s = *h->h_init;
+  std::memset(&s, 0, sizeof(DevState));
+  for (int l = 0; l < kMaxK; ++l) s.cg.lam2[l] = h->lam2[l];
+  s.cg.inner_tol = inner_tol;
+  s.cg.budget = budget;
+  s.cg.ctl_limit = 2;
+  s.cg.unroll = h->unroll;
+  s.out.status = MRCG_OK;
+}
+
+mrcg_status upload_state(mrcg_solver* h) {
+  CK(cudaMemcpyAsync(h->d_st, h->h_init, sizeof(DevState), cudaMemcpyHostToDevice, h->stream));
+  return MRCG_OK;
+}
+
+mrcg_status read_state(mrcg_solver* h) {
+  CK(cudaMemcpyAsync(h->h_st, h->d_st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return MRCG_OK;
+}
+
+mrcg_status lerr(cudaError_t e) {
+  if (e == cudaSuccess) return MRCG_OK;
+  if (getenv("MRCG_DEBUG")) fprintf(stderr, "mrcg: launch failed: %s\n", cudaGetErrorString(e));
+  return MRCG_ERR_CUDA;
+}
+
+#define LK(call)                          \
+  do {                                    \
+    mrcg_status s_ = lerr(call);          \
+    if (s_ != MRCG_OK) return s_;         \
+  } while (0)
+
+#define ST(call)                          \
+  do {                                    \
+    mrcg_status s_ = (call);              \
+    if (s_ != MRCG_OK) return s_;         \
+  } while (0)
+
+mrcg_status validate_subspace(const mrcg_create_args* a, const std::vector<int64_t>& rp,
+                              const std::vector<int32_t>& ci, const std::vector<double>& va,
+                              const std::vector<double>& V, const std::vector<double>& lam) {
+  const int64_t n = a->n;
+  const int k = a->k;
+  // Gram matrix V^T V ~ I
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double g = 0.0;
+      const double* vi = V.data() + (size_t)i * n;
+      const double* vj = V.data() + (size_t)j * n;
+      for (int64_t r = 0; r < n; ++r) g += vi[r] * vj[r];
+      if (std::fabs(g - (i == j ? 1.0 : 0.0)) > 1e-10) return MRCG_ERR_INVALID;
+    }
+  // ||A V - V Lambda||_F <= 1e-8 ||A||_F sqrt(k)
+  double anorm2 = 0.0;
+  for (double x : va) anorm2 += x * x;
+  double res2 = 0.0;
+  for (int j = 0; j < k; ++j) {
+    const double* vj = V.data() + (size_t)j * n;
+    for (int64_t r = 0; r < n; ++r) {
+      double s = 0.0;
+      for (int64_t p = rp[r]; p < rp[r + 1]; ++p) s += va[p] * vj[ci[p]];
+      const double d = s - lam[j] * vj[r];
+      res2 += d * d;
+    }
+  }
+  if (!(std::sqrt(res2) <= 1e-8 * std::sqrt(anorm2) * std::sqrt((double)k))) return MRCG_ERR_INVALID;
+  return MRCG_OK;
+}
+
+mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
+  const int64_t n = a->n;
+  h->n = n;
+  h->nnz = a->nnz;
+  h->k = a->k;
+  h->fp32 = a->precision == MRCG_MIXED_FP32;
+  h->mcg = a->inner_prec;
+  h->max_outer = a->max_outer > 0 ? a->max_outer : 200;
+  h->restart_factor = a->restart_factor == 0.0 ? 0.5 : a->restart_factor;
+  const int64_t nslices = (n + kSlice - 1) / kSlice;
+  const int64_t n_pad = nslices * kSlice;
+  h->n_pad = n_pad;
+
+  if (a->stream) {
+    h->stream = (cudaStream_t)a->stream;
+  } else {
+    CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    h->own_stream = true;
+  }
+
+  // ---- host copies and validation of the CSR input
+  std::vector<int64_t> rp;
+  std::vector<int32_t> ci;
+  std::vector<double> va, V, lam;
+  ST(fetch(a->rowptr, (size_t)n + 1, rp));
+  if (rp[0] != 0 || rp[n] != a->nnz) return MRCG_ERR_INVALID;
+  for (int64_t i = 0; i < n; ++i)
+    if (rp[i + 1] < rp[i]) return MRCG_ERR_INVALID;
+  ST(fetch(a->colind, (size_t)a->nnz, ci));
+  ST(fetch(a->val, (size_t)a->nnz, va));
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+      if (ci[p] < 0 || ci[p] >= n) return MRCG_ERR_INVALID;
+      if (p > rp[i] && ci[p] <= ci[p - 1]) return MRCG_ERR_INVALID;
+      if (!std::isfinite(va[p])) return MRCG_ERR_NONFINITE;
+    }
+  ST(fetch(a->lambda, (size_t)a->k, lam));
+  ST(fetch(a->V, (size_t)n * a->k, V));
+  for (int j = 0; j < a->k; ++j) {
+    if (!(lam[j] < 0.0) || !std::isfinite(lam[j])) return MRCG_ERR_INVALID;
+    h->lam2[j] = 2.0 * std::fabs(lam[j]);
+  }
+  for (double x : V)
+    if (!std::isfinite(x)) return MRCG_ERR_NONFINITE;
+  if (a->validate && a->k > 0) ST(validate_subspace(a, rp, ci, va, V, lam));
+
+  // ---- SELL-32 layout
+  std::vector<int64_t> sp((size_t)nslices + 1, 0);
+  for (int64_t s = 0; s < nslices; ++s) {
+    int64_t w = 0;
+    for (int64_t r = s * kSlice; r < std::min<int64_t>(n, (s + 1) * kSlice); ++r) w = std::max(w, rp[r + 1] - rp[r]);
+    sp[s + 1] = sp[s] + w * kSlice;
+  }
+  const int64_t total = sp[nslices];
+  ST(dalloc(h, &h->d_slice_ptr, (size_t)nslices + 1));
+  ST(dalloc(h, &h->d_col, (size_t)total));
+  ST(dalloc(h, &h->d_val64, (size_t)total));
+  if (h->fp32) ST(dalloc(h, &h->d_val32, (size_t)total));
+  CK(cudaMemcpyAsync(h->d_slice_ptr, sp.data(), sp.size() * sizeof(int64_t), cudaMemcpyHostToDevice, h->stream));
+
+  int64_t* t_rp = nullptr;
+  int32_t* t_ci = nullptr;
+  double* t_va = nullptr;
+  CK(cudaMalloc(&t_rp, rp.size() * sizeof(int64_t)));
+  CK(cudaMalloc(&t_ci, (ci.size() + 1) * sizeof(int32_t)));
+  CK(cudaMalloc(&t_va, (va.size() + 1) * sizeof(double)));
+  CK(cudaMemcpyAsync(t_rp, rp.data(), rp.size() * sizeof(int64_t), cudaMemcpyHostToDevice, h->stream));
+  if (!ci.empty()) {
+    CK(cudaMemcpyAsync(t_ci, ci.data(), ci.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(t_va, va.data(), va.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  }
+  LK(launch_sell_fill(h->stream, n, t_rp, t_ci, t_va, h->d_slice_ptr, h->d_col, h->d_val64, h->d_val32));
+
+  h->A.n = n;
+  h->A.n_pad = n_pad;
+  h->A.nslices = nslices;
+  h->A.total = total;
+  h->A.slice_ptr = h->d_slice_ptr;
+  h->A.col = h->d_col;
+  h->A.val64 = h->d_val64;
+  h->A.val32 = h->d_val32;
+
+  // ---- V_hat (n_pad rows, zero padded) and its FP32 copy
+  const size_t vcount = (size_t)n_pad * (a->k > 0 ? a->k : 1);
+  ST(dalloc(h, &h->d_V64, vcount));
+  CK(cudaMemsetAsync(h->d_V64, 0, vcount * sizeof(double), h->stream));
+  for (int j = 0; j < a->k; ++j)
+    CK(cudaMemcpyAsync(h->d_V64 + (size_t)j * n_pad, V.data() + (size_t)j * n, (size_t)n * sizeof(double),
+                       cudaMemcpyHostToDevice, h->stream));
+  if (h->fp32) {
+    ST(dalloc(h, &h->d_V32, vcount));
+    LK(launch_to_f32(h->stream, h->d_V64, h->d_V32, (int64_t)vcount));
+  }
+
+  // ---- vectors
+  double** f64[] = {&h->x, &h->b, &h->res, &h->zraw, &h->zn, &h->v[0], &h->v[1], &h->w[0], &h->w[1]};
+  for (double** p : f64) {
+    ST(dalloc(h, p, (size_t)n_pad));
+    CK(cudaMemsetAsync(*p, 0, (size_t)n_pad * sizeof(double), h->stream));
+  }
+  const size_t esz = h->fp32 ? sizeof(float) : sizeof(double);
+  void** inner[] = {&h->iz, &h->ir, &h->is, &h->ip0, &h->ip1, &h->iq};
+  for (void** p : inner) {
+    if (p == &h->is && h->mcg != MRCG_MCG_JACOBI) continue;
+    char* q = nullptr;
+    ST(dalloc(h, &q, (size_t)n_pad * esz));
+    CK(cudaMemsetAsync(q, 0, (size_t)n_pad * esz, h->stream));
+    *p = q;
+  }
+  ST(dalloc(h, &h->d_partials, (size_t)kMaxNV * kMaxBlocks));
+  ST(dalloc(h, &h->d_st, 1));
+  CK(cudaMemsetAsync(h->d_st, 0, sizeof(DevState), h->stream));
+  CK(cudaMallocHost(&h->h_st, sizeof(DevState)));
+  CK(cudaMallocHost(&h->h_init, sizeof(DevState)));
+  std::memset(h->h_st, 0, sizeof(DevState));
+
+  if (h->mcg == MRCG_MCG_JACOBI) {
+    double* d_lam2 = nullptr;
+    CK(cudaMalloc(&d_lam2, kMaxK * sizeof(double)));
+    CK(cudaMemcpyAsync(d_lam2, h->lam2, kMaxK * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    char* q = nullptr;
+    ST(dalloc(h, &q, (size_t)n_pad * esz));
+    h->d_dinv = q;
+    LK(launch_mmr_diag(h->stream, n, n_pad, t_rp, t_ci, t_va, h->d_V64, a->k, d_lam2, h->fp32, h->d_dinv));
+    CK(cudaStreamSynchronize(h->stream));
+    cudaFree(d_lam2);
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  cudaFree(t_rp);
+  cudaFree(t_ci);
+  cudaFree(t_va);
+
+  // ---- launch geometry
+  int nsm = 1;
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
+  int occ_spmv = 1, occ_stream = 1;
+  inner_occupancy(h->fp32, a->k, &occ_spmv, &occ_stream);
+  if (occ_spmv < 1) occ_spmv = 1;
+  if (occ_stream < 1) occ_stream = 1;
+  const int64_t want_spmv = (nslices + kThreads / 32 - 1) / (kThreads / 32);
+  const int64_t want_stream = (n_pad + kThreads - 1) / kThreads;
+  h->grid_spmv = (int)std::max<int64_t>(1, std::min<int64_t>({want_spmv, (int64_t)nsm * occ_spmv, kMaxBlocks}));
+  h->grid_stream =
+      (int)std::max<int64_t>(1, std::min<int64_t>({want_stream, (int64_t)nsm * occ_stream, kMaxBlocks}));
+  if (const char* u = getenv("MRCG_UNROLL")) h->unroll = std::max(2, atoi(u) & ~1);
+
+  h->oargs.st = h->d_st;
+  h->oargs.partials = h->d_partials;
+  h->oargs.A = h->A;
+  h->oargs.grid_spmv = h->grid_spmv;
+  h->oargs.grid_stream = h->grid_stream;
+  h->oargs.stream = h->stream;
+
+  // ---- inner CG graph
+  InnerGraphSpec g;
+  g.fp32 = h->fp32;
+  g.st = h->d_st;
+  g.partials = h->d_partials;
+  g.A = h->A;
+  g.V = h->fp32 ? (const void*)h->d_V32 : (const void*)h->d_V64;
+  g.k = a->k;
+  g.dinv = h->d_dinv;
+  g.z = h->iz;
+  g.r = h->ir;
+  g.s = h->is;
+  g.p0 = h->ip0;
+  g.p1 = h->ip1;
+  g.q = h->iq;
+  g.grid_spmv = h->grid_spmv;
+  g.grid_stream = h->grid_stream;
+  g.unroll = h->unroll;
+  h->spec = g;
+  CK(build_inner_graph(g, &h->graph));
+  CK(cudaGraphInstantiate(&h->graph_exec, h->graph, 0));
+  CK(cudaStreamSynchronize(h->stream));
+  return MRCG_OK;
+}
+
+void destroy_impl(mrcg_solver* h) {
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  for (void* p : h->allocations) cudaFree(p);
+  if (h->h_st) cudaFreeHost(h->h_st);
+  if (h->h_init) cudaFreeHost(h->h_init);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  cudaGetLastError();
+  delete h;
+}
+
+// run the inner-CG graph once (zout = P(vin), pointers already in the state)
+mrcg_status run_inner(mrcg_solver* h) {
+  CK(cudaGraphLaunch(h->graph_exec, h->stream));
+  return MRCG_OK;
+}
+
+mrcg_status solve_impl(mrcg_solver* h, const double* ub, double* ux, double outer_tol, double inner_tol,
+                       int64_t max_iters, mrcg_info* info) {
+  const long long budget = max_iters > 0 ? (long long)max_iters : (1LL << 31);
+  long long launches = 0, graphs = 0;
+#define LKC(call)  \
+  do {             \
+    ++launches;    \
+    LK(call);      \
+  } while (0)
+  ST(stage_in(h, ub, h->b));
+  ST(stage_in(h, ux, h->x));
+  reset_state(h, inner_tol, budget);
+  ST(upload_state(h));
+  LKC(launch_bnorm(h->oargs, h->b));
+  LKC(launch_residual(h->oargs, h->b, h->x, h->res));
+  ST(read_state(h));
+  const OuterState& O = h->h_st->out;
+
+  int32_t outer = 0, restarts = 0, hist_len = 0;
+  mrcg_status status = MRCG_ERR_MAXITER;
+  double relres = O.relres;
+  auto record = [&](double rr) {
+    if (info && info->relres_history && hist_len < info->history_cap) info->relres_history[hist_len] = rr;
+    ++hist_len;
+  };
+
+  if (O.status != MRCG_OK || !std::isfinite(O.bnorm)) {
+    status = MRCG_ERR_NONFINITE;
+  } else if (O.bnorm == 0.0) {
+    CK(cudaMemsetAsync(h->x, 0, (size_t)h->n_pad * sizeof(double), h->stream));
+    relres = 0.0;
+    status = MRCG_OK;
+  } else if (relres <= outer_tol) {
+    status = MRCG_OK;
+  } else {
+    int cur = 0;   // v[cur] = v_j, v[cur^1] = v_{j-1}; same for w
+    bool finished = false;
+    while (!finished) {
+      // ---- new cycle from the current residual
+      LKC(launch_cycle_start(h->oargs, h->res, h->v[cur], h->v[cur ^ 1], h->w[cur], h->w[cur ^ 1], h->zraw));
+      ST(run_inner(h)); graphs += 1;
+      LKC(launch_gamma_first(h->oargs, h->zraw, h->v[cur]));
+      std::vector<double> cyc;
+      for (;;) {
+        if (outer >= h->max_outer) {
+          ST(read_state(h));
+          status = h->h_st->out.status != MRCG_OK ? (mrcg_status)h->h_st->out.status : MRCG_ERR_MAXITER;
+          finished = true;
+          break;
+        }
+        const int nxt = cur ^ 1;
+        LKC(launch_lanczos_spmv(h->oargs, h->zraw, h->zn, h->res));
+        LKC(launch_lanczos_update(h->oargs, h->res, h->v[cur], h->v[nxt], h->v[nxt], h->zraw));
+        ST(run_inner(h)); graphs += 1;
+        LKC(launch_gamma_givens(h->oargs, h->zraw, h->v[nxt]));
+        LKC(launch_minres_update(h->oargs, h->zn, h->w[nxt], h->w[cur], h->w[nxt], h->x));
+        LKC(launch_residual(h->oargs, h->b, h->x, h->res));
+        ST(read_state(h));
+        if (O.status != MRCG_OK) {
+          status = (mrcg_status)O.status;
+          finished = true;
+          break;
+        }
+        ++outer;
+        relres = O.relres;
+        record(relres);
+        if (relres <= outer_tol) {
+          status = MRCG_OK;
+          finished = true;
+          break;
+        }
+        cur = nxt;
+        cyc.push_back(relres);
+        const size_t m = cyc.size();
+        bool restart = false;
+        if (h->restart_factor > 0.0 && m >= 4 && relres > h->restart_factor * cyc[m - 4]) restart = true;
+        if (O.gamma_new == 0.0) restart = true;
+        if (restart) {
+          ++restarts;
+          break;  // res holds b - A x: the next cycle starts from it
+        }
+      }
+    }
+  }
+  ST(stage_out(h, h->x, ux));
+  ST(read_state(h));
+  if (info) {
+    info->outer_iters = outer;
+    info->restarts = restarts;
+    info->inner_iters_total = h->h_st->out.inner_total;
+    info->prec_calls = h->h_st->out.prec_calls;
+    info->kernel_launches = launches + 3 * graphs + h->h_st->out.bodies * (2LL * h->unroll + 1);
+    info->true_relres = relres;
+    info->history_len = info->relres_history ? std::min(hist_len, info->history_cap) : 0;
+    info->status = status;
+  }
+  return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mrcg_status_string(mrcg_status s) {
+  switch (s) {
+    case MRCG_OK: return "MRCG_OK";
+    case MRCG_ERR_INVALID: return "MRCG_ERR_INVALID";
+    case MRCG_ERR_NOT_SPD: return "MRCG_ERR_NOT_SPD";
+    case MRCG_ERR_BREAKDOWN: return "MRCG_ERR_BREAKDOWN";
+    case MRCG_ERR_MAXITER: return "MRCG_ERR_MAXITER";
+    case MRCG_ERR_NONFINITE: return "MRCG_ERR_NONFINITE";
+    case MRCG_ERR_CUDA: return "MRCG_ERR_CUDA";
+    case MRCG_ERR_OOM: return "MRCG_ERR_OOM";
+  }
+  return "MRCG_ERR_UNKNOWN";
+}
+
+mrcg_status mrcg_solver_create(const mrcg_create_args* a, mrcg_handle* out) {
+  if (!a || !out) return MRCG_ERR_INVALID;
+  *out = nullptr;
+  if (a->n < 1 || a->n > (int64_t)0x7fffff00 || a->nnz < 0 || a->k < 0 || a->k > kMaxK) return MRCG_ERR_INVALID;
+  if (a->precision != MRCG_FP64 && a->precision != MRCG_MIXED_FP32) return MRCG_ERR_INVALID;
+  if (a->inner_prec != MRCG_MCG_IDENTITY && a->inner_prec != MRCG_MCG_JACOBI) return MRCG_ERR_INVALID;
+  if (!a->rowptr || (a->nnz > 0 && (!a->colind || !a->val))) return MRCG_ERR_INVALID;
+  if (a->k > 0 && (!a->V || !a->lambda)) return MRCG_ERR_INVALID;
+  if (std::isnan(a->restart_factor)) return MRCG_ERR_INVALID;
+  mrcg_solver* h = new (std::nothrow) mrcg_solver();
+  if (!h) return MRCG_ERR_OOM;
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    delete h;
+    return MRCG_ERR_CUDA;
+  }
+  mrcg_status s = create_impl(a, h);
+  if (s != MRCG_OK) {
+    cudaGetLastError();
+    destroy_impl(h);
+    return s;
+  }
+  *out = h;
+  return MRCG_OK;
+}
+
+void mrcg_solver_destroy(mrcg_handle h) {
+  if (!h) return;
+  DeviceGuard g(h->device);
+  destroy_impl(h);
+}
+
+mrcg_status mrcg_solve(mrcg_handle h, const double* b, double* x, double outer_tol, double inner_tol,
+                       int64_t max_iters, mrcg_info* info) {
+  if (!h || !b || !x) return MRCG_ERR_INVALID;
+  if (!(outer_tol >= 0.0) || !(inner_tol > 0.0) || !(inner_tol < 1.0)) return MRCG_ERR_INVALID;
+  if (info && info->relres_history && info->history_cap < 0) return MRCG_ERR_INVALID;
+  DeviceGuard g(h->device);
+  const auto t0 = std::chrono::steady_clock::now();
+  mrcg_status s = solve_impl(h, b, x, outer_tol, inner_tol, max_iters, info);
+  if (s == MRCG_ERR_CUDA || s == MRCG_ERR_OOM) cudaStreamSynchronize(h->stream);
+  if (info) {
+    info->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (s == MRCG_ERR_CUDA || s == MRCG_ERR_OOM) info->status = s;
+  }
+  return s;
+}
+
+mrcg_status mrcg_apply_A(mrcg_handle h, const double* x, double* y) {
+  if (!h || !x || !y) return MRCG_ERR_INVALID;
+  DeviceGuard g(h->device);
+  ST(stage_in(h, x, h->v[0]));
+  LK(launch_spmv(h->oargs, h->v[0], h->zraw));
+  ST(stage_out(h, h->zraw, y));
+  CK(cudaStreamSynchronize(h->stream));
+  return MRCG_OK;
+}
+
+mrcg_status mrcg_apply_mmr(mrcg_handle h, const double* u, double* out) {
+  if (!h || !u || !out) return MRCG_ERR_INVALID;
+  DeviceGuard g(h->device);
+  ST(stage_in(h, u, h->v[0]));
+  reset_state(h, 0.5, 0);
+  ST(upload_state(h));
+  const void* val = h->fp32 ? (const void*)h->d_val32 : (const void*)h->d_val64;
+  const void* V = h->fp32 ? (const void*)h->d_V32 : (const void*)h->d_V64;
+  LK(launch_mmr(h->oargs, h->fp32, val, V, h->k, nullptr, h->v[0], h->zraw, h->ir, h->iq));
+  ST(stage_out(h, h->zraw, out));
+  CK(cudaStreamSynchronize(h->stream));
+  return MRCG_OK;
+}
+
+mrcg_status mrcg_inner_solve(mrcg_handle h, const double* y, double* z, double inner_tol, int64_t max_iters,
+                             int64_t* iters) {
+  if (!h || !y || !z) return MRCG_ERR_INVALID;
+  if (!(inner_tol > 0.0) || !(inner_tol < 1.0)) return MRCG_ERR_INVALID;
+  DeviceGuard g(h->device);
+  ST(stage_in(h, y, h->v[0]));
+  reset_state(h, inner_tol, max_iters > 0 ? (long long)max_iters : (1LL << 31));
+  h->h_init->cg.vin = h->v[0];
+  h->h_init->cg.zout = h->zraw;
+  ST(upload_state(h));
+  ST(run_inner(h));
+  ST(stage_out(h, h->zraw, z));
+  ST(read_state(h));
+  if (iters) *iters = h->h_st->cg.iters;
+  switch (h->h_st->cg.done) {
+    case kConverged: return MRCG_OK;
+    case kNotSpd: return MRCG_ERR_NOT_SPD;
+    case kNonFinite: return MRCG_ERR_NONFINITE;
+    default: return MRCG_ERR_MAXITER;
+  }
+}
+
+mrcg_status mrcg_time_inner_kernels(mrcg_handle h, int32_t iters, double* ms) {
+  if (!h || !ms || iters < 1 || iters > 4096) return MRCG_ERR_INVALID;
+  DeviceGuard g(h->device);
+  reset_state(h, 1e-300, (long long)iters + 16);
+  h->h_init->cg.vin = h->v[0];
+  h->h_init->cg.zout = h->zraw;
+  ST(upload_state(h));
+  LK(time_inner_kernels(h->spec, iters, h->stream, h->v[0], h->n, ms));
+  ST(read_state(h));
+  if (h->h_st->cg.done != kRunning && h->h_st->cg.iters < iters) return MRCG_ERR_BREAKDOWN;
+  return MRCG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,141 @@
+// Shared definitions of the MINRES-CG CUDA library (sm_103a).
+//
+// Data layout in HBM (one solver handle):
+//   A        SELL-32: slices of 32 consecutive rows; inside a slice the j-th
+//            stored entry of every row is contiguous (col-major), so lane l of
+//            a warp reads entry j of row 32*s + l with one coalesced access.
+//            Padded entries carry value 0 and a valid column (the row itself).
+//   vectors  length n_pad = 32 * nslices, padding rows held at zero.
+//   V_hat    column-major n_pad x k (column j at V + j * n_pad).
+//   scalars  one DevState per handle: every scalar of the Krylov recurrences
+//            lives on the device, so the inner loop never waits for the host.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mrcg.h"
+
+namespace mrcg {
+
+constexpr int kSlice = 32;      // SELL slice height = warp width
+constexpr int kMaxK = 32;       // maximum columns of V_hat
+constexpr int kThreads = 256;   // block size of every streaming kernel
+constexpr int kMaxBlocks = 2048;
+constexpr int kMaxNV = kMaxK + 2;  // reduction values per block
+
+// inner CG outcome codes (CgState::done)
+enum : int { kRunning = 0, kConverged = 1, kNotSpd = 2, kNonFinite = 3, kMaxIter = 4, kLoopCap = 5 };
+
+struct CgState {
+  double rho;            // r^T s of the current residual (s = M_cg^{-1} r)
+  double alpha, beta;
+  double tol_abs;        // inner_tol * ||y_normalised||
+  double vnorm;          // ||v||: the inner solve runs on v / ||v||
+  double kappa;          // last p^T M_mr p
+  double lam2[kMaxK];    // 2 |lambda_j|
+  double c[kMaxK];       // 2 |lambda_j| (V^T p)_j for the current direction p
+  double t[kMaxK];       // (V^T p)_j for the current direction p
+  double inner_tol;      // per-call parameters (uploaded by the host)
+  long long budget;      // inner iterations still allowed (total budget)
+  long long iters;       // iterations of the current inner solve
+  long long maxit;
+  int done;
+  int ctl_count, ctl_limit;
+  int unroll;            // CG iterations per body of the device while loop
+  const double* vin;     // right-hand side of the inner solve (FP64)
+  double* zout;          // its solution (FP64)
+};
+
+struct OuterState {
+  double bnorm, relres, rnorm2;
+  double gamma, gamma_old, gamma_new;  // Lanczos normalisers gamma_j, gamma_{j-1}, gamma_{j+1}
+  double delta;
+  double eta, c, c_old, s, s_old;      // Givens state
+  double a1, a2, a3, ceta;             // coefficients of the current w / x update
+  long long inner_total;               // inner iterations of this solve
+  long long prec_calls;
+  long long bodies;                    // executed bodies of the inner while loop
+  int status;                         // mrcg_status of the solve so far
+  int pad0;
+};
+
+struct DevState {
+  CgState cg;
+  OuterState out;
+  unsigned int ticket;  // last-block ticket of the running kernel
+  unsigned int pad[3];
+};
+
+struct Sell {
+  int64_t n = 0, n_pad = 0, nslices = 0, total = 0;
+  const int64_t* slice_ptr = nullptr;  // [nslices + 1] element offsets
+  const int32_t* col = nullptr;        // [total]
+  const double* val64 = nullptr;       // [total]
+  const float* val32 = nullptr;        // [total] (mixed precision only)
+};
+
+// ------------------------------------------------------------------ device helpers
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Reduce NV per-thread values over the block and store them as this block's
+// partials, value-major: partials[i * gridDim.x + blockIdx.x].
+template <int NV>
+__device__ __forceinline__ void block_partials(double (&v)[NV], int nv, double* partials) {
+  __shared__ double sm[kThreads / 32][NV > 0 ? NV : 1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+    if (i < nv) v[i] = warp_sum(v[i]);
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+      if (i < nv) sm[warp][i] = v[i];
+  }
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) s += sm[w][threadIdx.x];
+    partials[threadIdx.x * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+// Last-block detection (no waiting): every block publishes its partials,
+// fences, and takes a ticket; the block that draws the final ticket sees all
+// partials and finishes the reduction.  It also rearms the ticket.
+__device__ __forceinline__ bool last_block(unsigned int* ticket) {
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int prev = atomicAdd(ticket, 1u);
+    is_last = (prev == gridDim.x - 1);
+    if (is_last) *ticket = 0u;
+  }
+  __syncthreads();
+  if (is_last) __threadfence();
+  return is_last;
+}
+
+// Sum the partials of nv values over all blocks in a fixed order
+// (deterministic).  Result in out[0..nv) (shared memory), valid after return.
+__device__ __forceinline__ void final_sums(const double* partials, int nv, double* out) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = warp; i < nv; i += kThreads / 32) {
+    double s = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(partials + (size_t)i * gridDim.x + b);
+    s = warp_sum(s);
+    if (lane == 0) out[i] = s;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ bool finite(double x) { return isfinite(x); }
+
+}  // namespace mrcg

@@ -1,0 +1,80 @@
+// Host-side entry points of the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace mrcg {
+
+// Everything the inner-CG graph needs.  Vector pointers are device buffers of
+// n_pad elements in the inner precision (double or float).
+struct InnerGraphSpec {
+  bool fp32 = false;
+  DevState* st = nullptr;
+  double* partials = nullptr;
+  Sell A;
+  const void* V = nullptr;     // n_pad x k, inner precision
+  int k = 0;
+  const void* dinv = nullptr;  // Jacobi: 1 / diag(M_mr) (inner precision) or nullptr
+  void* z = nullptr;
+  void* r = nullptr;
+  void* s = nullptr;
+  void* p0 = nullptr;
+  void* p1 = nullptr;
+  void* q = nullptr;
+  int grid_spmv = 1, grid_stream = 1;
+  int unroll = 4;  // CG iterations per body of the while loop (even)
+};
+
+cudaError_t build_inner_graph(const InnerGraphSpec& spec, cudaGraph_t* graph);
+// standalone launches of the two CG iteration kernels, timed with events
+cudaError_t time_inner_kernels(const InnerGraphSpec& spec, int iters, cudaStream_t stream, double* vin, int64_t n,
+                               double* ms);
+void inner_occupancy(bool fp32, int k, int* spmv_blocks_per_sm, int* stream_blocks_per_sm);
+
+// ---- outer MINRES kernels (FP64), launched on `stream` ----
+struct OuterArgs {
+  DevState* st;
+  double* partials;
+  Sell A;
+  int grid_spmv, grid_stream;
+  cudaStream_t stream;
+};
+
+// y = A x (FP64 SELL)
+cudaError_t launch_spmv(const OuterArgs& a, const double* x, double* y);
+// out = M_mr u in FP64 or FP32 (inner precision data, rounding u to T)
+cudaError_t launch_mmr(const OuterArgs& a, bool fp32, const void* val, const void* V, int k, const double* lam2,
+                       const double* u, double* out, void* tmp_in, void* tmp_out);
+// O.bnorm = ||b||
+cudaError_t launch_bnorm(const OuterArgs& a, const double* b);
+// res = b - A x ; O.rnorm2, O.relres = ||res|| / O.bnorm
+cudaError_t launch_residual(const OuterArgs& a, const double* b, const double* x, double* res);
+// cycle start: v_cur = res, v_prev = w_prev = w_cur = 0, cg.vin = v_cur, cg.zout = zraw
+cudaError_t launch_cycle_start(const OuterArgs& a, const double* res, double* v_cur, double* v_prev, double* w_cur,
+                               double* w_prev, double* zraw);
+// gamma_1 = sqrt(z^T v) and the Givens state of a new cycle
+cudaError_t launch_gamma_first(const OuterArgs& a, const double* zraw, const double* v);
+// zn = zraw / gamma ; az = A zn ; O.delta = zn^T az
+cudaError_t launch_lanczos_spmv(const OuterArgs& a, const double* zraw, double* zn, double* az);
+// v_new = az - (delta/gamma) v - (gamma/gamma_old) v_old ; cg.vin = v_new ; cg.zout = zraw
+cudaError_t launch_lanczos_update(const OuterArgs& a, const double* az, const double* v, const double* v_old,
+                                  double* v_new, double* zraw);
+// gamma_{j+1} = sqrt(z^T v_new) and the Givens rotation of step j
+cudaError_t launch_gamma_givens(const OuterArgs& a, const double* zraw, const double* v_new);
+// w_new = (zn - a3 w_old - a2 w) / a1 ; x += c eta w_new
+cudaError_t launch_minres_update(const OuterArgs& a, const double* zn, const double* w_old, const double* w,
+                                 double* w_new, double* x);
+// diag(M_mr) from CSR (device arrays) into d (n entries), and 1/d in T (n_pad entries)
+cudaError_t launch_mmr_diag(cudaStream_t stream, int64_t n, int64_t n_pad, const int64_t* rowptr,
+                            const int32_t* colind, const double* val, const double* V64, int k, const double* lam2,
+                            bool fp32, void* dinv);
+// SELL construction on the device from CSR (device arrays)
+cudaError_t launch_sell_fill(cudaStream_t stream, int64_t n, const int64_t* rowptr, const int32_t* colind,
+                             const double* val, const int64_t* slice_ptr, int32_t* col, double* val64, float* val32);
+// elementwise conversions
+cudaError_t launch_to_f32(cudaStream_t stream, const double* in, float* out, int64_t n);
+cudaError_t launch_to_f64(cudaStream_t stream, const float* in, double* out, int64_t n);
+
+}  // namespace mrcg

@@ -1,0 +1,273 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Bars (from the arithmetic):
+  * SpMV with A (FP64): same summation order as the CSR oracle; only FMA
+    contraction differs, so |y_gpu - y_oracle| <= 1e-14 * (|A| |x|)_i.
+  * M_mr product: FP64 within 1e-13 relative to (|A||u| + |V|t|)_i scale;
+    FP32 mode within 2e-6 relative (FP32 data and accumulation).
+  * Full solve (FP64): relative solution error vs the oracle <= 1e-8 and true
+    relative residual <= 1e-10, run at outer_tol 1e-12 so that the kappa(A)
+    amplification of the residual stays below the error bar.
+  * Mixed precision: true relative residual (recomputed in FP64 on the host)
+    <= the outer tolerance; error vs the oracle stated and bounded by
+    kappa(A) * tol.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from gen import (config1, config2, dense_to_csr, laplacian_csr, random_sparse_symmetric, shifted_laplacian_problem,
+                 small_3d)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU hosts too
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1805_12417_gb300 as m  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def cu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def host_relres(p, x):
+    return np.linalg.norm(p.b - p.scipy() @ x) / np.linalg.norm(p.b)
+
+
+# ------------------------------------------------------------------ SpMV / M_mr product
+
+@pytest.mark.parametrize("n,seed", [(1, 0), (31, 1), (32, 2), (33, 3), (1000, 4), (4099, 5)])
+def test_apply_A_ragged_rows(n, seed):
+    """Row lengths 0..70 (empty rows included), n around the slice height."""
+    rp, ci, va = random_sparse_symmetric(n, seed)
+    if len(va) == 0:
+        rp, ci, va = dense_to_csr(np.eye(n))
+    s = O.System(rp, ci, va)
+    x = np.random.default_rng(seed).standard_normal(n)
+    absA = O.System(rp, ci, np.abs(va))
+    with m.Solver(n, rp, ci, va) as g:
+        y = g.apply_A(x)
+        yd = torch.empty(n, dtype=torch.float64, device=DEV)
+        g.apply_A(cu(x), yd)
+    ref = s.spmv(x)
+    scale = absA.spmv(np.abs(x)) + 1e-300
+    assert np.all(np.abs(y - ref) <= 1e-14 * scale)
+    assert np.array_equal(yd.cpu().numpy(), y)
+
+
+@pytest.mark.parametrize("k", [1, 7, 8, 9, 16, 17, 32])
+def test_apply_mmr_fp64_all_k_buckets(k):
+    p = shifted_laplacian_problem("t", (13, 11, 9), k, seed=k)
+    s = O.System.from_problem(p)
+    u = np.random.default_rng(k).standard_normal(p.n)
+    ref = s.mmr_apply(u)
+    with m.Solver.from_problem(p) as g:
+        out = g.apply_mmr(u)
+    assert np.abs(out - ref).max() <= 1e-13 * np.abs(ref).max() * 10
+
+
+def test_apply_mmr_fp32():
+    p = small_3d()
+    s = O.System.from_problem(p)
+    u = np.random.default_rng(3).standard_normal(p.n)
+    ref = s.mmr_apply(u)
+    with m.Solver.from_problem(p, precision=m.MIXED_FP32) as g:
+        out = g.apply_mmr(u)
+    assert np.abs(out - ref).max() <= 2e-6 * np.abs(ref).max()
+
+
+def test_apply_mmr_k0_is_A():
+    rp, ci, va = laplacian_csr((17, 9))
+    x = np.random.default_rng(0).standard_normal(153)
+    with m.Solver(153, rp, ci, va) as g:
+        assert np.allclose(g.apply_mmr(x), g.apply_A(x), rtol=0, atol=1e-14)
+
+
+# ------------------------------------------------------------------ inner CG
+
+@pytest.mark.parametrize("mcg", [m.MCG_IDENTITY, m.MCG_JACOBI])
+@pytest.mark.parametrize("tol", [1e-2, 1e-6])
+def test_inner_solve_matches_oracle_cg(mcg, tol):
+    p = small_3d()
+    s = O.System.from_problem(p)
+    y = np.random.default_rng(4).standard_normal(p.n)
+    zr, itr, str_ = s.cg(y, tol, 100000, mcg)
+    assert str_ == O.OK
+    with m.Solver.from_problem(p, inner_prec=mcg) as g:
+        z, st, it = g.inner_solve(y, inner_tol=tol)
+    assert st == m.OK
+    assert abs(it - itr) <= 1
+    assert np.linalg.norm(z - zr) <= 1e-8 * np.linalg.norm(zr)
+    M = lambda v: s.mmr_apply(v)  # noqa: E731
+    assert np.linalg.norm(y - M(z)) <= tol * np.linalg.norm(y) * 1.001
+
+
+def test_inner_solve_fp32_residual():
+    p = small_3d()
+    s = O.System.from_problem(p)
+    y = np.random.default_rng(5).standard_normal(p.n)
+    with m.Solver.from_problem(p, precision=m.MIXED_FP32) as g:
+        z, st, it = g.inner_solve(y, inner_tol=1e-4)
+    assert st == m.OK and it > 0
+    assert np.linalg.norm(y - s.mmr_apply(z)) <= 1.5e-4 * np.linalg.norm(y)
+
+
+def test_inner_solve_budget_and_zero_rhs():
+    p = small_3d()
+    with m.Solver.from_problem(p) as g:
+        z, st, it = g.inner_solve(np.random.default_rng(0).standard_normal(p.n), inner_tol=1e-12, max_iters=5)
+        assert st == m.ERR_MAXITER and it == 5
+        z, st, it = g.inner_solve(np.zeros(p.n), inner_tol=1e-6)
+        assert st == m.OK and it == 0 and not z.any()
+
+
+def test_inner_solve_not_spd():
+    A = np.diag([-1.0] + [1.0] * 40)
+    rp, ci, va = dense_to_csr(A)
+    with m.Solver(41, rp, ci, va) as g:  # k = 0: M_mr = A is indefinite
+        y = np.zeros(41); y[0] = 1.0
+        z, st, it = g.inner_solve(y, inner_tol=1e-8)
+    assert st == m.ERR_NOT_SPD
+
+
+# ------------------------------------------------------------------ full solves
+
+def _solve_both(p, prec=m.FP64, mcg=m.MCG_IDENTITY, outer_tol=1e-12, inner_tol=1e-3, device=True):
+    ref = O.minres_cg(O.System.from_problem(p), p.b, outer_tol=outer_tol, inner_tol=inner_tol,
+                      mcg=O.MCG_JACOBI if mcg == m.MCG_JACOBI else O.MCG_IDENTITY)
+    with m.Solver.from_problem(p, precision=prec, inner_prec=mcg) as g:
+        if device:
+            x = torch.zeros(p.n, dtype=torch.float64, device=DEV)
+            _, info = g.solve(cu(p.b), x, outer_tol=outer_tol, inner_tol=inner_tol)
+            x = x.cpu().numpy()
+        else:
+            x, info = g.solve(p.b.copy(), outer_tol=outer_tol, inner_tol=inner_tol)
+    return ref, x, info
+
+
+@pytest.mark.parametrize("prob", [config1, small_3d, lambda: shifted_laplacian_problem("t", (45, 37), 6, seed=11)],
+                         ids=["lap2d_64x64_k4", "lap3d_12x11x10_k5", "lap2d_45x37_k6"])
+@pytest.mark.parametrize("device", [True, False], ids=["device_ptrs", "host_ptrs"])
+def test_solve_fp64_matches_oracle(prob, device):
+    p = prob()
+    ref, x, info = _solve_both(p, device=device)
+    assert ref.status == O.OK and info.status == m.OK
+    err = np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x)
+    assert err <= 1e-8
+    assert host_relres(p, x) <= 1e-10
+    assert info.true_relres <= 1e-12
+    assert np.isclose(info.true_relres, host_relres(p, x), rtol=1e-6, atol=1e-15)
+    assert np.linalg.norm(x - p.xstar) / np.linalg.norm(p.xstar) <= 1e-8
+    # same method, same rules: outer counts agree up to rounding-level drift
+    assert abs(info.outer_iters - ref.outer_iters) <= 2
+    assert len(info.relres_history) == info.outer_iters
+
+
+def test_solve_jacobi_matches_oracle():
+    p = shifted_laplacian_problem("t", (30, 29), 5, seed=12)
+    ref, x, info = _solve_both(p, mcg=m.MCG_JACOBI)
+    assert info.status == m.OK
+    assert np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x) <= 1e-8
+
+
+def test_solve_mixed_reaches_fp64_residual():
+    p = config1()
+    ref, x, info = _solve_both(p, prec=m.MIXED_FP32, outer_tol=1e-10)
+    assert info.status == m.OK
+    rr = host_relres(p, x)
+    assert rr <= 1e-10
+    err = np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x)
+    assert err <= p.meta["cond"] * 1e-10 * 3
+
+
+def test_solve_is_deterministic():
+    p = small_3d()
+    with m.Solver.from_problem(p) as g:
+        x1, i1 = g.solve(p.b.copy(), outer_tol=1e-11)
+        x2, i2 = g.solve(p.b.copy(), outer_tol=1e-11)
+    assert np.array_equal(x1, x2) and i1.inner_iters_total == i2.inner_iters_total
+
+
+def test_solve_edge_cases():
+    p = small_3d()
+    with m.Solver.from_problem(p) as g:
+        x, info = g.solve(np.zeros(p.n))
+        assert info.status == m.OK and not x.any() and info.outer_iters == 0
+        x, info = g.solve(p.b.copy(), x=p.xstar.copy(), outer_tol=1e-10)
+        assert info.status == m.OK and info.outer_iters == 0
+        x, info = g.solve(p.b.copy(), outer_tol=1e-12, max_iters=7)
+        assert info.status == m.ERR_MAXITER and info.inner_iters_total <= 7
+        ref = O.minres_cg(O.System.from_problem(p), p.b, outer_tol=1e-12, max_iters=7)
+        assert ref.status == O.ERR_MAXITER and ref.inner_iters_total == info.inner_iters_total
+        b = p.b.copy(); b[5] = np.nan
+        x, info = g.solve(b)
+        assert info.status == m.ERR_NONFINITE
+
+
+def test_solve_k0_spd():
+    rp, ci, va = laplacian_csr((21, 19))
+    n = 21 * 19
+    b = np.random.default_rng(1).standard_normal(n)
+    s = O.System(rp, ci, va)
+    ref = O.minres_cg(s, b, outer_tol=1e-12)
+    with m.Solver(n, rp, ci, va) as g:
+        x, info = g.solve(b.copy(), outer_tol=1e-12)
+    assert info.status == m.OK
+    assert np.linalg.norm(x - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
+
+
+def test_create_rejects_bad_inputs():
+    p = small_3d()
+    ci = p.colind.copy(); ci[10], ci[11] = ci[11], ci[10]
+    with pytest.raises(m.MrcgError):
+        m.Solver(p.n, p.rowptr, ci, p.val, p.V, p.lam)
+    ci = p.colind.copy(); ci[3] = p.n
+    with pytest.raises(m.MrcgError):
+        m.Solver(p.n, p.rowptr, ci, p.val, p.V, p.lam)
+    with pytest.raises(m.MrcgError):
+        m.Solver(p.n, p.rowptr, p.colind, p.val, p.V, -p.lam)       # lambda must be negative
+    V = p.V.copy(); V[:, 0] *= 1.01
+    with pytest.raises(m.MrcgError):
+        m.Solver(p.n, p.rowptr, p.colind, p.val, V, p.lam)          # fails V^T V ~ I
+    V = np.roll(p.V, 1, axis=1)
+    with pytest.raises(m.MrcgError):
+        m.Solver(p.n, p.rowptr, p.colind, p.val, V, p.lam)          # fails A V ~ V Lambda
+
+
+# ------------------------------------------------------------------ full size (bench workload)
+
+@pytest.fixture(scope="module")
+def big():
+    return config2()
+
+
+def test_full_size_mmr_and_spmv(big):
+    p = big
+    s = O.System.from_problem(p)
+    u = np.random.default_rng(9).standard_normal(p.n)
+    with m.Solver.from_problem(p) as g:
+        out = g.apply_mmr(u)
+        y = g.apply_A(u)
+    assert np.abs(y - s.spmv(u)).max() <= 1e-13
+    ref = s.mmr_apply(u)
+    assert np.abs(out - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("prec", [m.FP64, m.MIXED_FP32], ids=["fp64", "mixed"])
+def test_full_size_solve(big, prec):
+    """128^3 shifted Laplacian at the benchmark tolerance: the true residual is
+    recomputed here in FP64 and x is checked against x* within kappa * tol."""
+    p = big
+    with m.Solver.from_problem(p, precision=prec) as g:
+        x = torch.zeros(p.n, dtype=torch.float64, device=DEV)
+        _, info = g.solve(cu(p.b), x, outer_tol=1e-10, inner_tol=1e-3)
+    x = x.cpu().numpy()
+    assert info.status == m.OK
+    s = O.System.from_problem(p)
+    rr = s.true_relres(p.b, x)
+    assert rr <= 1e-10
+    assert np.linalg.norm(x - p.xstar) / np.linalg.norm(p.xstar) <= p.meta["cond"] * 1e-10 * 3
