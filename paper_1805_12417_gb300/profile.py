@@ -1,0 +1,43 @@
+"""Small profiling driver: launch the inner-CG iteration kernels on a workload.
+
+Creates a solver for a generated workload and runs `--iters` standalone
+launches of each inner-CG kernel (step a, step b) through
+mrcg_time_inner_kernels, printing their CUDA-event times.  Few other kernels
+run before them (setup only), which keeps an ncu capture of them small:
+
+  python -m paper_1805_12417_gb300.profile --workload lap3d_128 --precision mixed --iters 3
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def workload(name):
+    from gen import config1, config2, small_3d
+    return {"lap3d_128": config2, "lap2d_64": config1, "lap3d_small": small_3d}[name]()
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="lap3d_128", choices=["lap3d_128", "lap2d_64", "lap3d_small"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--iters", type=int, default=3)
+    a = ap.parse_args(argv)
+    import paper_1805_12417_gb300 as m
+    p = workload(a.workload)
+    prec = m.MIXED_FP32 if a.precision == "mixed" else m.FP64
+    with m.Solver.from_problem(p, precision=prec, validate=False) as s:
+        ta, tb = m.time_inner_kernels(s.h, a.iters)
+    print(json.dumps({"workload": p.name, "precision": a.precision, "iters": a.iters, "step_a_ms": ta,
+                      "step_b_ms": tb}))
+
+
+if __name__ == "__main__":
+    main()
