@@ -139,6 +139,31 @@ mrcg_status mrcg_inner_solve(mrcg_handle h, const double* y, double* z, double i
  * milliseconds.  Overwrites the handle's work vectors (not its matrix). */
 mrcg_status mrcg_time_inner_kernels(mrcg_handle h, int32_t iters, double* ms);
 
+/* Allocation-free M_mr product: out = A u + 2 V (|Lambda| (V^T u)) in FP64.
+ * The paper has no counterpart; this entry point exists for callers that
+ * cannot call cudaMalloc at all (code running inside another framework's
+ * fixed memory pool, plugins whose host forbids device allocations after
+ * start-up, paths that must not take the allocator's locks).  It needs no
+ * handle: the caller passes DEVICE arrays -- CSR A (rowptr[n+1], colind[nnz],
+ * val[nnz], same rules as mrcg_create_args), V (n x k column-major, k <= 32),
+ * lambda[k], u[n] and out[n] -- and the only scratch is a fixed 262,656-byte
+ * static device array inside the library, which every GPU that loads the
+ * library keeps until the process exits.  Nothing is allocated or freed.
+ *  - The first call on a device looks up that array's device address
+ *    (cudaGetSymbolAddress, with that device current); make the first call on
+ *    each device before any stream capture.
+ *  - Work is enqueued on `stream` (NULL = the default stream) and the call
+ *    returns without waiting; out is complete when the stream reaches it.
+ *  - All calls share the one scratch array and each call rewrites it (a
+ *    counter is cleared at the start of each call): calls that can overlap on
+ *    the GPU (different streams, several host threads) race and must be
+ *    serialised by the caller.
+ * Errors: MRCG_ERR_INVALID for n < 1, n > 2^31-1, k < 0, k > 32 or NULL
+ * arrays; MRCG_ERR_CUDA if the address lookup or a launch fails. */
+mrcg_status mrcg_mmr_apply_noalloc(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val,
+                                   int32_t k, const double* V, const double* lambda, const double* u, double* out,
+                                   void* stream);
+
 /* Release every device and host resource of the handle (NULL is a no-op). */
 void mrcg_solver_destroy(mrcg_handle h);
 
