@@ -54,7 +54,8 @@ struct mrcg_solver {
 
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
-  int grid_spmv = 1, grid_stream = 1, unroll = 4;
+  int grid_spmv = 1, grid_stream = 1, grid_stream_b = 1, unroll = 4;
+  bool host_loop = false;  // MRCG_INNER_LOOP=host: inner loop driven from the host (for profilers)
   OuterArgs oargs;
   InnerGraphSpec spec;
   std::vector<void*> allocations;
@@ -343,12 +344,21 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
   inner_occupancy(h->fp32, a->k, &occ_spmv, &occ_stream);
   if (occ_spmv < 1) occ_spmv = 1;
   if (occ_stream < 1) occ_stream = 1;
+  // blocks per SM of the two CG kernels: the occupancy limit, optionally
+  // capped (MRCG_BPSM_A / MRCG_BPSM_B) for launch-shape sweeps
+  if (const char* e = getenv("MRCG_BPSM_A")) occ_spmv = std::max(1, std::min(occ_spmv, atoi(e)));
+  int occ_b = occ_stream;
+  if (const char* e = getenv("MRCG_BPSM_B")) occ_b = std::max(1, std::min(occ_stream, atoi(e)));
+  const int vec_w = h->fp32 ? 4 : 2;  // elements per 16-byte access in step b
   const int64_t want_spmv = (nslices + kThreads / 32 - 1) / (kThreads / 32);
   const int64_t want_stream = (n_pad + kThreads - 1) / kThreads;
+  const int64_t want_b = (n_pad / vec_w + kThreads - 1) / kThreads;
   h->grid_spmv = (int)std::max<int64_t>(1, std::min<int64_t>({want_spmv, (int64_t)nsm * occ_spmv, kMaxBlocks}));
   h->grid_stream =
       (int)std::max<int64_t>(1, std::min<int64_t>({want_stream, (int64_t)nsm * occ_stream, kMaxBlocks}));
+  h->grid_stream_b = (int)std::max<int64_t>(1, std::min<int64_t>({want_b, (int64_t)nsm * occ_b, kMaxBlocks}));
   if (const char* u = getenv("MRCG_UNROLL")) h->unroll = std::max(2, atoi(u) & ~1);
+  if (const char* m = getenv("MRCG_INNER_LOOP")) h->host_loop = std::strcmp(m, "host") == 0;
 
   h->oargs.st = h->d_st;
   h->oargs.partials = h->d_partials;
@@ -374,6 +384,7 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
   g.q = h->iq;
   g.grid_spmv = h->grid_spmv;
   g.grid_stream = h->grid_stream;
+  g.grid_stream_b = h->grid_stream_b;
   g.unroll = h->unroll;
   h->spec = g;
   CK(build_inner_graph(g, &h->graph));
@@ -396,6 +407,10 @@ void destroy_impl(mrcg_solver* h) {
 
 // run the inner-CG graph once (zout = P(vin), pointers already in the state)
 mrcg_status run_inner(mrcg_solver* h) {
+  if (h->host_loop) {
+    CK(run_inner_host(h->spec, h->stream, &h->h_st->cg.done));
+    return MRCG_OK;
+  }
   CK(cudaGraphLaunch(h->graph_exec, h->stream));
   return MRCG_OK;
 }

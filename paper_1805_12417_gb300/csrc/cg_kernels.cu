@@ -6,17 +6,21 @@
 //           (the direction update is fused into the SpMV gathers, so p' is
 //           never re-read; c = 2|Lambda| (V^T p') arrives as scalars)
 //   step_b: z += alpha p' ; r -= alpha q ; s = M_cg^{-1} r ;
-//           partials r^T s, r^T r, V^T s
+//           partials r^T s, V^T s (and r^T r when M_cg is Jacobi)
 // V^T p' for the next step follows from V^T p' = V^T s + beta V^T p, so the
 // paper's two passes over V_hat per M_mr product (V^T u, then V t) stay two
 // and no third kernel is needed.  All scalar recurrences (alpha, beta, the
-// stopping test) run in FP64 in the last block of each kernel.
+// stopping test) run in FP64 in the last block of each kernel, which also
+// publishes FP32 copies for the FP32 kernels.  Per-thread sums and the block
+// reductions run in the kernel's own precision (FP32 in mixed mode), the
+// cross-block sum in FP64.
 //
 // The whole preconditioner application is one CUDA graph:
 //   norm(v) -> init -> while(not done) { U x (step_a, step_b), ctl } -> finish
 // The while loop is a conditional graph node: the inner iteration never
 // returns to the host.
 #include <cstdio>
+#include <cstring>
 #include <vector>
 
 #include "common.cuh"
@@ -47,9 +51,58 @@ struct CgArgs {
   T* q;
 };
 
+// ------------------------------------------------------------------ small helpers
+
 template <typename T>
 __device__ __forceinline__ T ld_stream(const T* p) {
   return __ldcs(p);
+}
+
+template <typename T>
+struct V16;
+template <>
+struct V16<float> {
+  using type = float4;
+  static constexpr int W = 4;
+};
+template <>
+struct V16<double> {
+  using type = double2;
+  static constexpr int W = 2;
+};
+
+// 16-byte vector load / store into a register array
+template <typename T>
+__device__ __forceinline__ void ld16(const T* p, T (&x)[V16<T>::W]) {
+  const typename V16<T>::type v = *reinterpret_cast<const typename V16<T>::type*>(p);
+  memcpy(x, &v, 16);
+}
+template <typename T>
+__device__ __forceinline__ void ld16_stream(const T* p, T (&x)[V16<T>::W]) {
+  const typename V16<T>::type v = __ldcs(reinterpret_cast<const typename V16<T>::type*>(p));
+  memcpy(x, &v, 16);
+}
+template <typename T>
+__device__ __forceinline__ void st16(T* p, const T (&x)[V16<T>::W]) {
+  typename V16<T>::type v;
+  memcpy(&v, x, 16);
+  *reinterpret_cast<typename V16<T>::type*>(p) = v;
+}
+
+// broadcast scalars in the kernel's precision
+__device__ __forceinline__ float alpha_of(const CgState& S, float) { return S.alpha32; }
+__device__ __forceinline__ double alpha_of(const CgState& S, double) { return S.alpha; }
+__device__ __forceinline__ float beta_of(const CgState& S, float) { return S.beta32; }
+__device__ __forceinline__ double beta_of(const CgState& S, double) { return S.beta; }
+__device__ __forceinline__ float c_of(const CgState& S, int l, float) { return S.c32[l]; }
+__device__ __forceinline__ double c_of(const CgState& S, int l, double) { return S.c[l]; }
+
+// set c = 2|lambda| t (FP64 and FP32 copies)
+__device__ __forceinline__ void publish_c(CgState& S, int k) {
+  for (int l = 0; l < k; ++l) {
+    S.c[l] = S.lam2[l] * S.t[l];
+    S.c32[l] = (float)S.c[l];
+  }
 }
 
 // ------------------------------------------------------------------ norm of v
@@ -70,47 +123,84 @@ __global__ void __launch_bounds__(kThreads) cg_vnorm_kernel(DevState* st, double
   }
 }
 
+// Reduction slots of init / step_b:  [0] = r^T s, [1 .. k] = V^T s,
+// [k + 1] = r^T r (Jacobi only; with M_cg = I, r^T s is r^T r).  Indices are
+// compile-time after unrolling, so the slot array stays in registers.
+template <typename T, int KB>
+__device__ __forceinline__ void pack_slots(T (&acc)[KB + 2], T rs, const T (&u)[KB > 0 ? KB : 1], T rr, int k,
+                                           bool jac) {
+  constexpr int KS = KB > 0 ? KB : 1;
+#pragma unroll
+  for (int l = 0; l < KB + 2; ++l) {
+    T val = (T)0;
+    if (l == 0) val = rs;
+    else if (l - 1 < KB && l - 1 < k) val = u[(l - 1 < KS) ? l - 1 : 0];
+    else if (jac && l == k + 1) val = rr;
+    acc[l] = val;
+  }
+}
+
 // ------------------------------------------------------------------ init
 
 template <typename T, int KB>
 __global__ void __launch_bounds__(kThreads) cg_init_kernel(CgArgs<T> a) {
+  constexpr int W = V16<T>::W;
+  constexpr int KS = KB > 0 ? KB : 1;
   CgState& S = a.st->cg;
   const double vn = S.vnorm;
   const double scale = (vn > 0.0 && isfinite(vn)) ? 1.0 / vn : 0.0;
   const double* v = S.vin;
+  const bool jac = a.dinv != nullptr;
   T rs = 0, rr = 0;
-  T u[KB > 0 ? KB : 1];
+  T u[KS];
 #pragma unroll
-  for (int l = 0; l < (KB > 0 ? KB : 1); ++l) u[l] = 0;
-  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < a.n_pad; i += (int64_t)gridDim.x * kThreads) {
-    const T r = (T)(v[i] * scale);
-    a.r[i] = r;
-    a.z[i] = 0;
-    a.p_old[i] = 0;
-    T s = r;
-    if (a.dinv) {
-      s = a.dinv[i] * r;
-      a.s[i] = s;
+  for (int l = 0; l < KS; ++l) u[l] = 0;
+  const T zero[W] = {};
+  const int64_t nvec = a.n_pad / W;
+  for (int64_t iv = blockIdx.x * (int64_t)kThreads + threadIdx.x; iv < nvec; iv += (int64_t)gridDim.x * kThreads) {
+    const int64_t i = iv * W;
+    T r[W], s[W];
+#pragma unroll
+    for (int e = 0; e < W; ++e) r[e] = (T)(v[i + e] * scale);
+    st16(a.r + i, r);
+    st16(a.z + i, zero);
+    st16(a.p_old + i, zero);
+    if (jac) {
+      T d[W];
+      ld16(a.dinv + i, d);
+#pragma unroll
+      for (int e = 0; e < W; ++e) s[e] = d[e] * r[e];
+      st16(a.s + i, s);
+    } else {
+#pragma unroll
+      for (int e = 0; e < W; ++e) s[e] = r[e];
     }
-    rs += r * s;
-    rr += r * r;
+#pragma unroll
+    for (int e = 0; e < W; ++e) {
+      rs += r[e] * s[e];
+      rr += r[e] * r[e];
+    }
 #pragma unroll
     for (int l = 0; l < KB; ++l)
-      if (l < a.k) u[l] += ld_stream(a.V + (size_t)l * a.n_pad + i) * s;
-  }
-  double acc[KB + 2];
-  acc[0] = (double)rs;
-  acc[1] = (double)rr;
+      if (l < a.k) {
+        T vv[W];
+        ld16_stream(a.V + (size_t)l * a.n_pad + i, vv);
 #pragma unroll
-  for (int l = 0; l < KB; ++l) acc[l + 2] = (double)u[l];
-  block_partials<KB + 2>(acc, a.k + 2, a.partials);
+        for (int e = 0; e < W; ++e) u[l] += vv[e] * s[e];
+      }
+  }
+  T acc[KB + 2];
+  pack_slots<T, KB>(acc, rs, u, rr, a.k, jac);
+  const int nv = a.k + 1 + (jac ? 1 : 0);
+  block_partials_t<T, KB + 2>(acc, nv, a.partials);
   if (last_block(&a.st->ticket)) {
     __shared__ double tot[KB + 2];
-    final_sums(a.partials, a.k + 2, tot);
+    final_sums(a.partials, nv, tot);
     if (threadIdx.x == 0) {
-      const double rho = tot[0], rnorm = sqrt(tot[1]);
+      const double rho = tot[0], rnorm = sqrt(jac ? tot[a.k + 1] : tot[0]);
       S.rho = rho;
       S.beta = 0.0;
+      S.beta32 = 0.0f;
       S.iters = 0;
       S.tol_abs = S.inner_tol * rnorm;
       S.maxit = S.budget;
@@ -128,10 +218,8 @@ __global__ void __launch_bounds__(kThreads) cg_init_kernel(CgArgs<T> a) {
       } else if (S.maxit <= 0) {
         S.done = kMaxIter;
       }
-      for (int l = 0; l < a.k; ++l) {
-        S.t[l] = tot[l + 2];
-        S.c[l] = S.lam2[l] * tot[l + 2];
-      }
+      for (int l = 0; l < a.k; ++l) S.t[l] = tot[l + 1];
+      publish_c(S, a.k);
     }
   }
 }
@@ -139,13 +227,15 @@ __global__ void __launch_bounds__(kThreads) cg_init_kernel(CgArgs<T> a) {
 // ------------------------------------------------------------------ step a
 
 template <typename T, int KB>
-__global__ void __launch_bounds__(kThreads) cg_step_a_kernel(CgArgs<T> a) {
+__global__ void __launch_bounds__(kThreads, 4) cg_step_a_kernel(CgArgs<T> a) {
+  constexpr int KS = KB > 0 ? KB : 1;
   CgState& S = a.st->cg;
   if (S.done != kRunning) return;
-  const T beta = (T)S.beta;
-  T cl[KB > 0 ? KB : 1];
-#pragma unroll
-  for (int l = 0; l < KB; ++l) cl[l] = (l < a.k) ? (T)S.c[l] : (T)0;
+  const T beta = beta_of(S, T(0));
+  // c = 2|Lambda| (V^T p') staged in shared memory (broadcast reads, no registers)
+  __shared__ T cl[KS];
+  if (threadIdx.x < KS) cl[threadIdx.x] = ((int)threadIdx.x < a.k) ? c_of(S, threadIdx.x, T(0)) : (T)0;
+  __syncthreads();
   const T* __restrict__ sv = a.s;
   const T* __restrict__ po = a.p_old;
   const int lane = threadIdx.x & 31;
@@ -153,28 +243,56 @@ __global__ void __launch_bounds__(kThreads) cg_step_a_kernel(CgArgs<T> a) {
   const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
   T dot = 0;
   for (int64_t sl = warp0; sl < a.nslices; sl += nwarps) {
+    const int64_t row = sl * kSlice + lane;
+    // FP32: loads that do not depend on the column indices go out first.
+    // FP64 (FP64-pipe bound, register-limited): V is read after the SpMV.
+    constexpr bool kEarlyV = sizeof(T) == 4;
+    T vrow[KS];
+    if (kEarlyV) {
+#pragma unroll
+      for (int l = 0; l < KS; ++l) vrow[l] = (l < a.k) ? ld_stream(a.V + (size_t)l * a.n_pad + row) : (T)0;
+    }
+    const T srow = sv[row], prow = po[row];
     const int64_t base = a.slice_ptr[sl];
     const int w = (int)((a.slice_ptr[sl + 1] - base) >> 5);
     const T* vp = a.val + base + lane;
     const int32_t* cp = a.col + base + lane;
     T acc = 0;
-#pragma unroll 4
-    for (int j = 0; j < w; ++j) {
-      const T av = ld_stream(vp + (size_t)j * kSlice);
-      const int c = ld_stream(cp + (size_t)j * kSlice);
-      acc += av * (__ldg(sv + c) + beta * __ldg(po + c));
-    }
-    const int64_t row = sl * kSlice + lane;
-    const T pn = sv[row] + beta * po[row];
+    if (kEarlyV && w <= 8) {
+      T av[8];
+      int cc[8];
 #pragma unroll
-    for (int l = 0; l < KB; ++l)
-      if (l < a.k) acc += ld_stream(a.V + (size_t)l * a.n_pad + row) * cl[l];
+      for (int j = 0; j < 8; ++j) {
+        av[j] = (j < w) ? ld_stream(vp + (size_t)j * kSlice) : (T)0;
+        cc[j] = (j < w) ? ld_stream(cp + (size_t)j * kSlice) : 0;
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (j < w) acc += av[j] * (__ldg(sv + cc[j]) + beta * __ldg(po + cc[j]));
+    } else {
+#pragma unroll 4
+      for (int j = 0; j < w; ++j) {
+        const T av = ld_stream(vp + (size_t)j * kSlice);
+        const int c = ld_stream(cp + (size_t)j * kSlice);
+        acc += av * (__ldg(sv + c) + beta * __ldg(po + c));
+      }
+    }
+    const T pn = srow + beta * prow;
+    if (kEarlyV) {
+#pragma unroll
+      for (int l = 0; l < KB; ++l)
+        if (l < a.k) acc += vrow[l] * cl[l];
+    } else {
+#pragma unroll
+      for (int l = 0; l < KB; ++l)
+        if (l < a.k) acc += ld_stream(a.V + (size_t)l * a.n_pad + row) * cl[l];
+    }
     a.q[row] = acc;
     a.p_new[row] = pn;
     dot += pn * acc;
   }
-  double part[1] = {(double)dot};
-  block_partials<1>(part, 1, a.partials);
+  T part[1] = {dot};
+  block_partials_t<T, 1>(part, 1, a.partials);
   if (last_block(&a.st->ticket)) {
     __shared__ double tot[1];
     final_sums(a.partials, 1, tot);
@@ -187,6 +305,7 @@ __global__ void __launch_bounds__(kThreads) cg_step_a_kernel(CgArgs<T> a) {
         S.done = kNotSpd;
       } else {
         S.alpha = S.rho / kappa;
+        S.alpha32 = (float)S.alpha;
       }
     }
   }
@@ -196,41 +315,64 @@ __global__ void __launch_bounds__(kThreads) cg_step_a_kernel(CgArgs<T> a) {
 
 template <typename T, int KB>
 __global__ void __launch_bounds__(kThreads) cg_step_b_kernel(CgArgs<T> a) {
+  constexpr int W = V16<T>::W;
+  constexpr int KS = KB > 0 ? KB : 1;
   CgState& S = a.st->cg;
   if (S.done != kRunning) return;
-  const T alpha = (T)S.alpha;
+  const T alpha = alpha_of(S, T(0));
+  const bool jac = a.dinv != nullptr;
   T rs = 0, rr = 0;
-  T u[KB > 0 ? KB : 1];
+  T u[KS];
 #pragma unroll
-  for (int l = 0; l < (KB > 0 ? KB : 1); ++l) u[l] = 0;
-  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < a.n_pad; i += (int64_t)gridDim.x * kThreads) {
-    const T pn = a.p_new[i];
-    const T qi = a.q[i];
-    a.z[i] = a.z[i] + alpha * pn;
-    const T r = a.r[i] - alpha * qi;
-    a.r[i] = r;
-    T s = r;
-    if (a.dinv) {
-      s = a.dinv[i] * r;
-      a.s[i] = s;
+  for (int l = 0; l < KS; ++l) u[l] = 0;
+  const int64_t nvec = a.n_pad / W;
+  for (int64_t iv = blockIdx.x * (int64_t)kThreads + threadIdx.x; iv < nvec; iv += (int64_t)gridDim.x * kThreads) {
+    const int64_t i = iv * W;
+    T pn[W], qv[W], zv[W], rv[W], s[W];
+    ld16(a.p_new + i, pn);
+    ld16(a.q + i, qv);
+    ld16(a.z + i, zv);
+    ld16(a.r + i, rv);
+#pragma unroll
+    for (int e = 0; e < W; ++e) {
+      zv[e] += alpha * pn[e];
+      rv[e] -= alpha * qv[e];
     }
-    rs += r * s;
-    rr += r * r;
+    st16(a.z + i, zv);
+    st16(a.r + i, rv);
+    if (jac) {
+      T d[W];
+      ld16(a.dinv + i, d);
+#pragma unroll
+      for (int e = 0; e < W; ++e) {
+        s[e] = d[e] * rv[e];
+        rr += rv[e] * rv[e];
+      }
+      st16(a.s + i, s);
+    } else {
+#pragma unroll
+      for (int e = 0; e < W; ++e) s[e] = rv[e];
+    }
+#pragma unroll
+    for (int e = 0; e < W; ++e) rs += rv[e] * s[e];
 #pragma unroll
     for (int l = 0; l < KB; ++l)
-      if (l < a.k) u[l] += ld_stream(a.V + (size_t)l * a.n_pad + i) * s;
-  }
-  double acc[KB + 2];
-  acc[0] = (double)rs;
-  acc[1] = (double)rr;
+      if (l < a.k) {
+        T vv[W];
+        ld16_stream(a.V + (size_t)l * a.n_pad + i, vv);
 #pragma unroll
-  for (int l = 0; l < KB; ++l) acc[l + 2] = (double)u[l];
-  block_partials<KB + 2>(acc, a.k + 2, a.partials);
+        for (int e = 0; e < W; ++e) u[l] += vv[e] * s[e];
+      }
+  }
+  T acc[KB + 2];
+  pack_slots<T, KB>(acc, rs, u, rr, a.k, jac);
+  const int nv = a.k + 1 + (jac ? 1 : 0);
+  block_partials_t<T, KB + 2>(acc, nv, a.partials);
   if (last_block(&a.st->ticket)) {
     __shared__ double tot[KB + 2];
-    final_sums(a.partials, a.k + 2, tot);
+    final_sums(a.partials, nv, tot);
     if (threadIdx.x == 0) {
-      const double rho_new = tot[0], rnorm = sqrt(tot[1]);
+      const double rho_new = tot[0], rnorm = sqrt(jac ? tot[a.k + 1] : tot[0]);
       S.iters += 1;
       if (!isfinite(rho_new) || !isfinite(rnorm)) {
         S.done = kNonFinite;
@@ -241,12 +383,10 @@ __global__ void __launch_bounds__(kThreads) cg_step_b_kernel(CgArgs<T> a) {
       } else {
         const double beta = rho_new / S.rho;
         S.beta = beta;
+        S.beta32 = (float)beta;
         S.rho = rho_new;
-        for (int l = 0; l < a.k; ++l) {
-          const double t = tot[l + 2] + beta * S.t[l];
-          S.t[l] = t;
-          S.c[l] = S.lam2[l] * t;
-        }
+        for (int l = 0; l < a.k; ++l) S.t[l] = tot[l + 1] + beta * S.t[l];
+        publish_c(S, a.k);
       }
     }
   }
@@ -259,6 +399,13 @@ __global__ void cg_ctl_kernel(DevState* st, cudaGraphConditionalHandle handle) {
   S.ctl_count += 1;
   if (S.done == kRunning && S.ctl_count >= S.ctl_limit) S.done = kLoopCap;
   cudaGraphSetConditional(handle, S.done == kRunning ? 1u : 0u);
+}
+
+// the same bookkeeping for the host-driven loop (no graph condition)
+__global__ void cg_ctl_host_kernel(DevState* st) {
+  CgState& S = st->cg;
+  S.ctl_count += 1;
+  if (S.done == kRunning && S.ctl_count >= S.ctl_limit) S.done = kLoopCap;
 }
 
 // ------------------------------------------------------------------ finish
@@ -284,28 +431,17 @@ __global__ void __launch_bounds__(kThreads) cg_finish_kernel(DevState* st, const
   }
 }
 
-// ------------------------------------------------------------------ graph assembly
+__global__ void fill_pattern_kernel(double* v, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
+    v[i] = 1.0 + 0.125 * (double)(i % 7) - 0.0625 * (double)(i % 3);
+}
+
+// ------------------------------------------------------------------ host side
 
 namespace {
 
-cudaError_t add_kernel(cudaGraph_t g, cudaGraphNode_t* node, const cudaGraphNode_t* deps, size_t ndeps,
-                       const void* fn, int grid, int block, void** args) {
-  cudaKernelNodeParams p = {};
-  p.func = const_cast<void*>(fn);
-  p.gridDim = dim3(grid);
-  p.blockDim = dim3(block);
-  p.sharedMemBytes = 0;
-  p.kernelParams = args;
-  p.extra = nullptr;
-  return cudaGraphAddKernelNode(node, g, deps, ndeps, &p);
-}
-
-template <typename T, int KB>
-cudaError_t build_graph_t(const InnerGraphSpec& spec, cudaGraph_t* out_graph) {
-  cudaError_t e;
-  cudaGraph_t g;
-  if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) return e;
-  CgArgs<T> a[2];
+template <typename T>
+void make_args(const InnerGraphSpec& spec, CgArgs<T> (&a)[2]) {
   for (int par = 0; par < 2; ++par) {
     CgArgs<T>& x = a[par];
     x.st = spec.st;
@@ -325,6 +461,27 @@ cudaError_t build_graph_t(const InnerGraphSpec& spec, cudaGraph_t* out_graph) {
     x.p_old = reinterpret_cast<T*>(par == 0 ? spec.p0 : spec.p1);
     x.p_new = reinterpret_cast<T*>(par == 0 ? spec.p1 : spec.p0);
   }
+}
+
+cudaError_t add_kernel(cudaGraph_t g, cudaGraphNode_t* node, const cudaGraphNode_t* deps, size_t ndeps,
+                       const void* fn, int grid, int block, void** args) {
+  cudaKernelNodeParams p = {};
+  p.func = const_cast<void*>(fn);
+  p.gridDim = dim3(grid);
+  p.blockDim = dim3(block);
+  p.sharedMemBytes = 0;
+  p.kernelParams = args;
+  p.extra = nullptr;
+  return cudaGraphAddKernelNode(node, g, deps, ndeps, &p);
+}
+
+template <typename T, int KB>
+cudaError_t build_graph_t(const InnerGraphSpec& spec, cudaGraph_t* out_graph) {
+  cudaError_t e;
+  cudaGraph_t g;
+  if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) return e;
+  CgArgs<T> a[2];
+  make_args(spec, a);
   DevState* st = spec.st;
   double* partials = spec.partials;
   int64_t n_pad = spec.A.n_pad;
@@ -357,7 +514,8 @@ cudaError_t build_graph_t(const InnerGraphSpec& spec, cudaGraph_t* out_graph) {
       if ((e = add_kernel(body, &na, prev ? &prev : nullptr, prev ? 1 : 0, (const void*)cg_step_a_kernel<T, KB>,
                           spec.grid_spmv, kThreads, aa)))
         goto fail;
-      if ((e = add_kernel(body, &nb, &na, 1, (const void*)cg_step_b_kernel<T, KB>, spec.grid_stream, kThreads, aa)))
+      if ((e = add_kernel(body, &nb, &na, 1, (const void*)cg_step_b_kernel<T, KB>, spec.grid_stream_b, kThreads,
+                          aa)))
         goto fail;
       prev = nb;
     }
@@ -378,42 +536,37 @@ fail:
   return e;
 }
 
-template <typename T>
-cudaError_t build_graph_k(const InnerGraphSpec& spec, cudaGraph_t* g) {
-  if (spec.k == 0) return build_graph_t<T, 0>(spec, g);
-  if (spec.k <= 8) return build_graph_t<T, 8>(spec, g);
-  if (spec.k <= 16) return build_graph_t<T, 16>(spec, g);
-  return build_graph_t<T, 32>(spec, g);
-}
-
-__global__ void fill_pattern_kernel(double* v, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
-    v[i] = 1.0 + 0.125 * (double)(i % 7) - 0.0625 * (double)(i % 3);
+// The same launch sequence as the graph, driven from the host: after every U
+// iterations the host reads the `done` word.  Used when a profiler must see
+// the individual kernels (kernel nodes under a conditional node cannot be
+// profiled).
+template <typename T, int KB>
+cudaError_t run_host_t(const InnerGraphSpec& spec, cudaStream_t stream, int* h_done) {
+  CgArgs<T> a[2];
+  make_args(spec, a);
+  cg_vnorm_kernel<<<spec.grid_stream, kThreads, 0, stream>>>(spec.st, spec.partials, spec.A.n_pad);
+  cg_init_kernel<T, KB><<<spec.grid_stream, kThreads, 0, stream>>>(a[0]);
+  cudaError_t e = cudaSuccess;
+  for (;;) {
+    for (int it = 0; it < spec.unroll; ++it) {
+      cg_step_a_kernel<T, KB><<<spec.grid_spmv, kThreads, 0, stream>>>(a[it & 1]);
+      cg_step_b_kernel<T, KB><<<spec.grid_stream_b, kThreads, 0, stream>>>(a[it & 1]);
+    }
+    cg_ctl_host_kernel<<<1, 1, 0, stream>>>(spec.st);
+    if ((e = cudaMemcpyAsync(h_done, &spec.st->cg.done, sizeof(int), cudaMemcpyDeviceToHost, stream))) return e;
+    if ((e = cudaStreamSynchronize(stream))) return e;
+    if (*h_done != kRunning) break;
+  }
+  cg_finish_kernel<T><<<spec.grid_stream, kThreads, 0, stream>>>(spec.st, reinterpret_cast<const T*>(spec.z),
+                                                                  spec.A.n_pad);
+  return cudaGetLastError();
 }
 
 template <typename T, int KB>
 cudaError_t time_t(const InnerGraphSpec& spec, int iters, cudaStream_t stream, double* vin, int64_t n,
                    double* ms) {
   CgArgs<T> a[2];
-  for (int par = 0; par < 2; ++par) {
-    CgArgs<T>& x = a[par];
-    x.st = spec.st;
-    x.partials = spec.partials;
-    x.slice_ptr = spec.A.slice_ptr;
-    x.col = spec.A.col;
-    x.val = reinterpret_cast<const T*>(sizeof(T) == 8 ? (const void*)spec.A.val64 : (const void*)spec.A.val32);
-    x.nslices = spec.A.nslices;
-    x.n_pad = spec.A.n_pad;
-    x.V = reinterpret_cast<const T*>(spec.V);
-    x.k = spec.k;
-    x.dinv = reinterpret_cast<const T*>(spec.dinv);
-    x.z = reinterpret_cast<T*>(spec.z);
-    x.r = reinterpret_cast<T*>(spec.r);
-    x.s = spec.dinv ? reinterpret_cast<T*>(spec.s) : reinterpret_cast<T*>(spec.r);
-    x.q = reinterpret_cast<T*>(spec.q);
-    x.p_old = reinterpret_cast<T*>(par == 0 ? spec.p0 : spec.p1);
-    x.p_new = reinterpret_cast<T*>(par == 0 ? spec.p1 : spec.p0);
-  }
+  make_args(spec, a);
   fill_pattern_kernel<<<spec.grid_stream, kThreads, 0, stream>>>(vin, n);
   cg_vnorm_kernel<<<spec.grid_stream, kThreads, 0, stream>>>(spec.st, spec.partials, spec.A.n_pad);
   cg_init_kernel<T, KB><<<spec.grid_stream, kThreads, 0, stream>>>(a[0]);
@@ -423,7 +576,7 @@ cudaError_t time_t(const InnerGraphSpec& spec, int iters, cudaStream_t stream, d
   for (int it = 0; it < iters; ++it) {
     cg_step_a_kernel<T, KB><<<spec.grid_spmv, kThreads, 0, stream>>>(a[it & 1]);
     cudaEventRecord(ev[2 * it + 1], stream);
-    cg_step_b_kernel<T, KB><<<spec.grid_stream, kThreads, 0, stream>>>(a[it & 1]);
+    cg_step_b_kernel<T, KB><<<spec.grid_stream_b, kThreads, 0, stream>>>(a[it & 1]);
     cudaEventRecord(ev[2 * it + 2], stream);
   }
   cudaError_t e = cudaStreamSynchronize(stream);
@@ -442,47 +595,71 @@ cudaError_t time_t(const InnerGraphSpec& spec, int iters, cudaStream_t stream, d
   return e;
 }
 
-template <typename T>
-cudaError_t time_k(const InnerGraphSpec& spec, int iters, cudaStream_t stream, double* vin, int64_t n, double* ms) {
-  if (spec.k == 0) return time_t<T, 0>(spec, iters, stream, vin, n, ms);
-  if (spec.k <= 8) return time_t<T, 8>(spec, iters, stream, vin, n, ms);
-  if (spec.k <= 16) return time_t<T, 16>(spec, iters, stream, vin, n, ms);
-  return time_t<T, 32>(spec, iters, stream, vin, n, ms);
-}
-
 template <typename T, int KB>
 void occupancy_t(int* a_blocks, int* b_blocks) {
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(a_blocks, (const void*)cg_step_a_kernel<T, KB>, kThreads, 0);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(b_blocks, (const void*)cg_step_b_kernel<T, KB>, kThreads, 0);
 }
 
+// dispatch on (precision, k bucket)
+template <template <typename, int> class F, typename... Args>
+cudaError_t dispatch(const InnerGraphSpec& spec, Args... args) {
+  if (spec.fp32) {
+    if (spec.k == 0) return F<float, 0>::run(spec, args...);
+    if (spec.k <= 8) return F<float, 8>::run(spec, args...);
+    if (spec.k <= 16) return F<float, 16>::run(spec, args...);
+    return F<float, 32>::run(spec, args...);
+  }
+  if (spec.k == 0) return F<double, 0>::run(spec, args...);
+  if (spec.k <= 8) return F<double, 8>::run(spec, args...);
+  if (spec.k <= 16) return F<double, 16>::run(spec, args...);
+  return F<double, 32>::run(spec, args...);
+}
+
+template <typename T, int KB>
+struct BuildF {
+  static cudaError_t run(const InnerGraphSpec& s, cudaGraph_t* g) { return build_graph_t<T, KB>(s, g); }
+};
+template <typename T, int KB>
+struct HostF {
+  static cudaError_t run(const InnerGraphSpec& s, cudaStream_t st, int* d) { return run_host_t<T, KB>(s, st, d); }
+};
+template <typename T, int KB>
+struct TimeF {
+  static cudaError_t run(const InnerGraphSpec& s, int it, cudaStream_t st, double* v, int64_t n, double* ms) {
+    return time_t<T, KB>(s, it, st, v, n, ms);
+  }
+};
+template <typename T, int KB>
+struct OccF {
+  static cudaError_t run(const InnerGraphSpec&, int* a, int* b) {
+    occupancy_t<T, KB>(a, b);
+    return cudaSuccess;
+  }
+};
+
 }  // namespace
+
+cudaError_t build_inner_graph(const InnerGraphSpec& spec, cudaGraph_t* graph) {
+  return dispatch<BuildF>(spec, graph);
+}
+
+cudaError_t run_inner_host(const InnerGraphSpec& spec, cudaStream_t stream, int* h_done) {
+  return dispatch<HostF>(spec, stream, h_done);
+}
 
 cudaError_t time_inner_kernels(const InnerGraphSpec& spec, int iters, cudaStream_t stream, double* vin, int64_t n,
                                double* ms) {
-  if (spec.fp32) return time_k<float>(spec, iters, stream, vin, n, ms);
-  return time_k<double>(spec, iters, stream, vin, n, ms);
-}
-
-cudaError_t build_inner_graph(const InnerGraphSpec& spec, cudaGraph_t* graph) {
-  if (spec.fp32) return build_graph_k<float>(spec, graph);
-  return build_graph_k<double>(spec, graph);
+  return dispatch<TimeF>(spec, iters, stream, vin, n, ms);
 }
 
 void inner_occupancy(bool fp32, int k, int* spmv_blocks_per_sm, int* stream_blocks_per_sm) {
   *spmv_blocks_per_sm = 1;
   *stream_blocks_per_sm = 1;
-  if (fp32) {
-    if (k == 0) occupancy_t<float, 0>(spmv_blocks_per_sm, stream_blocks_per_sm);
-    else if (k <= 8) occupancy_t<float, 8>(spmv_blocks_per_sm, stream_blocks_per_sm);
-    else if (k <= 16) occupancy_t<float, 16>(spmv_blocks_per_sm, stream_blocks_per_sm);
-    else occupancy_t<float, 32>(spmv_blocks_per_sm, stream_blocks_per_sm);
-  } else {
-    if (k == 0) occupancy_t<double, 0>(spmv_blocks_per_sm, stream_blocks_per_sm);
-    else if (k <= 8) occupancy_t<double, 8>(spmv_blocks_per_sm, stream_blocks_per_sm);
-    else if (k <= 16) occupancy_t<double, 16>(spmv_blocks_per_sm, stream_blocks_per_sm);
-    else occupancy_t<double, 32>(spmv_blocks_per_sm, stream_blocks_per_sm);
-  }
+  InnerGraphSpec s;
+  s.fp32 = fp32;
+  s.k = k;
+  dispatch<OccF>(s, spmv_blocks_per_sm, stream_blocks_per_sm);
 }
 
 }  // namespace mrcg

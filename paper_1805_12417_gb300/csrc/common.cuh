@@ -36,6 +36,8 @@ struct CgState {
   double lam2[kMaxK];    // 2 |lambda_j|
   double c[kMaxK];       // 2 |lambda_j| (V^T p)_j for the current direction p
   double t[kMaxK];       // (V^T p)_j for the current direction p
+  float c32[kMaxK];      // FP32 copies of c, alpha, beta for the FP32 kernels
+  float alpha32, beta32;
   double inner_tol;      // per-call parameters (uploaded by the host)
   long long budget;      // inner iterations still allowed (total budget)
   long long iters;       // iterations of the current inner solve
@@ -77,10 +79,35 @@ struct Sell {
 
 // ------------------------------------------------------------------ device helpers
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// Block reduction of NV per-thread values in the threads' own precision T
+// (FP32 in the mixed-precision kernels: no FP64 pipe work), stored as this
+// block's FP64 partials, value-major: partials[i * gridDim.x + blockIdx.x].
+template <typename T, int NV>
+__device__ __forceinline__ void block_partials_t(T (&v)[NV], int nv, double* partials) {
+  __shared__ T smt[kThreads / 32][NV > 0 ? NV : 1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+    if (i < nv) v[i] = warp_sum<T>(v[i]);
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+      if (i < nv) smt[warp][i] = v[i];
+  }
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    T s = 0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) s += smt[w][threadIdx.x];
+    partials[threadIdx.x * gridDim.x + blockIdx.x] = (double)s;
+  }
 }
 
 // Reduce NV per-thread values over the block and store them as this block's

@@ -23,11 +23,13 @@ struct InnerGraphSpec {
   void* p0 = nullptr;
   void* p1 = nullptr;
   void* q = nullptr;
-  int grid_spmv = 1, grid_stream = 1;
+  int grid_spmv = 1, grid_stream = 1, grid_stream_b = 1;
   int unroll = 4;  // CG iterations per body of the while loop (even)
 };
 
 cudaError_t build_inner_graph(const InnerGraphSpec& spec, cudaGraph_t* graph);
+// the same inner solve with the loop driven from the host (profiling mode)
+cudaError_t run_inner_host(const InnerGraphSpec& spec, cudaStream_t stream, int* h_done);
 // standalone launches of the two CG iteration kernels, timed with events
 cudaError_t time_inner_kernels(const InnerGraphSpec& spec, int iters, cudaStream_t stream, double* vin, int64_t n,
                                double* ms);
