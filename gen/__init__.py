@@ -17,6 +17,7 @@ from .problems import (  # noqa: F401
     random_sparse_symmetric,
     config1,
     config2,
+    config4,
     small_3d,
     CONFIGS,
 )

@@ -250,3 +250,26 @@ def random_sparse_symmetric(n: int, seed: int, density_rows=(0, 70), diag_shift:
     M.eliminate_zeros()
     M.sort_indices()
     return M.indptr.astype(np.int64), M.indices.astype(np.int32), M.data.astype(np.float64)
+
+
+def config4(count: int = 64, sides=(100, 400), kmax: int = 16, seed: int = 3):
+    """Batch of independent 2D 5-point Laplacian systems of uneven size.
+
+    For each system i: square side m_i ~ U{sides}, then k_i ~ U{1..kmax}
+    (raised to the end of its eigenvalue cluster), both drawn from
+    default_rng(seed) in that order for all systems; then one right-hand side
+    per system, uniform[-1, 1], from the same generator.  x* is unknown
+    (xstar = None): the check is the true residual and the oracle solution.
+    """
+    rng = np.random.default_rng(seed)
+    ms = rng.integers(sides[0], sides[1] + 1, size=count)
+    ks = rng.integers(1, kmax + 1, size=count)
+    out = []
+    for i, (mi, ki) in enumerate(zip(ms, ks)):
+        p = shifted_laplacian_problem(f"lap2d_{mi}x{mi}_k{ki}", (int(mi), int(mi)), int(ki), seed=None,
+                                      xstar=np.zeros(int(mi) * int(mi)))
+        out.append(p)
+    for p in out:
+        p.b = rng.uniform(-1.0, 1.0, p.n)
+        p.xstar = None
+    return out

@@ -139,6 +139,42 @@ mrcg_status mrcg_inner_solve(mrcg_handle h, const double* y, double* z, double i
  * milliseconds.  Overwrites the handle's work vectors (not its matrix). */
 mrcg_status mrcg_time_inner_kernels(mrcg_handle h, int32_t iters, double* ms);
 
+/* ---- Batches of independent systems (many uneven systems in one launch sequence) ----
+ *
+ * The paper's motivating use solves many systems with related coefficient
+ * matrices after one setup (Sec. 2, "many linear systems with the same
+ * coefficient matrix (or closely related coefficient matrices) need to be
+ * solved"; Sec. 3, shifted systems of shift-and-invert Arnoldi).  A batch
+ * holds nsys independent systems A_i x_i = b_i, each with its own M_mr
+ * (V_hat_i, Lambda_hat_i), and runs Algorithm 1 for all of them at once: every
+ * kernel covers all systems, with per-system scalars, per-system reductions
+ * and per-system convergence masks; the inner CG loop of all systems is one
+ * device-side graph loop. */
+typedef struct mrcg_batch* mrcg_batch_handle; /* opaque */
+
+/* Create a batch from nsys (1..4096) create-argument records, deep-copied
+ * like mrcg_solver_create.  All records must share precision and inner_prec;
+ * max_outer, restart_factor and stream are taken from sys[0].  The sum of the
+ * systems' rows (each padded to a multiple of 32) must stay below 2^31.
+ * Errors: MRCG_ERR_INVALID, MRCG_ERR_NONFINITE, MRCG_ERR_OOM, MRCG_ERR_CUDA. */
+mrcg_status mrcg_batch_create(int32_t nsys, const mrcg_create_args* sys, mrcg_batch_handle* out);
+
+/* Solve every system of the batch by MINRES-CG with the rules of mrcg_solve.
+ * B and X hold the systems' vectors back to back in system order
+ * (sum of n_i entries, host or device); X holds x0 on entry.  max_iters bounds
+ * the total inner iterations of EACH system.  infos (may be NULL) receives one
+ * record per system; kernel_launches there counts the launches of the whole
+ * batched call.  Returns MRCG_OK when every system converged, else the
+ * status of the first system (in order) that did not. */
+mrcg_status mrcg_batched_solve(mrcg_batch_handle h, const double* B, double* X, double outer_tol, double inner_tol,
+                               int64_t max_iters, mrcg_info* infos);
+
+/* Number of systems in the batch (0 for NULL). */
+int32_t mrcg_batch_size(mrcg_batch_handle h);
+
+/* Release a batch (NULL is a no-op). */
+void mrcg_batch_destroy(mrcg_batch_handle h);
+
 /* Allocation-free M_mr product: out = A u + 2 V (|Lambda| (V^T u)) in FP64.
  * The paper has no counterpart; this entry point exists for callers that
  * cannot call cudaMalloc at all (code running inside another framework's

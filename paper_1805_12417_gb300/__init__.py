@@ -63,6 +63,14 @@ def lib() -> C.CDLL:
         L.mrcg_inner_solve.restype = C.c_int
         L.mrcg_time_inner_kernels.argtypes = [P, C.c_int32, P]
         L.mrcg_time_inner_kernels.restype = C.c_int
+        L.mrcg_batch_create.argtypes = [C.c_int32, C.POINTER(CreateArgs), C.POINTER(C.c_void_p)]
+        L.mrcg_batch_create.restype = C.c_int
+        L.mrcg_batched_solve.argtypes = [P, P, P, C.c_double, C.c_double, C.c_int64, C.POINTER(Info)]
+        L.mrcg_batched_solve.restype = C.c_int
+        L.mrcg_batch_size.argtypes = [P]
+        L.mrcg_batch_size.restype = C.c_int32
+        L.mrcg_batch_destroy.argtypes = [P]
+        L.mrcg_batch_destroy.restype = None
         L.mrcg_solver_destroy.argtypes = [P]
         L.mrcg_solver_destroy.restype = None
         L.mrcg_status_string.argtypes = [C.c_int]
@@ -246,6 +254,91 @@ class Solver:
     def close(self):
         if getattr(self, "h", None):
             solver_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def _create_args(n, rowptr, colind, val, V, lam, precision, inner_prec, validate, max_outer, restart_factor,
+                 stream, keep):
+    _check_dtype(rowptr, np.int64, "rowptr"); _check_dtype(colind, np.int32, "colind")
+    _check_dtype(val, np.float64, "val")
+    k = 0
+    Vp = lamp = None
+    if V is not None and lam is not None and len(lam) > 0:
+        V = np.ascontiguousarray(np.asarray(V, dtype=np.float64).reshape(n, -1).T)
+        k = V.shape[0]
+        lam = np.ascontiguousarray(lam, dtype=np.float64)
+        Vp, kv = _ptr(V); lamp, kl = _ptr(lam); keep += [kv, kl]
+    rp, k1 = _ptr(rowptr); ci, k2 = _ptr(colind); va, k3 = _ptr(val)
+    keep += [k1, k2, k3]
+    return CreateArgs(int(n), int(rowptr[-1]), rp, ci, va, k, Vp, lamp, int(precision), int(inner_prec),
+                      1 if validate else 0, int(max_outer), float(restart_factor), stream)
+
+
+def batch_create(problems, precision=FP64, inner_prec=MCG_IDENTITY, validate=True, max_outer=0,
+                 restart_factor=0.0, stream=None) -> int:
+    """mrcg_batch_create from a list of objects with n, rowptr, colind, val, V, lam."""
+    keep = []
+    arr = (CreateArgs * len(problems))()
+    for i, p in enumerate(problems):
+        arr[i] = _create_args(p.n, p.rowptr, p.colind, p.val, p.V if p.k else None, p.lam if p.k else None,
+                              precision, inner_prec, validate, max_outer, restart_factor, stream, keep)
+    h = C.c_void_p()
+    st = lib().mrcg_batch_create(len(problems), arr, C.byref(h))
+    if st != OK:
+        raise MrcgError(st, "mrcg_batch_create")
+    return h.value
+
+
+def batched_solve(h, B, X, outer_tol=1e-10, inner_tol=1e-3, max_iters=0, history_cap=256):
+    """mrcg_batched_solve: returns (status, [SolveInfo per system])."""
+    _check_dtype(B, np.float64, "B"); _check_dtype(X, np.float64, "X")
+    S = lib().mrcg_batch_size(h)
+    infos = (Info * S)()
+    hists = [np.zeros(max(history_cap, 1)) for _ in range(S)]
+    for i in range(S):
+        infos[i].relres_history = hists[i].ctypes.data
+        infos[i].history_cap = history_cap
+    bp, kb = _ptr(B); xp, kx = _ptr(X)
+    st = lib().mrcg_batched_solve(h, bp, xp, float(outer_tol), float(inner_tol), int(max_iters), infos)
+    if st in (ERR_INVALID, ERR_CUDA, ERR_OOM):
+        raise MrcgError(st, "mrcg_batched_solve")
+    out = [SolveInfo(f.status, f.outer_iters, f.restarts, f.inner_iters_total, f.prec_calls, f.kernel_launches,
+                     f.true_relres, f.solve_ms, hists[i][: f.history_len].copy()) for i, f in enumerate(infos)]
+    return st, out
+
+
+class Batch:
+    """Owning wrapper of one batch handle; vectors are concatenated in system order."""
+
+    def __init__(self, problems, **kw):
+        self.sizes = [int(p.n) for p in problems]
+        self.offsets = np.concatenate([[0], np.cumsum(self.sizes)]).astype(np.int64)
+        self.h = batch_create(problems, **kw)
+
+    def solve(self, B, X=None, **kw):
+        if X is None:
+            X = np.zeros(int(self.offsets[-1])) if isinstance(B, np.ndarray) else B.new_zeros(B.shape)
+        st, infos = batched_solve(self.h, B, X, **kw)
+        return X, st, infos
+
+    def split(self, X):
+        return [X[self.offsets[i]:self.offsets[i + 1]] for i in range(len(self.sizes))]
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mrcg_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -58,7 +58,9 @@ struct OuterState {
   long long inner_total;               // inner iterations of this solve
   long long prec_calls;
   long long bodies;                    // executed bodies of the inner while loop
-  int status;                         // mrcg_status of the solve so far
+  int status;                          // mrcg_status of the solve so far
+  int mode;                            // batched solves: 0 idle, 1 cycle start, 2 outer step
+  int cur;                             // batched solves: which of the two v / w buffers holds v_j, w_j
   int pad0;
 };
 
