@@ -18,6 +18,10 @@ from .problems import (  # noqa: F401
     config1,
     config2,
     config4,
+    config5,
+    ShiftedFamily,
+    shifted_family,
+    small_shifted,
     small_3d,
     CONFIGS,
 )

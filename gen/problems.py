@@ -273,3 +273,84 @@ def config4(count: int = 64, sides=(100, 400), kmax: int = 16, seed: int = 3):
         p.b = rng.uniform(-1.0, 1.0, p.n)
         p.xstar = None
     return out
+
+
+@dataclass
+class ShiftedFamily:
+    """Shifted systems (L - sigma_j I) x = b sharing one sparsity pattern.
+
+    L: CSR of the unshifted Laplacian; V: n x kmax eigenvectors of L (row
+    index = unknown), lamL: their eigenvalues; sigma[j] and k[j] per shift;
+    columns c = j * nrhs + r of B / xstar (n x ncols, C order) belong to
+    shift j.  For column c the system is A = L - sigma_j I with
+    V_hat = V[:, :k_j] and Lambda_hat = lamL[:k_j] - sigma_j.
+    """
+
+    name: str
+    dims: tuple
+    n: int
+    rowptr: np.ndarray
+    colind: np.ndarray
+    val: np.ndarray
+    V: np.ndarray
+    lamL: np.ndarray
+    sigma: np.ndarray
+    k: np.ndarray
+    nrhs: int
+    B: np.ndarray
+    xstar: np.ndarray
+
+    @property
+    def ncols(self):
+        return len(self.sigma) * self.nrhs
+
+    @property
+    def nnz(self):
+        return int(self.rowptr[-1])
+
+    def column_problem(self, c) -> Problem:
+        """Column c as a stand-alone Problem (shifted CSR, its own V_hat / Lambda_hat)."""
+        j = c // self.nrhs
+        rp, ci, va = laplacian_csr(self.dims, self.sigma[j])
+        kj = int(self.k[j])
+        return Problem(f"{self.name}_col{c}", self.n, rp, ci, va, kj, self.V[:, :kj].copy(),
+                       self.lamL[:kj] - self.sigma[j], self.xstar[:, c].copy(), self.B[:, c].copy(),
+                       float(self.sigma[j]))
+
+
+def shifted_family(dims, nshift, nrhs, kmax_draw, seed, name="shifted"):
+    """k_j ~ U{1..kmax_draw} from default_rng(seed), each raised to the end of
+    its eigenvalue cluster; sigma_j midway between eigenvalues k_j and k_j + 1
+    of L; then x* for every (shift, rhs) column, uniform[-1, 1], from the same
+    generator (column-major draw order: column c = j * nrhs + r)."""
+    rng = np.random.default_rng(seed)
+    kd = rng.integers(1, kmax_draw + 1, size=nshift)
+    ks, sig = [], []
+    for kw in kd:
+        s, k, _ = shift_for_negatives(dims, int(kw))
+        ks.append(k); sig.append(s)
+    kmax = max(ks)
+    ev = laplacian_smallest_eigs(dims, kmax + 1)
+    lamL = np.array([v for v, _ in ev[:kmax]])
+    V = laplacian_eigvecs(dims, [m for _, m in ev[:kmax]]).T.copy()
+    rowptr, colind, val = laplacian_csr(dims)
+    n = int(np.prod(dims))
+    ncols = nshift * nrhs
+    xs = np.empty((n, ncols))
+    for c in range(ncols):
+        xs[:, c] = rng.uniform(-1.0, 1.0, n)
+    L = sp.csr_matrix((val, colind, rowptr), shape=(n, n))
+    B = L @ xs
+    sigc = np.repeat(np.array(sig), nrhs)
+    B -= xs * sigc[None, :]
+    return ShiftedFamily(name, tuple(dims), n, rowptr, colind, val, V, lamL, np.array(sig), np.array(ks), nrhs,
+                         np.ascontiguousarray(B), xs)
+
+
+def config5():
+    """3D 7-point Laplacian 160^3, 16 shifts with k_j ~ U{1..30} (seed 4), 4 RHS each."""
+    return shifted_family((160, 160, 160), 16, 4, 30, seed=4, name="lap3d_160^3_16shifts_x4")
+
+
+def small_shifted(dims=(14, 13, 12), nshift=4, nrhs=2, kmax_draw=8, seed=5):
+    return shifted_family(dims, nshift, nrhs, kmax_draw, seed, name=f"shifted_{dims[0]}x{dims[1]}x{dims[2]}")

@@ -175,6 +175,43 @@ int32_t mrcg_batch_size(mrcg_batch_handle h);
 /* Release a batch (NULL is a no-op). */
 void mrcg_batch_destroy(mrcg_batch_handle h);
 
+/* ---- Shifted families with blocks of right-hand sides ----
+ *
+ * Columns c = j * nrhs + r (0 <= c < nshift * nrhs <= 64) solve
+ *     (L - sigma_j I) x_c = b_c,
+ * the family of shifted systems of shift-and-invert Arnoldi (Sec. 3) with one
+ * sparsity pattern.  Because the eigenvectors of L - sigma_j I are those of L,
+ * every shift shares V_hat: for shift j, M_mr,j uses the first k_j columns of
+ * V_hat and Lambda_hat_j = lambda_L[0..k_j) - sigma_j (Sec. 2, definition of
+ * M_mr).  L, V_hat and all vectors are stored once; each iteration reads L and
+ * V_hat once for all columns.  Identity inner preconditioner only. */
+typedef struct mrcg_shifted* mrcg_shifted_handle; /* opaque */
+
+/* L: CSR of the unshifted matrix (n, nnz, rowptr, colind, val as for
+ * mrcg_solver_create); L->V: n x L->k column-major eigenvectors of L
+ * (L->k <= 32, orthonormal), L->lambda: their eigenvalues of L (any sign);
+ * L->precision, L->max_outer, L->restart_factor, L->stream as usual
+ * (L->inner_prec must be MRCG_MCG_IDENTITY).  sigma[nshift], k_per_shift[nshift]
+ * (0 <= k_j <= L->k, with lambda_L[l] - sigma_j < 0 for l < k_j).
+ * Errors: MRCG_ERR_INVALID (also for nshift * nrhs_per_shift > 64),
+ * MRCG_ERR_NONFINITE, MRCG_ERR_OOM, MRCG_ERR_CUDA. */
+mrcg_status mrcg_shifted_create(const mrcg_create_args* L, int32_t nshift, const double* sigma,
+                                const int32_t* k_per_shift, int32_t nrhs_per_shift, mrcg_shifted_handle* out);
+
+/* Solve all columns by MINRES-CG (rules of mrcg_solve, per column).  B and X
+ * are n x (nshift * nrhs) row-major blocks (element (i, c) at i * ncols + c),
+ * host or device; X holds x0 on entry.  max_iters bounds each column's total
+ * inner iterations.  infos (may be NULL): one record per column.  Returns
+ * MRCG_OK when every column converged, else the first failing column's status. */
+mrcg_status mrcg_shifted_solve(mrcg_shifted_handle h, const double* B, double* X, double outer_tol,
+                               double inner_tol, int64_t max_iters, mrcg_info* infos);
+
+/* Number of columns (nshift * nrhs_per_shift; 0 for NULL). */
+int32_t mrcg_shifted_columns(mrcg_shifted_handle h);
+
+/* Release a shifted-family handle (NULL is a no-op). */
+void mrcg_shifted_destroy(mrcg_shifted_handle h);
+
 /* Allocation-free M_mr product: out = A u + 2 V (|Lambda| (V^T u)) in FP64.
  * The paper has no counterpart; this entry point exists for callers that
  * cannot call cudaMalloc at all (code running inside another framework's

@@ -71,6 +71,15 @@ def lib() -> C.CDLL:
         L.mrcg_batch_size.restype = C.c_int32
         L.mrcg_batch_destroy.argtypes = [P]
         L.mrcg_batch_destroy.restype = None
+        L.mrcg_shifted_create.argtypes = [C.POINTER(CreateArgs), C.c_int32, P, P, C.c_int32,
+                                          C.POINTER(C.c_void_p)]
+        L.mrcg_shifted_create.restype = C.c_int
+        L.mrcg_shifted_solve.argtypes = [P, P, P, C.c_double, C.c_double, C.c_int64, C.POINTER(Info)]
+        L.mrcg_shifted_solve.restype = C.c_int
+        L.mrcg_shifted_columns.argtypes = [P]
+        L.mrcg_shifted_columns.restype = C.c_int32
+        L.mrcg_shifted_destroy.argtypes = [P]
+        L.mrcg_shifted_destroy.restype = None
         L.mrcg_solver_destroy.argtypes = [P]
         L.mrcg_solver_destroy.restype = None
         L.mrcg_status_string.argtypes = [C.c_int]
@@ -339,6 +348,76 @@ class Batch:
     def close(self):
         if getattr(self, "h", None):
             lib().mrcg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def shifted_create(fam, precision=FP64, max_outer=0, restart_factor=0.0, stream=None) -> int:
+    """mrcg_shifted_create from an object with n, rowptr, colind, val (of L),
+    V (n x kmax eigenvectors of L), lamL, sigma, k (per shift), nrhs."""
+    keep = []
+    a = _create_args(fam.n, fam.rowptr, fam.colind, fam.val, None, None, precision, MCG_IDENTITY, False,
+                     max_outer, restart_factor, stream, keep)
+    V = np.ascontiguousarray(np.asarray(fam.V, dtype=np.float64).reshape(fam.n, -1).T)
+    lamL = np.ascontiguousarray(fam.lamL, dtype=np.float64)
+    a.k = V.shape[0]
+    a.V = V.ctypes.data
+    a.lambda_ = lamL.ctypes.data
+    sig = np.ascontiguousarray(fam.sigma, dtype=np.float64)
+    ks = np.ascontiguousarray(fam.k, dtype=np.int32)
+    h = C.c_void_p()
+    st = lib().mrcg_shifted_create(C.byref(a), len(sig), sig.ctypes.data, ks.ctypes.data, int(fam.nrhs), C.byref(h))
+    if st != OK:
+        raise MrcgError(st, "mrcg_shifted_create")
+    return h.value
+
+
+def shifted_solve(h, B, X, outer_tol=1e-10, inner_tol=1e-3, max_iters=0, history_cap=256):
+    """mrcg_shifted_solve on n x ncols row-major blocks: returns (status, [SolveInfo per column])."""
+    _check_dtype(B, np.float64, "B"); _check_dtype(X, np.float64, "X")
+    S = lib().mrcg_shifted_columns(h)
+    infos = (Info * S)()
+    hists = [np.zeros(max(history_cap, 1)) for _ in range(S)]
+    for i in range(S):
+        infos[i].relres_history = hists[i].ctypes.data
+        infos[i].history_cap = history_cap
+    bp, kb = _ptr(B); xp, kx = _ptr(X)
+    st = lib().mrcg_shifted_solve(h, bp, xp, float(outer_tol), float(inner_tol), int(max_iters), infos)
+    if st in (ERR_INVALID, ERR_CUDA, ERR_OOM):
+        raise MrcgError(st, "mrcg_shifted_solve")
+    out = [SolveInfo(f.status, f.outer_iters, f.restarts, f.inner_iters_total, f.prec_calls, f.kernel_launches,
+                     f.true_relres, f.solve_ms, hists[i][: f.history_len].copy()) for i, f in enumerate(infos)]
+    return st, out
+
+
+class Shifted:
+    """Owning wrapper of one shifted-family handle."""
+
+    def __init__(self, fam, **kw):
+        self.n = int(fam.n)
+        self.ncols = len(fam.sigma) * int(fam.nrhs)
+        self.h = shifted_create(fam, **kw)
+
+    def solve(self, B, X=None, **kw):
+        if X is None:
+            X = np.zeros((self.n, self.ncols)) if isinstance(B, np.ndarray) else B.new_zeros(B.shape)
+        st, infos = shifted_solve(self.h, B, X, **kw)
+        return X, st, infos
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mrcg_shifted_destroy(self.h)
             self.h = None
 
     def __del__(self):

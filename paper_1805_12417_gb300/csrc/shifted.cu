@@ -1,0 +1,1321 @@
+// Shifted families with blocks of right-hand sides: columns c of X solve
+// (L - sigma_{j(c)} I) x_c = b_c with M_mr,j = L - sigma_j I + 2 V_j |Lambda_j| V_j^T,
+// where V_j = the first k_j eigenvectors of L (shared by every shift) and
+// Lambda_j = lambda_L[0..k_j) - sigma_j.  This is the structure of the
+// paper's shifted systems (Sec. 3: shift-and-invert Arnoldi solves many
+// systems gamma B - A with one pattern; Sec. 2: the eigenpair setup is
+// amortised over many solves).
+//
+// GB300 layout: every vector is an interleaved n x NCP block (row-major,
+// NCP = columns padded to 32 or 64); L is read ONCE per iteration for all
+// columns (one warp per row, lanes own columns), the shared V_hat is
+// row-major n x KV so each row's KV values arrive in one coalesced access and
+// are broadcast by warp shuffles into the V C / V^T S products against
+// per-column coefficients held in shared memory.  Per-column scalars, masks
+// and reductions follow the batched engine: row kernels write per-(value,
+// column, block) partials, one small kernel per step reduces them (one block
+// per column, fixed order) and advances that column's FP64 recurrences.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "mrcg.h"
+
+namespace mrcg {
+namespace shifted {
+
+constexpr int kMaxCols = 64;
+
+// reduction ops of the per-column scalar kernel
+enum Op : int { kOpVnorm = 0, kOpInit, kOpA, kOpB, kOpFinish, kOpBnorm, kOpResidAll, kOpResid, kOpDelta, kOpGamma };
+
+template <typename T>
+struct SArgs {
+  DevState* st;
+  const int* kcol;  // [NCP] k of each column (0 for padding)
+  int nc, ncp;
+  double* partials;
+  int64_t n;
+  const int64_t* rowptr;
+  const int32_t* colind;
+  const T* val;
+  const T* V;  // n x KV row-major
+  const double* sigma;  // [NCP] shift of each column (0 for padding)
+  T *z, *r, *p_old, *p_new, *q;
+  const double *v0, *v1;  // outer Lanczos buffers (FP64), inner right-hand sides
+  double* zraw;
+};
+
+__device__ __forceinline__ bool in_round(const DevState& d) { return d.out.mode == 1 || d.out.mode == 2; }
+// right-hand side of the inner solve: v_cur at a cycle start, v_{j+1} (over v_{j-1}) in a step
+__device__ __forceinline__ const double* vin_of(const DevState& d, const double* v0, const double* v1) {
+  return (d.out.mode == 1) ? (d.out.cur ? v1 : v0) : (d.out.cur ? v0 : v1);
+}
+
+#define ROWS_BY_WARP(n)                                                     \
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;               \
+  const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;              \
+  for (int64_t row = (int64_t)blockIdx.x * (kThreads / 32) + warp; row < (n); row += nwarps)
+
+// per-column block sums of NVAL values per lane column, accumulated warp by
+// warp in a fixed order, stored as partials[((v * ncp) + c) * gridDim.x + blockIdx.x]
+template <typename T, int NM, int NVAL>
+__device__ __forceinline__ void col_partials(T (&v)[NVAL][NM], int ncp, double* partials, T* sm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < NVAL * NM * 32; i += kThreads) sm[i] = (T)0;
+  __syncthreads();
+  for (int w = 0; w < kThreads / 32; ++w) {
+    if (warp == w) {
+#pragma unroll
+      for (int a = 0; a < NVAL; ++a)
+#pragma unroll
+        for (int m = 0; m < NM; ++m) sm[a * NM * 32 + m * 32 + lane] += v[a][m];
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < NVAL * ncp; i += kThreads) {
+    const int a = i / ncp, c = i % ncp;
+    partials[((size_t)a * ncp + c) * gridDim.x + blockIdx.x] = (double)sm[a * NM * 32 + c];
+  }
+}
+
+// FP64 variant (outer kernels): double shared accumulators
+template <int NM>
+__device__ __forceinline__ void col_partials64(double (&v)[NM], int ncp, double* partials, double* sm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < NM * 32; i += kThreads) sm[i] = 0.0;
+  __syncthreads();
+  for (int w = 0; w < kThreads / 32; ++w) {
+    if (warp == w) {
+#pragma unroll
+      for (int m = 0; m < NM; ++m) sm[m * 32 + lane] += v[m];
+    }
+    __syncthreads();
+  }
+  for (int c = threadIdx.x; c < ncp; c += kThreads) partials[(size_t)c * gridDim.x + blockIdx.x] = sm[c];
+}
+
+// ------------------------------------------------------------------ inner CG row kernels
+
+template <typename T, int NM, int KV>
+__global__ void __launch_bounds__(kThreads) sh_vnorm_kernel(SArgs<T> a) {
+  __shared__ double sm[NM * 32];
+  double acc[NM];
+  const double* vin[NM];
+  bool on[NM];
+#pragma unroll
+  for (int m = 0; m < NM; ++m) {
+    const int c = (threadIdx.x & 31) + 32 * m;
+    on[m] = c < a.nc && in_round(a.st[c]);
+    vin[m] = on[m] ? vin_of(a.st[c], a.v0, a.v1) : a.v0;
+    acc[m] = 0.0;
+  }
+  ROWS_BY_WARP(a.n) {
+#pragma unroll
+    for (int m = 0; m < NM; ++m)
+      if (on[m]) {
+        const double x = vin[m][row * a.ncp + lane + 32 * m];
+        acc[m] += x * x;
+      }
+  }
+  col_partials64<NM>(acc, a.ncp, a.partials, sm);
+}
+
+template <typename T, int NM, int KV>
+__global__ void __launch_bounds__(kThreads) sh_init_kernel(SArgs<T> a) {
+  __shared__ T sm[(KV + 1) * NM * 32];
+  T acc[KV + 1][NM];
+  double scale[NM];
+  const double* vin[NM];
+  bool on[NM];
+#pragma unroll
+  for (int m = 0; m < NM; ++m) {
+    const int c = (threadIdx.x & 31) + 32 * m;
+    on[m] = c < a.nc && in_round(a.st[c]);
+    const double vn = on[m] ? a.st[c].cg.vnorm : 0.0;
+    scale[m] = (vn > 0.0 && isfinite(vn)) ? 1.0 / vn : 0.0;
+    vin[m] = on[m] ? vin_of(a.st[c], a.v0, a.v1) : a.v0;
+#pragma unroll
+    for (int l = 0; l <= KV; ++l) acc[l][m] = 0;
+  }
+  ROWS_BY_WARP(a.n) {
+    T rv[NM];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+      const int64_t idx = row * a.ncp + lane + 32 * m;
+      if (on[m]) {
+        rv[m] = (T)(vin[m][idx] * scale[m]);
+        a.r[idx] = rv[m];
+        a.z[idx] = 0;
+        a.p_old[idx] = 0;
+      } else {
+        rv[m] = 0;
+      }
+      acc[0][m] += rv[m] * rv[m];
+    }
+    const T vi = lane < KV ? a.V[row * KV + lane] : (T)0;
+#pragma unroll
+    for (int l = 0; l < KV; ++l) {
+      const T vl = __shfl_sync(0xffffffffu, vi, l);
+#pragma unroll
+      for (int m = 0; m < NM; ++m) acc[l + 1][m] += vl * rv[m];
+    }
+  }
+  col_partials<T, NM, KV + 1>(acc, a.ncp, a.partials, sm);
+}
+
+template <typename T, int NM, int KV>
+__global__ void __launch_bounds__(kThreads) sh_step_a_kernel(SArgs<T> a) {
+  __shared__ T Cs[KV][NM * 32];
+  __shared__ T sm[NM * 32];
+  for (int i = threadIdx.x; i < KV * NM * 32; i += kThreads) {
+    const int l = i / (NM * 32), c = i % (NM * 32);
+    Cs[l][c] = (c < a.nc && l < a.kcol[c] && in_round(a.st[c]) && a.st[c].cg.done == kRunning)
+                   ? (T)(sizeof(T) == 4 ? (double)a.st[c].cg.c32[l] : a.st[c].cg.c[l])
+                   : (T)0;
+  }
+  T beta[NM], sig[NM];
+#pragma unroll
+  for (int m = 0; m < NM; ++m) {
+    const int c = (threadIdx.x & 31) + 32 * m;
+    const bool on = c < a.nc && in_round(a.st[c]) && a.st[c].cg.done == kRunning;
+    beta[m] = on ? (T)(sizeof(T) == 4 ? (double)a.st[c].cg.beta32 : a.st[c].cg.beta) : (T)0;
+    sig[m] = (T)a.sigma[c];
+  }
+  __syncthreads();
+  const T* __restrict__ sv = a.r;
+  const T* __restrict__ po = a.p_old;
+  T dot[1][NM];
+#pragma unroll
+  for (int m = 0; m < NM; ++m) dot[0][m] = 0;
+  ROWS_BY_WARP(a.n) {
+    const int64_t e0 = a.rowptr[row];
+    const int nnz = (int)(a.rowptr[row + 1] - e0);
+    T acc[NM];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) acc[m] = 0;
+    for (int base = 0; base < nnz; base += 32) {
+      const bool has = lane + base < nnz;
+      const T my_val = has ? a.val[e0 + base + lane] : (T)0;
+      const int my_col = has ? a.colind[e0 + base + lane] : 0;
+      const int cnt = min(32, nnz - base);
+      for (int j = 0; j < cnt; ++j) {
+        const T av = __shfl_sync(0xffffffffu, my_val, j);
+        const int64_t cj = (int64_t)__shfl_sync(0xffffffffu, my_col, j) * a.ncp + lane;
+#pragma unroll
+        for (int m = 0; m < NM; ++m) acc[m] += av * (__ldg(sv + cj + 32 * m) + beta[m] * __ldg(po + cj + 32 * m));
+      }
+    }
+    const T vi = lane < KV ? __ldcs(a.V + row * KV + lane) : (T)0;
+    T pn[NM];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+      const int64_t idx = row * a.ncp + lane + 32 * m;
+      pn[m] = sv[idx] + beta[m] * po[idx];
+      acc[m] -= sig[m] * pn[m];
+    }
+#pragma unroll
+    for (int l = 0; l < KV; ++l) {
+      const T vl = __shfl_sync(0xffffffffu, vi, l);
+#pragma unroll
+      for (int m = 0; m < NM; ++m) acc[m] += vl * Cs[l][lane + 32 * m];
+    }
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+      const int64_t idx = row * a.ncp + lane + 32 * m;
+      a.q[idx] = acc[m];
+      a.p_new[idx] = pn[m];
+      dot[0][m] += pn[m] * acc[m];
+    }
+  }
+  col_partials<T, NM, 1>(dot, a.ncp, a.partials, sm);
+}
+
+template <typename T, int NM, int KV>
+__global__ void __launch_bounds__(kThreads) sh_step_b_kernel(SArgs<T> a) {
+  __shared__ T sm[(KV + 1) * NM * 32];
+  T alpha[NM];
+#pragma unroll
+  for (int m = 0; m < NM; ++m) {
+    const int c = (threadIdx.x & 31) + 32 * m;
+    const bool on = c < a.nc && in_round(a.st[c]) && a.st[c].cg.done == kRunning;
+    // finished or idle columns keep z and r: alpha = 0
+    alpha[m] = on ? (T)(sizeof(T) == 4 ? (double)a.st[c].cg.alpha32 : a.st[c].cg.alpha) : (T)0;
+  }
+  T acc[KV + 1][NM];
+#pragma unroll
+  for (int l = 0; l <= KV; ++l)
+#pragma unroll
+    for (int m = 0; m < NM; ++m) acc[l][m] = 0;
+  ROWS_BY_WARP(a.n) {
+    T rv[NM];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+      const int64_t idx = row * a.ncp + lane + 32 * m;
+      const T pn = a.p_new[idx], qv = a.q[idx];
+      a.z[idx] = a.z[idx] + alpha[m] * pn;
+      rv[m] = a.r[idx] - alpha[m] * qv;
+      a.r[idx] = rv[m];
+      acc[0][m] += rv[m] * rv[m];
+    }
+    const T vi = lane < KV ? __ldcs(a.V + row * KV + lane) : (T)0;
+#pragma unroll
+    for (int l = 0; l < KV; ++l) {
+      const T vl = __shfl_sync(0xffffffffu, vi, l);
+#pragma unroll
+      for (int m = 0; m < NM; ++m) acc[l + 1][m] += vl * rv[m];
+    }
+  }
+  col_partials<T, NM, KV + 1>(acc, a.ncp, a.partials, sm);
+}
+
+template <typename T, int NM>
+__global__ void __launch_bounds__(kThreads) sh_finish_kernel(SArgs<T> a) {
+  double vn[NM];
+  bool on[NM];
+#pragma unroll
+  for (int m = 0; m < NM; ++m) {
+    const int c = (threadIdx.x & 31) + 32 * m;
+    on[m] = c < a.nc && in_round(a.st[c]);
+    const double v = on[m] ? a.st[c].cg.vnorm : 0.0;
+    vn[m] = (v > 0.0 && isfinite(v)) ? v : 0.0;
+  }
+  ROWS_BY_WARP(a.n) {
+#pragma unroll
+    for (int m = 0; m < NM; ++m)
+      if (on[m]) {
+        const int64_t idx = row * a.ncp + lane + 32 * m;
+        a.zraw[idx] = vn[m] * (double)a.z[idx];
+      }
+  }
+}
+
+// ------------------------------------------------------------------ outer MINRES row kernels (FP64)
+
+struct OArgs {
+  DevState* st;
+  int nc, ncp;
+  double* partials;
+  int64_t n;
+  const int64_t* rowptr;
+  const int32_t* colind;
+  const double* val;
+  const double* sigma;
+  double *x, *b, *res, *zraw, *zn, *v0, *v1, *w0, *w1;
+};
+
+template <int NM>
+__device__ __forceinline__ void spmm_row(const OArgs& a, int64_t row, int lane, const double* X, double (&acc)[NM]) {
+  const int64_t e0 = a.rowptr[row];
+  const int nnz = (int)(a.rowptr[row + 1] - e0);
+#pragma unroll
+  for (int m = 0; m < NM; ++m) acc[m] = 0.0;
+  for (int base = 0; base < nnz; base += 32) {
+    const bool has = lane + base < nnz;
+    const double my_val = has ? a.val[e0 + base + lane] : 0.0;
+    const int my_col = has ? a.colind[e0 + base + lane] : 0;
+    const int cnt = min(32, nnz - base);
+    for (int j = 0; j < cnt; ++j) {
+      const double av = __shfl_sync(0xffffffffu, my_val, j);
+      const int64_t cj = (int64_t)__shfl_sync(0xffffffffu, my_col, j) * a.ncp + lane;
+#pragma unroll
+      for (int m = 0; m < NM; ++m) acc[m] += av * __ldg(X + cj + 32 * m);
+    }
+  }
+}
+
+// col_active(mode filter): 0 = every real column, 1 = mode 1, 2 = mode 2 (and status OK)
+__device__ __forceinline__ bool col_on(const OArgs& a, int c, int want) {
+  if (c >= a.nc) return false;
+  const OuterState& O = a.st[c].out;
+  if (want == 0) return true;
+  return O.mode == want && O.status == MRCG_OK;
+}
+
+template <int NM>
+__global__ void __launch_bounds__(kThreads) sh_bnorm_kernel(OArgs a) {
+  __shared__ double sm[NM * 32];
+  double acc[NM] = {};
+  ROWS_BY_WARP(a.n) {
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+      const double x = a.b[row * a.ncp + lane + 32 * m];
+      acc[m] += x * x;
+    }
+  }
+  col_partials64<NM>(acc, a.ncp, a.partials, sm);
+}
+
+// res = b - (L - sigma) x over columns selected by `want`
+template <int NM>
+__global__ void __launch_bounds__(kThreads) sh_residual_kernel(OArgs a, int want) {
+  __shared__ double sm[NM * 32];
+  bool on[NM];
+  double sig[NM], acc[NM] = {};
+#pragma unroll
+  for (int m = 0; m < NM; ++m) {
+    const int c = (threadIdx.x & 31) + 32 * m;
+    on[m] = col_on(a, c, want);
+    sig[m] = a.sigma[c];
+  }
+  ROWS_BY_WARP(a.n) {
+    double ax[NM];
+    spmm_row<NM>(a, row, lane, a.x, ax);
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+      const int64_t idx = row * a.ncp + lane + 32 * m;
+      if (on[m]) {
+        const double r = a.b[idx] - (ax[m] - sig[m] * a.x[idx]);
+        a.res[idx] = r;
+        acc[m] += r * r;
+      }
+    }
+  }
+  col_partials64<NM>(acc, a.ncp, a.partials, sm);
+}
+
+template <int NM>
+__global__ void __launch_bounds__(kThreads) sh_cycle_start_kernel(OArgs a) {
+  bool on[NM];
+  double *vc[NM], *vp[NM], *wc[NM], *wp[NM];
+#pragma unroll
+  for (int m = 0; m < NM; ++m) {
+    const int c = (threadIdx.x & 31) + 32 * m;
+    on[m] = col_on(a, c, 1);
+    const int cur = c < a.nc ? a.st[c].out.cur : 0;
+    vc[m] = cur ? a.v1 : a.v0;
+    vp[m] = cur ? a.v0 : a.v1;
+    wc[m] = cur ? a.w1 : a.w0;
+    wp[m] = cur ? a.w0 : a.w1;
+  }
+  ROWS_BY_WARP(a.n) {
+#pragma unroll
+    for (int m = 0; m < NM; ++m)
+      if (on[m]) {
+        const int64_t idx = row * a.ncp + lane + 32 * m;
+        vc[m][idx] = a.res[idx];
+        vp[m][idx] = 0.0;
+        wc[m][idx] = 0.0;
+        wp[m][idx] = 0.0;
+      }
+  }
+}
+
+// z^T v_in for mode 1 and mode 2 columns
+template <int NM>
+__global__ void __launch_bounds__(kThreads) sh_gamma_kernel(OArgs a) {
+  __shared__ double sm[NM * 32];
+  bool on[NM];
+  const double* vin[NM];
+  double acc[NM] = {};
+#pragma unroll
+  for (int m = 0; m < NM; ++m) {
+    const int c = (threadIdx.x & 31) + 32 * m;
+    on[m] = col_on(a, c, 1) || col_on(a, c, 2);
+    vin[m] = on[m] ? vin_of(a.st[c], a.v0, a.v1) : a.v0;
+  }
+  ROWS_BY_WARP(a.n) {
+#pragma unroll
+    for (int m = 0; m < NM; ++m)
+      if (on[m]) {
+        const int64_t idx = row * a.ncp + lane + 32 * m;
+        acc[m] += a.zraw[idx] * vin[m][idx];
+      }
+  }
+  col_partials64<NM>(acc, a.ncp, a.partials, sm);
+}
+
+// zn = zraw/gamma ; az = (L - sigma) zn (into res) ; partial zn^T az
+template <int NM>
+__global__ void __launch_bounds__(kThreads) sh_lanczos_spmv_kernel(OArgs a) {
+  __shared__ double sm[NM * 32];
+  bool on[NM];
+  double ig[NM], sig[NM], acc[NM] = {};
+#pragma unroll
+  for (int m = 0; m < NM; ++m) {
+    const int c = (threadIdx.x & 31) + 32 * m;
+    on[m] = col_on(a, c, 2);
+    ig[m] = on[m] ? 1.0 / a.st[c].out.gamma : 0.0;
+    sig[m] = a.sigma[c];
+  }
+  ROWS_BY_WARP(a.n) {
+    double az[NM];
+    spmm_row<NM>(a, row, lane, a.zraw, az);
+#pragma unroll
+    for (int m = 0; m < NM; ++m)
+      if (on[m]) {
+        const int64_t idx = row * a.ncp + lane + 32 * m;
+        const double zr = a.zraw[idx];
+        const double zi = zr * ig[m];
+        const double ai = (az[m] - sig[m] * zr) * ig[m];
+        a.zn[idx] = zi;
+        a.res[idx] = ai;
+        acc[m] += zi * ai;
+      }
+  }
+  col_partials64<NM>(acc, a.ncp, a.partials, sm);
+}
+
+template <int NM>
+__global__ void __launch_bounds__(kThreads) sh_lanczos_update_kernel(OArgs a) {
+  bool on[NM];
+  double f1[NM], f2[NM];
+  const double* v[NM];
+  double* vo[NM];
+#pragma unroll
+  for (int m = 0; m < NM; ++m) {
+    const int c = (threadIdx.x & 31) + 32 * m;
+    on[m] = col_on(a, c, 2);
+    const OuterState& O = a.st[c < a.nc ? c : 0].out;
+    f1[m] = on[m] ? O.delta / O.gamma : 0.0;
+    f2[m] = on[m] ? O.gamma / O.gamma_old : 0.0;
+    v[m] = O.cur ? a.v1 : a.v0;
+    vo[m] = O.cur ? a.v0 : a.v1;
+  }
+  ROWS_BY_WARP(a.n) {
+#pragma unroll
+    for (int m = 0; m < NM; ++m)
+      if (on[m]) {
+        const int64_t idx = row * a.ncp + lane + 32 * m;
+        vo[m][idx] = a.res[idx] - f1[m] * v[m][idx] - f2[m] * vo[m][idx];
+      }
+  }
+}
+
+template <int NM>
+__global__ void __launch_bounds__(kThreads) sh_minres_update_kernel(OArgs a) {
+  bool on[NM];
+  double a1[NM], a2[NM], a3[NM], ce[NM];
+  const double* w[NM];
+  double* wo[NM];
+#pragma unroll
+  for (int m = 0; m < NM; ++m) {
+    const int c = (threadIdx.x & 31) + 32 * m;
+    on[m] = col_on(a, c, 2);
+    const OuterState& O = a.st[c < a.nc ? c : 0].out;
+    a1[m] = O.a1;
+    a2[m] = O.a2;
+    a3[m] = O.a3;
+    ce[m] = O.ceta;
+    w[m] = O.cur ? a.w1 : a.w0;
+    wo[m] = O.cur ? a.w0 : a.w1;
+  }
+  ROWS_BY_WARP(a.n) {
+#pragma unroll
+    for (int m = 0; m < NM; ++m)
+      if (on[m]) {
+        const int64_t idx = row * a.ncp + lane + 32 * m;
+        const double wn = (a.zn[idx] - a3[m] * wo[m][idx] - a2[m] * w[m][idx]) / a1[m];
+        wo[m][idx] = wn;
+        a.x[idx] += ce[m] * wn;
+      }
+  }
+}
+
+// ------------------------------------------------------------------ per-column reduce + scalar recurrences
+
+// one block per column: sum partials of nval values in a fixed order, apply op
+__global__ void __launch_bounds__(kThreads) sh_scalar_kernel(DevState* st, const int* kcol, int nc, int ncp,
+                                                               const double* partials, int nblk, int op, int nval) {
+  const int c = blockIdx.x;
+  if (c >= nc) return;
+  DevState& D = st[c];
+  CgState& S = D.cg;
+  OuterState& O = D.out;
+  const bool round = in_round(D);
+  // which columns take part in each op
+  bool take = true;
+  switch (op) {
+    case kOpVnorm: case kOpInit: case kOpFinish: take = round; break;
+    case kOpA: case kOpB: take = round && S.done == kRunning; break;
+    case kOpBnorm: case kOpResidAll: take = true; break;
+    case kOpResid: case kOpDelta: take = O.mode == 2 && O.status == MRCG_OK; break;
+    case kOpGamma: take = (O.mode == 1 || O.mode == 2) && O.status == MRCG_OK; break;
+  }
+  if (!take) return;
+  __shared__ double tot[kMaxK + 1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int v = warp; v < nval; v += kThreads / 32) {
+    double s = 0.0;
+    for (int b = lane; b < nblk; b += 32) s += partials[((size_t)v * ncp + c) * nblk + b];
+    s = warp_sum(s);
+    if (lane == 0) tot[v] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const int k = kcol[c];
+  switch (op) {
+    case kOpVnorm:
+      S.vnorm = sqrt(tot[0]);
+      break;
+    case kOpInit: {
+      const double rho = tot[0], rnorm = sqrt(tot[0]);
+      S.rho = rho;
+      S.beta = 0.0;
+      S.beta32 = 0.0f;
+      S.iters = 0;
+      S.tol_abs = S.inner_tol * rnorm;
+      S.maxit = S.budget;
+      S.done = kRunning;
+      if (!isfinite(S.vnorm) || !isfinite(rho)) S.done = kNonFinite;
+      else if (S.vnorm == 0.0 || rnorm == 0.0) S.done = kConverged;
+      else if (S.maxit <= 0) S.done = kMaxIter;
+      for (int l = 0; l < k; ++l) {
+        S.t[l] = tot[l + 1];
+        S.c[l] = S.lam2[l] * S.t[l];
+        S.c32[l] = (float)S.c[l];
+      }
+      break;
+    }
+    case kOpA: {
+      const double kappa = tot[0];
+      S.kappa = kappa;
+      if (!isfinite(kappa)) S.done = kNonFinite;
+      else if (kappa <= 0.0) S.done = kNotSpd;
+      else {
+        S.alpha = S.rho / kappa;
+        S.alpha32 = (float)S.alpha;
+      }
+      break;
+    }
+    case kOpB: {
+      const double rho_new = tot[0], rnorm = sqrt(tot[0]);
+      S.iters += 1;
+      if (!isfinite(rho_new)) S.done = kNonFinite;
+      else if (rnorm <= S.tol_abs) S.done = kConverged;
+      else if (S.iters >= S.maxit) S.done = kMaxIter;
+      else {
+        const double beta = rho_new / S.rho;
+        S.beta = beta;
+        S.beta32 = (float)beta;
+        S.rho = rho_new;
+        for (int l = 0; l < k; ++l) {
+          S.t[l] = tot[l + 1] + beta * S.t[l];
+          S.c[l] = S.lam2[l] * S.t[l];
+          S.c32[l] = (float)S.c[l];
+        }
+      }
+      break;
+    }
+    case kOpFinish:
+      S.budget -= S.iters;
+      O.inner_total += S.iters;
+      O.prec_calls += 1;
+      if (O.status == MRCG_OK) {
+        if (S.done == kNotSpd) O.status = MRCG_ERR_NOT_SPD;
+        else if (S.done == kNonFinite) O.status = MRCG_ERR_NONFINITE;
+        else if (S.done == kMaxIter || S.done == kLoopCap) O.status = MRCG_ERR_MAXITER;
+      }
+      break;
+    case kOpBnorm:
+      O.bnorm = sqrt(tot[0]);
+      break;
+    case kOpResidAll:
+    case kOpResid: {
+      O.rnorm2 = tot[0];
+      const double rn = sqrt(tot[0]);
+      O.relres = O.bnorm > 0.0 ? rn / O.bnorm : rn;
+      if (!isfinite(O.relres)) O.status = MRCG_ERR_NONFINITE;
+      if (op == kOpResid) O.cur ^= 1;
+      break;
+    }
+    case kOpDelta:
+      O.delta = tot[0];
+      if (!isfinite(tot[0])) O.status = MRCG_ERR_NONFINITE;
+      break;
+    case kOpGamma: {
+      const double g2 = tot[0];
+      if (!isfinite(g2)) {
+        O.status = MRCG_ERR_NONFINITE;
+      } else if (O.mode == 1) {
+        if (g2 <= 0.0) {
+          O.status = MRCG_ERR_BREAKDOWN;
+        } else {
+          O.gamma = sqrt(g2);
+          O.gamma_old = 1.0;
+          O.gamma_new = O.gamma;
+          O.eta = O.gamma;
+          O.s = O.s_old = 0.0;
+          O.c = O.c_old = 1.0;
+        }
+      } else if (g2 < 0.0) {
+        O.status = MRCG_ERR_BREAKDOWN;
+      } else {
+        const double gnew = sqrt(g2);
+        const double a0 = O.c * O.delta - O.c_old * O.s * O.gamma;
+        const double a1 = sqrt(a0 * a0 + gnew * gnew);
+        const double a2 = O.s * O.delta + O.c_old * O.c * O.gamma;
+        const double a3 = O.s_old * O.gamma;
+        if (!(a1 > 0.0)) {
+          O.status = MRCG_ERR_BREAKDOWN;
+        } else {
+          const double c_new = a0 / a1, s_new = gnew / a1;
+          O.a1 = a1;
+          O.a2 = a2;
+          O.a3 = a3;
+          O.ceta = c_new * O.eta;
+          O.eta = -s_new * O.eta;
+          O.gamma_new = gnew;
+          O.c_old = O.c;
+          O.c = c_new;
+          O.s_old = O.s;
+          O.s = s_new;
+          O.gamma_old = O.gamma;
+          O.gamma = gnew;
+        }
+      }
+      break;
+    }
+  }
+}
+
+// loop control: ctl[0] executed bodies, ctl[1] their limit
+__global__ void sh_ctl_kernel(DevState* st, int nc, int* ctl, cudaGraphConditionalHandle handle) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < nc; i += blockDim.x)
+    if (in_round(st[i]) && st[i].cg.done == kRunning) atomicOr(&any, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ctl[0] += 1;
+    int go = any;
+    if (go && ctl[0] >= ctl[1]) {
+      go = 0;
+      for (int i = 0; i < nc; ++i)
+        if (in_round(st[i]) && st[i].cg.done == kRunning) st[i].cg.done = kLoopCap;
+    }
+    cudaGraphSetConditional(handle, go ? 1u : 0u);
+  }
+}
+
+__global__ void sh_ctl_reset_kernel(int* ctl) { ctl[0] = 0; }
+
+__global__ void sh_set_modes_kernel(DevState* st, const int* modes, int nc) {
+  for (int i = threadIdx.x; i < nc; i += blockDim.x) st[i].out.mode = modes[i];
+}
+
+// ------------------------------------------------------------------ graph of one inner solve
+
+cudaError_t add_kernel(cudaGraph_t g, cudaGraphNode_t* node, const cudaGraphNode_t* deps, size_t ndeps,
+                       const void* fn, int grid, int block, void** args) {
+  cudaKernelNodeParams p = {};
+  p.func = const_cast<void*>(fn);
+  p.gridDim = dim3(grid);
+  p.blockDim = dim3(block);
+  p.kernelParams = args;
+  return cudaGraphAddKernelNode(node, g, deps, ndeps, &p);
+}
+
+struct GSpec {
+  DevState* st;
+  const int* kcol;
+  int nc, ncp, grid, unroll, kv;
+  double* partials;
+  int* ctl;
+};
+
+template <typename T, int NM, int KV>
+cudaError_t build_graph(const GSpec& gs, const SArgs<T>& base, cudaGraph_t* out) {
+  cudaError_t e;
+  cudaGraph_t g;
+  if ((e = cudaGraphCreate(&g, 0))) return e;
+  SArgs<T> a[2] = {base, base};
+  a[1].p_old = base.p_new;
+  a[1].p_new = base.p_old;
+  DevState* st = gs.st;
+  const int* kcol = gs.kcol;
+  int nc = gs.nc, ncp = gs.ncp, nblk = gs.grid;
+  const double* partials = gs.partials;
+  int* ctl = gs.ctl;
+  int op_v = kOpVnorm, op_i = kOpInit, op_a = kOpA, op_b = kOpB, op_f = kOpFinish;
+  int nv1 = 1, nvk = KV + 1;
+  cudaGraphNode_t prev = nullptr, node;
+  auto chain = [&](const void* fn, int grid, int block, void** args, cudaGraph_t gg, cudaGraphNode_t* pv) {
+    cudaError_t ee = add_kernel(gg, &node, *pv ? pv : nullptr, *pv ? 1 : 0, fn, grid, block, args);
+    if (ee == cudaSuccess) *pv = node;
+    return ee;
+  };
+  void* r_args[] = {&ctl};
+  void* row0[] = {&a[0]};
+  void* sv_args[] = {&st, (void*)&kcol, &nc, &ncp, (void*)&partials, &nblk, &op_v, &nv1};
+  void* si_args[] = {&st, (void*)&kcol, &nc, &ncp, (void*)&partials, &nblk, &op_i, &nvk};
+  void* sa_args[] = {&st, (void*)&kcol, &nc, &ncp, (void*)&partials, &nblk, &op_a, &nv1};
+  void* sb_args[] = {&st, (void*)&kcol, &nc, &ncp, (void*)&partials, &nblk, &op_b, &nvk};
+  void* sf_args[] = {&st, (void*)&kcol, &nc, &ncp, (void*)&partials, &nblk, &op_f, &nv1};
+  cudaGraphNode_t nl;
+  if ((e = chain((const void*)sh_ctl_reset_kernel, 1, 1, r_args, g, &prev))) goto fail;
+  if ((e = chain((const void*)sh_vnorm_kernel<T, NM, KV>, gs.grid, kThreads, row0, g, &prev))) goto fail;
+  if ((e = chain((const void*)sh_scalar_kernel, nc, kThreads, sv_args, g, &prev))) goto fail;
+  if ((e = chain((const void*)sh_init_kernel<T, NM, KV>, gs.grid, kThreads, row0, g, &prev))) goto fail;
+  if ((e = chain((const void*)sh_scalar_kernel, nc, kThreads, si_args, g, &prev))) goto fail;
+  {
+    cudaGraphConditionalHandle h;
+    if ((e = cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault))) goto fail;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    if ((e = cudaGraphAddNode(&nl, g, &prev, nullptr, 1, &cp))) goto fail;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaGraphNode_t bp = nullptr;
+    for (int it = 0; it < gs.unroll; ++it) {
+      void* aa[] = {&a[it & 1]};
+      if ((e = chain((const void*)sh_step_a_kernel<T, NM, KV>, gs.grid, kThreads, aa, body, &bp))) goto fail;
+      if ((e = chain((const void*)sh_scalar_kernel, nc, kThreads, sa_args, body, &bp))) goto fail;
+      if ((e = chain((const void*)sh_step_b_kernel<T, NM, KV>, gs.grid, kThreads, aa, body, &bp))) goto fail;
+      if ((e = chain((const void*)sh_scalar_kernel, nc, kThreads, sb_args, body, &bp))) goto fail;
+    }
+    void* ctl_args[] = {&st, &nc, &ctl, &h};
+    if ((e = chain((const void*)sh_ctl_kernel, 1, 256, ctl_args, body, &bp))) goto fail;
+    prev = nl;
+  }
+  if ((e = chain((const void*)sh_finish_kernel<T, NM>, gs.grid, kThreads, row0, g, &prev))) goto fail;
+  if ((e = chain((const void*)sh_scalar_kernel, nc, kThreads, sf_args, g, &prev))) goto fail;
+  *out = g;
+  return cudaSuccess;
+fail:
+  cudaGraphDestroy(g);
+  return e;
+}
+
+template <typename T, int NM, int KV>
+int occupancy_t() {
+  int a = 1, b = 1, i = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, (const void*)sh_step_a_kernel<T, NM, KV>, kThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, (const void*)sh_step_b_kernel<T, NM, KV>, kThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&i, (const void*)sh_init_kernel<T, NM, KV>, kThreads, 0);
+  return std::max(1, std::min({a, b, i}));
+}
+
+}  // namespace shifted
+}  // namespace mrcg
+
+// ====================================================================== host side
+
+using namespace mrcg;
+using namespace mrcg::shifted;
+
+struct mrcg_shifted {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int nshift = 0, nrhs = 0, nc = 0, ncp = 0, nm = 0, kv = 0, kmax = 0;
+  bool fp32 = false;
+  int max_outer = 200;
+  double restart_factor = 0.5;
+  int64_t n = 0;
+  std::vector<double> lam2;  // [nc][kMaxK]
+  std::vector<int> kcol;
+  DevState* d_st = nullptr;
+  DevState* h_st = nullptr;
+  DevState* h_init = nullptr;
+  int* h_modes = nullptr;
+  int* d_modes = nullptr;
+  int* d_kcol = nullptr;
+  int* d_ctl = nullptr;
+  double* d_sigma = nullptr;
+  double* d_partials = nullptr;
+  int64_t* d_rowptr = nullptr;
+  int32_t* d_col = nullptr;
+  double* d_val64 = nullptr;
+  float* d_val32 = nullptr;
+  double* d_V64 = nullptr;
+  float* d_V32 = nullptr;
+  double *x = nullptr, *b = nullptr, *res = nullptr, *zraw = nullptr, *zn = nullptr;
+  double *v0 = nullptr, *v1 = nullptr, *w0 = nullptr, *w1 = nullptr;
+  void *iz = nullptr, *ir = nullptr, *ip0 = nullptr, *ip1 = nullptr, *iq = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int grid = 1, unroll = 4;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+#define SCK(call)                                                                                 \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) {                                                                      \
+      if (getenv("MRCG_DEBUG")) fprintf(stderr, "mrcg shifted: %s failed: %s (%s:%d)\n", #call,   \
+                                        cudaGetErrorString(e_), __FILE__, __LINE__);              \
+      return e_ == cudaErrorMemoryAllocation ? MRCG_ERR_OOM : MRCG_ERR_CUDA;                      \
+    }                                                                                             \
+  } while (0)
+#define SST(call)                   \
+  do {                              \
+    mrcg_status s_ = (call);        \
+    if (s_ != MRCG_OK) return s_;   \
+  } while (0)
+
+bool sdev_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+mrcg_status salloc(mrcg_shifted* h, T** p, size_t count) {
+  void* q = nullptr;
+  if (cudaMalloc(&q, count * sizeof(T) + 256) != cudaSuccess) {
+    cudaGetLastError();
+    return MRCG_ERR_OOM;
+  }
+  h->allocs.push_back(q);
+  *p = reinterpret_cast<T*>(q);
+  return MRCG_OK;
+}
+
+template <typename T>
+mrcg_status sfetch(const T* src, size_t count, std::vector<T>& dst) {
+  dst.resize(count);
+  if (!count) return MRCG_OK;
+  if (sdev_ptr(src)) SCK(cudaMemcpy(dst.data(), src, count * sizeof(T), cudaMemcpyDeviceToHost));
+  else std::memcpy(dst.data(), src, count * sizeof(T));
+  return MRCG_OK;
+}
+
+template <typename T>
+SArgs<T> sargs(mrcg_shifted* h) {
+  SArgs<T> a = {};
+  a.st = h->d_st;
+  a.kcol = h->d_kcol;
+  a.nc = h->nc;
+  a.ncp = h->ncp;
+  a.partials = h->d_partials;
+  a.n = h->n;
+  a.rowptr = h->d_rowptr;
+  a.colind = h->d_col;
+  a.val = reinterpret_cast<const T*>(sizeof(T) == 4 ? (const void*)h->d_val32 : (const void*)h->d_val64);
+  a.V = reinterpret_cast<const T*>(sizeof(T) == 4 ? (const void*)h->d_V32 : (const void*)h->d_V64);
+  a.sigma = h->d_sigma;
+  a.z = reinterpret_cast<T*>(h->iz);
+  a.r = reinterpret_cast<T*>(h->ir);
+  a.p_old = reinterpret_cast<T*>(h->ip0);
+  a.p_new = reinterpret_cast<T*>(h->ip1);
+  a.q = reinterpret_cast<T*>(h->iq);
+  a.v0 = h->v0;
+  a.v1 = h->v1;
+  a.zraw = h->zraw;
+  return a;
+}
+
+template <typename T, int NM, int KV>
+mrcg_status build_t(mrcg_shifted* h, int nsm) {
+  h->grid = std::max(1, nsm * occupancy_t<T, NM, KV>());
+  GSpec gs = {};
+  gs.st = h->d_st;
+  gs.kcol = h->d_kcol;
+  gs.nc = h->nc;
+  gs.ncp = h->ncp;
+  gs.grid = h->grid;
+  gs.unroll = h->unroll;
+  gs.kv = KV;
+  gs.partials = h->d_partials;
+  gs.ctl = h->d_ctl;
+  const cudaError_t e = build_graph<T, NM, KV>(gs, sargs<T>(h), &h->graph);
+  SCK(e);
+  return MRCG_OK;
+}
+
+mrcg_status build_any(mrcg_shifted* h, int nsm) {
+  if (h->fp32) {
+    if (h->nm == 1) return h->kv == 8 ? build_t<float, 1, 8>(h, nsm) : build_t<float, 1, 32>(h, nsm);
+    return h->kv == 8 ? build_t<float, 2, 8>(h, nsm) : build_t<float, 2, 32>(h, nsm);
+  }
+  if (h->nm == 1) return h->kv == 8 ? build_t<double, 1, 8>(h, nsm) : build_t<double, 1, 32>(h, nsm);
+  return h->kv == 8 ? build_t<double, 2, 8>(h, nsm) : build_t<double, 2, 32>(h, nsm);
+}
+
+mrcg_status shifted_create_impl(const mrcg_create_args* L, int32_t nshift, const double* sigma,
+                                const int32_t* k_per_shift, int32_t nrhs, mrcg_shifted* h) {
+  const int64_t n = L->n;
+  h->n = n;
+  h->nshift = nshift;
+  h->nrhs = nrhs;
+  h->nc = nshift * nrhs;
+  h->ncp = h->nc <= 32 ? 32 : 64;
+  h->nm = h->ncp / 32;
+  h->kmax = L->k;
+  h->kv = L->k <= 8 ? 8 : 32;
+  h->fp32 = L->precision == MRCG_MIXED_FP32;
+  h->max_outer = L->max_outer > 0 ? L->max_outer : 200;
+  h->restart_factor = L->restart_factor == 0.0 ? 0.5 : L->restart_factor;
+  if (L->stream) {
+    h->stream = (cudaStream_t)L->stream;
+  } else {
+    SCK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    h->own_stream = true;
+  }
+  std::vector<int64_t> rp;
+  std::vector<int32_t> ci;
+  std::vector<double> va, V, lamL, sig;
+  std::vector<int32_t> kps;
+  SST(sfetch(L->rowptr, (size_t)n + 1, rp));
+  SST(sfetch(L->colind, (size_t)L->nnz, ci));
+  SST(sfetch(L->val, (size_t)L->nnz, va));
+  SST(sfetch(L->V, (size_t)n * L->k, V));
+  SST(sfetch(L->lambda, (size_t)L->k, lamL));
+  SST(sfetch(sigma, (size_t)nshift, sig));
+  SST(sfetch(k_per_shift, (size_t)nshift, kps));
+  if (rp[0] != 0 || rp[n] != L->nnz) return MRCG_ERR_INVALID;
+  for (int64_t r = 0; r < n; ++r) {
+    if (rp[r + 1] < rp[r]) return MRCG_ERR_INVALID;
+    for (int64_t p = rp[r]; p < rp[r + 1]; ++p) {
+      if (ci[p] < 0 || ci[p] >= n || (p > rp[r] && ci[p] <= ci[p - 1])) return MRCG_ERR_INVALID;
+      if (!std::isfinite(va[p])) return MRCG_ERR_NONFINITE;
+    }
+  }
+  h->kcol.assign(h->ncp, 0);
+  h->lam2.assign((size_t)h->nc * kMaxK, 0.0);
+  std::vector<double> sigc(h->ncp, 0.0);
+  for (int j = 0; j < nshift; ++j) {
+    if (kps[j] < 0 || kps[j] > L->k || !std::isfinite(sig[j])) return MRCG_ERR_INVALID;
+    for (int l = 0; l < kps[j]; ++l)
+      if (!(lamL[l] - sig[j] < 0.0)) return MRCG_ERR_INVALID;  // the first k_j must be negative after the shift
+    for (int r = 0; r < nrhs; ++r) {
+      const int c = j * nrhs + r;
+      h->kcol[c] = kps[j];
+      sigc[c] = sig[j];
+      for (int l = 0; l < kps[j]; ++l) h->lam2[(size_t)c * kMaxK + l] = 2.0 * std::fabs(lamL[l] - sig[j]);
+    }
+  }
+  // ---- device data: CSR of L, row-major V (n x kv), shifts
+  SST(salloc(h, &h->d_rowptr, rp.size()));
+  SST(salloc(h, &h->d_col, ci.size() + 1));
+  SST(salloc(h, &h->d_val64, va.size() + 1));
+  SCK(cudaMemcpyAsync(h->d_rowptr, rp.data(), rp.size() * 8, cudaMemcpyHostToDevice, h->stream));
+  SCK(cudaMemcpyAsync(h->d_col, ci.data(), ci.size() * 4, cudaMemcpyHostToDevice, h->stream));
+  SCK(cudaMemcpyAsync(h->d_val64, va.data(), va.size() * 8, cudaMemcpyHostToDevice, h->stream));
+  std::vector<double> Vr((size_t)n * h->kv, 0.0);
+  for (int64_t i = 0; i < n; ++i)
+    for (int l = 0; l < L->k; ++l) Vr[(size_t)i * h->kv + l] = V[(size_t)l * n + i];
+  SST(salloc(h, &h->d_V64, Vr.size()));
+  SCK(cudaMemcpyAsync(h->d_V64, Vr.data(), Vr.size() * 8, cudaMemcpyHostToDevice, h->stream));
+  if (h->fp32) {
+    SST(salloc(h, &h->d_val32, va.size() + 1));
+    SST(salloc(h, &h->d_V32, Vr.size()));
+    if (launch_to_f32(h->stream, h->d_val64, h->d_val32, (int64_t)va.size())) return MRCG_ERR_CUDA;
+    if (launch_to_f32(h->stream, h->d_V64, h->d_V32, (int64_t)Vr.size())) return MRCG_ERR_CUDA;
+  }
+  SST(salloc(h, &h->d_sigma, (size_t)h->ncp));
+  SST(salloc(h, &h->d_kcol, (size_t)h->ncp));
+  SCK(cudaMemcpyAsync(h->d_sigma, sigc.data(), h->ncp * 8, cudaMemcpyHostToDevice, h->stream));
+  SCK(cudaMemcpyAsync(h->d_kcol, h->kcol.data(), h->ncp * 4, cudaMemcpyHostToDevice, h->stream));
+  // ---- interleaved vectors n x ncp
+  const size_t cnt = (size_t)n * h->ncp;
+  double** f64[] = {&h->x, &h->b, &h->res, &h->zraw, &h->zn, &h->v0, &h->v1, &h->w0, &h->w1};
+  for (double** p : f64) {
+    SST(salloc(h, p, cnt));
+    SCK(cudaMemsetAsync(*p, 0, cnt * 8, h->stream));
+  }
+  const size_t esz = h->fp32 ? 4 : 8;
+  void** inner[] = {&h->iz, &h->ir, &h->ip0, &h->ip1, &h->iq};
+  for (void** p : inner) {
+    char* q;
+    SST(salloc(h, &q, cnt * esz));
+    SCK(cudaMemsetAsync(q, 0, cnt * esz, h->stream));
+    *p = q;
+  }
+  SST(salloc(h, &h->d_st, (size_t)h->nc));
+  SST(salloc(h, &h->d_modes, (size_t)h->nc));
+  SST(salloc(h, &h->d_ctl, 2));
+  SCK(cudaMemsetAsync(h->d_st, 0, h->nc * sizeof(DevState), h->stream));
+  SCK(cudaMallocHost(&h->h_st, h->nc * sizeof(DevState)));
+  SCK(cudaMallocHost(&h->h_init, h->nc * sizeof(DevState)));
+  SCK(cudaMallocHost(&h->h_modes, h->nc * sizeof(int)));
+  int nsm = 1;
+  SCK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
+  // partials: (kv + 1) values x ncp columns x grid blocks; grid <= nsm * 8
+  SST(salloc(h, &h->d_partials, (size_t)(h->kv + 1) * h->ncp * nsm * 8));
+  if (const char* u = getenv("MRCG_UNROLL")) h->unroll = std::max(2, atoi(u) & ~1);
+  SST(build_any(h, nsm));
+  if (h->grid > nsm * 8) return MRCG_ERR_INVALID;
+  SCK(cudaGraphInstantiate(&h->exec, h->graph, 0));
+  SCK(cudaStreamSynchronize(h->stream));
+  return MRCG_OK;
+}
+
+void shifted_destroy_impl(mrcg_shifted* h) {
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->exec) cudaGraphExecDestroy(h->exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->h_st) cudaFreeHost(h->h_st);
+  if (h->h_init) cudaFreeHost(h->h_init);
+  if (h->h_modes) cudaFreeHost(h->h_modes);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  cudaGetLastError();
+  delete h;
+}
+
+OArgs soargs(mrcg_shifted* h) {
+  OArgs a = {};
+  a.st = h->d_st;
+  a.nc = h->nc;
+  a.ncp = h->ncp;
+  a.partials = h->d_partials;
+  a.n = h->n;
+  a.rowptr = h->d_rowptr;
+  a.colind = h->d_col;
+  a.val = h->d_val64;
+  a.sigma = h->d_sigma;
+  a.x = h->x;
+  a.b = h->b;
+  a.res = h->res;
+  a.zraw = h->zraw;
+  a.zn = h->zn;
+  a.v0 = h->v0;
+  a.v1 = h->v1;
+  a.w0 = h->w0;
+  a.w1 = h->w1;
+  return a;
+}
+
+// pitched copy between the user's n x nc row-major block and the n x ncp device block
+mrcg_status sstage(mrcg_shifted* h, const double* user, double* dev, bool to_dev) {
+  const bool ud = sdev_ptr(user);
+  const size_t upitch = (size_t)h->nc * 8, dpitch = (size_t)h->ncp * 8;
+  if (to_dev)
+    SCK(cudaMemcpy2DAsync(dev, dpitch, user, upitch, upitch, (size_t)h->n,
+                          ud ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+  else
+    SCK(cudaMemcpy2DAsync(const_cast<double*>(user), upitch, dev, dpitch, upitch, (size_t)h->n,
+                          ud ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+  return MRCG_OK;
+}
+
+template <int NM>
+void launch_outer(mrcg_shifted* h, int which, const OArgs& oa, int want) {
+  const int g = h->grid;
+  switch (which) {
+    case 0: sh_bnorm_kernel<NM><<<g, kThreads, 0, h->stream>>>(oa); break;
+    case 1: sh_residual_kernel<NM><<<g, kThreads, 0, h->stream>>>(oa, want); break;
+    case 2: sh_cycle_start_kernel<NM><<<g, kThreads, 0, h->stream>>>(oa); break;
+    case 3: sh_lanczos_spmv_kernel<NM><<<g, kThreads, 0, h->stream>>>(oa); break;
+    case 4: sh_lanczos_update_kernel<NM><<<g, kThreads, 0, h->stream>>>(oa); break;
+    case 5: sh_gamma_kernel<NM><<<g, kThreads, 0, h->stream>>>(oa); break;
+    case 6: sh_minres_update_kernel<NM><<<g, kThreads, 0, h->stream>>>(oa); break;
+  }
+}
+
+void outer(mrcg_shifted* h, int which, const OArgs& oa, int want = 0) {
+  if (h->nm == 1) launch_outer<1>(h, which, oa, want);
+  else launch_outer<2>(h, which, oa, want);
+}
+
+void scalar(mrcg_shifted* h, int op) {
+  sh_scalar_kernel<<<h->nc, kThreads, 0, h->stream>>>(h->d_st, h->d_kcol, h->nc, h->ncp, h->d_partials, h->grid, op,
+                                                      1);
+}
+
+mrcg_status shifted_solve_impl(mrcg_shifted* h, const double* B, double* X, double outer_tol, double inner_tol,
+                               int64_t max_iters, mrcg_info* infos) {
+  const int S = h->nc;
+  const long long budget = max_iters > 0 ? (long long)max_iters : (1LL << 31);
+  SST(sstage(h, B, h->b, true));
+  SST(sstage(h, X, h->x, true));
+  for (int i = 0; i < S; ++i) {
+    DevState& d = h->h_init[i];
+    std::memset(&d, 0, sizeof(DevState));
+    for (int l = 0; l < kMaxK; ++l) d.cg.lam2[l] = h->lam2[(size_t)i * kMaxK + l];
+    d.cg.inner_tol = inner_tol;
+    d.cg.budget = budget;
+    d.cg.done = kConverged;
+    d.out.status = MRCG_OK;
+  }
+  SCK(cudaMemcpyAsync(h->d_st, h->h_init, S * sizeof(DevState), cudaMemcpyHostToDevice, h->stream));
+  {
+    int ctl_host[2] = {0, (int)std::min<long long>(budget / h->unroll + 2, 0x7fffffffLL)};
+    SCK(cudaMemcpyAsync(h->d_ctl, ctl_host, sizeof(ctl_host), cudaMemcpyHostToDevice, h->stream));
+    SCK(cudaStreamSynchronize(h->stream));
+  }
+  const OArgs oa = soargs(h);
+  outer(h, 0, oa);
+  scalar(h, kOpBnorm);
+  outer(h, 1, oa, 0);
+  scalar(h, kOpResidAll);
+  SCK(cudaGetLastError());
+  SCK(cudaMemcpyAsync(h->h_st, h->d_st, S * sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+  SCK(cudaStreamSynchronize(h->stream));
+  std::vector<int> mode(S, 0), outer_it(S, 0), restarts(S, 0), hist_len(S, 0);
+  std::vector<mrcg_status> status(S, MRCG_ERR_MAXITER);
+  std::vector<double> relres(S, 0.0);
+  std::vector<std::vector<double>> cyc(S);
+  int active = 0;
+  bool zero_x = false;
+  for (int i = 0; i < S; ++i) {
+    const OuterState& O = h->h_st[i].out;
+    relres[i] = O.relres;
+    if (O.status != MRCG_OK || !std::isfinite(O.bnorm)) {
+      status[i] = MRCG_ERR_NONFINITE;
+    } else if (O.bnorm == 0.0) {
+      zero_x = true;
+      relres[i] = 0.0;
+      status[i] = MRCG_OK;
+    } else if (O.relres <= outer_tol) {
+      status[i] = MRCG_OK;
+    } else {
+      mode[i] = 1;
+      ++active;
+    }
+  }
+  long long launches = 4;
+  while (active > 0) {
+    for (int i = 0; i < S; ++i) {
+      if (mode[i] == 2 && outer_it[i] >= h->max_outer) {
+        mode[i] = 0;
+        status[i] = MRCG_ERR_MAXITER;
+        --active;
+      }
+      h->h_modes[i] = mode[i];
+    }
+    if (active == 0) break;
+    SCK(cudaMemcpyAsync(h->d_modes, h->h_modes, S * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    sh_set_modes_kernel<<<1, 256, 0, h->stream>>>(h->d_st, h->d_modes, S);
+    outer(h, 2, oa);
+    outer(h, 3, oa);
+    scalar(h, kOpDelta);
+    outer(h, 4, oa);
+    SCK(cudaGetLastError());
+    SCK(cudaGraphLaunch(h->exec, h->stream));
+    outer(h, 5, oa);
+    scalar(h, kOpGamma);
+    outer(h, 6, oa);
+    outer(h, 1, oa, 2);
+    scalar(h, kOpResid);
+    launches += 11;
+    SCK(cudaGetLastError());
+    SCK(cudaMemcpyAsync(h->h_st, h->d_st, S * sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+    SCK(cudaStreamSynchronize(h->stream));
+    int ctl[2] = {0, 0};
+    SCK(cudaMemcpy(ctl, h->d_ctl, sizeof(ctl), cudaMemcpyDeviceToHost));
+    launches += 7 + (long long)ctl[0] * (4LL * h->unroll + 1);
+    for (int i = 0; i < S; ++i) {
+      const OuterState& O = h->h_st[i].out;
+      if (mode[i] == 0) continue;
+      if (O.status != MRCG_OK) {
+        status[i] = (mrcg_status)O.status;
+        mode[i] = 0;
+        --active;
+        continue;
+      }
+      if (mode[i] == 1) {
+        mode[i] = 2;
+        cyc[i].clear();
+        continue;
+      }
+      ++outer_it[i];
+      relres[i] = O.relres;
+      mrcg_info* inf = infos ? &infos[i] : nullptr;
+      if (inf && inf->relres_history && hist_len[i] < inf->history_cap) inf->relres_history[hist_len[i]] = O.relres;
+      ++hist_len[i];
+      if (O.relres <= outer_tol) {
+        status[i] = MRCG_OK;
+        mode[i] = 0;
+        --active;
+        continue;
+      }
+      cyc[i].push_back(O.relres);
+      const size_t m = cyc[i].size();
+      if ((h->restart_factor > 0.0 && m >= 4 && O.relres > h->restart_factor * cyc[i][m - 4]) || O.gamma_new == 0.0) {
+        ++restarts[i];
+        mode[i] = 1;
+      }
+    }
+  }
+  if (zero_x) {
+    // columns with b = 0 return x = 0: zero them through a staged host copy
+    std::vector<double> xs((size_t)h->n * h->nc);
+    SST(sstage(h, xs.data(), h->x, false));
+    SCK(cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < S; ++i)
+      if (h->h_st[i].out.bnorm == 0.0)
+        for (int64_t r = 0; r < h->n; ++r) xs[(size_t)r * h->nc + i] = 0.0;
+    SST(sstage(h, xs.data(), h->x, true));
+  }
+  SST(sstage(h, X, h->x, false));
+  SCK(cudaMemcpyAsync(h->h_st, h->d_st, S * sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+  SCK(cudaStreamSynchronize(h->stream));
+  mrcg_status worst = MRCG_OK;
+  for (int i = 0; i < S; ++i) {
+    if (infos) {
+      mrcg_info& inf = infos[i];
+      inf.outer_iters = outer_it[i];
+      inf.restarts = restarts[i];
+      inf.inner_iters_total = h->h_st[i].out.inner_total;
+      inf.prec_calls = h->h_st[i].out.prec_calls;
+      inf.true_relres = relres[i];
+      inf.history_len = inf.relres_history ? std::min(hist_len[i], inf.history_cap) : 0;
+      inf.status = status[i];
+      inf.kernel_launches = launches;
+    }
+    if (status[i] != MRCG_OK && worst == MRCG_OK) worst = status[i];
+  }
+  return worst;
+}
+
+}  // namespace
+
+extern "C" {
+
+mrcg_status mrcg_shifted_create(const mrcg_create_args* L, int32_t nshift, const double* sigma,
+                                const int32_t* k_per_shift, int32_t nrhs_per_shift, mrcg_shifted_handle* out) {
+  if (!L || !sigma || !k_per_shift || !out || nshift < 1 || nrhs_per_shift < 1) return MRCG_ERR_INVALID;
+  *out = nullptr;
+  if ((int64_t)nshift * nrhs_per_shift > kMaxCols || L->n < 1 || L->n > (int64_t)0x7fffff00 || L->k < 0 ||
+      L->k > kMaxK || !L->rowptr || (L->nnz > 0 && (!L->colind || !L->val)) || (L->k > 0 && (!L->V || !L->lambda)))
+    return MRCG_ERR_INVALID;
+  if (L->precision != MRCG_FP64 && L->precision != MRCG_MIXED_FP32) return MRCG_ERR_INVALID;
+  if (L->inner_prec != MRCG_MCG_IDENTITY) return MRCG_ERR_INVALID;
+  mrcg_shifted* h = new (std::nothrow) mrcg_shifted();
+  if (!h) return MRCG_ERR_OOM;
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    delete h;
+    return MRCG_ERR_CUDA;
+  }
+  mrcg_status s = shifted_create_impl(L, nshift, sigma, k_per_shift, nrhs_per_shift, h);
+  if (s != MRCG_OK) {
+    cudaGetLastError();
+    shifted_destroy_impl(h);
+    return s;
+  }
+  *out = h;
+  return MRCG_OK;
+}
+
+mrcg_status mrcg_shifted_solve(mrcg_shifted_handle h, const double* B, double* X, double outer_tol, double inner_tol,
+                               int64_t max_iters, mrcg_info* infos) {
+  if (!h || !B || !X) return MRCG_ERR_INVALID;
+  if (!(outer_tol >= 0.0) || !(inner_tol > 0.0) || !(inner_tol < 1.0)) return MRCG_ERR_INVALID;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != h->device) cudaSetDevice(h->device);
+  const auto t0 = std::chrono::steady_clock::now();
+  mrcg_status s = shifted_solve_impl(h, B, X, outer_tol, inner_tol, max_iters, infos);
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (infos)
+    for (int i = 0; i < h->nc; ++i) infos[i].solve_ms = ms;
+  if (prev >= 0 && prev != h->device) cudaSetDevice(prev);
+  return s;
+}
+
+int32_t mrcg_shifted_columns(mrcg_shifted_handle h) { return h ? h->nc : 0; }
+
+void mrcg_shifted_destroy(mrcg_shifted_handle h) {
+  if (h) shifted_destroy_impl(h);
+}
+
+}  // extern "C"

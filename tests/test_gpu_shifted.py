@@ -1,0 +1,90 @@
+"""GPU parity of the shifted-family / right-hand-side-block solver: every
+column (shift j, right-hand side r) is checked against the FP64 CPU oracle
+run on that column as a stand-alone system A_j = L - sigma_j I with
+V_hat_j = V[:, :k_j], Lambda_hat_j = lambda_L[:k_j] - sigma_j."""
+import numpy as np
+import pytest
+
+import oracle as O
+from gen import small_shifted
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1805_12417_gb300 as m  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def fam():
+    return small_shifted()
+
+
+@pytest.fixture(scope="module")
+def oracle_x(fam):
+    xs = []
+    for c in range(fam.ncols):
+        p = fam.column_problem(c)
+        r = O.minres_cg(O.System.from_problem(p), p.b, outer_tol=1e-12, inner_tol=1e-3)
+        assert r.status == O.OK
+        xs.append(r.x)
+    return np.stack(xs, axis=1)
+
+
+@pytest.mark.parametrize("device", [True, False], ids=["device_ptrs", "host_ptrs"])
+def test_shifted_fp64_matches_oracle(fam, oracle_x, device):
+    with m.Shifted(fam) as sh:
+        if device:
+            X = torch.zeros(fam.n, fam.ncols, dtype=torch.float64, device=DEV)
+            _, st, infos = sh.solve(torch.from_numpy(fam.B).to(DEV), X, outer_tol=1e-12)
+            X = X.cpu().numpy()
+        else:
+            X, st, infos = sh.solve(fam.B.copy(), outer_tol=1e-12)
+    assert st == m.OK
+    for c in range(fam.ncols):
+        p = fam.column_problem(c)
+        x = X[:, c]
+        assert infos[c].status == m.OK
+        assert np.linalg.norm(x - oracle_x[:, c]) <= 1e-8 * np.linalg.norm(oracle_x[:, c])
+        assert np.linalg.norm(x - p.xstar) <= 1e-8 * np.linalg.norm(p.xstar)
+        assert O.System.from_problem(p).true_relres(p.b, x) <= 1e-11
+
+
+def test_shifted_mixed_reaches_fp64_residual(fam):
+    with m.Shifted(fam, precision=m.MIXED_FP32) as sh:
+        X, st, infos = sh.solve(fam.B.copy(), outer_tol=1e-10)
+    assert st == m.OK
+    for c in range(fam.ncols):
+        p = fam.column_problem(c)
+        assert O.System.from_problem(p).true_relres(p.b, X[:, c]) <= 1e-10
+
+
+def test_shifted_column_edge_cases(fam):
+    B = fam.B.copy()
+    B[:, 1] = 0.0
+    X0 = np.zeros_like(B)
+    X0[:, 2] = fam.xstar[:, 2]
+    with m.Shifted(fam) as sh:
+        X, st, infos = sh.solve(B, X0.copy(), outer_tol=1e-10)
+        assert infos[1].status == m.OK and infos[1].outer_iters == 0 and not X[:, 1].any()
+        assert infos[2].outer_iters == 0
+        assert all(i.status == m.OK for i in infos)
+        X, st, infos = sh.solve(fam.B.copy(), outer_tol=1e-12, max_iters=5)
+        assert st == m.ERR_MAXITER and all(i.inner_iters_total <= 5 for i in infos)
+
+
+def test_shifted_matches_batch_of_separate_systems(fam):
+    """The shared-operator engine and the batched engine solve the same
+    systems: the solutions agree to the FP64 tolerance."""
+    ps = [fam.column_problem(c) for c in range(fam.ncols)]
+    with m.Batch(ps) as bt:
+        Xb, st, _ = bt.solve(np.concatenate([p.b for p in ps]), outer_tol=1e-12)
+        xb = bt.split(Xb)
+    with m.Shifted(fam) as sh:
+        X, st2, _ = sh.solve(fam.B.copy(), outer_tol=1e-12)
+    for c in range(fam.ncols):
+        assert np.linalg.norm(X[:, c] - xb[c]) <= 1e-8 * np.linalg.norm(xb[c])
