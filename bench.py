@@ -42,9 +42,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["lap3d_128", "batch64"], default="lap3d_128",
+    ap.add_argument("--workload", choices=["lap3d_128", "batch64", "shifted64"], default="lap3d_128",
                     help="lap3d_128: the headline single-system workload; batch64: 64 independent uneven "
-                         "2D systems (sides 100..400, k_i 1..16, seed 3) solved as one batch")
+                         "2D systems (sides 100..400, k_i 1..16, seed 3) solved as one batch; shifted64: 16 "
+                         "shifts x 4 RHS of the 160^3 Laplacian as one right-hand-side block")
     return ap.parse_args()
 
 
@@ -279,6 +280,90 @@ def run_batch64(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_shifted64(args, ws, rank, local):
+    """16 shifts x 4 right-hand sides of the 160^3 Laplacian solved as one
+    right-hand-side block; a step is one solve of all 64 columns."""
+    import torch
+
+    from gen import config5
+    from paper_1805_12417_gb300 import build as _b
+    _b.build()
+    import paper_1805_12417_gb300 as m
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    fam = config5()
+    Bd = torch.from_numpy(fam.B).to(dev)
+    Xd = torch.zeros_like(Bd)
+    out = {}
+    n, nc = fam.n, fam.ncols
+    for name, prec, steps, warm in (("mixed", m.MIXED_FP32, args.steps, args.warmup), ("fp64", m.FP64, 1, 1)):
+        with m.Shifted(fam, precision=prec, stream=stream.cuda_stream) as sh:
+            for _ in range(warm):
+                Xd.zero_()
+                sh.solve(Bd, Xd, outer_tol=OUTER_TOL, inner_tol=INNER_TOL)
+            barrier(ws)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ck = Clocks(local) if (rank == 0 and name == "mixed") else None
+            if ck:
+                ck.__enter__()
+            e0.record(stream)
+            ok, infos = 0, None
+            for _ in range(steps):
+                Xd.zero_()
+                _, st, infos = sh.solve(Bd, Xd, outer_tol=OUTER_TOL, inner_tol=INNER_TOL)
+                ok += sum(1 for i in infos if i.status == m.OK and i.true_relres <= OUTER_TOL)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            barrier(ws)
+            if ck:
+                ck.__exit__(None, None, None)
+            ms = max_over_ranks(e0.elapsed_time(e1), ws, dev)
+            ok = sum_over_ranks(ok, ws, dev)
+            w = 4 if prec == m.MIXED_FP32 else 8
+            iters = max(i.inner_iters_total for i in infos)  # lock-step block iterations
+            byts = iters * (fam.nnz * (w + 4) + 10 * n * 64 * w + 2 * n * 32 * w)
+            xh = Xd.cpu().numpy()
+            err = max(float(np.linalg.norm(xh[:, c] - fam.xstar[:, c]) / np.linalg.norm(fam.xstar[:, c]))
+                      for c in range(nc))
+            out[name] = {"value": ok / (ms / 1000.0), "ms_per_step": ms / steps, "steps": steps,
+                         "inner_gbs": byts / (ms / steps * 1e-3) / 1e9, "launches": infos[0].kernel_launches,
+                         "inner_iters_max": iters, "outer_iters_max": max(i.outer_iters for i in infos),
+                         "max_rel_err_vs_xstar": err, "clocks": ck.summary() if ck else None}
+            if name == "mixed":
+                b_h = torch.from_numpy(fam.B.copy()).pin_memory()
+                x_h = torch.zeros(fam.B.shape, dtype=torch.float64).pin_memory()
+                t0 = time.perf_counter()
+                ok_e2e = 0
+                for _ in range(steps):
+                    x_h.zero_()
+                    _, st, inf = sh.solve(b_h, x_h, outer_tol=OUTER_TOL, inner_tol=INNER_TOL)
+                    ok_e2e += sum(1 for i in inf if i.status == m.OK and i.true_relres <= OUTER_TOL)
+                out["e2e"] = {"value": ok_e2e / (time.perf_counter() - t0), "unit": "solves/s",
+                              "h2d_bytes_per_step": 2 * n * nc * 8, "d2h_bytes_per_step": n * nc * 8}
+    if rank == 0:
+        peak, kind = measured_peak_gbs()
+        mx = out["mixed"]
+        line = {"metric": METRIC, "value": mx["value"], "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": mx["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner CG + f64 outer MINRES",
+                "data": "synthetic",
+                "config": {"workload": "shifted64: 3D 7-pt Laplacian 160^3 (n=4,096,000), 16 shifts with k_j "
+                                       "U{1..30} cluster-rounded (seed 4), 4 RHS each, one 64-column block",
+                           "columns": nc, "outer_tol": OUTER_TOL, "inner_tol": INNER_TOL,
+                           "l2": "inputs larger than L2", "parallelism": "replicas" if ws > 1 else "single GPU"},
+                "roofline": {"kernel": "whole inner loop (block step a + step b)", "bound": "hbm",
+                             "achieved": round(mx["inner_gbs"], 1), "peak": peak, "unit": "GB/s",
+                             "frac": round(mx["inner_gbs"] / peak, 4), "traffic": None,
+                             "peak_kind": f"{kind} copy bandwidth"},
+                "fp64": out["fp64"], "mixed": mx, "mixed_vs_fp64_speedup": mx["value"] / out["fp64"]["value"],
+                "e2e": out["e2e"], "gpu_launches": int(mx["launches"] * args.steps), "clocks": mx["clocks"],
+                "cpu_baseline": None}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup()
@@ -287,6 +372,9 @@ def main():
         return
     if args.workload == "batch64":
         run_batch64(args, ws, rank, local)
+        return
+    if args.workload == "shifted64":
+        run_shifted64(args, ws, rank, local)
         return
     import torch
 

@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(kThreads) b_vnorm_kernel(DevState* st, const S
 }
 
 template <typename T, int KB>
-__global__ void __launch_bounds__(kThreads) b_init_kernel(BArgs<T> a) {
+__global__ void __launch_bounds__(kThreads, KB >= 32 ? 2 : 4) b_init_kernel(BArgs<T> a) {
   constexpr int W = V16<T>::W;
   constexpr int KS = KB > 0 ? KB : 1;
   const bool jac = a.dinv != nullptr;
@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(kThreads, 4) b_step_a_kernel(BArgs<T> a) {
 }
 
 template <typename T, int KB>
-__global__ void __launch_bounds__(kThreads) b_step_b_kernel(BArgs<T> a) {
+__global__ void __launch_bounds__(kThreads, KB >= 32 ? 2 : 4) b_step_b_kernel(BArgs<T> a) {
   constexpr int W = V16<T>::W;
   constexpr int KS = KB > 0 ? KB : 1;
   const bool jac = a.dinv != nullptr;
@@ -726,7 +726,7 @@ struct GraphSpec {
   const void* dinv;
   void *z, *r, *s, *p0, *p1, *q;
   int* ctl;
-  int grid, unroll;
+  int grid, grid_b, unroll;  // grid of step a and the other kernels, grid of step b
 };
 
 template <typename T>
@@ -792,7 +792,8 @@ cudaError_t build_graph(const GraphSpec& gs, cudaGraph_t* out) {
       if ((e = add_kernel(body, &na, prev ? &prev : nullptr, prev ? 1 : 0, (const void*)b_step_a_kernel<T, KB>,
                           gs.grid, kThreads, aa)))
         goto fail;
-      if ((e = add_kernel(body, &nb, &na, 1, (const void*)b_step_b_kernel<T, KB>, gs.grid, kThreads, aa))) goto fail;
+      if ((e = add_kernel(body, &nb, &na, 1, (const void*)b_step_b_kernel<T, KB>, gs.grid_b, kThreads, aa)))
+        goto fail;
       prev = nb;
     }
     cudaGraphNode_t nctl;
@@ -823,7 +824,8 @@ cudaError_t build_graph_any(const GraphSpec& gs, cudaGraph_t* out) {
   return build_graph<double, 32>(gs, out);
 }
 
-int occupancy(bool fp32, int kb) {
+// resident blocks per SM of step a (returned) and step b (*occ_b)
+int occupancy(bool fp32, int kb, int* occ_b) {
   int a = 1, b = 1;
   const void* fa;
   const void* fb;
@@ -844,7 +846,8 @@ int occupancy(bool fp32, int kb) {
   }
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, fa, kThreads, 0);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fb, kThreads, 0);
-  return std::max(1, std::min(a, b));
+  *occ_b = std::max(1, b);
+  return std::max(1, a);
 }
 
 }  // namespace batch
@@ -886,7 +889,7 @@ struct mrcg_batch {
   void *iz = nullptr, *ir = nullptr, *is = nullptr, *ip0 = nullptr, *ip1 = nullptr, *iq = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  int grid = 1, unroll = 4;
+  int grid = 1, grid_b = 1, unroll = 4;
   std::vector<void*> allocs;
 };
 
@@ -1132,8 +1135,10 @@ mrcg_status batch_create_impl(int32_t nsys, const mrcg_create_args* args, mrcg_b
   // ---- geometry and graph
   int nsm = 1;
   BCK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
-  const int occ = occupancy(h->fp32, h->kb);
+  int occ_b = 1;
+  const int occ = occupancy(h->fp32, h->kb, &occ_b);
   h->grid = std::max(1, std::min(h->nc, nsm * occ));
+  h->grid_b = std::max(1, std::min(h->nc, nsm * occ_b));
   if (const char* u = getenv("MRCG_UNROLL")) h->unroll = std::max(2, atoi(u) & ~1);
   GraphSpec gs = {};
   gs.fp32 = h->fp32;
@@ -1155,6 +1160,7 @@ mrcg_status batch_create_impl(int32_t nsys, const mrcg_create_args* args, mrcg_b
   gs.q = h->iq;
   gs.ctl = h->d_ctl;
   gs.grid = h->grid;
+  gs.grid_b = h->grid_b;
   gs.unroll = h->unroll;
   BCK(build_graph_any(gs, &h->graph));
   BCK(cudaGraphInstantiate(&h->exec, h->graph, 0));

@@ -46,6 +46,8 @@ struct SArgs {
   const int64_t* rowptr;
   const int32_t* colind;
   const T* val;
+  const int32_t* ell_col;  // rows of at most 8 entries: n x 8 (padding: own column, value 0), else nullptr
+  const T* ell_val;
   const T* V;  // n x KV row-major
   const double* sigma;  // [NCP] shift of each column (0 for padding)
   T *z, *r, *p_old, *p_new, *q;
@@ -195,30 +197,124 @@ __global__ void __launch_bounds__(kThreads) sh_step_a_kernel(SArgs<T> a) {
   T dot[1][NM];
 #pragma unroll
   for (int m = 0; m < NM; ++m) dot[0][m] = 0;
+  if (a.ell_col) {
+    // ELL-8: one coalesced load brings the entries of 4 rows (lane = 8 * row + entry)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+    for (int64_t r0 = ((int64_t)blockIdx.x * (kThreads / 32) + warp) * 4; r0 < a.n; r0 += nwarps * 4) {
+      const int64_t er = r0 + (lane >> 3);
+      const bool okr = er < a.n;
+      const T my_val = okr ? a.ell_val[er * 8 + (lane & 7)] : (T)0;
+      const int my_col = okr ? a.ell_col[er * 8 + (lane & 7)] : 0;
+      T vi[4], srow[4][NM], prow[4][NM];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int64_t row = r0 + q;
+        const bool ok = row < a.n;
+        vi[q] = (ok && lane < KV) ? __ldcs(a.V + row * KV + lane) : (T)0;
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+          const int64_t idx = row * a.ncp + lane + 32 * m;
+          srow[q][m] = ok ? sv[idx] : (T)0;
+          prow[q][m] = ok ? po[idx] : (T)0;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int64_t row = r0 + q;
+        if (row >= a.n) break;
+        T gs[8][NM], gp[8][NM], av[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          av[j] = __shfl_sync(0xffffffffu, my_val, q * 8 + j);
+          const int64_t cj = (int64_t)__shfl_sync(0xffffffffu, my_col, q * 8 + j) * a.ncp + lane;
+#pragma unroll
+          for (int m = 0; m < NM; ++m) {
+            gs[j][m] = __ldg(sv + cj + 32 * m);
+            gp[j][m] = __ldg(po + cj + 32 * m);
+          }
+        }
+        T acc[NM], pn[NM];
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+          acc[m] = 0;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[m] += av[j] * (gs[j][m] + beta[m] * gp[j][m]);
+          pn[m] = srow[q][m] + beta[m] * prow[q][m];
+          acc[m] -= sig[m] * pn[m];
+        }
+#pragma unroll
+        for (int l = 0; l < KV; ++l) {
+          const T vl = __shfl_sync(0xffffffffu, vi[q], l);
+#pragma unroll
+          for (int m = 0; m < NM; ++m) acc[m] += vl * Cs[l][lane + 32 * m];
+        }
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+          const int64_t idx = row * a.ncp + lane + 32 * m;
+          a.q[idx] = acc[m];
+          a.p_new[idx] = pn[m];
+          dot[0][m] += pn[m] * acc[m];
+        }
+      }
+    }
+    col_partials<T, NM, 1>(dot, a.ncp, a.partials, sm);
+    return;
+  }
   ROWS_BY_WARP(a.n) {
+    // loads that do not depend on the row's column indices go out first
+    const T vi = lane < KV ? __ldcs(a.V + row * KV + lane) : (T)0;
+    T srow[NM], prow[NM];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+      const int64_t idx = row * a.ncp + lane + 32 * m;
+      srow[m] = sv[idx];
+      prow[m] = po[idx];
+    }
     const int64_t e0 = a.rowptr[row];
     const int nnz = (int)(a.rowptr[row + 1] - e0);
     T acc[NM];
 #pragma unroll
     for (int m = 0; m < NM; ++m) acc[m] = 0;
-    for (int base = 0; base < nnz; base += 32) {
-      const bool has = lane + base < nnz;
-      const T my_val = has ? a.val[e0 + base + lane] : (T)0;
-      const int my_col = has ? a.colind[e0 + base + lane] : 0;
-      const int cnt = min(32, nnz - base);
-      for (int j = 0; j < cnt; ++j) {
-        const T av = __shfl_sync(0xffffffffu, my_val, j);
+    if (nnz <= 8) {
+      // short rows (stencils): every gather of the row in flight at once
+      const bool has = lane < nnz;
+      const T my_val = has ? a.val[e0 + lane] : (T)0;
+      const int my_col = has ? a.colind[e0 + lane] : 0;
+      T gs[8][NM], gp[8][NM], av[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        av[j] = __shfl_sync(0xffffffffu, my_val, j);
         const int64_t cj = (int64_t)__shfl_sync(0xffffffffu, my_col, j) * a.ncp + lane;
 #pragma unroll
-        for (int m = 0; m < NM; ++m) acc[m] += av * (__ldg(sv + cj + 32 * m) + beta[m] * __ldg(po + cj + 32 * m));
+        for (int m = 0; m < NM; ++m) {
+          gs[j][m] = (j < nnz) ? __ldg(sv + cj + 32 * m) : (T)0;
+          gp[j][m] = (j < nnz) ? __ldg(po + cj + 32 * m) : (T)0;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+#pragma unroll
+        for (int m = 0; m < NM; ++m) acc[m] += av[j] * (gs[j][m] + beta[m] * gp[j][m]);
+    } else {
+      for (int base = 0; base < nnz; base += 32) {
+        const bool has = lane + base < nnz;
+        const T my_val = has ? a.val[e0 + base + lane] : (T)0;
+        const int my_col = has ? a.colind[e0 + base + lane] : 0;
+        const int cnt = min(32, nnz - base);
+        for (int j = 0; j < cnt; ++j) {
+          const T av = __shfl_sync(0xffffffffu, my_val, j);
+          const int64_t cj = (int64_t)__shfl_sync(0xffffffffu, my_col, j) * a.ncp + lane;
+#pragma unroll
+          for (int m = 0; m < NM; ++m)
+            acc[m] += av * (__ldg(sv + cj + 32 * m) + beta[m] * __ldg(po + cj + 32 * m));
+        }
       }
     }
-    const T vi = lane < KV ? __ldcs(a.V + row * KV + lane) : (T)0;
     T pn[NM];
 #pragma unroll
     for (int m = 0; m < NM; ++m) {
-      const int64_t idx = row * a.ncp + lane + 32 * m;
-      pn[m] = sv[idx] + beta[m] * po[idx];
+      pn[m] = srow[m] + beta[m] * prow[m];
       acc[m] -= sig[m] * pn[m];
     }
 #pragma unroll
@@ -254,23 +350,43 @@ __global__ void __launch_bounds__(kThreads) sh_step_b_kernel(SArgs<T> a) {
   for (int l = 0; l <= KV; ++l)
 #pragma unroll
     for (int m = 0; m < NM; ++m) acc[l][m] = 0;
-  ROWS_BY_WARP(a.n) {
-    T rv[NM];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+  // two rows per trip: all loads of both rows are issued before any use
+  for (int64_t row = (int64_t)blockIdx.x * (kThreads / 32) + warp; row < a.n; row += 2 * nwarps) {
+    const int64_t rows[2] = {row, row + nwarps};
+    const bool two = rows[1] < a.n;
+    T pn[2][NM], qv[2][NM], zv[2][NM], rv[2][NM], vi[2];
 #pragma unroll
-    for (int m = 0; m < NM; ++m) {
-      const int64_t idx = row * a.ncp + lane + 32 * m;
-      const T pn = a.p_new[idx], qv = a.q[idx];
-      a.z[idx] = a.z[idx] + alpha[m] * pn;
-      rv[m] = a.r[idx] - alpha[m] * qv;
-      a.r[idx] = rv[m];
-      acc[0][m] += rv[m] * rv[m];
+    for (int h = 0; h < 2; ++h) {
+      const bool ok = h == 0 || two;
+      vi[h] = (ok && lane < KV) ? __ldcs(a.V + rows[h] * KV + lane) : (T)0;
+#pragma unroll
+      for (int m = 0; m < NM; ++m) {
+        const int64_t idx = rows[h] * a.ncp + lane + 32 * m;
+        pn[h][m] = ok ? a.p_new[idx] : (T)0;
+        qv[h][m] = ok ? a.q[idx] : (T)0;
+        zv[h][m] = ok ? a.z[idx] : (T)0;
+        rv[h][m] = ok ? a.r[idx] : (T)0;
+      }
     }
-    const T vi = lane < KV ? __ldcs(a.V + row * KV + lane) : (T)0;
 #pragma unroll
-    for (int l = 0; l < KV; ++l) {
-      const T vl = __shfl_sync(0xffffffffu, vi, l);
+    for (int h = 0; h < 2; ++h) {
+      if (h == 1 && !two) break;
 #pragma unroll
-      for (int m = 0; m < NM; ++m) acc[l + 1][m] += vl * rv[m];
+      for (int m = 0; m < NM; ++m) {
+        const int64_t idx = rows[h] * a.ncp + lane + 32 * m;
+        a.z[idx] = zv[h][m] + alpha[m] * pn[h][m];
+        rv[h][m] = rv[h][m] - alpha[m] * qv[h][m];
+        a.r[idx] = rv[h][m];
+        acc[0][m] += rv[h][m] * rv[h][m];
+      }
+#pragma unroll
+      for (int l = 0; l < KV; ++l) {
+        const T vl = __shfl_sync(0xffffffffu, vi[h], l);
+#pragma unroll
+        for (int m = 0; m < NM; ++m) acc[l + 1][m] += vl * rv[h][m];
+      }
     }
   }
   col_partials<T, NM, KV + 1>(acc, a.ncp, a.partials, sm);
@@ -307,16 +423,55 @@ struct OArgs {
   const int64_t* rowptr;
   const int32_t* colind;
   const double* val;
+  const int32_t* ell_col;
+  const double* ell_val;
   const double* sigma;
   double *x, *b, *res, *zraw, *zn, *v0, *v1, *w0, *w1;
 };
 
 template <int NM>
 __device__ __forceinline__ void spmm_row(const OArgs& a, int64_t row, int lane, const double* X, double (&acc)[NM]) {
+  if (a.ell_col) {
+    const double my_val = lane < 8 ? a.ell_val[row * 8 + lane] : 0.0;
+    const int my_col = lane < 8 ? a.ell_col[row * 8 + lane] : 0;
+    double g[8][NM], av[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      av[j] = __shfl_sync(0xffffffffu, my_val, j);
+      const int64_t cj = (int64_t)__shfl_sync(0xffffffffu, my_col, j) * a.ncp + lane;
+#pragma unroll
+      for (int m = 0; m < NM; ++m) g[j][m] = __ldg(X + cj + 32 * m);
+    }
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+      acc[m] = 0.0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[m] += av[j] * g[j][m];
+    }
+    return;
+  }
   const int64_t e0 = a.rowptr[row];
   const int nnz = (int)(a.rowptr[row + 1] - e0);
 #pragma unroll
   for (int m = 0; m < NM; ++m) acc[m] = 0.0;
+  if (nnz <= 8) {
+    const bool has = lane < nnz;
+    const double my_val = has ? a.val[e0 + lane] : 0.0;
+    const int my_col = has ? a.colind[e0 + lane] : 0;
+    double g[8][NM], av[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      av[j] = __shfl_sync(0xffffffffu, my_val, j);
+      const int64_t cj = (int64_t)__shfl_sync(0xffffffffu, my_col, j) * a.ncp + lane;
+#pragma unroll
+      for (int m = 0; m < NM; ++m) g[j][m] = (j < nnz) ? __ldg(X + cj + 32 * m) : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+      for (int m = 0; m < NM; ++m) acc[m] += av[j] * g[j][m];
+    return;
+  }
   for (int base = 0; base < nnz; base += 32) {
     const bool has = lane + base < nnz;
     const double my_val = has ? a.val[e0 + base + lane] : 0.0;
@@ -828,6 +983,9 @@ struct mrcg_shifted {
   int32_t* d_col = nullptr;
   double* d_val64 = nullptr;
   float* d_val32 = nullptr;
+  int32_t* d_ell_col = nullptr;  // ELL-8 copy of L when every row has at most 8 entries
+  double* d_ell64 = nullptr;
+  float* d_ell32 = nullptr;
   double* d_V64 = nullptr;
   float* d_V32 = nullptr;
   double *x = nullptr, *b = nullptr, *res = nullptr, *zraw = nullptr, *zn = nullptr;
@@ -899,6 +1057,8 @@ SArgs<T> sargs(mrcg_shifted* h) {
   a.rowptr = h->d_rowptr;
   a.colind = h->d_col;
   a.val = reinterpret_cast<const T*>(sizeof(T) == 4 ? (const void*)h->d_val32 : (const void*)h->d_val64);
+  a.ell_col = h->d_ell_col;
+  a.ell_val = reinterpret_cast<const T*>(sizeof(T) == 4 ? (const void*)h->d_ell32 : (const void*)h->d_ell64);
   a.V = reinterpret_cast<const T*>(sizeof(T) == 4 ? (const void*)h->d_V32 : (const void*)h->d_V64);
   a.sigma = h->d_sigma;
   a.z = reinterpret_cast<T*>(h->iz);
@@ -999,6 +1159,29 @@ mrcg_status shifted_create_impl(const mrcg_create_args* L, int32_t nshift, const
   SCK(cudaMemcpyAsync(h->d_rowptr, rp.data(), rp.size() * 8, cudaMemcpyHostToDevice, h->stream));
   SCK(cudaMemcpyAsync(h->d_col, ci.data(), ci.size() * 4, cudaMemcpyHostToDevice, h->stream));
   SCK(cudaMemcpyAsync(h->d_val64, va.data(), va.size() * 8, cudaMemcpyHostToDevice, h->stream));
+  {
+    int64_t wmax = 0;
+    for (int64_t r = 0; r < n; ++r) wmax = std::max(wmax, rp[r + 1] - rp[r]);
+    if (wmax <= 8) {
+      std::vector<int32_t> ec((size_t)n * 8);
+      std::vector<double> ev((size_t)n * 8, 0.0);
+      for (int64_t r = 0; r < n; ++r)
+        for (int64_t j = 0; j < 8; ++j) {
+          const int64_t p = rp[r] + j;
+          ec[r * 8 + j] = p < rp[r + 1] ? ci[p] : (int32_t)r;
+          ev[r * 8 + j] = p < rp[r + 1] ? va[p] : 0.0;
+        }
+      SST(salloc(h, &h->d_ell_col, ec.size()));
+      SST(salloc(h, &h->d_ell64, ev.size()));
+      SCK(cudaMemcpyAsync(h->d_ell_col, ec.data(), ec.size() * 4, cudaMemcpyHostToDevice, h->stream));
+      SCK(cudaMemcpyAsync(h->d_ell64, ev.data(), ev.size() * 8, cudaMemcpyHostToDevice, h->stream));
+      if (h->fp32) {
+        SST(salloc(h, &h->d_ell32, ev.size()));
+        if (launch_to_f32(h->stream, h->d_ell64, h->d_ell32, (int64_t)ev.size())) return MRCG_ERR_CUDA;
+      }
+      SCK(cudaStreamSynchronize(h->stream));
+    }
+  }
   std::vector<double> Vr((size_t)n * h->kv, 0.0);
   for (int64_t i = 0; i < n; ++i)
     for (int l = 0; l < L->k; ++l) Vr[(size_t)i * h->kv + l] = V[(size_t)l * n + i];
@@ -1071,6 +1254,8 @@ OArgs soargs(mrcg_shifted* h) {
   a.rowptr = h->d_rowptr;
   a.colind = h->d_col;
   a.val = h->d_val64;
+  a.ell_col = h->d_ell_col;
+  a.ell_val = h->d_ell64;
   a.sigma = h->d_sigma;
   a.x = h->x;
   a.b = h->b;
