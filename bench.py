@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["lap3d_128", "batch64", "shifted64"], default="lap3d_128",
+    ap.add_argument("--workload", choices=["lap3d_128", "saddle", "batch64", "shifted64"], default="lap3d_128",
                     help="lap3d_128: the headline single-system workload; batch64: 64 independent uneven "
                          "2D systems (sides 100..400, k_i 1..16, seed 3) solved as one batch; shifted64: 16 "
                          "shifts x 4 RHS of the 160^3 Laplacian as one right-hand-side block")
@@ -378,7 +378,7 @@ def main():
         return
     import torch
 
-    from gen import config2
+    from gen import config2, config3
     from paper_1805_12417_gb300 import build as _b
     _b.build()
     import paper_1805_12417_gb300 as m
@@ -386,7 +386,13 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    p = config2()
+    workload = WORKLOAD
+    if args.workload == "saddle":
+        p = config3()
+        workload = ("saddle_96^3_B20x64: [K B^T; B 0], K 27-pt log-normal(0,1) SPD stencil on 96^3, B 20 rows x 64 "
+                    "uniform[-1,1] entries (n=884,756, 20 negative eigenvalues), seed 2, 1 RHS")
+    else:
+        p = config2()
     b_dev = torch.from_numpy(p.b).to(dev)
     x_dev = torch.zeros(p.n, dtype=torch.float64, device=dev)
     solvers = {prec: m.Solver.from_problem(p, precision=prec, stream=stream.cuda_stream, validate=False)
@@ -465,7 +471,7 @@ def main():
 
     peak, peak_kind = measured_peak_gbs()
     ach_a = bytes_a(4) / (ta_mx * 1e-3) / 1e9
-    roof = {"kernel": "cg_step_a_kernel<float,16>", "bound": "hbm", "achieved": round(ach_a, 1), "peak": peak,
+    roof = {"kernel": f"cg_step_a_kernel<float,{0 if k == 0 else 8 if k <= 8 else 16 if k <= 16 else 32}>", "bound": "hbm", "achieved": round(ach_a, 1), "peak": peak,
             "unit": "GB/s", "frac": round(ach_a / peak, 4), "traffic": None,
             "peak_kind": f"{peak_kind} copy bandwidth (burst: kernel timed alone)",
             "bytes_per_launch": bytes_a(4), "avg_ms": round(ta_mx, 5)}
@@ -487,9 +493,10 @@ def main():
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_mx / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 inner CG + f64 outer MINRES", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": n, "nnz": nnz, "k": k, "outer_tol": OUTER_TOL,
+            "config": {"workload": workload, "n": n, "nnz": nnz, "k": k, "outer_tol": OUTER_TOL,
                        "inner_tol": INNER_TOL, "precision": "mixed: FP32 inner CG, FP64 outer MINRES",
-                       "l2": "inputs larger than L2 (FP32 A 117 MB + V 84 MB + vectors per inner iteration)",
+                       "l2": f"inputs larger than L2 (FP32 A {nnz * 8 / 1e6:.0f} MB + V {k * n * 4 / 1e6:.0f} MB "
+                             "+ vectors per inner iteration)",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "roofline": roof,
             "spmv_hbm_gbs": {"mixed_step_a": round(kernels["mixed"]["step_a_gbs"], 1),

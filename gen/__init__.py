@@ -25,3 +25,4 @@ from .problems import (  # noqa: F401
     small_3d,
     CONFIGS,
 )
+from .saddle import config3, saddle_problem, small_saddle  # noqa: F401,E402

@@ -357,3 +357,31 @@ def test_generator_tie_rounding():
 def test_generator_is_reproducible():
     a, b = config1(), config1()
     assert np.array_equal(a.b, b.b) and np.array_equal(a.V, b.V) and a.sigma == b.sigma
+
+
+# ---------------------------------------------------------------- saddle-point generator
+
+def test_saddle_inertia_and_eigenpairs():
+    """[K B^T; B 0] with K SPD, B full row rank: exactly nb negative eigenvalues (Sylvester)."""
+    from gen import small_saddle
+    p = small_saddle()
+    w = np.linalg.eigvalsh(p.dense())
+    assert int(np.sum(w < 0)) == p.k == 6
+    assert np.allclose(np.sort(p.lam), w[:6], atol=1e-12)
+    assert p.meta["eig_residual_max"] < 1e-11
+    s = O.System.from_problem(p)
+    r = O.minres_cg(s, p.b, outer_tol=1e-12, inner_tol=1e-3)
+    assert r.status == O.OK
+    assert np.linalg.norm(r.x - p.xstar) <= 1e-8 * np.linalg.norm(p.xstar)
+
+
+def test_saddle_krylov_eigensolver_matches_dense():
+    """The Rayleigh-Ritz eigensolver of the large saddle generator agrees with dense eigh."""
+    torch = pytest.importorskip("torch")
+    from gen.saddle import _negative_eigenpairs_dense, _negative_eigenpairs_krylov, saddle_matrix
+    A, K, B, _ = saddle_matrix(10, 8, 16, 4)
+    Vk, lk = _negative_eigenpairs_krylov(K, B, 8, -0.3, 12, device="cpu")
+    Vd, ld = _negative_eigenpairs_dense(A, 8)
+    assert np.allclose(lk, ld, atol=1e-12)
+    assert np.linalg.norm(A @ Vk - Vk * lk, axis=0).max() < 1e-10
+    assert np.linalg.svd(Vk.T @ Vd, compute_uv=False).min() > 1 - 1e-10
