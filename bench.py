@@ -499,6 +499,8 @@ def main():
                              "+ vectors per inner iteration)",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "roofline": roof,
+            "launch_config": {"mixed": m.launch_config(solvers[m.MIXED_FP32].h),
+                              "fp64": m.launch_config(solvers[m.FP64].h)},
             "spmv_hbm_gbs": {"mixed_step_a": round(kernels["mixed"]["step_a_gbs"], 1),
                              "fp64_step_a": round(kernels["fp64"]["step_a_gbs"], 1), "peak": peak},
             "kernels": {kk: {a: round(b, 5) for a, b in v.items()} for kk, v in kernels.items()},

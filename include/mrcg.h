@@ -139,6 +139,14 @@ mrcg_status mrcg_inner_solve(mrcg_handle h, const double* y, double* z, double i
  * milliseconds.  Overwrites the handle's work vectors (not its matrix). */
 mrcg_status mrcg_time_inner_kernels(mrcg_handle h, int32_t iters, double* ms);
 
+/* Launch configuration chosen for the handle's inner-CG kernels (at create,
+ * by timing candidate shapes on this matrix unless MRCG_AUTOTUNE=0):
+ * cfg[0] step-a variant (0: V_hat rows loaded before the SpMV, 1: after it,
+ * 2: two slices per warp), cfg[1] step-a grid (blocks), cfg[2] step-b grid,
+ * cfg[3] CG iterations per body of the device loop, cfg[4] k bucket of the
+ * kernels (0, 8, 16, 24 or 32).  cfg must hold 5 values. */
+mrcg_status mrcg_launch_config(mrcg_handle h, int32_t* cfg);
+
 /* ---- Batches of independent systems (many uneven systems in one launch sequence) ----
  *
  * The paper's motivating use solves many systems with related coefficient

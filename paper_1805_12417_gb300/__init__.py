@@ -63,6 +63,8 @@ def lib() -> C.CDLL:
         L.mrcg_inner_solve.restype = C.c_int
         L.mrcg_time_inner_kernels.argtypes = [P, C.c_int32, P]
         L.mrcg_time_inner_kernels.restype = C.c_int
+        L.mrcg_launch_config.argtypes = [P, P]
+        L.mrcg_launch_config.restype = C.c_int
         L.mrcg_batch_create.argtypes = [C.c_int32, C.POINTER(CreateArgs), C.POINTER(C.c_void_p)]
         L.mrcg_batch_create.restype = C.c_int
         L.mrcg_batched_solve.argtypes = [P, P, P, C.c_double, C.c_double, C.c_int64, C.POINTER(Info)]
@@ -217,6 +219,16 @@ def inner_solve(h, y, z, inner_tol=1e-3, max_iters=0):
     if st in (ERR_INVALID, ERR_CUDA, ERR_OOM):
         raise MrcgError(st, "mrcg_inner_solve")
     return st, it.value
+
+
+def launch_config(h):
+    """mrcg_launch_config: the autotuned launch shape of the inner-CG kernels."""
+    cfg = np.zeros(5, dtype=np.int32)
+    st = lib().mrcg_launch_config(h, cfg.ctypes.data)
+    if st != OK:
+        raise MrcgError(st, "mrcg_launch_config")
+    return {"step_a_variant": int(cfg[0]), "step_a_grid": int(cfg[1]), "step_b_grid": int(cfg[2]),
+            "unroll": int(cfg[3]), "k_bucket": int(cfg[4])}
 
 
 def time_inner_kernels(h, iters=20):

@@ -386,6 +386,51 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
   g.grid_stream = h->grid_stream;
   g.grid_stream_b = h->grid_stream_b;
   g.unroll = h->unroll;
+  // ---- launch-shape autotuner: step-a variant and blocks per SM of both CG
+  // kernels, timed on this matrix (standalone launches, a few iterations each)
+  if (const char* va = getenv("MRCG_VAR_A")) g.var_a = std::min(2, std::max(0, atoi(va)));
+  const char* at = getenv("MRCG_AUTOTUNE");
+  const bool tune = (!at || atoi(at) != 0) && n_pad >= (1 << 18) && !getenv("MRCG_BPSM_A") &&
+                    !getenv("MRCG_BPSM_B") && !getenv("MRCG_VAR_A");
+  if (tune) {
+    double ms[2] = {0.0, 0.0}, best = 1e30;
+    InnerGraphSpec bestg = g;
+    for (int var = 0; var < 3; ++var)
+      for (int bp = std::max(1, occ_spmv - 1); bp <= occ_spmv; ++bp) {
+        InnerGraphSpec t = g;
+        t.var_a = var;
+        t.grid_spmv = (int)std::max<int64_t>(1, std::min<int64_t>({want_spmv, (int64_t)nsm * bp, kMaxBlocks}));
+        reset_state(h, 1e-300, 64);
+        h->h_init->cg.vin = h->v[0];
+        h->h_init->cg.zout = h->zraw;
+        ST(upload_state(h));
+        CK(time_inner_kernels(t, 6, h->stream, h->v[0], n, ms));
+        if (ms[0] < best) {
+          best = ms[0];
+          bestg.var_a = var;
+          bestg.grid_spmv = t.grid_spmv;
+        }
+      }
+    best = 1e30;
+    for (int bp = std::max(1, occ_b - 2); bp <= occ_b; ++bp) {
+      InnerGraphSpec t = bestg;
+      t.grid_stream_b = (int)std::max<int64_t>(1, std::min<int64_t>({want_b, (int64_t)nsm * bp, kMaxBlocks}));
+      reset_state(h, 1e-300, 64);
+      h->h_init->cg.vin = h->v[0];
+      h->h_init->cg.zout = h->zraw;
+      ST(upload_state(h));
+      CK(time_inner_kernels(t, 6, h->stream, h->v[0], n, ms));
+      if (ms[1] < best) {
+        best = ms[1];
+        bestg.grid_stream_b = t.grid_stream_b;
+      }
+    }
+    g = bestg;
+    h->grid_spmv = g.grid_spmv;
+    h->grid_stream_b = g.grid_stream_b;
+    if (getenv("MRCG_DEBUG"))
+      fprintf(stderr, "mrcg autotune: var_a=%d grid_a=%d grid_b=%d\n", g.var_a, g.grid_spmv, g.grid_stream_b);
+  }
   h->spec = g;
   CK(build_inner_graph(g, &h->graph));
   CK(cudaGraphInstantiate(&h->graph_exec, h->graph, 0));
@@ -623,6 +668,16 @@ mrcg_status mrcg_inner_solve(mrcg_handle h, const double* y, double* z, double i
     case kNonFinite: return MRCG_ERR_NONFINITE;
     default: return MRCG_ERR_MAXITER;
   }
+}
+
+mrcg_status mrcg_launch_config(mrcg_handle h, int32_t* cfg) {
+  if (!h || !cfg) return MRCG_ERR_INVALID;
+  cfg[0] = h->spec.var_a;
+  cfg[1] = h->spec.grid_spmv;
+  cfg[2] = h->spec.grid_stream_b;
+  cfg[3] = h->spec.unroll;
+  cfg[4] = h->k == 0 ? 0 : h->k <= 8 ? 8 : h->k <= 16 ? 16 : h->k <= 24 ? 24 : 32;
+  return MRCG_OK;
 }
 
 mrcg_status mrcg_time_inner_kernels(mrcg_handle h, int32_t iters, double* ms) {

@@ -226,9 +226,36 @@ __global__ void __launch_bounds__(kThreads) cg_init_kernel(CgArgs<T> a) {
 
 // ------------------------------------------------------------------ step a
 
-template <typename T, int KB>
+// The entries of one slice row, 8 at a time: all value / index loads of a
+// group are in flight before the gathers that depend on them.
+template <typename T>
+__device__ __forceinline__ T slice_row(const T* vp, const int32_t* cp, int w, const T* __restrict__ sv,
+                                       const T* __restrict__ po, T beta) {
+  T acc = 0;
+  for (int j0 = 0; j0 < w; j0 += 8) {
+    T av[8];
+    int cc[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      av[j] = (j0 + j < w) ? ld_stream(vp + (size_t)(j0 + j) * kSlice) : (T)0;
+      cc[j] = (j0 + j < w) ? ld_stream(cp + (size_t)(j0 + j) * kSlice) : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (j0 + j < w) acc += av[j] * (__ldg(sv + cc[j]) + beta * __ldg(po + cc[j]));
+  }
+  return acc;
+}
+
+// Variants (picked per handle by the launch-shape autotuner):
+//   VAR 0: V_hat row loads issued before the SpMV (more bytes in flight)
+//   VAR 1: V_hat read after the SpMV (fewer registers)
+//   VAR 2: two slices per warp per trip, V_hat early (more independent work)
+template <typename T, int KB, int VAR>
 __global__ void __launch_bounds__(kThreads, 4) cg_step_a_kernel(CgArgs<T> a) {
   constexpr int KS = KB > 0 ? KB : 1;
+  constexpr int NSL = VAR == 2 ? 2 : 1;
+  constexpr bool kEarlyV = VAR != 1;
   CgState& S = a.st->cg;
   if (S.done != kRunning) return;
   const T beta = beta_of(S, T(0));
@@ -242,54 +269,53 @@ __global__ void __launch_bounds__(kThreads, 4) cg_step_a_kernel(CgArgs<T> a) {
   const int64_t warp0 = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
   T dot = 0;
-  for (int64_t sl = warp0; sl < a.nslices; sl += nwarps) {
-    const int64_t row = sl * kSlice + lane;
-    // FP32: loads that do not depend on the column indices go out first.
-    // FP64 (FP64-pipe bound, register-limited): V is read after the SpMV.
-    constexpr bool kEarlyV = sizeof(T) == 4;
-    T vrow[KS];
-    if (kEarlyV) {
+  for (int64_t sl0 = warp0 * NSL; sl0 < a.nslices; sl0 += nwarps * NSL) {
+    T vrow[NSL][KS], srow[NSL], prow[NSL], acc[NSL];
+    int64_t rowv[NSL];
+    bool ok[NSL];
 #pragma unroll
-      for (int l = 0; l < KS; ++l) vrow[l] = (l < a.k) ? ld_stream(a.V + (size_t)l * a.n_pad + row) : (T)0;
-    }
-    const T srow = sv[row], prow = po[row];
-    const int64_t base = a.slice_ptr[sl];
-    const int w = (int)((a.slice_ptr[sl + 1] - base) >> 5);
-    const T* vp = a.val + base + lane;
-    const int32_t* cp = a.col + base + lane;
-    T acc = 0;
-    if (kEarlyV && w <= 8) {
-      T av[8];
-      int cc[8];
+    for (int h = 0; h < NSL; ++h) {
+      const int64_t sl = sl0 + h;
+      ok[h] = sl < a.nslices;
+      rowv[h] = (ok[h] ? sl : sl0) * kSlice + lane;
+      if (kEarlyV) {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        av[j] = (j < w) ? ld_stream(vp + (size_t)j * kSlice) : (T)0;
-        cc[j] = (j < w) ? ld_stream(cp + (size_t)j * kSlice) : 0;
+        for (int l = 0; l < KS; ++l)
+          vrow[h][l] = (ok[h] && l < a.k) ? ld_stream(a.V + (size_t)l * a.n_pad + rowv[h]) : (T)0;
       }
+      srow[h] = sv[rowv[h]];
+      prow[h] = po[rowv[h]];
+    }
 #pragma unroll
-      for (int j = 0; j < 8; ++j)
-        if (j < w) acc += av[j] * (__ldg(sv + cc[j]) + beta * __ldg(po + cc[j]));
-    } else {
-#pragma unroll 4
-      for (int j = 0; j < w; ++j) {
-        const T av = ld_stream(vp + (size_t)j * kSlice);
-        const int c = ld_stream(cp + (size_t)j * kSlice);
-        acc += av * (__ldg(sv + c) + beta * __ldg(po + c));
+    for (int h = 0; h < NSL; ++h) {
+      if (!ok[h]) {
+        acc[h] = 0;
+        continue;
       }
+      const int64_t sl = sl0 + h;
+      const int64_t base = a.slice_ptr[sl];
+      const int w = (int)((a.slice_ptr[sl + 1] - base) >> 5);
+      acc[h] = slice_row<T>(a.val + base + lane, a.col + base + lane, w, sv, po, beta);
     }
-    const T pn = srow + beta * prow;
-    if (kEarlyV) {
 #pragma unroll
-      for (int l = 0; l < KB; ++l)
-        if (l < a.k) acc += vrow[l] * cl[l];
-    } else {
+    for (int h = 0; h < NSL; ++h) {
+      if (!ok[h]) continue;
+      const int64_t row = rowv[h];
+      const T pn = srow[h] + beta * prow[h];
+      T q = acc[h];
+      if (kEarlyV) {
 #pragma unroll
-      for (int l = 0; l < KB; ++l)
-        if (l < a.k) acc += ld_stream(a.V + (size_t)l * a.n_pad + row) * cl[l];
+        for (int l = 0; l < KB; ++l)
+          if (l < a.k) q += vrow[h][l] * cl[l];
+      } else {
+#pragma unroll
+        for (int l = 0; l < KB; ++l)
+          if (l < a.k) q += ld_stream(a.V + (size_t)l * a.n_pad + row) * cl[l];
+      }
+      a.q[row] = q;
+      a.p_new[row] = pn;
+      dot += pn * q;
     }
-    a.q[row] = acc;
-    a.p_new[row] = pn;
-    dot += pn * acc;
   }
   T part[1] = {dot};
   block_partials_t<T, 1>(part, 1, a.partials);
@@ -476,6 +502,21 @@ cudaError_t add_kernel(cudaGraph_t g, cudaGraphNode_t* node, const cudaGraphNode
 }
 
 template <typename T, int KB>
+const void* step_a_fn(int var) {
+  switch (var) {
+    case 1: return (const void*)cg_step_a_kernel<T, KB, 1>;
+    case 2: return (const void*)cg_step_a_kernel<T, KB, 2>;
+    default: return (const void*)cg_step_a_kernel<T, KB, 0>;
+  }
+}
+
+template <typename T>
+cudaError_t launch_a(const void* fn, int grid, cudaStream_t stream, CgArgs<T>& a) {
+  void* args[] = {&a};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(kThreads), args, 0, stream);
+}
+
+template <typename T, int KB>
 cudaError_t build_graph_t(const InnerGraphSpec& spec, cudaGraph_t* out_graph) {
   cudaError_t e;
   cudaGraph_t g;
@@ -511,7 +552,7 @@ cudaError_t build_graph_t(const InnerGraphSpec& spec, cudaGraph_t* out_graph) {
     for (int it = 0; it < spec.unroll; ++it) {
       void* aa[] = {&a[it & 1]};
       cudaGraphNode_t na, nb;
-      if ((e = add_kernel(body, &na, prev ? &prev : nullptr, prev ? 1 : 0, (const void*)cg_step_a_kernel<T, KB>,
+      if ((e = add_kernel(body, &na, prev ? &prev : nullptr, prev ? 1 : 0, step_a_fn<T, KB>(spec.var_a),
                           spec.grid_spmv, kThreads, aa)))
         goto fail;
       if ((e = add_kernel(body, &nb, &na, 1, (const void*)cg_step_b_kernel<T, KB>, spec.grid_stream_b, kThreads,
@@ -549,7 +590,7 @@ cudaError_t run_host_t(const InnerGraphSpec& spec, cudaStream_t stream, int* h_d
   cudaError_t e = cudaSuccess;
   for (;;) {
     for (int it = 0; it < spec.unroll; ++it) {
-      cg_step_a_kernel<T, KB><<<spec.grid_spmv, kThreads, 0, stream>>>(a[it & 1]);
+      launch_a<T>(step_a_fn<T, KB>(spec.var_a), spec.grid_spmv, stream, a[it & 1]);
       cg_step_b_kernel<T, KB><<<spec.grid_stream_b, kThreads, 0, stream>>>(a[it & 1]);
     }
     cg_ctl_host_kernel<<<1, 1, 0, stream>>>(spec.st);
@@ -574,7 +615,7 @@ cudaError_t time_t(const InnerGraphSpec& spec, int iters, cudaStream_t stream, d
   for (auto& e : ev) cudaEventCreate(&e);
   cudaEventRecord(ev[0], stream);
   for (int it = 0; it < iters; ++it) {
-    cg_step_a_kernel<T, KB><<<spec.grid_spmv, kThreads, 0, stream>>>(a[it & 1]);
+    launch_a<T>(step_a_fn<T, KB>(spec.var_a), spec.grid_spmv, stream, a[it & 1]);
     cudaEventRecord(ev[2 * it + 1], stream);
     cg_step_b_kernel<T, KB><<<spec.grid_stream_b, kThreads, 0, stream>>>(a[it & 1]);
     cudaEventRecord(ev[2 * it + 2], stream);
@@ -597,7 +638,7 @@ cudaError_t time_t(const InnerGraphSpec& spec, int iters, cudaStream_t stream, d
 
 template <typename T, int KB>
 void occupancy_t(int* a_blocks, int* b_blocks) {
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(a_blocks, (const void*)cg_step_a_kernel<T, KB>, kThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(a_blocks, step_a_fn<T, KB>(0), kThreads, 0);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(b_blocks, (const void*)cg_step_b_kernel<T, KB>, kThreads, 0);
 }
 
@@ -608,11 +649,13 @@ cudaError_t dispatch(const InnerGraphSpec& spec, Args... args) {
     if (spec.k == 0) return F<float, 0>::run(spec, args...);
     if (spec.k <= 8) return F<float, 8>::run(spec, args...);
     if (spec.k <= 16) return F<float, 16>::run(spec, args...);
+    if (spec.k <= 24) return F<float, 24>::run(spec, args...);
     return F<float, 32>::run(spec, args...);
   }
   if (spec.k == 0) return F<double, 0>::run(spec, args...);
   if (spec.k <= 8) return F<double, 8>::run(spec, args...);
   if (spec.k <= 16) return F<double, 16>::run(spec, args...);
+  if (spec.k <= 24) return F<double, 24>::run(spec, args...);
   return F<double, 32>::run(spec, args...);
 }
 

@@ -25,6 +25,7 @@ struct InnerGraphSpec {
   void* q = nullptr;
   int grid_spmv = 1, grid_stream = 1, grid_stream_b = 1;
   int unroll = 4;  // CG iterations per body of the while loop (even)
+  int var_a = 0;   // step-a kernel variant (0: early V loads, 1: late V loads, 2: two slices per warp)
 };
 
 cudaError_t build_inner_graph(const InnerGraphSpec& spec, cudaGraph_t* graph);
