@@ -463,11 +463,13 @@ def main():
     ta_64, tb_64 = m.time_inner_kernels(solvers[m.FP64].h, 50)
     n, nnz, k = p.n, p.nnz, p.k
 
-    def bytes_a(w):  # A values + int32 indices, s and p_old read, V read, q and p_new written
-        return nnz * (w + 4) + 2 * n * w + k * n * w + 2 * n * w
+    ib = m.launch_config(solvers[m.MIXED_FP32].h)["index_bytes"]
 
-    def bytes_b(w):  # p, q, z, r read; z, r written; V read
-        return 6 * n * w + k * n * w
+    def bytes_a(w):  # A values + column indices, s and p_old read, V read, q and p_new written
+        return nnz * (w + ib) + 2 * n * w + k * n * w + 2 * n * w
+
+    def bytes_b(w):  # p, q, z, r read; z, r written (V^T s by recurrence: no V pass)
+        return 6 * n * w
 
     peak, peak_kind = measured_peak_gbs()
     ach_a = bytes_a(4) / (ta_mx * 1e-3) / 1e9

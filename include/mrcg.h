@@ -144,7 +144,9 @@ mrcg_status mrcg_time_inner_kernels(mrcg_handle h, int32_t iters, double* ms);
  * cfg[0] step-a variant (0: V_hat rows loaded before the SpMV, 1: after it,
  * 2: two slices per warp), cfg[1] step-a grid (blocks), cfg[2] step-b grid,
  * cfg[3] CG iterations per body of the device loop, cfg[4] k bucket of the
- * kernels (0, 8, 16, 24 or 32).  cfg must hold 5 values. */
+ * kernels (0, 8, 16, 24 or 32), cfg[5] bytes per column index read by the
+ * inner kernels (2: 16-bit col - row deltas, used when every delta fits; 4).
+ * cfg must hold 6 values. */
 mrcg_status mrcg_launch_config(mrcg_handle h, int32_t* cfg);
 
 /* ---- Batches of independent systems (many uneven systems in one launch sequence) ----

@@ -286,6 +286,19 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
   h->A.col = h->d_col;
   h->A.val64 = h->d_val64;
   h->A.val32 = h->d_val32;
+  // 16-bit column deltas for the inner kernels when every |col - row| fits
+  {
+    int64_t dmax = 0;
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t p = rp[i]; p < rp[i + 1]; ++p) dmax = std::max<int64_t>(dmax, std::llabs((int64_t)ci[p] - i));
+    const char* e = getenv("MRCG_IDX16");
+    if (dmax <= 32767 && !(e && atoi(e) == 0)) {
+      int16_t* c16 = nullptr;
+      ST(dalloc(h, &c16, (size_t)total + 1));
+      LK(launch_sell_delta16(h->stream, n_pad, h->d_slice_ptr, h->d_col, c16));
+      h->A.col16 = c16;
+    }
+  }
 
   // ---- V_hat (n_pad rows, zero padded) and its FP32 copy
   const size_t vcount = (size_t)n_pad * (a->k > 0 ? a->k : 1);
@@ -396,7 +409,7 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
     double ms[2] = {0.0, 0.0}, best = 1e30;
     InnerGraphSpec bestg = g;
     for (int var = 0; var < 3; ++var)
-      for (int bp = std::max(1, occ_spmv - 1); bp <= occ_spmv; ++bp) {
+      for (int bp = std::max(1, occ_spmv - 2); bp <= occ_spmv; ++bp) {
         InnerGraphSpec t = g;
         t.var_a = var;
         t.grid_spmv = (int)std::max<int64_t>(1, std::min<int64_t>({want_spmv, (int64_t)nsm * bp, kMaxBlocks}));
@@ -404,7 +417,7 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
         h->h_init->cg.vin = h->v[0];
         h->h_init->cg.zout = h->zraw;
         ST(upload_state(h));
-        CK(time_inner_kernels(t, 6, h->stream, h->v[0], n, ms));
+        CK(time_inner_kernels(t, 10, h->stream, h->v[0], n, ms));
         if (ms[0] < best) {
           best = ms[0];
           bestg.var_a = var;
@@ -412,14 +425,14 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
         }
       }
     best = 1e30;
-    for (int bp = std::max(1, occ_b - 2); bp <= occ_b; ++bp) {
+    for (int bp = 1; bp <= occ_b; bp += (bp < 4 ? 1 : 2)) {
       InnerGraphSpec t = bestg;
       t.grid_stream_b = (int)std::max<int64_t>(1, std::min<int64_t>({want_b, (int64_t)nsm * bp, kMaxBlocks}));
       reset_state(h, 1e-300, 64);
       h->h_init->cg.vin = h->v[0];
       h->h_init->cg.zout = h->zraw;
       ST(upload_state(h));
-      CK(time_inner_kernels(t, 6, h->stream, h->v[0], n, ms));
+      CK(time_inner_kernels(t, 10, h->stream, h->v[0], n, ms));
       if (ms[1] < best) {
         best = ms[1];
         bestg.grid_stream_b = t.grid_stream_b;
@@ -677,6 +690,7 @@ mrcg_status mrcg_launch_config(mrcg_handle h, int32_t* cfg) {
   cfg[2] = h->spec.grid_stream_b;
   cfg[3] = h->spec.unroll;
   cfg[4] = h->k == 0 ? 0 : h->k <= 8 ? 8 : h->k <= 16 ? 16 : h->k <= 24 ? 24 : 32;
+  cfg[5] = h->A.col16 ? 2 : 4;
   return MRCG_OK;
 }
 

@@ -153,7 +153,7 @@ __device__ __forceinline__ void system_sums(const double* partials, int nc, int 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i = warp; i < nv; i += kThreads / 32) {
     double s = 0.0;
-    for (int b = lane; b < ncs; b += 32) s += __ldcg(partials + (size_t)i * nc + c0 + b);
+    s = lane_sum8(partials + (size_t)i * nc + c0, ncs, lane);
     s = warp_sum(s);
     if (lane == 0) out[i] = s;
   }

@@ -35,6 +35,7 @@ struct CgArgs {
   // SELL A in the inner precision
   const int64_t* slice_ptr;
   const int32_t* col;
+  const int16_t* col16;  // col - row (16 bit) when it fits, else nullptr
   const T* val;
   int64_t nslices, n_pad;
   // low-rank term
@@ -218,7 +219,7 @@ __global__ void __launch_bounds__(kThreads) cg_init_kernel(CgArgs<T> a) {
       } else if (S.maxit <= 0) {
         S.done = kMaxIter;
       }
-      for (int l = 0; l < a.k; ++l) S.t[l] = tot[l + 1];
+      for (int l = 0; l < a.k; ++l) S.t[l] = S.u[l] = tot[l + 1];
       publish_c(S, a.k);
     }
   }
@@ -239,6 +240,26 @@ __device__ __forceinline__ T slice_row(const T* vp, const int32_t* cp, int w, co
     for (int j = 0; j < 8; ++j) {
       av[j] = (j0 + j < w) ? ld_stream(vp + (size_t)(j0 + j) * kSlice) : (T)0;
       cc[j] = (j0 + j < w) ? ld_stream(cp + (size_t)(j0 + j) * kSlice) : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (j0 + j < w) acc += av[j] * (__ldg(sv + cc[j]) + beta * __ldg(po + cc[j]));
+  }
+  return acc;
+}
+
+// The same with 16-bit column deltas (col = row + delta): half the index bytes.
+template <typename T>
+__device__ __forceinline__ T slice_row16(const T* vp, const int16_t* cp, int row, int w, const T* __restrict__ sv,
+                                         const T* __restrict__ po, T beta) {
+  T acc = 0;
+  for (int j0 = 0; j0 < w; j0 += 8) {
+    T av[8];
+    int cc[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      av[j] = (j0 + j < w) ? ld_stream(vp + (size_t)(j0 + j) * kSlice) : (T)0;
+      cc[j] = (j0 + j < w) ? row + (int)ld_stream(cp + (size_t)(j0 + j) * kSlice) : row;
     }
 #pragma unroll
     for (int j = 0; j < 8; ++j)
@@ -268,7 +289,12 @@ __global__ void __launch_bounds__(kThreads, 4) cg_step_a_kernel(CgArgs<T> a) {
   const int lane = threadIdx.x & 31;
   const int64_t warp0 = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+  const bool jac = a.dinv != nullptr;
   T dot = 0;
+  // wq[l] = (V^T M_cg^{-1} q)_l: with this step b needs no pass over V (see step b)
+  T wq[KS];
+#pragma unroll
+  for (int l = 0; l < KS; ++l) wq[l] = 0;
   for (int64_t sl0 = warp0 * NSL; sl0 < a.nslices; sl0 += nwarps * NSL) {
     T vrow[NSL][KS], srow[NSL], prow[NSL], acc[NSL];
     int64_t rowv[NSL];
@@ -295,7 +321,8 @@ __global__ void __launch_bounds__(kThreads, 4) cg_step_a_kernel(CgArgs<T> a) {
       const int64_t sl = sl0 + h;
       const int64_t base = a.slice_ptr[sl];
       const int w = (int)((a.slice_ptr[sl + 1] - base) >> 5);
-      acc[h] = slice_row<T>(a.val + base + lane, a.col + base + lane, w, sv, po, beta);
+      acc[h] = a.col16 ? slice_row16<T>(a.val + base + lane, a.col16 + base + lane, (int)rowv[h], w, sv, po, beta)
+                       : slice_row<T>(a.val + base + lane, a.col + base + lane, w, sv, po, beta);
     }
 #pragma unroll
     for (int h = 0; h < NSL; ++h) {
@@ -303,28 +330,35 @@ __global__ void __launch_bounds__(kThreads, 4) cg_step_a_kernel(CgArgs<T> a) {
       const int64_t row = rowv[h];
       const T pn = srow[h] + beta * prow[h];
       T q = acc[h];
-      if (kEarlyV) {
+      if (!kEarlyV) {
 #pragma unroll
-        for (int l = 0; l < KB; ++l)
-          if (l < a.k) q += vrow[h][l] * cl[l];
-      } else {
-#pragma unroll
-        for (int l = 0; l < KB; ++l)
-          if (l < a.k) q += ld_stream(a.V + (size_t)l * a.n_pad + row) * cl[l];
+        for (int l = 0; l < KS; ++l)
+          vrow[h][l] = (l < a.k) ? ld_stream(a.V + (size_t)l * a.n_pad + row) : (T)0;
       }
+#pragma unroll
+      for (int l = 0; l < KB; ++l)
+        if (l < a.k) q += vrow[h][l] * cl[l];
       a.q[row] = q;
       a.p_new[row] = pn;
       dot += pn * q;
+      const T qs = jac ? a.dinv[row] * q : q;
+#pragma unroll
+      for (int l = 0; l < KB; ++l)
+        if (l < a.k) wq[l] += vrow[h][l] * qs;
     }
   }
-  T part[1] = {dot};
-  block_partials_t<T, 1>(part, 1, a.partials);
+  T part[KB + 1];
+  part[0] = dot;
+#pragma unroll
+  for (int l = 0; l < KB; ++l) part[l + 1] = wq[l];
+  block_partials_t<T, KB + 1>(part, a.k + 1, a.partials);
   if (last_block(&a.st->ticket)) {
-    __shared__ double tot[1];
-    final_sums(a.partials, 1, tot);
+    __shared__ double tot[KB + 1];
+    final_sums(a.partials, a.k + 1, tot);
     if (threadIdx.x == 0) {
       const double kappa = tot[0];
       S.kappa = kappa;
+      for (int l = 0; l < a.k; ++l) S.vq[l] = tot[l + 1];
       if (!isfinite(kappa)) {
         S.done = kNonFinite;
       } else if (kappa <= 0.0) {
@@ -339,18 +373,17 @@ __global__ void __launch_bounds__(kThreads, 4) cg_step_a_kernel(CgArgs<T> a) {
 
 // ------------------------------------------------------------------ step b
 
+// V^T s_{i+1} = V^T s_i - alpha V^T (M_cg^{-1} q_i) follows from the
+// partials step a already formed (exact algebra, the same recurrence CG uses
+// for r itself), so this kernel streams only the four CG vectors.
 template <typename T, int KB>
 __global__ void __launch_bounds__(kThreads) cg_step_b_kernel(CgArgs<T> a) {
   constexpr int W = V16<T>::W;
-  constexpr int KS = KB > 0 ? KB : 1;
   CgState& S = a.st->cg;
   if (S.done != kRunning) return;
   const T alpha = alpha_of(S, T(0));
   const bool jac = a.dinv != nullptr;
   T rs = 0, rr = 0;
-  T u[KS];
-#pragma unroll
-  for (int l = 0; l < KS; ++l) u[l] = 0;
   const int64_t nvec = a.n_pad / W;
   for (int64_t iv = blockIdx.x * (int64_t)kThreads + threadIdx.x; iv < nvec; iv += (int64_t)gridDim.x * kThreads) {
     const int64_t i = iv * W;
@@ -381,24 +414,17 @@ __global__ void __launch_bounds__(kThreads) cg_step_b_kernel(CgArgs<T> a) {
     }
 #pragma unroll
     for (int e = 0; e < W; ++e) rs += rv[e] * s[e];
-#pragma unroll
-    for (int l = 0; l < KB; ++l)
-      if (l < a.k) {
-        T vv[W];
-        ld16_stream(a.V + (size_t)l * a.n_pad + i, vv);
-#pragma unroll
-        for (int e = 0; e < W; ++e) u[l] += vv[e] * s[e];
-      }
   }
-  T acc[KB + 2];
-  pack_slots<T, KB>(acc, rs, u, rr, a.k, jac);
-  const int nv = a.k + 1 + (jac ? 1 : 0);
-  block_partials_t<T, KB + 2>(acc, nv, a.partials);
+  T acc[2] = {rs, rr};
+  const int nv = jac ? 2 : 1;
+  block_partials_t<T, 2>(acc, nv, a.partials);
   if (last_block(&a.st->ticket)) {
-    __shared__ double tot[KB + 2];
+    __shared__ double tot[2];
     final_sums(a.partials, nv, tot);
     if (threadIdx.x == 0) {
-      const double rho_new = tot[0], rnorm = sqrt(jac ? tot[a.k + 1] : tot[0]);
+      const double rho_new = tot[0], rnorm = sqrt(jac ? tot[1] : tot[0]);
+      const double alpha_d = S.alpha;
+      for (int l = 0; l < a.k; ++l) S.u[l] -= alpha_d * S.vq[l];
       S.iters += 1;
       if (!isfinite(rho_new) || !isfinite(rnorm)) {
         S.done = kNonFinite;
@@ -411,7 +437,7 @@ __global__ void __launch_bounds__(kThreads) cg_step_b_kernel(CgArgs<T> a) {
         S.beta = beta;
         S.beta32 = (float)beta;
         S.rho = rho_new;
-        for (int l = 0; l < a.k; ++l) S.t[l] = tot[l + 1] + beta * S.t[l];
+        for (int l = 0; l < a.k; ++l) S.t[l] = S.u[l] + beta * S.t[l];
         publish_c(S, a.k);
       }
     }
@@ -474,6 +500,7 @@ void make_args(const InnerGraphSpec& spec, CgArgs<T> (&a)[2]) {
     x.partials = spec.partials;
     x.slice_ptr = spec.A.slice_ptr;
     x.col = spec.A.col;
+    x.col16 = spec.A.col16;
     x.val = reinterpret_cast<const T*>(sizeof(T) == 8 ? (const void*)spec.A.val64 : (const void*)spec.A.val32);
     x.nslices = spec.A.nslices;
     x.n_pad = spec.A.n_pad;

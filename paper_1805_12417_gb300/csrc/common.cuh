@@ -36,6 +36,8 @@ struct CgState {
   double lam2[kMaxK];    // 2 |lambda_j|
   double c[kMaxK];       // 2 |lambda_j| (V^T p)_j for the current direction p
   double t[kMaxK];       // (V^T p)_j for the current direction p
+  double u[kMaxK];       // V^T s of the current preconditioned residual s (recurrence)
+  double vq[kMaxK];      // V^T (M_cg^{-1} q) of the last M_mr product q
   float c32[kMaxK];      // FP32 copies of c, alpha, beta for the FP32 kernels
   float alpha32, beta32;
   double inner_tol;      // per-call parameters (uploaded by the host)
@@ -77,6 +79,7 @@ struct Sell {
   const int32_t* col = nullptr;        // [total]
   const double* val64 = nullptr;       // [total]
   const float* val32 = nullptr;        // [total] (mixed precision only)
+  const int16_t* col16 = nullptr;      // [total] col - row, when every such delta fits in 16 bits (inner kernels)
 };
 
 // ------------------------------------------------------------------ device helpers
@@ -135,6 +138,20 @@ __device__ __forceinline__ void block_partials(double (&v)[NV], int nv, double* 
   }
 }
 
+// Sum of x[lane], x[lane + 32], ... x[< count] with eight independent
+// accumulators, so eight L2 loads per lane are in flight at once (a single
+// accumulator would serialise on load latency).  The order is fixed by count.
+__device__ __forceinline__ double lane_sum8(const double* x, int count, int lane) {
+  double s[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  int b = lane;
+  for (; b + 7 * 32 < count; b += 8 * 32) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s[u] += __ldcg(x + b + u * 32);
+  }
+  for (int u = 0; b < count; b += 32, ++u) s[u] += __ldcg(x + b);
+  return ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
+}
+
 // Last-block detection (no waiting): every block publishes its partials,
 // fences, and takes a ticket; the block that draws the final ticket sees all
 // partials and finishes the reduction.  It also rearms the ticket.
@@ -158,7 +175,7 @@ __device__ __forceinline__ void final_sums(const double* partials, int nv, doubl
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i = warp; i < nv; i += kThreads / 32) {
     double s = 0.0;
-    for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(partials + (size_t)i * gridDim.x + b);
+    s = lane_sum8(partials + (size_t)i * gridDim.x, (int)gridDim.x, lane);
     s = warp_sum(s);
     if (lane == 0) out[i] = s;
   }

@@ -78,6 +78,9 @@ cudaError_t launch_sell_fill(cudaStream_t stream, int64_t n, const int64_t* rowp
                              const double* val, const int64_t* slice_ptr, int32_t* col, double* val64, float* val32);
 // elementwise conversions
 cudaError_t launch_to_f32(cudaStream_t stream, const double* in, float* out, int64_t n);
+// col16[idx] = col[idx] - row(idx) over the SELL layout
+cudaError_t launch_sell_delta16(cudaStream_t stream, int64_t n_pad, const int64_t* slice_ptr, const int32_t* col,
+                                int16_t* col16);
 cudaError_t launch_to_f64(cudaStream_t stream, const float* in, double* out, int64_t n);
 
 }  // namespace mrcg

@@ -346,6 +346,20 @@ __global__ void __launch_bounds__(kThreads) mmr_diag_kernel(int64_t n, int64_t n
   }
 }
 
+// col16 = col - row for every stored SELL entry (the caller checked that it fits)
+__global__ void sell_delta16_kernel(int64_t n_pad, const int64_t* __restrict__ slice_ptr,
+                                    const int32_t* __restrict__ col, int16_t* __restrict__ col16) {
+  ROW_LOOP(i, n_pad) {
+    const int64_t sl = i / kSlice, lane = i % kSlice;
+    const int64_t base = slice_ptr[sl];
+    const int w = (int)((slice_ptr[sl + 1] - base) / kSlice);
+    for (int j = 0; j < w; ++j) {
+      const int64_t idx = base + (int64_t)j * kSlice + lane;
+      col16[idx] = (int16_t)(col[idx] - i);
+    }
+  }
+}
+
 __global__ void to_f32_kernel(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
   ROW_LOOP(i, n) out[i] = (float)in[i];
 }
@@ -455,6 +469,12 @@ cudaError_t launch_sell_fill(cudaStream_t stream, int64_t n, const int64_t* rowp
   const int64_t n_pad = ((n + kSlice - 1) / kSlice) * kSlice;
   sell_fill_kernel<<<grid_for(n_pad, kMaxBlocks), kThreads, 0, stream>>>(n, n_pad, rowptr, colind, val, slice_ptr,
                                                                          col, val64, val32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sell_delta16(cudaStream_t stream, int64_t n_pad, const int64_t* slice_ptr, const int32_t* col,
+                                int16_t* col16) {
+  sell_delta16_kernel<<<grid_for(n_pad, kMaxBlocks), kThreads, 0, stream>>>(n_pad, slice_ptr, col, col16);
   return cudaGetLastError();
 }
 

@@ -699,7 +699,7 @@ __global__ void __launch_bounds__(kThreads) sh_scalar_kernel(DevState* st, const
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int v = warp; v < nval; v += kThreads / 32) {
     double s = 0.0;
-    for (int b = lane; b < nblk; b += 32) s += partials[((size_t)v * ncp + c) * nblk + b];
+    s = lane_sum8(partials + ((size_t)v * ncp + c) * nblk, nblk, lane);
     s = warp_sum(s);
     if (lane == 0) tot[v] = s;
   }
