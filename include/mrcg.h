@@ -130,23 +130,28 @@ mrcg_status mrcg_inner_solve(mrcg_handle h, const double* y, double* z, double i
 
 /* Diagnostic timing of the two kernels of one inner CG iteration (Eq. 2):
  *   ms[0]: step a  -- p = s + beta p fused into q = A p + V (2|Lambda| V^T p)
- *          and the partial p^T q (the M_mr product of Sec. 2),
+ *          and the partials p^T q and V^T M_cg^{-1} A p (the M_mr product
+ *          of Sec. 2; V^T s then follows by recurrence),
  *   ms[1]: step b  -- z += alpha p, r -= alpha q, s = M_cg^{-1} r and the
- *          partials r^T s, r^T r, V^T s.
+ *          partials r^T s, r^T r.
  * Each is launched `iters` times (1 <= iters <= 4096) on the handle's stream,
  * outside the solver's graph, on a fixed synthetic right-hand side, and
- * bracketed by CUDA events; ms receives the average duration in
+ * bracketed by CUDA events; ms receives the median duration in
  * milliseconds.  Overwrites the handle's work vectors (not its matrix). */
 mrcg_status mrcg_time_inner_kernels(mrcg_handle h, int32_t iters, double* ms);
 
 /* Launch configuration chosen for the handle's inner-CG kernels (at create,
  * by timing candidate shapes on this matrix unless MRCG_AUTOTUNE=0):
  * cfg[0] step-a variant (0: V_hat rows loaded before the SpMV, 1: after it,
- * 2: two slices per warp), cfg[1] step-a grid (blocks), cfg[2] step-b grid,
+ * 2: two slices per warp, 3 / 4: as 1 with registers capped for 6 / 8
+ * resident blocks per SM, 5 / 6: every streamed operand staged in shared
+ * memory by bulk copies, a persistent grid over tiles of 8 slices, registers
+ * capped for 2 / 4 blocks per SM), cfg[1] step-a grid (blocks), cfg[2] step-b grid,
  * cfg[3] CG iterations per body of the device loop, cfg[4] k bucket of the
  * kernels (0, 8, 16, 24 or 32), cfg[5] bytes per column index read by the
- * inner kernels (2: 16-bit col - row deltas, used when every delta fits; 4).
- * cfg must hold 6 values. */
+ * inner kernels (2: 16-bit col - row deltas, used when every delta fits; 4),
+ * cfg[6] shared-memory stages of variants 5 and 6 (0 for the others).
+ * cfg must hold 7 values. */
 mrcg_status mrcg_launch_config(mrcg_handle h, int32_t* cfg);
 
 /* ---- Batches of independent systems (many uneven systems in one launch sequence) ----

@@ -223,16 +223,17 @@ def inner_solve(h, y, z, inner_tol=1e-3, max_iters=0):
 
 def launch_config(h):
     """mrcg_launch_config: the autotuned launch shape of the inner-CG kernels."""
-    cfg = np.zeros(6, dtype=np.int32)
+    cfg = np.zeros(7, dtype=np.int32)
     st = lib().mrcg_launch_config(h, cfg.ctypes.data)
     if st != OK:
         raise MrcgError(st, "mrcg_launch_config")
     return {"step_a_variant": int(cfg[0]), "step_a_grid": int(cfg[1]), "step_b_grid": int(cfg[2]),
-            "unroll": int(cfg[3]), "k_bucket": int(cfg[4]), "index_bytes": int(cfg[5])}
+            "unroll": int(cfg[3]), "k_bucket": int(cfg[4]), "index_bytes": int(cfg[5]),
+            "stages": int(cfg[6])}
 
 
 def time_inner_kernels(h, iters=20):
-    """mrcg_time_inner_kernels: average ms of (step a, step b) of one inner CG iteration."""
+    """mrcg_time_inner_kernels: median ms of (step a, step b) of one inner CG iteration."""
     ms = np.zeros(2)
     st = lib().mrcg_time_inner_kernels(h, int(iters), ms.ctypes.data)
     if st != OK:

@@ -40,6 +40,7 @@ struct mrcg_solver {
   double* d_V64 = nullptr;
   float* d_V32 = nullptr;
   void* d_dinv = nullptr;
+  double* d_gram = nullptr;  // k x k V^T M_cg^{-1} V of the inner kernels' V
   DevState* d_st = nullptr;
   DevState* h_st = nullptr;    // pinned mirror (read back)
   DevState* h_init = nullptr;  // pinned staging (upload)
@@ -353,23 +354,16 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
   // ---- launch geometry
   int nsm = 1;
   CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
-  int occ_spmv = 1, occ_stream = 1;
-  inner_occupancy(h->fp32, a->k, &occ_spmv, &occ_stream);
-  if (occ_spmv < 1) occ_spmv = 1;
-  if (occ_stream < 1) occ_stream = 1;
-  // blocks per SM of the two CG kernels: the occupancy limit, optionally
-  // capped (MRCG_BPSM_A / MRCG_BPSM_B) for launch-shape sweeps
-  if (const char* e = getenv("MRCG_BPSM_A")) occ_spmv = std::max(1, std::min(occ_spmv, atoi(e)));
-  int occ_b = occ_stream;
-  if (const char* e = getenv("MRCG_BPSM_B")) occ_b = std::max(1, std::min(occ_stream, atoi(e)));
   const int vec_w = h->fp32 ? 4 : 2;  // elements per 16-byte access in step b
   const int64_t want_spmv = (nslices + kThreads / 32 - 1) / (kThreads / 32);
   const int64_t want_stream = (n_pad + kThreads - 1) / kThreads;
   const int64_t want_b = (n_pad / vec_w + kThreads - 1) / kThreads;
-  h->grid_spmv = (int)std::max<int64_t>(1, std::min<int64_t>({want_spmv, (int64_t)nsm * occ_spmv, kMaxBlocks}));
-  h->grid_stream =
-      (int)std::max<int64_t>(1, std::min<int64_t>({want_stream, (int64_t)nsm * occ_stream, kMaxBlocks}));
-  h->grid_stream_b = (int)std::max<int64_t>(1, std::min<int64_t>({want_b, (int64_t)nsm * occ_b, kMaxBlocks}));
+  auto clamp_grid = [&](int64_t want, int bp) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>({want, (int64_t)nsm * std::max(1, bp), kMaxBlocks}));
+  };
+  // outer FP64 kernels: four resident 256-thread blocks per SM
+  h->grid_spmv = clamp_grid(want_spmv, 4);
+  h->grid_stream = clamp_grid(want_stream, 4);
   if (const char* u = getenv("MRCG_UNROLL")) h->unroll = std::max(2, atoi(u) & ~1);
   if (const char* m = getenv("MRCG_INNER_LOOP")) h->host_loop = std::strcmp(m, "host") == 0;
 
@@ -389,61 +383,97 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
   g.V = h->fp32 ? (const void*)h->d_V32 : (const void*)h->d_V64;
   g.k = a->k;
   g.dinv = h->d_dinv;
+  if (a->k > 0) {
+    ST(dalloc(h, &h->d_gram, (size_t)a->k * a->k));
+    CK(launch_gram(g, h->stream, h->d_gram));
+  }
+  g.gram = h->d_gram;
   g.z = h->iz;
   g.r = h->ir;
   g.s = h->is;
   g.p0 = h->ip0;
   g.p1 = h->ip1;
   g.q = h->iq;
-  g.grid_spmv = h->grid_spmv;
   g.grid_stream = h->grid_stream;
-  g.grid_stream_b = h->grid_stream_b;
   g.unroll = h->unroll;
-  // ---- launch-shape autotuner: step-a variant and blocks per SM of both CG
-  // kernels, timed on this matrix (standalone launches, a few iterations each)
-  if (const char* va = getenv("MRCG_VAR_A")) g.var_a = std::min(2, std::max(0, atoi(va)));
+  // SELL entries of the largest tile of 8 slices (the staged step a's buffers)
+  for (int64_t s0 = 0; s0 < nslices; s0 += 8) g.tile_entries = std::max(g.tile_entries, sp[std::min(s0 + 8, nslices)] - sp[s0]);
+  if (const char* e = getenv("MRCG_STAGES")) g.stages = std::max(2, std::min(8, atoi(e)));
+  const int64_t ntiles = (nslices + 7) / 8;
+  // step-a grid of a variant at bp blocks per SM (the staged variant is persistent over tiles)
+  auto grid_a = [&](const InnerGraphSpec& t, int bp) {
+    return t.var_a >= 5 ? clamp_grid(ntiles, bp) : clamp_grid(want_spmv, bp);
+  };
+  if (const char* va = getenv("MRCG_VAR_A")) g.var_a = std::min(6, std::max(0, atoi(va)));
+  int occ_a = 1, occ_b = 1;
+  inner_occupancy(g, &occ_a, &occ_b);
+  if (occ_a < 1) {  // the staged variant does not fit this matrix
+    g.var_a = 0;
+    inner_occupancy(g, &occ_a, &occ_b);
+  }
+  occ_a = std::max(1, occ_a);
+  occ_b = std::max(1, occ_b);
+  // blocks per SM of the two CG kernels: the occupancy limit, optionally
+  // capped (MRCG_BPSM_A / MRCG_BPSM_B) for launch-shape sweeps
+  if (const char* e = getenv("MRCG_BPSM_A")) occ_a = std::max(1, std::min(occ_a, atoi(e)));
+  if (const char* e = getenv("MRCG_BPSM_B")) occ_b = std::max(1, std::min(occ_b, atoi(e)));
+  g.grid_spmv = grid_a(g, occ_a);
+  g.grid_stream_b = clamp_grid(want_b, occ_b);
+  // ---- launch-shape autotuner: step-a variant (and stages) with its blocks
+  // per SM, then step-b blocks per SM, timed on this matrix (standalone
+  // launches, medians of a few iterations)
   const char* at = getenv("MRCG_AUTOTUNE");
   const bool tune = (!at || atoi(at) != 0) && n_pad >= (1 << 18) && !getenv("MRCG_BPSM_A") &&
                     !getenv("MRCG_BPSM_B") && !getenv("MRCG_VAR_A");
   if (tune) {
     double ms[2] = {0.0, 0.0}, best = 1e30;
     InnerGraphSpec bestg = g;
-    for (int var = 0; var < 3; ++var)
-      for (int bp = std::max(1, occ_spmv - 2); bp <= occ_spmv; ++bp) {
-        InnerGraphSpec t = g;
-        t.var_a = var;
-        t.grid_spmv = (int)std::max<int64_t>(1, std::min<int64_t>({want_spmv, (int64_t)nsm * bp, kMaxBlocks}));
-        reset_state(h, 1e-300, 64);
-        h->h_init->cg.vin = h->v[0];
-        h->h_init->cg.zout = h->zraw;
-        ST(upload_state(h));
-        CK(time_inner_kernels(t, 10, h->stream, h->v[0], n, ms));
-        if (ms[0] < best) {
-          best = ms[0];
-          bestg.var_a = var;
-          bestg.grid_spmv = t.grid_spmv;
-        }
-      }
-    best = 1e30;
-    for (int bp = 1; bp <= occ_b; bp += (bp < 4 ? 1 : 2)) {
-      InnerGraphSpec t = bestg;
-      t.grid_stream_b = (int)std::max<int64_t>(1, std::min<int64_t>({want_b, (int64_t)nsm * bp, kMaxBlocks}));
+    auto time_spec = [&](const InnerGraphSpec& t) -> mrcg_status {
       reset_state(h, 1e-300, 64);
       h->h_init->cg.vin = h->v[0];
       h->h_init->cg.zout = h->zraw;
       ST(upload_state(h));
-      CK(time_inner_kernels(t, 10, h->stream, h->v[0], n, ms));
+      CK(time_inner_kernels(t, 15, h->stream, h->v[0], n, ms));
+      return MRCG_OK;
+    };
+    for (int var = 0; var <= 6; ++var) {
+      for (int nst = 2; nst <= (var >= 5 ? 4 : 2); ++nst) {
+        InnerGraphSpec t = g;
+        t.var_a = var;
+        t.stages = var >= 5 ? nst : g.stages;
+        int occ_v = 0, occ_unused = 0;
+        inner_occupancy(t, &occ_v, &occ_unused);
+        if (occ_v < 1) continue;
+        for (int bp = std::max(1, occ_v - 1); bp <= occ_v; ++bp) {
+          t.grid_spmv = grid_a(t, bp);
+          ST(time_spec(t));
+          if (ms[0] < best) {
+            best = ms[0];
+            bestg.var_a = t.var_a;
+            bestg.stages = t.stages;
+            bestg.grid_spmv = t.grid_spmv;
+          }
+        }
+      }
+    }
+    best = 1e30;
+    int occ_unused = 0, occ_bmax = 1;
+    inner_occupancy(bestg, &occ_unused, &occ_bmax);
+    for (int bp = 1; bp <= std::max(1, occ_bmax); bp += (bp < 4 ? 1 : 2)) {
+      InnerGraphSpec t = bestg;
+      t.grid_stream_b = clamp_grid(want_b, bp);
+      ST(time_spec(t));
       if (ms[1] < best) {
         best = ms[1];
         bestg.grid_stream_b = t.grid_stream_b;
       }
     }
     g = bestg;
-    h->grid_spmv = g.grid_spmv;
-    h->grid_stream_b = g.grid_stream_b;
     if (getenv("MRCG_DEBUG"))
-      fprintf(stderr, "mrcg autotune: var_a=%d grid_a=%d grid_b=%d\n", g.var_a, g.grid_spmv, g.grid_stream_b);
+      fprintf(stderr, "mrcg autotune: var_a=%d stages=%d grid_a=%d grid_b=%d\n", g.var_a, g.stages, g.grid_spmv,
+              g.grid_stream_b);
   }
+  h->grid_stream_b = g.grid_stream_b;
   h->spec = g;
   CK(build_inner_graph(g, &h->graph));
   CK(cudaGraphInstantiate(&h->graph_exec, h->graph, 0));
@@ -691,6 +721,7 @@ mrcg_status mrcg_launch_config(mrcg_handle h, int32_t* cfg) {
   cfg[3] = h->spec.unroll;
   cfg[4] = h->k == 0 ? 0 : h->k <= 8 ? 8 : h->k <= 16 ? 16 : h->k <= 24 ? 24 : 32;
   cfg[5] = h->A.col16 ? 2 : 4;
+  cfg[6] = h->spec.var_a >= 5 ? h->spec.stages : 0;
   return MRCG_OK;
 }
 

@@ -25,7 +25,8 @@ constexpr int kMaxBlocks = 2048;
 constexpr int kMaxNV = kMaxK + 2;  // reduction values per block
 
 // inner CG outcome codes (CgState::done)
-enum : int { kRunning = 0, kConverged = 1, kNotSpd = 2, kNonFinite = 3, kMaxIter = 4, kLoopCap = 5 };
+// (kStall: a staged copy did not arrive within its wait limit; reported as a CUDA error)
+enum : int { kRunning = 0, kConverged = 1, kNotSpd = 2, kNonFinite = 3, kMaxIter = 4, kLoopCap = 5, kStall = 6 };
 
 struct CgState {
   double rho;            // r^T s of the current residual (s = M_cg^{-1} r)
@@ -94,9 +95,9 @@ __device__ __forceinline__ T warp_sum(T v) {
 // Block reduction of NV per-thread values in the threads' own precision T
 // (FP32 in the mixed-precision kernels: no FP64 pipe work), stored as this
 // block's FP64 partials, value-major: partials[i * gridDim.x + blockIdx.x].
-template <typename T, int NV>
+template <typename T, int NV, int NW = kThreads / 32>
 __device__ __forceinline__ void block_partials_t(T (&v)[NV], int nv, double* partials) {
-  __shared__ T smt[kThreads / 32][NV > 0 ? NV : 1];
+  __shared__ T smt[NW][NV > 0 ? NV : 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int i = 0; i < NV; ++i)
@@ -110,7 +111,7 @@ __device__ __forceinline__ void block_partials_t(T (&v)[NV], int nv, double* par
   if (threadIdx.x < nv) {
     T s = 0;
 #pragma unroll
-    for (int w = 0; w < kThreads / 32; ++w) s += smt[w][threadIdx.x];
+    for (int w = 0; w < NW; ++w) s += smt[w][threadIdx.x];
     partials[threadIdx.x * gridDim.x + blockIdx.x] = (double)s;
   }
 }
@@ -173,7 +174,7 @@ __device__ __forceinline__ bool last_block(unsigned int* ticket) {
 // (deterministic).  Result in out[0..nv) (shared memory), valid after return.
 __device__ __forceinline__ void final_sums(const double* partials, int nv, double* out) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int i = warp; i < nv; i += kThreads / 32) {
+  for (int i = warp; i < nv; i += (int)(blockDim.x >> 5)) {
     double s = 0.0;
     s = lane_sum8(partials + (size_t)i * gridDim.x, (int)gridDim.x, lane);
     s = warp_sum(s);
@@ -183,5 +184,78 @@ __device__ __forceinline__ void final_sums(const double* partials, int nv, doubl
 }
 
 __device__ __forceinline__ bool finite(double x) { return isfinite(x); }
+
+// ------------------------------------------------------------------ bulk copies (TMA) and mbarriers
+//
+// cp.async.bulk moves a contiguous global range into shared memory on the
+// copy engine and signals an mbarrier with the bytes delivered; waits are
+// bounded by a clock limit so a copy that never lands turns into an error
+// status instead of a hang.
+
+constexpr long long kWaitCycles = 1ll << 31;  // about one second at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// make mbarrier initialisation visible to the copy engine
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// order this thread's earlier shared-memory accesses before later bulk copies into shared memory
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// global -> shared bulk copy; dst, src 16-byte aligned, bytes a positive multiple of 16
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// wait for the phase with this parity to complete; false after kWaitCycles
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > kWaitCycles) return false;
+  return true;
+}
+
+// the same, giving up early once another warp of the block has raised *abort
+// (and raising it itself when its own limit runs out)
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, int* abort) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*(volatile int*)abort) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      *(volatile int*)abort = 1;
+      return false;
+    }
+  }
+  return true;
+}
 
 }  // namespace mrcg

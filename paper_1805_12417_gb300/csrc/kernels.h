@@ -17,6 +17,7 @@ struct InnerGraphSpec {
   const void* V = nullptr;     // n_pad x k, inner precision
   int k = 0;
   const void* dinv = nullptr;  // Jacobi: 1 / diag(M_mr) (inner precision) or nullptr
+  const double* gram = nullptr;  // k x k  V^T M_cg^{-1} V  of the kernels' V (row-major)
   void* z = nullptr;
   void* r = nullptr;
   void* s = nullptr;
@@ -25,7 +26,12 @@ struct InnerGraphSpec {
   void* q = nullptr;
   int grid_spmv = 1, grid_stream = 1, grid_stream_b = 1;
   int unroll = 4;  // CG iterations per body of the while loop (even)
-  int var_a = 0;   // step-a kernel variant (0: early V loads, 1: late V loads, 2: two slices per warp)
+  int var_a = 0;   // step-a kernel variant (0: early V loads, 1: late V loads, 2: two slices per warp,
+                 // 3 / 4: late V loads with registers capped for 6 / 8 blocks per SM,
+                 // 5 / 6: operands staged in shared memory by bulk copies, registers capped for
+                 // 2 / 4 blocks per SM)
+  int64_t tile_entries = 0;  // most SELL entries in one tile of 8 slices (sizes the staged variant's buffers)
+  int stages = 3;            // staged variant: shared-memory stages per block
 };
 
 cudaError_t build_inner_graph(const InnerGraphSpec& spec, cudaGraph_t* graph);
@@ -34,7 +40,12 @@ cudaError_t run_inner_host(const InnerGraphSpec& spec, cudaStream_t stream, int*
 // standalone launches of the two CG iteration kernels, timed with events
 cudaError_t time_inner_kernels(const InnerGraphSpec& spec, int iters, cudaStream_t stream, double* vin, int64_t n,
                                double* ms);
-void inner_occupancy(bool fp32, int k, int* spmv_blocks_per_sm, int* stream_blocks_per_sm);
+// dynamic shared memory of the staged step a for this spec (0 when it does not fit in a block)
+int staged_smem_bytes(const InnerGraphSpec& spec);
+// resident blocks per SM of step-a variant var_a (spec.stages for the staged one) and of step b
+void inner_occupancy(const InnerGraphSpec& spec, int* spmv_blocks_per_sm, int* stream_blocks_per_sm);
+// gram = V^T M_cg^{-1} V (k x k) from spec.V and spec.dinv, FP64
+cudaError_t launch_gram(const InnerGraphSpec& spec, cudaStream_t stream, double* gram);
 
 // ---- outer MINRES kernels (FP64), launched on `stream` ----
 struct OuterArgs {

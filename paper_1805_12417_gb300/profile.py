@@ -6,6 +6,10 @@ mrcg_time_inner_kernels, printing their CUDA-event times.  Few other kernels
 run before them (setup only), which keeps an ncu capture of them small:
 
   python -m paper_1805_12417_gb300.profile --workload lap3d_128 --precision mixed --iters 3
+
+A profiler slows every launch, which misleads the launch-shape autotuner that
+runs at solver creation; `--var-a / --bpsm-a / --bpsm-b` fix the shape instead
+(the values a normal run reports through mrcg_launch_config).
 """
 from __future__ import annotations
 
@@ -29,14 +33,22 @@ def main(argv=None):
     ap.add_argument("--workload", default="lap3d_128", choices=["lap3d_128", "lap2d_64", "lap3d_small"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--iters", type=int, default=3)
+    ap.add_argument("--var-a", type=int, default=None, help="step-a kernel variant (0-4)")
+    ap.add_argument("--bpsm-a", type=int, default=None, help="step-a blocks per SM")
+    ap.add_argument("--bpsm-b", type=int, default=None, help="step-b blocks per SM")
     a = ap.parse_args(argv)
+    # read by the library when the solver is created
+    for key, val in (("MRCG_VAR_A", a.var_a), ("MRCG_BPSM_A", a.bpsm_a), ("MRCG_BPSM_B", a.bpsm_b)):
+        if val is not None:
+            os.environ[key] = str(val)
     import paper_1805_12417_gb300 as m
     p = workload(a.workload)
     prec = m.MIXED_FP32 if a.precision == "mixed" else m.FP64
     with m.Solver.from_problem(p, precision=prec, validate=False) as s:
         ta, tb = m.time_inner_kernels(s.h, a.iters)
+        cfg = m.launch_config(s.h)
     print(json.dumps({"workload": p.name, "precision": a.precision, "iters": a.iters, "step_a_ms": ta,
-                      "step_b_ms": tb}))
+                      "step_b_ms": tb, "launch_config": cfg}))
 
 
 if __name__ == "__main__":

@@ -1,0 +1,166 @@
+"""GPU parity of every step-a kernel variant of the inner CG (Eq. 2).
+
+The launch-shape autotuner may pick any variant for a matrix, so each one is
+forced here (MRCG_VAR_A, read when a solver is created) and checked against
+the FP64 oracle CG on the same inputs:
+
+  * FP64 kernels: iteration count within 1 of the oracle and the solution
+    within 1e-8 relative (the variants differ from the oracle only in the
+    order of the block sums);
+  * FP32 kernels: the M_mr residual of the returned z, recomputed by the
+    oracle in FP64, meets the inner tolerance (1e-4: FP32 arithmetic bounds
+    how far the true residual can follow the recursive one).
+
+Variants 5 and 6 (the same kernel with registers capped for 2 and 4 blocks
+per SM) stage every streamed operand in shared memory by bulk copies; they
+are run with 2, 3 and 4 stages (a shape whose stages do not fit in a block
+falls back to variant 0, which the fallback test checks), with 16-bit and 32-bit column indices, with
+Jacobi M_cg, on ragged last tiles and on rows far longer than the stencil's.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from gen import config2, random_sparse_symmetric, shifted_laplacian_problem, small_3d
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU hosts too
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1805_12417_gb300 as m  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+SHAPES = [(0, None), (1, None), (2, None), (3, None), (4, None), (5, 2), (5, 3), (5, 4), (6, 2), (6, 3)]
+SHAPE_IDS = ["v0", "v1", "v2", "v3", "v4", "staged2", "staged3", "staged4", "staged4bpsm_2", "staged4bpsm_3"]
+
+
+@pytest.fixture
+def shape_env(monkeypatch):
+    def set_shape(var, stages, idx16=True):
+        monkeypatch.setenv("MRCG_VAR_A", str(var))
+        if stages is not None:
+            monkeypatch.setenv("MRCG_STAGES", str(stages))
+        else:
+            monkeypatch.delenv("MRCG_STAGES", raising=False)
+        if not idx16:
+            monkeypatch.setenv("MRCG_IDX16", "0")
+    return set_shape
+
+
+def _check_cfg(g, var, stages, idx_bytes=None):
+    cfg = m.launch_config(g.h)
+    assert cfg["step_a_variant"] == var
+    if var >= 5:
+        assert cfg["stages"] == stages
+    if idx_bytes is not None:
+        assert cfg["index_bytes"] == idx_bytes
+
+
+def _inner_vs_oracle(p, prec, mcg, tol, seed, var, stages, idx_bytes=None, V=None, lam=None, sysargs=None):
+    s = O.System(*sysargs, V, lam) if sysargs is not None else O.System.from_problem(p)
+    n = sysargs[0].shape[0] - 1 if sysargs is not None else p.n
+    y = np.random.default_rng(seed).standard_normal(n)
+    zr, itr, st_r = s.cg(y, tol, 100000, mcg)
+    assert st_r == O.OK
+    if sysargs is not None:
+        g = m.Solver(n, *sysargs, V, lam, precision=prec, inner_prec=mcg, validate=False)
+    else:
+        g = m.Solver.from_problem(p, precision=prec, inner_prec=mcg)
+    with g:
+        _check_cfg(g, var, stages, idx_bytes)
+        z, st, it = g.inner_solve(y, inner_tol=tol)
+    assert st == m.OK
+    if prec == m.FP64:
+        assert abs(it - itr) <= 1
+        assert np.linalg.norm(z - zr) <= 1e-8 * np.linalg.norm(zr)
+    res = np.linalg.norm(y - s.mmr_apply(z))
+    assert res <= tol * np.linalg.norm(y) * (1.001 if prec == m.FP64 else 1.5)
+
+
+@pytest.mark.parametrize("var,stages", SHAPES, ids=SHAPE_IDS)
+@pytest.mark.parametrize("prec", [m.FP64, m.MIXED_FP32], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("mcg", [m.MCG_IDENTITY, m.MCG_JACOBI], ids=["id", "jacobi"])
+def test_inner_variants_small_3d(shape_env, var, stages, prec, mcg):
+    """12 x 11 x 10 Laplacian (n = 1320: 42 slices, last tile 2 slices), k = 5."""
+    shape_env(var, stages)
+    _inner_vs_oracle(small_3d(), prec, mcg, 1e-6 if prec == m.FP64 else 1e-4, 4, var, stages, idx_bytes=2)
+
+
+@pytest.mark.parametrize("k", [0, 1, 9, 17, 32])
+@pytest.mark.parametrize("var,stages", [(1, None), (3, None), (5, 2), (6, 2)], ids=["v1", "v3", "staged2", "staged4bpsm"])
+def test_inner_variants_k_buckets(shape_env, k, var, stages):
+    """Every k bucket of the kernels (FP64 stages of k = 32 hold 86 KB, so two fit a block)."""
+    p = shifted_laplacian_problem("t", (13, 11, 9), max(k, 1), seed=k) if k else None
+    shape_env(var, stages)
+    if p is None:
+        from gen import laplacian_csr
+        rp, ci, va = laplacian_csr((13, 11, 9), sigma=-0.5)  # SPD: M_mr = A
+        _inner_vs_oracle(None, m.FP64, m.MCG_IDENTITY, 1e-8, 1, var, stages, sysargs=(rp, ci, va))
+        return
+    _inner_vs_oracle(p, m.FP64, m.MCG_IDENTITY, 1e-8, k, var, stages)
+    _inner_vs_oracle(p, m.MIXED_FP32, m.MCG_IDENTITY, 1e-4, k, var, stages)
+
+
+@pytest.mark.parametrize("idx16", [True, False], ids=["idx16", "idx32"])
+@pytest.mark.parametrize("prec", [m.FP64, m.MIXED_FP32], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("stages", [2, 3])
+def test_staged_long_rows(shape_env, idx16, prec, stages):
+    """Rows of 2 to 19 entries at random columns (tiles of 3,488 entries, half
+    again the stencil's), n = 3001 (ragged last slice and tile), k = 6 random
+    orthonormal columns with negative lambdas (M_mr = A + 2 V |Lambda| V^T
+    stays SPD because A is), Jacobi M_cg."""
+    n = 3001
+    rp, ci, va = random_sparse_symmetric(n, 21, density_rows=(2, 12), diag_shift=30.0, empty_rows=0)
+    rng = np.random.default_rng(22)
+    V, _ = np.linalg.qr(rng.standard_normal((n, 6)))
+    lam = -rng.uniform(0.5, 3.0, 6)
+    shape_env(5, stages, idx16=idx16)
+    _inner_vs_oracle(None, prec, m.MCG_JACOBI, 1e-7 if prec == m.FP64 else 1e-4, 23, 5, stages,
+                     idx_bytes=2 if idx16 else 4, V=V, lam=lam, sysargs=(rp, ci, va))
+
+
+def test_staged_falls_back_when_stages_do_not_fit(shape_env):
+    """FP64, k = 32: three stages of 86 KB exceed a block's shared memory; and
+    rows of up to 64 entries make one stage of a tile 164 KB."""
+    shape_env(5, 3)
+    p = shifted_laplacian_problem("t", (13, 11, 9), 32, seed=32)
+    with m.Solver.from_problem(p) as g:
+        assert m.launch_config(g.h)["step_a_variant"] == 0
+        z, st, it = g.inner_solve(np.ones(p.n), inner_tol=1e-8)
+    assert st == m.OK and it > 0
+    shape_env(5, 2)
+    rp, ci, va = random_sparse_symmetric(3001, 21, density_rows=(2, 70), diag_shift=90.0, empty_rows=0)
+    with m.Solver(3001, rp, ci, va) as g:
+        assert m.launch_config(g.h)["step_a_variant"] == 0
+        z, st, it = g.inner_solve(np.ones(3001), inner_tol=1e-8)
+    assert st == m.OK and it > 0
+
+
+@pytest.mark.parametrize("var,stages", [(0, None), (5, 3), (6, 2)], ids=["v0", "staged3", "staged4bpsm"])
+def test_variants_full_solve_small(shape_env, var, stages):
+    """A whole MINRES-CG solve on every step-a path agrees with the oracle's."""
+    shape_env(var, stages)
+    p = small_3d()
+    ref = O.minres_cg(O.System.from_problem(p), p.b, outer_tol=1e-12, inner_tol=1e-3)
+    with m.Solver.from_problem(p) as g:
+        _check_cfg(g, var, stages)
+        x, info = g.solve(p.b.copy(), outer_tol=1e-12, inner_tol=1e-3)
+    assert info.status == m.OK
+    assert np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x) <= 1e-8
+
+
+def test_staged_full_size_mixed(shape_env):
+    """128^3 shifted Laplacian, mixed precision, staged step a with 3 stages:
+    the FP64 true residual reaches the benchmark tolerance."""
+    shape_env(5, 3)
+    p = config2()
+    with m.Solver.from_problem(p, precision=m.MIXED_FP32) as g:
+        _check_cfg(g, 5, 3)
+        x = torch.zeros(p.n, dtype=torch.float64, device=DEV)
+        _, info = g.solve(torch.from_numpy(p.b).to(DEV), x, outer_tol=1e-10, inner_tol=1e-3)
+    x = x.cpu().numpy()
+    assert info.status == m.OK
+    assert O.System.from_problem(p).true_relres(p.b, x) <= 1e-10
