@@ -146,11 +146,12 @@ mrcg_status mrcg_time_inner_kernels(mrcg_handle h, int32_t iters, double* ms);
  * 2: two slices per warp, 3 / 4: as 1 with registers capped for 6 / 8
  * resident blocks per SM, 5 / 6: every streamed operand staged in shared
  * memory by bulk copies, a persistent grid over tiles of 8 slices, registers
- * capped for 2 / 4 blocks per SM), cfg[1] step-a grid (blocks), cfg[2] step-b grid,
+ * capped for 2 / 4 blocks per SM, 7: as 5 with each warp's gathers issued
+ * one tile ahead), cfg[1] step-a grid (blocks), cfg[2] step-b grid,
  * cfg[3] CG iterations per body of the device loop, cfg[4] k bucket of the
- * kernels (0, 8, 16, 24 or 32), cfg[5] bytes per column index read by the
+ * kernels (0, 8, 12, 16, 24 or 32), cfg[5] bytes per column index read by the
  * inner kernels (2: 16-bit col - row deltas, used when every delta fits; 4),
- * cfg[6] shared-memory stages of variants 5 and 6 (0 for the others).
+ * cfg[6] shared-memory stages of variants 5 to 7 (0 for the others).
  * cfg must hold 7 values. */
 mrcg_status mrcg_launch_config(mrcg_handle h, int32_t* cfg);
 

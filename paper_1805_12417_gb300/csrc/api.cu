@@ -404,7 +404,7 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
   auto grid_a = [&](const InnerGraphSpec& t, int bp) {
     return t.var_a >= 5 ? clamp_grid(ntiles, bp) : clamp_grid(want_spmv, bp);
   };
-  if (const char* va = getenv("MRCG_VAR_A")) g.var_a = std::min(6, std::max(0, atoi(va)));
+  if (const char* va = getenv("MRCG_VAR_A")) g.var_a = std::min(7, std::max(0, atoi(va)));
   int occ_a = 1, occ_b = 1;
   inner_occupancy(g, &occ_a, &occ_b);
   if (occ_a < 1) {  // the staged variant does not fit this matrix
@@ -436,7 +436,7 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
       CK(time_inner_kernels(t, 15, h->stream, h->v[0], n, ms));
       return MRCG_OK;
     };
-    for (int var = 0; var <= 6; ++var) {
+    for (int var = 0; var <= 7; ++var) {
       for (int nst = 2; nst <= (var >= 5 ? 4 : 2); ++nst) {
         InnerGraphSpec t = g;
         t.var_a = var;
@@ -444,7 +444,15 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
         int occ_v = 0, occ_unused = 0;
         inner_occupancy(t, &occ_v, &occ_unused);
         if (occ_v < 1) continue;
-        for (int bp = std::max(1, occ_v - 1); bp <= occ_v; ++bp) {
+        // blocks per SM: the occupancy limit and one below; the staged kernels
+        // (no waits between blocks) also one wave of blocks above it and two
+        std::vector<int> bps = {occ_v};
+        if (occ_v > 1) bps.push_back(occ_v - 1);
+        if (var >= 5) {
+          bps.push_back(occ_v + 1);
+          bps.push_back(2 * occ_v);
+        }
+        for (int bp : bps) {
           t.grid_spmv = grid_a(t, bp);
           ST(time_spec(t));
           if (ms[0] < best) {
@@ -719,7 +727,7 @@ mrcg_status mrcg_launch_config(mrcg_handle h, int32_t* cfg) {
   cfg[1] = h->spec.grid_spmv;
   cfg[2] = h->spec.grid_stream_b;
   cfg[3] = h->spec.unroll;
-  cfg[4] = h->k == 0 ? 0 : h->k <= 8 ? 8 : h->k <= 16 ? 16 : h->k <= 24 ? 24 : 32;
+  cfg[4] = h->k == 0 ? 0 : h->k <= 8 ? 8 : h->k <= 12 ? 12 : h->k <= 16 ? 16 : h->k <= 24 ? 24 : 32;
   cfg[5] = h->A.col16 ? 2 : 4;
   cfg[6] = h->spec.var_a >= 5 ? h->spec.stages : 0;
   return MRCG_OK;

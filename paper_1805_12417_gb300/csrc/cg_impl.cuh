@@ -1,0 +1,1198 @@
+// Inner CG on M_mr z = y (Eq. 2, the inner block of Algorithm 1), one
+// application of the preconditioner of the outer MINRES.
+//
+// One CG iteration is two streaming kernels (one grid-wide reduction each):
+//   step_a: p' = s + beta p ; q = A p' + V c ; partials p'^T q and
+//           V^T M_cg^{-1} (A p')  (the direction update is fused into the
+//           SpMV gathers, so p' is never re-read; c = 2|Lambda| (V^T p')
+//           arrives as scalars)
+//   step_b: z += alpha p' ; r -= alpha q ; s = M_cg^{-1} r ;
+//           partials r^T s (and r^T r when M_cg is Jacobi)
+// The k numbers V^T s, V^T p' that the low-rank term needs come from exact
+// recurrences instead of passes over V_hat:
+//   V^T M_cg^{-1} q = V^T M_cg^{-1} (A p') + G c      (G = V^T M_cg^{-1} V)
+//   V^T s_{i+1}    = V^T s_i - alpha V^T M_cg^{-1} q_i (s = M_cg^{-1} r)
+//   V^T p'_{i+1}   = V^T s_{i+1} + beta V^T p'_i
+// so V_hat is read once per iteration (in step a, for both V c and the
+// partials) where the paper's M_mr product reads it twice (V^T u, then V t).
+// All scalar recurrences (alpha, beta, the stopping test) run in FP64 in the
+// last block of each kernel, which also publishes FP32 copies for the FP32
+// kernels.  Per-thread sums and the block reductions run in the kernel's own
+// precision (FP32 in mixed mode), the cross-block sum in FP64.
+//
+// The whole preconditioner application is one CUDA graph:
+//   norm(v) -> init -> while(not done) { U x (step_a, step_b), ctl } -> finish
+// The while loop is a conditional graph node: the inner iteration never
+// returns to the host.
+#pragma once
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace mrcg {
+
+template <typename T>
+struct CgArgs {
+  DevState* st;
+  double* partials;
+  // SELL A in the inner precision
+  const int64_t* slice_ptr;
+  const int32_t* col;
+  const int16_t* col16;  // col - row (16 bit) when it fits, else nullptr
+  const T* val;
+  int64_t nslices, n_pad;
+  // low-rank term
+  const T* V;  // n_pad x k column-major
+  int k;
+  // Jacobi: dinv != nullptr, s is a separate vector; identity: s == r
+  const T* dinv;
+  const double* gram;  // k x k V^T M_cg^{-1} V (row-major) of the kernels' V
+  // staged step a: ring of shared-memory stages (bytes; region offsets inside a stage)
+  int stages, stage_bytes, off_col, off_v, off_s, off_p, off_d;
+  // vectors
+  T* z;
+  T* r;
+  T* s;
+  T* p_old;
+  T* p_new;
+  T* q;
+};
+
+// ------------------------------------------------------------------ small helpers
+
+template <typename T>
+__device__ __forceinline__ T ld_stream(const T* p) {
+  return __ldcs(p);
+}
+
+template <typename T>
+struct V16;
+template <>
+struct V16<float> {
+  using type = float4;
+  static constexpr int W = 4;
+};
+template <>
+struct V16<double> {
+  using type = double2;
+  static constexpr int W = 2;
+};
+
+// 16-byte vector load / store into a register array
+template <typename T>
+__device__ __forceinline__ void ld16(const T* p, T (&x)[V16<T>::W]) {
+  const typename V16<T>::type v = *reinterpret_cast<const typename V16<T>::type*>(p);
+  memcpy(x, &v, 16);
+}
+template <typename T>
+__device__ __forceinline__ void ld16_stream(const T* p, T (&x)[V16<T>::W]) {
+  const typename V16<T>::type v = __ldcs(reinterpret_cast<const typename V16<T>::type*>(p));
+  memcpy(x, &v, 16);
+}
+template <typename T>
+__device__ __forceinline__ void st16(T* p, const T (&x)[V16<T>::W]) {
+  typename V16<T>::type v;
+  memcpy(&v, x, 16);
+  *reinterpret_cast<typename V16<T>::type*>(p) = v;
+}
+
+// broadcast scalars in the kernel's precision
+__device__ __forceinline__ float alpha_of(const CgState& S, float) { return S.alpha32; }
+__device__ __forceinline__ double alpha_of(const CgState& S, double) { return S.alpha; }
+__device__ __forceinline__ float beta_of(const CgState& S, float) { return S.beta32; }
+__device__ __forceinline__ double beta_of(const CgState& S, double) { return S.beta; }
+__device__ __forceinline__ float c_of(const CgState& S, int l, float) { return S.c32[l]; }
+__device__ __forceinline__ double c_of(const CgState& S, int l, double) { return S.c[l]; }
+
+// set c = 2|lambda| t (FP64 and FP32 copies)
+__device__ __forceinline__ void publish_c(CgState& S, int k) {
+  for (int l = 0; l < k; ++l) {
+    S.c[l] = S.lam2[l] * S.t[l];
+    S.c32[l] = (float)S.c[l];
+  }
+}
+
+// ------------------------------------------------------------------ norm of v
+
+static __global__ void __launch_bounds__(kThreads) cg_vnorm_kernel(DevState* st, double* partials, int64_t n_pad) {
+  CgState& S = st->cg;
+  const double* v = S.vin;
+  double acc[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n_pad; i += (int64_t)gridDim.x * kThreads) {
+    const double x = v[i];
+    acc[0] += x * x;
+  }
+  block_partials<1>(acc, 1, partials);
+  if (last_block(&st->ticket)) {
+    __shared__ double tot[1];
+    final_sums(partials, 1, tot);
+    if (threadIdx.x == 0) S.vnorm = sqrt(tot[0]);
+  }
+}
+
+// Reduction slots of init / step_b:  [0] = r^T s, [1 .. k] = V^T s,
+// [k + 1] = r^T r (Jacobi only; with M_cg = I, r^T s is r^T r).  Indices are
+// compile-time after unrolling, so the slot array stays in registers.
+template <typename T, int KB>
+__device__ __forceinline__ void pack_slots(T (&acc)[KB + 2], T rs, const T (&u)[KB > 0 ? KB : 1], T rr, int k,
+                                           bool jac) {
+  constexpr int KS = KB > 0 ? KB : 1;
+#pragma unroll
+  for (int l = 0; l < KB + 2; ++l) {
+    T val = (T)0;
+    if (l == 0) val = rs;
+    else if (l - 1 < KB && l - 1 < k) val = u[(l - 1 < KS) ? l - 1 : 0];
+    else if (jac && l == k + 1) val = rr;
+    acc[l] = val;
+  }
+}
+
+// ------------------------------------------------------------------ init
+
+template <typename T, int KB>
+__global__ void __launch_bounds__(kThreads) cg_init_kernel(CgArgs<T> a) {
+  constexpr int W = V16<T>::W;
+  constexpr int KS = KB > 0 ? KB : 1;
+  CgState& S = a.st->cg;
+  const double vn = S.vnorm;
+  const double scale = (vn > 0.0 && isfinite(vn)) ? 1.0 / vn : 0.0;
+  const double* v = S.vin;
+  const bool jac = a.dinv != nullptr;
+  T rs = 0, rr = 0;
+  T u[KS];
+#pragma unroll
+  for (int l = 0; l < KS; ++l) u[l] = 0;
+  const T zero[W] = {};
+  const int64_t nvec = a.n_pad / W;
+  for (int64_t iv = blockIdx.x * (int64_t)kThreads + threadIdx.x; iv < nvec; iv += (int64_t)gridDim.x * kThreads) {
+    const int64_t i = iv * W;
+    T r[W], s[W];
+#pragma unroll
+    for (int e = 0; e < W; ++e) r[e] = (T)(v[i + e] * scale);
+    st16(a.r + i, r);
+    st16(a.z + i, zero);
+    st16(a.p_old + i, zero);
+    if (jac) {
+      T d[W];
+      ld16(a.dinv + i, d);
+#pragma unroll
+      for (int e = 0; e < W; ++e) s[e] = d[e] * r[e];
+      st16(a.s + i, s);
+    } else {
+#pragma unroll
+      for (int e = 0; e < W; ++e) s[e] = r[e];
+    }
+#pragma unroll
+    for (int e = 0; e < W; ++e) {
+      rs += r[e] * s[e];
+      rr += r[e] * r[e];
+    }
+#pragma unroll
+    for (int l = 0; l < KB; ++l)
+      if (l < a.k) {
+        T vv[W];
+        ld16_stream(a.V + (size_t)l * a.n_pad + i, vv);
+#pragma unroll
+        for (int e = 0; e < W; ++e) u[l] += vv[e] * s[e];
+      }
+  }
+  T acc[KB + 2];
+  pack_slots<T, KB>(acc, rs, u, rr, a.k, jac);
+  const int nv = a.k + 1 + (jac ? 1 : 0);
+  block_partials_t<T, KB + 2>(acc, nv, a.partials);
+  if (last_block(&a.st->ticket)) {
+    __shared__ double tot[KB + 2];
+    final_sums(a.partials, nv, tot);
+    if (threadIdx.x == 0) {
+      const double rho = tot[0], rnorm = sqrt(jac ? tot[a.k + 1] : tot[0]);
+      S.rho = rho;
+      S.beta = 0.0;
+      S.beta32 = 0.0f;
+      S.iters = 0;
+      S.tol_abs = S.inner_tol * rnorm;
+      S.maxit = S.budget;
+      S.ctl_count = 0;
+      {
+        const long long per = S.unroll > 0 ? S.unroll : 1;
+        const long long lim = (S.maxit > 0 ? S.maxit : 0) / per + 2;
+        S.ctl_limit = (int)(lim < 0x7fffffffLL ? lim : 0x7fffffffLL);
+      }
+      S.done = kRunning;
+      if (!isfinite(vn) || !isfinite(rho)) {
+        S.done = kNonFinite;
+      } else if (vn == 0.0 || rnorm == 0.0) {
+        S.done = kConverged;
+      } else if (S.maxit <= 0) {
+        S.done = kMaxIter;
+      }
+      for (int l = 0; l < a.k; ++l) S.t[l] = S.u[l] = tot[l + 1];
+      publish_c(S, a.k);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ step a
+
+// The entries of one slice row, 8 at a time: all value / index loads of a
+// group are in flight before the gathers that depend on them.
+template <typename T>
+__device__ __forceinline__ T slice_row(const T* vp, const int32_t* cp, int w, const T* __restrict__ sv,
+                                       const T* __restrict__ po, T beta) {
+  T acc = 0;
+  for (int j0 = 0; j0 < w; j0 += 8) {
+    T av[8];
+    int cc[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      av[j] = (j0 + j < w) ? ld_stream(vp + (size_t)(j0 + j) * kSlice) : (T)0;
+      cc[j] = (j0 + j < w) ? ld_stream(cp + (size_t)(j0 + j) * kSlice) : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (j0 + j < w) acc += av[j] * (__ldg(sv + cc[j]) + beta * __ldg(po + cc[j]));
+  }
+  return acc;
+}
+
+// The same with 16-bit column deltas (col = row + delta): half the index bytes.
+template <typename T>
+__device__ __forceinline__ T slice_row16(const T* vp, const int16_t* cp, int row, int w, const T* __restrict__ sv,
+                                         const T* __restrict__ po, T beta) {
+  T acc = 0;
+  for (int j0 = 0; j0 < w; j0 += 8) {
+    T av[8];
+    int cc[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      av[j] = (j0 + j < w) ? ld_stream(vp + (size_t)(j0 + j) * kSlice) : (T)0;
+      cc[j] = (j0 + j < w) ? row + (int)ld_stream(cp + (size_t)(j0 + j) * kSlice) : row;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (j0 + j < w) acc += av[j] * (__ldg(sv + cc[j]) + beta * __ldg(po + cc[j]));
+  }
+  return acc;
+}
+
+// Block partials of p'^T q and V^T M_cg^{-1} (A p'), then in the last block:
+// kappa = p'^T q, alpha = rho / kappa and vq = V^T M_cg^{-1} (A p') + G c with
+// the c the kernels applied.  G is fetched (all loads independent) before the
+// cross-block sums, so its L2 latency overlaps theirs.  A block that met a
+// stalled copy has set S.done already; the last block then leaves alpha alone.
+template <typename T, int KB, int NW = kThreads / 32>
+__device__ __forceinline__ void step_a_reduce(const CgArgs<T>& a, CgState& S, T dot, const T (&wq)[KB > 0 ? KB : 1],
+                                              const T* cl) {
+  constexpr int KS = KB > 0 ? KB : 1;
+  T part[KB + 1];
+  part[0] = dot;
+#pragma unroll
+  for (int l = 0; l < KB; ++l) part[l + 1] = wq[l];
+  block_partials_t<T, KB + 1, NW>(part, a.k + 1, a.partials);
+  if (last_block(&a.st->ticket)) {
+    constexpr int KK = KS * KS;
+    constexpr int NT = NW * 32;
+    constexpr int GPT = (KK + NT - 1) / NT;
+    __shared__ double gs[KK];
+    double greg[GPT];
+    const int kk = a.k * a.k;
+#pragma unroll
+    for (int j = 0; j < GPT; ++j) {
+      const int e = threadIdx.x + j * NT;
+      greg[j] = (e < kk) ? __ldcg(a.gram + e) : 0.0;
+    }
+    __shared__ double tot[KB + 1];
+    final_sums(a.partials, a.k + 1, tot);
+#pragma unroll
+    for (int j = 0; j < GPT; ++j) {
+      const int e = threadIdx.x + j * NT;
+      if (e < kk) gs[e] = greg[j];
+    }
+    __syncthreads();
+    const int l = threadIdx.x;
+    if (l < a.k) {
+      // G is symmetric: column l, conflict-free shared reads
+      double g = tot[l + 1];
+#pragma unroll 8
+      for (int m = 0; m < KB; ++m)
+        if (m < a.k) g += gs[m * a.k + l] * (double)cl[m];
+      S.vq[l] = g;
+    }
+    if (threadIdx.x == 0 && *(volatile int*)&S.done == kRunning) {
+      const double kappa = tot[0];
+      S.kappa = kappa;
+      if (!isfinite(kappa)) {
+        S.done = kNonFinite;
+      } else if (kappa <= 0.0) {
+        S.done = kNotSpd;
+      } else {
+        S.alpha = S.rho / kappa;
+        S.alpha32 = (float)S.alpha;
+      }
+    }
+  }
+}
+
+// Variants (picked per handle by the launch-shape autotuner):
+//   VAR 0: V_hat row loads issued before the SpMV (more bytes in flight)
+//   VAR 1: V_hat read after the SpMV (fewer registers: no V_hat row is kept)
+//   VAR 2: two slices per warp per trip, V_hat early (more independent work)
+//   VAR 3, 4: as VAR 1 with registers capped for 6 and 8 resident blocks per SM
+//   (VAR 5, 6, 7: cg_step_a_staged_kernel below, registers capped for 2 / 4 blocks
+//   per SM; 7 issues each warp's gathers one tile ahead)
+//
+// V^T M_cg^{-1} q splits exactly as V^T M_cg^{-1} (A p') + G c with the
+// k x k Gram matrix G = V^T M_cg^{-1} V of the kernels' own V and M_cg^{-1}
+// (formed once per handle).  The kernel therefore accumulates only
+// V^T M_cg^{-1} (A p'), which is known before any V_hat entry of the row is
+// touched, and each V_hat entry is used once and dropped; the last block
+// adds G c.
+template <typename T, int KB, int VAR>
+__global__ void __launch_bounds__(kThreads, VAR == 3 ? 6 : (VAR == 4 ? 8 : 4)) cg_step_a_kernel(CgArgs<T> a) {
+  constexpr int KS = KB > 0 ? KB : 1;
+  constexpr int NSL = VAR == 2 ? 2 : 1;
+  constexpr bool kEarlyV = VAR == 0 || VAR == 2;
+  constexpr int VS = kEarlyV ? KS : 1;
+  CgState& S = a.st->cg;
+  if (S.done != kRunning) return;
+  const T beta = beta_of(S, T(0));
+  // c = 2|Lambda| (V^T p') staged in shared memory (broadcast reads, no registers)
+  __shared__ T cl[KS];
+  if (threadIdx.x < KS) cl[threadIdx.x] = ((int)threadIdx.x < a.k) ? c_of(S, threadIdx.x, T(0)) : (T)0;
+  __syncthreads();
+  const T* __restrict__ sv = a.s;
+  const T* __restrict__ po = a.p_old;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+  const bool jac = a.dinv != nullptr;
+  T dot = 0;
+  // wq[l] = (V^T M_cg^{-1} A p')_l: with this step b needs no pass over V (see step b)
+  T wq[KS];
+#pragma unroll
+  for (int l = 0; l < KS; ++l) wq[l] = 0;
+  for (int64_t sl0 = warp0 * NSL; sl0 < a.nslices; sl0 += nwarps * NSL) {
+    T vrow[NSL][VS], srow[NSL], prow[NSL], drow[NSL], acc[NSL];
+    int64_t rowv[NSL];
+    bool ok[NSL];
+#pragma unroll
+    for (int h = 0; h < NSL; ++h) {
+      const int64_t sl = sl0 + h;
+      ok[h] = sl < a.nslices;
+      rowv[h] = (ok[h] ? sl : sl0) * kSlice + lane;
+      if constexpr (kEarlyV) {
+#pragma unroll
+        for (int l = 0; l < KS; ++l)
+          vrow[h][l] = (ok[h] && l < a.k) ? ld_stream(a.V + (size_t)l * a.n_pad + rowv[h]) : (T)0;
+      }
+      srow[h] = sv[rowv[h]];
+      prow[h] = po[rowv[h]];
+      drow[h] = jac ? a.dinv[rowv[h]] : (T)1;
+    }
+#pragma unroll
+    for (int h = 0; h < NSL; ++h) {
+      if (!ok[h]) {
+        acc[h] = 0;
+        continue;
+      }
+      const int64_t sl = sl0 + h;
+      const int64_t base = a.slice_ptr[sl];
+      const int w = (int)((a.slice_ptr[sl + 1] - base) >> 5);
+      acc[h] = a.col16 ? slice_row16<T>(a.val + base + lane, a.col16 + base + lane, (int)rowv[h], w, sv, po, beta)
+                       : slice_row<T>(a.val + base + lane, a.col + base + lane, w, sv, po, beta);
+    }
+#pragma unroll
+    for (int h = 0; h < NSL; ++h) {
+      if (!ok[h]) continue;
+      const int64_t row = rowv[h];
+      const T pn = srow[h] + beta * prow[h];
+      const T ap = acc[h];
+      const T aps = jac ? drow[h] * ap : ap;  // (M_cg^{-1} A p')_row
+      T q = ap;
+      T vv[KS];  // this row of V_hat (the late loads are all issued before their first use)
+#pragma unroll
+      for (int l = 0; l < KS; ++l) {
+        if constexpr (kEarlyV) vv[l] = vrow[h][l < VS ? l : 0];
+        else vv[l] = (l < a.k) ? ld_stream(a.V + (size_t)l * a.n_pad + row) : (T)0;
+      }
+#pragma unroll
+      for (int l = 0; l < KB; ++l)
+        if (l < a.k) q += vv[l] * cl[l];
+#pragma unroll
+      for (int l = 0; l < KB; ++l)
+        if (l < a.k) wq[l] += vv[l] * aps;
+      a.q[row] = q;
+      a.p_new[row] = pn;
+      dot += pn * q;
+    }
+  }
+  step_a_reduce<T, KB>(a, S, dot, wq, cl);
+}
+
+// ------------------------------------------------------------------ step a, staged
+//
+// The arithmetic of cg_step_a_kernel, with every streamed operand of a tile
+// of 8 slices (256 rows) -- the tile's SELL values and indices, its rows of
+// each V_hat column, of s, p and (Jacobi) M_cg^{-1} -- brought into shared
+// memory by bulk copies (TMA), several tiles ahead: a ring of `stages`
+// buffers, each with a "full" mbarrier (copies landed) and an "empty" one
+// (every consumer warp has left it).  A producer warp issues the copies;
+// eight consumer warps take one slice of each tile and never wait on each
+// other.  Only the gathers s[col], p[col] of the SpMV go through the caches.
+// The grid is persistent: block b takes tiles b, b + grid, ...
+constexpr int kTileSlices = kThreads / 32;       // one consumer warp per slice
+constexpr int kTileRows = kTileSlices * kSlice;
+constexpr int kStagedThreads = kThreads + 32;    // consumer warps + one producer warp
+constexpr int kMaxStages = 8;
+
+template <typename T>
+__device__ __forceinline__ void issue_tile(const CgArgs<T>& a, unsigned char* b, uint64_t* bar, int64_t t, int64_t e0,
+                                           int64_t e1, uint64_t stream_pol) {
+  const bool jac = a.dinv != nullptr;
+  const int ib = a.col16 ? 2 : 4;
+  const char* idx = a.col16 ? (const char*)a.col16 : (const char*)a.col;
+  const int64_t s0 = t * kTileSlices, s1 = min(s0 + kTileSlices, a.nslices);
+  const int64_t row0 = s0 * kSlice;
+  const uint32_t rb = (uint32_t)((s1 - s0) * kSlice * (int64_t)sizeof(T));
+  const uint32_t ne = (uint32_t)(e1 - e0);
+  mbar_arrive_expect_tx(bar, ne * (uint32_t)(sizeof(T) + ib) + (uint32_t)(a.k + 2 + (jac ? 1 : 0)) * rb);
+  // the matrix and V_hat are read once per pass: evict-first in L2
+  if (ne > 0) {
+    bulk_g2s_hint(b, a.val + e0, ne * (uint32_t)sizeof(T), bar, stream_pol);
+    bulk_g2s_hint(b + a.off_col, idx + e0 * ib, ne * (uint32_t)ib, bar, stream_pol);
+  }
+  for (int l = 0; l < a.k; ++l)
+    bulk_g2s_hint(b + a.off_v + (size_t)l * kTileRows * sizeof(T), a.V + (size_t)l * a.n_pad + row0, rb, bar,
+                  stream_pol);
+  bulk_g2s(b + a.off_s, a.s + row0, rb, bar);
+  bulk_g2s(b + a.off_p, a.p_old + row0, rb, bar);
+  if (jac) bulk_g2s(b + a.off_d, a.dinv + row0, rb, bar);
+}
+
+// entries of one slice row from a staged tile: values and indices in shared
+// memory, the gathered s, p from global memory (8 gathers in flight)
+template <typename T, typename I>
+__device__ __forceinline__ T staged_row(const T* vp, const I* cp, int row, bool delta, int w,
+                                        const T* __restrict__ sv, const T* __restrict__ po, T beta) {
+  T acc = 0;
+  for (int j0 = 0; j0 < w; j0 += 8) {
+    T av[8];
+    int cc[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      av[j] = (j0 + j < w) ? vp[(j0 + j) * kSlice] : (T)0;
+      cc[j] = (j0 + j < w) ? (delta ? row : 0) + (int)cp[(j0 + j) * kSlice] : row;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (j0 + j < w) acc += av[j] * (__ldg(sv + cc[j]) + beta * __ldg(po + cc[j]));
+  }
+  return acc;
+}
+
+// The first eight entries of a slice row: gathers s[col], p[col] issued into
+// registers (the pipelined consumers issue them one tile ahead of their use).
+template <typename T, typename I>
+__device__ __forceinline__ void gather8(const I* cp, int row, bool delta, int w, const T* __restrict__ sv,
+                                        const T* __restrict__ po, T (&gs)[8], T (&gp)[8]) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int c = (j < w) ? (delta ? row : 0) + (int)cp[j * kSlice] : row;
+    gs[j] = (j < w) ? __ldg(sv + c) : (T)0;
+    gp[j] = (j < w) ? __ldg(po + c) : (T)0;
+  }
+}
+
+// A p' of a slice row from its first eight gathered pairs plus the rest of the row
+template <typename T, typename I>
+__device__ __forceinline__ T finish_row(const T* vp, const I* cp, int row, bool delta, int w, const T (&gs)[8],
+                                        const T (&gp)[8], const T* __restrict__ sv, const T* __restrict__ po, T beta) {
+  T acc = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    if (j < w) acc += vp[j * kSlice] * (gs[j] + beta * gp[j]);
+  if (w > 8) acc += staged_row<T, I>(vp + 8 * kSlice, cp + 8 * kSlice, row, delta, w - 8, sv, po, beta);
+  return acc;
+}
+
+template <typename T, int KB, int MB, bool PIPE>
+__global__ void __launch_bounds__(kStagedThreads, MB) cg_step_a_staged_kernel(CgArgs<T> a) {
+  constexpr int KS = KB > 0 ? KB : 1;
+  extern __shared__ __align__(128) unsigned char stage_mem[];
+  __shared__ __align__(8) uint64_t full[kMaxStages];   // tile landed (1 arrival + bytes)
+  __shared__ __align__(8) uint64_t empty[kMaxStages];  // all consumer warps left the tile
+  __shared__ int stalled;
+  __shared__ T cl[KS];
+  CgState& S = a.st->cg;
+  if (S.done != kRunning) return;
+  const T beta = beta_of(S, T(0));
+  if (threadIdx.x < KS) cl[threadIdx.x] = ((int)threadIdx.x < a.k) ? c_of(S, threadIdx.x, T(0)) : (T)0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool jac = a.dinv != nullptr;
+  const int nst = a.stages;
+  const int64_t ntiles = (a.nslices + kTileSlices - 1) / kTileSlices;
+  const int64_t ntl = (int64_t)blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t G = gridDim.x;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < nst; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], kTileSlices);
+    }
+    stalled = 0;
+    mbar_init_fence();
+  }
+  __syncthreads();
+  T dot = 0;
+  T wq[KS];
+#pragma unroll
+  for (int l = 0; l < KS; ++l) wq[l] = 0;
+  if (warp == kTileSlices) {
+    // producer warp (one lane): refill a stage as soon as every consumer warp
+    // has left it; tile offsets are fetched one tile ahead
+    if (lane == 0) {
+      const uint64_t stream_pol = l2_evict_first_policy();
+      int64_t issued = 0;
+      int64_t e0 = 0, e1 = 0;
+      if (ntl > 0) {
+        e0 = a.slice_ptr[(int64_t)blockIdx.x * kTileSlices];
+        e1 = a.slice_ptr[min((int64_t)(blockIdx.x + 1) * kTileSlices, a.nslices)];
+      }
+      // stage st of tile i = i mod nst, and the parity of its use (i / nst) & 1,
+      // kept incrementally (no integer division in the loop)
+      int st = 0;
+      uint32_t ph = 0;
+      int64_t t = blockIdx.x;
+      for (int64_t i = 0; i < ntl; ++i, t += G) {
+        if (i >= nst && !mbar_wait_or_abort(&empty[st], ph ^ 1u, &stalled)) break;
+        const int64_t c0 = e0, c1 = e1;
+        if (i + 1 < ntl) {
+          e0 = a.slice_ptr[(t + G) * kTileSlices];
+          e1 = a.slice_ptr[min((t + G + 1) * kTileSlices, a.nslices)];
+        }
+        fence_proxy_async_smem();
+        issue_tile(a, stage_mem + (size_t)st * a.stage_bytes, &full[st], t, c0, c1, stream_pol);
+        ++issued;
+        if (++st == nst) {
+          st = 0;
+          ph ^= 1u;
+        }
+      }
+      // no copy may still be writing this block's shared memory when it exits
+      for (int64_t j = issued > nst ? issued - nst : 0; j < issued; ++j)
+        mbar_wait(&full[j % nst], (uint32_t)((j / nst) & 1));
+    }
+  } else if constexpr (PIPE) {
+    // consumer warps, software-pipelined: while a warp finishes its slice of
+    // tile i it already has the gathers of its slice of tile i + 1 in flight
+    // (the tile's stage is waited for first), so gather latency overlaps
+    // the V_hat products, stores and sums of the tile before
+    const T* __restrict__ sv = a.s;
+    const T* __restrict__ po = a.p_old;
+    const bool d16 = a.col16 != nullptr;
+    int st = 0;
+    uint32_t ph = 0;
+    int64_t t = blockIdx.x;
+    // offsets of this warp's slice: tile i (cur_*) and the next tile (c_*, fetched ahead)
+    int cur_off = 0, cur_w = 0;
+    int64_t c_t0 = 0, c_s0 = 0, c_s1 = 0;
+    T gs[8], gp[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) gs[j] = gp[j] = 0;
+    auto offsets = [&](int64_t tt) {
+      const int64_t sl = tt * kTileSlices + warp;
+      c_t0 = a.slice_ptr[tt * kTileSlices];
+      if (sl < a.nslices) {
+        c_s0 = a.slice_ptr[sl];
+        c_s1 = a.slice_ptr[sl + 1];
+      } else {
+        c_s0 = c_s1 = c_t0;
+      }
+    };
+    // the gathers of this warp's slice of tile tt (stage sst, landed)
+    auto start = [&](int64_t tt, int sst, T (&g1)[8], T (&g2)[8]) {
+      const int64_t sl = tt * kTileSlices + warp;
+      cur_off = (int)(c_s0 - c_t0) + lane;
+      cur_w = (int)((c_s1 - c_s0) >> 5);
+      if (sl < a.nslices) {
+        const unsigned char* b = stage_mem + (size_t)sst * a.stage_bytes;
+        const int row = (int)(sl * kSlice + lane);
+        if (d16) gather8<T, int16_t>(reinterpret_cast<const int16_t*>(b + a.off_col) + cur_off, row, true, cur_w, sv,
+                                     po, g1, g2);
+        else gather8<T, int32_t>(reinterpret_cast<const int32_t*>(b + a.off_col) + cur_off, row, false, cur_w, sv, po,
+                                 g1, g2);
+      }
+    };
+    bool alive = true;
+    if (ntl > 0) {
+      offsets(t);
+      alive = mbar_wait_or_abort(&full[0], 0u, &stalled);
+      if (alive) start(t, 0, gs, gp);
+      if (ntl > 1) offsets(t + G);
+    }
+    for (int64_t i = 0; alive && i < ntl; ++i, t += G) {
+      const int off = cur_off, w = cur_w;
+      const int stn = st + 1 == nst ? 0 : st + 1;
+      const uint32_t phn = st + 1 == nst ? ph ^ 1u : ph;
+      T gsn[8], gpn[8];
+      if (i + 1 < ntl) {
+        if (!mbar_wait_or_abort(&full[stn], phn, &stalled)) break;
+        start(t + G, stn, gsn, gpn);
+        if (i + 2 < ntl) offsets(t + 2 * G);
+      }
+      const int64_t sl = t * kTileSlices + warp;
+      if (sl < a.nslices) {
+        const unsigned char* b = stage_mem + (size_t)st * a.stage_bytes;
+        const int r = warp * kSlice + lane;
+        const int64_t row = sl * kSlice + lane;
+        const T* vp = reinterpret_cast<const T*>(b) + off;
+        const T ap = d16 ? finish_row<T, int16_t>(vp, reinterpret_cast<const int16_t*>(b + a.off_col) + off, (int)row,
+                                                  true, w, gs, gp, sv, po, beta)
+                         : finish_row<T, int32_t>(vp, reinterpret_cast<const int32_t*>(b + a.off_col) + off, (int)row,
+                                                  false, w, gs, gp, sv, po, beta);
+        const T pn =
+            reinterpret_cast<const T*>(b + a.off_s)[r] + beta * reinterpret_cast<const T*>(b + a.off_p)[r];
+        const T aps = jac ? reinterpret_cast<const T*>(b + a.off_d)[r] * ap : ap;
+        const T* vt = reinterpret_cast<const T*>(b + a.off_v) + r;
+        T q = ap;
+#pragma unroll
+        for (int l = 0; l < KB; ++l)
+          if (l < a.k) {
+            const T v = vt[l * kTileRows];
+            q += v * cl[l];
+            wq[l] += v * aps;
+          }
+        a.q[row] = q;
+        a.p_new[row] = pn;
+        dot += pn * q;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[st]);
+      if (i + 1 < ntl) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          gs[j] = gsn[j];
+          gp[j] = gpn[j];
+        }
+      }
+      st = stn;
+      ph = phn;
+    }
+  } else {
+    // consumer warps: warp w takes slice w of every tile
+    int64_t c_t0 = 0, c_s0 = 0, c_s1 = 0;
+    if (ntl > 0) {
+      const int64_t sl = blockIdx.x * (int64_t)kTileSlices + warp;
+      c_t0 = a.slice_ptr[blockIdx.x * (int64_t)kTileSlices];
+      if (sl < a.nslices) {
+        c_s0 = a.slice_ptr[sl];
+        c_s1 = a.slice_ptr[sl + 1];
+      }
+    }
+    const T* __restrict__ sv = a.s;
+    const T* __restrict__ po = a.p_old;
+    int st = 0;
+    uint32_t ph = 0;
+    int64_t t = blockIdx.x;
+    for (int64_t i = 0; i < ntl; ++i, t += G) {
+      const int64_t sl = t * kTileSlices + warp;
+      const int64_t t0 = c_t0, s0 = c_s0, s1 = c_s1;
+      if (i + 1 < ntl) {
+        const int64_t tn = t + G, sln = tn * kTileSlices + warp;
+        c_t0 = a.slice_ptr[tn * kTileSlices];
+        if (sln < a.nslices) {
+          c_s0 = a.slice_ptr[sln];
+          c_s1 = a.slice_ptr[sln + 1];
+        }
+      }
+      if (!mbar_wait_or_abort(&full[st], ph, &stalled)) break;
+      if (sl < a.nslices) {
+        const unsigned char* b = stage_mem + (size_t)st * a.stage_bytes;
+        const int off = (int)(s0 - t0) + lane;
+        const int w = (int)((s1 - s0) >> 5);
+        const int r = warp * kSlice + lane;
+        const int64_t row = sl * kSlice + lane;
+        const T* vp = reinterpret_cast<const T*>(b) + off;
+        const T ap = a.col16 ? staged_row<T, int16_t>(vp, reinterpret_cast<const int16_t*>(b + a.off_col) + off,
+                                                      (int)row, true, w, sv, po, beta)
+                             : staged_row<T, int32_t>(vp, reinterpret_cast<const int32_t*>(b + a.off_col) + off,
+                                                      (int)row, false, w, sv, po, beta);
+        const T pn =
+            reinterpret_cast<const T*>(b + a.off_s)[r] + beta * reinterpret_cast<const T*>(b + a.off_p)[r];
+        const T aps = jac ? reinterpret_cast<const T*>(b + a.off_d)[r] * ap : ap;  // (M_cg^{-1} A p')_row
+        const T* vt = reinterpret_cast<const T*>(b + a.off_v) + r;
+        T q = ap;
+#pragma unroll
+        for (int l = 0; l < KB; ++l)
+          if (l < a.k) {
+            const T v = vt[l * kTileRows];
+            q += v * cl[l];
+            wq[l] += v * aps;
+          }
+        a.q[row] = q;
+        a.p_new[row] = pn;
+        dot += pn * q;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[st]);
+      if (++st == nst) {
+        st = 0;
+        ph ^= 1u;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && stalled) *(volatile int*)&S.done = kStall;
+  step_a_reduce<T, KB, kStagedThreads / 32>(a, S, dot, wq, cl);
+}
+
+// G = V^T M_cg^{-1} V (k x k, both triangles) from the kernels' own V and
+// M_cg^{-1} in FP64: one block per pair l <= m.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) cg_gram_kernel(const T* V, const T* dinv, int64_t n_pad, int k,
+                                                          double* G) {
+  int p = blockIdx.x, l = 0;
+  while (l < k && p >= k - l) {
+    p -= k - l;
+    ++l;
+  }
+  if (l >= k) return;
+  const int m = l + p;
+  const T* vl = V + (size_t)l * n_pad;
+  const T* vm = V + (size_t)m * n_pad;
+  double s[1] = {0.0};
+  for (int64_t i = threadIdx.x; i < n_pad; i += kThreads) {
+    const double d = dinv ? (double)dinv[i] : 1.0;
+    s[0] += (double)vl[i] * d * (double)vm[i];
+  }
+  __shared__ double sm[kThreads / 32];
+  const double w = warp_sum(s[0]);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = w;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < kThreads / 32; ++i) t += sm[i];
+    G[(size_t)l * k + m] = t;
+    G[(size_t)m * k + l] = t;
+  }
+}
+
+// ------------------------------------------------------------------ step b
+
+// V^T s_{i+1} = V^T s_i - alpha V^T (M_cg^{-1} q_i) follows from what step a
+// already formed (exact algebra, the same recurrence CG uses for r itself),
+// so this kernel streams only the four CG vectors.
+template <typename T, int KB>
+__global__ void __launch_bounds__(kThreads) cg_step_b_kernel(CgArgs<T> a) {
+  constexpr int W = V16<T>::W;
+  CgState& S = a.st->cg;
+  if (S.done != kRunning) return;
+  const T alpha = alpha_of(S, T(0));
+  const bool jac = a.dinv != nullptr;
+  T rs = 0, rr = 0;
+  const int64_t nvec = a.n_pad / W;
+  for (int64_t iv = blockIdx.x * (int64_t)kThreads + threadIdx.x; iv < nvec; iv += (int64_t)gridDim.x * kThreads) {
+    const int64_t i = iv * W;
+    T pn[W], qv[W], zv[W], rv[W], s[W];
+    ld16(a.p_new + i, pn);
+    ld16(a.q + i, qv);
+    ld16(a.z + i, zv);
+    ld16(a.r + i, rv);
+#pragma unroll
+    for (int e = 0; e < W; ++e) {
+      zv[e] += alpha * pn[e];
+      rv[e] -= alpha * qv[e];
+    }
+    st16(a.z + i, zv);
+    st16(a.r + i, rv);
+    if (jac) {
+      T d[W];
+      ld16(a.dinv + i, d);
+#pragma unroll
+      for (int e = 0; e < W; ++e) {
+        s[e] = d[e] * rv[e];
+        rr += rv[e] * rv[e];
+      }
+      st16(a.s + i, s);
+    } else {
+#pragma unroll
+      for (int e = 0; e < W; ++e) s[e] = rv[e];
+    }
+#pragma unroll
+    for (int e = 0; e < W; ++e) rs += rv[e] * s[e];
+  }
+  T acc[2] = {rs, rr};
+  const int nv = jac ? 2 : 1;
+  block_partials_t<T, 2>(acc, nv, a.partials);
+  if (last_block(&a.st->ticket)) {
+    __shared__ double tot[2];
+    final_sums(a.partials, nv, tot);
+    if (threadIdx.x == 0) {
+      const double rho_new = tot[0], rnorm = sqrt(jac ? tot[1] : tot[0]);
+      const double alpha_d = S.alpha;
+      for (int l = 0; l < a.k; ++l) S.u[l] -= alpha_d * S.vq[l];
+      S.iters += 1;
+      if (!isfinite(rho_new) || !isfinite(rnorm)) {
+        S.done = kNonFinite;
+      } else if (rnorm <= S.tol_abs) {
+        S.done = kConverged;
+      } else if (S.iters >= S.maxit) {
+        S.done = kMaxIter;
+      } else {
+        const double beta = rho_new / S.rho;
+        S.beta = beta;
+        S.beta32 = (float)beta;
+        S.rho = rho_new;
+        for (int l = 0; l < a.k; ++l) S.t[l] = S.u[l] + beta * S.t[l];
+        publish_c(S, a.k);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ loop control
+
+static __global__ void cg_ctl_kernel(DevState* st, cudaGraphConditionalHandle handle) {
+  CgState& S = st->cg;
+  S.ctl_count += 1;
+  if (S.done == kRunning && S.ctl_count >= S.ctl_limit) S.done = kLoopCap;
+  cudaGraphSetConditional(handle, S.done == kRunning ? 1u : 0u);
+}
+
+// the same bookkeeping for the host-driven loop (no graph condition)
+static __global__ void cg_ctl_host_kernel(DevState* st) {
+  CgState& S = st->cg;
+  S.ctl_count += 1;
+  if (S.done == kRunning && S.ctl_count >= S.ctl_limit) S.done = kLoopCap;
+}
+
+// ------------------------------------------------------------------ finish
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) cg_finish_kernel(DevState* st, const T* z, int64_t n_pad) {
+  CgState& S = st->cg;
+  const double vn = (S.vnorm > 0.0 && isfinite(S.vnorm)) ? S.vnorm : 0.0;
+  double* out = S.zout;
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n_pad; i += (int64_t)gridDim.x * kThreads)
+    out[i] = vn * (double)z[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    S.budget -= S.iters;
+    OuterState& O = st->out;
+    O.inner_total += S.iters;
+    O.prec_calls += 1;
+    O.bodies += S.ctl_count;
+    if (O.status == MRCG_OK) {
+      if (S.done == kNotSpd) O.status = MRCG_ERR_NOT_SPD;
+      else if (S.done == kNonFinite) O.status = MRCG_ERR_NONFINITE;
+      else if (S.done == kMaxIter || S.done == kLoopCap) O.status = MRCG_ERR_MAXITER;
+    }
+  }
+}
+
+static __global__ void fill_pattern_kernel(double* v, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
+    v[i] = 1.0 + 0.125 * (double)(i % 7) - 0.0625 * (double)(i % 3);
+}
+
+// ------------------------------------------------------------------ host side
+
+namespace {
+
+// stage layout of the staged step a (128-byte aligned regions)
+struct StageGeo {
+  int off_col, off_v, off_s, off_p, off_d, bytes;
+};
+
+StageGeo stage_geo(const InnerGraphSpec& spec) {
+  auto up = [](int64_t x) { return (x + 127) / 128 * 128; };
+  const int64_t w = spec.fp32 ? 4 : 8, ib = spec.A.col16 ? 2 : 4, E = spec.tile_entries;
+  StageGeo g;
+  int64_t o = up(E * w);
+  g.off_col = (int)o;
+  o += up(E * ib);
+  g.off_v = (int)o;
+  o += (int64_t)spec.k * kTileRows * w;
+  g.off_s = (int)o;
+  o += kTileRows * w;
+  g.off_p = (int)o;
+  o += kTileRows * w;
+  g.off_d = (int)o;
+  if (spec.dinv) o += kTileRows * w;
+  g.bytes = o > (1 << 30) ? (1 << 30) : (int)o;
+  return g;
+}
+
+constexpr int kMaxDynSmem = 227 * 1024 - 16 * 1024;  // leaves room for the kernel's static shared memory
+
+template <typename T>
+void make_args(const InnerGraphSpec& spec, CgArgs<T> (&a)[2]) {
+  const StageGeo geo = stage_geo(spec);
+  for (int par = 0; par < 2; ++par) {
+    CgArgs<T>& x = a[par];
+    x.stages = spec.stages;
+    x.stage_bytes = geo.bytes;
+    x.off_col = geo.off_col;
+    x.off_v = geo.off_v;
+    x.off_s = geo.off_s;
+    x.off_p = geo.off_p;
+    x.off_d = geo.off_d;
+    x.st = spec.st;
+    x.partials = spec.partials;
+    x.slice_ptr = spec.A.slice_ptr;
+    x.col = spec.A.col;
+    x.col16 = spec.A.col16;
+    x.val = reinterpret_cast<const T*>(sizeof(T) == 8 ? (const void*)spec.A.val64 : (const void*)spec.A.val32);
+    x.nslices = spec.A.nslices;
+    x.n_pad = spec.A.n_pad;
+    x.V = reinterpret_cast<const T*>(spec.V);
+    x.k = spec.k;
+    x.dinv = reinterpret_cast<const T*>(spec.dinv);
+    x.gram = spec.gram;
+    x.z = reinterpret_cast<T*>(spec.z);
+    x.r = reinterpret_cast<T*>(spec.r);
+    x.s = spec.dinv ? reinterpret_cast<T*>(spec.s) : reinterpret_cast<T*>(spec.r);
+    x.q = reinterpret_cast<T*>(spec.q);
+    x.p_old = reinterpret_cast<T*>(par == 0 ? spec.p0 : spec.p1);
+    x.p_new = reinterpret_cast<T*>(par == 0 ? spec.p1 : spec.p0);
+  }
+}
+
+cudaError_t add_kernel(cudaGraph_t g, cudaGraphNode_t* node, const cudaGraphNode_t* deps, size_t ndeps,
+                       const void* fn, int grid, int block, void** args, unsigned smem = 0) {
+  cudaKernelNodeParams p = {};
+  p.func = const_cast<void*>(fn);
+  p.gridDim = dim3(grid);
+  p.blockDim = dim3(block);
+  p.sharedMemBytes = smem;
+  p.kernelParams = args;
+  p.extra = nullptr;
+  return cudaGraphAddKernelNode(node, g, deps, ndeps, &p);
+}
+
+template <typename T, int KB>
+const void* step_a_fn(int var) {
+  switch (var) {
+    case 1: return (const void*)cg_step_a_kernel<T, KB, 1>;
+    case 2: return (const void*)cg_step_a_kernel<T, KB, 2>;
+    case 3: return (const void*)cg_step_a_kernel<T, KB, 3>;
+    case 4: return (const void*)cg_step_a_kernel<T, KB, 4>;
+    case 5: return (const void*)cg_step_a_staged_kernel<T, KB, 2, false>;
+    case 6: return (const void*)cg_step_a_staged_kernel<T, KB, 4, false>;
+    case 7: return (const void*)cg_step_a_staged_kernel<T, KB, 2, true>;
+    default: return (const void*)cg_step_a_kernel<T, KB, 0>;
+  }
+}
+
+// dynamic shared memory of the step-a launch (opting the staged kernel in above 48 KB)
+template <typename T, int KB>
+unsigned step_a_smem(const InnerGraphSpec& spec) {
+  if (spec.var_a < 5) return 0;
+  const int bytes = stage_geo(spec).bytes * spec.stages;
+  cudaFuncSetAttribute(step_a_fn<T, KB>(spec.var_a), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return (unsigned)bytes;
+}
+
+// threads per block of the step-a launch
+int step_a_block(const InnerGraphSpec& spec) { return spec.var_a >= 5 ? kStagedThreads : kThreads; }
+
+template <typename T>
+cudaError_t launch_a(const void* fn, int grid, int block, cudaStream_t stream, CgArgs<T>& a, unsigned smem) {
+  void* args[] = {&a};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, stream);
+}
+
+template <typename T, int KB>
+cudaError_t build_graph_t(const InnerGraphSpec& spec, cudaGraph_t* out_graph) {
+  cudaError_t e;
+  cudaGraph_t g;
+  if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) return e;
+  CgArgs<T> a[2];
+  make_args(spec, a);
+  DevState* st = spec.st;
+  double* partials = spec.partials;
+  int64_t n_pad = spec.A.n_pad;
+  const T* zc = reinterpret_cast<const T*>(spec.z);
+  const unsigned smem_a = step_a_smem<T, KB>(spec);
+
+  cudaGraphNode_t n_norm, n_init, n_loop, n_fin;
+  void* norm_args[] = {&st, &partials, &n_pad};
+  if ((e = add_kernel(g, &n_norm, nullptr, 0, (const void*)cg_vnorm_kernel, spec.grid_stream, kThreads, norm_args)))
+    goto fail;
+  {
+    void* init_args[] = {&a[0]};
+    if ((e = add_kernel(g, &n_init, &n_norm, 1, (const void*)cg_init_kernel<T, KB>, spec.grid_stream, kThreads,
+                        init_args)))
+      goto fail;
+  }
+  {
+    cudaGraphConditionalHandle h;
+    if ((e = cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault))) goto fail;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    if ((e = cudaGraphAddNode(&n_loop, g, &n_init, nullptr, 1, &cp))) goto fail;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaGraphNode_t prev = nullptr;
+    for (int it = 0; it < spec.unroll; ++it) {
+      void* aa[] = {&a[it & 1]};
+      cudaGraphNode_t na, nb;
+      if ((e = add_kernel(body, &na, prev ? &prev : nullptr, prev ? 1 : 0, step_a_fn<T, KB>(spec.var_a),
+                          spec.grid_spmv, step_a_block(spec), aa, smem_a)))
+        goto fail;
+      if ((e = add_kernel(body, &nb, &na, 1, (const void*)cg_step_b_kernel<T, KB>, spec.grid_stream_b, kThreads,
+                          aa)))
+        goto fail;
+      prev = nb;
+    }
+    cudaGraphNode_t nc;
+    void* ctl_args[] = {&st, &h};
+    if ((e = add_kernel(body, &nc, &prev, 1, (const void*)cg_ctl_kernel, 1, 1, ctl_args))) goto fail;
+  }
+  {
+    void* fin_args[] = {&st, (void*)&zc, &n_pad};
+    if ((e = add_kernel(g, &n_fin, &n_loop, 1, (const void*)cg_finish_kernel<T>, spec.grid_stream, kThreads,
+                        fin_args)))
+      goto fail;
+  }
+  *out_graph = g;
+  return cudaSuccess;
+fail:
+  cudaGraphDestroy(g);
+  return e;
+}
+
+// The same launch sequence as the graph, driven from the host: after every U
+// iterations the host reads the `done` word.  Used when a profiler must see
+// the individual kernels (kernel nodes under a conditional node cannot be
+// profiled).
+template <typename T, int KB>
+cudaError_t run_host_t(const InnerGraphSpec& spec, cudaStream_t stream, int* h_done) {
+  CgArgs<T> a[2];
+  make_args(spec, a);
+  const unsigned smem_a = step_a_smem<T, KB>(spec);
+  cg_vnorm_kernel<<<spec.grid_stream, kThreads, 0, stream>>>(spec.st, spec.partials, spec.A.n_pad);
+  cg_init_kernel<T, KB><<<spec.grid_stream, kThreads, 0, stream>>>(a[0]);
+  cudaError_t e = cudaSuccess;
+  for (;;) {
+    for (int it = 0; it < spec.unroll; ++it) {
+      launch_a<T>(step_a_fn<T, KB>(spec.var_a), spec.grid_spmv, step_a_block(spec), stream, a[it & 1], smem_a);
+      cg_step_b_kernel<T, KB><<<spec.grid_stream_b, kThreads, 0, stream>>>(a[it & 1]);
+    }
+    cg_ctl_host_kernel<<<1, 1, 0, stream>>>(spec.st);
+    if ((e = cudaMemcpyAsync(h_done, &spec.st->cg.done, sizeof(int), cudaMemcpyDeviceToHost, stream))) return e;
+    if ((e = cudaStreamSynchronize(stream))) return e;
+    if (*h_done != kRunning) break;
+  }
+  cg_finish_kernel<T><<<spec.grid_stream, kThreads, 0, stream>>>(spec.st, reinterpret_cast<const T*>(spec.z),
+                                                                  spec.A.n_pad);
+  return cudaGetLastError();
+}
+
+template <typename T, int KB>
+cudaError_t time_t(const InnerGraphSpec& spec, int iters, cudaStream_t stream, double* vin, int64_t n,
+                   double* ms) {
+  CgArgs<T> a[2];
+  make_args(spec, a);
+  const unsigned smem_a = step_a_smem<T, KB>(spec);
+  fill_pattern_kernel<<<spec.grid_stream, kThreads, 0, stream>>>(vin, n);
+  cg_vnorm_kernel<<<spec.grid_stream, kThreads, 0, stream>>>(spec.st, spec.partials, spec.A.n_pad);
+  cg_init_kernel<T, KB><<<spec.grid_stream, kThreads, 0, stream>>>(a[0]);
+  std::vector<cudaEvent_t> ev(2 * (size_t)iters + 1);
+  for (auto& e : ev) cudaEventCreate(&e);
+  cudaEventRecord(ev[0], stream);
+  for (int it = 0; it < iters; ++it) {
+    launch_a<T>(step_a_fn<T, KB>(spec.var_a), spec.grid_spmv, step_a_block(spec), stream, a[it & 1], smem_a);
+    cudaEventRecord(ev[2 * it + 1], stream);
+    cg_step_b_kernel<T, KB><<<spec.grid_stream_b, kThreads, 0, stream>>>(a[it & 1]);
+    cudaEventRecord(ev[2 * it + 2], stream);
+  }
+  cudaError_t e = cudaStreamSynchronize(stream);
+  // medians over the iterations (robust against a stray slow launch)
+  std::vector<float> ta(iters, 0.f), tb(iters, 0.f);
+  for (int it = 0; it < iters && e == cudaSuccess; ++it) {
+    cudaEventElapsedTime(&ta[it], ev[2 * it], ev[2 * it + 1]);
+    cudaEventElapsedTime(&tb[it], ev[2 * it + 1], ev[2 * it + 2]);
+  }
+  for (auto& ee : ev) cudaEventDestroy(ee);
+  std::sort(ta.begin(), ta.end());
+  std::sort(tb.begin(), tb.end());
+  ms[0] = iters > 0 ? ta[iters / 2] : 0.0;
+  ms[1] = iters > 0 ? tb[iters / 2] : 0.0;
+  if (e == cudaSuccess) e = cudaGetLastError();
+  return e;
+}
+
+template <typename T, int KB>
+void occupancy_t(const InnerGraphSpec& spec, int* a_blocks, int* b_blocks) {
+  const unsigned smem = step_a_smem<T, KB>(spec);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(a_blocks, step_a_fn<T, KB>(spec.var_a), step_a_block(spec), smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(b_blocks, (const void*)cg_step_b_kernel<T, KB>, kThreads, 0);
+}
+
+// dispatch on the k bucket of the kernels (one precision per translation unit)
+template <typename T, template <typename, int> class F, typename... Args>
+cudaError_t dispatch_k(const InnerGraphSpec& spec, Args... args) {
+  if (spec.k == 0) return F<T, 0>::run(spec, args...);
+  if (spec.k <= 8) return F<T, 8>::run(spec, args...);
+  if (spec.k <= 12) return F<T, 12>::run(spec, args...);
+  if (spec.k <= 16) return F<T, 16>::run(spec, args...);
+  if (spec.k <= 24) return F<T, 24>::run(spec, args...);
+  return F<T, 32>::run(spec, args...);
+}
+
+template <typename T, int KB>
+struct BuildF {
+  static cudaError_t run(const InnerGraphSpec& s, cudaGraph_t* g) { return build_graph_t<T, KB>(s, g); }
+};
+template <typename T, int KB>
+struct HostF {
+  static cudaError_t run(const InnerGraphSpec& s, cudaStream_t st, int* d) { return run_host_t<T, KB>(s, st, d); }
+};
+template <typename T, int KB>
+struct TimeF {
+  static cudaError_t run(const InnerGraphSpec& s, int it, cudaStream_t st, double* v, int64_t n, double* ms) {
+    return time_t<T, KB>(s, it, st, v, n, ms);
+  }
+};
+template <typename T, int KB>
+struct OccF {
+  static cudaError_t run(const InnerGraphSpec& s, int* a, int* b) {
+    occupancy_t<T, KB>(s, a, b);
+    return cudaSuccess;
+  }
+};
+
+template <typename T>
+cudaError_t launch_gram_t(const InnerGraphSpec& spec, cudaStream_t stream, double* gram) {
+  if (spec.k <= 0) return cudaSuccess;
+  const int pairs = spec.k * (spec.k + 1) / 2;
+  cg_gram_kernel<T><<<pairs, kThreads, 0, stream>>>(reinterpret_cast<const T*>(spec.V),
+                                                     reinterpret_cast<const T*>(spec.dinv), spec.A.n_pad, spec.k, gram);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// the entry points of one precision, defined by cg_f32.cu and cg_f64.cu
+#define MRCG_CG_PRECISION_ENTRY_POINTS(T, SUFFIX)                                                                \
+  cudaError_t build_inner_graph_##SUFFIX(const InnerGraphSpec& spec, cudaGraph_t* graph) {                      \
+    return dispatch_k<T, BuildF>(spec, graph);                                                                   \
+  }                                                                                                              \
+  cudaError_t run_inner_host_##SUFFIX(const InnerGraphSpec& spec, cudaStream_t stream, int* h_done) {           \
+    return dispatch_k<T, HostF>(spec, stream, h_done);                                                           \
+  }                                                                                                              \
+  cudaError_t time_inner_kernels_##SUFFIX(const InnerGraphSpec& spec, int iters, cudaStream_t stream,           \
+                                          double* vin, int64_t n, double* ms) {                                  \
+    return dispatch_k<T, TimeF>(spec, iters, stream, vin, n, ms);                                                \
+  }                                                                                                              \
+  cudaError_t launch_gram_##SUFFIX(const InnerGraphSpec& spec, cudaStream_t stream, double* gram) {             \
+    return launch_gram_t<T>(spec, stream, gram);                                                                 \
+  }                                                                                                              \
+  void inner_occupancy_##SUFFIX(const InnerGraphSpec& spec, int* a, int* b) { dispatch_k<T, OccF>(spec, a, b); }
+
+}  // namespace mrcg

@@ -29,7 +29,7 @@ struct InnerGraphSpec {
   int var_a = 0;   // step-a kernel variant (0: early V loads, 1: late V loads, 2: two slices per warp,
                  // 3 / 4: late V loads with registers capped for 6 / 8 blocks per SM,
                  // 5 / 6: operands staged in shared memory by bulk copies, registers capped for
-                 // 2 / 4 blocks per SM)
+                 // 2 / 4 blocks per SM; 7: as 5 with the gathers issued one tile ahead)
   int64_t tile_entries = 0;  // most SELL entries in one tile of 8 slices (sizes the staged variant's buffers)
   int stages = 3;            // staged variant: shared-memory stages per block
 };

@@ -11,9 +11,9 @@ the FP64 oracle CG on the same inputs:
     oracle in FP64, meets the inner tolerance (1e-4: FP32 arithmetic bounds
     how far the true residual can follow the recursive one).
 
-Variants 5 and 6 (the same kernel with registers capped for 2 and 4 blocks
-per SM) stage every streamed operand in shared memory by bulk copies; they
-are run with 2, 3 and 4 stages (a shape whose stages do not fit in a block
+Variants 5, 6 and 7 (one kernel: registers capped for 2 or 4 blocks per SM;
+7 issues each warp's gathers one tile ahead) stage every streamed operand in
+shared memory by bulk copies; they are run with 2, 3 and 4 stages (a shape whose stages do not fit in a block
 falls back to variant 0, which the fallback test checks), with 16-bit and 32-bit column indices, with
 Jacobi M_cg, on ragged last tiles and on rows far longer than the stencil's.
 """
@@ -33,8 +33,10 @@ import paper_1805_12417_gb300 as m  # noqa: E402
 
 DEV = torch.device("cuda:0")
 
-SHAPES = [(0, None), (1, None), (2, None), (3, None), (4, None), (5, 2), (5, 3), (5, 4), (6, 2), (6, 3)]
-SHAPE_IDS = ["v0", "v1", "v2", "v3", "v4", "staged2", "staged3", "staged4", "staged4bpsm_2", "staged4bpsm_3"]
+SHAPES = [(0, None), (1, None), (2, None), (3, None), (4, None), (5, 2), (5, 3), (5, 4), (6, 2), (6, 3), (7, 2),
+          (7, 3)]
+SHAPE_IDS = ["v0", "v1", "v2", "v3", "v4", "staged2", "staged3", "staged4", "staged4bpsm_2", "staged4bpsm_3",
+             "pipelined2", "pipelined3"]
 
 
 @pytest.fixture
@@ -89,8 +91,9 @@ def test_inner_variants_small_3d(shape_env, var, stages, prec, mcg):
     _inner_vs_oracle(small_3d(), prec, mcg, 1e-6 if prec == m.FP64 else 1e-4, 4, var, stages, idx_bytes=2)
 
 
-@pytest.mark.parametrize("k", [0, 1, 9, 17, 32])
-@pytest.mark.parametrize("var,stages", [(1, None), (3, None), (5, 2), (6, 2)], ids=["v1", "v3", "staged2", "staged4bpsm"])
+@pytest.mark.parametrize("k", [0, 1, 10, 13, 17, 32])
+@pytest.mark.parametrize("var,stages", [(1, None), (3, None), (5, 2), (6, 2), (7, 2)],
+                         ids=["v1", "v3", "staged2", "staged4bpsm", "pipelined2"])
 def test_inner_variants_k_buckets(shape_env, k, var, stages):
     """Every k bucket of the kernels (FP64 stages of k = 32 hold 86 KB, so two fit a block)."""
     p = shifted_laplacian_problem("t", (13, 11, 9), max(k, 1), seed=k) if k else None
@@ -117,9 +120,10 @@ def test_staged_long_rows(shape_env, idx16, prec, stages):
     rng = np.random.default_rng(22)
     V, _ = np.linalg.qr(rng.standard_normal((n, 6)))
     lam = -rng.uniform(0.5, 3.0, 6)
-    shape_env(5, stages, idx16=idx16)
-    _inner_vs_oracle(None, prec, m.MCG_JACOBI, 1e-7 if prec == m.FP64 else 1e-4, 23, 5, stages,
-                     idx_bytes=2 if idx16 else 4, V=V, lam=lam, sysargs=(rp, ci, va))
+    for var in (5, 7):
+        shape_env(var, stages, idx16=idx16)
+        _inner_vs_oracle(None, prec, m.MCG_JACOBI, 1e-7 if prec == m.FP64 else 1e-4, 23, var, stages,
+                         idx_bytes=2 if idx16 else 4, V=V, lam=lam, sysargs=(rp, ci, va))
 
 
 def test_staged_falls_back_when_stages_do_not_fit(shape_env):
@@ -139,7 +143,8 @@ def test_staged_falls_back_when_stages_do_not_fit(shape_env):
     assert st == m.OK and it > 0
 
 
-@pytest.mark.parametrize("var,stages", [(0, None), (5, 3), (6, 2)], ids=["v0", "staged3", "staged4bpsm"])
+@pytest.mark.parametrize("var,stages", [(0, None), (5, 3), (6, 2), (7, 3)],
+                         ids=["v0", "staged3", "staged4bpsm", "pipelined3"])
 def test_variants_full_solve_small(shape_env, var, stages):
     """A whole MINRES-CG solve on every step-a path agrees with the oracle's."""
     shape_env(var, stages)
