@@ -138,6 +138,43 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
 
 
+KERNEL_SOURCES = ["paper_1805_12417_gb300/csrc/cg_impl.cuh", "paper_1805_12417_gb300/csrc/common.cuh"]
+TRAFFIC_NOTE = "profiles/cg_step_a_lap3d_128.md"
+
+
+def step_a_kernel_name(cfg, prec="float"):
+    """Name of the step-a kernel a launch configuration runs, as ncu prints it."""
+    var, kb = cfg["step_a_variant"], cfg["k_bucket"]
+    if var >= 5:
+        mb, pipe = {5: (2, 0), 6: (4, 0), 7: (2, 1)}[var]
+        return f"cg_step_a_staged_kernel<{prec}, {kb}, {mb}, {pipe}>"
+    return f"cg_step_a_kernel<{prec}, {kb}, {var}>"
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, TRAFFIC_NOTE)
+    if not os.path.exists(path):
+        return None
+    want = kernel_source_hash()
+    for line in open(path):
+        if line.startswith("traffic_per_launch:"):
+            kv = dict(x.strip().split("=", 1) for x in line.split(":", 1)[1].strip().split(";") if "=" in x)
+            if kv.get("kernel") == kernel and kv.get("source_sha256") == want:
+                return int(kv["bytes"])
+    return None
+
+
 def measured_peak_gbs():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -473,8 +510,9 @@ def main():
 
     peak, peak_kind = measured_peak_gbs()
     ach_a = bytes_a(4) / (ta_mx * 1e-3) / 1e9
-    roof = {"kernel": f"cg_step_a_kernel<float,{0 if k == 0 else 8 if k <= 8 else 16 if k <= 16 else 32}>", "bound": "hbm", "achieved": round(ach_a, 1), "peak": peak,
-            "unit": "GB/s", "frac": round(ach_a / peak, 4), "traffic": None,
+    kname = step_a_kernel_name(m.launch_config(solvers[m.MIXED_FP32].h))
+    roof = {"kernel": kname, "bound": "hbm", "achieved": round(ach_a, 1), "peak": peak,
+            "unit": "GB/s", "frac": round(ach_a / peak, 4), "traffic": recorded_traffic(kname),
             "peak_kind": f"{peak_kind} copy bandwidth (burst: kernel timed alone)",
             "bytes_per_launch": bytes_a(4), "avg_ms": round(ta_mx, 5)}
 

@@ -136,7 +136,7 @@ mrcg_status mrcg_inner_solve(mrcg_handle h, const double* y, double* z, double i
  *          partials r^T s, r^T r.
  * Each is launched `iters` times (1 <= iters <= 4096) on the handle's stream,
  * outside the solver's graph, on a fixed synthetic right-hand side, and
- * bracketed by CUDA events; ms receives the median duration in
+ * bracketed by CUDA events; ms receives the average duration in
  * milliseconds.  Overwrites the handle's work vectors (not its matrix). */
 mrcg_status mrcg_time_inner_kernels(mrcg_handle h, int32_t iters, double* ms);
 

@@ -233,7 +233,7 @@ def launch_config(h):
 
 
 def time_inner_kernels(h, iters=20):
-    """mrcg_time_inner_kernels: median ms of (step a, step b) of one inner CG iteration."""
+    """mrcg_time_inner_kernels: average ms of (step a, step b) of one inner CG iteration."""
     ms = np.zeros(2)
     st = lib().mrcg_time_inner_kernels(h, int(iters), ms.ctypes.data)
     if st != OK:

@@ -1112,17 +1112,23 @@ cudaError_t time_t(const InnerGraphSpec& spec, int iters, cudaStream_t stream, d
     cudaEventRecord(ev[2 * it + 2], stream);
   }
   cudaError_t e = cudaStreamSynchronize(stream);
-  // medians over the iterations (robust against a stray slow launch)
+  // ms[0], ms[1]: medians over the iterations (robust against a stray slow
+  // launch; the autotuner's measure); ms[2], ms[3]: means
   std::vector<float> ta(iters, 0.f), tb(iters, 0.f);
+  double sa = 0.0, sb = 0.0;
   for (int it = 0; it < iters && e == cudaSuccess; ++it) {
     cudaEventElapsedTime(&ta[it], ev[2 * it], ev[2 * it + 1]);
     cudaEventElapsedTime(&tb[it], ev[2 * it + 1], ev[2 * it + 2]);
+    sa += ta[it];
+    sb += tb[it];
   }
   for (auto& ee : ev) cudaEventDestroy(ee);
   std::sort(ta.begin(), ta.end());
   std::sort(tb.begin(), tb.end());
   ms[0] = iters > 0 ? ta[iters / 2] : 0.0;
   ms[1] = iters > 0 ? tb[iters / 2] : 0.0;
+  ms[2] = iters > 0 ? sa / iters : 0.0;
+  ms[3] = iters > 0 ? sb / iters : 0.0;
   if (e == cudaSuccess) e = cudaGetLastError();
   return e;
 }

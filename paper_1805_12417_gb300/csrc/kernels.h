@@ -37,7 +37,8 @@ struct InnerGraphSpec {
 cudaError_t build_inner_graph(const InnerGraphSpec& spec, cudaGraph_t* graph);
 // the same inner solve with the loop driven from the host (profiling mode)
 cudaError_t run_inner_host(const InnerGraphSpec& spec, cudaStream_t stream, int* h_done);
-// standalone launches of the two CG iteration kernels, timed with events
+// standalone launches of the two CG iteration kernels, timed with events:
+// ms[0..1] median ms of step a, step b; ms[2..3] their means
 cudaError_t time_inner_kernels(const InnerGraphSpec& spec, int iters, cudaStream_t stream, double* vin, int64_t n,
                                double* ms);
 // dynamic shared memory of the staged step a for this spec (0 when it does not fit in a block)

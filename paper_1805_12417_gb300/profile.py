@@ -8,7 +8,8 @@ run before them (setup only), which keeps an ncu capture of them small:
   python -m paper_1805_12417_gb300.profile --workload lap3d_128 --precision mixed --iters 3
 
 A profiler slows every launch, which misleads the launch-shape autotuner that
-runs at solver creation; `--var-a / --bpsm-a / --bpsm-b` fix the shape instead
+runs at solver creation; `--var-a / --bpsm-a / --bpsm-b` (or MRCG_SHAPE_F32 /
+MRCG_SHAPE_F64) fix the shape instead
 (the values a normal run reports through mrcg_launch_config).
 """
 from __future__ import annotations
@@ -33,7 +34,7 @@ def main(argv=None):
     ap.add_argument("--workload", default="lap3d_128", choices=["lap3d_128", "lap2d_64", "lap3d_small"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--iters", type=int, default=3)
-    ap.add_argument("--var-a", type=int, default=None, help="step-a kernel variant (0-4)")
+    ap.add_argument("--var-a", type=int, default=None, help="step-a kernel variant (0-7)")
     ap.add_argument("--bpsm-a", type=int, default=None, help="step-a blocks per SM")
     ap.add_argument("--bpsm-b", type=int, default=None, help="step-b blocks per SM")
     a = ap.parse_args(argv)
