@@ -128,7 +128,7 @@ static __global__ void __launch_bounds__(kThreads) cg_vnorm_kernel(DevState* st,
     acc[0] += x * x;
   }
   block_partials<1>(acc, 1, partials);
-  if (last_block(&st->ticket)) {
+  if (last_block_after_partials(&st->ticket)) {
     __shared__ double tot[1];
     final_sums(partials, 1, tot);
     if (threadIdx.x == 0) S.vnorm = sqrt(tot[0]);
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(kThreads) cg_init_kernel(CgArgs<T> a) {
   pack_slots<T, KB>(acc, rs, u, rr, a.k, jac);
   const int nv = a.k + 1 + (jac ? 1 : 0);
   block_partials_t<T, KB + 2>(acc, nv, a.partials);
-  if (last_block(&a.st->ticket)) {
+  if (last_block_after_partials(&a.st->ticket)) {
     __shared__ double tot[KB + 2];
     final_sums(a.partials, nv, tot);
     if (threadIdx.x == 0) {
@@ -293,7 +293,7 @@ __device__ __forceinline__ void step_a_reduce(const CgArgs<T>& a, CgState& S, T 
 #pragma unroll
   for (int l = 0; l < KB; ++l) part[l + 1] = wq[l];
   block_partials_t<T, KB + 1, NW>(part, a.k + 1, a.partials);
-  if (last_block(&a.st->ticket)) {
+  if (last_block_after_partials(&a.st->ticket)) {
     constexpr int KK = KS * KS;
     constexpr int NT = NW * 32;
     constexpr int GPT = (KK + NT - 1) / NT;
@@ -794,40 +794,56 @@ __global__ void __launch_bounds__(kThreads) cg_step_b_kernel(CgArgs<T> a) {
   const bool jac = a.dinv != nullptr;
   T rs = 0, rr = 0;
   const int64_t nvec = a.n_pad / W;
-  for (int64_t iv = blockIdx.x * (int64_t)kThreads + threadIdx.x; iv < nvec; iv += (int64_t)gridDim.x * kThreads) {
-    const int64_t i = iv * W;
-    T pn[W], qv[W], zv[W], rv[W], s[W];
-    ld16(a.p_new + i, pn);
-    ld16(a.q + i, qv);
-    ld16(a.z + i, zv);
-    ld16(a.r + i, rv);
+  const int64_t stride = (int64_t)gridDim.x * kThreads;
+  // U grid-stride chunks per trip, all their loads issued before any use
+  // (the kernel is latency-bound: more bytes in flight per thread)
+  constexpr int U = 4;
+  for (int64_t iv0 = blockIdx.x * (int64_t)kThreads + threadIdx.x; iv0 < nvec; iv0 += stride * U) {
+    T pn[U][W], qv[U][W], zv[U][W], rv[U][W], d[U][W];
 #pragma unroll
-    for (int e = 0; e < W; ++e) {
-      zv[e] += alpha * pn[e];
-      rv[e] -= alpha * qv[e];
+    for (int u = 0; u < U; ++u) {
+      const int64_t iv = iv0 + u * stride;
+      if (iv < nvec) {
+        const int64_t i = iv * W;
+        ld16(a.p_new + i, pn[u]);
+        ld16(a.q + i, qv[u]);
+        ld16(a.z + i, zv[u]);
+        ld16(a.r + i, rv[u]);
+        if (jac) ld16(a.dinv + i, d[u]);
+      }
     }
-    st16(a.z + i, zv);
-    st16(a.r + i, rv);
-    if (jac) {
-      T d[W];
-      ld16(a.dinv + i, d);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t iv = iv0 + u * stride;
+      if (iv >= nvec) continue;
+      const int64_t i = iv * W;
+      T s[W];
 #pragma unroll
       for (int e = 0; e < W; ++e) {
-        s[e] = d[e] * rv[e];
-        rr += rv[e] * rv[e];
+        zv[u][e] += alpha * pn[u][e];
+        rv[u][e] -= alpha * qv[u][e];
       }
-      st16(a.s + i, s);
-    } else {
+      st16(a.z + i, zv[u]);
+      st16(a.r + i, rv[u]);
+      if (jac) {
 #pragma unroll
-      for (int e = 0; e < W; ++e) s[e] = rv[e];
+        for (int e = 0; e < W; ++e) {
+          s[e] = d[u][e] * rv[u][e];
+          rr += rv[u][e] * rv[u][e];
+        }
+        st16(a.s + i, s);
+      } else {
+#pragma unroll
+        for (int e = 0; e < W; ++e) s[e] = rv[u][e];
+      }
+#pragma unroll
+      for (int e = 0; e < W; ++e) rs += rv[u][e] * s[e];
     }
-#pragma unroll
-    for (int e = 0; e < W; ++e) rs += rv[e] * s[e];
   }
   T acc[2] = {rs, rr};
   const int nv = jac ? 2 : 1;
   block_partials_t<T, 2>(acc, nv, a.partials);
-  if (last_block(&a.st->ticket)) {
+  if (last_block_after_partials(&a.st->ticket)) {
     __shared__ double tot[2];
     final_sums(a.partials, nv, tot);
     if (threadIdx.x == 0) {

@@ -113,6 +113,7 @@ __device__ __forceinline__ void block_partials_t(T (&v)[NV], int nv, double* par
 #pragma unroll
     for (int w = 0; w < NW; ++w) s += smt[w][threadIdx.x];
     partials[threadIdx.x * gridDim.x + blockIdx.x] = (double)s;
+    __threadfence();  // the partial is visible before this block draws its ticket
   }
 }
 
@@ -136,6 +137,7 @@ __device__ __forceinline__ void block_partials(double (&v)[NV], int nv, double* 
 #pragma unroll
     for (int w = 0; w < kThreads / 32; ++w) s += sm[w][threadIdx.x];
     partials[threadIdx.x * gridDim.x + blockIdx.x] = s;
+    __threadfence();  // the partial is visible before this block draws its ticket
   }
 }
 
@@ -159,6 +161,22 @@ __device__ __forceinline__ double lane_sum8(const double* x, int count, int lane
 __device__ __forceinline__ bool last_block(unsigned int* ticket) {
   __shared__ bool is_last;
   __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int prev = atomicAdd(ticket, 1u);
+    is_last = (prev == gridDim.x - 1);
+    if (is_last) *ticket = 0u;
+  }
+  __syncthreads();
+  if (is_last) __threadfence();
+  return is_last;
+}
+
+// The same for kernels whose partials come from block_partials / block_partials_t
+// (their writers fence their own partials): the other threads skip the fence,
+// which would make them wait for all of their vector stores to complete.
+__device__ __forceinline__ bool last_block_after_partials(unsigned int* ticket) {
+  __shared__ bool is_last;
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned int prev = atomicAdd(ticket, 1u);
