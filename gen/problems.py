@@ -156,8 +156,13 @@ def shift_for_negatives(dims, k_wanted: int, rel_tie: float = 1e-10):
         return 0.5 * (lk + lk1), k, ev[: k + 1]
 
 
-def shifted_laplacian_problem(name, dims, k_wanted, seed, xstar=None) -> Problem:
+def shifted_laplacian_problem(name, dims, k_wanted, seed, xstar=None, sigma_frac=0.5) -> Problem:
+    """A = L - sigma I with sigma between eigenvalues k and k+1 of L: midway by
+    default; sigma_frac < 0.5 puts it closer to lambda_k (negative eigenvalues
+    of A closer to zero than the positive ones)."""
     sigma, k, ev = shift_for_negatives(dims, k_wanted)
+    if sigma_frac != 0.5:
+        sigma = ev[k - 1][0] + sigma_frac * (ev[k][0] - ev[k - 1][0])
     rowptr, colind, val = laplacian_csr(dims, sigma)
     n = int(np.prod(dims))
     modes = [m for _, m in ev[:k]]

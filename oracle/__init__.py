@@ -21,7 +21,7 @@ _HDR = os.path.join(_HERE, "mrcg_oracle.h")
 _OUT = os.path.join(_HERE, "_build", "liboracle.so")
 
 OK, ERR_INVALID, ERR_NOT_SPD, ERR_BREAKDOWN, ERR_MAXITER, ERR_NONFINITE = range(6)
-MCG_IDENTITY, MCG_JACOBI = 0, 1
+MCG_IDENTITY, MCG_JACOBI, MCG_SMW = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "NOT_SPD", 3: "BREAKDOWN", 4: "MAXITER", 5: "NONFINITE"}
 
 
@@ -61,6 +61,8 @@ def lib():
         _lib.orc_csr_spmv.argtypes = [C.POINTER(_System), P, P]
         _lib.orc_mmr_apply.argtypes = [C.POINTER(_System), P, P, P, C.POINTER(C.c_int64)]
         _lib.orc_mmr_diag.argtypes = [C.POINTER(_System), P]
+        _lib.orc_mcg_apply.argtypes = [C.POINTER(_System), C.c_int, P, P, P]
+        _lib.orc_mcg_apply.restype = C.c_int
         _lib.orc_cg.argtypes = [C.POINTER(_System), C.c_int, P, P, C.c_double, C.c_int64,
                                 C.POINTER(C.c_int64), P]
         _lib.orc_cg.restype = C.c_int
@@ -125,6 +127,12 @@ class System:
         d = np.empty(self.n)
         lib().orc_mmr_diag(self.ptr, d.ctypes.data)
         return d
+
+    def mcg_apply(self, r, mcg):
+        """M_cg^{-1} r (identity, Jacobi on M_mr, or the MINRES-CG* form).  Returns (out, status)."""
+        r = _f64(r); out = np.empty(self.n); work = np.empty(self.n + self.k + 1)
+        st = lib().orc_mcg_apply(self.ptr, mcg, r.ctypes.data, out.ctypes.data, work.ctypes.data)
+        return out, st
 
     def cg(self, y, tol, maxit, mcg=MCG_IDENTITY):
         """Inner CG on M_mr z = y.  Returns (z, iters, status)."""

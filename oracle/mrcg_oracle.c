@@ -56,8 +56,59 @@ void orc_mmr_diag(const orc_system* s, double* d) {
   }
 }
 
+/* Sec. 2.1 (MINRES-CG*): the inner CG's preconditioner taken from the
+ * Sherman-Morrison-Woodbury form of M_mr^{-1}, with the action of A^{-1}
+ * approximated:  M_cg^{-1} r = Atilde^{-1} r - 2 V (Lambda^{-1} (V^T r)).
+ * Here Atilde = diag(A).  Steps in the formula's order: t = V^T r;
+ * t <- -2 Lambda^{-1} t; out = diag(A)^{-1} r + V t.  dainv holds 1/diag(A). */
+static void smw_apply(const orc_system* s, const double* dainv, const double* r, double* out, double* t) {
+  const int64_t n = s->n;
+  for (int32_t j = 0; j < s->k; ++j) t[j] = dot(n, s->V + (int64_t)j * n, r);
+  for (int32_t j = 0; j < s->k; ++j) t[j] = -2.0 * t[j] / s->lam[j];
+  for (int64_t i = 0; i < n; ++i) {
+    double acc = dainv[i] * r[i];
+    for (int32_t j = 0; j < s->k; ++j) acc += s->V[(int64_t)j * n + i] * t[j];
+    out[i] = acc;
+  }
+}
+
+/* 1 / diag(A); ORC_ERR_INVALID when a diagonal entry is zero or not finite
+ * (Atilde = diag(A) must be invertible).  Sec. 2.1 notes that with an
+ * approximate Atilde the preconditioner need not be positive definite; it is
+ * positive definite whenever diag(A) > 0. */
+static int diag_a_inverse(const orc_system* s, double* dainv) {
+  for (int64_t i = 0; i < s->n; ++i) {
+    double a = 0.0;
+    for (int64_t p = s->rowptr[i]; p < s->rowptr[i + 1]; ++p)
+      if (s->colind[p] == i) a += s->val[p];
+    if (a == 0.0 || !isfinite(a)) return ORC_ERR_INVALID;
+    dainv[i] = 1.0 / a;
+  }
+  return ORC_OK;
+}
+
+int orc_mcg_apply(const orc_system* s, int mcg, const double* r, double* out, double* work) {
+  const int64_t n = s->n;
+  double* d = work;
+  double* t = work + n;
+  if (mcg == ORC_MCG_SMW) {
+    const int rc = diag_a_inverse(s, d);
+    if (rc != ORC_OK) return rc;
+    smw_apply(s, d, r, out, t);
+    return ORC_OK;
+  }
+  if (mcg == ORC_MCG_JACOBI) {
+    orc_mmr_diag(s, d);
+    for (int64_t i = 0; i < n; ++i) out[i] = r[i] / d[i];
+    return ORC_OK;
+  }
+  for (int64_t i = 0; i < n; ++i) out[i] = r[i];
+  return ORC_OK;
+}
+
 /* Preconditioned CG (Hestenes-Stiefel) on the SPD system M_mr z = y, Eq. 2,
- * with M_cg = I or Jacobi.  Start z = 0, stop when ||r|| <= tol ||y||. */
+ * with M_cg = I, Jacobi, or the MINRES-CG* preconditioner of Sec. 2.1.
+ * Start z = 0, stop when ||r|| <= tol ||y||. */
 int orc_cg(const orc_system* s, int mcg, const double* y, double* z, double tol, int64_t maxit,
            int64_t* iters, double* work) {
   const int64_t n = s->n;
@@ -68,7 +119,10 @@ int orc_cg(const orc_system* s, int mcg, const double* y, double* z, double tol,
   double* dinv = work + 4 * n;
   double* t = work + 5 * n;
   *iters = 0;
-  if (mcg == ORC_MCG_JACOBI) {
+  if (mcg == ORC_MCG_SMW) {
+    const int rc = diag_a_inverse(s, dinv);
+    if (rc != ORC_OK) return rc;
+  } else if (mcg == ORC_MCG_JACOBI) {
     orc_mmr_diag(s, dinv);
     for (int64_t i = 0; i < n; ++i) dinv[i] = 1.0 / dinv[i];
   } else {
@@ -77,9 +131,13 @@ int orc_cg(const orc_system* s, int mcg, const double* y, double* z, double tol,
   for (int64_t i = 0; i < n; ++i) {
     z[i] = 0.0;
     r[i] = y[i];
-    sv[i] = dinv[i] * r[i];
-    p[i] = sv[i];
   }
+  if (mcg == ORC_MCG_SMW) {
+    smw_apply(s, dinv, r, sv, t);
+  } else {
+    for (int64_t i = 0; i < n; ++i) sv[i] = dinv[i] * r[i];
+  }
+  for (int64_t i = 0; i < n; ++i) p[i] = sv[i];
   const double ynorm = nrm2(n, y);
   if (!isfinite(ynorm)) return ORC_ERR_NONFINITE;
   if (ynorm == 0.0) return ORC_OK;
@@ -98,8 +156,14 @@ int orc_cg(const orc_system* s, int mcg, const double* y, double* z, double tol,
     const double rnorm = nrm2(n, r);
     if (!isfinite(rnorm)) return ORC_ERR_NONFINITE;
     if (rnorm <= tol * ynorm) return ORC_OK;
-    for (int64_t i = 0; i < n; ++i) sv[i] = dinv[i] * r[i];
+    if (mcg == ORC_MCG_SMW) {
+      smw_apply(s, dinv, r, sv, t);
+    } else {
+      for (int64_t i = 0; i < n; ++i) sv[i] = dinv[i] * r[i];
+    }
     const double rho_new = dot(n, r, sv);
+    if (!isfinite(rho_new)) return ORC_ERR_NONFINITE;
+    if (rho_new == 0.0) return ORC_ERR_BREAKDOWN; /* r^T M_cg^{-1} r = 0 with r != 0: indefinite M_cg */
     const double beta = rho_new / rho;
     rho = rho_new;
     for (int64_t i = 0; i < n; ++i) p[i] = sv[i] + beta * p[i];

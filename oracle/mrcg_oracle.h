@@ -26,8 +26,9 @@ enum {
   ORC_ERR_NONFINITE = 5
 };
 
-/* inner preconditioner M_cg: identity, or Jacobi with diag(M_mr) */
-enum { ORC_MCG_IDENTITY = 0, ORC_MCG_JACOBI = 1 };
+/* inner preconditioner M_cg: identity; Jacobi with diag(M_mr); or the
+ * MINRES-CG* preconditioner of Sec. 2.1, M_cg^{-1} = diag(A)^{-1} - 2 V Lambda^{-1} V^T */
+enum { ORC_MCG_IDENTITY = 0, ORC_MCG_JACOBI = 1, ORC_MCG_SMW = 2 };
 
 typedef struct {
   int64_t n;
@@ -51,11 +52,18 @@ void orc_mmr_apply(const orc_system* s, const double* u, double* out, double* wo
 /* diag(M_mr)_i = A_ii + 2 sum_j |lam_j| V_ij^2 */
 void orc_mmr_diag(const orc_system* s, double* d);
 
+/* out = M_cg^{-1} r for the preconditioner mcg selects.  work: n + k
+ * doubles.  ORC_ERR_INVALID for ORC_MCG_SMW when a diagonal entry of A is
+ * zero or not finite. */
+int orc_mcg_apply(const orc_system* s, int mcg, const double* r, double* out, double* work);
+
 /* Inner CG on M_mr z = y (Eq. 2; Alg. 1 inner block), x0 = 0, stopping on
  * the recursive residual ||r|| <= tol ||y||.  mcg selects M_cg.
  * iters: number of M_mr products done.  work: 5n + k doubles.
- * Returns ORC_OK, ORC_ERR_NOT_SPD (p^T M p <= 0), ORC_ERR_NONFINITE or
- * ORC_ERR_MAXITER (z holds the last iterate). */
+ * Returns ORC_OK, ORC_ERR_NOT_SPD (p^T M p <= 0), ORC_ERR_NONFINITE,
+ * ORC_ERR_INVALID (ORC_MCG_SMW with a zero diagonal entry of A),
+ * ORC_ERR_BREAKDOWN (r^T M_cg^{-1} r = 0 before convergence, possible only
+ * with an indefinite M_cg) or ORC_ERR_MAXITER (z holds the last iterate). */
 int orc_cg(const orc_system* s, int mcg, const double* y, double* z, double tol, int64_t maxit,
            int64_t* iters, double* work);
 

@@ -176,6 +176,95 @@ def test_cg_zero_rhs():
     assert st == O.OK and it == 0 and not z.any()
 
 
+# ---------------------------------------------------------------- MINRES-CG* inner preconditioner (Sec. 2.1)
+
+def test_smw_prec_is_exact_inverse_when_A_is_diagonal():
+    """With A diagonal, Atilde = diag(A) = A is exact, so the Sec. 2.1 form
+    diag(A)^{-1} - 2 V Lambda^{-1} V^T is M_mr^{-1} itself (= |A|^{-1}): it undoes
+    M_mr, and the preconditioned CG converges in one iteration."""
+    d = np.array([3.0, -0.5, 2.0, -4.0, 1.5, 0.25, -1.0, 5.0])
+    neg = np.where(d < 0)[0]
+    V = np.eye(len(d))[:, neg]
+    rp, ci, va = dense_to_csr(np.diag(d))
+    s = O.System(rp, ci, va, V, d[neg])
+    u = np.random.default_rng(3).standard_normal(len(d))
+    out, st = s.mcg_apply(s.mmr_apply(u), O.MCG_SMW)
+    assert st == O.OK and np.allclose(out, u, rtol=0, atol=1e-14)
+    z, it, st = s.cg(u, 1e-13, 10, O.MCG_SMW)
+    assert st == O.OK and it == 1
+    assert np.allclose(z, u / np.abs(d), rtol=0, atol=1e-14)
+
+
+def test_smw_prec_spectrum_on_shifted_laplacian():
+    """Exact V_hat and a constant diagonal c = 2d - sigma: on V the product
+    M_cg^{-1} M_mr acts as (1/c - 2/lambda_j)|lambda_j| = |lambda_j|/c + 2, on the
+    rest of the spectrum as lambda_i/c."""
+    p = shifted_laplacian_problem("t", (7, 6), 4, seed=0)
+    s = O.System.from_problem(p)
+    M = dense_op(s.mmr_apply, p.n)
+    P = dense_op(lambda r: s.mcg_apply(r, O.MCG_SMW)[0], p.n)
+    c = 4.0 - p.sigma
+    lamA = np.linalg.eigvalsh(p.dense())
+    want = np.sort(np.concatenate([np.abs(lamA[:p.k]) / c + 2.0, lamA[p.k:] / c]))
+    got = np.sort(np.linalg.eigvals(P @ M).real)
+    assert np.allclose(got, want, rtol=0, atol=1e-11)
+
+
+def test_smw_cg_iterates_are_galerkin():
+    """With the Sec. 2.1 preconditioner P, each CG iterate is the M_mr-energy best
+    approximation from K_m(P M_mr, P y)."""
+    p = shifted_laplacian_problem("t", (6, 5), 3, seed=2)
+    s = O.System.from_problem(p)
+    M = dense_op(s.mmr_apply, p.n)
+    P = dense_op(lambda r: s.mcg_apply(r, O.MCG_SMW)[0], p.n)
+    y = np.random.default_rng(5).standard_normal(p.n)
+    for m in range(1, 6):
+        z, it, st = s.cg(y, 1e-300, m, O.MCG_SMW)
+        assert it == m and st == O.ERR_MAXITER
+        vecs = [P @ y]
+        for _ in range(m - 1):
+            vecs.append(P @ (M @ vecs[-1]))
+        K, _ = np.linalg.qr(np.column_stack(vecs))
+        zg = K @ np.linalg.solve(K.T @ M @ K, K.T @ y)
+        assert np.allclose(z, zg, rtol=0, atol=1e-9 * np.linalg.norm(zg))
+
+
+def test_smw_cuts_inner_iterations_when_negative_eigenvalues_are_small():
+    """Sec. 2.1 / 4.3: the improvement pays off when the negative eigenvalues are
+    the ones closest to zero.  With sigma near lambda_k the plain inner CG slows
+    down while the MINRES-CG* inner CG does not."""
+    y = None
+    counts = {}
+    for frac in (0.5, 0.02):
+        p = shifted_laplacian_problem("t", (24, 20), 4, seed=0, sigma_frac=frac)
+        s = O.System.from_problem(p)
+        y = np.random.default_rng(0).standard_normal(p.n)
+        counts[frac] = [s.cg(y, 1e-6, 100000, mcg)[1] for mcg in (O.MCG_IDENTITY, O.MCG_SMW)]
+    assert counts[0.5][1] < counts[0.5][0]
+    assert counts[0.02][0] > 1.2 * counts[0.5][0]        # plain CG slows down
+    assert counts[0.02][1] <= counts[0.5][1] + 2          # MINRES-CG* does not
+    assert counts[0.02][1] < 0.7 * counts[0.02][0]
+
+
+def test_smw_rejects_zero_diagonal():
+    """A saddle-point row with a zero diagonal leaves diag(A) singular."""
+    A = np.array([[2.0, 1.0], [1.0, 0.0]])
+    rp, ci, va = dense_to_csr(A)
+    s = O.System(rp, ci, va)
+    out, st = s.mcg_apply(np.ones(2), O.MCG_SMW)
+    assert st == O.ERR_INVALID
+    z, it, st = s.cg(np.ones(2), 1e-8, 10, O.MCG_SMW)
+    assert st == O.ERR_INVALID
+
+
+def test_minres_cg_star_dense_solution():
+    """MINRES-CG* (Alg. 1 with the Sec. 2.1 inner preconditioner) solves A x = b."""
+    p = shifted_laplacian_problem("t", (9, 8), 4, seed=6, sigma_frac=0.1)
+    r = O.minres_cg(O.System.from_problem(p), p.b, outer_tol=1e-12, inner_tol=1e-3, mcg=O.MCG_SMW)
+    assert r.status == O.OK
+    assert np.allclose(r.x, np.linalg.solve(p.dense(), p.b), rtol=0, atol=1e-8 * np.abs(p.xstar).max() * 10)
+
+
 # ---------------------------------------------------------------- outer MINRES
 
 def test_minres_identity_prec_matches_residual_norm():
