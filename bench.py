@@ -46,6 +46,9 @@ def parse():
                     help="lap3d_128: the headline single-system workload; batch64: 64 independent uneven "
                          "2D systems (sides 100..400, k_i 1..16, seed 3) solved as one batch; shifted64: 16 "
                          "shifts x 4 RHS of the 160^3 Laplacian as one right-hand-side block")
+    ap.add_argument("--mcg", choices=["identity", "jacobi", "smw"], default="identity",
+                    help="inner preconditioner of the single-system workloads: identity (default), Jacobi on "
+                         "M_mr, or smw, the MINRES-CG* form diag(A)^-1 - 2 V Lambda^-1 V^T (Sec. 2.1)")
     return ap.parse_args()
 
 
@@ -432,7 +435,9 @@ def main():
         p = config2()
     b_dev = torch.from_numpy(p.b).to(dev)
     x_dev = torch.zeros(p.n, dtype=torch.float64, device=dev)
-    solvers = {prec: m.Solver.from_problem(p, precision=prec, stream=stream.cuda_stream, validate=False)
+    mcg = {"identity": m.MCG_IDENTITY, "jacobi": m.MCG_JACOBI, "smw": m.MCG_SMW}[args.mcg]
+    solvers = {prec: m.Solver.from_problem(p, precision=prec, inner_prec=mcg, stream=stream.cuda_stream,
+                                           validate=False)
                for prec in (m.MIXED_FP32, m.FP64)}
 
     def run(prec, steps, warmup, clocks=False):
@@ -503,9 +508,13 @@ def main():
     ib = m.launch_config(solvers[m.MIXED_FP32].h)["index_bytes"]
 
     def bytes_a(w):  # A values + column indices, s and p_old read, V read, q and p_new written
-        return nnz * (w + ib) + 2 * n * w + k * n * w + 2 * n * w
+        return nnz * (w + ib) + 2 * n * w + k * n * w + 2 * n * w + (n * w if args.mcg == "jacobi" else 0)
 
     def bytes_b(w):  # p, q, z, r read; z, r written (V^T s by recurrence: no V pass)
+        if args.mcg == "jacobi":  # + M_cg^{-1} read, s written
+            return 8 * n * w
+        if args.mcg == "smw":  # + diag(A)^{-1} and V read, s written
+            return 8 * n * w + k * n * w
         return 6 * n * w
 
     peak, peak_kind = measured_peak_gbs()
@@ -534,7 +543,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_mx / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 inner CG + f64 outer MINRES", "data": "synthetic",
             "config": {"workload": workload, "n": n, "nnz": nnz, "k": k, "outer_tol": OUTER_TOL,
-                       "inner_tol": INNER_TOL, "precision": "mixed: FP32 inner CG, FP64 outer MINRES",
+                       "inner_tol": INNER_TOL, "inner_prec": args.mcg, "precision": "mixed: FP32 inner CG, FP64 outer MINRES",
                        "l2": f"inputs larger than L2 (FP32 A {nnz * 8 / 1e6:.0f} MB + V {k * n * 4 / 1e6:.0f} MB "
                              "+ vectors per inner iteration)",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},

@@ -39,7 +39,8 @@ typedef enum {
   MRCG_OK = 0,
   MRCG_ERR_INVALID = 1,    /* malformed arguments or inputs */
   MRCG_ERR_NOT_SPD = 2,    /* inner CG met p^T M_mr p <= 0: M_mr is not SPD */
-  MRCG_ERR_BREAKDOWN = 3,  /* MINRES Lanczos/Givens breakdown */
+  MRCG_ERR_BREAKDOWN = 3,  /* MINRES Lanczos/Givens breakdown, or r^T M_cg^{-1} r = 0 in the
+                              inner CG (possible only with MRCG_MCG_SMW, whose M_cg may be indefinite) */
   MRCG_ERR_MAXITER = 4,    /* iteration budget exhausted; x = last iterate */
   MRCG_ERR_NONFINITE = 5,  /* NaN/Inf met in the data or the recurrences */
   MRCG_ERR_CUDA = 6,       /* a CUDA runtime call failed */
@@ -56,7 +57,13 @@ typedef enum {
 /* Inner preconditioner M_cg of Algorithm 1 ("solve M_cg t = g"). */
 typedef enum {
   MRCG_MCG_IDENTITY = 0, /* M_cg = I */
-  MRCG_MCG_JACOBI = 1    /* M_cg = diag(M_mr) */
+  MRCG_MCG_JACOBI = 1,   /* M_cg = diag(M_mr) */
+  MRCG_MCG_SMW = 2       /* MINRES-CG* (Sec. 2.1): M_cg^{-1} = Atilde^{-1} - 2 V_hat Lambda_hat^{-1} V_hat^T,
+                            the Sherman-Morrison-Woodbury form of M_mr^{-1} with A^{-1} approximated by
+                            Atilde^{-1} = diag(A)^{-1}.  Needs a nonzero diagonal in every row of A
+                            (else MRCG_ERR_INVALID at create); positive definite when diag(A) > 0.
+                            Costs one more pass over V_hat per inner iteration.  Single systems only
+                            (mrcg_batch_create and mrcg_shifted_create reject it). */
 } mrcg_inner_prec;
 
 typedef struct {

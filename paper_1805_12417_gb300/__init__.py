@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libmrcg.so")
 
 OK, ERR_INVALID, ERR_NOT_SPD, ERR_BREAKDOWN, ERR_MAXITER, ERR_NONFINITE, ERR_CUDA, ERR_OOM = range(8)
 FP64, MIXED_FP32 = 0, 1
-MCG_IDENTITY, MCG_JACOBI = 0, 1
+MCG_IDENTITY, MCG_JACOBI, MCG_SMW = 0, 1, 2
 
 
 class CreateArgs(C.Structure):

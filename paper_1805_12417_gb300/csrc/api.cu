@@ -40,6 +40,7 @@ struct mrcg_solver {
   double* d_V64 = nullptr;
   float* d_V32 = nullptr;
   void* d_dinv = nullptr;
+  void* d_dsmw = nullptr;    // MINRES-CG* M_cg: 1 / diag(A) in the inner precision
   double* d_gram = nullptr;  // k x k V^T M_cg^{-1} V of the inner kernels' V
   DevState* d_st = nullptr;
   DevState* h_st = nullptr;    // pinned mirror (read back)
@@ -251,6 +252,18 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
   for (double x : V)
     if (!std::isfinite(x)) return MRCG_ERR_NONFINITE;
   if (a->validate && a->k > 0) ST(validate_subspace(a, rp, ci, va, V, lam));
+  // MINRES-CG* M_cg: Atilde = diag(A) of Sec. 2.1, every diagonal entry nonzero
+  std::vector<double> dd;
+  if (h->mcg == MRCG_MCG_SMW) {
+    dd.assign((size_t)n_pad, 0.0);
+    for (int64_t i = 0; i < n; ++i) {
+      double d = 0.0;
+      for (int64_t p = rp[i]; p < rp[i + 1]; ++p)
+        if (ci[p] == i) d += va[p];
+      if (d == 0.0 || !std::isfinite(d)) return MRCG_ERR_INVALID;
+      dd[i] = 1.0 / d;
+    }
+  }
 
   // ---- SELL-32 layout
   std::vector<int64_t> sp((size_t)nslices + 1, 0);
@@ -322,7 +335,7 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
   const size_t esz = h->fp32 ? sizeof(float) : sizeof(double);
   void** inner[] = {&h->iz, &h->ir, &h->is, &h->ip0, &h->ip1, &h->iq};
   for (void** p : inner) {
-    if (p == &h->is && h->mcg != MRCG_MCG_JACOBI) continue;
+    if (p == &h->is && h->mcg == MRCG_MCG_IDENTITY) continue;
     char* q = nullptr;
     ST(dalloc(h, &q, (size_t)n_pad * esz));
     CK(cudaMemsetAsync(q, 0, (size_t)n_pad * esz, h->stream));
@@ -345,6 +358,18 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
     LK(launch_mmr_diag(h->stream, n, n_pad, t_rp, t_ci, t_va, h->d_V64, a->k, d_lam2, h->fp32, h->d_dinv));
     CK(cudaStreamSynchronize(h->stream));
     cudaFree(d_lam2);
+  }
+  if (h->mcg == MRCG_MCG_SMW) {
+    double* d64 = nullptr;
+    CK(cudaMalloc(&d64, dd.size() * sizeof(double)));
+    CK(cudaMemcpyAsync(d64, dd.data(), dd.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    char* q = nullptr;
+    ST(dalloc(h, &q, (size_t)n_pad * esz));
+    if (h->fp32) LK(launch_to_f32(h->stream, d64, reinterpret_cast<float*>(q), n_pad));
+    else CK(cudaMemcpyAsync(q, d64, dd.size() * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    cudaFree(d64);
+    h->d_dsmw = q;
   }
   CK(cudaStreamSynchronize(h->stream));
   cudaFree(t_rp);
@@ -383,6 +408,7 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
   g.V = h->fp32 ? (const void*)h->d_V32 : (const void*)h->d_V64;
   g.k = a->k;
   g.dinv = h->d_dinv;
+  g.dsmw = h->d_dsmw;
   if (a->k > 0) {
     ST(dalloc(h, &h->d_gram, (size_t)a->k * a->k));
     CK(launch_gram(g, h->stream, h->d_gram));
@@ -653,7 +679,8 @@ mrcg_status mrcg_solver_create(const mrcg_create_args* a, mrcg_handle* out) {
   *out = nullptr;
   if (a->n < 1 || a->n > (int64_t)0x7fffff00 || a->nnz < 0 || a->k < 0 || a->k > kMaxK) return MRCG_ERR_INVALID;
   if (a->precision != MRCG_FP64 && a->precision != MRCG_MIXED_FP32) return MRCG_ERR_INVALID;
-  if (a->inner_prec != MRCG_MCG_IDENTITY && a->inner_prec != MRCG_MCG_JACOBI) return MRCG_ERR_INVALID;
+  if (a->inner_prec != MRCG_MCG_IDENTITY && a->inner_prec != MRCG_MCG_JACOBI && a->inner_prec != MRCG_MCG_SMW)
+    return MRCG_ERR_INVALID;
   if (!a->rowptr || (a->nnz > 0 && (!a->colind || !a->val))) return MRCG_ERR_INVALID;
   if (a->k > 0 && (!a->V || !a->lambda)) return MRCG_ERR_INVALID;
   if (std::isnan(a->restart_factor)) return MRCG_ERR_INVALID;

@@ -51,6 +51,9 @@ struct CgArgs {
   int k;
   // Jacobi: dinv != nullptr, s is a separate vector; identity: s == r
   const T* dinv;
+  // MINRES-CG* (Sec. 2.1): 1 / diag(A) != nullptr, s = diag(A)^{-1} r - 2 V Lambda^{-1} V^T r
+  // is a separate vector, and dinv is nullptr (step a then forms V^T (A p'))
+  const T* dsmw;
   const double* gram;  // k x k V^T M_cg^{-1} V (row-major) of the kernels' V
   // staged step a: ring of shared-memory stages (bytes; region offsets inside a stage)
   int stages, stage_bytes, off_col, off_v, off_s, off_p, off_d;
@@ -154,6 +157,32 @@ __device__ __forceinline__ void pack_slots(T (&acc)[KB + 2], T rs, const T (&u)[
 
 // ------------------------------------------------------------------ init
 
+// Scalars of a new inner solve, once rho = r^T s, ||r|| and S.u = V^T s are known.
+__device__ __forceinline__ void start_cg(CgState& S, int k, double vn, double rho, double rnorm) {
+  S.rho = rho;
+  S.beta = 0.0;
+  S.beta32 = 0.0f;
+  S.iters = 0;
+  S.tol_abs = S.inner_tol * rnorm;
+  S.maxit = S.budget;
+  S.ctl_count = 0;
+  {
+    const long long per = S.unroll > 0 ? S.unroll : 1;
+    const long long lim = (S.maxit > 0 ? S.maxit : 0) / per + 2;
+    S.ctl_limit = (int)(lim < 0x7fffffffLL ? lim : 0x7fffffffLL);
+  }
+  S.done = kRunning;
+  if (!isfinite(vn) || !isfinite(rho)) {
+    S.done = kNonFinite;
+  } else if (vn == 0.0 || rnorm == 0.0) {
+    S.done = kConverged;
+  } else if (S.maxit <= 0) {
+    S.done = kMaxIter;
+  }
+  for (int l = 0; l < k; ++l) S.t[l] = S.u[l];
+  publish_c(S, k);
+}
+
 template <typename T, int KB>
 __global__ void __launch_bounds__(kThreads) cg_init_kernel(CgArgs<T> a) {
   constexpr int W = V16<T>::W;
@@ -210,28 +239,217 @@ __global__ void __launch_bounds__(kThreads) cg_init_kernel(CgArgs<T> a) {
     final_sums(a.partials, nv, tot);
     if (threadIdx.x == 0) {
       const double rho = tot[0], rnorm = sqrt(jac ? tot[a.k + 1] : tot[0]);
-      S.rho = rho;
-      S.beta = 0.0;
-      S.beta32 = 0.0f;
-      S.iters = 0;
-      S.tol_abs = S.inner_tol * rnorm;
-      S.maxit = S.budget;
-      S.ctl_count = 0;
-      {
-        const long long per = S.unroll > 0 ? S.unroll : 1;
-        const long long lim = (S.maxit > 0 ? S.maxit : 0) / per + 2;
-        S.ctl_limit = (int)(lim < 0x7fffffffLL ? lim : 0x7fffffffLL);
+      for (int l = 0; l < a.k; ++l) S.u[l] = tot[l + 1];
+      start_cg(S, a.k, vn, rho, rnorm);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ MINRES-CG* inner preconditioner
+//
+// Sec. 2.1: M_cg^{-1} = Atilde^{-1} - 2 V Lambda^{-1} V^T with Atilde = diag(A),
+// so s = M_cg^{-1} r = diag(A)^{-1} r + V e,  e = -2 Lambda^{-1} (V^T r)
+// = 4 (V^T r) / (2|lambda|).  V^T r follows the recurrence
+// V^T r_{i+1} = V^T r_i - alpha V^T q_i (V^T q from step a), and
+// V^T s = V^T diag(A)^{-1} r + (V^T V) e, so each V_hat entry is read once per
+// iteration (in step b, which must form s explicitly for the next SpMV).
+
+// e = 4 vr / lam2 in the kernel's precision, shared by the block
+template <typename T, int KS>
+__device__ __forceinline__ void smw_coeffs(const CgState& S, const double* vr, int k, T (&es)[KS]) {
+  if ((int)threadIdx.x < KS) es[threadIdx.x] = ((int)threadIdx.x < k) ? (T)(4.0 * vr[threadIdx.x] / S.lam2[threadIdx.x]) : (T)0;
+  __syncthreads();
+}
+
+// init, pass 1: r = v / ||v||, z = p = 0, and S.vr = V^T r
+template <typename T, int KB>
+__global__ void __launch_bounds__(kThreads) cg_init_smw_vr_kernel(CgArgs<T> a) {
+  constexpr int W = V16<T>::W;
+  constexpr int KS = KB > 0 ? KB : 1;
+  CgState& S = a.st->cg;
+  const double vn = S.vnorm;
+  const double scale = (vn > 0.0 && isfinite(vn)) ? 1.0 / vn : 0.0;
+  const double* v = S.vin;
+  T u[KS];
+#pragma unroll
+  for (int l = 0; l < KS; ++l) u[l] = 0;
+  const T zero[W] = {};
+  const int64_t nvec = a.n_pad / W;
+  for (int64_t iv = blockIdx.x * (int64_t)kThreads + threadIdx.x; iv < nvec; iv += (int64_t)gridDim.x * kThreads) {
+    const int64_t i = iv * W;
+    T r[W];
+#pragma unroll
+    for (int e = 0; e < W; ++e) r[e] = (T)(v[i + e] * scale);
+    st16(a.r + i, r);
+    st16(a.z + i, zero);
+    st16(a.p_old + i, zero);
+#pragma unroll
+    for (int l = 0; l < KB; ++l)
+      if (l < a.k) {
+        T vv[W];
+        ld16_stream(a.V + (size_t)l * a.n_pad + i, vv);
+#pragma unroll
+        for (int e = 0; e < W; ++e) u[l] += vv[e] * r[e];
       }
-      S.done = kRunning;
-      if (!isfinite(vn) || !isfinite(rho)) {
+  }
+  T acc[KS];
+#pragma unroll
+  for (int l = 0; l < KS; ++l) acc[l] = u[l];
+  const int nv = a.k > 0 ? a.k : 1;
+  block_partials_t<T, KS>(acc, nv, a.partials);
+  if (last_block_after_partials(&a.st->ticket)) {
+    __shared__ double tot[KS];
+    final_sums(a.partials, nv, tot);
+    if ((int)threadIdx.x < a.k) S.vr[threadIdx.x] = tot[threadIdx.x];
+  }
+}
+
+// One pass over rows [i, i + W): s = diag(A)^{-1} r + V e, accumulating
+// r^T s, r^T r and wd = V^T (diag(A)^{-1} r).
+template <typename T, int KB, int W>
+__device__ __forceinline__ void smw_rows(const CgArgs<T>& a, int64_t i, const T (&r)[W], const T* es, T& rs, T& rr,
+                                         T (&wd)[KB > 0 ? KB : 1]) {
+  T d[W], dr[W], s[W];
+  ld16(a.dsmw + i, d);
+#pragma unroll
+  for (int e = 0; e < W; ++e) {
+    dr[e] = d[e] * r[e];
+    s[e] = dr[e];
+  }
+#pragma unroll
+  for (int l = 0; l < KB; ++l)
+    if (l < a.k) {
+      T vv[W];
+      ld16_stream(a.V + (size_t)l * a.n_pad + i, vv);
+#pragma unroll
+      for (int e = 0; e < W; ++e) {
+        s[e] += vv[e] * es[l];
+        wd[l] += vv[e] * dr[e];
+      }
+    }
+  st16(a.s + i, s);
+#pragma unroll
+  for (int e = 0; e < W; ++e) {
+    rs += r[e] * s[e];
+    rr += r[e] * r[e];
+  }
+}
+
+// u = V^T s = wd + (V^T V) e: thread l of the last block, after final_sums
+// left wd in tot[1 .. k] (G = V^T V is symmetric: column l)
+__device__ __forceinline__ void smw_u(CgState& S, const double* gram, const double* tot, int k, const double* e) {
+  const int l = threadIdx.x;
+  if (l < k) {
+    double u = tot[l + 1];
+    for (int m = 0; m < k; ++m) u += gram[(size_t)m * k + l] * e[m];
+    S.u[l] = u;
+  }
+}
+
+// init, pass 2: s = M_cg^{-1} r and the scalars of the new solve
+template <typename T, int KB>
+__global__ void __launch_bounds__(kThreads) cg_init_smw_kernel(CgArgs<T> a) {
+  constexpr int W = V16<T>::W;
+  constexpr int KS = KB > 0 ? KB : 1;
+  CgState& S = a.st->cg;
+  __shared__ T es[KS];
+  smw_coeffs<T, KS>(S, S.vr, a.k, es);
+  T rs = 0, rr = 0;
+  T wd[KS];
+#pragma unroll
+  for (int l = 0; l < KS; ++l) wd[l] = 0;
+  const int64_t nvec = a.n_pad / W;
+  for (int64_t iv = blockIdx.x * (int64_t)kThreads + threadIdx.x; iv < nvec; iv += (int64_t)gridDim.x * kThreads) {
+    const int64_t i = iv * W;
+    T r[W];
+    ld16(a.r + i, r);
+    smw_rows<T, KB, W>(a, i, r, es, rs, rr, wd);
+  }
+  T acc[KB + 2];
+  pack_slots<T, KB>(acc, rs, wd, rr, a.k, true);
+  const int nv = a.k + 2;
+  block_partials_t<T, KB + 2>(acc, nv, a.partials);
+  if (last_block_after_partials(&a.st->ticket)) {
+    __shared__ double tot[KB + 2];
+    __shared__ double ed[KS];
+    final_sums(a.partials, nv, tot);
+    if ((int)threadIdx.x < a.k) ed[threadIdx.x] = 4.0 * S.vr[threadIdx.x] / S.lam2[threadIdx.x];
+    __syncthreads();
+    smw_u(S, a.gram, tot, a.k, ed);
+    __syncthreads();
+    if (threadIdx.x == 0) start_cg(S, a.k, S.vnorm, tot[0], sqrt(tot[a.k + 1]));
+  }
+}
+
+// step b with the MINRES-CG* M_cg: z += alpha p', r -= alpha q, s = M_cg^{-1} r
+template <typename T, int KB>
+__global__ void __launch_bounds__(kThreads) cg_step_b_smw_kernel(CgArgs<T> a) {
+  constexpr int W = V16<T>::W;
+  constexpr int KS = KB > 0 ? KB : 1;
+  CgState& S = a.st->cg;
+  if (S.done != kRunning) return;
+  const T alpha = alpha_of(S, T(0));
+  // V^T r_{i+1} = V^T r_i - alpha V^T q_i, formed alike in every block
+  __shared__ double vr_new[KS];
+  __shared__ T es[KS];
+  if ((int)threadIdx.x < KS) vr_new[threadIdx.x] = ((int)threadIdx.x < a.k) ? S.vr[threadIdx.x] - S.alpha * S.vq[threadIdx.x] : 0.0;
+  __syncthreads();
+  smw_coeffs<T, KS>(S, vr_new, a.k, es);
+  T rs = 0, rr = 0;
+  T wd[KS];
+#pragma unroll
+  for (int l = 0; l < KS; ++l) wd[l] = 0;
+  const int64_t nvec = a.n_pad / W;
+  for (int64_t iv = blockIdx.x * (int64_t)kThreads + threadIdx.x; iv < nvec; iv += (int64_t)gridDim.x * kThreads) {
+    const int64_t i = iv * W;
+    T pn[W], qv[W], zv[W], rv[W];
+    ld16(a.p_new + i, pn);
+    ld16(a.q + i, qv);
+    ld16(a.z + i, zv);
+    ld16(a.r + i, rv);
+#pragma unroll
+    for (int e = 0; e < W; ++e) {
+      zv[e] += alpha * pn[e];
+      rv[e] -= alpha * qv[e];
+    }
+    st16(a.z + i, zv);
+    st16(a.r + i, rv);
+    smw_rows<T, KB, W>(a, i, rv, es, rs, rr, wd);
+  }
+  T acc[KB + 2];
+  pack_slots<T, KB>(acc, rs, wd, rr, a.k, true);
+  const int nv = a.k + 2;
+  block_partials_t<T, KB + 2>(acc, nv, a.partials);
+  if (last_block_after_partials(&a.st->ticket)) {
+    __shared__ double tot[KB + 2];
+    __shared__ double ed[KS];
+    final_sums(a.partials, nv, tot);
+    if ((int)threadIdx.x < a.k) {
+      S.vr[threadIdx.x] = vr_new[threadIdx.x];
+      ed[threadIdx.x] = 4.0 * vr_new[threadIdx.x] / S.lam2[threadIdx.x];
+    }
+    __syncthreads();
+    smw_u(S, a.gram, tot, a.k, ed);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const double rho_new = tot[0], rnorm = sqrt(tot[a.k + 1]);
+      S.iters += 1;
+      if (!isfinite(rho_new) || !isfinite(rnorm)) {
         S.done = kNonFinite;
-      } else if (vn == 0.0 || rnorm == 0.0) {
+      } else if (rnorm <= S.tol_abs) {
         S.done = kConverged;
-      } else if (S.maxit <= 0) {
+      } else if (S.iters >= S.maxit) {
         S.done = kMaxIter;
+      } else if (rho_new == 0.0) {
+        S.done = kBreakdown;
+      } else {
+        const double beta = rho_new / S.rho;
+        S.beta = beta;
+        S.beta32 = (float)beta;
+        S.rho = rho_new;
+        for (int l = 0; l < a.k; ++l) S.t[l] = S.u[l] + beta * S.t[l];
+        publish_c(S, a.k);
       }
-      for (int l = 0; l < a.k; ++l) S.t[l] = S.u[l] = tot[l + 1];
-      publish_c(S, a.k);
     }
   }
 }
@@ -857,6 +1075,8 @@ __global__ void __launch_bounds__(kThreads) cg_step_b_kernel(CgArgs<T> a) {
         S.done = kConverged;
       } else if (S.iters >= S.maxit) {
         S.done = kMaxIter;
+      } else if (rho_new == 0.0) {
+        S.done = kBreakdown;
       } else {
         const double beta = rho_new / S.rho;
         S.beta = beta;
@@ -904,6 +1124,8 @@ __global__ void __launch_bounds__(kThreads) cg_finish_kernel(DevState* st, const
       if (S.done == kNotSpd) O.status = MRCG_ERR_NOT_SPD;
       else if (S.done == kNonFinite) O.status = MRCG_ERR_NONFINITE;
       else if (S.done == kMaxIter || S.done == kLoopCap) O.status = MRCG_ERR_MAXITER;
+      else if (S.done == kBreakdown) O.status = MRCG_ERR_BREAKDOWN;
+      else if (S.done == kStall) O.status = MRCG_ERR_CUDA;
     }
   }
 }
@@ -966,10 +1188,11 @@ void make_args(const InnerGraphSpec& spec, CgArgs<T> (&a)[2]) {
     x.V = reinterpret_cast<const T*>(spec.V);
     x.k = spec.k;
     x.dinv = reinterpret_cast<const T*>(spec.dinv);
+    x.dsmw = reinterpret_cast<const T*>(spec.dsmw);
     x.gram = spec.gram;
     x.z = reinterpret_cast<T*>(spec.z);
     x.r = reinterpret_cast<T*>(spec.r);
-    x.s = spec.dinv ? reinterpret_cast<T*>(spec.s) : reinterpret_cast<T*>(spec.r);
+    x.s = (spec.dinv || spec.dsmw) ? reinterpret_cast<T*>(spec.s) : reinterpret_cast<T*>(spec.r);
     x.q = reinterpret_cast<T*>(spec.q);
     x.p_old = reinterpret_cast<T*>(par == 0 ? spec.p0 : spec.p1);
     x.p_new = reinterpret_cast<T*>(par == 0 ? spec.p1 : spec.p0);
@@ -1020,6 +1243,29 @@ cudaError_t launch_a(const void* fn, int grid, int block, cudaStream_t stream, C
   return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, stream);
 }
 
+// step b of the spec's inner preconditioner
+template <typename T, int KB>
+const void* step_b_fn(const InnerGraphSpec& spec) {
+  return spec.dsmw ? (const void*)cg_step_b_smw_kernel<T, KB> : (const void*)cg_step_b_kernel<T, KB>;
+}
+
+template <typename T, int KB>
+void launch_b(const InnerGraphSpec& spec, cudaStream_t stream, CgArgs<T>& a) {
+  void* args[] = {&a};
+  cudaLaunchKernel(step_b_fn<T, KB>(spec), dim3(spec.grid_stream_b), dim3(kThreads), args, 0, stream);
+}
+
+// the first residual and its preconditioned form (two passes for the MINRES-CG* M_cg)
+template <typename T, int KB>
+void launch_init(const InnerGraphSpec& spec, cudaStream_t stream, CgArgs<T>& a) {
+  if (spec.dsmw) {
+    cg_init_smw_vr_kernel<T, KB><<<spec.grid_stream, kThreads, 0, stream>>>(a);
+    cg_init_smw_kernel<T, KB><<<spec.grid_stream, kThreads, 0, stream>>>(a);
+  } else {
+    cg_init_kernel<T, KB><<<spec.grid_stream, kThreads, 0, stream>>>(a);
+  }
+}
+
 template <typename T, int KB>
 cudaError_t build_graph_t(const InnerGraphSpec& spec, cudaGraph_t* out_graph) {
   cudaError_t e;
@@ -1039,9 +1285,18 @@ cudaError_t build_graph_t(const InnerGraphSpec& spec, cudaGraph_t* out_graph) {
     goto fail;
   {
     void* init_args[] = {&a[0]};
-    if ((e = add_kernel(g, &n_init, &n_norm, 1, (const void*)cg_init_kernel<T, KB>, spec.grid_stream, kThreads,
-                        init_args)))
+    if (spec.dsmw) {
+      cudaGraphNode_t n_vr;
+      if ((e = add_kernel(g, &n_vr, &n_norm, 1, (const void*)cg_init_smw_vr_kernel<T, KB>, spec.grid_stream,
+                          kThreads, init_args)))
+        goto fail;
+      if ((e = add_kernel(g, &n_init, &n_vr, 1, (const void*)cg_init_smw_kernel<T, KB>, spec.grid_stream, kThreads,
+                          init_args)))
+        goto fail;
+    } else if ((e = add_kernel(g, &n_init, &n_norm, 1, (const void*)cg_init_kernel<T, KB>, spec.grid_stream,
+                               kThreads, init_args))) {
       goto fail;
+    }
   }
   {
     cudaGraphConditionalHandle h;
@@ -1060,7 +1315,7 @@ cudaError_t build_graph_t(const InnerGraphSpec& spec, cudaGraph_t* out_graph) {
       if ((e = add_kernel(body, &na, prev ? &prev : nullptr, prev ? 1 : 0, step_a_fn<T, KB>(spec.var_a),
                           spec.grid_spmv, step_a_block(spec), aa, smem_a)))
         goto fail;
-      if ((e = add_kernel(body, &nb, &na, 1, (const void*)cg_step_b_kernel<T, KB>, spec.grid_stream_b, kThreads,
+      if ((e = add_kernel(body, &nb, &na, 1, step_b_fn<T, KB>(spec), spec.grid_stream_b, kThreads,
                           aa)))
         goto fail;
       prev = nb;
@@ -1092,12 +1347,12 @@ cudaError_t run_host_t(const InnerGraphSpec& spec, cudaStream_t stream, int* h_d
   make_args(spec, a);
   const unsigned smem_a = step_a_smem<T, KB>(spec);
   cg_vnorm_kernel<<<spec.grid_stream, kThreads, 0, stream>>>(spec.st, spec.partials, spec.A.n_pad);
-  cg_init_kernel<T, KB><<<spec.grid_stream, kThreads, 0, stream>>>(a[0]);
+  launch_init<T, KB>(spec, stream, a[0]);
   cudaError_t e = cudaSuccess;
   for (;;) {
     for (int it = 0; it < spec.unroll; ++it) {
       launch_a<T>(step_a_fn<T, KB>(spec.var_a), spec.grid_spmv, step_a_block(spec), stream, a[it & 1], smem_a);
-      cg_step_b_kernel<T, KB><<<spec.grid_stream_b, kThreads, 0, stream>>>(a[it & 1]);
+      launch_b<T, KB>(spec, stream, a[it & 1]);
     }
     cg_ctl_host_kernel<<<1, 1, 0, stream>>>(spec.st);
     if ((e = cudaMemcpyAsync(h_done, &spec.st->cg.done, sizeof(int), cudaMemcpyDeviceToHost, stream))) return e;
@@ -1117,14 +1372,14 @@ cudaError_t time_t(const InnerGraphSpec& spec, int iters, cudaStream_t stream, d
   const unsigned smem_a = step_a_smem<T, KB>(spec);
   fill_pattern_kernel<<<spec.grid_stream, kThreads, 0, stream>>>(vin, n);
   cg_vnorm_kernel<<<spec.grid_stream, kThreads, 0, stream>>>(spec.st, spec.partials, spec.A.n_pad);
-  cg_init_kernel<T, KB><<<spec.grid_stream, kThreads, 0, stream>>>(a[0]);
+  launch_init<T, KB>(spec, stream, a[0]);
   std::vector<cudaEvent_t> ev(2 * (size_t)iters + 1);
   for (auto& e : ev) cudaEventCreate(&e);
   cudaEventRecord(ev[0], stream);
   for (int it = 0; it < iters; ++it) {
     launch_a<T>(step_a_fn<T, KB>(spec.var_a), spec.grid_spmv, step_a_block(spec), stream, a[it & 1], smem_a);
     cudaEventRecord(ev[2 * it + 1], stream);
-    cg_step_b_kernel<T, KB><<<spec.grid_stream_b, kThreads, 0, stream>>>(a[it & 1]);
+    launch_b<T, KB>(spec, stream, a[it & 1]);
     cudaEventRecord(ev[2 * it + 2], stream);
   }
   cudaError_t e = cudaStreamSynchronize(stream);
@@ -1153,7 +1408,7 @@ template <typename T, int KB>
 void occupancy_t(const InnerGraphSpec& spec, int* a_blocks, int* b_blocks) {
   const unsigned smem = step_a_smem<T, KB>(spec);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(a_blocks, step_a_fn<T, KB>(spec.var_a), step_a_block(spec), smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(b_blocks, (const void*)cg_step_b_kernel<T, KB>, kThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(b_blocks, step_b_fn<T, KB>(spec), kThreads, 0);
 }
 
 // dispatch on the k bucket of the kernels (one precision per translation unit)

@@ -26,7 +26,17 @@ constexpr int kMaxNV = kMaxK + 2;  // reduction values per block
 
 // inner CG outcome codes (CgState::done)
 // (kStall: a staged copy did not arrive within its wait limit; reported as a CUDA error)
-enum : int { kRunning = 0, kConverged = 1, kNotSpd = 2, kNonFinite = 3, kMaxIter = 4, kLoopCap = 5, kStall = 6 };
+// (kBreakdown: r^T M_cg^{-1} r = 0 before convergence, possible only with an indefinite M_cg)
+enum : int {
+  kRunning = 0,
+  kConverged = 1,
+  kNotSpd = 2,
+  kNonFinite = 3,
+  kMaxIter = 4,
+  kLoopCap = 5,
+  kStall = 6,
+  kBreakdown = 7
+};
 
 struct CgState {
   double rho;            // r^T s of the current residual (s = M_cg^{-1} r)
@@ -38,7 +48,8 @@ struct CgState {
   double c[kMaxK];       // 2 |lambda_j| (V^T p)_j for the current direction p
   double t[kMaxK];       // (V^T p)_j for the current direction p
   double u[kMaxK];       // V^T s of the current preconditioned residual s (recurrence)
-  double vq[kMaxK];      // V^T (M_cg^{-1} q) of the last M_mr product q
+  double vq[kMaxK];      // V^T (M_cg^{-1} q) of the last M_mr product q (V^T q with the MINRES-CG* M_cg)
+  double vr[kMaxK];      // V^T r (MINRES-CG* M_cg only, by recurrence)
   float c32[kMaxK];      // FP32 copies of c, alpha, beta for the FP32 kernels
   float alpha32, beta32;
   double inner_tol;      // per-call parameters (uploaded by the host)

@@ -17,7 +17,8 @@ struct InnerGraphSpec {
   const void* V = nullptr;     // n_pad x k, inner precision
   int k = 0;
   const void* dinv = nullptr;  // Jacobi: 1 / diag(M_mr) (inner precision) or nullptr
-  const double* gram = nullptr;  // k x k  V^T M_cg^{-1} V  of the kernels' V (row-major)
+  const void* dsmw = nullptr;  // MINRES-CG* M_cg: 1 / diag(A) (inner precision; dinv is then nullptr)
+  const double* gram = nullptr;  // k x k  V^T M V  of the kernels' V (row-major; M = diag(dinv) or I)
   void* z = nullptr;
   void* r = nullptr;
   void* s = nullptr;
