@@ -42,8 +42,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["lap3d_128", "saddle", "batch64", "shifted64"], default="lap3d_128",
-                    help="lap3d_128: the headline single-system workload; batch64: 64 independent uneven "
+    ap.add_argument("--workload", choices=["lap3d_128", "lap3d_128_near", "saddle", "batch64", "shifted64"],
+                    default="lap3d_128",
+                    help="lap3d_128: the headline single-system workload; lap3d_128_near: the same matrix with "
+                         "sigma close to lambda_10 (for --mcg smw, MINRES-CG*); batch64: 64 independent uneven "
                          "2D systems (sides 100..400, k_i 1..16, seed 3) solved as one batch; shifted64: 16 "
                          "shifts x 4 RHS of the 160^3 Laplacian as one right-hand-side block")
     ap.add_argument("--mcg", choices=["identity", "jacobi", "smw"], default="identity",
@@ -418,7 +420,7 @@ def main():
         return
     import torch
 
-    from gen import config2, config3
+    from gen import config2, config2_near, config3
     from paper_1805_12417_gb300 import build as _b
     _b.build()
     import paper_1805_12417_gb300 as m
@@ -431,6 +433,10 @@ def main():
         p = config3()
         workload = ("saddle_96^3_B20x64: [K B^T; B 0], K 27-pt log-normal(0,1) SPD stencil on 96^3, B 20 rows x 64 "
                     "uniform[-1,1] entries (n=884,756, 20 negative eigenvalues), seed 2, 1 RHS")
+    elif args.workload == "lap3d_128_near":
+        p = config2_near()
+        workload = ("lap3d_128^3_k10_near: the lap3d_128 matrix with sigma at lambda_10 + 0.05 (lambda_11 - "
+                    "lambda_10), so the 10 negative eigenvalues are the smallest in modulus, 1 RHS")
     else:
         p = config2()
     b_dev = torch.from_numpy(p.b).to(dev)

@@ -17,6 +17,7 @@ from .problems import (  # noqa: F401
     random_sparse_symmetric,
     config1,
     config2,
+    config2_near,
     config4,
     config5,
     ShiftedFamily,

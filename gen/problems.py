@@ -189,6 +189,13 @@ def config2() -> Problem:
     return shifted_laplacian_problem("lap3d_128^3_k10", (128, 128, 128), 10, seed=1)
 
 
+def config2_near() -> Problem:
+    """Config 2's matrix with sigma moved to lambda_10 + 0.05 (lambda_11 - lambda_10):
+    the 10 negative eigenvalues are the ones closest to zero (where the
+    MINRES-CG* inner preconditioner of Sec. 2.1 pays off)."""
+    return shifted_laplacian_problem("lap3d_128^3_k10_near", (128, 128, 128), 10, seed=1, sigma_frac=0.05)
+
+
 def small_3d(m=(12, 11, 10), k=5, seed=7) -> Problem:
     """Small 3D analogue used by the parity tests (ragged in every dimension)."""
     return shifted_laplacian_problem(f"lap3d_{m[0]}x{m[1]}x{m[2]}_k{k}", m, k, seed=seed)

@@ -316,17 +316,24 @@ __device__ __forceinline__ void smw_rows(const CgArgs<T>& a, int64_t i, const T 
     dr[e] = d[e] * r[e];
     s[e] = dr[e];
   }
+  // V rows in groups of G (FP64: four, the loads of a group in flight together)
+  constexpr int G = sizeof(T) == 8 ? 4 : 1;
 #pragma unroll
-  for (int l = 0; l < KB; ++l)
-    if (l < a.k) {
-      T vv[W];
-      ld16_stream(a.V + (size_t)l * a.n_pad + i, vv);
+  for (int l0 = 0; l0 < KB; l0 += G) {
+    T vv[G][W];
 #pragma unroll
-      for (int e = 0; e < W; ++e) {
-        s[e] += vv[e] * es[l];
-        wd[l] += vv[e] * dr[e];
+    for (int j = 0; j < G; ++j)
+      if (l0 + j < KB && l0 + j < a.k) ld16_stream(a.V + (size_t)(l0 + j) * a.n_pad + i, vv[j]);
+#pragma unroll
+    for (int j = 0; j < G; ++j)
+      if (l0 + j < KB && l0 + j < a.k) {
+#pragma unroll
+        for (int e = 0; e < W; ++e) {
+          s[e] += vv[j][e] * es[l0 + j];
+          wd[l0 + j] += vv[j][e] * dr[e];
+        }
       }
-    }
+  }
   st16(a.s + i, s);
 #pragma unroll
   for (int e = 0; e < W; ++e) {
@@ -400,21 +407,37 @@ __global__ void __launch_bounds__(kThreads) cg_step_b_smw_kernel(CgArgs<T> a) {
 #pragma unroll
   for (int l = 0; l < KS; ++l) wd[l] = 0;
   const int64_t nvec = a.n_pad / W;
-  for (int64_t iv = blockIdx.x * (int64_t)kThreads + threadIdx.x; iv < nvec; iv += (int64_t)gridDim.x * kThreads) {
-    const int64_t i = iv * W;
-    T pn[W], qv[W], zv[W], rv[W];
-    ld16(a.p_new + i, pn);
-    ld16(a.q + i, qv);
-    ld16(a.z + i, zv);
-    ld16(a.r + i, rv);
+  const int64_t stride = (int64_t)gridDim.x * kThreads;
+  // FP64: two grid-stride chunks per trip, their vector loads issued together
+  // (measured faster there; in FP32 one chunk per trip keeps more blocks resident)
+  constexpr int U = sizeof(T) == 8 ? 2 : 1;
+  for (int64_t iv0 = blockIdx.x * (int64_t)kThreads + threadIdx.x; iv0 < nvec; iv0 += U * stride) {
+    T pn[U][W], qv[U][W], zv[U][W], rv[U][W];
 #pragma unroll
-    for (int e = 0; e < W; ++e) {
-      zv[e] += alpha * pn[e];
-      rv[e] -= alpha * qv[e];
+    for (int u = 0; u < U; ++u) {
+      const int64_t iv = iv0 + u * stride;
+      if (iv < nvec) {
+        const int64_t i = iv * W;
+        ld16(a.p_new + i, pn[u]);
+        ld16(a.q + i, qv[u]);
+        ld16(a.z + i, zv[u]);
+        ld16(a.r + i, rv[u]);
+      }
     }
-    st16(a.z + i, zv);
-    st16(a.r + i, rv);
-    smw_rows<T, KB, W>(a, i, rv, es, rs, rr, wd);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t iv = iv0 + u * stride;
+      if (iv >= nvec) continue;
+      const int64_t i = iv * W;
+#pragma unroll
+      for (int e = 0; e < W; ++e) {
+        zv[u][e] += alpha * pn[u][e];
+        rv[u][e] -= alpha * qv[u][e];
+      }
+      st16(a.z + i, zv[u]);
+      st16(a.r + i, rv[u]);
+      smw_rows<T, KB, W>(a, i, rv[u], es, rs, rr, wd);
+    }
   }
   T acc[KB + 2];
   pack_slots<T, KB>(acc, rs, wd, rr, a.k, true);
