@@ -66,6 +66,15 @@ def dist_setup():
     return ws, rank, local
 
 
+def replica_throughput(ms_local, ok_local, ws, dev):
+    """Whole-job throughput of independent replicas: the solves that met the
+    tolerance on all ranks over the slowest rank's time.  Returns (max ms,
+    total ok, solves/s)."""
+    ms = max_over_ranks(ms_local, ws, dev)
+    ok = sum_over_ranks(ok_local, ws, dev)
+    return ms, ok, ok / (ms / 1000.0)
+
+
 def barrier(ws):
     if ws > 1:
         import torch.distributed as dist
@@ -468,17 +477,13 @@ def main():
         barrier(ws)
         if ck:
             ck.__exit__(None, None, None)
-        ms = e0.elapsed_time(e1)
-        ms = max_over_ranks(ms, ws, dev)
         ok = sum(1 for i in infos if i.status == m.OK and i.true_relres <= OUTER_TOL)
-        ok = sum_over_ranks(ok, ws, dev)
-        return ms, ok, infos, (ck.summary() if ck else None)
+        ms, ok, v = replica_throughput(e0.elapsed_time(e1), ok, ws, dev)
+        return ms, ok, v, infos, (ck.summary() if ck else None)
 
     # mixed precision (headline) and plain FP64
-    ms_mx, ok_mx, inf_mx, clocks = run(m.MIXED_FP32, args.steps, args.warmup, clocks=(rank == 0))
-    ms_64, ok_64, inf_64, _ = run(m.FP64, args.steps, max(1, args.warmup))
-    value = ok_mx / (ms_mx / 1000.0)
-    fp64_value = ok_64 / (ms_64 / 1000.0)
+    ms_mx, ok_mx, value, inf_mx, clocks = run(m.MIXED_FP32, args.steps, args.warmup, clocks=(rank == 0))
+    ms_64, ok_64, fp64_value, inf_64, _ = run(m.FP64, args.steps, max(1, args.warmup))
 
     # errors against x* (FP64 check on the host)
     x_last = x_dev.cpu().numpy()
