@@ -131,7 +131,9 @@ mrcg_status mrcg_apply_mmr(mrcg_handle h, const double* u, double* out);
  * from z = 0 (Eq. 2), in the handle's precision, until
  * ||y - M_mr z||_recursive <= inner_tol ||y|| or max_iters iterations.
  * iters (may be NULL) receives the iteration count.  Returns MRCG_OK,
- * MRCG_ERR_MAXITER, MRCG_ERR_NOT_SPD or MRCG_ERR_NONFINITE. */
+ * MRCG_ERR_MAXITER, MRCG_ERR_NOT_SPD, MRCG_ERR_NONFINITE, MRCG_ERR_BREAKDOWN
+ * (MRCG_MCG_SMW only) or MRCG_ERR_CUDA (a staged copy of the inner kernels did
+ * not arrive within its wait limit of about a second; the handle stays usable). */
 mrcg_status mrcg_inner_solve(mrcg_handle h, const double* y, double* z, double inner_tol, int64_t max_iters,
                              int64_t* iters);
 

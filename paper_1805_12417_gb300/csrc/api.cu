@@ -422,6 +422,10 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
   g.q = h->iq;
   g.grid_stream = h->grid_stream;
   g.unroll = h->unroll;
+  // failure-detection test hook: the staged step a stops issuing its copies
+  // after the first tile, so its bounded waits run out and the solve reports
+  // MRCG_ERR_CUDA (the GPU context stays usable)
+  if (const char* e = getenv("MRCG_TEST_STALL")) g.stall_test = atoi(e) != 0;
   // SELL entries of the largest tile of 8 slices (the staged step a's buffers)
   for (int64_t s0 = 0; s0 < nslices; s0 += 8) g.tile_entries = std::max(g.tile_entries, sp[std::min(s0 + 8, nslices)] - sp[s0]);
   if (const char* e = getenv("MRCG_STAGES")) g.stages = std::max(2, std::min(8, atoi(e)));
@@ -764,6 +768,8 @@ mrcg_status mrcg_inner_solve(mrcg_handle h, const double* y, double* z, double i
     case kConverged: return MRCG_OK;
     case kNotSpd: return MRCG_ERR_NOT_SPD;
     case kNonFinite: return MRCG_ERR_NONFINITE;
+    case kBreakdown: return MRCG_ERR_BREAKDOWN;
+    case kStall: return MRCG_ERR_CUDA;
     default: return MRCG_ERR_MAXITER;
   }
 }

@@ -57,6 +57,7 @@ struct CgArgs {
   const double* gram;  // k x k V^T M_cg^{-1} V (row-major) of the kernels' V
   // staged step a: ring of shared-memory stages (bytes; region offsets inside a stage)
   int stages, stage_bytes, off_col, off_v, off_s, off_p, off_d;
+  int stall_test;  // test hook: the producer stops after the first tile (waits then run out)
   // vectors
   T* z;
   T* r;
@@ -808,6 +809,7 @@ __global__ void __launch_bounds__(kStagedThreads, MB) cg_step_a_staged_kernel(Cg
       uint32_t ph = 0;
       int64_t t = blockIdx.x;
       for (int64_t i = 0; i < ntl; ++i, t += G) {
+        if (a.stall_test && i >= 1) break;
         if (i >= nst && !mbar_wait_or_abort(&empty[st], ph ^ 1u, &stalled)) break;
         const int64_t c0 = e0, c1 = e1;
         if (i + 1 < ntl) {
@@ -1194,6 +1196,7 @@ void make_args(const InnerGraphSpec& spec, CgArgs<T> (&a)[2]) {
   for (int par = 0; par < 2; ++par) {
     CgArgs<T>& x = a[par];
     x.stages = spec.stages;
+    x.stall_test = spec.stall_test ? 1 : 0;
     x.stage_bytes = geo.bytes;
     x.off_col = geo.off_col;
     x.off_v = geo.off_v;

@@ -33,6 +33,7 @@ struct InnerGraphSpec {
                  // 2 / 4 blocks per SM; 7: as 5 with the gathers issued one tile ahead)
   int64_t tile_entries = 0;  // most SELL entries in one tile of 8 slices (sizes the staged variant's buffers)
   int stages = 3;            // staged variant: shared-memory stages per block
+  bool stall_test = false;   // test hook: the staged producer issues only the first tile
 };
 
 cudaError_t build_inner_graph(const InnerGraphSpec& spec, cudaGraph_t* graph);
