@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["lap3d_128", "lap3d_128_near", "saddle", "batch64", "shifted64"],
+    ap.add_argument("--workload", choices=["lap3d_128", "lap2d_64", "lap3d_128_near", "saddle", "batch64",
+                                           "shifted64"],
                     default="lap3d_128",
                     help="lap3d_128: the headline single-system workload; lap3d_128_near: the same matrix with "
                          "sigma close to lambda_10 (for --mcg smw, MINRES-CG*); batch64: 64 independent uneven "
@@ -429,7 +430,7 @@ def main():
         return
     import torch
 
-    from gen import config2, config2_near, config3
+    from gen import config1, config2, config2_near, config3
     from paper_1805_12417_gb300 import build as _b
     _b.build()
     import paper_1805_12417_gb300 as m
@@ -442,6 +443,10 @@ def main():
         p = config3()
         workload = ("saddle_96^3_B20x64: [K B^T; B 0], K 27-pt log-normal(0,1) SPD stencil on 96^3, B 20 rows x 64 "
                     "uniform[-1,1] entries (n=884,756, 20 negative eigenvalues), seed 2, 1 RHS")
+    elif args.workload == "lap2d_64":
+        p = config1()
+        workload = ("lap2d_64x64_k4: 2D 5-pt Laplacian 64^2 (n=4,096) shifted to 4 negative eigenvalues, 1 RHS; "
+                    "L2-resident and latency-bound: read solves/s and launches per solve, not the HBM fraction")
     elif args.workload == "lap3d_128_near":
         p = config2_near()
         workload = ("lap3d_128^3_k10_near: the lap3d_128 matrix with sigma at lambda_10 + 0.05 (lambda_11 - "
@@ -574,6 +579,7 @@ def main():
             "e2e": {"value": ok_e2e / t_e2e, "unit": "solves/s", "h2d_bytes_per_step": 2 * n * 8,
                     "d2h_bytes_per_step": n * 8},
             "gpu_launches": int(launches),
+            "launches_per_solve": round(launches / max(1, len(inf_mx)), 1),
             "clocks": clocks,
             "cpu_baseline": cpu,
         }
