@@ -160,9 +160,11 @@ TRAFFIC_NOTE = "profiles/cg_step_a_lap3d_128.md"
 def step_a_kernel_name(cfg, prec="float"):
     """Name of the step-a kernel a launch configuration runs, as ncu prints it."""
     var, kb = cfg["step_a_variant"], cfg["k_bucket"]
+    if var == 8:
+        return f"cg_step_a_staged_kernel<{prec}, {kb}, 3, 0, 1>"
     if var >= 5:
         mb, pipe = {5: (2, 0), 6: (4, 0), 7: (2, 1)}[var]
-        return f"cg_step_a_staged_kernel<{prec}, {kb}, {mb}, {pipe}>"
+        return f"cg_step_a_staged_kernel<{prec}, {kb}, {mb}, {pipe}, 0>"
     return f"cg_step_a_kernel<{prec}, {kb}, {var}>"
 
 
@@ -523,10 +525,17 @@ def main():
 
     ib = m.launch_config(solvers[m.MIXED_FP32].h)["index_bytes"]
 
+    fused_of = {4: m.launch_config(solvers[m.MIXED_FP32].h)["step_a_variant"] == 8,
+                8: m.launch_config(solvers[m.FP64].h)["step_a_variant"] == 8}
+
     def bytes_a(w):  # A values + column indices, s and p_old read, V read, q and p_new written
+        if fused_of[w]:  # one-kernel iteration: r, q, p, z read and r, z, p, q written for the own rows
+            return nnz * (w + ib) + k * n * w + 8 * n * w
         return nnz * (w + ib) + 2 * n * w + k * n * w + 2 * n * w + (n * w if args.mcg == "jacobi" else 0)
 
     def bytes_b(w):  # p, q, z, r read; z, r written (V^T s by recurrence: no V pass)
+        if fused_of[w]:
+            return 0
         if args.mcg == "jacobi":  # + M_cg^{-1} read, s written
             return 8 * n * w
         if args.mcg == "smw":  # + diag(A)^{-1} and V read, s written
@@ -543,9 +552,9 @@ def main():
 
     kernels = {
         "mixed": {"step_a_ms": ta_mx, "step_b_ms": tb_mx, "step_a_gbs": bytes_a(4) / (ta_mx * 1e-3) / 1e9,
-                  "step_b_gbs": bytes_b(4) / (tb_mx * 1e-3) / 1e9},
+                  "step_b_gbs": bytes_b(4) / (max(tb_mx, 1e-6) * 1e-3) / 1e9},
         "fp64": {"step_a_ms": ta_64, "step_b_ms": tb_64, "step_a_gbs": bytes_a(8) / (ta_64 * 1e-3) / 1e9,
-                 "step_b_gbs": bytes_b(8) / (tb_64 * 1e-3) / 1e9},
+                 "step_b_gbs": bytes_b(8) / (max(tb_64, 1e-6) * 1e-3) / 1e9},
     }
     launches = sum(i.kernel_launches for i in inf_mx)
 

@@ -146,7 +146,7 @@ mrcg_status mrcg_inner_solve(mrcg_handle h, const double* y, double* z, double i
  * Each is launched `iters` times (1 <= iters <= 4096) on the handle's stream,
  * outside the solver's graph, on a fixed synthetic right-hand side, and
  * bracketed by CUDA events; ms receives the average duration in
- * milliseconds.  Overwrites the handle's work vectors (not its matrix). */
+ * milliseconds (ms[1] is near zero for step-a variant 8, which has no step b).  Overwrites the handle's work vectors (not its matrix). */
 mrcg_status mrcg_time_inner_kernels(mrcg_handle h, int32_t iters, double* ms);
 
 /* Launch configuration chosen for the handle's inner-CG kernels (at create,
@@ -156,11 +156,12 @@ mrcg_status mrcg_time_inner_kernels(mrcg_handle h, int32_t iters, double* ms);
  * resident blocks per SM, 5 / 6: every streamed operand staged in shared
  * memory by bulk copies, a persistent grid over tiles of 8 slices, registers
  * capped for 2 / 4 blocks per SM, 7: as 5 with each warp's gathers issued
- * one tile ahead), cfg[1] step-a grid (blocks), cfg[2] step-b grid,
+ * one tile ahead, 8: the whole CG iteration in one staged kernel, with the
+ * residual norm by expansion and no step b; M_cg = I only), cfg[1] step-a grid (blocks), cfg[2] step-b grid,
  * cfg[3] CG iterations per body of the device loop, cfg[4] k bucket of the
  * kernels (0, 8, 12, 16, 24 or 32), cfg[5] bytes per column index read by the
  * inner kernels (2: 16-bit col - row deltas, used when every delta fits; 4),
- * cfg[6] shared-memory stages of variants 5 to 7 (0 for the others).
+ * cfg[6] shared-memory stages of variants 5 to 8 (0 for the others).
  * cfg must hold 7 values. */
 mrcg_status mrcg_launch_config(mrcg_handle h, int32_t* cfg);
 

@@ -53,6 +53,7 @@ struct mrcg_solver {
   double* w[2] = {nullptr, nullptr};
   // inner-precision vectors
   void *iz = nullptr, *ir = nullptr, *is = nullptr, *ip0 = nullptr, *ip1 = nullptr, *iq = nullptr;
+  void *ir2 = nullptr, *iq2 = nullptr;  // one-kernel iteration (M_cg = I): second r and q buffers
 
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -333,9 +334,10 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
     CK(cudaMemsetAsync(*p, 0, (size_t)n_pad * sizeof(double), h->stream));
   }
   const size_t esz = h->fp32 ? sizeof(float) : sizeof(double);
-  void** inner[] = {&h->iz, &h->ir, &h->is, &h->ip0, &h->ip1, &h->iq};
+  void** inner[] = {&h->iz, &h->ir, &h->is, &h->ip0, &h->ip1, &h->iq, &h->ir2, &h->iq2};
   for (void** p : inner) {
     if (p == &h->is && h->mcg == MRCG_MCG_IDENTITY) continue;
+    if ((p == &h->ir2 || p == &h->iq2) && h->mcg != MRCG_MCG_IDENTITY) continue;
     char* q = nullptr;
     ST(dalloc(h, &q, (size_t)n_pad * esz));
     CK(cudaMemsetAsync(q, 0, (size_t)n_pad * esz, h->stream));
@@ -420,6 +422,8 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
   g.p0 = h->ip0;
   g.p1 = h->ip1;
   g.q = h->iq;
+  g.r2 = h->ir2;
+  g.q2 = h->iq2;
   g.grid_stream = h->grid_stream;
   g.unroll = h->unroll;
   // failure-detection test hook: the staged step a stops issuing its copies
@@ -434,7 +438,7 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
   auto grid_a = [&](const InnerGraphSpec& t, int bp) {
     return t.var_a >= 5 ? clamp_grid(ntiles, bp) : clamp_grid(want_spmv, bp);
   };
-  if (const char* va = getenv("MRCG_VAR_A")) g.var_a = std::min(7, std::max(0, atoi(va)));
+  if (const char* va = getenv("MRCG_VAR_A")) g.var_a = std::min(8, std::max(0, atoi(va)));
   int occ_a = 1, occ_b = 1;
   inner_occupancy(g, &occ_a, &occ_b);
   if (occ_a < 1) {  // the staged variant does not fit this matrix
@@ -458,7 +462,7 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
   const char* fixed = getenv(h->fp32 ? "MRCG_SHAPE_F32" : "MRCG_SHAPE_F64");
   if (fixed) {
     int v = 0, nst = 0, ga = 0, gb = 0;
-    if (sscanf(fixed, "%d,%d,%d,%d", &v, &nst, &ga, &gb) == 4 && v >= 0 && v <= 7 && ga >= 1 && gb >= 1 &&
+    if (sscanf(fixed, "%d,%d,%d,%d", &v, &nst, &ga, &gb) == 4 && v >= 0 && v <= 8 && ga >= 1 && gb >= 1 &&
         ga <= kMaxBlocks && gb <= kMaxBlocks) {
       InnerGraphSpec t = g;
       t.var_a = v;
@@ -473,7 +477,7 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
     }
   }
   const char* at = getenv("MRCG_AUTOTUNE");
-  const bool tune = (!at || atoi(at) != 0) && n_pad >= (1 << 18) && !getenv("MRCG_BPSM_A") &&
+  const bool tune = (!at || atoi(at) != 0) && n_pad >= (1 << 12) && !getenv("MRCG_BPSM_A") &&
                     !getenv("MRCG_BPSM_B") && !getenv("MRCG_VAR_A") && !fixed;
   if (tune) {
     double ms[4] = {0.0, 0.0, 0.0, 0.0}, best = 1e30;
@@ -514,6 +518,7 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
         }
       }
     }
+    const double best_a = best;
     best = 1e30;
     int occ_unused = 0, occ_bmax = 1;
     inner_occupancy(bestg, &occ_unused, &occ_bmax);
@@ -526,7 +531,31 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
         bestg.grid_stream_b = t.grid_stream_b;
       }
     }
-    g = bestg;
+    // the one-kernel iteration (variant 8, M_cg = I) competes with the best
+    // step a + step b pair on the time of a whole iteration
+    const double best_pair = best_a + best;
+    double best8 = 1e30;
+    InnerGraphSpec best8g = bestg;
+    for (int nst = 2; nst <= 3; ++nst) {
+      InnerGraphSpec t = g;
+      t.var_a = 8;
+      t.stages = nst;
+      int occ_v = 0, occ_unused = 0;
+      inner_occupancy(t, &occ_v, &occ_unused);
+      if (occ_v < 1) continue;
+      for (int bp : {occ_v, occ_v + 1}) {
+        t.grid_spmv = grid_a(t, bp);
+        ST(time_spec(t));
+        if (ms[0] < best8) {
+          best8 = ms[0];
+          best8g = t;
+          best8g.grid_stream_b = bestg.grid_stream_b;
+        }
+      }
+    }
+    g = best8 < best_pair ? best8g : bestg;
+    if (getenv("MRCG_DEBUG"))
+      fprintf(stderr, "mrcg autotune: best pair %.4f ms, one-kernel %.4f ms\n", best_pair, best8);
     if (getenv("MRCG_DEBUG"))
       fprintf(stderr, "mrcg autotune: var_a=%d stages=%d grid_a=%d grid_b=%d\n", g.var_a, g.stages, g.grid_spmv,
               g.grid_stream_b);
@@ -652,7 +681,11 @@ mrcg_status solve_impl(mrcg_solver* h, const double* ub, double* ux, double oute
     info->restarts = restarts;
     info->inner_iters_total = h->h_st->out.inner_total;
     info->prec_calls = h->h_st->out.prec_calls;
-    info->kernel_launches = launches + 3 * graphs + h->h_st->out.bodies * (2LL * h->unroll + 1);
+    // per inner solve: norm, init (two passes for MINRES-CG*), finish; per body
+    // of the while loop: U iterations of one or two kernels, then the control kernel
+    const long long per_graph = 3 + (h->mcg == MRCG_MCG_SMW ? 1 : 0);
+    const long long per_body = (h->spec.var_a == 8 ? 1LL : 2LL) * h->unroll + 1;
+    info->kernel_launches = launches + per_graph * graphs + h->h_st->out.bodies * per_body;
     info->true_relres = relres;
     info->history_len = info->relres_history ? std::min(hist_len, info->history_cap) : 0;
     info->status = status;

@@ -56,8 +56,11 @@ struct CgArgs {
   const T* dsmw;
   const double* gram;  // k x k V^T M_cg^{-1} V (row-major) of the kernels' V
   // staged step a: ring of shared-memory stages (bytes; region offsets inside a stage)
-  int stages, stage_bytes, off_col, off_v, off_s, off_p, off_d;
+  int stages, stage_bytes, off_col, off_v, off_s, off_p, off_d, off_z;
   int stall_test;  // test hook: the producer stops after the first tile (waits then run out)
+  // one-kernel iteration: r and q ping-pong (r = r_{i-1} read, r_new written; q = q_i written, q_old read)
+  T* r_new;
+  T* q_old;
   // vectors
   T* z;
   T* r;
@@ -161,8 +164,11 @@ __device__ __forceinline__ void pack_slots(T (&acc)[KB + 2], T rs, const T (&u)[
 // Scalars of a new inner solve, once rho = r^T s, ||r|| and S.u = V^T s are known.
 __device__ __forceinline__ void start_cg(CgState& S, int k, double vn, double rho, double rnorm) {
   S.rho = rho;
+  S.alpha = 0.0;
+  S.alpha32 = 0.0f;
   S.beta = 0.0;
   S.beta32 = 0.0f;
+  S.fused_pending = 0;
   S.iters = 0;
   S.tol_abs = S.inner_tol * rnorm;
   S.maxit = S.budget;
@@ -207,6 +213,7 @@ __global__ void __launch_bounds__(kThreads) cg_init_kernel(CgArgs<T> a) {
     st16(a.r + i, r);
     st16(a.z + i, zero);
     st16(a.p_old + i, zero);
+    if (a.q_old) st16(a.q_old + i, zero);  // one-kernel iteration: q_{-1} = 0
     if (jac) {
       T d[W];
       ld16(a.dinv + i, d);
@@ -691,17 +698,18 @@ constexpr int kTileRows = kTileSlices * kSlice;
 constexpr int kStagedThreads = kThreads + 32;    // consumer warps + one producer warp
 constexpr int kMaxStages = 8;
 
-template <typename T>
+template <typename T, bool FUSED>
 __device__ __forceinline__ void issue_tile(const CgArgs<T>& a, unsigned char* b, uint64_t* bar, int64_t t, int64_t e0,
                                            int64_t e1, uint64_t stream_pol) {
-  const bool jac = a.dinv != nullptr;
+  const bool jac = !FUSED && a.dinv != nullptr;
   const int ib = a.col16 ? 2 : 4;
   const char* idx = a.col16 ? (const char*)a.col16 : (const char*)a.col;
   const int64_t s0 = t * kTileSlices, s1 = min(s0 + kTileSlices, a.nslices);
   const int64_t row0 = s0 * kSlice;
   const uint32_t rb = (uint32_t)((s1 - s0) * kSlice * (int64_t)sizeof(T));
   const uint32_t ne = (uint32_t)(e1 - e0);
-  mbar_arrive_expect_tx(bar, ne * (uint32_t)(sizeof(T) + ib) + (uint32_t)(a.k + 2 + (jac ? 1 : 0)) * rb);
+  const int own = FUSED ? 4 : 2 + (jac ? 1 : 0);  // own-row vectors staged per tile
+  mbar_arrive_expect_tx(bar, ne * (uint32_t)(sizeof(T) + ib) + (uint32_t)(a.k + own) * rb);
   // the matrix and V_hat are read once per pass: evict-first in L2
   if (ne > 0) {
     bulk_g2s_hint(b, a.val + e0, ne * (uint32_t)sizeof(T), bar, stream_pol);
@@ -710,9 +718,144 @@ __device__ __forceinline__ void issue_tile(const CgArgs<T>& a, unsigned char* b,
   for (int l = 0; l < a.k; ++l)
     bulk_g2s_hint(b + a.off_v + (size_t)l * kTileRows * sizeof(T), a.V + (size_t)l * a.n_pad + row0, rb, bar,
                   stream_pol);
-  bulk_g2s(b + a.off_s, a.s + row0, rb, bar);
-  bulk_g2s(b + a.off_p, a.p_old + row0, rb, bar);
-  if (jac) bulk_g2s(b + a.off_d, a.dinv + row0, rb, bar);
+  if constexpr (FUSED) {
+    bulk_g2s(b + a.off_s, a.r + row0, rb, bar);
+    bulk_g2s(b + a.off_p, a.p_old + row0, rb, bar);
+    bulk_g2s(b + a.off_d, a.q_old + row0, rb, bar);
+    bulk_g2s(b + a.off_z, a.z + row0, rb, bar);
+  } else {
+    bulk_g2s(b + a.off_s, a.s + row0, rb, bar);
+    bulk_g2s(b + a.off_p, a.p_old + row0, rb, bar);
+    if (jac) bulk_g2s(b + a.off_d, a.dinv + row0, rb, bar);
+  }
+}
+
+// ------------------------------------------------------------------ one-kernel CG iteration (variant 8)
+//
+// With M_cg = I the two kernels of a CG iteration fold into one.  Iteration i
+// starts from alpha_{i-1}, beta_{i-1} and c_i (set by the last block of
+// iteration i-1) and forms, for its own rows,
+//   r_i = r_{i-1} - alpha_{i-1} q_{i-1},  z_i = z_{i-1} + alpha_{i-1} p_{i-1},
+//   p_i = r_i + beta_{i-1} p_{i-1},
+// while its SpMV rebuilds p_i at every column it gathers from r_{i-1},
+// q_{i-1} and p_{i-1}, so no grid-wide step separates the vector updates from
+// the product q_i = A p_i + V c_i.  The reduction gives p_i^T q_i,
+// r_i^T q_i, q_i^T q_i, rho_i = r_i^T r_i and V^T A p_i; the last block sets
+// alpha_i = rho_i / p_i^T q_i and
+//   rho_{i+1} = ||r_i - alpha_i q_i||^2 = rho_i - 2 alpha_i r_i^T q_i + alpha_i^2 q_i^T q_i
+// (exact algebra from fresh dot products, so rounding does not carry from one
+// estimate to the next) for the stopping test and beta_i.  r and q ping-pong
+// between two buffers (they are gathered while rewritten); the last z update
+// is left to the finish kernel.
+
+// A p_i of a slice row for the one-kernel iteration: p_i at each column is
+// rebuilt from the gathered r_{i-1}, q_{i-1}, p_{i-1} (8 entries in flight)
+template <typename T, typename I>
+__device__ __forceinline__ T fused_row(const T* vp, const I* cp, int row, bool delta, int w, const T* __restrict__ ro,
+                                       const T* __restrict__ qo, const T* __restrict__ po, T alpha, T beta) {
+  T acc = 0;
+  for (int j0 = 0; j0 < w; j0 += 8) {
+    T av[8];
+    int cc[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      av[j] = (j0 + j < w) ? vp[(j0 + j) * kSlice] : (T)0;
+      cc[j] = (j0 + j < w) ? (delta ? row : 0) + (int)cp[(j0 + j) * kSlice] : row;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (j0 + j < w) {
+        const T rn = __ldg(ro + cc[j]) - alpha * __ldg(qo + cc[j]);
+        acc += av[j] * (rn + beta * __ldg(po + cc[j]));
+      }
+  }
+  return acc;
+}
+
+// Last block of the one-kernel iteration (M_cg = I: s = r).  rho_i = r_i^T r_i
+// is the fresh dot product of this iteration (it sets alpha_i and is the base
+// of the expansion, so the expansion's rounding never accumulates); rho_{i+1}
+// by expansion gives the stopping test and beta_i; then the V^T recurrences.
+template <typename T, int KB, int NW>
+__device__ __forceinline__ void fused_reduce(const CgArgs<T>& a, CgState& S, T pq, T rq, T qq, T rr,
+                                             const T (&wq)[KB > 0 ? KB : 1], const T* cl) {
+  constexpr int KS = KB > 0 ? KB : 1;
+  T part[KB + 4];
+  part[0] = pq;
+  part[1] = rq;
+  part[2] = qq;
+  part[3] = rr;
+#pragma unroll
+  for (int l = 0; l < KB; ++l) part[l + 4] = wq[l];
+  block_partials_t<T, KB + 4, NW>(part, a.k + 4, a.partials);
+  if (last_block_after_partials(&a.st->ticket)) {
+    constexpr int KK = KS * KS;
+    constexpr int NT = NW * 32;
+    constexpr int GPT = (KK + NT - 1) / NT;
+    __shared__ double gs[KK];
+    double greg[GPT];
+    const int kk = a.k * a.k;
+#pragma unroll
+    for (int j = 0; j < GPT; ++j) {
+      const int e = threadIdx.x + j * NT;
+      greg[j] = (e < kk) ? __ldcg(a.gram + e) : 0.0;
+    }
+    __shared__ double tot[KB + 4];
+    final_sums(a.partials, a.k + 4, tot);
+#pragma unroll
+    for (int j = 0; j < GPT; ++j) {
+      const int e = threadIdx.x + j * NT;
+      if (e < kk) gs[e] = greg[j];
+    }
+    __syncthreads();
+    const int l = threadIdx.x;
+    if (l < a.k) {  // V^T q_i = V^T A p_i + (V^T V) c_i
+      double g = tot[l + 4];
+#pragma unroll 8
+      for (int m = 0; m < KB; ++m)
+        if (m < a.k) g += gs[m * a.k + l] * (double)cl[m];
+      S.vq[l] = g;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && *(volatile int*)&S.done == kRunning) {
+      const double kappa = tot[0], rho = tot[3];
+      S.kappa = kappa;
+      if (!isfinite(kappa) || !isfinite(rho)) {
+        S.done = kNonFinite;
+      } else if (kappa <= 0.0) {
+        S.done = kNotSpd;
+      } else {
+        const double alpha = rho / kappa;
+        const double rho_new = rho - 2.0 * alpha * tot[1] + alpha * alpha * tot[2];
+        S.alpha = alpha;
+        S.alpha32 = (float)alpha;
+        S.iters += 1;
+        // z_{i+1} = z_i + alpha_i p_i is done by the next iteration, or by
+        // the finish kernel when this one ends the solve
+        S.fused_pending = 1;
+        S.p_last = a.p_new;
+        const double rnorm = sqrt(rho_new > 0.0 ? rho_new : 0.0);
+        if (!isfinite(rho_new)) {
+          S.done = kNonFinite;
+        } else if (rnorm <= S.tol_abs) {
+          S.done = kConverged;
+        } else if (S.iters >= S.maxit) {
+          S.done = kMaxIter;
+        } else {
+          S.fused_pending = 0;
+          const double beta = rho_new / rho;
+          S.beta = beta;
+          S.beta32 = (float)beta;
+          S.rho = rho_new;
+          for (int m = 0; m < a.k; ++m) {
+            S.u[m] -= alpha * S.vq[m];
+            S.t[m] = S.u[m] + beta * S.t[m];
+          }
+          publish_c(S, a.k);
+        }
+      }
+    }
+  }
 }
 
 // entries of one slice row from a staged tile: values and indices in shared
@@ -761,7 +904,7 @@ __device__ __forceinline__ T finish_row(const T* vp, const I* cp, int row, bool 
   return acc;
 }
 
-template <typename T, int KB, int MB, bool PIPE>
+template <typename T, int KB, int MB, bool PIPE, bool FUSED = false>
 __global__ void __launch_bounds__(kStagedThreads, MB) cg_step_a_staged_kernel(CgArgs<T> a) {
   constexpr int KS = KB > 0 ? KB : 1;
   extern __shared__ __align__(128) unsigned char stage_mem[];
@@ -788,7 +931,7 @@ __global__ void __launch_bounds__(kStagedThreads, MB) cg_step_a_staged_kernel(Cg
     mbar_init_fence();
   }
   __syncthreads();
-  T dot = 0;
+  T dot = 0, rq = 0, qq = 0, rr = 0;
   T wq[KS];
 #pragma unroll
   for (int l = 0; l < KS; ++l) wq[l] = 0;
@@ -817,7 +960,7 @@ __global__ void __launch_bounds__(kStagedThreads, MB) cg_step_a_staged_kernel(Cg
           e1 = a.slice_ptr[min((t + G + 1) * kTileSlices, a.nslices)];
         }
         fence_proxy_async_smem();
-        issue_tile(a, stage_mem + (size_t)st * a.stage_bytes, &full[st], t, c0, c1, stream_pol);
+        issue_tile<T, FUSED>(a, stage_mem + (size_t)st * a.stage_bytes, &full[st], t, c0, c1, stream_pol);
         ++issued;
         if (++st == nst) {
           st = 0;
@@ -827,6 +970,78 @@ __global__ void __launch_bounds__(kStagedThreads, MB) cg_step_a_staged_kernel(Cg
       // no copy may still be writing this block's shared memory when it exits
       for (int64_t j = issued > nst ? issued - nst : 0; j < issued; ++j)
         mbar_wait(&full[j % nst], (uint32_t)((j / nst) & 1));
+    }
+  } else if constexpr (FUSED) {
+    // consumer warps of the one-kernel iteration (M_cg = I): warp w takes slice w of every tile
+    const T alpha = alpha_of(S, T(0));
+    const T* __restrict__ ro = a.r;
+    const T* __restrict__ qo = a.q_old;
+    const T* __restrict__ po = a.p_old;
+    int64_t c_t0 = 0, c_s0 = 0, c_s1 = 0;
+    if (ntl > 0) {
+      const int64_t sl = blockIdx.x * (int64_t)kTileSlices + warp;
+      c_t0 = a.slice_ptr[blockIdx.x * (int64_t)kTileSlices];
+      if (sl < a.nslices) {
+        c_s0 = a.slice_ptr[sl];
+        c_s1 = a.slice_ptr[sl + 1];
+      }
+    }
+    int st = 0;
+    uint32_t ph = 0;
+    int64_t t = blockIdx.x;
+    for (int64_t i = 0; i < ntl; ++i, t += G) {
+      const int64_t sl = t * kTileSlices + warp;
+      const int64_t t0 = c_t0, s0 = c_s0, s1 = c_s1;
+      if (i + 1 < ntl) {
+        const int64_t tn = t + G, sln = tn * kTileSlices + warp;
+        c_t0 = a.slice_ptr[tn * kTileSlices];
+        if (sln < a.nslices) {
+          c_s0 = a.slice_ptr[sln];
+          c_s1 = a.slice_ptr[sln + 1];
+        }
+      }
+      if (!mbar_wait_or_abort(&full[st], ph, &stalled)) break;
+      if (sl < a.nslices) {
+        const unsigned char* b = stage_mem + (size_t)st * a.stage_bytes;
+        const int off = (int)(s0 - t0) + lane;
+        const int w = (int)((s1 - s0) >> 5);
+        const int r = warp * kSlice + lane;
+        const int64_t row = sl * kSlice + lane;
+        const T* vp = reinterpret_cast<const T*>(b) + off;
+        const T ap = a.col16 ? fused_row<T, int16_t>(vp, reinterpret_cast<const int16_t*>(b + a.off_col) + off,
+                                                     (int)row, true, w, ro, qo, po, alpha, beta)
+                             : fused_row<T, int32_t>(vp, reinterpret_cast<const int32_t*>(b + a.off_col) + off,
+                                                     (int)row, false, w, ro, qo, po, alpha, beta);
+        const T r_old = reinterpret_cast<const T*>(b + a.off_s)[r];
+        const T p_old = reinterpret_cast<const T*>(b + a.off_p)[r];
+        const T q_old = reinterpret_cast<const T*>(b + a.off_d)[r];
+        const T z_old = reinterpret_cast<const T*>(b + a.off_z)[r];
+        const T rn = r_old - alpha * q_old;  // r_i
+        const T pn = rn + beta * p_old;      // p_i
+        const T* vt = reinterpret_cast<const T*>(b + a.off_v) + r;
+        T q = ap;
+#pragma unroll
+        for (int l = 0; l < KB; ++l)
+          if (l < a.k) {
+            const T v = vt[l * kTileRows];
+            q += v * cl[l];
+            wq[l] += v * ap;
+          }
+        a.q[row] = q;
+        a.p_new[row] = pn;
+        a.r_new[row] = rn;
+        a.z[row] = z_old + alpha * p_old;
+        dot += pn * q;
+        rq += rn * q;
+        qq += q * q;
+        rr += rn * rn;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[st]);
+      if (++st == nst) {
+        st = 0;
+        ph ^= 1u;
+      }
     }
   } else if constexpr (PIPE) {
     // consumer warps, software-pipelined: while a warp finishes its slice of
@@ -989,7 +1204,8 @@ __global__ void __launch_bounds__(kStagedThreads, MB) cg_step_a_staged_kernel(Cg
   }
   __syncthreads();
   if (threadIdx.x == 0 && stalled) *(volatile int*)&S.done = kStall;
-  step_a_reduce<T, KB, kStagedThreads / 32>(a, S, dot, wq, cl);
+  if constexpr (FUSED) fused_reduce<T, KB, kStagedThreads / 32>(a, S, dot, rq, qq, rr, wq, cl);
+  else step_a_reduce<T, KB, kStagedThreads / 32>(a, S, dot, wq, cl);
 }
 
 // G = V^T M_cg^{-1} V (k x k, both triangles) from the kernels' own V and
@@ -1137,8 +1353,11 @@ __global__ void __launch_bounds__(kThreads) cg_finish_kernel(DevState* st, const
   CgState& S = st->cg;
   const double vn = (S.vnorm > 0.0 && isfinite(S.vnorm)) ? S.vnorm : 0.0;
   double* out = S.zout;
+  // the one-kernel iteration leaves its last z update z += alpha p to this kernel
+  const T* pl = S.fused_pending ? reinterpret_cast<const T*>(S.p_last) : nullptr;
+  const T alpha = alpha_of(S, T(0));
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n_pad; i += (int64_t)gridDim.x * kThreads)
-    out[i] = vn * (double)z[i];
+    out[i] = vn * (double)(pl ? z[i] + alpha * pl[i] : z[i]);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     S.budget -= S.iters;
     OuterState& O = st->out;
@@ -1166,7 +1385,7 @@ namespace {
 
 // stage layout of the staged step a (128-byte aligned regions)
 struct StageGeo {
-  int off_col, off_v, off_s, off_p, off_d, bytes;
+  int off_col, off_v, off_s, off_p, off_d, off_z, bytes;
 };
 
 StageGeo stage_geo(const InnerGraphSpec& spec) {
@@ -1183,7 +1402,9 @@ StageGeo stage_geo(const InnerGraphSpec& spec) {
   g.off_p = (int)o;
   o += kTileRows * w;
   g.off_d = (int)o;
-  if (spec.dinv) o += kTileRows * w;
+  if (spec.dinv || spec.var_a == 8) o += kTileRows * w;  // M_cg^{-1} (Jacobi) or q_{i-1} (one-kernel iteration)
+  g.off_z = (int)o;
+  if (spec.var_a == 8) o += kTileRows * w;  // z (one-kernel iteration)
   g.bytes = o > (1 << 30) ? (1 << 30) : (int)o;
   return g;
 }
@@ -1203,6 +1424,7 @@ void make_args(const InnerGraphSpec& spec, CgArgs<T> (&a)[2]) {
     x.off_s = geo.off_s;
     x.off_p = geo.off_p;
     x.off_d = geo.off_d;
+    x.off_z = geo.off_z;
     x.st = spec.st;
     x.partials = spec.partials;
     x.slice_ptr = spec.A.slice_ptr;
@@ -1222,6 +1444,15 @@ void make_args(const InnerGraphSpec& spec, CgArgs<T> (&a)[2]) {
     x.q = reinterpret_cast<T*>(spec.q);
     x.p_old = reinterpret_cast<T*>(par == 0 ? spec.p0 : spec.p1);
     x.p_new = reinterpret_cast<T*>(par == 0 ? spec.p1 : spec.p0);
+    x.r_new = nullptr;
+    x.q_old = nullptr;
+    if (spec.var_a == 8) {  // one-kernel iteration: r and q ping-pong as p does
+      x.r = reinterpret_cast<T*>(par == 0 ? spec.r : spec.r2);
+      x.r_new = reinterpret_cast<T*>(par == 0 ? spec.r2 : spec.r);
+      x.q = reinterpret_cast<T*>(par == 0 ? spec.q : spec.q2);
+      x.q_old = reinterpret_cast<T*>(par == 0 ? spec.q2 : spec.q);
+      x.s = x.r;
+    }
   }
 }
 
@@ -1247,6 +1478,7 @@ const void* step_a_fn(int var) {
     case 5: return (const void*)cg_step_a_staged_kernel<T, KB, 2, false>;
     case 6: return (const void*)cg_step_a_staged_kernel<T, KB, 4, false>;
     case 7: return (const void*)cg_step_a_staged_kernel<T, KB, 2, true>;
+    case 8: return (const void*)cg_step_a_staged_kernel<T, KB, 3, false, true>;
     default: return (const void*)cg_step_a_kernel<T, KB, 0>;
   }
 }
@@ -1341,6 +1573,10 @@ cudaError_t build_graph_t(const InnerGraphSpec& spec, cudaGraph_t* out_graph) {
       if ((e = add_kernel(body, &na, prev ? &prev : nullptr, prev ? 1 : 0, step_a_fn<T, KB>(spec.var_a),
                           spec.grid_spmv, step_a_block(spec), aa, smem_a)))
         goto fail;
+      if (spec.var_a == 8) {  // the one-kernel iteration has no step b
+        prev = na;
+        continue;
+      }
       if ((e = add_kernel(body, &nb, &na, 1, step_b_fn<T, KB>(spec), spec.grid_stream_b, kThreads,
                           aa)))
         goto fail;
@@ -1378,7 +1614,7 @@ cudaError_t run_host_t(const InnerGraphSpec& spec, cudaStream_t stream, int* h_d
   for (;;) {
     for (int it = 0; it < spec.unroll; ++it) {
       launch_a<T>(step_a_fn<T, KB>(spec.var_a), spec.grid_spmv, step_a_block(spec), stream, a[it & 1], smem_a);
-      launch_b<T, KB>(spec, stream, a[it & 1]);
+      if (spec.var_a != 8) launch_b<T, KB>(spec, stream, a[it & 1]);
     }
     cg_ctl_host_kernel<<<1, 1, 0, stream>>>(spec.st);
     if ((e = cudaMemcpyAsync(h_done, &spec.st->cg.done, sizeof(int), cudaMemcpyDeviceToHost, stream))) return e;
@@ -1405,7 +1641,7 @@ cudaError_t time_t(const InnerGraphSpec& spec, int iters, cudaStream_t stream, d
   for (int it = 0; it < iters; ++it) {
     launch_a<T>(step_a_fn<T, KB>(spec.var_a), spec.grid_spmv, step_a_block(spec), stream, a[it & 1], smem_a);
     cudaEventRecord(ev[2 * it + 1], stream);
-    launch_b<T, KB>(spec, stream, a[it & 1]);
+    if (spec.var_a != 8) launch_b<T, KB>(spec, stream, a[it & 1]);
     cudaEventRecord(ev[2 * it + 2], stream);
   }
   cudaError_t e = cudaStreamSynchronize(stream);

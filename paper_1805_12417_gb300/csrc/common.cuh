@@ -22,7 +22,7 @@ constexpr int kSlice = 32;      // SELL slice height = warp width
 constexpr int kMaxK = 32;       // maximum columns of V_hat
 constexpr int kThreads = 256;   // block size of every streaming kernel
 constexpr int kMaxBlocks = 2048;
-constexpr int kMaxNV = kMaxK + 2;  // reduction values per block
+constexpr int kMaxNV = kMaxK + 4;  // reduction values per block
 
 // inner CG outcome codes (CgState::done)
 // (kStall: a staged copy did not arrive within its wait limit; reported as a CUDA error)
@@ -61,6 +61,11 @@ struct CgState {
   int unroll;            // CG iterations per body of the device while loop
   const double* vin;     // right-hand side of the inner solve (FP64)
   double* zout;          // its solution (FP64)
+  // one-kernel iteration (identity M_cg): its last z update z += alpha p is
+  // left to the finish kernel when the solve stops (fused_pending, p_last)
+  int fused_pending;
+  int pad_f;
+  const void* p_last;
 };
 
 struct OuterState {

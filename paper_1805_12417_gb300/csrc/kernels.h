@@ -25,12 +25,15 @@ struct InnerGraphSpec {
   void* p0 = nullptr;
   void* p1 = nullptr;
   void* q = nullptr;
+  void* r2 = nullptr;  // second r and q buffers of the one-kernel iteration (variant 8, M_cg = I)
+  void* q2 = nullptr;
   int grid_spmv = 1, grid_stream = 1, grid_stream_b = 1;
   int unroll = 4;  // CG iterations per body of the while loop (even)
   int var_a = 0;   // step-a kernel variant (0: early V loads, 1: late V loads, 2: two slices per warp,
                  // 3 / 4: late V loads with registers capped for 6 / 8 blocks per SM,
                  // 5 / 6: operands staged in shared memory by bulk copies, registers capped for
-                 // 2 / 4 blocks per SM; 7: as 5 with the gathers issued one tile ahead)
+                 // 2 / 4 blocks per SM; 7: as 5 with the gathers issued one tile ahead;
+                 // 8: the whole CG iteration in one staged kernel, M_cg = I only)
   int64_t tile_entries = 0;  // most SELL entries in one tile of 8 slices (sizes the staged variant's buffers)
   int stages = 3;            // staged variant: shared-memory stages per block
   bool stall_test = false;   // test hook: the staged producer issues only the first tile

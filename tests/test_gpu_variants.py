@@ -169,3 +169,71 @@ def test_staged_full_size_mixed(shape_env):
     x = x.cpu().numpy()
     assert info.status == m.OK
     assert O.System.from_problem(p).true_relres(p.b, x) <= 1e-10
+
+
+# ---------------------------------------------------------------- variant 8: the one-kernel iteration (M_cg = I)
+
+@pytest.mark.parametrize("stages", [2, 3])
+@pytest.mark.parametrize("prec", [m.FP64, m.MIXED_FP32], ids=["fp64", "mixed"])
+def test_one_kernel_iteration_small_3d(shape_env, stages, prec):
+    """z += alpha p, r -= alpha q and the next direction fold into the SpMV
+    kernel; rho_{i+1} comes from the expansion rho - 2 alpha r^T q + alpha^2 q^T q."""
+    shape_env(8, stages)
+    _inner_vs_oracle(small_3d(), prec, m.MCG_IDENTITY, 1e-6 if prec == m.FP64 else 1e-4, 4, 8, stages,
+                     idx_bytes=2)
+
+
+@pytest.mark.parametrize("k", [0, 1, 10, 13, 17, 32])
+def test_one_kernel_iteration_k_buckets(shape_env, k):
+    shape_env(8, 2)
+    if k == 0:
+        from gen import laplacian_csr
+        rp, ci, va = laplacian_csr((13, 11, 9), sigma=-0.5)
+        _inner_vs_oracle(None, m.FP64, m.MCG_IDENTITY, 1e-8, 1, 8, 2, sysargs=(rp, ci, va))
+        return
+    p = shifted_laplacian_problem("t", (13, 11, 9), k, seed=k)
+    _inner_vs_oracle(p, m.FP64, m.MCG_IDENTITY, 1e-8, k, 8, 2)
+    _inner_vs_oracle(p, m.MIXED_FP32, m.MCG_IDENTITY, 1e-4, k, 8, 2)
+
+
+def test_one_kernel_iteration_budget_and_long_rows(shape_env):
+    """The last z update is left to the finish kernel: an iteration cap must
+    still return z_m (compared with the oracle's m-step iterate), also on rows
+    longer than the stencil's and with 32-bit indices."""
+    shape_env(8, 2, idx16=False)
+    n = 3001
+    rp, ci, va = random_sparse_symmetric(n, 21, density_rows=(2, 12), diag_shift=30.0, empty_rows=0)
+    s = O.System(rp, ci, va)
+    y = np.random.default_rng(9).standard_normal(n)
+    for m_it in (1, 2, 5, 9):
+        zr, itr, st_r = s.cg(y, 1e-300, m_it, O.MCG_IDENTITY)
+        with m.Solver(n, rp, ci, va, validate=False) as g:
+            _check_cfg(g, 8, 2, 4)
+            z, st, it = g.inner_solve(y, inner_tol=1e-12, max_iters=m_it)
+        assert st == m.ERR_MAXITER and it == m_it
+        assert np.linalg.norm(z - zr) <= 1e-10 * np.linalg.norm(zr)
+
+
+def test_one_kernel_iteration_falls_back_without_identity(shape_env):
+    shape_env(8, 2)
+    with m.Solver.from_problem(small_3d(), inner_prec=m.MCG_JACOBI) as g:
+        assert m.launch_config(g.h)["step_a_variant"] == 0
+
+
+def test_one_kernel_iteration_full_solves(shape_env):
+    shape_env(8, 3)
+    p = small_3d()
+    ref = O.minres_cg(O.System.from_problem(p), p.b, outer_tol=1e-12, inner_tol=1e-3)
+    with m.Solver.from_problem(p) as g:
+        _check_cfg(g, 8, 3)
+        x, info = g.solve(p.b.copy(), outer_tol=1e-12, inner_tol=1e-3)
+    assert info.status == m.OK
+    assert np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x) <= 1e-8
+    p = config2()
+    with m.Solver.from_problem(p, precision=m.MIXED_FP32) as g:
+        _check_cfg(g, 8, 3)
+        x = torch.zeros(p.n, dtype=torch.float64, device=DEV)
+        _, info = g.solve(torch.from_numpy(p.b).to(DEV), x, outer_tol=1e-10, inner_tol=1e-3)
+    assert info.status == m.OK
+    assert O.System.from_problem(p).true_relres(p.b, x.cpu().numpy()) <= 1e-10
+
