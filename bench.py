@@ -231,8 +231,8 @@ def cpu_baseline(p, n_full_fallback):
 def run_reference(args, ws, rank):
     if rank != 0:
         return
-    from gen import config2
-    p = config2()
+    from gen import lap3d_128_k10
+    p = lap3d_128_k10()
     vals = []
     for i in range(args.warmup + args.steps):
         cb = cpu_baseline(p, 2303)
@@ -256,7 +256,7 @@ def run_batch64(args, ws, rank, local):
     one batched solve of all 64 systems."""
     import torch
 
-    from gen import config4
+    from gen import batch64_lap2d
     from paper_1805_12417_gb300 import build as _b
     _b.build()
     import paper_1805_12417_gb300 as m
@@ -264,7 +264,7 @@ def run_batch64(args, ws, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    ps = config4()
+    ps = batch64_lap2d()
     B = np.concatenate([p.b for p in ps])
     Bd = torch.from_numpy(B).to(dev)
     Xd = torch.zeros_like(Bd)
@@ -339,7 +339,7 @@ def run_shifted64(args, ws, rank, local):
     right-hand-side block; a step is one solve of all 64 columns."""
     import torch
 
-    from gen import config5
+    from gen import shifted_lap3d_160
     from paper_1805_12417_gb300 import build as _b
     _b.build()
     import paper_1805_12417_gb300 as m
@@ -347,7 +347,7 @@ def run_shifted64(args, ws, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    fam = config5()
+    fam = shifted_lap3d_160()
     Bd = torch.from_numpy(fam.B).to(dev)
     Xd = torch.zeros_like(Bd)
     out = {}
@@ -432,7 +432,7 @@ def main():
         return
     import torch
 
-    from gen import config1, config2, config2_near, config3
+    from gen import lap2d_64_k4, lap3d_128_k10, lap3d_128_k10_near, saddle_96_b20x64
     from paper_1805_12417_gb300 import build as _b
     _b.build()
     import paper_1805_12417_gb300 as m
@@ -442,19 +442,19 @@ def main():
     stream = torch.cuda.current_stream(dev)
     workload = WORKLOAD
     if args.workload == "saddle":
-        p = config3()
+        p = saddle_96_b20x64()
         workload = ("saddle_96^3_B20x64: [K B^T; B 0], K 27-pt log-normal(0,1) SPD stencil on 96^3, B 20 rows x 64 "
                     "uniform[-1,1] entries (n=884,756, 20 negative eigenvalues), seed 2, 1 RHS")
     elif args.workload == "lap2d_64":
-        p = config1()
+        p = lap2d_64_k4()
         workload = ("lap2d_64x64_k4: 2D 5-pt Laplacian 64^2 (n=4,096) shifted to 4 negative eigenvalues, 1 RHS; "
                     "L2-resident and latency-bound: read solves/s and launches per solve, not the HBM fraction")
     elif args.workload == "lap3d_128_near":
-        p = config2_near()
+        p = lap3d_128_k10_near()
         workload = ("lap3d_128^3_k10_near: the lap3d_128 matrix with sigma at lambda_10 + 0.05 (lambda_11 - "
                     "lambda_10), so the 10 negative eigenvalues are the smallest in modulus, 1 RHS")
     else:
-        p = config2()
+        p = lap3d_128_k10()
     b_dev = torch.from_numpy(p.b).to(dev)
     x_dev = torch.zeros(p.n, dtype=torch.float64, device=dev)
     mcg = {"identity": m.MCG_IDENTITY, "jacobi": m.MCG_JACOBI, "smw": m.MCG_SMW}[args.mcg]

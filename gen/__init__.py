@@ -15,15 +15,15 @@ from .problems import (  # noqa: F401
     random_indefinite_dense,
     dense_to_csr,
     random_sparse_symmetric,
-    config1,
-    config2,
-    config2_near,
-    config4,
-    config5,
+    lap2d_64_k4,
+    lap3d_128_k10,
+    lap3d_128_k10_near,
+    batch64_lap2d,
+    shifted_lap3d_160,
     ShiftedFamily,
     shifted_family,
     small_shifted,
     small_3d,
-    CONFIGS,
+    WORKLOADS,
 )
-from .saddle import config3, saddle_problem, small_saddle  # noqa: F401,E402
+from .saddle import saddle_96_b20x64, saddle_problem, small_saddle  # noqa: F401,E402

@@ -179,18 +179,18 @@ def shifted_laplacian_problem(name, dims, k_wanted, seed, xstar=None, sigma_frac
     return Problem(name, n, rowptr, colind, val, k, V, lam, xstar, b, sigma, meta)
 
 
-def config1() -> Problem:
+def lap2d_64_k4() -> Problem:
     """2D 5-point Laplacian 64x64 (n=4096), 4 negative eigenvalues, seed 0."""
     return shifted_laplacian_problem("lap2d_64x64_k4", (64, 64), 4, seed=0)
 
 
-def config2() -> Problem:
+def lap3d_128_k10() -> Problem:
     """3D 7-point Laplacian 128^3 (n=2,097,152), 10 negative eigenvalues, seed 1."""
     return shifted_laplacian_problem("lap3d_128^3_k10", (128, 128, 128), 10, seed=1)
 
 
-def config2_near() -> Problem:
-    """Config 2's matrix with sigma moved to lambda_10 + 0.05 (lambda_11 - lambda_10):
+def lap3d_128_k10_near() -> Problem:
+    """The lap3d_128_k10 matrix with sigma moved to lambda_10 + 0.05 (lambda_11 - lambda_10):
     the 10 negative eigenvalues are the ones closest to zero (where the
     MINRES-CG* inner preconditioner of Sec. 2.1 pays off)."""
     return shifted_laplacian_problem("lap3d_128^3_k10_near", (128, 128, 128), 10, seed=1, sigma_frac=0.05)
@@ -224,9 +224,9 @@ def dense_to_csr(A: np.ndarray):
     return M.indptr.astype(np.int64), M.indices.astype(np.int32), M.data.astype(np.float64)
 
 
-CONFIGS = {
-    "lap2d_64x64_k4": config1,
-    "lap3d_128^3_k10": config2,
+WORKLOADS = {
+    "lap2d_64x64_k4": lap2d_64_k4,
+    "lap3d_128^3_k10": lap3d_128_k10,
 }
 
 
@@ -264,7 +264,7 @@ def random_sparse_symmetric(n: int, seed: int, density_rows=(0, 70), diag_shift:
     return M.indptr.astype(np.int64), M.indices.astype(np.int32), M.data.astype(np.float64)
 
 
-def config4(count: int = 64, sides=(100, 400), kmax: int = 16, seed: int = 3):
+def batch64_lap2d(count: int = 64, sides=(100, 400), kmax: int = 16, seed: int = 3):
     """Batch of independent 2D 5-point Laplacian systems of uneven size.
 
     For each system i: square side m_i ~ U{sides}, then k_i ~ U{1..kmax}
@@ -359,7 +359,7 @@ def shifted_family(dims, nshift, nrhs, kmax_draw, seed, name="shifted"):
                          np.ascontiguousarray(B), xs)
 
 
-def config5():
+def shifted_lap3d_160():
     """3D 7-point Laplacian 160^3, 16 shifts with k_j ~ U{1..30} (seed 4), 4 RHS each."""
     return shifted_family((160, 160, 160), 16, 4, 30, seed=4, name="lap3d_160^3_16shifts_x4")
 

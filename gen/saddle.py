@@ -149,7 +149,7 @@ def saddle_problem(m: int, nb: int = 20, nnzb: int = 64, seed: int = 2, shift: f
                    A.data.astype(np.float64), nb, V, lam, xstar, b, 0.0, meta)
 
 
-def config3() -> Problem:
+def saddle_96_b20x64() -> Problem:
     """[K B^T; B 0], K 27-point log-normal on 96^3 (n = 884,756), B 20 x 64, seed 2."""
     return saddle_problem(96, 20, 64, seed=2, name="saddle_96^3_B20x64")
 

@@ -14,14 +14,14 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 
 import oracle as O  # noqa: E402
-from gen import config1, config2  # noqa: E402
+from gen import lap2d_64_k4, lap3d_128_k10  # noqa: E402
 
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "full_solve_counts.json")
 
 
 def main():
     rec = {}
-    for make in (config1, config2):
+    for make in (lap2d_64_k4, lap3d_128_k10):
         p = make()
         s = O.System.from_problem(p)
         for outer_tol, inner_tol in ((1e-10, 1e-3),):

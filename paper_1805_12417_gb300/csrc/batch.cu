@@ -1,5 +1,5 @@
 // Batched MINRES-CG: many independent systems of uneven size in one launch
-// sequence (north star, batching of independent systems).
+// sequence (the paper's many-systems-after-one-setup use, Sec. 2-3).
 //
 // The systems are concatenated block-diagonally: one SELL-32 matrix with
 // global column indices, every system padded to whole slices, each with its

@@ -25,8 +25,8 @@ if ROOT not in sys.path:
 
 
 def workload(name):
-    from gen import config1, config2, small_3d
-    return {"lap3d_128": config2, "lap2d_64": config1, "lap3d_small": small_3d}[name]()
+    from gen import lap2d_64_k4, lap3d_128_k10, small_3d
+    return {"lap3d_128": lap3d_128_k10, "lap2d_64": lap2d_64_k4, "lap3d_small": small_3d}[name]()
 
 
 def main(argv=None):

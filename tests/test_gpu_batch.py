@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from gen import config4, laplacian_csr, shifted_laplacian_problem, small_3d
+from gen import batch64_lap2d, laplacian_csr, shifted_laplacian_problem, small_3d
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -116,10 +116,10 @@ def test_batch_per_system_edge_cases():
         assert inf4[0].status == m.ERR_NONFINITE and inf4[2].status == m.OK
 
 
-def test_config4_batch_mixed():
+def test_batch64_lap2d_mixed():
     """64 uneven 2D systems (sides 100..400, k_i up to 17): every system reaches
     FP64 true relative residual 1e-10 in one batched solve."""
-    ps = config4()
+    ps = batch64_lap2d()
     B = np.concatenate([p.b for p in ps])
     with m.Batch(ps, precision=m.MIXED_FP32, validate=False) as bt:
         Bd = torch.from_numpy(B).to(DEV)

@@ -16,7 +16,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from gen import (config1, config2, dense_to_csr, laplacian_csr, random_sparse_symmetric, shifted_laplacian_problem,
+from gen import (lap2d_64_k4, lap3d_128_k10, dense_to_csr, laplacian_csr, random_sparse_symmetric, shifted_laplacian_problem,
                  small_3d)
 
 torch = pytest.importorskip("torch")
@@ -149,7 +149,7 @@ def _solve_both(p, prec=m.FP64, mcg=m.MCG_IDENTITY, outer_tol=1e-12, inner_tol=1
     return ref, x, info
 
 
-@pytest.mark.parametrize("prob", [config1, small_3d, lambda: shifted_laplacian_problem("t", (45, 37), 6, seed=11)],
+@pytest.mark.parametrize("prob", [lap2d_64_k4, small_3d, lambda: shifted_laplacian_problem("t", (45, 37), 6, seed=11)],
                          ids=["lap2d_64x64_k4", "lap3d_12x11x10_k5", "lap2d_45x37_k6"])
 @pytest.mark.parametrize("device", [True, False], ids=["device_ptrs", "host_ptrs"])
 def test_solve_fp64_matches_oracle(prob, device):
@@ -175,7 +175,7 @@ def test_solve_jacobi_matches_oracle():
 
 
 def test_solve_mixed_reaches_fp64_residual():
-    p = config1()
+    p = lap2d_64_k4()
     ref, x, info = _solve_both(p, prec=m.MIXED_FP32, outer_tol=1e-10)
     assert info.status == m.OK
     rr = host_relres(p, x)
@@ -242,7 +242,7 @@ def test_create_rejects_bad_inputs():
 
 @pytest.fixture(scope="module")
 def big():
-    return config2()
+    return lap3d_128_k10()
 
 
 def test_full_size_mmr_and_spmv(big):

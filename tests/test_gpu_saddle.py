@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from gen import config3, small_saddle
+from gen import saddle_96_b20x64, small_saddle
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -42,10 +42,10 @@ def test_small_saddle_mmr_product():
 
 @pytest.fixture(scope="module")
 def big():
-    return config3()
+    return saddle_96_b20x64()
 
 
-def test_config3_eigenpairs(big):
+def test_saddle_96_eigenpairs(big):
     p = big
     assert p.k == 20 and p.n == 96 ** 3 + 20
     assert np.all(p.lam < 0)
@@ -53,7 +53,7 @@ def test_config3_eigenpairs(big):
 
 
 @pytest.mark.parametrize("prec", [m.FP64, m.MIXED_FP32], ids=["fp64", "mixed"])
-def test_config3_solve(big, prec):
+def test_saddle_96_solve(big, prec):
     """Full-size saddle system at the benchmark tolerance: FP64 true residual
     recomputed on the host and the error against x*."""
     p = big

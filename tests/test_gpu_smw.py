@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from gen import config2, dense_to_csr, random_sparse_symmetric, shifted_laplacian_problem, small_3d
+from gen import lap3d_128_k10, dense_to_csr, random_sparse_symmetric, shifted_laplacian_problem, small_3d
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -147,7 +147,7 @@ def test_smw_indefinite_diagonal_runs_or_reports():
 def test_smw_full_size_mixed():
     """128^3 shifted Laplacian, mixed precision, MINRES-CG*: the FP64 true
     residual reaches the benchmark tolerance."""
-    p = config2()
+    p = lap3d_128_k10()
     with m.Solver.from_problem(p, precision=m.MIXED_FP32, inner_prec=m.MCG_SMW) as g:
         x = torch.zeros(p.n, dtype=torch.float64, device=DEV)
         _, info = g.solve(torch.from_numpy(p.b).to(DEV), x, outer_tol=1e-10, inner_tol=1e-3)

@@ -21,7 +21,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from gen import config2, random_sparse_symmetric, shifted_laplacian_problem, small_3d
+from gen import lap3d_128_k10, random_sparse_symmetric, shifted_laplacian_problem, small_3d
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -161,7 +161,7 @@ def test_staged_full_size_mixed(shape_env):
     """128^3 shifted Laplacian, mixed precision, staged step a with 3 stages:
     the FP64 true residual reaches the benchmark tolerance."""
     shape_env(5, 3)
-    p = config2()
+    p = lap3d_128_k10()
     with m.Solver.from_problem(p, precision=m.MIXED_FP32) as g:
         _check_cfg(g, 5, 3)
         x = torch.zeros(p.n, dtype=torch.float64, device=DEV)
@@ -229,7 +229,7 @@ def test_one_kernel_iteration_full_solves(shape_env):
         x, info = g.solve(p.b.copy(), outer_tol=1e-12, inner_tol=1e-3)
     assert info.status == m.OK
     assert np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x) <= 1e-8
-    p = config2()
+    p = lap3d_128_k10()
     with m.Solver.from_problem(p, precision=m.MIXED_FP32) as g:
         _check_cfg(g, 8, 3)
         x = torch.zeros(p.n, dtype=torch.float64, device=DEV)

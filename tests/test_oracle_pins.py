@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from gen import (config1, dense_to_csr, laplacian_csr, laplacian_smallest_eigs, random_indefinite_dense,
+from gen import (lap2d_64_k4, dense_to_csr, laplacian_csr, laplacian_smallest_eigs, random_indefinite_dense,
                  shifted_laplacian_problem)
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -322,9 +322,9 @@ def test_minres_cg_dense_solution():
     assert np.isclose(r.true_relres, np.linalg.norm(b - A @ r.x) / np.linalg.norm(b), rtol=1e-6)
 
 
-def test_minres_cg_config1_matches_xstar():
+def test_minres_cg_lap2d_64_matches_xstar():
     """64x64 shifted Laplacian (4 negatives): x* is recovered to kappa * tol."""
-    p = config1()
+    p = lap2d_64_k4()
     s = O.System.from_problem(p)
     r = O.minres_cg(s, p.b, outer_tol=1e-12, inner_tol=1e-3)
     assert r.status == O.OK and r.true_relres <= 1e-12
@@ -444,7 +444,7 @@ def test_generator_tie_rounding():
 
 
 def test_generator_is_reproducible():
-    a, b = config1(), config1()
+    a, b = lap2d_64_k4(), lap2d_64_k4()
     assert np.array_equal(a.b, b.b) and np.array_equal(a.V, b.V) and a.sigma == b.sigma
 
 
