@@ -453,9 +453,6 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
   if (const char* e = getenv("MRCG_BPSM_B")) occ_b = std::max(1, std::min(occ_b, atoi(e)));
   g.grid_spmv = grid_a(g, occ_a);
   g.grid_stream_b = clamp_grid(want_b, occ_b);
-  // ---- launch-shape autotuner: step-a variant (and stages) with its blocks
-  // per SM, then step-b blocks per SM, timed on this matrix (standalone
-  // launches, medians of a few iterations)
   // MRCG_SHAPE_F32 / MRCG_SHAPE_F64 = "variant,stages,grid_a,grid_b" replays a
   // shape a previous run reported (mrcg_launch_config), e.g. under a profiler,
   // whose slowed launches would mislead the timing below
@@ -476,6 +473,10 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
       }
     }
   }
+  // ---- launch-shape autotuner: step-a variant (and stages) with its blocks
+  // per SM, then step-b blocks per SM, then the one-kernel iteration against
+  // the best pair, timed on this matrix (standalone launches, medians of a few
+  // iterations)
   const char* at = getenv("MRCG_AUTOTUNE");
   const bool tune = (!at || atoi(at) != 0) && n_pad >= (1 << 12) && !getenv("MRCG_BPSM_A") &&
                     !getenv("MRCG_BPSM_B") && !getenv("MRCG_VAR_A") && !fixed;
