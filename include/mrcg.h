@@ -104,7 +104,8 @@ typedef struct {
  * rows, column-major within a slice) with FP64 values and, in mixed mode, an
  * FP32 copy of A and V_hat.
  * Errors: MRCG_ERR_INVALID (bad sizes, unsorted or out-of-range columns,
- * lambda >= 0, a V_hat that fails validation), MRCG_ERR_OOM, MRCG_ERR_CUDA. */
+ * lambda >= 0, a V_hat that fails validation, a zero diagonal entry of A with
+ * MRCG_MCG_SMW), MRCG_ERR_OOM, MRCG_ERR_CUDA. */
 mrcg_status mrcg_solver_create(const mrcg_create_args* args, mrcg_handle* out);
 
 /* Solve A x = b by MINRES-CG (Algorithm 1).  On entry x holds x0, on exit the
