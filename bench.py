@@ -210,15 +210,23 @@ def full_solve_inner_iters(name):
         return None
 
 
-def cpu_baseline(p, n_full_fallback):
-    """The oracle as it stands (serial C, FP64) on the first CPU_SAMPLE_ITERS
-    inner iterations of this workload's solve, scaled to one full solve."""
+def cpu_baseline(p, n_full_fallback, mcg=0):
+    """The oracle as it stands (serial C, FP64) with the same inner
+    preconditioner: a whole solve for small workloads (up to 100,000 rows),
+    else its first CPU_SAMPLE_ITERS inner iterations scaled to one full solve."""
     import oracle as O
     s = O.System.from_problem(p)
+    if p.n <= 100_000:
+        t = time.perf_counter()
+        r = O.minres_cg(s, p.b, outer_tol=OUTER_TOL, inner_tol=INNER_TOL, mcg=mcg)
+        dt = time.perf_counter() - t
+        return {"value": 1.0 / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                "sample": f"one full FP64 oracle solve ({r.inner_iters_total} inner iterations, {dt:.2f} s)",
+                "seconds": round(dt, 3)}
     t = time.perf_counter()
-    r = O.minres_cg(s, p.b, outer_tol=OUTER_TOL, inner_tol=INNER_TOL, max_iters=CPU_SAMPLE_ITERS)
+    r = O.minres_cg(s, p.b, outer_tol=OUTER_TOL, inner_tol=INNER_TOL, max_iters=CPU_SAMPLE_ITERS, mcg=mcg)
     dt = time.perf_counter() - t
-    n_full = full_solve_inner_iters(p.name) or n_full_fallback
+    n_full = (full_solve_inner_iters(p.name) if mcg == 0 else None) or n_full_fallback
     frac = r.inner_iters_total / n_full
     return {"value": frac / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
             "sample": f"first {r.inner_iters_total} inner CG iterations of the FP64 oracle solve ({dt:.1f} s), "
@@ -560,7 +568,7 @@ def main():
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(p, inf_64[-1].inner_iters_total)
+        cpu = cpu_baseline(p, inf_64[-1].inner_iters_total, mcg)
 
     if rank == 0:
         line = {
