@@ -456,6 +456,27 @@ __global__ void b_ctl_kernel(DevState* st, int nsys, int* ctl, cudaGraphConditio
   }
 }
 
+// the same loop control for the host-driven loop (profiling mode): the
+// decision goes to ctl[2] for the host to read instead of a graph condition
+__global__ void b_ctl_host_kernel(DevState* st, int nsys, int* ctl) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < nsys; i += blockDim.x)
+    if (in_round(st[i]) && st[i].cg.done == kRunning) atomicOr(&any, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ctl[0] += 1;
+    int go = any;
+    if (go && ctl[0] >= ctl[1]) {
+      go = 0;
+      for (int i = 0; i < nsys; ++i)
+        if (in_round(st[i]) && st[i].cg.done == kRunning) st[i].cg.done = kLoopCap;
+    }
+    ctl[2] = go;
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads) b_finish_kernel(DevState* st, const SysDesc* sys, const Chunk* chunks,
                                                               int nc, const T* z) {
@@ -811,6 +832,46 @@ fail:
   return e;
 }
 
+// The graph's launch sequence driven from the host: after every U iterations
+// the host reads the loop decision.  Used when a profiler must see the
+// individual kernels (kernel nodes under a conditional node cannot be profiled).
+template <typename T, int KB>
+cudaError_t run_host(const GraphSpec& gs, cudaStream_t stream) {
+  BArgs<T> a[2];
+  make_bargs(gs, a);
+  const T* zc = reinterpret_cast<const T*>(gs.z);
+  b_ctl_reset_kernel<<<1, 1, 0, stream>>>(gs.ctl);
+  b_vnorm_kernel<<<gs.grid, kThreads, 0, stream>>>(gs.st, gs.sys, gs.chunks, gs.nc, gs.partials);
+  b_init_kernel<T, KB><<<gs.grid, kThreads, 0, stream>>>(a[0]);
+  cudaError_t e = cudaSuccess;
+  for (;;) {
+    for (int it = 0; it < gs.unroll; ++it) {
+      b_step_a_kernel<T, KB><<<gs.grid, kThreads, 0, stream>>>(a[it & 1]);
+      b_step_b_kernel<T, KB><<<gs.grid_b, kThreads, 0, stream>>>(a[it & 1]);
+    }
+    b_ctl_host_kernel<<<1, 256, 0, stream>>>(gs.st, gs.nsys, gs.ctl);
+    int go = 0;
+    if ((e = cudaMemcpyAsync(&go, gs.ctl + 2, sizeof(int), cudaMemcpyDeviceToHost, stream))) return e;
+    if ((e = cudaStreamSynchronize(stream))) return e;
+    if (!go) break;
+  }
+  b_finish_kernel<T><<<gs.grid, kThreads, 0, stream>>>(gs.st, gs.sys, gs.chunks, gs.nc, zc);
+  return cudaGetLastError();
+}
+
+cudaError_t run_host_any(const GraphSpec& gs, cudaStream_t stream) {
+  if (gs.fp32) {
+    if (gs.kb == 0) return run_host<float, 0>(gs, stream);
+    if (gs.kb == 8) return run_host<float, 8>(gs, stream);
+    if (gs.kb == 16) return run_host<float, 16>(gs, stream);
+    return run_host<float, 32>(gs, stream);
+  }
+  if (gs.kb == 0) return run_host<double, 0>(gs, stream);
+  if (gs.kb == 8) return run_host<double, 8>(gs, stream);
+  if (gs.kb == 16) return run_host<double, 16>(gs, stream);
+  return run_host<double, 32>(gs, stream);
+}
+
 cudaError_t build_graph_any(const GraphSpec& gs, cudaGraph_t* out) {
   if (gs.fp32) {
     if (gs.kb == 0) return build_graph<float, 0>(gs, out);
@@ -890,6 +951,8 @@ struct mrcg_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int grid = 1, grid_b = 1, unroll = 4;
+  bool host_loop = false;  // MRCG_INNER_LOOP=host: inner loop driven from the host (for profilers)
+  GraphSpec gs;
   std::vector<void*> allocs;
 };
 
@@ -1126,7 +1189,7 @@ mrcg_status batch_create_impl(int32_t nsys, const mrcg_create_args* args, mrcg_b
   BST(balloc(h, &h->d_st, (size_t)nsys));
   BST(balloc(h, &h->d_partials, (size_t)kMaxNV * h->nc));
   BST(balloc(h, &h->d_modes, (size_t)nsys));
-  BST(balloc(h, &h->d_ctl, 2));
+  BST(balloc(h, &h->d_ctl, 3));
   BCK(cudaMemcpyAsync(h->d_sys, h->h_sys.data(), nsys * sizeof(SysDesc), cudaMemcpyHostToDevice, h->stream));
   BCK(cudaMemcpyAsync(h->d_chunks, h->h_chunks.data(), h->nc * sizeof(Chunk), cudaMemcpyHostToDevice, h->stream));
   BCK(cudaMemsetAsync(h->d_st, 0, nsys * sizeof(DevState), h->stream));
@@ -1163,6 +1226,8 @@ mrcg_status batch_create_impl(int32_t nsys, const mrcg_create_args* args, mrcg_b
   gs.grid = h->grid;
   gs.grid_b = h->grid_b;
   gs.unroll = h->unroll;
+  h->gs = gs;
+  if (const char* m = getenv("MRCG_INNER_LOOP")) h->host_loop = std::strcmp(m, "host") == 0;
   BCK(build_graph_any(gs, &h->graph));
   BCK(cudaGraphInstantiate(&h->exec, h->graph, 0));
   BCK(cudaStreamSynchronize(h->stream));
@@ -1300,7 +1365,8 @@ mrcg_status batched_solve_impl(mrcg_batch* h, const double* B, double* X, double
     b_lanczos_spmv_kernel<<<g, kThreads, 0, h->stream>>>(oa);
     b_lanczos_update_kernel<<<g, kThreads, 0, h->stream>>>(oa);
     BCK(cudaGetLastError());
-    BCK(cudaGraphLaunch(h->exec, h->stream));
+    if (h->host_loop) BCK(run_host_any(h->gs, h->stream));
+    else BCK(cudaGraphLaunch(h->exec, h->stream));
     b_gamma_kernel<<<g, kThreads, 0, h->stream>>>(oa);
     b_minres_update_kernel<<<g, kThreads, 0, h->stream>>>(oa);
     b_residual_kernel<<<g, kThreads, 0, h->stream>>>(oa, 0);

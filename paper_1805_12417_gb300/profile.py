@@ -31,10 +31,12 @@ def workload(name):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="lap3d_128", choices=["lap3d_128", "lap2d_64", "lap3d_small"])
+    ap.add_argument("--workload", default="lap3d_128", choices=["lap3d_128", "lap2d_64", "lap3d_small", "batch64"],
+                    help="batch64: one batched solve of the 64 uneven 2D systems with the inner loop driven from "
+                         "the host (MRCG_INNER_LOOP=host), so a profiler sees the batch kernels")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--iters", type=int, default=3)
-    ap.add_argument("--var-a", type=int, default=None, help="step-a kernel variant (0-7)")
+    ap.add_argument("--var-a", type=int, default=None, help="step-a kernel variant (0-8)")
     ap.add_argument("--bpsm-a", type=int, default=None, help="step-a blocks per SM")
     ap.add_argument("--bpsm-b", type=int, default=None, help="step-b blocks per SM")
     a = ap.parse_args(argv)
@@ -43,8 +45,19 @@ def main(argv=None):
         if val is not None:
             os.environ[key] = str(val)
     import paper_1805_12417_gb300 as m
-    p = workload(a.workload)
     prec = m.MIXED_FP32 if a.precision == "mixed" else m.FP64
+    if a.workload == "batch64":
+        import numpy as np
+        from gen import batch64_lap2d
+        os.environ["MRCG_INNER_LOOP"] = "host"
+        ps = batch64_lap2d()
+        B = np.concatenate([q.b for q in ps])
+        with m.Batch(ps, precision=prec, validate=False) as bt:
+            X, st, infos = bt.solve(B.copy(), outer_tol=1e-10, max_iters=a.iters * 100)
+        print(json.dumps({"workload": "batch64", "precision": a.precision, "status": int(st),
+                          "inner_iters": int(sum(i.inner_iters_total for i in infos))}))
+        return
+    p = workload(a.workload)
     with m.Solver.from_problem(p, precision=prec, validate=False) as s:
         ta, tb = m.time_inner_kernels(s.h, a.iters)
         cfg = m.launch_config(s.h)

@@ -80,6 +80,24 @@ def test_batch_matches_single_system_solver():
         assert abs(inf.inner_iters_total - i1.inner_iters_total) <= 2 * max(1, i1.outer_iters)
 
 
+@pytest.mark.parametrize("prec", [m.FP64, m.MIXED_FP32], ids=["fp64", "mixed"])
+def test_batch_host_driven_loop_is_identical(prec, monkeypatch):
+    """MRCG_INNER_LOOP=host (the profiling mode) runs the graph's kernels in the
+    same order from a host loop: bitwise the same solutions and counts."""
+    ps = _small_batch()
+    B = np.concatenate([p.b for p in ps])
+    out = []
+    for mode in (None, "host"):
+        if mode:
+            monkeypatch.setenv("MRCG_INNER_LOOP", mode)
+        with m.Batch(ps, precision=prec) as bt:
+            X, st, infos = bt.solve(B.copy(), outer_tol=1e-10)
+        out.append((X, st, [(i.outer_iters, i.inner_iters_total) for i in infos]))
+    assert out[0][1] == out[1][1] == m.OK
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][2] == out[1][2]
+
+
 def test_batch_mixed_reaches_fp64_residual():
     ps = _small_batch()
     B = np.concatenate([p.b for p in ps])
