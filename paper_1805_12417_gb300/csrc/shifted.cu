@@ -831,24 +831,38 @@ __global__ void __launch_bounds__(kThreads) sh_scalar_kernel(DevState* st, const
   }
 }
 
-// loop control: ctl[0] executed bodies, ctl[1] their limit
-__global__ void sh_ctl_kernel(DevState* st, int nc, int* ctl, cudaGraphConditionalHandle handle) {
+// loop control: ctl[0] executed bodies, ctl[1] their limit.  Returns (in
+// thread 0) whether another body runs; at the limit the still-running columns
+// are stopped with kLoopCap.
+__device__ int sh_ctl_decide(DevState* st, int nc, int* ctl) {
   __shared__ int any;
   if (threadIdx.x == 0) any = 0;
   __syncthreads();
   for (int i = threadIdx.x; i < nc; i += blockDim.x)
     if (in_round(st[i]) && st[i].cg.done == kRunning) atomicOr(&any, 1);
   __syncthreads();
+  int go = 0;
   if (threadIdx.x == 0) {
     ctl[0] += 1;
-    int go = any;
+    go = any;
     if (go && ctl[0] >= ctl[1]) {
       go = 0;
       for (int i = 0; i < nc; ++i)
         if (in_round(st[i]) && st[i].cg.done == kRunning) st[i].cg.done = kLoopCap;
     }
-    cudaGraphSetConditional(handle, go ? 1u : 0u);
   }
+  return go;
+}
+
+__global__ void sh_ctl_kernel(DevState* st, int nc, int* ctl, cudaGraphConditionalHandle handle) {
+  const int go = sh_ctl_decide(st, nc, ctl);
+  if (threadIdx.x == 0) cudaGraphSetConditional(handle, go ? 1u : 0u);
+}
+
+// the host-driven loop (profiling mode) reads the decision from ctl[2]
+__global__ void sh_ctl_host_kernel(DevState* st, int nc, int* ctl) {
+  const int go = sh_ctl_decide(st, nc, ctl);
+  if (threadIdx.x == 0) ctl[2] = go;
 }
 
 __global__ void sh_ctl_reset_kernel(int* ctl) { ctl[0] = 0; }
@@ -942,6 +956,56 @@ fail:
   return e;
 }
 
+// The graph's launch sequence driven from the host: after every U iterations
+// the host reads the loop decision.  Used when a profiler must see the
+// individual kernels (kernel nodes under a conditional node cannot be profiled).
+template <typename T, int NM, int KV>
+cudaError_t run_host(const GSpec& gs, const SArgs<T>& base, cudaStream_t stream) {
+  SArgs<T> a[2] = {base, base};
+  a[1].p_old = base.p_new;
+  a[1].p_new = base.p_old;
+  DevState* st = gs.st;
+  const int* kcol = gs.kcol;
+  int nc = gs.nc, ncp = gs.ncp, nblk = gs.grid;
+  const double* partials = gs.partials;
+  int* ctl = gs.ctl;
+  int op_v = kOpVnorm, op_i = kOpInit, op_a = kOpA, op_b = kOpB, op_f = kOpFinish;
+  int nv1 = 1, nvk = KV + 1;
+  void* r_args[] = {&ctl};
+  void* row0[] = {&a[0]};
+  void* sv_args[] = {&st, (void*)&kcol, &nc, &ncp, (void*)&partials, &nblk, &op_v, &nv1};
+  void* si_args[] = {&st, (void*)&kcol, &nc, &ncp, (void*)&partials, &nblk, &op_i, &nvk};
+  void* sa_args[] = {&st, (void*)&kcol, &nc, &ncp, (void*)&partials, &nblk, &op_a, &nv1};
+  void* sb_args[] = {&st, (void*)&kcol, &nc, &ncp, (void*)&partials, &nblk, &op_b, &nvk};
+  void* sf_args[] = {&st, (void*)&kcol, &nc, &ncp, (void*)&partials, &nblk, &op_f, &nv1};
+  void* ctl_args[] = {&st, &nc, &ctl};
+  auto go = [&](const void* fn, int grid, int block, void** args) {
+    return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, 0, stream);
+  };
+  cudaError_t e;
+  if ((e = go((const void*)sh_ctl_reset_kernel, 1, 1, r_args))) return e;
+  if ((e = go((const void*)sh_vnorm_kernel<T, NM, KV>, gs.grid, kThreads, row0))) return e;
+  if ((e = go((const void*)sh_scalar_kernel, nc, kThreads, sv_args))) return e;
+  if ((e = go((const void*)sh_init_kernel<T, NM, KV>, gs.grid, kThreads, row0))) return e;
+  if ((e = go((const void*)sh_scalar_kernel, nc, kThreads, si_args))) return e;
+  for (;;) {
+    for (int it = 0; it < gs.unroll; ++it) {
+      void* aa[] = {&a[it & 1]};
+      if ((e = go((const void*)sh_step_a_kernel<T, NM, KV>, gs.grid, kThreads, aa))) return e;
+      if ((e = go((const void*)sh_scalar_kernel, nc, kThreads, sa_args))) return e;
+      if ((e = go((const void*)sh_step_b_kernel<T, NM, KV>, gs.grid, kThreads, aa))) return e;
+      if ((e = go((const void*)sh_scalar_kernel, nc, kThreads, sb_args))) return e;
+    }
+    if ((e = go((const void*)sh_ctl_host_kernel, 1, 256, ctl_args))) return e;
+    int more = 0;
+    if ((e = cudaMemcpyAsync(&more, ctl + 2, sizeof(int), cudaMemcpyDeviceToHost, stream))) return e;
+    if ((e = cudaStreamSynchronize(stream))) return e;
+    if (!more) break;
+  }
+  if ((e = go((const void*)sh_finish_kernel<T, NM>, gs.grid, kThreads, row0))) return e;
+  return go((const void*)sh_scalar_kernel, nc, kThreads, sf_args);
+}
+
 template <typename T, int NM, int KV>
 int occupancy_t() {
   int a = 1, b = 1, i = 1;
@@ -994,6 +1058,8 @@ struct mrcg_shifted {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int grid = 1, unroll = 4;
+  bool host_loop = false;  // MRCG_INNER_LOOP=host: inner loop driven from the host (for profilers)
+  GSpec gs = {};
   std::vector<void*> allocs;
 };
 
@@ -1085,9 +1151,24 @@ mrcg_status build_t(mrcg_shifted* h, int nsm) {
   gs.kv = KV;
   gs.partials = h->d_partials;
   gs.ctl = h->d_ctl;
+  h->gs = gs;
   const cudaError_t e = build_graph<T, NM, KV>(gs, sargs<T>(h), &h->graph);
   SCK(e);
   return MRCG_OK;
+}
+
+template <typename T, int NM, int KV>
+cudaError_t run_host_t(mrcg_shifted* h) {
+  return run_host<T, NM, KV>(h->gs, sargs<T>(h), h->stream);
+}
+
+cudaError_t run_host_any(mrcg_shifted* h) {
+  if (h->fp32) {
+    if (h->nm == 1) return h->kv == 8 ? run_host_t<float, 1, 8>(h) : run_host_t<float, 1, 32>(h);
+    return h->kv == 8 ? run_host_t<float, 2, 8>(h) : run_host_t<float, 2, 32>(h);
+  }
+  if (h->nm == 1) return h->kv == 8 ? run_host_t<double, 1, 8>(h) : run_host_t<double, 1, 32>(h);
+  return h->kv == 8 ? run_host_t<double, 2, 8>(h) : run_host_t<double, 2, 32>(h);
 }
 
 mrcg_status build_any(mrcg_shifted* h, int nsm) {
@@ -1214,7 +1295,8 @@ mrcg_status shifted_create_impl(const mrcg_create_args* L, int32_t nshift, const
   }
   SST(salloc(h, &h->d_st, (size_t)h->nc));
   SST(salloc(h, &h->d_modes, (size_t)h->nc));
-  SST(salloc(h, &h->d_ctl, 2));
+  SST(salloc(h, &h->d_ctl, 3));
+  if (const char* m = getenv("MRCG_INNER_LOOP")) h->host_loop = std::strcmp(m, "host") == 0;
   SCK(cudaMemsetAsync(h->d_st, 0, h->nc * sizeof(DevState), h->stream));
   SCK(cudaMallocHost(&h->h_st, h->nc * sizeof(DevState)));
   SCK(cudaMallocHost(&h->h_init, h->nc * sizeof(DevState)));
@@ -1375,7 +1457,8 @@ mrcg_status shifted_solve_impl(mrcg_shifted* h, const double* B, double* X, doub
     scalar(h, kOpDelta);
     outer(h, 4, oa);
     SCK(cudaGetLastError());
-    SCK(cudaGraphLaunch(h->exec, h->stream));
+    if (h->host_loop) SCK(run_host_any(h));
+    else SCK(cudaGraphLaunch(h->exec, h->stream));
     outer(h, 5, oa);
     scalar(h, kOpGamma);
     outer(h, 6, oa);

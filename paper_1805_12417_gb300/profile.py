@@ -31,9 +31,10 @@ def workload(name):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="lap3d_128", choices=["lap3d_128", "lap2d_64", "lap3d_small", "batch64"],
-                    help="batch64: one batched solve of the 64 uneven 2D systems with the inner loop driven from "
-                         "the host (MRCG_INNER_LOOP=host), so a profiler sees the batch kernels")
+    ap.add_argument("--workload", default="lap3d_128", choices=["lap3d_128", "lap2d_64", "lap3d_small", "batch64", "shifted64"],
+                    help="batch64: one batched solve of the 64 uneven 2D systems; shifted64: one solve of a "
+                         "64^3 Laplacian family (16 shifts, k_j up to 30, 4 right-hand sides each); both with the "
+                         "inner loop driven from the host (MRCG_INNER_LOOP=host), so a profiler sees their kernels")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--iters", type=int, default=3)
     ap.add_argument("--var-a", type=int, default=None, help="step-a kernel variant (0-8)")
@@ -55,6 +56,15 @@ def main(argv=None):
         with m.Batch(ps, precision=prec, validate=False) as bt:
             X, st, infos = bt.solve(B.copy(), outer_tol=1e-10, max_iters=a.iters * 100)
         print(json.dumps({"workload": "batch64", "precision": a.precision, "status": int(st),
+                          "inner_iters": int(sum(i.inner_iters_total for i in infos))}))
+        return
+    if a.workload == "shifted64":
+        from gen import shifted_family
+        os.environ["MRCG_INNER_LOOP"] = "host"
+        fam = shifted_family((64, 64, 64), 16, 4, 30, seed=4, name="lap3d_64^3_16shifts_x4")
+        with m.Shifted(fam, precision=prec) as sh:
+            X, st, infos = sh.solve(fam.B.copy(), outer_tol=1e-10, max_iters=a.iters * 100)
+        print(json.dumps({"workload": "shifted64", "precision": a.precision, "status": int(st),
                           "inner_iters": int(sum(i.inner_iters_total for i in infos))}))
         return
     p = workload(a.workload)

@@ -88,3 +88,23 @@ def test_shifted_matches_batch_of_separate_systems(fam):
         X, st2, _ = sh.solve(fam.B.copy(), outer_tol=1e-12)
     for c in range(fam.ncols):
         assert np.linalg.norm(X[:, c] - xb[c]) <= 1e-8 * np.linalg.norm(xb[c])
+
+
+@pytest.mark.parametrize("prec", [m.FP64, m.MIXED_FP32], ids=["fp64", "mixed"])
+def test_shifted_host_driven_loop_is_identical(fam, prec, monkeypatch):
+    """MRCG_INNER_LOOP=host (the profiling mode) runs the graph's kernels in the
+    same order from a host loop: bitwise the same solutions, counts and
+    statuses, including a run stopped by the iteration budget."""
+    out = []
+    for mode in (None, "host"):
+        if mode:
+            monkeypatch.setenv("MRCG_INNER_LOOP", mode)
+        with m.Shifted(fam, precision=prec) as sh:
+            X, st, infos = sh.solve(fam.B.copy(), outer_tol=1e-10)
+            X5, st5, inf5 = sh.solve(fam.B.copy(), outer_tol=1e-12, max_iters=5)
+        out.append((X, st, [(i.outer_iters, i.inner_iters_total, i.status) for i in infos],
+                    X5, st5, [(i.inner_iters_total, i.status) for i in inf5]))
+    (a, b) = out
+    assert a[1] == b[1] == m.OK and a[4] == b[4] == m.ERR_MAXITER
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[3], b[3])
+    assert a[2] == b[2] and a[5] == b[5]
