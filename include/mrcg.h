@@ -9,8 +9,9 @@
  * negative eigenvalues) is applied approximately by an inner CG solve of
  * M_mr z = y (Eq. 2, Algorithm 1).  The solve stage is the third of the
  * paper's three stages (Sec. 2, "In summary ..."): the caller supplies the
- * eigenpairs (stage two); the inner preconditioner M_cg is the identity or
- * Jacobi (stage one, see mrcg_inner_prec).
+ * eigenpairs (stage two); the inner preconditioner M_cg is the identity,
+ * Jacobi or the MINRES-CG* preconditioner of Sec. 2.1 (stage one, see
+ * mrcg_inner_prec).
  *
  * Conventions for every entry point:
  *  - Status codes are returned; nothing is thrown across the ABI.
@@ -23,6 +24,32 @@
  *  - A handle is used by one host thread at a time.
  *  - CSR inputs: full symmetric storage, int64 row pointers (rowptr[0] = 0),
  *    int32 column indices in [0, n), float64 values.
+ *
+ * Environment variables, read when a handle is created (none is needed; the
+ * defaults are the tuned path):
+ *  - MRCG_AUTOTUNE=0      skip the launch-shape autotuner of mrcg_solver_create
+ *                         (it runs for n_pad >= 4096) and keep the default shape.
+ *  - MRCG_SHAPE_F32 / MRCG_SHAPE_F64 = "variant,stages,grid_a,grid_b"
+ *                         replay a shape reported by mrcg_launch_config (for
+ *                         profilers, whose slowed launches mislead the tuner);
+ *                         ignored when the shape does not fit the matrix.
+ *  - MRCG_VAR_A (0-8), MRCG_STAGES (2-8), MRCG_BPSM_A, MRCG_BPSM_B
+ *                         fix the step-a variant, its pipeline depth and the
+ *                         blocks per SM of the two inner kernels; any of them
+ *                         turns the autotuner off.
+ *  - MRCG_IDX16=0         keep 32-bit column indices in the inner kernels
+ *                         (16-bit deltas are used whenever |col - row| <= 32767).
+ *  - MRCG_UNROLL=U        inner iterations per convergence check (even, >= 2).
+ *  - MRCG_INNER_LOOP=host drive the inner loop from the host instead of a
+ *                         conditional CUDA graph, so that a profiler sees each
+ *                         kernel; results are bitwise the same.  All three
+ *                         handle kinds.
+ *  - MRCG_DEBUG           print failed CUDA calls and the tuner's choice to
+ *                         stderr.
+ *  - MRCG_TEST_STALL=1    test hook: the producer warp of the staged step-a
+ *                         kernels (variants 5-7) stops after the first tile, the
+ *                         consumers' bounded waits give up and the call returns
+ *                         MRCG_ERR_CUDA; the context stays usable.
  */
 #ifndef MRCG_H
 #define MRCG_H
