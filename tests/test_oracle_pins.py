@@ -80,6 +80,32 @@ def test_mmr_flop_count():
     assert fl == 2 * p.nnz + 4 * p.k * p.n + p.k
 
 
+def test_mmr_independent_of_basis_within_a_cluster():
+    """M_mr depends on the negative invariant subspace, not on its basis
+    (Sec. 2): rotating V_hat within a degenerate eigenvalue cluster and
+    flipping column signs leaves every product unchanged, while mixing two
+    columns of different eigenvalues changes it."""
+    p = shifted_laplacian_problem("t", (9, 9), 3, seed=0)  # lambda_2 = lambda_3: modes (1,2), (2,1)
+    assert p.k == 3 and p.lam[1] == p.lam[2] and p.lam[0] != p.lam[1]
+    u = np.random.default_rng(8).standard_normal((p.n, 4))
+    ref = O.System.from_problem(p)
+
+    def mixed(i, j, t, flip):
+        V = p.V.copy()
+        c, sn = np.cos(t), np.sin(t)
+        V[:, [i, j]] = p.V[:, [i, j]] @ np.array([[c, -sn], [sn, c]])
+        V[:, flip] *= -1.0
+        return O.System(p.rowptr, p.colind, p.val, V, p.lam)
+
+    for t in (0.3, 1.1, 2.9):
+        s = mixed(1, 2, t, 0)
+        for col in u.T:
+            y0 = ref.mmr_apply(col)
+            assert np.linalg.norm(s.mmr_apply(col) - y0) <= 1e-13 * np.linalg.norm(y0)
+    bad = mixed(0, 1, 0.3, 2)
+    assert np.linalg.norm(bad.mmr_apply(u[:, 0]) - ref.mmr_apply(u[:, 0])) > 1e-3 * np.linalg.norm(u[:, 0])
+
+
 def test_mmr_diag():
     A, Vn, lam, d, Q, s = dense_system(25, 3, 8)
     M = dense_op(s.mmr_apply, 25)
