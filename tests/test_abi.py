@@ -77,3 +77,30 @@ def test_binding_struct_layout_matches_header(cname, pyname):
     cf = _c_struct_fields(cname)
     pf = [f[0].rstrip("_") for f in getattr(m, pyname)._fields_]
     assert cf == pf
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No fallback: without libmrcg.so every entry point raises."""
+    import numpy as np
+
+    import paper_1805_12417_gb300 as m
+    monkeypatch.setattr(m, "LIB_PATH", str(tmp_path / "libmrcg.so"))
+    monkeypatch.setattr(m, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        m.lib()
+    with pytest.raises(RuntimeError, match="not built"):
+        m.solver_create(1, np.array([0, 1], np.int64), np.array([0], np.int32), np.array([2.0]))
+
+
+def test_product_package_never_reaches_the_oracle():
+    """The package (binding, build, profiling driver, CUDA sources) neither
+    imports nor links anything under oracle/."""
+    pkg = os.path.join(ROOT, "paper_1805_12417_gb300")
+    hits = []
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                src = open(os.path.join(dirpath, f)).read()
+                if re.search(r"\boracle\b|mrcg_oracle|orc_", src):
+                    hits.append(f)
+    assert hits == []
