@@ -10,8 +10,8 @@ import numpy as np
 import pytest
 
 import oracle as O
-from gen import (lap2d_64_k4, dense_to_csr, laplacian_csr, laplacian_smallest_eigs, random_indefinite_dense,
-                 shifted_laplacian_problem)
+from gen import (batch64_lap2d, lap2d_64_k4, dense_to_csr, laplacian_csr, laplacian_smallest_eigs,
+                 random_indefinite_dense, shifted_family, shifted_laplacian_problem)
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -467,6 +467,44 @@ def test_generator_tie_rounding():
     assert np.isclose(ev[0][0], 2 * (2 - 2 * np.cos(np.pi / 65)))
     assert np.isclose(p.sigma, 0.5 * (laplacian_smallest_eigs((5, 5, 5), 5)[3][0] +
                                       laplacian_smallest_eigs((5, 5, 5), 5)[4][0]))
+
+
+def test_shifted_family_columns_are_the_stated_systems():
+    """Every column c = j * nrhs + r of a shifted family is (L - sigma_j I) x = b
+    with exactly k_j negative eigenvalues (dense eigvalsh), sigma_j midway
+    between eigenvalues k_j and k_j + 1 of L, V_hat_j / Lambda_hat_j its
+    negative eigenpairs, and b = A x*."""
+    fam = shifted_family((6, 5, 4), 3, 2, 8, seed=9)
+    rp, ci, va = laplacian_csr((6, 5, 4))
+    L = np.zeros((fam.n, fam.n))
+    for i in range(fam.n):
+        L[i, ci[rp[i]:rp[i + 1]]] = va[rp[i]:rp[i + 1]]
+    wL = np.linalg.eigvalsh(L)
+    assert np.allclose(fam.lamL, wL[:len(fam.lamL)], atol=1e-12)
+    assert fam.ncols == 6 and fam.B.shape == (fam.n, 6)
+    for c in range(fam.ncols):
+        j = c // fam.nrhs
+        p = fam.column_problem(c)
+        A = p.dense()
+        assert np.allclose(A, L - fam.sigma[j] * np.eye(fam.n), atol=0)
+        w = np.linalg.eigvalsh(A)
+        kj = int(fam.k[j])
+        assert p.k == kj and int(np.sum(w < 0)) == kj
+        assert np.isclose(fam.sigma[j], 0.5 * (wL[kj - 1] + wL[kj]), rtol=0, atol=1e-12)
+        assert np.abs(A @ p.V - p.V * p.lam).max() <= 1e-12
+        assert np.allclose(A @ fam.xstar[:, c], fam.B[:, c], atol=1e-13)
+
+
+def test_batch_generator_draws_squares_and_rounded_k():
+    """Uneven batch: square sides in the stated range, k_i raised to the end of
+    its cluster (exactly k_i negative analytic eigenvalues), one RHS each."""
+    ps = batch64_lap2d(count=6, sides=(8, 14), kmax=6, seed=3)
+    for p in ps:
+        m_ = int(round(np.sqrt(p.n)))
+        assert m_ * m_ == p.n and 8 <= m_ <= 14
+        w = np.linalg.eigvalsh(p.dense())
+        assert int(np.sum(w < 0)) == p.k and 1 <= p.k
+        assert p.xstar is None and p.b.shape == (p.n,) and np.all(np.abs(p.b) <= 1.0)
 
 
 def test_generator_is_reproducible():
