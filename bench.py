@@ -31,6 +31,10 @@ import numpy as np  # noqa: E402
 
 METRIC = "solves/s & SpMV HBM GB/s at true rel. residual 1e-10, mixed vs FP64, 1xGB300"
 WORKLOAD = "lap3d_128^3_k10: 3D 7-pt Laplacian 128^3 (n=2,097,152) shifted to 10 negative eigenvalues, 1 RHS"
+BATCH_WORKLOAD = ("batch64: 64 x 2D 5-pt Laplacian, sides U{100..400}, k_i U{1..16} (cluster-rounded), "
+                  "RHS uniform[-1,1], seed 3, one batched solve per step")
+SHIFTED_WORKLOAD = ("shifted64: 3D 7-pt Laplacian 160^3 (n=4,096,000), 16 shifts with k_j U{1..30} "
+                    "cluster-rounded (seed 4), 4 RHS each, one 64-column block")
 OUTER_TOL, INNER_TOL = 1e-10, 1e-3
 CPU_SAMPLE_ITERS = 120  # inner iterations of the oracle's solve timed for the CPU baseline
 
@@ -200,57 +204,127 @@ def measured_peak_gbs():
         return 6800.0, "fallback"
 
 
-def full_solve_inner_iters(name):
+def full_solve_inner_iters(name, mcg="identity"):
+    """Inner iterations of a whole FP64 oracle solve, as recorded by
+    oracle/record_counts.py (None when that workload was not recorded)."""
     path = os.path.join(ROOT, "oracle", "full_solve_counts.json")
+    k = f"{name}|outer={OUTER_TOL:g}|inner={INNER_TOL:g}" + ("" if mcg == "identity" else f"|mcg={mcg}")
     try:
         with open(path) as f:
             rec = json.load(f)
-        return int(rec[f"{name}|outer={OUTER_TOL:g}|inner={INNER_TOL:g}"]["inner_iters_total"])
+        return int(rec[k]["inner_iters_total"])
     except Exception:
         return None
 
 
-def cpu_baseline(p, n_full_fallback, mcg=0):
+def single_system(name):
+    """(problem, description) of a single-system workload."""
+    from gen import lap2d_64_k4, lap3d_128_k10, lap3d_128_k10_near, saddle_96_b20x64
+    if name == "saddle":
+        return saddle_96_b20x64(), (
+            "saddle_96^3_B20x64: [K B^T; B 0], K 27-pt log-normal(0,1) SPD stencil on 96^3, B 20 rows x 64 "
+            "uniform[-1,1] entries (n=884,756, 20 negative eigenvalues), seed 2, 1 RHS")
+    if name == "lap2d_64":
+        return lap2d_64_k4(), (
+            "lap2d_64x64_k4: 2D 5-pt Laplacian 64^2 (n=4,096) shifted to 4 negative eigenvalues, 1 RHS; "
+            "L2-resident and latency-bound: read solves/s and launches per solve, not the HBM fraction")
+    if name == "lap3d_128_near":
+        return lap3d_128_k10_near(), (
+            "lap3d_128^3_k10_near: the lap3d_128 matrix with sigma at lambda_10 + 0.05 (lambda_11 - "
+            "lambda_10), so the 10 negative eigenvalues are the smallest in modulus, 1 RHS")
+    return lap3d_128_k10(), WORKLOAD
+
+
+def cpu_baseline(p, mcg="identity"):
     """The oracle as it stands (serial C, FP64) with the same inner
     preconditioner: a whole solve for small workloads (up to 100,000 rows),
-    else its first CPU_SAMPLE_ITERS inner iterations scaled to one full solve."""
+    else its first CPU_SAMPLE_ITERS inner iterations scaled to one full solve
+    by the oracle's own recorded count (value None when none is recorded)."""
     import oracle as O
+    code = {"identity": O.MCG_IDENTITY, "jacobi": O.MCG_JACOBI, "smw": O.MCG_SMW}[mcg]
     s = O.System.from_problem(p)
     if p.n <= 100_000:
         t = time.perf_counter()
-        r = O.minres_cg(s, p.b, outer_tol=OUTER_TOL, inner_tol=INNER_TOL, mcg=mcg)
+        r = O.minres_cg(s, p.b, outer_tol=OUTER_TOL, inner_tol=INNER_TOL, mcg=code)
         dt = time.perf_counter() - t
         return {"value": 1.0 / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
                 "sample": f"one full FP64 oracle solve ({r.inner_iters_total} inner iterations, {dt:.2f} s)",
                 "seconds": round(dt, 3)}
     t = time.perf_counter()
-    r = O.minres_cg(s, p.b, outer_tol=OUTER_TOL, inner_tol=INNER_TOL, max_iters=CPU_SAMPLE_ITERS, mcg=mcg)
+    r = O.minres_cg(s, p.b, outer_tol=OUTER_TOL, inner_tol=INNER_TOL, max_iters=CPU_SAMPLE_ITERS, mcg=code)
     dt = time.perf_counter() - t
-    n_full = (full_solve_inner_iters(p.name) if mcg == 0 else None) or n_full_fallback
-    frac = r.inner_iters_total / n_full
-    return {"value": frac / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {r.inner_iters_total} inner CG iterations of the FP64 oracle solve ({dt:.1f} s), "
-                      f"scaled by the {n_full} inner iterations of a full oracle solve",
+    n_full = full_solve_inner_iters(p.name, mcg)
+    head = f"first {r.inner_iters_total} inner CG iterations of the FP64 oracle solve ({dt:.1f} s)"
+    if n_full is None:
+        return {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle", "seconds": round(dt, 2),
+                "sample": head + "; no whole oracle solve of this workload is recorded to scale them by"}
+    return {"value": r.inner_iters_total / n_full / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": head + f", scaled by the {n_full} inner iterations of a whole oracle solve",
             "seconds": round(dt, 2)}
+
+
+def cpu_baseline_batch(ps, budget_s=20.0):
+    """The oracle on an uneven batch: whole solves of the systems in batch
+    order until budget_s has passed (at least one); solves/s of that sample."""
+    import oracle as O
+    t0 = time.perf_counter()
+    done, iters = 0, 0
+    for p in ps:
+        r = O.minres_cg(O.System.from_problem(p), p.b, outer_tol=OUTER_TOL, inner_tol=INNER_TOL)
+        done += 1
+        iters += r.inner_iters_total
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "solves/s", "cores": 1, "kind": "oracle", "seconds": round(dt, 2),
+            "sample": f"whole FP64 oracle solves of the first {done} of {len(ps)} systems in batch order "
+                      f"({sum(p.n for p in ps[:done])} rows, {iters} inner iterations, {dt:.1f} s)"}
+
+
+def cpu_baseline_shifted(fam):
+    """The oracle on one column of a shifted family: its first
+    CPU_SAMPLE_ITERS inner iterations.  A whole solve of one column takes tens
+    of minutes, so no count is recorded and the value is None."""
+    import oracle as O
+    p = fam.column_problem(0)
+    t = time.perf_counter()
+    r = O.minres_cg(O.System.from_problem(p), p.b, outer_tol=OUTER_TOL, inner_tol=INNER_TOL,
+                    max_iters=CPU_SAMPLE_ITERS)
+    dt = time.perf_counter() - t
+    return {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle", "seconds": round(dt, 2),
+            "sample": f"first {r.inner_iters_total} inner CG iterations of the FP64 oracle solve of column 0 "
+                      f"({dt:.1f} s, {dt / max(1, r.inner_iters_total) * 1e3:.0f} ms per iteration); no whole "
+                      f"oracle solve of a column is recorded to scale them by"}
 
 
 # ------------------------------------------------------------------ reference arm (the oracle)
 
 def run_reference(args, ws, rank):
+    """The oracle, as it stands, on this arm's workload: each step is one
+    bounded sample (cpu_baseline*)."""
     if rank != 0:
         return
-    from gen import lap3d_128_k10
-    p = lap3d_128_k10()
+    if args.workload == "batch64":
+        from gen import batch64_lap2d
+        ps = batch64_lap2d()
+        sample, desc = (lambda: cpu_baseline_batch(ps)), BATCH_WORKLOAD
+    elif args.workload == "shifted64":
+        from gen import shifted_lap3d_160
+        fam = shifted_lap3d_160()
+        sample, desc = (lambda: cpu_baseline_shifted(fam)), SHIFTED_WORKLOAD
+    else:
+        p, desc = single_system(args.workload)
+        sample = lambda: cpu_baseline(p, args.mcg)  # noqa: E731
     vals = []
     for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(p, 2303)
+        cb = sample()
         if i >= args.warmup:
             vals.append(cb["value"])
-    v = statistics.mean(vals)
+    v = None if any(x is None for x in vals) else statistics.mean(vals)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "outer_tol": OUTER_TOL, "inner_tol": INNER_TOL,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": (1000.0 / v) if v else None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "inner_prec": args.mcg, "outer_tol": OUTER_TOL, "inner_tol": INNER_TOL,
                        "parallelism": "rank 0 only (CPU oracle)"},
             "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": cb["sample"]},
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -328,8 +402,7 @@ def run_batch64(args, ws, rank, local):
                 "warmup": args.warmup, "ms_per_step": mx["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner CG + f64 outer MINRES",
                 "data": "synthetic",
-                "config": {"workload": "batch64: 64 x 2D 5-pt Laplacian, sides U{100..400}, k_i U{1..16} "
-                                       "(cluster-rounded), RHS uniform[-1,1], seed 3, one batched solve per step",
+                "config": {"workload": BATCH_WORKLOAD,
                            "systems": len(ps), "rows": int(len(B)), "outer_tol": OUTER_TOL, "inner_tol": INNER_TOL,
                            "l2": "inputs larger than L2", "parallelism": "replicas" if ws > 1 else "single GPU"},
                 "roofline": {"kernel": "whole inner loop (batched step a + step b)", "bound": "hbm",
@@ -338,7 +411,7 @@ def run_batch64(args, ws, rank, local):
                              "peak_kind": f"{kind} copy bandwidth"},
                 "fp64": out["fp64"], "mixed": mx, "mixed_vs_fp64_speedup": mx["value"] / out["fp64"]["value"],
                 "e2e": out["e2e"], "gpu_launches": int(mx["launches"] * args.steps), "clocks": mx["clocks"],
-                "cpu_baseline": None}
+                "cpu_baseline": cpu_baseline_batch(ps) if (ws == 1 and not args.no_cpu_baseline) else None}
         print(json.dumps(line), flush=True)
 
 
@@ -412,8 +485,7 @@ def run_shifted64(args, ws, rank, local):
                 "warmup": args.warmup, "ms_per_step": mx["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner CG + f64 outer MINRES",
                 "data": "synthetic",
-                "config": {"workload": "shifted64: 3D 7-pt Laplacian 160^3 (n=4,096,000), 16 shifts with k_j "
-                                       "U{1..30} cluster-rounded (seed 4), 4 RHS each, one 64-column block",
+                "config": {"workload": SHIFTED_WORKLOAD,
                            "columns": nc, "outer_tol": OUTER_TOL, "inner_tol": INNER_TOL,
                            "l2": "inputs larger than L2", "parallelism": "replicas" if ws > 1 else "single GPU"},
                 "roofline": {"kernel": "whole inner loop (block step a + step b)", "bound": "hbm",
@@ -422,7 +494,7 @@ def run_shifted64(args, ws, rank, local):
                              "peak_kind": f"{kind} copy bandwidth"},
                 "fp64": out["fp64"], "mixed": mx, "mixed_vs_fp64_speedup": mx["value"] / out["fp64"]["value"],
                 "e2e": out["e2e"], "gpu_launches": int(mx["launches"] * args.steps), "clocks": mx["clocks"],
-                "cpu_baseline": None}
+                "cpu_baseline": cpu_baseline_shifted(fam) if (ws == 1 and not args.no_cpu_baseline) else None}
         print(json.dumps(line), flush=True)
 
 
@@ -440,7 +512,6 @@ def main():
         return
     import torch
 
-    from gen import lap2d_64_k4, lap3d_128_k10, lap3d_128_k10_near, saddle_96_b20x64
     from paper_1805_12417_gb300 import build as _b
     _b.build()
     import paper_1805_12417_gb300 as m
@@ -448,21 +519,7 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    workload = WORKLOAD
-    if args.workload == "saddle":
-        p = saddle_96_b20x64()
-        workload = ("saddle_96^3_B20x64: [K B^T; B 0], K 27-pt log-normal(0,1) SPD stencil on 96^3, B 20 rows x 64 "
-                    "uniform[-1,1] entries (n=884,756, 20 negative eigenvalues), seed 2, 1 RHS")
-    elif args.workload == "lap2d_64":
-        p = lap2d_64_k4()
-        workload = ("lap2d_64x64_k4: 2D 5-pt Laplacian 64^2 (n=4,096) shifted to 4 negative eigenvalues, 1 RHS; "
-                    "L2-resident and latency-bound: read solves/s and launches per solve, not the HBM fraction")
-    elif args.workload == "lap3d_128_near":
-        p = lap3d_128_k10_near()
-        workload = ("lap3d_128^3_k10_near: the lap3d_128 matrix with sigma at lambda_10 + 0.05 (lambda_11 - "
-                    "lambda_10), so the 10 negative eigenvalues are the smallest in modulus, 1 RHS")
-    else:
-        p = lap3d_128_k10()
+    p, workload = single_system(args.workload)
     b_dev = torch.from_numpy(p.b).to(dev)
     x_dev = torch.zeros(p.n, dtype=torch.float64, device=dev)
     mcg = {"identity": m.MCG_IDENTITY, "jacobi": m.MCG_JACOBI, "smw": m.MCG_SMW}[args.mcg]
@@ -568,7 +625,7 @@ def main():
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(p, inf_64[-1].inner_iters_total, mcg)
+        cpu = cpu_baseline(p, args.mcg)
 
     if rank == 0:
         line = {

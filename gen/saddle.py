@@ -72,11 +72,14 @@ def _negative_eigenpairs_dense(A: sp.csr_matrix, nb: int):
     return Q[:, :nb].copy(), w[:nb].copy()
 
 
-def _negative_eigenpairs_krylov(K, B, nb, shift, blocks, cg_tol=1e-13, device="cuda"):
+def _negative_eigenpairs_krylov(K, B, nb, shift, blocks, cg_tol=1e-13, device=None):
     """Rayleigh-Ritz of A on span{[Y_j; 0], [0; I]}, Y_j an orthonormal block
-    Krylov basis of (K - shift I)^{-1} applied to B^T (block CG solves)."""
+    Krylov basis of (K - shift I)^{-1} applied to B^T (block CG solves).  Runs
+    on the GPU when there is one (device None), else on the CPU (slowly)."""
     import torch
 
+    if device is None:
+        device = "cuda" if torch.cuda.is_available() else "cpu"
     dev = torch.device(device)
     nK = K.shape[0]
     Kt = torch.sparse_csr_tensor(torch.from_numpy(K.indptr.astype(np.int64)),

@@ -44,3 +44,43 @@ def test_committed_note_parses():
     assert len(lines) == 1
     kv = dict(x.strip().split("=", 1) for x in lines[0].split(":", 1)[1].split(";"))
     assert set(kv) == {"kernel", "bytes", "source_sha256"} and int(kv["bytes"]) > 0
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`bench.py --impl reference` times the oracle on the arm's own workload
+    and prints one JSON line with the keys the benchmark contract names."""
+    import json
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                          "lap2d_64", "--steps", "2", "--warmup", "3"], capture_output=True, text=True,
+                         timeout=600, check=True).stdout.strip().splitlines()
+    line = json.loads(out[-1])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["steps"] == 2 and line["warmup"] == 3
+    assert line["value"] > 0 and line["unit"] == "solves/s" and line["higher_is_better"] is True
+    assert line["config"]["workload"].startswith("lap2d_64x64_k4")
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_cpu_baseline_scales_only_by_the_oracles_own_count(monkeypatch):
+    """A sampled baseline is scaled by the inner-iteration count of a whole
+    oracle solve recorded by oracle/record_counts.py, never by anything else:
+    with no record its value is None."""
+    from gen import lap2d_64_k4
+    p = lap2d_64_k4()
+    monkeypatch.setattr(bench, "full_solve_inner_iters", lambda name, mcg="identity": None)
+    big = type("P", (), {})()
+    for a in ("rowptr", "colind", "val", "V", "lam", "b", "k"):
+        setattr(big, a, getattr(p, a))
+    big.n, big.name = 200_000, p.name  # past the whole-solve threshold: sampled
+    import oracle as O
+    monkeypatch.setattr(O.System, "from_problem", classmethod(
+        lambda cls, q: cls(p.rowptr, p.colind, p.val, p.V, p.lam)))
+    cb = bench.cpu_baseline(big)
+    assert cb["value"] is None and "no whole oracle solve" in cb["sample"]
+    monkeypatch.setattr(bench, "full_solve_inner_iters", lambda name, mcg="identity": 815)
+    cb = bench.cpu_baseline(big)
+    assert cb["value"] > 0 and "scaled by the 815 inner iterations" in cb["sample"]
