@@ -7,6 +7,11 @@ run before them (setup only), which keeps an ncu capture of them small:
 
   python -m paper_1805_12417_gb300.profile --workload lap3d_128 --precision mixed --iters 3
 
+The batch64 and shifted64 workloads instead run one solve of the batch or
+shifted-family engine with an inner budget of 100 * --iters iterations and
+the inner loop driven from the host (MRCG_INNER_LOOP=host), so that a
+profiler sees those engines' kernels.
+
 A profiler slows every launch, which misleads the launch-shape autotuner that
 runs at solver creation; `--var-a / --bpsm-a / --bpsm-b` (or MRCG_SHAPE_F32 /
 MRCG_SHAPE_F64) fix the shape instead
