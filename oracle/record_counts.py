@@ -36,9 +36,12 @@ WORKLOADS = {
     # the saddle's eigenpairs come from a Krylov eigensolver in torch, on the
     # GPU when there is one, else on the CPU (slow; residuals as on the GPU)
     "saddle": lambda: gen.saddle_96_b20x64(),
+    # one column of the 160^3 shifted family (shift 0, right-hand side 0) as a
+    # stand-alone system: a whole oracle solve of all 64 columns takes a day
+    "shifted64_col0": lambda: gen.shifted_lap3d_160().column_problem(0),
 }
 RECORDS = ["lap2d_64:identity", "lap3d_128:identity", "lap3d_128:jacobi", "lap3d_128:smw",
-           "lap3d_128_near:identity", "lap3d_128_near:smw", "saddle:identity"]
+           "lap3d_128_near:identity", "lap3d_128_near:smw", "saddle:identity", "shifted64_col0:identity"]
 
 
 def key(name, mcg):
