@@ -17,6 +17,7 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "mrcg.h"
+#include "trace.h"
 
 using namespace mrcg;
 
@@ -585,6 +586,7 @@ void destroy_impl(mrcg_solver* h) {
 
 // run the inner-CG graph once (zout = P(vin), pointers already in the state)
 mrcg_status run_inner(mrcg_solver* h) {
+  TraceRange tr("mrcg inner CG");
   if (h->host_loop) {
     CK(run_inner_host(h->spec, h->stream, &h->h_st->cg.done));
     return MRCG_OK;
@@ -595,6 +597,7 @@ mrcg_status run_inner(mrcg_solver* h) {
 
 mrcg_status solve_impl(mrcg_solver* h, const double* ub, double* ux, double outer_tol, double inner_tol,
                        int64_t max_iters, mrcg_info* info) {
+  TraceRange tr("mrcg_solve");
   const long long budget = max_iters > 0 ? (long long)max_iters : (1LL << 31);
   long long launches = 0, graphs = 0;
 #define LKC(call)  \
@@ -644,6 +647,7 @@ mrcg_status solve_impl(mrcg_solver* h, const double* ub, double* ux, double oute
           break;
         }
         const int nxt = cur ^ 1;
+        TraceRange step("mrcg outer MINRES step");
         LKC(launch_lanczos_spmv(h->oargs, h->zraw, h->zn, h->res));
         LKC(launch_lanczos_update(h->oargs, h->res, h->v[cur], h->v[nxt], h->v[nxt], h->zraw));
         ST(run_inner(h)); graphs += 1;

@@ -29,6 +29,7 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "mrcg.h"
+#include "trace.h"
 
 namespace mrcg {
 namespace batch {
@@ -1455,6 +1456,7 @@ mrcg_status mrcg_batch_create(int32_t nsys, const mrcg_create_args* sys, mrcg_ba
 
 mrcg_status mrcg_batched_solve(mrcg_batch_handle h, const double* B, double* X, double outer_tol, double inner_tol,
                                int64_t max_iters, mrcg_info* infos) {
+  mrcg::TraceRange tr("mrcg_batched_solve");
   if (!h || !B || !X) return MRCG_ERR_INVALID;
   if (!(outer_tol >= 0.0) || !(inner_tol > 0.0) || !(inner_tol < 1.0)) return MRCG_ERR_INVALID;
   int prev = -1;

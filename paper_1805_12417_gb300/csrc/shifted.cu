@@ -27,6 +27,7 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "mrcg.h"
+#include "trace.h"
 
 namespace mrcg {
 namespace shifted {
@@ -1566,6 +1567,7 @@ mrcg_status mrcg_shifted_create(const mrcg_create_args* L, int32_t nshift, const
 
 mrcg_status mrcg_shifted_solve(mrcg_shifted_handle h, const double* B, double* X, double outer_tol, double inner_tol,
                                int64_t max_iters, mrcg_info* infos) {
+  mrcg::TraceRange tr("mrcg_shifted_solve");
   if (!h || !B || !X) return MRCG_ERR_INVALID;
   if (!(outer_tol >= 0.0) || !(inner_tol > 0.0) || !(inner_tol < 1.0)) return MRCG_ERR_INVALID;
   int prev = -1;
