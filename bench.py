@@ -53,6 +53,9 @@ def parse():
                          "sigma close to lambda_10 (for --mcg smw, MINRES-CG*); batch64: 64 independent uneven "
                          "2D systems (sides 100..400, k_i 1..16, seed 3) solved as one batch; shifted64: 16 "
                          "shifts x 4 RHS of the 160^3 Laplacian as one right-hand-side block")
+    ap.add_argument("--inner-tol", type=float, default=INNER_TOL,
+                    help="relative recursive-residual tolerance of every inner CG solve (default 1e-3); the CPU "
+                         "baseline of a sampled workload is scaled only by a count recorded at the same tolerance")
     ap.add_argument("--mcg", choices=["identity", "jacobi", "smw"], default="identity",
                     help="inner preconditioner of the single-system workloads: identity (default), Jacobi on "
                          "M_mr, or smw, the MINRES-CG* form diag(A)^-1 - 2 V Lambda^-1 V^T (Sec. 2.1)")
@@ -507,7 +510,9 @@ def run_shifted64(args, ws, rank, local):
 
 
 def main():
+    global INNER_TOL
     args = parse()
+    INNER_TOL = args.inner_tol
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, ws, rank)

@@ -84,3 +84,13 @@ def test_cpu_baseline_scales_only_by_the_oracles_own_count(monkeypatch):
     monkeypatch.setattr(bench, "full_solve_inner_iters", lambda name, mcg="identity": 815)
     cb = bench.cpu_baseline(big)
     assert cb["value"] > 0 and "scaled by the 815 inner iterations" in cb["sample"]
+
+
+def test_reference_arm_follows_the_inner_tolerance():
+    import json
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                          "lap2d_64", "--steps", "1", "--warmup", "3", "--inner-tol", "1e-2"], capture_output=True,
+                         text=True, timeout=600, check=True).stdout.strip().splitlines()
+    line = json.loads(out[-1])
+    assert line["config"]["inner_tol"] == 1e-2 and line["value"] > 0
