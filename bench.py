@@ -161,7 +161,7 @@ class Clocks:
 
 
 KERNEL_SOURCES = ["paper_1805_12417_gb300/csrc/cg_impl.cuh", "paper_1805_12417_gb300/csrc/common.cuh"]
-TRAFFIC_NOTE = "profiles/cg_step_a_lap3d_128.md"
+TRAFFIC_RECORDS = "profiles/traffic.json"
 
 
 def step_a_kernel_name(cfg, prec="float"):
@@ -185,17 +185,19 @@ def kernel_source_hash():
 
 
 def recorded_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current kernel sources (else None)."""
-    path = os.path.join(ROOT, TRAFFIC_NOTE)
-    if not os.path.exists(path):
+    """DRAM bytes per launch of `kernel` from the committed ncu record
+    (profiles/traffic.json), if it was taken on the current kernel sources
+    (else None)."""
+    path = os.path.join(ROOT, TRAFFIC_RECORDS)
+    try:
+        with open(path) as f:
+            recs = json.load(f)["records"]
+    except (OSError, ValueError, KeyError):
         return None
     want = kernel_source_hash()
-    for line in open(path):
-        if line.startswith("traffic_per_launch:"):
-            kv = dict(x.strip().split("=", 1) for x in line.split(":", 1)[1].strip().split(";") if "=" in x)
-            if kv.get("kernel") == kernel and kv.get("source_sha256") == want:
-                return int(kv["bytes"])
+    for r in recs:
+        if r.get("kernel") == kernel and r.get("source_sha256") == want:
+            return int(r["bytes_per_launch"])
     return None
 
 

@@ -330,6 +330,17 @@ class ShiftedFamily:
                        float(self.sigma[j]))
 
 
+    def subfamily(self, shifts) -> "ShiftedFamily":
+        """The family restricted to the listed shifts (their columns, in order;
+        L, V and lamL shared)."""
+        shifts = [int(j) for j in shifts]
+        cols = [j * self.nrhs + r for j in shifts for r in range(self.nrhs)]
+        return ShiftedFamily(f"{self.name}_shifts{'_'.join(map(str, shifts))}", self.dims, self.n, self.rowptr,
+                             self.colind, self.val, self.V, self.lamL, self.sigma[shifts].copy(),
+                             self.k[shifts].copy(), self.nrhs, np.ascontiguousarray(self.B[:, cols]),
+                             np.ascontiguousarray(self.xstar[:, cols]))
+
+
 def shifted_family(dims, nshift, nrhs, kmax_draw, seed, name="shifted"):
     """k_j ~ U{1..kmax_draw} from default_rng(seed), each raised to the end of
     its eigenvalue cluster; sigma_j midway between eigenvalues k_j and k_j + 1

@@ -8,7 +8,7 @@
  * (V_hat: n x k basis of the negative invariant subspace, Lambda_hat: its k
  * negative eigenvalues) is applied approximately by an inner CG solve of
  * M_mr z = y (Eq. 2, Algorithm 1).  The solve stage is the third of the
- * paper's three stages (Sec. 2, "In summary ..."): the caller supplies the
+ * paper's three stages (the summary closing Sec. 2): the caller supplies the
  * eigenpairs (stage two); the inner preconditioner M_cg is the identity,
  * Jacobi or the MINRES-CG* preconditioner of Sec. 2.1 (stage one, see
  * mrcg_inner_prec).
@@ -81,7 +81,7 @@ typedef enum {
   MRCG_MIXED_FP32 = 1  /* inner CG with FP32 copies of A, V_hat and FP32 vectors */
 } mrcg_precision;
 
-/* Inner preconditioner M_cg of Algorithm 1 ("solve M_cg t = g"). */
+/* Inner preconditioner M_cg of Algorithm 1 (the solves with M_cg inside each CG step). */
 typedef enum {
   MRCG_MCG_IDENTITY = 0, /* M_cg = I */
   MRCG_MCG_JACOBI = 1,   /* M_cg = diag(M_mr) */
@@ -139,14 +139,14 @@ mrcg_status mrcg_solver_create(const mrcg_create_args* args, mrcg_handle* out);
  * last iterate.  Stops when the FP64 true relative residual
  * ||b - A x|| / ||b|| <= outer_tol (Sec. 4.2); each inner CG solve stops when
  * its recursive residual falls to inner_tol times its right-hand side's norm.
- * max_iters bounds the TOTAL inner CG iterations (the paper's "maximum
- * (total) number of iterations", Sec. 4.1-4.2); <= 0 means no bound beyond
+ * max_iters bounds the TOTAL inner CG iterations (the paper caps the sum of
+ * all iterations, Sec. 4.1-4.2); <= 0 means no bound beyond
  * 2^31.  info may be NULL.  Returns the solve status (MRCG_ERR_MAXITER keeps
  * x and info valid). */
 mrcg_status mrcg_solve(mrcg_handle h, const double* b, double* x, double outer_tol, double inner_tol,
                        int64_t max_iters, mrcg_info* info);
 
-/* y = A x in FP64 (Algorithm 1, "matrix-vector products with A"). */
+/* y = A x in FP64 (the products with A that Algorithm 1 takes). */
 mrcg_status mrcg_apply_A(mrcg_handle h, const double* x, double* y);
 
 /* out = M_mr u = A u + 2 V (|Lambda| (V^T u))  (Sec. 2, the product procedure
@@ -196,9 +196,9 @@ mrcg_status mrcg_launch_config(mrcg_handle h, int32_t* cfg);
 /* ---- Batches of independent systems (many uneven systems in one launch sequence) ----
  *
  * The paper's motivating use solves many systems with related coefficient
- * matrices after one setup (Sec. 2, "many linear systems with the same
- * coefficient matrix (or closely related coefficient matrices) need to be
- * solved"; Sec. 3, shifted systems of shift-and-invert Arnoldi).  A batch
+ * matrices after one setup (Sec. 2: the costly eigenpair stage pays off when
+ * many systems share a coefficient matrix or have close ones; Sec. 3, shifted
+ * systems of shift-and-invert Arnoldi).  A batch
  * holds nsys independent systems A_i x_i = b_i, each with its own M_mr
  * (V_hat_i, Lambda_hat_i), and runs Algorithm 1 for all of them at once: every
  * kernel covers all systems, with per-system scalars, per-system reductions
@@ -276,9 +276,13 @@ void mrcg_shifted_destroy(mrcg_shifted_handle h);
  * lambda[k], u[n] and out[n] -- and the only scratch is a fixed 262,656-byte
  * static device array inside the library, which every GPU that loads the
  * library keeps until the process exits.  Nothing is allocated or freed.
- *  - The first call on a device looks up that array's device address
- *    (cudaGetSymbolAddress, with that device current); make the first call on
- *    each device before any stream capture.
+ *  - The first call in each CUDA context (normally: on each device, in its
+ *    primary context) looks up that array's device address with
+ *    cudaGetSymbolAddress, with the device current, and caches it for that
+ *    context.  Make that first call before any stream capture.  After a
+ *    cudaDeviceReset the library's module is loaded afresh and the array may
+ *    move: the next call sees a new context and looks the address up again
+ *    (so it, too, should come before any capture).
  *  - Work is enqueued on `stream` (NULL = the default stream) and the call
  *    returns without waiting; out is complete when the stream reaches it.
  *  - All calls share the one scratch array and each call rewrites it (a

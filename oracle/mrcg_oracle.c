@@ -188,8 +188,7 @@ double orc_true_relres(const orc_system* s, const double* b, const double* x, do
  * the P^{-1} inner product with unnormalised vectors v (z = P^{-1} v,
  * gamma = sqrt(z^T v)), QR of the tridiagonal by Givens rotations, and the
  * short recurrence for the search directions w.  Stopping test: the true
- * relative residual (Sec. 4.2: "stop when the true relative residual is less
- * than the tolerance"). */
+ * relative residual against the tolerance (Sec. 4.2). */
 int orc_minres(const orc_system* s, const double* b, double* x, orc_prec_fn prec, void* prec_ctx,
                double outer_tol, int32_t max_outer, int64_t max_inner_total, double restart_factor,
                double* hist_relres, double* hist_eta, int32_t hist_cap, orc_info* info) {

@@ -40,7 +40,7 @@ typedef struct {
   const double* lam; /* k eigenvalues (negative) */
 } orc_system;
 
-/* y = A x (Alg. 1: "matrix-vector products with A"). */
+/* y = A x (the products with A that Alg. 1 takes). */
 void orc_csr_spmv(const orc_system* s, const double* x, double* y);
 
 /* out = M_mr u = A u + 2 V (|Lambda| (V^T u))   (Sec. 2, the product

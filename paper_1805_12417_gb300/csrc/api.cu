@@ -101,8 +101,11 @@ bool is_device_ptr(const void* p) {
 
 template <typename T>
 mrcg_status dalloc(mrcg_solver* h, T** p, size_t count) {
+  // exact sizes: every kernel stays inside n_pad rows / the SELL arrays, and a
+  // guard tail would push a vector of a whole number of 2 MiB pages onto one
+  // more page (an empty array still gets a small allocation of its own)
   void* q = nullptr;
-  cudaError_t e = cudaMalloc(&q, count * sizeof(T) + 16);
+  cudaError_t e = cudaMalloc(&q, std::max<size_t>(count * sizeof(T), 256));
   if (e != cudaSuccess) {
     cudaGetLastError();
     return MRCG_ERR_OOM;

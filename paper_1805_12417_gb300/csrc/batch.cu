@@ -69,49 +69,6 @@ struct BArgs {
 
 // ------------------------------------------------------------------ helpers
 
-template <typename T>
-struct V16;
-template <>
-struct V16<float> {
-  using type = float4;
-  static constexpr int W = 4;
-};
-template <>
-struct V16<double> {
-  using type = double2;
-  static constexpr int W = 2;
-};
-template <typename T>
-__device__ __forceinline__ void ld16(const T* p, T (&x)[V16<T>::W]) {
-  const typename V16<T>::type v = *reinterpret_cast<const typename V16<T>::type*>(p);
-  memcpy(x, &v, 16);
-}
-template <typename T>
-__device__ __forceinline__ void ld16_stream(const T* p, T (&x)[V16<T>::W]) {
-  const typename V16<T>::type v = __ldcs(reinterpret_cast<const typename V16<T>::type*>(p));
-  memcpy(x, &v, 16);
-}
-template <typename T>
-__device__ __forceinline__ void st16(T* p, const T (&x)[V16<T>::W]) {
-  typename V16<T>::type v;
-  memcpy(&v, x, 16);
-  *reinterpret_cast<typename V16<T>::type*>(p) = v;
-}
-
-__device__ __forceinline__ float alpha_of(const CgState& S, float) { return S.alpha32; }
-__device__ __forceinline__ double alpha_of(const CgState& S, double) { return S.alpha; }
-__device__ __forceinline__ float beta_of(const CgState& S, float) { return S.beta32; }
-__device__ __forceinline__ double beta_of(const CgState& S, double) { return S.beta; }
-__device__ __forceinline__ float c_of(const CgState& S, int l, float) { return S.c32[l]; }
-__device__ __forceinline__ double c_of(const CgState& S, int l, double) { return S.c[l]; }
-
-__device__ __forceinline__ void publish_c(CgState& S, int k) {
-  for (int l = 0; l < k; ++l) {
-    S.c[l] = S.lam2[l] * S.t[l];
-    S.c32[l] = (float)S.c[l];
-  }
-}
-
 // block reduction of NV values into partials[i * nc + c]
 template <typename T, int NV>
 __device__ __forceinline__ void chunk_partials(T (&v)[NV], int nv, double* partials, int nc, int c) {
@@ -161,19 +118,6 @@ __device__ __forceinline__ void system_sums(const double* partials, int nc, int 
   __syncthreads();
 }
 
-template <typename T, int KB>
-__device__ __forceinline__ void pack_slots(T (&acc)[KB + 2], T rs, const T (&u)[KB > 0 ? KB : 1], T rr, int k,
-                                           bool jac) {
-  constexpr int KS = KB > 0 ? KB : 1;
-#pragma unroll
-  for (int l = 0; l < KB + 2; ++l) {
-    T val = (T)0;
-    if (l == 0) val = rs;
-    else if (l - 1 < KB && l - 1 < k) val = u[(l - 1 < KS) ? l - 1 : 0];
-    else if (jac && l == k + 1) val = rr;
-    acc[l] = val;
-  }
-}
 
 #define CHUNK_LOOP(nc) for (int c = blockIdx.x; c < (nc); c += gridDim.x)
 

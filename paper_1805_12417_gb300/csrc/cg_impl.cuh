@@ -77,53 +77,6 @@ __device__ __forceinline__ T ld_stream(const T* p) {
   return __ldcs(p);
 }
 
-template <typename T>
-struct V16;
-template <>
-struct V16<float> {
-  using type = float4;
-  static constexpr int W = 4;
-};
-template <>
-struct V16<double> {
-  using type = double2;
-  static constexpr int W = 2;
-};
-
-// 16-byte vector load / store into a register array
-template <typename T>
-__device__ __forceinline__ void ld16(const T* p, T (&x)[V16<T>::W]) {
-  const typename V16<T>::type v = *reinterpret_cast<const typename V16<T>::type*>(p);
-  memcpy(x, &v, 16);
-}
-template <typename T>
-__device__ __forceinline__ void ld16_stream(const T* p, T (&x)[V16<T>::W]) {
-  const typename V16<T>::type v = __ldcs(reinterpret_cast<const typename V16<T>::type*>(p));
-  memcpy(x, &v, 16);
-}
-template <typename T>
-__device__ __forceinline__ void st16(T* p, const T (&x)[V16<T>::W]) {
-  typename V16<T>::type v;
-  memcpy(&v, x, 16);
-  *reinterpret_cast<typename V16<T>::type*>(p) = v;
-}
-
-// broadcast scalars in the kernel's precision
-__device__ __forceinline__ float alpha_of(const CgState& S, float) { return S.alpha32; }
-__device__ __forceinline__ double alpha_of(const CgState& S, double) { return S.alpha; }
-__device__ __forceinline__ float beta_of(const CgState& S, float) { return S.beta32; }
-__device__ __forceinline__ double beta_of(const CgState& S, double) { return S.beta; }
-__device__ __forceinline__ float c_of(const CgState& S, int l, float) { return S.c32[l]; }
-__device__ __forceinline__ double c_of(const CgState& S, int l, double) { return S.c[l]; }
-
-// set c = 2|lambda| t (FP64 and FP32 copies)
-__device__ __forceinline__ void publish_c(CgState& S, int k) {
-  for (int l = 0; l < k; ++l) {
-    S.c[l] = S.lam2[l] * S.t[l];
-    S.c32[l] = (float)S.c[l];
-  }
-}
-
 // ------------------------------------------------------------------ norm of v
 
 static __global__ void __launch_bounds__(kThreads) cg_vnorm_kernel(DevState* st, double* partials, int64_t n_pad) {
@@ -139,23 +92,6 @@ static __global__ void __launch_bounds__(kThreads) cg_vnorm_kernel(DevState* st,
     __shared__ double tot[1];
     final_sums(partials, 1, tot);
     if (threadIdx.x == 0) S.vnorm = sqrt(tot[0]);
-  }
-}
-
-// Reduction slots of init / step_b:  [0] = r^T s, [1 .. k] = V^T s,
-// [k + 1] = r^T r (Jacobi only; with M_cg = I, r^T s is r^T r).  Indices are
-// compile-time after unrolling, so the slot array stays in registers.
-template <typename T, int KB>
-__device__ __forceinline__ void pack_slots(T (&acc)[KB + 2], T rs, const T (&u)[KB > 0 ? KB : 1], T rr, int k,
-                                           bool jac) {
-  constexpr int KS = KB > 0 ? KB : 1;
-#pragma unroll
-  for (int l = 0; l < KB + 2; ++l) {
-    T val = (T)0;
-    if (l == 0) val = rs;
-    else if (l - 1 < KB && l - 1 < k) val = u[(l - 1 < KS) ? l - 1 : 0];
-    else if (jac && l == k + 1) val = rr;
-    acc[l] = val;
   }
 }
 
@@ -822,11 +758,22 @@ __device__ __forceinline__ void fused_reduce(const CgArgs<T>& a, CgState& S, T p
       S.kappa = kappa;
       if (!isfinite(kappa) || !isfinite(rho)) {
         S.done = kNonFinite;
+      } else if (sqrt(rho) <= S.tol_abs) {
+        // the fresh ||r_i|| already meets the test (the previous iteration's
+        // expansion was below its rounding floor, so it did not stop there):
+        // z_i is complete, nothing is pending
+        S.done = kConverged;
       } else if (kappa <= 0.0) {
         S.done = kNotSpd;
       } else {
         const double alpha = rho / kappa;
-        const double rho_new = rho - 2.0 * alpha * tot[1] + alpha * alpha * tot[2];
+        const double aqq = alpha * alpha * tot[2];
+        const double rho_new = rho - 2.0 * alpha * tot[1] + aqq;
+        // the expansion cancels O(rho + alpha^2 q^T q) terms computed in the
+        // kernel's precision; below this floor its value (and its sign) is
+        // rounding noise and must not end the solve
+        constexpr double kEpsT = sizeof(T) == 4 ? 5.9604644775390625e-08 : 1.1102230246251565e-16;
+        const bool reliable = rho_new > 32.0 * kEpsT * (rho + aqq);
         S.alpha = alpha;
         S.alpha32 = (float)alpha;
         S.iters += 1;
@@ -837,13 +784,15 @@ __device__ __forceinline__ void fused_reduce(const CgArgs<T>& a, CgState& S, T p
         const double rnorm = sqrt(rho_new > 0.0 ? rho_new : 0.0);
         if (!isfinite(rho_new)) {
           S.done = kNonFinite;
-        } else if (rnorm <= S.tol_abs) {
+        } else if (reliable && rnorm <= S.tol_abs) {
           S.done = kConverged;
         } else if (S.iters >= S.maxit) {
           S.done = kMaxIter;
         } else {
+          // an unreliable expansion continues with beta >= 0 near zero (a
+          // steepest-descent step); the next iteration tests its fresh ||r||
           S.fused_pending = 0;
-          const double beta = rho_new / rho;
+          const double beta = (rho_new > 0.0 ? rho_new : 0.0) / rho;
           S.beta = beta;
           S.beta32 = (float)beta;
           S.rho = rho_new;

@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cstring>
+
 #include "mrcg.h"
 
 namespace mrcg {
@@ -218,6 +220,75 @@ __device__ __forceinline__ void final_sums(const double* partials, int nv, doubl
 }
 
 __device__ __forceinline__ bool finite(double x) { return isfinite(x); }
+
+// ------------------------------------------------------------------ vector and scalar helpers
+//
+// shared by the single-system inner kernels and the batch engine
+
+template <typename T>
+struct V16;
+template <>
+struct V16<float> {
+  using type = float4;
+  static constexpr int W = 4;
+};
+template <>
+struct V16<double> {
+  using type = double2;
+  static constexpr int W = 2;
+};
+
+// 16-byte vector load / store into a register array
+template <typename T>
+__device__ __forceinline__ void ld16(const T* p, T (&x)[V16<T>::W]) {
+  const typename V16<T>::type v = *reinterpret_cast<const typename V16<T>::type*>(p);
+  memcpy(x, &v, 16);
+}
+template <typename T>
+__device__ __forceinline__ void ld16_stream(const T* p, T (&x)[V16<T>::W]) {
+  const typename V16<T>::type v = __ldcs(reinterpret_cast<const typename V16<T>::type*>(p));
+  memcpy(x, &v, 16);
+}
+template <typename T>
+__device__ __forceinline__ void st16(T* p, const T (&x)[V16<T>::W]) {
+  typename V16<T>::type v;
+  memcpy(&v, x, 16);
+  *reinterpret_cast<typename V16<T>::type*>(p) = v;
+}
+
+// broadcast scalars in the kernel's precision
+__device__ __forceinline__ float alpha_of(const CgState& S, float) { return S.alpha32; }
+__device__ __forceinline__ double alpha_of(const CgState& S, double) { return S.alpha; }
+__device__ __forceinline__ float beta_of(const CgState& S, float) { return S.beta32; }
+__device__ __forceinline__ double beta_of(const CgState& S, double) { return S.beta; }
+__device__ __forceinline__ float c_of(const CgState& S, int l, float) { return S.c32[l]; }
+__device__ __forceinline__ double c_of(const CgState& S, int l, double) { return S.c[l]; }
+
+// set c = 2|lambda| t (FP64 and FP32 copies)
+__device__ __forceinline__ void publish_c(CgState& S, int k) {
+  for (int l = 0; l < k; ++l) {
+    S.c[l] = S.lam2[l] * S.t[l];
+    S.c32[l] = (float)S.c[l];
+  }
+}
+
+// Reduction slots of init / step_b:  [0] = r^T s, [1 .. k] = V^T s,
+// [k + 1] = r^T r (Jacobi only; with M_cg = I, r^T s is r^T r).  Indices are
+// compile-time after unrolling, so the slot array stays in registers.
+template <typename T, int KB>
+__device__ __forceinline__ void pack_slots(T (&acc)[KB + 2], T rs, const T (&u)[KB > 0 ? KB : 1], T rr, int k,
+                                           bool jac) {
+  constexpr int KS = KB > 0 ? KB : 1;
+#pragma unroll
+  for (int l = 0; l < KB + 2; ++l) {
+    T val = (T)0;
+    if (l == 0) val = rs;
+    else if (l - 1 < KB && l - 1 < k) val = u[(l - 1 < KS) ? l - 1 : 0];
+    else if (jac && l == k + 1) val = rr;
+    acc[l] = val;
+  }
+}
+
 
 // ------------------------------------------------------------------ bulk copies (TMA) and mbarriers
 //

@@ -23,7 +23,6 @@ namespace mrcg {
 namespace {
 
 constexpr int kNaBlocks = 1024;
-constexpr int kNaMaxDevices = 64;
 
 struct NaScratch {
   double partials[kMaxK * kNaBlocks];  // value-major: [value][block]
@@ -34,9 +33,80 @@ struct NaScratch {
 
 static __device__ __align__(256) NaScratch g_na_scratch;
 
-// device address of g_na_scratch, looked up once per device
-NaScratch* g_na_ptr[kNaMaxDevices] = {};
+// Device address of g_na_scratch, looked up once per CUDA context.  The
+// address belongs to the module instance loaded in one context: after a
+// cudaDeviceReset, or in another context on the same device, the module is
+// loaded again and the array may sit elsewhere.  So the cache is keyed by the
+// context's process-unique id (cuCtxGetId), not by the device ordinal, and a
+// new context gets its own lookup.  The two driver calls are reached through
+// the runtime's entry-point query, so the library does not link libcuda.
+constexpr int kNaMaxContexts = 64;
+struct NaEntry {
+  unsigned long long ctx_id;
+  NaScratch* ptr;
+};
+NaEntry g_na_cache[kNaMaxContexts] = {};
+int g_na_count = 0;
 std::mutex g_na_mutex;
+
+typedef int (*CtxGetCurrentFn)(void** ctx);
+typedef int (*CtxGetIdFn)(void* ctx, unsigned long long* id);
+
+// id of the calling thread's current context; false when there is none (yet)
+bool current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool tried = false;
+  if (!tried) {  // under g_na_mutex
+    tried = true;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+        q2 == cudaDriverEntryPointSuccess) {
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+      get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    }
+    cudaGetLastError();
+  }
+  if (!get_current || !get_id) return false;
+  void* ctx = nullptr;
+  if (get_current(&ctx) != 0 || !ctx) return false;
+  return get_id(ctx, id) == 0;
+}
+
+// set-up of the current context: the symbol's device address, cached per context
+mrcg_status scratch_address(NaScratch** out) {
+  std::lock_guard<std::mutex> lock(g_na_mutex);
+  unsigned long long id = 0;
+  if (current_context_id(&id)) {
+    for (int i = 0; i < g_na_count; ++i)
+      if (g_na_cache[i].ctx_id == id) {
+        *out = g_na_cache[i].ptr;
+        return MRCG_OK;
+      }
+  }
+  // first call in this context (this also creates the device's primary
+  // context when none is current yet)
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_na_scratch) != cudaSuccess || !p) {
+    cudaGetLastError();
+    return MRCG_ERR_CUDA;
+  }
+  *out = reinterpret_cast<NaScratch*>(p);
+  if (current_context_id(&id)) {
+    if (g_na_count < kNaMaxContexts) {
+      g_na_cache[g_na_count++] = {id, *out};
+    } else {  // many contexts over the process lifetime: recycle the oldest slot
+      for (int i = 1; i < kNaMaxContexts; ++i) g_na_cache[i - 1] = g_na_cache[i];
+      g_na_cache[kNaMaxContexts - 1] = {id, *out};
+    }
+  }
+  // without a context id nothing is cached: the lookup then runs on every call
+  return MRCG_OK;
+}
 
 __global__ void __launch_bounds__(kThreads) na_vtu_kernel(NaScratch* sc, int64_t n, int k,
                                                             const double* __restrict__ V,
@@ -85,22 +155,8 @@ extern "C" mrcg_status mrcg_mmr_apply_noalloc(int64_t n, const int64_t* rowptr, 
                                               const double* lambda, const double* u, double* out, void* stream) {
   if (n < 1 || n > (int64_t)0x7fffffff || k < 0 || k > kMaxK) return MRCG_ERR_INVALID;
   if (!rowptr || !val || !colind || !u || !out || (k > 0 && (!V || !lambda))) return MRCG_ERR_INVALID;
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) return MRCG_ERR_CUDA;
   NaScratch* sc = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_ptr[dev]) {
-      // set-up on this device (the current one): the symbol's device address
-      void* p = nullptr;
-      if (cudaGetSymbolAddress(&p, g_na_scratch) != cudaSuccess || !p) {
-        cudaGetLastError();
-        return MRCG_ERR_CUDA;
-      }
-      g_na_ptr[dev] = reinterpret_cast<NaScratch*>(p);
-    }
-    sc = g_na_ptr[dev];
-  }
+  if (const mrcg_status st = scratch_address(&sc); st != MRCG_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   // the ticket must start at zero; the partials and c are overwritten in full
   if (cudaMemsetAsync(&sc->ticket, 0, sizeof(unsigned int), s) != cudaSuccess) return MRCG_ERR_CUDA;

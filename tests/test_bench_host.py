@@ -25,11 +25,13 @@ def test_kernel_name_per_variant(var, name):
 
 
 def test_recorded_traffic_needs_matching_kernel_and_sources(tmp_path, monkeypatch):
-    note = tmp_path / "note.md"
+    import json
+    rec = tmp_path / "traffic.json"
     h = bench.kernel_source_hash()
-    note.write_text("text\ntraffic_per_launch: kernel=K<float, 12, 4, 0, 0>; bytes=123; source_sha256=%s\n" % h)
+    rec.write_text(json.dumps({"records": [{"kernel": "K<float, 12, 4, 0, 0>", "bytes_per_launch": 123,
+                                            "source_sha256": h}]}))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path.parent))
-    monkeypatch.setattr(bench, "TRAFFIC_NOTE", os.path.join(tmp_path.name, "note.md"))
+    monkeypatch.setattr(bench, "TRAFFIC_RECORDS", os.path.join(tmp_path.name, "traffic.json"))
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: h)
     assert bench.recorded_traffic("K<float, 12, 4, 0, 0>") == 123
     assert bench.recorded_traffic("K<float, 12, 2, 0, 0>") is None
@@ -37,13 +39,15 @@ def test_recorded_traffic_needs_matching_kernel_and_sources(tmp_path, monkeypatc
     assert bench.recorded_traffic("K<float, 12, 4, 0, 0>") is None
 
 
-def test_committed_note_parses():
-    """The committed ncu summary carries a well-formed traffic line."""
-    path = os.path.join(ROOT, bench.TRAFFIC_NOTE)
-    lines = [l for l in open(path) if l.startswith("traffic_per_launch:")]
-    assert len(lines) == 1
-    kv = dict(x.strip().split("=", 1) for x in lines[0].split(":", 1)[1].split(";"))
-    assert set(kv) == {"kernel", "bytes", "source_sha256"} and int(kv["bytes"]) > 0
+def test_committed_traffic_records_parse():
+    """The committed ncu traffic records are well-formed JSON."""
+    import json
+    with open(os.path.join(ROOT, bench.TRAFFIC_RECORDS)) as f:
+        recs = json.load(f)["records"]
+    assert recs
+    for r in recs:
+        assert {"kernel", "bytes_per_launch", "source_sha256", "workload"} <= set(r)
+        assert int(r["bytes_per_launch"]) > 0 and len(r["source_sha256"]) == 16
 
 
 def test_reference_arm_prints_the_contract_line():

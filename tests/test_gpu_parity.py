@@ -167,6 +167,42 @@ def test_solve_fp64_matches_oracle(prob, device):
     assert len(info.relres_history) == info.outer_iters
 
 
+def _restart_steps(hist, f, tol):
+    """Steps at which the restart rule fires on a history of true relative
+    residuals (within a cycle: j >= 4 and relres_j > f * relres_{j-3})."""
+    cyc, steps = [], []
+    for j, rr in enumerate(hist, start=1):
+        cyc.append(rr)
+        if rr <= tol:
+            break
+        if len(cyc) >= 4 and rr > f * cyc[-4]:
+            steps.append(j)
+            cyc = []
+    return steps
+
+
+@pytest.mark.parametrize("dims,k,seed", [((40, 37), 6, 9), ((12, 11, 10), 4, 3)], ids=["lap2d_40x37_k6", "lap3d_12x11x10_k4"])
+def test_solve_restart_rule_matches_oracle(dims, k, seed):
+    """The restart safeguard fires on the GPU where it fires in the oracle: with
+    a loose inner tolerance (1e-2) and f = 1e-2 (restart unless three outer
+    steps gain a factor 100) both restart twice, at the same outer steps, and
+    x agrees to 1e-8.  The oracle's decisions sit at least 8 % from f, far
+    beyond the rounding drift between the two FP64 paths."""
+    p = shifted_laplacian_problem("t", dims, k, seed=seed)
+    f = 1e-2
+    ref = O.minres_cg(O.System.from_problem(p), p.b, outer_tol=1e-12, inner_tol=1e-2, restart_factor=f)
+    assert ref.status == O.OK and ref.restarts == 2
+    ref_steps = _restart_steps(ref.relres_history, f, 1e-12)
+    assert len(ref_steps) == 2
+    with m.Solver.from_problem(p, restart_factor=f) as g:
+        x, info = g.solve(p.b.copy(), outer_tol=1e-12, inner_tol=1e-2)
+    assert info.status == m.OK
+    assert info.restarts == ref.restarts
+    assert _restart_steps(info.relres_history, f, 1e-12) == ref_steps
+    assert abs(info.outer_iters - ref.outer_iters) <= 2
+    assert np.linalg.norm(x - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
+
+
 def test_solve_jacobi_matches_oracle():
     p = shifted_laplacian_problem("t", (30, 29), 5, seed=12)
     ref, x, info = _solve_both(p, mcg=m.MCG_JACOBI)
@@ -271,3 +307,20 @@ def test_full_size_solve(big, prec):
     rr = s.true_relres(p.b, x)
     assert rr <= 1e-10
     assert np.linalg.norm(x - p.xstar) / np.linalg.norm(p.xstar) <= p.meta["cond"] * 1e-10 * 3
+
+
+@pytest.mark.parametrize("prec", [m.FP64, m.MIXED_FP32], ids=["fp64", "mixed"])
+def test_full_size_solve_at_parity_tolerance(big, prec):
+    """128^3 shifted Laplacian at outer_tol 1e-12: relative error against x*
+    (the exact solution of the generated system up to kappa * eps ~ 1e-11) at
+    most 1e-8 and FP64 true residual at most 1e-12, in FP64 and in mixed
+    precision (the outer MINRES and its stopping test are FP64 in both)."""
+    p = big
+    with m.Solver.from_problem(p, precision=prec) as g:
+        x = torch.zeros(p.n, dtype=torch.float64, device=DEV)
+        _, info = g.solve(cu(p.b), x, outer_tol=1e-12, inner_tol=1e-3)
+    x = x.cpu().numpy()
+    assert info.status == m.OK, info
+    rr = O.System.from_problem(p).true_relres(p.b, x)
+    assert rr <= 1e-12
+    assert np.linalg.norm(x - p.xstar) / np.linalg.norm(p.xstar) <= 1e-8

@@ -65,3 +65,19 @@ def test_saddle_96_solve(big, prec):
     rr = O.System.from_problem(p).true_relres(p.b, x)
     assert rr <= 1e-10
     assert np.linalg.norm(x - p.xstar) / np.linalg.norm(p.xstar) <= 1e-6
+
+
+@pytest.mark.parametrize("prec", [m.FP64, m.MIXED_FP32], ids=["fp64", "mixed"])
+def test_saddle_96_solve_at_parity_tolerance(big, prec):
+    """Full-size saddle system at outer_tol 1e-12: relative error against x* at
+    most 1e-8 (x* solves the generated system up to kappa * eps) and FP64 true
+    residual at most 1e-12."""
+    p = big
+    with m.Solver.from_problem(p, precision=prec, validate=False) as g:
+        x = torch.zeros(p.n, dtype=torch.float64, device=DEV)
+        _, info = g.solve(torch.from_numpy(p.b).to(DEV), x, outer_tol=1e-12, inner_tol=1e-3)
+    x = x.cpu().numpy()
+    assert info.status == m.OK, info
+    rr = O.System.from_problem(p).true_relres(p.b, x)
+    assert rr <= 1e-12
+    assert np.linalg.norm(x - p.xstar) / np.linalg.norm(p.xstar) <= 1e-8

@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from gen import small_shifted
+from gen import shifted_lap3d_160, small_shifted
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -108,3 +108,61 @@ def test_shifted_host_driven_loop_is_identical(fam, prec, monkeypatch):
     assert a[1] == b[1] == m.OK and a[4] == b[4] == m.ERR_MAXITER
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[3], b[3])
     assert a[2] == b[2] and a[5] == b[5]
+
+
+@pytest.fixture(scope="module")
+def fam160():
+    return shifted_lap3d_160()
+
+
+def test_shifted64_full_size_mixed(fam160):
+    """The 160^3 family (16 shifts x 4 right-hand sides, k_j up to 32) at full
+    size in mixed precision: every one of the 64 columns reaches an FP64 true
+    residual (recomputed here on the host) of at most 1e-10, and its error
+    against x* stays within kappa_j * 1e-10 * 3."""
+    fam = fam160
+    L = fam_scipy(fam)
+    with m.Shifted(fam, precision=m.MIXED_FP32) as sh:
+        X = torch.zeros((fam.n, fam.ncols), dtype=torch.float64, device=DEV)
+        _, st, infos = sh.solve(torch.from_numpy(fam.B).to(DEV), X, outer_tol=1e-10, inner_tol=1e-3)
+    X = X.cpu().numpy()
+    assert st == m.OK
+    for c in range(fam.ncols):
+        j = c // fam.nrhs
+        r = fam.B[:, c] - (L @ X[:, c] - fam.sigma[j] * X[:, c])
+        rr = np.linalg.norm(r) / np.linalg.norm(fam.B[:, c])
+        assert infos[c].status == m.OK and rr <= 1e-10, (c, rr)
+        kappa = shift_condition(fam, j)
+        err = np.linalg.norm(X[:, c] - fam.xstar[:, c]) / np.linalg.norm(fam.xstar[:, c])
+        assert err <= kappa * 1e-10 * 3, (c, err)
+
+
+def test_shifted64_full_size_fp64_one_shift(fam160):
+    """FP64 engine on the four right-hand sides of shift 0 of the 160^3 family
+    at outer_tol 1e-12: every column matches x* to a relative error of 1e-8."""
+    sub = fam160.subfamily([0])
+    with m.Shifted(sub, precision=m.FP64) as sh:
+        X = torch.zeros((sub.n, sub.ncols), dtype=torch.float64, device=DEV)
+        _, st, infos = sh.solve(torch.from_numpy(sub.B).to(DEV), X, outer_tol=1e-12, inner_tol=1e-3)
+    X = X.cpu().numpy()
+    assert st == m.OK
+    for c in range(sub.ncols):
+        err = np.linalg.norm(X[:, c] - sub.xstar[:, c]) / np.linalg.norm(sub.xstar[:, c])
+        assert infos[c].status == m.OK and err <= 1e-8, (c, err)
+
+
+def fam_scipy(fam):
+    import scipy.sparse as sp
+    return sp.csr_matrix((fam.val, fam.colind, fam.rowptr), shape=(fam.n, fam.n))
+
+
+def shift_condition(fam, j):
+    """kappa of L - sigma_j I from its analytic spectrum: largest |eigenvalue|
+    over the smallest (the eigenvalues of L closest to sigma_j sit next to the
+    k_j-th and (k_j+1)-th)."""
+    from gen import laplacian_smallest_eigs
+    kj = int(fam.k[j])
+    ev = [v for v, _ in laplacian_smallest_eigs(fam.dims, kj + 1)]
+    gap = min(abs(ev[kj - 1] - fam.sigma[j]), abs(ev[kj] - fam.sigma[j]))
+    lam_max = 4.0 * len(fam.dims)
+    return (lam_max - fam.sigma[j]) / gap

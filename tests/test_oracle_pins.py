@@ -336,6 +336,85 @@ def test_minres_exact_mmr_converges_in_two_steps():
     assert np.allclose(r.x, np.linalg.solve(A, b), atol=1e-10)
 
 
+def _min_residual_iterate(A, b, xc, j):
+    """x in xc + K_j(A, b - A xc) of least 2-norm residual: an orthonormal basis
+    of the Krylov space (Gram-Schmidt, twice) and a dense least-squares solve.
+    This is the defining property of MINRES with P = I, computed without its
+    Lanczos / Givens recurrences."""
+    r0 = b - A @ xc
+    Q = np.zeros((len(b), j))
+    q = r0 / np.linalg.norm(r0)
+    for i in range(j):
+        for _ in range(2):
+            q = q - Q[:, :i] @ (Q[:, :i].T @ q)
+        Q[:, i] = q / np.linalg.norm(q)
+        q = A @ Q[:, i]
+    y, *_ = np.linalg.lstsq(A @ Q, r0, rcond=None)
+    return xc + Q @ y
+
+
+def _restarted_minres_model(A, b, f, steps, window=3, restart_from_current=True):
+    """Restarted MINRES (P = I) by the reading of the restart rule: within a
+    cycle, after its j-th step (j > window), restart when
+    relres_j > f * relres_{j - window}; the next cycle's Krylov space is built
+    on b - A x at the current x.  Returns (x, relres history, restart steps,
+    smallest |log(ratio / f)| over the decisions taken)."""
+    bn = np.linalg.norm(b)
+    xc = np.zeros(len(b))
+    cyc, hist, restarts, margin = [], [], [], np.inf
+    x = xc
+    for step in range(1, steps + 1):
+        x = _min_residual_iterate(A, b, xc, len(cyc) + 1)
+        rr = np.linalg.norm(b - A @ x) / bn
+        hist.append(rr)
+        cyc.append(rr)
+        m = len(cyc)
+        if m > window:
+            ratio = rr / cyc[m - 1 - window]
+            margin = min(margin, abs(np.log(ratio / f)))
+            if ratio > f:
+                restarts.append(step)
+                xc = x.copy() if restart_from_current else np.zeros(len(b))
+                cyc = []
+    return x, np.array(hist), restarts, margin
+
+
+def test_minres_restart_rule_matches_restarted_least_squares_model():
+    """Restart safeguard (the paper is silent; the reading: restart a cycle from
+    the current x when relres_j > f * relres_{j-3}, j >= 4 within the cycle).
+    With P = I every MINRES iterate is the least-residual point of its cycle's
+    Krylov space, so a dense least-squares model of restarted MINRES fixes the
+    whole residual history, the steps at which cycles restart and the final x.
+    The decisions are taken with a margin of at least 10 % from f, and the model
+    restarts at steps 5, 9 and 13 (a first cycle of five steps, then cycles of
+    four), so a shifted window or a cycle restarted from the wrong point gives a
+    different history."""
+    rng = np.random.default_rng(7)
+    n = 40
+    lam = np.concatenate([-rng.uniform(0.05, 1.0, 6), rng.uniform(0.05, 1.0, n - 6)])
+    Qm, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A = (Qm * lam) @ Qm.T
+    A = 0.5 * (A + A.T)
+    b = rng.standard_normal(n)
+    rp, ci, va = dense_to_csr(A)
+    s = O.System(rp, ci, va)
+    f, steps = 0.6, 14
+    x, hist, restarts, margin = _restarted_minres_model(A, b, f, steps)
+    assert restarts == [5, 9, 13] and margin > 0.1
+    r = O.minres(s, b, lambda v: v, outer_tol=1e-300, max_outer=steps, restart_factor=f)
+    assert r.outer_iters == steps and r.restarts == len(restarts)
+    assert np.allclose(r.relres_history, hist, rtol=1e-10, atol=0)
+    assert np.linalg.norm(r.x - x) <= 1e-10 * np.linalg.norm(x)
+    # the model is sensitive to the two mistakes the pin is for
+    _, h_shift, rs_shift, _ = _restarted_minres_model(A, b, f, steps, window=2)
+    _, h_zero, _, _ = _restarted_minres_model(A, b, f, steps, restart_from_current=False)
+    assert rs_shift != restarts or not np.allclose(h_shift, hist, rtol=1e-6)
+    assert not np.allclose(h_zero, hist, rtol=1e-6)
+    # f < 0 turns the rule off: no restart, and the history is monotone (P = I)
+    r0 = O.minres(s, b, lambda v: v, outer_tol=1e-300, max_outer=steps, restart_factor=-1.0)
+    assert r0.restarts == 0 and np.all(np.diff(r0.relres_history) <= 1e-14)
+
+
 def test_minres_cg_dense_solution():
     """Alg. 1 end to end on a tiny dense problem: x equals the LU solution."""
     A, Vn, lam, d, Q, s = dense_system(60, 5, 29)
