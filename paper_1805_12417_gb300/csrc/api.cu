@@ -12,6 +12,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <initializer_list>
 #include <vector>
 
 #include "common.cuh"
@@ -440,9 +441,9 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
   const int64_t ntiles = (nslices + 7) / 8;
   // step-a grid of a variant at bp blocks per SM (the staged variant is persistent over tiles)
   auto grid_a = [&](const InnerGraphSpec& t, int bp) {
-    return t.var_a >= 5 ? clamp_grid(ntiles, bp) : clamp_grid(want_spmv, bp);
+    return is_staged_variant(t.var_a) ? clamp_grid(ntiles, bp) : clamp_grid(want_spmv, bp);
   };
-  if (const char* va = getenv("MRCG_VAR_A")) g.var_a = std::min(8, std::max(0, atoi(va)));
+  if (const char* va = getenv("MRCG_VAR_A")) g.var_a = std::min(kNumStepAVariants - 1, std::max(0, atoi(va)));
   int occ_a = 1, occ_b = 1;
   inner_occupancy(g, &occ_a, &occ_b);
   if (occ_a < 1) {  // the staged variant does not fit this matrix
@@ -463,11 +464,11 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
   const char* fixed = getenv(h->fp32 ? "MRCG_SHAPE_F32" : "MRCG_SHAPE_F64");
   if (fixed) {
     int v = 0, nst = 0, ga = 0, gb = 0;
-    if (sscanf(fixed, "%d,%d,%d,%d", &v, &nst, &ga, &gb) == 4 && v >= 0 && v <= 8 && ga >= 1 && gb >= 1 &&
+    if (sscanf(fixed, "%d,%d,%d,%d", &v, &nst, &ga, &gb) == 4 && v >= 0 && v < kNumStepAVariants && ga >= 1 && gb >= 1 &&
         ga <= kMaxBlocks && gb <= kMaxBlocks) {
       InnerGraphSpec t = g;
       t.var_a = v;
-      if (v >= 5) t.stages = std::max(2, std::min(8, nst));
+      if (is_staged_variant(v)) t.stages = std::max(2, std::min(8, nst));
       int occ_t = 0, occ_unused = 0;
       inner_occupancy(t, &occ_t, &occ_unused);
       if (occ_t >= 1) {
@@ -485,8 +486,7 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
   const bool tune = (!at || atoi(at) != 0) && n_pad >= (1 << 12) && !getenv("MRCG_BPSM_A") &&
                     !getenv("MRCG_BPSM_B") && !getenv("MRCG_VAR_A") && !fixed;
   if (tune) {
-    double ms[4] = {0.0, 0.0, 0.0, 0.0}, best = 1e30;
-    InnerGraphSpec bestg = g;
+    double ms[4] = {0.0, 0.0, 0.0, 0.0};
     auto time_spec = [&](const InnerGraphSpec& t) -> mrcg_status {
       reset_state(h, 1e-300, 64);
       h->h_init->cg.vin = h->v[0];
@@ -495,50 +495,67 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
       CK(time_inner_kernels(t, 15, h->stream, h->v[0], n, ms));
       return MRCG_OK;
     };
-    for (int var = 0; var <= 7; ++var) {
-      for (int nst = 2; nst <= (var >= 5 ? 4 : 2); ++nst) {
-        InnerGraphSpec t = g;
-        t.var_a = var;
-        t.stages = var >= 5 ? nst : g.stages;
-        int occ_v = 0, occ_unused = 0;
-        inner_occupancy(t, &occ_v, &occ_unused);
-        if (occ_v < 1) continue;
-        // blocks per SM: the occupancy limit and one below; the staged kernels
-        // (no waits between blocks) also one wave of blocks above it and two
-        std::vector<int> bps = {occ_v};
-        if (occ_v > 1) bps.push_back(occ_v - 1);
-        if (var >= 5) {
-          bps.push_back(occ_v + 1);
-          bps.push_back(2 * occ_v);
-        }
-        for (int bp : bps) {
-          t.grid_spmv = grid_a(t, bp);
-          ST(time_spec(t));
-          if (ms[0] < best) {
-            best = ms[0];
-            bestg.var_a = t.var_a;
-            bestg.stages = t.stages;
-            bestg.grid_spmv = t.grid_spmv;
+    // one family of step-a variants sharing a step b: the best step a (variant,
+    // stages, blocks per SM), then the best step-b blocks per SM for it;
+    // returns the time of a whole iteration (1e30 when none fits)
+    auto tune_family = [&](std::initializer_list<int> vars, InnerGraphSpec* out, double* total) -> mrcg_status {
+      double best = 1e30;
+      InnerGraphSpec bestg = g;
+      bool any = false;
+      for (int var : vars) {
+        for (int nst = 2; nst <= (is_staged_variant(var) ? 4 : 2); ++nst) {
+          InnerGraphSpec t = g;
+          t.var_a = var;
+          t.stages = is_staged_variant(var) ? nst : g.stages;
+          int occ_v = 0, occ_unused = 0;
+          inner_occupancy(t, &occ_v, &occ_unused);
+          if (occ_v < 1) continue;
+          // blocks per SM: the occupancy limit and one below; the staged kernels
+          // (no waits between blocks) also one wave of blocks above it and two
+          std::vector<int> bps = {occ_v};
+          if (occ_v > 1) bps.push_back(occ_v - 1);
+          if (is_staged_variant(var)) {
+            bps.push_back(occ_v + 1);
+            bps.push_back(2 * occ_v);
+          }
+          for (int bp : bps) {
+            t.grid_spmv = grid_a(t, bp);
+            ST(time_spec(t));
+            if (ms[0] < best) {
+              best = ms[0];
+              bestg = t;
+              any = true;
+            }
           }
         }
       }
-    }
-    const double best_a = best;
-    best = 1e30;
-    int occ_unused = 0, occ_bmax = 1;
-    inner_occupancy(bestg, &occ_unused, &occ_bmax);
-    for (int bp = 1; bp <= std::max(1, occ_bmax); bp += (bp < 4 ? 1 : 2)) {
-      InnerGraphSpec t = bestg;
-      t.grid_stream_b = clamp_grid(want_b, bp);
-      ST(time_spec(t));
-      if (ms[1] < best) {
-        best = ms[1];
-        bestg.grid_stream_b = t.grid_stream_b;
+      *total = 1e30;
+      if (!any) return MRCG_OK;
+      const double best_a = best;
+      best = 1e30;
+      int occ_unused = 0, occ_bmax = 1;
+      inner_occupancy(bestg, &occ_unused, &occ_bmax);
+      for (int bp = 1; bp <= std::max(1, occ_bmax); bp += (bp < 4 ? 1 : 2)) {
+        InnerGraphSpec t = bestg;
+        t.grid_stream_b = clamp_grid(want_b, bp);
+        ST(time_spec(t));
+        if (ms[1] < best) {
+          best = ms[1];
+          bestg.grid_stream_b = t.grid_stream_b;
+        }
       }
-    }
+      *out = bestg;
+      *total = best_a + best;
+      return MRCG_OK;
+    };
+    InnerGraphSpec classic = g, onegather = g;
+    double t_classic = 1e30, t_onegather = 1e30;
+    ST(tune_family({0, 1, 2, 3, 4, 5, 6, 7}, &classic, &t_classic));
+    ST(tune_family({9, 10, 11}, &onegather, &t_onegather));
+    InnerGraphSpec bestg = t_onegather < t_classic ? onegather : classic;
+    const double best_pair = std::min(t_classic, t_onegather);
     // the one-kernel iteration (variant 8, M_cg = I) competes with the best
     // step a + step b pair on the time of a whole iteration
-    const double best_pair = best_a + best;
     double best8 = 1e30;
     InnerGraphSpec best8g = bestg;
     for (int nst = 2; nst <= 3; ++nst) {
@@ -562,7 +579,8 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
     // graph (about 10 % at 128^3), so the one-kernel iteration must win by more
     g = best8 < 0.9 * best_pair ? best8g : bestg;
     if (getenv("MRCG_DEBUG"))
-      fprintf(stderr, "mrcg autotune: best pair %.4f ms, one-kernel %.4f ms\n", best_pair, best8);
+      fprintf(stderr, "mrcg autotune: two-gather pair %.4f ms, one-gather pair %.4f ms, one-kernel %.4f ms\n",
+              t_classic, t_onegather, best8);
     if (getenv("MRCG_DEBUG"))
       fprintf(stderr, "mrcg autotune: var_a=%d stages=%d grid_a=%d grid_b=%d\n", g.var_a, g.stages, g.grid_spmv,
               g.grid_stream_b);
@@ -825,7 +843,7 @@ mrcg_status mrcg_launch_config(mrcg_handle h, int32_t* cfg) {
   cfg[3] = h->spec.unroll;
   cfg[4] = h->k == 0 ? 0 : h->k <= 8 ? 8 : h->k <= 12 ? 12 : h->k <= 16 ? 16 : h->k <= 24 ? 24 : 32;
   cfg[5] = h->A.col16 ? 2 : 4;
-  cfg[6] = h->spec.var_a >= 5 ? h->spec.stages : 0;
+  cfg[6] = is_staged_variant(h->spec.var_a) ? h->spec.stages : 0;
   return MRCG_OK;
 }
 

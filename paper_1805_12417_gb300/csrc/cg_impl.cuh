@@ -148,18 +148,20 @@ __global__ void __launch_bounds__(kThreads) cg_init_kernel(CgArgs<T> a) {
     for (int e = 0; e < W; ++e) r[e] = (T)(v[i + e] * scale);
     st16(a.r + i, r);
     st16(a.z + i, zero);
-    st16(a.p_old + i, zero);
     if (a.q_old) st16(a.q_old + i, zero);  // one-kernel iteration: q_{-1} = 0
     if (jac) {
       T d[W];
       ld16(a.dinv + i, d);
 #pragma unroll
       for (int e = 0; e < W; ++e) s[e] = d[e] * r[e];
-      st16(a.s + i, s);
+      if (a.s != a.r) st16(a.s + i, s);
     } else {
 #pragma unroll
       for (int e = 0; e < W; ++e) s[e] = r[e];
     }
+    // p_0 = s_0: variants 9-11 use it as their first direction; the others
+    // form s + beta p with beta = 0, which is s again
+    st16(a.p_old + i, s);
 #pragma unroll
     for (int e = 0; e < W; ++e) {
       rs += r[e] * s[e];
@@ -666,6 +668,46 @@ __device__ __forceinline__ void issue_tile(const CgArgs<T>& a, unsigned char* b,
   }
 }
 
+// The producer lane of a staged kernel: refills a stage as soon as every
+// consumer warp has left it (tile offsets fetched one tile ahead), then waits
+// (bounded) until no copy it issued is still writing this block's shared
+// memory.  Tile i of this block is tile blockIdx.x + i * gridDim.x.
+template <typename T, bool FUSED>
+__device__ __forceinline__ void stage_producer(const CgArgs<T>& a, unsigned char* stage_mem, uint64_t* full,
+                                               uint64_t* empty, int* stalled, int64_t ntl, int nst) {
+  const int64_t G = gridDim.x;
+  const uint64_t stream_pol = l2_evict_first_policy();
+  int64_t issued = 0;
+  int64_t e0 = 0, e1 = 0;
+  if (ntl > 0) {
+    e0 = a.slice_ptr[(int64_t)blockIdx.x * kTileSlices];
+    e1 = a.slice_ptr[min((int64_t)(blockIdx.x + 1) * kTileSlices, a.nslices)];
+  }
+  // stage st of tile i = i mod nst, and the parity of its use (i / nst) & 1,
+  // kept incrementally (no integer division in the loop)
+  int st = 0;
+  uint32_t ph = 0;
+  int64_t t = blockIdx.x;
+  for (int64_t i = 0; i < ntl; ++i, t += G) {
+    if (a.stall_test && i >= 1) break;
+    if (i >= nst && !mbar_wait_or_abort(&empty[st], ph ^ 1u, stalled)) break;
+    const int64_t c0 = e0, c1 = e1;
+    if (i + 1 < ntl) {
+      e0 = a.slice_ptr[(t + G) * kTileSlices];
+      e1 = a.slice_ptr[min((t + G + 1) * kTileSlices, a.nslices)];
+    }
+    fence_proxy_async_smem();
+    issue_tile<T, FUSED>(a, stage_mem + (size_t)st * a.stage_bytes, &full[st], t, c0, c1, stream_pol);
+    ++issued;
+    if (++st == nst) {
+      st = 0;
+      ph ^= 1u;
+    }
+  }
+  for (int64_t j = issued > nst ? issued - nst : 0; j < issued; ++j)
+    mbar_wait(&full[j % nst], (uint32_t)((j / nst) & 1));
+}
+
 // ------------------------------------------------------------------ one-kernel CG iteration (variant 8)
 //
 // With M_cg = I the two kernels of a CG iteration fold into one.  Iteration i
@@ -885,41 +927,7 @@ __global__ void __launch_bounds__(kStagedThreads, MB) cg_step_a_staged_kernel(Cg
 #pragma unroll
   for (int l = 0; l < KS; ++l) wq[l] = 0;
   if (warp == kTileSlices) {
-    // producer warp (one lane): refill a stage as soon as every consumer warp
-    // has left it; tile offsets are fetched one tile ahead
-    if (lane == 0) {
-      const uint64_t stream_pol = l2_evict_first_policy();
-      int64_t issued = 0;
-      int64_t e0 = 0, e1 = 0;
-      if (ntl > 0) {
-        e0 = a.slice_ptr[(int64_t)blockIdx.x * kTileSlices];
-        e1 = a.slice_ptr[min((int64_t)(blockIdx.x + 1) * kTileSlices, a.nslices)];
-      }
-      // stage st of tile i = i mod nst, and the parity of its use (i / nst) & 1,
-      // kept incrementally (no integer division in the loop)
-      int st = 0;
-      uint32_t ph = 0;
-      int64_t t = blockIdx.x;
-      for (int64_t i = 0; i < ntl; ++i, t += G) {
-        if (a.stall_test && i >= 1) break;
-        if (i >= nst && !mbar_wait_or_abort(&empty[st], ph ^ 1u, &stalled)) break;
-        const int64_t c0 = e0, c1 = e1;
-        if (i + 1 < ntl) {
-          e0 = a.slice_ptr[(t + G) * kTileSlices];
-          e1 = a.slice_ptr[min((t + G + 1) * kTileSlices, a.nslices)];
-        }
-        fence_proxy_async_smem();
-        issue_tile<T, FUSED>(a, stage_mem + (size_t)st * a.stage_bytes, &full[st], t, c0, c1, stream_pol);
-        ++issued;
-        if (++st == nst) {
-          st = 0;
-          ph ^= 1u;
-        }
-      }
-      // no copy may still be writing this block's shared memory when it exits
-      for (int64_t j = issued > nst ? issued - nst : 0; j < issued; ++j)
-        mbar_wait(&full[j % nst], (uint32_t)((j / nst) & 1));
-    }
+    if (lane == 0) stage_producer<T, FUSED>(a, stage_mem, full, empty, &stalled, ntl, nst);
   } else if constexpr (FUSED) {
     // consumer warps of the one-kernel iteration (M_cg = I): warp w takes slice w of every tile
     const T alpha = alpha_of(S, T(0));
@@ -1155,6 +1163,350 @@ __global__ void __launch_bounds__(kStagedThreads, MB) cg_step_a_staged_kernel(Cg
   if (threadIdx.x == 0 && stalled) *(volatile int*)&S.done = kStall;
   if constexpr (FUSED) fused_reduce<T, KB, kStagedThreads / 32>(a, S, dot, rq, qq, rr, wq, cl);
   else step_a_reduce<T, KB, kStagedThreads / 32>(a, S, dot, wq, cl);
+}
+
+// ------------------------------------------------------------------ step a / step b with one gather per entry
+//
+// Variants 9-11 (M_cg = I or Jacobi) keep the next direction p explicit so
+// that the SpMV gathers one vector instead of rebuilding p' = s + beta p at
+// every gathered column.  That needs beta before step b, and step a has it:
+// its reduction also forms s^T q and q^T M_cg^{-1} q, and with the fresh
+// rho_i = r_i^T s_i of step b
+//   rho_{i+1} = (r - alpha q)^T M_cg^{-1} (r - alpha q)
+//             = rho_i - 2 alpha s^T q + alpha^2 q^T M_cg^{-1} q
+// (exact algebra; the base rho_i and all three dot products are of this
+// iteration, so the expansion's rounding does not carry over).  So
+//   step a: q = A p + V c ; partials p^T q, s^T q, q^T M_cg^{-1} q and
+//           V^T M_cg^{-1} (A p); last block: alpha, beta and the k-vector
+//           recurrences (V^T s_{i+1}, V^T p_{i+1}, c_{i+1})
+//   step b: z += alpha p ; r -= alpha q ; s = M_cg^{-1} r ; p = s + beta p
+//           (in place) ; partials r^T s (the fresh rho_{i+1}), r^T r;
+//           last block: the stopping test on the fresh values.
+// The stopping test and alpha use freshly reduced values; only beta comes
+// from the expansion.  Per row and iteration the two kernels stream as many
+// vector bytes as variants 0-7 (p, r read and q written in step a; p, q, z, r
+// read and z, r, p written in step b) and one gather per matrix entry fewer.
+
+// A p of a slice row: entries in groups of 8, every gather p[col] of a group
+// in flight before the products (vp, cp: column-major slice, stride 32)
+template <typename T, typename I, bool GLOBAL>
+__device__ __forceinline__ T pg_row(const T* vp, const I* cp, int row, bool delta, int w, const T* __restrict__ pv) {
+  T acc = 0;
+  for (int j0 = 0; j0 < w; j0 += 8) {
+    T av[8];
+    int cc[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (GLOBAL) {
+        av[j] = (j0 + j < w) ? ld_stream(vp + (size_t)(j0 + j) * kSlice) : (T)0;
+        cc[j] = (j0 + j < w) ? (delta ? row : 0) + (int)ld_stream(cp + (size_t)(j0 + j) * kSlice) : row;
+      } else {
+        av[j] = (j0 + j < w) ? vp[(j0 + j) * kSlice] : (T)0;
+        cc[j] = (j0 + j < w) ? (delta ? row : 0) + (int)cp[(j0 + j) * kSlice] : row;
+      }
+    }
+    T g[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) g[j] = (j0 + j < w) ? __ldg(pv + cc[j]) : (T)0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (j0 + j < w) acc += av[j] * g[j];
+  }
+  return acc;
+}
+
+// Reduction of step a (variants 9-11) and its last block: alpha from the
+// fresh rho, beta from the expansion, and the recurrences of V^T s, V^T p
+// and c = 2|Lambda| V^T p for the next step a.
+template <typename T, int KB, int NW>
+__device__ __forceinline__ void pg_reduce(const CgArgs<T>& a, CgState& S, T pq, T sq, T qdq,
+                                          const T (&wq)[KB > 0 ? KB : 1], const T* cl) {
+  constexpr int KS = KB > 0 ? KB : 1;
+  T part[KB + 3];
+  part[0] = pq;
+  part[1] = sq;
+  part[2] = qdq;
+#pragma unroll
+  for (int l = 0; l < KB; ++l) part[l + 3] = wq[l];
+  block_partials_t<T, KB + 3, NW>(part, a.k + 3, a.partials);
+  if (last_block_after_partials(&a.st->ticket)) {
+    constexpr int KK = KS * KS;
+    constexpr int NT = NW * 32;
+    constexpr int GPT = (KK + NT - 1) / NT;
+    __shared__ double gs[KK];
+    double greg[GPT];
+    const int kk = a.k * a.k;
+#pragma unroll
+    for (int j = 0; j < GPT; ++j) {
+      const int e = threadIdx.x + j * NT;
+      greg[j] = (e < kk) ? __ldcg(a.gram + e) : 0.0;
+    }
+    __shared__ double tot[KB + 3];
+    final_sums(a.partials, a.k + 3, tot);
+#pragma unroll
+    for (int j = 0; j < GPT; ++j) {
+      const int e = threadIdx.x + j * NT;
+      if (e < kk) gs[e] = greg[j];
+    }
+    __syncthreads();
+    const int l = threadIdx.x;
+    if (l < a.k) {  // V^T M_cg^{-1} q = V^T M_cg^{-1} A p + G c
+      double g = tot[l + 3];
+#pragma unroll 8
+      for (int m = 0; m < KB; ++m)
+        if (m < a.k) g += gs[m * a.k + l] * (double)cl[m];
+      S.vq[l] = g;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && *(volatile int*)&S.done == kRunning) {
+      const double kappa = tot[0], rho = S.rho;
+      S.kappa = kappa;
+      if (!isfinite(kappa)) {
+        S.done = kNonFinite;
+      } else if (kappa <= 0.0) {
+        S.done = kNotSpd;
+      } else {
+        const double alpha = rho / kappa;
+        const double rho_e = rho - 2.0 * alpha * tot[1] + alpha * alpha * tot[2];
+        // below its rounding floor the expansion is noise around a true
+        // rho_{i+1} << rho_i: beta is then ~0 either way (>= 0 is kept)
+        const double beta = (rho_e > 0.0 ? rho_e : 0.0) / rho;
+        if (!isfinite(rho_e)) {
+          S.done = kNonFinite;
+        } else {
+          S.alpha = alpha;
+          S.alpha32 = (float)alpha;
+          S.beta = beta;
+          S.beta32 = (float)beta;
+          for (int m = 0; m < a.k; ++m) {
+            S.u[m] -= alpha * S.vq[m];
+            S.t[m] = S.u[m] + beta * S.t[m];
+          }
+          publish_c(S, a.k);
+        }
+      }
+    }
+  }
+}
+
+// per-row part of step a (variants 9-11): q = A p + V c and the row's terms of the partials
+template <typename T, int KB, int VSTRIDE>
+__device__ __forceinline__ void pg_row_update(const CgArgs<T>& a, int64_t row, T ap, T pv, T rv, T d, bool jac,
+                                              const T* vrow, const T* cl, T& pq, T& sq, T& qdq,
+                                              T (&wq)[KB > 0 ? KB : 1]) {
+  const T aps = jac ? d * ap : ap;  // (M_cg^{-1} A p)_row
+  T q = ap;
+#pragma unroll
+  for (int l = 0; l < KB; ++l)
+    if (l < a.k) {
+      const T v = vrow[l * VSTRIDE];
+      q += v * cl[l];
+      wq[l] += v * aps;
+    }
+  a.q[row] = q;
+  const T sv = jac ? d * rv : rv;
+  pq += pv * q;
+  sq += sv * q;
+  qdq += jac ? d * q * q : q * q;
+}
+
+// Variants 9 / 10: operands staged by bulk copies as in variants 5 / 6 (the
+// "s" region of a stage holds r), registers capped for MB = 2 / 3 blocks per
+// SM (at 4 the three extra accumulators spill).
+template <typename T, int KB, int MB>
+__global__ void __launch_bounds__(kStagedThreads, MB) cg_step_a_pg_staged_kernel(CgArgs<T> a) {
+  constexpr int KS = KB > 0 ? KB : 1;
+  extern __shared__ __align__(128) unsigned char stage_mem[];
+  __shared__ __align__(8) uint64_t full[kMaxStages];
+  __shared__ __align__(8) uint64_t empty[kMaxStages];
+  __shared__ int stalled;
+  __shared__ T cl[KS];
+  CgState& S = a.st->cg;
+  if (S.done != kRunning) return;
+  if (threadIdx.x < KS) cl[threadIdx.x] = ((int)threadIdx.x < a.k) ? c_of(S, threadIdx.x, T(0)) : (T)0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool jac = a.dinv != nullptr;
+  const int nst = a.stages;
+  const int64_t ntiles = (a.nslices + kTileSlices - 1) / kTileSlices;
+  const int64_t ntl = (int64_t)blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t G = gridDim.x;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < nst; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], kTileSlices);
+    }
+    stalled = 0;
+    mbar_init_fence();
+  }
+  __syncthreads();
+  T pq = 0, sq = 0, qdq = 0;
+  T wq[KS];
+#pragma unroll
+  for (int l = 0; l < KS; ++l) wq[l] = 0;
+  if (warp == kTileSlices) {
+    if (lane == 0) stage_producer<T, false>(a, stage_mem, full, empty, &stalled, ntl, nst);
+  } else {
+    const T* __restrict__ pv = a.p_old;
+    int64_t c_t0 = 0, c_s0 = 0, c_s1 = 0;
+    if (ntl > 0) {
+      const int64_t sl = blockIdx.x * (int64_t)kTileSlices + warp;
+      c_t0 = a.slice_ptr[blockIdx.x * (int64_t)kTileSlices];
+      if (sl < a.nslices) {
+        c_s0 = a.slice_ptr[sl];
+        c_s1 = a.slice_ptr[sl + 1];
+      }
+    }
+    int st = 0;
+    uint32_t ph = 0;
+    int64_t t = blockIdx.x;
+    for (int64_t i = 0; i < ntl; ++i, t += G) {
+      const int64_t sl = t * kTileSlices + warp;
+      const int64_t t0 = c_t0, s0 = c_s0, s1 = c_s1;
+      if (i + 1 < ntl) {
+        const int64_t tn = t + G, sln = tn * kTileSlices + warp;
+        c_t0 = a.slice_ptr[tn * kTileSlices];
+        if (sln < a.nslices) {
+          c_s0 = a.slice_ptr[sln];
+          c_s1 = a.slice_ptr[sln + 1];
+        }
+      }
+      if (!mbar_wait_or_abort(&full[st], ph, &stalled)) break;
+      if (sl < a.nslices) {
+        const unsigned char* b = stage_mem + (size_t)st * a.stage_bytes;
+        const int off = (int)(s0 - t0) + lane;
+        const int w = (int)((s1 - s0) >> 5);
+        const int r = warp * kSlice + lane;
+        const int64_t row = sl * kSlice + lane;
+        const T* vp = reinterpret_cast<const T*>(b) + off;
+        const T ap = a.col16 ? pg_row<T, int16_t, false>(vp, reinterpret_cast<const int16_t*>(b + a.off_col) + off,
+                                                         (int)row, true, w, pv)
+                             : pg_row<T, int32_t, false>(vp, reinterpret_cast<const int32_t*>(b + a.off_col) + off,
+                                                         (int)row, false, w, pv);
+        const T pr = reinterpret_cast<const T*>(b + a.off_p)[r];
+        const T rr = reinterpret_cast<const T*>(b + a.off_s)[r];
+        const T d = jac ? reinterpret_cast<const T*>(b + a.off_d)[r] : (T)1;
+        pg_row_update<T, KB, kTileRows>(a, row, ap, pr, rr, d, jac, reinterpret_cast<const T*>(b + a.off_v) + r, cl,
+                                        pq, sq, qdq, wq);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[st]);
+      if (++st == nst) {
+        st = 0;
+        ph ^= 1u;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && stalled) *(volatile int*)&S.done = kStall;
+  pg_reduce<T, KB, kStagedThreads / 32>(a, S, pq, sq, qdq, wq, cl);
+}
+
+// Variant 11: the same arithmetic with plain loads, one warp per SELL slice,
+// grid-stride (matrices whose tiles do not fit two shared-memory stages);
+// registers capped for 4 blocks per SM in FP32, 2 in FP64 (no spills)
+template <typename T, int KB>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? 2 : 4) cg_step_a_pg_kernel(CgArgs<T> a) {
+  constexpr int KS = KB > 0 ? KB : 1;
+  CgState& S = a.st->cg;
+  if (S.done != kRunning) return;
+  __shared__ T cl[KS];
+  if (threadIdx.x < KS) cl[threadIdx.x] = ((int)threadIdx.x < a.k) ? c_of(S, threadIdx.x, T(0)) : (T)0;
+  __syncthreads();
+  const T* __restrict__ pv = a.p_old;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+  const bool jac = a.dinv != nullptr;
+  T pq = 0, sq = 0, qdq = 0;
+  T wq[KS];
+#pragma unroll
+  for (int l = 0; l < KS; ++l) wq[l] = 0;
+  for (int64_t sl = warp0; sl < a.nslices; sl += nwarps) {
+    const int64_t row = sl * kSlice + lane;
+    const T pr = pv[row];
+    const T rr = a.r[row];
+    const T d = jac ? a.dinv[row] : (T)1;
+    const int64_t base = a.slice_ptr[sl];
+    const int w = (int)((a.slice_ptr[sl + 1] - base) >> 5);
+    const T ap = a.col16 ? pg_row<T, int16_t, true>(a.val + base + lane, a.col16 + base + lane, (int)row, true, w, pv)
+                         : pg_row<T, int32_t, true>(a.val + base + lane, a.col + base + lane, (int)row, false, w, pv);
+    T vv[KS];  // this row of V_hat, all loads issued before the first use
+#pragma unroll
+    for (int l = 0; l < KS; ++l) vv[l] = (l < a.k) ? ld_stream(a.V + (size_t)l * a.n_pad + row) : (T)0;
+    pg_row_update<T, KB, 1>(a, row, ap, pr, rr, d, jac, vv, cl, pq, sq, qdq, wq);
+  }
+  pg_reduce<T, KB, kThreads / 32>(a, S, pq, sq, qdq, wq, cl);
+}
+
+// step b of variants 9-11: z += alpha p, r -= alpha q, s = M_cg^{-1} r,
+// p = s + beta p in place, and the stopping test on the fresh r^T s, r^T r
+template <typename T, int KB>
+__global__ void __launch_bounds__(kThreads) cg_step_b_pg_kernel(CgArgs<T> a) {
+  constexpr int W = V16<T>::W;
+  CgState& S = a.st->cg;
+  if (S.done != kRunning) return;
+  const T alpha = alpha_of(S, T(0));
+  const T beta = beta_of(S, T(0));
+  const bool jac = a.dinv != nullptr;
+  T rs = 0, rr = 0;
+  const int64_t nvec = a.n_pad / W;
+  const int64_t stride = (int64_t)gridDim.x * kThreads;
+  constexpr int U = 4;
+  for (int64_t iv0 = blockIdx.x * (int64_t)kThreads + threadIdx.x; iv0 < nvec; iv0 += stride * U) {
+    T pv[U][W], qv[U][W], zv[U][W], rv[U][W], d[U][W];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t iv = iv0 + u * stride;
+      if (iv < nvec) {
+        const int64_t i = iv * W;
+        ld16(a.p_old + i, pv[u]);
+        ld16(a.q + i, qv[u]);
+        ld16(a.z + i, zv[u]);
+        ld16(a.r + i, rv[u]);
+        if (jac) ld16(a.dinv + i, d[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t iv = iv0 + u * stride;
+      if (iv >= nvec) continue;
+      const int64_t i = iv * W;
+#pragma unroll
+      for (int e = 0; e < W; ++e) {
+        zv[u][e] += alpha * pv[u][e];
+        rv[u][e] -= alpha * qv[u][e];
+        const T s = jac ? d[u][e] * rv[u][e] : rv[u][e];
+        pv[u][e] = s + beta * pv[u][e];
+        rs += rv[u][e] * s;
+        if (jac) rr += rv[u][e] * rv[u][e];
+      }
+      st16(a.z + i, zv[u]);
+      st16(a.r + i, rv[u]);
+      st16(a.p_old + i, pv[u]);
+    }
+  }
+  T acc[2] = {rs, rr};
+  const int nv = jac ? 2 : 1;
+  block_partials_t<T, 2>(acc, nv, a.partials);
+  if (last_block_after_partials(&a.st->ticket)) {
+    __shared__ double tot[2];
+    final_sums(a.partials, nv, tot);
+    if (threadIdx.x == 0) {
+      const double rho_new = tot[0], rnorm = sqrt(jac ? tot[1] : tot[0]);
+      S.iters += 1;
+      if (!isfinite(rho_new) || !isfinite(rnorm)) {
+        S.done = kNonFinite;
+      } else if (rnorm <= S.tol_abs) {
+        S.done = kConverged;
+      } else if (S.iters >= S.maxit) {
+        S.done = kMaxIter;
+      } else if (rho_new <= 0.0) {
+        S.done = kBreakdown;
+      } else {
+        S.rho = rho_new;
+      }
+    }
+  }
 }
 
 // G = V^T M_cg^{-1} V (k x k, both triangles) from the kernels' own V and
@@ -1402,6 +1754,10 @@ void make_args(const InnerGraphSpec& spec, CgArgs<T> (&a)[2]) {
       x.q_old = reinterpret_cast<T*>(par == 0 ? spec.q2 : spec.q);
       x.s = x.r;
     }
+    if (is_pg_variant(spec.var_a)) {  // one p updated in place; s = M_cg^{-1} r formed where it is used
+      x.p_old = x.p_new = reinterpret_cast<T*>(spec.p0);
+      x.s = x.r;
+    }
   }
 }
 
@@ -1420,6 +1776,9 @@ cudaError_t add_kernel(cudaGraph_t g, cudaGraphNode_t* node, const cudaGraphNode
 template <typename T, int KB>
 const void* step_a_fn(int var) {
   switch (var) {
+    case 9: return (const void*)cg_step_a_pg_staged_kernel<T, KB, 2>;
+    case 10: return (const void*)cg_step_a_pg_staged_kernel<T, KB, 3>;
+    case 11: return (const void*)cg_step_a_pg_kernel<T, KB>;
     case 1: return (const void*)cg_step_a_kernel<T, KB, 1>;
     case 2: return (const void*)cg_step_a_kernel<T, KB, 2>;
     case 3: return (const void*)cg_step_a_kernel<T, KB, 3>;
@@ -1435,14 +1794,14 @@ const void* step_a_fn(int var) {
 // dynamic shared memory of the step-a launch (opting the staged kernel in above 48 KB)
 template <typename T, int KB>
 unsigned step_a_smem(const InnerGraphSpec& spec) {
-  if (spec.var_a < 5) return 0;
+  if (!is_staged_variant(spec.var_a)) return 0;
   const int bytes = stage_geo(spec).bytes * spec.stages;
   cudaFuncSetAttribute(step_a_fn<T, KB>(spec.var_a), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   return (unsigned)bytes;
 }
 
 // threads per block of the step-a launch
-int step_a_block(const InnerGraphSpec& spec) { return spec.var_a >= 5 ? kStagedThreads : kThreads; }
+int step_a_block(const InnerGraphSpec& spec) { return is_staged_variant(spec.var_a) ? kStagedThreads : kThreads; }
 
 template <typename T>
 cudaError_t launch_a(const void* fn, int grid, int block, cudaStream_t stream, CgArgs<T>& a, unsigned smem) {
@@ -1453,6 +1812,7 @@ cudaError_t launch_a(const void* fn, int grid, int block, cudaStream_t stream, C
 // step b of the spec's inner preconditioner
 template <typename T, int KB>
 const void* step_b_fn(const InnerGraphSpec& spec) {
+  if (is_pg_variant(spec.var_a)) return (const void*)cg_step_b_pg_kernel<T, KB>;
   return spec.dsmw ? (const void*)cg_step_b_smw_kernel<T, KB> : (const void*)cg_step_b_kernel<T, KB>;
 }
 

@@ -44,8 +44,9 @@ cudaError_t launch_gram(const InnerGraphSpec& spec, cudaStream_t stream, double*
 void inner_occupancy(const InnerGraphSpec& s, int* spmv_blocks_per_sm, int* stream_blocks_per_sm) {
   *spmv_blocks_per_sm = 1;
   *stream_blocks_per_sm = 1;
-  if ((s.var_a >= 5 && staged_smem_bytes(s) == 0) ||
-      (s.var_a == 8 && (s.dinv || s.dsmw || !s.r2 || !s.q2))) {  // the one-kernel iteration needs M_cg = I
+  if ((is_staged_variant(s.var_a) && staged_smem_bytes(s) == 0) ||
+      (s.var_a == 8 && (s.dinv || s.dsmw || !s.r2 || !s.q2)) ||  // the one-kernel iteration needs M_cg = I
+      (is_pg_variant(s.var_a) && s.dsmw)) {  // variants 9-11: M_cg = I or Jacobi
     *spmv_blocks_per_sm = 0;
     return;
   }

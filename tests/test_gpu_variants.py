@@ -34,9 +34,14 @@ import paper_1805_12417_gb300 as m  # noqa: E402
 DEV = torch.device("cuda:0")
 
 SHAPES = [(0, None), (1, None), (2, None), (3, None), (4, None), (5, 2), (5, 3), (5, 4), (6, 2), (6, 3), (7, 2),
-          (7, 3)]
+          (7, 3), (9, 2), (9, 3), (10, 2), (10, 4), (11, None)]
 SHAPE_IDS = ["v0", "v1", "v2", "v3", "v4", "staged2", "staged3", "staged4", "staged4bpsm_2", "staged4bpsm_3",
-             "pipelined2", "pipelined3"]
+             "pipelined2", "pipelined3", "onegather_staged2", "onegather_staged3", "onegather_staged3bpsm_2",
+             "onegather_staged3bpsm_4", "onegather_plain"]
+
+
+def is_staged(var):
+    return 5 <= var <= 10
 
 
 @pytest.fixture
@@ -55,7 +60,7 @@ def shape_env(monkeypatch):
 def _check_cfg(g, var, stages, idx_bytes=None):
     cfg = m.launch_config(g.h)
     assert cfg["step_a_variant"] == var
-    if var >= 5:
+    if is_staged(var):
         assert cfg["stages"] == stages
     if idx_bytes is not None:
         assert cfg["index_bytes"] == idx_bytes
@@ -92,8 +97,9 @@ def test_inner_variants_small_3d(shape_env, var, stages, prec, mcg):
 
 
 @pytest.mark.parametrize("k", [0, 1, 10, 13, 17, 32])
-@pytest.mark.parametrize("var,stages", [(1, None), (3, None), (5, 2), (6, 2), (7, 2)],
-                         ids=["v1", "v3", "staged2", "staged4bpsm", "pipelined2"])
+@pytest.mark.parametrize("var,stages", [(1, None), (3, None), (5, 2), (6, 2), (7, 2), (9, 2), (10, 2), (11, None)],
+                         ids=["v1", "v3", "staged2", "staged4bpsm", "pipelined2", "onegather_staged2",
+                              "onegather_staged3bpsm", "onegather_plain"])
 def test_inner_variants_k_buckets(shape_env, k, var, stages):
     """Every k bucket of the kernels (FP64 stages of k = 32 hold 86 KB, so two fit a block)."""
     p = shifted_laplacian_problem("t", (13, 11, 9), max(k, 1), seed=k) if k else None
@@ -120,22 +126,23 @@ def test_staged_long_rows(shape_env, idx16, prec, stages):
     rng = np.random.default_rng(22)
     V, _ = np.linalg.qr(rng.standard_normal((n, 6)))
     lam = -rng.uniform(0.5, 3.0, 6)
-    for var in (5, 7):
+    for var in (5, 7, 9, 11):
         shape_env(var, stages, idx16=idx16)
         _inner_vs_oracle(None, prec, m.MCG_JACOBI, 1e-7 if prec == m.FP64 else 1e-4, 23, var, stages,
                          idx_bytes=2 if idx16 else 4, V=V, lam=lam, sysargs=(rp, ci, va))
 
 
-def test_staged_falls_back_when_stages_do_not_fit(shape_env):
+@pytest.mark.parametrize("var", [5, 9])
+def test_staged_falls_back_when_stages_do_not_fit(shape_env, var):
     """FP64, k = 32: three stages of 86 KB exceed a block's shared memory; and
     rows of up to 64 entries make one stage of a tile 164 KB."""
-    shape_env(5, 3)
+    shape_env(var, 3)
     p = shifted_laplacian_problem("t", (13, 11, 9), 32, seed=32)
     with m.Solver.from_problem(p) as g:
         assert m.launch_config(g.h)["step_a_variant"] == 0
         z, st, it = g.inner_solve(np.ones(p.n), inner_tol=1e-8)
     assert st == m.OK and it > 0
-    shape_env(5, 2)
+    shape_env(var, 2)
     rp, ci, va = random_sparse_symmetric(3001, 21, density_rows=(2, 70), diag_shift=90.0, empty_rows=0)
     with m.Solver(3001, rp, ci, va) as g:
         assert m.launch_config(g.h)["step_a_variant"] == 0
@@ -143,8 +150,9 @@ def test_staged_falls_back_when_stages_do_not_fit(shape_env):
     assert st == m.OK and it > 0
 
 
-@pytest.mark.parametrize("var,stages", [(0, None), (5, 3), (6, 2), (7, 3)],
-                         ids=["v0", "staged3", "staged4bpsm", "pipelined3"])
+@pytest.mark.parametrize("var,stages", [(0, None), (5, 3), (6, 2), (7, 3), (9, 3), (10, 2), (11, None)],
+                         ids=["v0", "staged3", "staged4bpsm", "pipelined3", "onegather_staged3",
+                              "onegather_staged3bpsm", "onegather_plain"])
 def test_variants_full_solve_small(shape_env, var, stages):
     """A whole MINRES-CG solve on every step-a path agrees with the oracle's."""
     shape_env(var, stages)
@@ -237,3 +245,74 @@ def test_one_kernel_iteration_full_solves(shape_env):
     assert info.status == m.OK
     assert O.System.from_problem(p).true_relres(p.b, x.cpu().numpy()) <= 1e-10
 
+
+
+# ---------------------------------------------------------------- variants 9-11: one gather per matrix entry
+
+def test_one_gather_falls_back_with_smw(shape_env):
+    """Variants 9-11 cover M_cg = I and Jacobi; the MINRES-CG* M_cg keeps its own kernels."""
+    for var in (9, 11):
+        shape_env(var, 2)
+        with m.Solver.from_problem(small_3d(), inner_prec=m.MCG_SMW) as g:
+            assert m.launch_config(g.h)["step_a_variant"] == 0
+
+
+@pytest.mark.parametrize("prec", [m.FP64, m.MIXED_FP32], ids=["fp64", "mixed"])
+def test_one_gather_budget_returns_mth_iterate(shape_env, prec):
+    """z_m after an iteration cap equals the oracle's m-step iterate (FP64), and
+    the in-place p update leaves later solves on the same handle unaffected."""
+    shape_env(9, 2)
+    p = small_3d()
+    s = O.System.from_problem(p)
+    y = np.random.default_rng(9).standard_normal(p.n)
+    with m.Solver.from_problem(p, precision=prec) as g:
+        for m_it in (1, 2, 5, 9):
+            zr, itr, st_r = s.cg(y, 1e-300, m_it, O.MCG_IDENTITY)
+            z, st, it = g.inner_solve(y, inner_tol=1e-12, max_iters=m_it)
+            assert st == m.ERR_MAXITER and it == m_it
+            bar = 1e-10 if prec == m.FP64 else 1e-4
+            assert np.linalg.norm(z - zr) <= bar * np.linalg.norm(zr)
+
+
+def test_one_gather_full_size_mixed(shape_env):
+    """128^3 shifted Laplacian, mixed precision, one-gather staged step a: the
+    FP64 true residual reaches the benchmark tolerance and x matches x*."""
+    shape_env(9, 2)
+    p = lap3d_128_k10()
+    with m.Solver.from_problem(p, precision=m.MIXED_FP32) as g:
+        _check_cfg(g, 9, 2)
+        x = torch.zeros(p.n, dtype=torch.float64, device=DEV)
+        _, info = g.solve(torch.from_numpy(p.b).to(DEV), x, outer_tol=1e-10, inner_tol=1e-3)
+    x = x.cpu().numpy()
+    assert info.status == m.OK
+    assert O.System.from_problem(p).true_relres(p.b, x) <= 1e-10
+    assert np.linalg.norm(x - p.xstar) / np.linalg.norm(p.xstar) <= p.meta["cond"] * 1e-10 * 3
+
+
+# ---------------------------------------------------------------- a CG step that removes almost all of the residual
+
+@pytest.mark.parametrize("var,stages", [(8, 2), (9, 2)], ids=["one_kernel", "onegather"])
+@pytest.mark.parametrize("prec", [m.FP64, m.MIXED_FP32], ids=["fp64", "mixed"])
+def test_sharp_single_step_reduction(shape_env, var, stages, prec):
+    """A = diag(2 + 1e-3 u): the first CG step cuts ||r|| by about 1e-4, so the
+    expansion rho - 2 alpha r^T q + alpha^2 q^T q cancels to its rounding level
+    in FP32.  The solve must not stop on that noise: the returned z meets the
+    inner tolerance 1e-5 on the true M_mr residual (recomputed in FP64)."""
+    shape_env(var, stages)
+    n = 8192
+    rng = np.random.default_rng(31)
+    d = 2.0 + 1e-3 * rng.uniform(0.0, 1.0, n)
+    rp = np.arange(n + 1, dtype=np.int64)
+    ci = np.arange(n, dtype=np.int32)
+    s = O.System(rp, ci, d)
+    y = rng.standard_normal(n)
+    tol = 1e-5
+    zr, itr, st_r = s.cg(y, tol, 1000, O.MCG_IDENTITY)
+    assert st_r == O.OK and itr >= 2
+    with m.Solver(n, rp, ci, d, validate=False, precision=prec) as g:
+        _check_cfg(g, var, stages)
+        z, st, it = g.inner_solve(y, inner_tol=tol)
+    assert st == m.OK
+    res = np.linalg.norm(y - s.mmr_apply(z))
+    assert res <= tol * np.linalg.norm(y) * (1.001 if prec == m.FP64 else 1.5)
+    assert it <= itr + 2

@@ -11,6 +11,11 @@ systems.  Each model below follows the kernels' order of operations:
   * the one-kernel iteration (M_cg = I): each iteration updates r, then p,
     from the previous iteration's scalars, and the next residual norm comes
     from the expansion rho - 2 alpha r^T q + alpha^2 q^T q;
+  * the one-gather iteration (M_cg = I or Jacobi): step a forms q = M_mr p
+    with p explicit and, from the fresh rho_i = r_i^T s_i and the dots
+    s^T q, q^T M_cg^{-1} q of the same iteration, beta_i by the expansion
+    rho_i - 2 alpha s^T q + alpha^2 q^T M_cg^{-1} q; step b updates z, r and
+    p = s + beta p and reduces the fresh rho_{i+1} for the next alpha;
   * the inner right-hand side normalised to unit length and the solution
     scaled back (CG is homogeneous).
 
@@ -181,6 +186,81 @@ def test_one_kernel_iteration_reproduces_cg():
         assert np.linalg.norm(z - zo) <= 1e-10 * np.linalg.norm(zo), m
         for est, true in pairs:
             assert abs(est - true) <= 1e-10 * (y @ y)
+
+
+def _one_gather_cg(A, V, lam, y, m, mcg):
+    """Variants 9-11 with their step b: p is a stored vector (p_0 = s_0),
+    step a reduces p^T q, s^T q, q^T M_cg^{-1} q and V^T M_cg^{-1} A p; its
+    last block takes alpha from the fresh rho, beta from the expansion and
+    advances V^T s, V^T p and c; step b applies z, r, p updates and reduces
+    the fresh rho for the next iteration.  Returns z_m and the largest gaps of
+    the expanded rho_{i+1} and of the recurred V^T p from the direct ones."""
+    c2, minv = _ops(A, V, lam, mcg)
+    dinv = minv(np.ones(A.shape[0]))  # the diagonal of M_cg^{-1} (identity or Jacobi)
+    G = V.T @ (dinv[:, None] * V)
+    z = np.zeros_like(y)
+    r = y.copy()
+    s = dinv * r
+    p = s.copy()
+    rho = r @ s
+    vs = V.T @ s
+    vp = vs.copy()
+    gap_rho = gap_vp = 0.0
+    for _ in range(m):
+        # step a
+        c = c2 * vp
+        Ap = A @ p
+        q = Ap + V @ c
+        pq, sq, qdq = p @ q, s @ q, q @ (dinv * q)
+        vq = V.T @ (dinv * Ap) + G @ c
+        alpha = rho / pq
+        rho_e = rho - 2.0 * alpha * sq + alpha * alpha * qdq
+        beta = max(rho_e, 0.0) / rho
+        vs = vs - alpha * vq
+        vp = vs + beta * vp
+        # step b
+        z = z + alpha * p
+        r = r - alpha * q
+        s = dinv * r
+        p = s + beta * p
+        rho_fresh = r @ s
+        gap_rho = max(gap_rho, abs(rho_e - rho_fresh))
+        gap_vp = max(gap_vp, np.abs(vp - V.T @ p).max())
+        rho = rho_fresh
+    return z, gap_rho, gap_vp
+
+
+@pytest.mark.parametrize("mcg", [O.MCG_IDENTITY, O.MCG_JACOBI], ids=["identity", "jacobi"])
+def test_one_gather_iteration_reproduces_cg(mcg):
+    A, V, lam = _system(seed=19)
+    y = np.random.default_rng(8).standard_normal(A.shape[0])
+    for m in (1, 2, 7, 16):
+        z, gap_rho, gap_vp = _one_gather_cg(A, V, lam, y, m, mcg)
+        zo = _oracle_iterate(A, V, lam, y, m, mcg)
+        assert np.linalg.norm(z - zo) <= 1e-10 * np.linalg.norm(zo), m
+        assert gap_rho <= 1e-10 * (y @ y) and gap_vp <= 1e-10 * np.linalg.norm(y)
+
+
+def test_one_gather_model_detects_planted_mistakes():
+    """The model fails when the expansion's cross term loses its factor 2 or
+    beta comes from the previous iteration's rho: the pin is not vacuous."""
+    A, V, lam = _system(seed=19)
+    y = np.random.default_rng(8).standard_normal(A.shape[0])
+    zo = _oracle_iterate(A, V, lam, y, 7, O.MCG_JACOBI)
+    c2, minv = _ops(A, V, lam, O.MCG_JACOBI)
+    dinv = minv(np.ones(A.shape[0]))
+    M = lambda u: A @ u + V @ (c2 * (V.T @ u))  # noqa: E731
+    for mistake in ("cross_term", "stale_beta"):
+        z = np.zeros_like(y); r = y.copy(); s = dinv * r; p = s.copy(); rho = r @ s; rho_old = rho
+        for _ in range(7):
+            q = M(p)
+            alpha = rho / (p @ q)
+            cross = 1.0 if mistake == "cross_term" else 2.0
+            rho_e = rho - cross * alpha * (s @ q) + alpha * alpha * (q @ (dinv * q))
+            beta = rho_e / rho if mistake == "cross_term" else rho / rho_old
+            z = z + alpha * p; r = r - alpha * q; s = dinv * r; p = s + beta * p
+            rho_old, rho = rho, r @ s
+        assert np.linalg.norm(z - zo) > 1e-6 * np.linalg.norm(zo), mistake
 
 
 @pytest.mark.parametrize("mcg", [O.MCG_IDENTITY, O.MCG_JACOBI, O.MCG_SMW], ids=["identity", "jacobi", "smw"])
