@@ -167,6 +167,11 @@ TRAFFIC_RECORDS = "profiles/traffic.json"
 def step_a_kernel_name(cfg, prec="float"):
     """Name of the step-a kernel a launch configuration runs, as ncu prints it."""
     var, kb = cfg["step_a_variant"], cfg["k_bucket"]
+    if var in (9, 10, 12, 13):
+        mb, pipe = {9: (2, 0), 10: (3, 0), 12: (2, 1), 13: (3, 1)}[var]
+        return f"cg_step_a_pg_staged_kernel<{prec}, {kb}, {mb}, {pipe}>"
+    if var == 11:
+        return f"cg_step_a_pg_kernel<{prec}, {kb}>"
     if var == 8:
         return f"cg_step_a_staged_kernel<{prec}, {kb}, 3, 0, 1>"
     if var >= 5:

@@ -33,7 +33,7 @@
  *                         replay a shape reported by mrcg_launch_config (for
  *                         profilers, whose slowed launches mislead the tuner);
  *                         ignored when the shape does not fit the matrix.
- *  - MRCG_VAR_A (0-8), MRCG_STAGES (2-8), MRCG_BPSM_A, MRCG_BPSM_B
+ *  - MRCG_VAR_A (0-11), MRCG_STAGES (2-8), MRCG_BPSM_A, MRCG_BPSM_B
  *                         fix the step-a variant, its pipeline depth and the
  *                         blocks per SM of the two inner kernels; any of them
  *                         turns the autotuner off.
@@ -47,7 +47,7 @@
  *  - MRCG_DEBUG           print failed CUDA calls and the tuner's choice to
  *                         stderr.
  *  - MRCG_TEST_STALL=1    test hook: the producer warp of the staged step-a
- *                         kernels (variants 5-7) stops after the first tile, the
+ *                         kernels (variants 5-10) stops after the first tile, the
  *                         consumers' bounded waits give up and the call returns
  *                         MRCG_ERR_CUDA; the context stays usable.
  */
@@ -177,6 +177,26 @@ mrcg_status mrcg_inner_solve(mrcg_handle h, const double* y, double* z, double i
  * milliseconds (ms[1] is near zero for step-a variant 8, which has no step b).  Overwrites the handle's work vectors (not its matrix). */
 mrcg_status mrcg_time_inner_kernels(mrcg_handle h, int32_t iters, double* ms);
 
+/* In-situ time of one inner CG iteration (Eq. 2) as it runs inside the
+ * solver: the handle's own inner-CG graph (the device-side loop, or the
+ * host-driven loop under MRCG_INNER_LOOP=host) is launched on a fixed
+ * synthetic right-hand side for exactly 2U and 2U + iters iterations
+ * (U = iterations per loop body), each bracketed by CUDA events on the
+ * handle's stream, and *ms_per_iter receives the difference divided by iters
+ * (the per-solve kernels cancel).  8 <= iters <= 65536.  Overwrites the
+ * handle's work vectors (not its matrix).  Errors: MRCG_ERR_INVALID,
+ * MRCG_ERR_BREAKDOWN (the solve stopped before the count), MRCG_ERR_CUDA. */
+mrcg_status mrcg_time_inner_graph(mrcg_handle h, int32_t iters, double* ms_per_iter);
+
+/* Measured FP64 fused-multiply-add throughput of the current device, in
+ * TFLOP/s (2 flops per FMA): eight independent FMA chains per thread, eight
+ * 256-thread blocks per SM, best of seven CUDA-event-timed launches after
+ * three warm-ups.  The denominator of the FP64 kernels' arithmetic roofline.
+ * ms (may be NULL) receives the best launch's duration.  Allocates and frees
+ * a small scratch buffer.  Errors: MRCG_ERR_INVALID (tflops NULL),
+ * MRCG_ERR_OOM, MRCG_ERR_CUDA. */
+mrcg_status mrcg_fp64_fma_peak(double* tflops, double* ms);
+
 /* Launch configuration chosen for the handle's inner-CG kernels (at create,
  * by timing candidate shapes on this matrix unless MRCG_AUTOTUNE=0):
  * cfg[0] step-a variant (0: V_hat rows loaded before the SpMV, 1: after it,
@@ -185,11 +205,15 @@ mrcg_status mrcg_time_inner_kernels(mrcg_handle h, int32_t iters, double* ms);
  * memory by bulk copies, a persistent grid over tiles of 8 slices, registers
  * capped for 2 / 4 blocks per SM, 7: as 5 with each warp's gathers issued
  * one tile ahead, 8: the whole CG iteration in one staged kernel, with the
- * residual norm by expansion and no step b; M_cg = I only), cfg[1] step-a grid (blocks), cfg[2] step-b grid,
+ * residual norm by expansion and no step b; M_cg = I only; 9 / 10: staged as
+ * 5 with registers capped for 2 / 3 blocks per SM and 11: plain loads, all
+ * three gathering only p (one load per matrix entry) with beta formed by
+ * expansion in step a and p = s + beta p done by their own step b; M_cg = I
+ * or Jacobi), cfg[1] step-a grid (blocks), cfg[2] step-b grid,
  * cfg[3] CG iterations per body of the device loop, cfg[4] k bucket of the
  * kernels (0, 8, 12, 16, 24 or 32), cfg[5] bytes per column index read by the
  * inner kernels (2: 16-bit col - row deltas, used when every delta fits; 4),
- * cfg[6] shared-memory stages of variants 5 to 8 (0 for the others).
+ * cfg[6] shared-memory stages of variants 5 to 10 (0 for the others).
  * cfg must hold 7 values. */
 mrcg_status mrcg_launch_config(mrcg_handle h, int32_t* cfg);
 

@@ -19,21 +19,33 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mrcg_oracle.c")
 _HDR = os.path.join(_HERE, "mrcg_oracle.h")
 _OUT = os.path.join(_HERE, "_build", "liboracle.so")
+_OUT_OMP = os.path.join(_HERE, "_build", "liboracle_omp.so")
 
 OK, ERR_INVALID, ERR_NOT_SPD, ERR_BREAKDOWN, ERR_MAXITER, ERR_NONFINITE = range(6)
 MCG_IDENTITY, MCG_JACOBI, MCG_SMW = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "NOT_SPD", 3: "BREAKDOWN", 4: "MAXITER", 5: "NONFINITE"}
 
 
+def _build_one(out, extra):
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    stale = (not os.path.exists(out)) or any(os.path.getmtime(p) > os.path.getmtime(out) for p in (_SRC, _HDR))
+    if stale:
+        tmp = out + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", *extra, "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
-    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
-    stale = (not os.path.exists(_OUT)) or any(
-        os.path.getmtime(p) > os.path.getmtime(_OUT) for p in (_SRC, _HDR))
-    if force or stale:
-        tmp = _OUT + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _OUT)
-    return _OUT
+    """Compile the serial oracle (the pinned one) and its all-core build for
+    the CPU baseline (the same source with -fopenmp); returns the serial
+    library's path."""
+    if force:
+        for p in (_OUT, _OUT_OMP):
+            if os.path.exists(p):
+                os.remove(p)
+    _build_one(_OUT_OMP, ["-fopenmp"])
+    return _build_one(_OUT, [])
 
 
 class _System(C.Structure):
@@ -51,31 +63,54 @@ PREC_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int64, C.POINTER(C.c_double), C.P
                       C.c_int64, C.POINTER(C.c_int64))
 
 _lib = None
+_lib_omp = None
 
 
-def lib():
-    global _lib
+def lib(threads: bool = False):
+    """The serial oracle library, or (threads=True) its all-core OpenMP build,
+    which the benchmark's CPU baseline times (same arithmetic, the length-n
+    loops split over the cores)."""
+    global _lib, _lib_omp
+    if threads:
+        if _lib_omp is None:
+            build()
+            _lib_omp = _declare(C.CDLL(_OUT_OMP))
+        return _lib_omp
     if _lib is None:
-        _lib = C.CDLL(build())
-        P = C.c_void_p
-        _lib.orc_csr_spmv.argtypes = [C.POINTER(_System), P, P]
-        _lib.orc_mmr_apply.argtypes = [C.POINTER(_System), P, P, P, C.POINTER(C.c_int64)]
-        _lib.orc_mmr_diag.argtypes = [C.POINTER(_System), P]
-        _lib.orc_mcg_apply.argtypes = [C.POINTER(_System), C.c_int, P, P, P]
-        _lib.orc_mcg_apply.restype = C.c_int
-        _lib.orc_cg.argtypes = [C.POINTER(_System), C.c_int, P, P, C.c_double, C.c_int64,
-                                C.POINTER(C.c_int64), P]
-        _lib.orc_cg.restype = C.c_int
-        _lib.orc_minres.argtypes = [C.POINTER(_System), P, P, PREC_FN, P, C.c_double, C.c_int32,
-                                    C.c_int64, C.c_double, P, P, C.c_int32, C.POINTER(_Info)]
-        _lib.orc_minres.restype = C.c_int
-        _lib.orc_minres_cg.argtypes = [C.POINTER(_System), C.c_int, P, P, C.c_double, C.c_double,
-                                       C.c_int64, C.c_int32, C.c_double, P, P, C.c_int32, C.POINTER(_Info)]
-        _lib.orc_minres_cg.restype = C.c_int
-        _lib.orc_abs_2x2.argtypes = [C.c_double, C.c_double, C.c_double, P, P, P]
-        _lib.orc_true_relres.argtypes = [C.POINTER(_System), P, P, P]
-        _lib.orc_true_relres.restype = C.c_double
+        _lib = _declare(C.CDLL(build()))
     return _lib
+
+
+def threads_available() -> int:
+    """Cores the all-core build may use: OMP_NUM_THREADS if set, else the
+    process's CPU affinity."""
+    env = os.environ.get("OMP_NUM_THREADS")
+    if env and env.isdigit():
+        return int(env)
+    return len(os.sched_getaffinity(0))
+
+
+def _declare(L):
+    """Argument and result types of the C entry points."""
+    P = C.c_void_p
+    L.orc_csr_spmv.argtypes = [C.POINTER(_System), P, P]
+    L.orc_mmr_apply.argtypes = [C.POINTER(_System), P, P, P, C.POINTER(C.c_int64)]
+    L.orc_mmr_diag.argtypes = [C.POINTER(_System), P]
+    L.orc_mcg_apply.argtypes = [C.POINTER(_System), C.c_int, P, P, P]
+    L.orc_mcg_apply.restype = C.c_int
+    L.orc_cg.argtypes = [C.POINTER(_System), C.c_int, P, P, C.c_double, C.c_int64,
+                            C.POINTER(C.c_int64), P]
+    L.orc_cg.restype = C.c_int
+    L.orc_minres.argtypes = [C.POINTER(_System), P, P, PREC_FN, P, C.c_double, C.c_int32,
+                                C.c_int64, C.c_double, P, P, C.c_int32, C.POINTER(_Info)]
+    L.orc_minres.restype = C.c_int
+    L.orc_minres_cg.argtypes = [C.POINTER(_System), C.c_int, P, P, C.c_double, C.c_double,
+                                   C.c_int64, C.c_int32, C.c_double, P, P, C.c_int32, C.POINTER(_Info)]
+    L.orc_minres_cg.restype = C.c_int
+    L.orc_abs_2x2.argtypes = [C.c_double, C.c_double, C.c_double, P, P, P]
+    L.orc_true_relres.argtypes = [C.POINTER(_System), P, P, P]
+    L.orc_true_relres.restype = C.c_double
+    return L
 
 
 def _f64(a):
@@ -167,12 +202,13 @@ def _result(x, info, hr, he):
 
 
 def minres_cg(sys: System, b, x0=None, outer_tol=1e-10, inner_tol=1e-3, max_iters=10**9,
-              max_outer=200, restart_factor=0.5, mcg=MCG_IDENTITY, hist_cap=4096) -> SolveResult:
-    """Alg. 1: outer preconditioned MINRES, inner CG on M_mr (all FP64)."""
+              max_outer=200, restart_factor=0.5, mcg=MCG_IDENTITY, hist_cap=4096, threads=False) -> SolveResult:
+    """Alg. 1: outer preconditioned MINRES, inner CG on M_mr (all FP64).
+    threads=True runs the all-core build (CPU baseline timing only)."""
     b = _f64(b)
     x = np.zeros(sys.n) if x0 is None else _f64(x0).copy()
     hr = np.zeros(hist_cap); he = np.zeros(hist_cap); info = _Info()
-    lib().orc_minres_cg(sys.ptr, mcg, b.ctypes.data, x.ctypes.data, outer_tol, inner_tol, int(max_iters),
+    lib(threads).orc_minres_cg(sys.ptr, mcg, b.ctypes.data, x.ctypes.data, outer_tol, inner_tol, int(max_iters),
                         int(max_outer), restart_factor, hr.ctypes.data, he.ctypes.data, hist_cap,
                         C.byref(info))
     return _result(x, info, hr, he)

@@ -16,8 +16,21 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* The same source builds twice: serially (the pinned oracle) and with
+ * -fopenmp for the all-core CPU baseline, where these markers split the
+ * length-n loops over the cores (the reductions then sum in another order).
+ * Without OpenMP they expand to nothing. */
+#ifdef _OPENMP
+#define ORC_FOR _Pragma("omp parallel for schedule(static)")
+#define ORC_FOR_SUM _Pragma("omp parallel for schedule(static) reduction(+ : s)")
+#else
+#define ORC_FOR
+#define ORC_FOR_SUM
+#endif
+
 static double dot(int64_t n, const double* a, const double* b) {
   double s = 0.0;
+  ORC_FOR_SUM
   for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
   return s;
 }
@@ -26,6 +39,7 @@ static double nrm2(int64_t n, const double* a) { return sqrt(dot(n, a, a)); }
 
 /* Alg. 1: products with the sparse coefficient matrix A. */
 void orc_csr_spmv(const orc_system* s, const double* x, double* y) {
+  ORC_FOR
   for (int64_t i = 0; i < s->n; ++i) {
     double acc = 0.0;
     for (int64_t p = s->rowptr[i]; p < s->rowptr[i + 1]; ++p) acc += s->val[p] * x[s->colind[p]];
@@ -40,6 +54,7 @@ void orc_mmr_apply(const orc_system* s, const double* u, double* out, double* t,
   const int32_t k = s->k;
   for (int32_t j = 0; j < k; ++j) t[j] = dot(n, s->V + (int64_t)j * n, u); /* 2n flops each */
   for (int32_t j = 0; j < k; ++j) t[j] *= 2.0 * fabs(s->lam[j]);           /* 1 flop each: the factor 2|lam| is data */
+  ORC_FOR
   for (int64_t i = 0; i < n; ++i) {
     double acc = 0.0;
     for (int64_t p = s->rowptr[i]; p < s->rowptr[i + 1]; ++p) acc += s->val[p] * u[s->colind[p]];
@@ -154,6 +169,7 @@ int orc_cg(const orc_system* s, int mcg, const double* y, double* z, double tol,
     if (!isfinite(kappa)) return ORC_ERR_NONFINITE;
     if (kappa <= 0.0) return ORC_ERR_NOT_SPD;
     const double alpha = rho / kappa;
+    ORC_FOR
     for (int64_t i = 0; i < n; ++i) {
       z[i] += alpha * p[i];
       r[i] -= alpha * q[i];
@@ -165,6 +181,7 @@ int orc_cg(const orc_system* s, int mcg, const double* y, double* z, double tol,
     if (mcg == ORC_MCG_SMW) {
       smw_apply(s, dinv, r, sv, t);
     } else {
+      ORC_FOR
       for (int64_t i = 0; i < n; ++i) sv[i] = dinv[i] * r[i];
     }
     const double rho_new = dot(n, r, sv);
@@ -172,6 +189,7 @@ int orc_cg(const orc_system* s, int mcg, const double* y, double* z, double tol,
     if (rho_new == 0.0) return ORC_ERR_BREAKDOWN; /* r^T M_cg^{-1} r = 0 with r != 0: indefinite M_cg */
     const double beta = rho_new / rho;
     rho = rho_new;
+    ORC_FOR
     for (int64_t i = 0; i < n; ++i) p[i] = sv[i] + beta * p[i];
   }
   return ORC_ERR_MAXITER;
@@ -243,9 +261,11 @@ int orc_minres(const orc_system* s, const double* b, double* x, orc_prec_fn prec
     while (!restart) {
       if (info->outer_iters >= max_outer) { status = ORC_ERR_MAXITER; goto done; }
       /* Lanczos step */
+      ORC_FOR
       for (int64_t i = 0; i < n; ++i) z[i] /= gamma;
       orc_csr_spmv(s, z, az);
       const double delta = dot(n, z, az);
+      ORC_FOR
       for (int64_t i = 0; i < n; ++i)
         v_new[i] = az[i] - (delta / gamma) * v[i] - (gamma / gamma_old) * v_old[i];
       rc = prec(prec_ctx, n, v_new, z_new, max_inner_total - info->inner_iters_total, &used);
@@ -265,6 +285,7 @@ int orc_minres(const orc_system* s, const double* b, double* x, orc_prec_fn prec
       const double c_new = a0 / a1;
       const double s_new = gamma_new / a1;
       /* direction and solution update */
+      ORC_FOR
       for (int64_t i = 0; i < n; ++i) {
         w_new[i] = (z[i] - a3 * w_old[i] - a2 * w[i]) / a1;
         x[i] += c_new * eta * w_new[i];

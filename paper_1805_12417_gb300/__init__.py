@@ -65,6 +65,10 @@ def lib() -> C.CDLL:
         L.mrcg_time_inner_kernels.restype = C.c_int
         L.mrcg_launch_config.argtypes = [P, P]
         L.mrcg_launch_config.restype = C.c_int
+        L.mrcg_time_inner_graph.argtypes = [P, C.c_int32, C.POINTER(C.c_double)]
+        L.mrcg_time_inner_graph.restype = C.c_int
+        L.mrcg_fp64_fma_peak.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        L.mrcg_fp64_fma_peak.restype = C.c_int
         L.mrcg_batch_create.argtypes = [C.c_int32, C.POINTER(CreateArgs), C.POINTER(C.c_void_p)]
         L.mrcg_batch_create.restype = C.c_int
         L.mrcg_batched_solve.argtypes = [P, P, P, C.c_double, C.c_double, C.c_int64, C.POINTER(Info)]
@@ -239,6 +243,24 @@ def time_inner_kernels(h, iters=20):
     if st != OK:
         raise MrcgError(st, "mrcg_time_inner_kernels")
     return float(ms[0]), float(ms[1])
+
+
+def time_inner_graph(h, iters=256):
+    """mrcg_time_inner_graph: ms of one inner CG iteration inside the solver's own loop."""
+    ms = C.c_double(0.0)
+    st = lib().mrcg_time_inner_graph(h, int(iters), C.byref(ms))
+    if st != OK:
+        raise MrcgError(st, "mrcg_time_inner_graph")
+    return float(ms.value)
+
+
+def fp64_fma_peak():
+    """mrcg_fp64_fma_peak: (TFLOP/s, ms of the best launch) of FP64 FMAs on the current device."""
+    tf, ms = C.c_double(0.0), C.c_double(0.0)
+    st = lib().mrcg_fp64_fma_peak(C.byref(tf), C.byref(ms))
+    if st != OK:
+        raise MrcgError(st, "mrcg_fp64_fma_peak")
+    return float(tf.value), float(ms.value)
 
 
 class Solver:

@@ -551,7 +551,7 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
     InnerGraphSpec classic = g, onegather = g;
     double t_classic = 1e30, t_onegather = 1e30;
     ST(tune_family({0, 1, 2, 3, 4, 5, 6, 7}, &classic, &t_classic));
-    ST(tune_family({9, 10, 11}, &onegather, &t_onegather));
+    ST(tune_family({9, 10, 11, 12, 13}, &onegather, &t_onegather));
     InnerGraphSpec bestg = t_onegather < t_classic ? onegather : classic;
     const double best_pair = std::min(t_classic, t_onegather);
     // the one-kernel iteration (variant 8, M_cg = I) competes with the best
@@ -860,6 +860,45 @@ mrcg_status mrcg_time_inner_kernels(mrcg_handle h, int32_t iters, double* ms) {
   ms[1] = t4[3];
   ST(read_state(h));
   if (h->h_st->cg.done != kRunning && h->h_st->cg.iters < iters) return MRCG_ERR_BREAKDOWN;
+  return MRCG_OK;
+}
+
+mrcg_status mrcg_time_inner_graph(mrcg_handle h, int32_t iters, double* ms_per_iter) {
+  if (!h || !ms_per_iter || iters < 8 || iters > 65536) return MRCG_ERR_INVALID;
+  DeviceGuard g(h->device);
+  // a fixed right-hand side (the pattern of the standalone timing) in v[0]
+  std::vector<double> pat((size_t)h->n_pad, 0.0);
+  for (int64_t i = 0; i < h->n; ++i) pat[i] = 1.0 + 0.125 * (double)(i % 7) - 0.0625 * (double)(i % 3);
+  CK(cudaMemcpyAsync(h->v[0], pat.data(), pat.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  // one inner solve of exactly `n_it` iterations (tolerance 1e-300: only the
+  // budget stops it), bracketed by events on the handle's stream
+  auto timed = [&](long long n_it, float* ms) -> mrcg_status {
+    reset_state(h, 1e-300, n_it);
+    h->h_init->cg.vin = h->v[0];
+    h->h_init->cg.zout = h->zraw;
+    ST(upload_state(h));
+    CK(cudaEventRecord(e0, h->stream));
+    ST(run_inner(h));
+    CK(cudaEventRecord(e1, h->stream));
+    CK(cudaEventSynchronize(e1));
+    CK(cudaEventElapsedTime(ms, e0, e1));
+    ST(read_state(h));
+    if (h->h_st->cg.iters != n_it) return MRCG_ERR_BREAKDOWN;
+    return MRCG_OK;
+  };
+  const long long base = 2LL * h->unroll;
+  float t_short = 0.f, t_long = 0.f, unused = 0.f;
+  mrcg_status st = timed(base, &unused);  // warm-up
+  // the difference of two solves cancels the per-solve kernels (norm, init, finish)
+  if (st == MRCG_OK) st = timed(base, &t_short);
+  if (st == MRCG_OK) st = timed(base + iters, &t_long);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != MRCG_OK) return st;
+  *ms_per_iter = (double)(t_long - t_short) / (double)iters;
   return MRCG_OK;
 }
 

@@ -1312,8 +1312,9 @@ __device__ __forceinline__ void pg_row_update(const CgArgs<T>& a, int64_t row, T
 
 // Variants 9 / 10: operands staged by bulk copies as in variants 5 / 6 (the
 // "s" region of a stage holds r), registers capped for MB = 2 / 3 blocks per
-// SM (at 4 the three extra accumulators spill).
-template <typename T, int KB, int MB>
+// SM (at 4 the three extra accumulators spill); 12 / 13: the same with each
+// warp's gathers issued one tile ahead (PIPE).
+template <typename T, int KB, int MB, bool PIPE>
 __global__ void __launch_bounds__(kStagedThreads, MB) cg_step_a_pg_staged_kernel(CgArgs<T> a) {
   constexpr int KS = KB > 0 ? KB : 1;
   extern __shared__ __align__(128) unsigned char stage_mem[];
@@ -1345,6 +1346,96 @@ __global__ void __launch_bounds__(kStagedThreads, MB) cg_step_a_pg_staged_kernel
   for (int l = 0; l < KS; ++l) wq[l] = 0;
   if (warp == kTileSlices) {
     if (lane == 0) stage_producer<T, false>(a, stage_mem, full, empty, &stalled, ntl, nst);
+  } else if constexpr (PIPE) {
+    // software-pipelined consumers: the gathers of this warp's slice of tile
+    // i + 1 are in flight while it finishes tile i, so two L2 round trips
+    // overlap per warp
+    const T* __restrict__ pv = a.p_old;
+    const bool d16 = a.col16 != nullptr;
+    int st = 0;
+    uint32_t ph = 0;
+    int64_t t = blockIdx.x;
+    int cur_off = 0, cur_w = 0;                 // this warp's slice of the tile being finished
+    int64_t c_t0 = 0, c_s0 = 0, c_s1 = 0;       // offsets of the next tile (fetched ahead)
+    T gc[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) gc[j] = 0;
+    auto offsets = [&](int64_t tt) {
+      const int64_t sl = tt * kTileSlices + warp;
+      c_t0 = a.slice_ptr[tt * kTileSlices];
+      if (sl < a.nslices) {
+        c_s0 = a.slice_ptr[sl];
+        c_s1 = a.slice_ptr[sl + 1];
+      } else {
+        c_s0 = c_s1 = c_t0;
+      }
+    };
+    // issue the gathers p[col] of the first eight entries of this warp's slice of tile tt (stage sst, landed)
+    auto start = [&](int64_t tt, int sst, T (&g)[8]) {
+      const int64_t sl = tt * kTileSlices + warp;
+      cur_off = (int)(c_s0 - c_t0) + lane;
+      cur_w = (int)((c_s1 - c_s0) >> 5);
+      if (sl < a.nslices) {
+        const unsigned char* b = stage_mem + (size_t)sst * a.stage_bytes;
+        const int row = (int)(sl * kSlice + lane);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int c = j < cur_w ? (d16 ? row + (int)reinterpret_cast<const int16_t*>(b + a.off_col)[cur_off + j * kSlice]
+                                         : reinterpret_cast<const int32_t*>(b + a.off_col)[cur_off + j * kSlice])
+                                  : row;
+          g[j] = j < cur_w ? __ldg(pv + c) : (T)0;
+        }
+      }
+    };
+    bool alive = true;
+    if (ntl > 0) {
+      offsets(t);
+      alive = mbar_wait_or_abort(&full[0], 0u, &stalled);
+      if (alive) start(t, 0, gc);
+      if (ntl > 1) offsets(t + G);
+    }
+    for (int64_t i = 0; alive && i < ntl; ++i, t += G) {
+      const int off = cur_off, w = cur_w;
+      const int stn = st + 1 == nst ? 0 : st + 1;
+      const uint32_t phn = st + 1 == nst ? ph ^ 1u : ph;
+      T gn[8];
+      if (i + 1 < ntl) {
+        if (!mbar_wait_or_abort(&full[stn], phn, &stalled)) break;
+        start(t + G, stn, gn);
+        if (i + 2 < ntl) offsets(t + 2 * G);
+      }
+      const int64_t sl = t * kTileSlices + warp;
+      if (sl < a.nslices) {
+        const unsigned char* b = stage_mem + (size_t)st * a.stage_bytes;
+        const int r = warp * kSlice + lane;
+        const int64_t row = sl * kSlice + lane;
+        const T* vp = reinterpret_cast<const T*>(b) + off;
+        T ap = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (j < w) ap += vp[j * kSlice] * gc[j];
+        if (w > 8)
+          ap += d16 ? pg_row<T, int16_t, false>(vp + 8 * kSlice,
+                                                reinterpret_cast<const int16_t*>(b + a.off_col) + off + 8 * kSlice,
+                                                (int)row, true, w - 8, pv)
+                    : pg_row<T, int32_t, false>(vp + 8 * kSlice,
+                                                reinterpret_cast<const int32_t*>(b + a.off_col) + off + 8 * kSlice,
+                                                (int)row, false, w - 8, pv);
+        const T pr = reinterpret_cast<const T*>(b + a.off_p)[r];
+        const T rr = reinterpret_cast<const T*>(b + a.off_s)[r];
+        const T d = jac ? reinterpret_cast<const T*>(b + a.off_d)[r] : (T)1;
+        pg_row_update<T, KB, kTileRows>(a, row, ap, pr, rr, d, jac, reinterpret_cast<const T*>(b + a.off_v) + r, cl,
+                                        pq, sq, qdq, wq);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[st]);
+      if (i + 1 < ntl) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) gc[j] = gn[j];
+      }
+      st = stn;
+      ph = phn;
+    }
   } else {
     const T* __restrict__ pv = a.p_old;
     int64_t c_t0 = 0, c_s0 = 0, c_s1 = 0;
@@ -1776,9 +1867,11 @@ cudaError_t add_kernel(cudaGraph_t g, cudaGraphNode_t* node, const cudaGraphNode
 template <typename T, int KB>
 const void* step_a_fn(int var) {
   switch (var) {
-    case 9: return (const void*)cg_step_a_pg_staged_kernel<T, KB, 2>;
-    case 10: return (const void*)cg_step_a_pg_staged_kernel<T, KB, 3>;
+    case 9: return (const void*)cg_step_a_pg_staged_kernel<T, KB, 2, false>;
+    case 10: return (const void*)cg_step_a_pg_staged_kernel<T, KB, 3, false>;
     case 11: return (const void*)cg_step_a_pg_kernel<T, KB>;
+    case 12: return (const void*)cg_step_a_pg_staged_kernel<T, KB, 2, true>;
+    case 13: return (const void*)cg_step_a_pg_staged_kernel<T, KB, 3, true>;
     case 1: return (const void*)cg_step_a_kernel<T, KB, 1>;
     case 2: return (const void*)cg_step_a_kernel<T, KB, 2>;
     case 3: return (const void*)cg_step_a_kernel<T, KB, 3>;

@@ -35,17 +35,18 @@ struct InnerGraphSpec {
                  // 2 / 4 blocks per SM; 7: as 5 with the gathers issued one tile ahead;
                  // 8: the whole CG iteration in one staged kernel, M_cg = I only;
                  // 9 / 10: staged as 5 / 6 and 11: plain, all three with one gather per
-                 // matrix entry (p explicit, beta by expansion in step a; M_cg = I or Jacobi))
+                 // matrix entry (p explicit, beta by expansion in step a; M_cg = I or Jacobi);
+                 // 12 / 13: 9 / 10 with each warp's gathers issued one tile ahead)
   int64_t tile_entries = 0;  // most SELL entries in one tile of 8 slices (sizes the staged variant's buffers)
   int stages = 3;            // staged variant: shared-memory stages per block
   bool stall_test = false;   // test hook: the staged producer issues only the first tile
 };
 
 // step-a variants whose operands are staged in shared memory by bulk copies
-inline bool is_staged_variant(int var) { return var >= 5 && var <= 10; }
-// step-a variants 9-11: one gather per matrix entry, p kept explicit (their own step b)
-inline bool is_pg_variant(int var) { return var >= 9 && var <= 11; }
-constexpr int kNumStepAVariants = 12;
+inline bool is_staged_variant(int var) { return (var >= 5 && var <= 10) || var == 12 || var == 13; }
+// step-a variants 9-13: one gather per matrix entry, p kept explicit (their own step b)
+inline bool is_pg_variant(int var) { return var >= 9 && var <= 13; }
+constexpr int kNumStepAVariants = 14;
 
 cudaError_t build_inner_graph(const InnerGraphSpec& spec, cudaGraph_t* graph);
 // the same inner solve with the loop driven from the host (profiling mode)

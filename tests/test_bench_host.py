@@ -19,6 +19,11 @@ import bench  # noqa: E402
     (6, "cg_step_a_staged_kernel<float, 12, 4, 0, 0>"),
     (7, "cg_step_a_staged_kernel<float, 12, 2, 1, 0>"),
     (8, "cg_step_a_staged_kernel<float, 12, 3, 0, 1>"),
+    (9, "cg_step_a_pg_staged_kernel<float, 12, 2, 0>"),
+    (10, "cg_step_a_pg_staged_kernel<float, 12, 3, 0>"),
+    (11, "cg_step_a_pg_kernel<float, 12>"),
+    (12, "cg_step_a_pg_staged_kernel<float, 12, 2, 1>"),
+    (13, "cg_step_a_pg_staged_kernel<float, 12, 3, 1>"),
 ])
 def test_kernel_name_per_variant(var, name):
     assert bench.step_a_kernel_name({"step_a_variant": var, "k_bucket": 12}) == name

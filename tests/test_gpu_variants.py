@@ -34,14 +34,15 @@ import paper_1805_12417_gb300 as m  # noqa: E402
 DEV = torch.device("cuda:0")
 
 SHAPES = [(0, None), (1, None), (2, None), (3, None), (4, None), (5, 2), (5, 3), (5, 4), (6, 2), (6, 3), (7, 2),
-          (7, 3), (9, 2), (9, 3), (10, 2), (10, 4), (11, None)]
+          (7, 3), (9, 2), (9, 3), (10, 2), (10, 4), (11, None), (12, 2), (12, 3), (13, 3)]
 SHAPE_IDS = ["v0", "v1", "v2", "v3", "v4", "staged2", "staged3", "staged4", "staged4bpsm_2", "staged4bpsm_3",
              "pipelined2", "pipelined3", "onegather_staged2", "onegather_staged3", "onegather_staged3bpsm_2",
-             "onegather_staged3bpsm_4", "onegather_plain"]
+             "onegather_staged3bpsm_4", "onegather_plain", "onegather_pipelined2", "onegather_pipelined3",
+             "onegather_pipelined3bpsm"]
 
 
 def is_staged(var):
-    return 5 <= var <= 10
+    return 5 <= var <= 10 or var in (12, 13)
 
 
 @pytest.fixture
@@ -97,9 +98,11 @@ def test_inner_variants_small_3d(shape_env, var, stages, prec, mcg):
 
 
 @pytest.mark.parametrize("k", [0, 1, 10, 13, 17, 32])
-@pytest.mark.parametrize("var,stages", [(1, None), (3, None), (5, 2), (6, 2), (7, 2), (9, 2), (10, 2), (11, None)],
+@pytest.mark.parametrize("var,stages", [(1, None), (3, None), (5, 2), (6, 2), (7, 2), (9, 2), (10, 2), (11, None),
+                                       (12, 2), (13, 2)],
                          ids=["v1", "v3", "staged2", "staged4bpsm", "pipelined2", "onegather_staged2",
-                              "onegather_staged3bpsm", "onegather_plain"])
+                              "onegather_staged3bpsm", "onegather_plain", "onegather_pipelined2",
+                              "onegather_pipelined3bpsm"])
 def test_inner_variants_k_buckets(shape_env, k, var, stages):
     """Every k bucket of the kernels (FP64 stages of k = 32 hold 86 KB, so two fit a block)."""
     p = shifted_laplacian_problem("t", (13, 11, 9), max(k, 1), seed=k) if k else None
@@ -126,13 +129,13 @@ def test_staged_long_rows(shape_env, idx16, prec, stages):
     rng = np.random.default_rng(22)
     V, _ = np.linalg.qr(rng.standard_normal((n, 6)))
     lam = -rng.uniform(0.5, 3.0, 6)
-    for var in (5, 7, 9, 11):
+    for var in (5, 7, 9, 11, 12):
         shape_env(var, stages, idx16=idx16)
         _inner_vs_oracle(None, prec, m.MCG_JACOBI, 1e-7 if prec == m.FP64 else 1e-4, 23, var, stages,
                          idx_bytes=2 if idx16 else 4, V=V, lam=lam, sysargs=(rp, ci, va))
 
 
-@pytest.mark.parametrize("var", [5, 9])
+@pytest.mark.parametrize("var", [5, 9, 12])
 def test_staged_falls_back_when_stages_do_not_fit(shape_env, var):
     """FP64, k = 32: three stages of 86 KB exceed a block's shared memory; and
     rows of up to 64 entries make one stage of a tile 164 KB."""
@@ -150,9 +153,11 @@ def test_staged_falls_back_when_stages_do_not_fit(shape_env, var):
     assert st == m.OK and it > 0
 
 
-@pytest.mark.parametrize("var,stages", [(0, None), (5, 3), (6, 2), (7, 3), (9, 3), (10, 2), (11, None)],
+@pytest.mark.parametrize("var,stages", [(0, None), (5, 3), (6, 2), (7, 3), (9, 3), (10, 2), (11, None), (12, 3),
+                                       (13, 2)],
                          ids=["v0", "staged3", "staged4bpsm", "pipelined3", "onegather_staged3",
-                              "onegather_staged3bpsm", "onegather_plain"])
+                              "onegather_staged3bpsm", "onegather_plain", "onegather_pipelined3",
+                              "onegather_pipelined3bpsm"])
 def test_variants_full_solve_small(shape_env, var, stages):
     """A whole MINRES-CG solve on every step-a path agrees with the oracle's."""
     shape_env(var, stages)
@@ -250,8 +255,8 @@ def test_one_kernel_iteration_full_solves(shape_env):
 # ---------------------------------------------------------------- variants 9-11: one gather per matrix entry
 
 def test_one_gather_falls_back_with_smw(shape_env):
-    """Variants 9-11 cover M_cg = I and Jacobi; the MINRES-CG* M_cg keeps its own kernels."""
-    for var in (9, 11):
+    """Variants 9-13 cover M_cg = I and Jacobi; the MINRES-CG* M_cg keeps its own kernels."""
+    for var in (9, 11, 12):
         shape_env(var, 2)
         with m.Solver.from_problem(small_3d(), inner_prec=m.MCG_SMW) as g:
             assert m.launch_config(g.h)["step_a_variant"] == 0
@@ -291,7 +296,7 @@ def test_one_gather_full_size_mixed(shape_env):
 
 # ---------------------------------------------------------------- a CG step that removes almost all of the residual
 
-@pytest.mark.parametrize("var,stages", [(8, 2), (9, 2)], ids=["one_kernel", "onegather"])
+@pytest.mark.parametrize("var,stages", [(8, 2), (9, 2), (12, 3)], ids=["one_kernel", "onegather", "onegather_pipelined"])
 @pytest.mark.parametrize("prec", [m.FP64, m.MIXED_FP32], ids=["fp64", "mixed"])
 def test_sharp_single_step_reduction(shape_env, var, stages, prec):
     """A = diag(2 + 1e-3 u): the first CG step cuts ||r|| by about 1e-4, so the
