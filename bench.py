@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--inner-tol", type=float, default=INNER_TOL,
                     help="relative recursive-residual tolerance of every inner CG solve (default 1e-3); the CPU "
                          "baseline of a sampled workload is scaled only by a count recorded at the same tolerance")
+    ap.add_argument("--workloads", default="saddle,shifted64,batch64",
+                    help="comma-separated extra workloads measured after the headline and reported in the same "
+                         "line under 'workloads' (saddle, shifted64, batch64; empty for none)")
     ap.add_argument("--mcg", choices=["identity", "jacobi", "smw"], default="identity",
                     help="inner preconditioner of the single-system workloads: identity (default), Jacobi on "
                          "M_mr, or smw, the MINRES-CG* form diag(A)^-1 - 2 V Lambda^-1 V^T (Sec. 2.1)")
@@ -245,81 +248,129 @@ def single_system(name):
     return lap3d_128_k10(), WORKLOAD
 
 
-def cpu_baseline(p, mcg="identity"):
-    """The oracle as it stands (serial C, FP64) with the same inner
-    preconditioner: a whole solve for small workloads (up to 100,000 rows),
-    else its first CPU_SAMPLE_ITERS inner iterations scaled to one full solve
-    by the oracle's own recorded count (value None when none is recorded)."""
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the baseline's record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part", "hardware")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def _cores(threads):
+    import oracle as O
+    return O.threads_available() if threads else 1
+
+
+def cpu_baseline_one(p, mcg="identity", threads=False, sample_iters=CPU_SAMPLE_ITERS):
+    """The oracle as it stands (FP64 C; serial, or its all-core OpenMP build)
+    with the same inner preconditioner: a whole solve for small workloads (up
+    to 100,000 rows), else its first `sample_iters` inner iterations scaled to
+    one full solve by the oracle's own recorded count (value None when none is
+    recorded)."""
     import oracle as O
     code = {"identity": O.MCG_IDENTITY, "jacobi": O.MCG_JACOBI, "smw": O.MCG_SMW}[mcg]
     s = O.System.from_problem(p)
+    cores = _cores(threads)
+    build = f"all-core OpenMP build, {cores} threads" if threads else "serial build"
     if p.n <= 100_000:
         t = time.perf_counter()
-        r = O.minres_cg(s, p.b, outer_tol=OUTER_TOL, inner_tol=INNER_TOL, mcg=code)
+        r = O.minres_cg(s, p.b, outer_tol=OUTER_TOL, inner_tol=INNER_TOL, mcg=code, threads=threads)
         dt = time.perf_counter() - t
-        return {"value": 1.0 / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                "sample": f"one full FP64 oracle solve ({r.inner_iters_total} inner iterations, {dt:.2f} s)",
-                "seconds": round(dt, 3)}
+        return {"value": 1.0 / dt, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                "sample": f"one full FP64 oracle solve ({build}; {r.inner_iters_total} inner iterations, {dt:.2f} s)",
+                "seconds": round(dt, 3), "extrapolated": False}
     t = time.perf_counter()
-    r = O.minres_cg(s, p.b, outer_tol=OUTER_TOL, inner_tol=INNER_TOL, max_iters=CPU_SAMPLE_ITERS, mcg=code)
+    r = O.minres_cg(s, p.b, outer_tol=OUTER_TOL, inner_tol=INNER_TOL, max_iters=sample_iters, mcg=code,
+                    threads=threads)
     dt = time.perf_counter() - t
     n_full = full_solve_inner_iters(p.name, mcg)
-    head = f"first {r.inner_iters_total} inner CG iterations of the FP64 oracle solve ({dt:.1f} s)"
+    head = f"first {r.inner_iters_total} inner CG iterations of the FP64 oracle solve ({build}; {dt:.1f} s)"
     if n_full is None:
-        return {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle", "seconds": round(dt, 2),
-                "sample": head + "; no whole oracle solve of this workload is recorded to scale them by"}
-    return {"value": r.inner_iters_total / n_full / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
+        return {"value": None, "unit": "solves/s", "cores": cores, "kind": "oracle", "seconds": round(dt, 2),
+                "sample": head + "; no whole oracle solve of this workload is recorded to scale them by",
+                "extrapolated": True}
+    return {"value": r.inner_iters_total / n_full / dt, "unit": "solves/s", "cores": cores, "kind": "oracle",
             "sample": head + f", scaled by the {n_full} inner iterations of a whole oracle solve",
-            "seconds": round(dt, 2)}
+            "seconds": round(dt, 2), "extrapolated": True, "sample_fraction": r.inner_iters_total / n_full}
 
 
-def cpu_baseline_batch(ps, budget_s=20.0):
+def cpu_baseline(p, mcg="identity"):
+    """The all-core oracle as the reported baseline, with the serial oracle
+    beside it (the serial sample is the same length; the all-core one four
+    times longer, to span 10 s or so of CPU work)."""
+    allc = cpu_baseline_one(p, mcg, threads=True, sample_iters=4 * CPU_SAMPLE_ITERS)
+    ser = cpu_baseline_one(p, mcg, threads=False)
+    allc["serial"] = {k: ser[k] for k in ("value", "cores", "sample", "seconds")}
+    allc["cpu_model"] = cpu_model()
+    return allc
+
+
+def cpu_baseline_batch(ps, budget_s=20.0, threads=True):
     """The oracle on an uneven batch: whole solves of the systems in batch
     order until budget_s has passed (at least one); solves/s of that sample."""
     import oracle as O
     t0 = time.perf_counter()
     done, iters = 0, 0
     for p in ps:
-        r = O.minres_cg(O.System.from_problem(p), p.b, outer_tol=OUTER_TOL, inner_tol=INNER_TOL)
+        r = O.minres_cg(O.System.from_problem(p), p.b, outer_tol=OUTER_TOL, inner_tol=INNER_TOL, threads=threads)
         done += 1
         iters += r.inner_iters_total
         if time.perf_counter() - t0 >= budget_s:
             break
     dt = time.perf_counter() - t0
-    return {"value": done / dt, "unit": "solves/s", "cores": 1, "kind": "oracle", "seconds": round(dt, 2),
-            "sample": f"whole FP64 oracle solves of the first {done} of {len(ps)} systems in batch order "
-                      f"({sum(p.n for p in ps[:done])} rows, {iters} inner iterations, {dt:.1f} s)"}
+    cores = _cores(threads)
+    return {"value": done / dt, "unit": "solves/s", "cores": cores, "kind": "oracle", "seconds": round(dt, 2),
+            "sample": f"whole FP64 oracle solves ({'all-core build' if threads else 'serial build'}) of the first "
+                      f"{done} of {len(ps)} systems in batch order ({sum(p.n for p in ps[:done])} rows, {iters} inner "
+                      f"iterations, {dt:.1f} s)", "extrapolated": False, "cpu_model": cpu_model()}
 
 
-def cpu_baseline_shifted(fam):
+def cpu_baseline_shifted(fam, threads=True):
     """The oracle on a shifted family, sampled on column 0 (shift 0, right-hand
-    side 0) as a stand-alone system: its first CPU_SAMPLE_ITERS inner
-    iterations, scaled by the inner-iteration count of a whole oracle solve of
-    that column (value None when none is recorded).  Columns differ in k_j
-    and sigma_j, so this is a per-column rate of one representative column."""
+    side 0) as a stand-alone system: its first inner iterations, scaled by the
+    inner-iteration count of a whole oracle solve of that column (value None
+    when none is recorded).  Columns differ in k_j and sigma_j, so this is a
+    per-column rate of one representative column."""
     import oracle as O
     p = fam.column_problem(0)
+    iters = (4 if threads else 1) * CPU_SAMPLE_ITERS
     t = time.perf_counter()
-    r = O.minres_cg(O.System.from_problem(p), p.b, outer_tol=OUTER_TOL, inner_tol=INNER_TOL,
-                    max_iters=CPU_SAMPLE_ITERS)
+    r = O.minres_cg(O.System.from_problem(p), p.b, outer_tol=OUTER_TOL, inner_tol=INNER_TOL, max_iters=iters,
+                    threads=threads)
     dt = time.perf_counter() - t
     n_full = full_solve_inner_iters(p.name)
+    cores = _cores(threads)
     head = (f"first {r.inner_iters_total} inner CG iterations of the FP64 oracle solve of column 0 "
-            f"(shift 0, k = {p.k}; {dt:.1f} s)")
+            f"(shift 0, k = {p.k}; {'all-core build' if threads else 'serial build'}; {dt:.1f} s)")
     if n_full is None:
-        return {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle", "seconds": round(dt, 2),
-                "sample": head + "; no whole oracle solve of that column is recorded to scale them by"}
-    return {"value": r.inner_iters_total / n_full / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "seconds": round(dt, 2),
+        return {"value": None, "unit": "solves/s", "cores": cores, "kind": "oracle", "seconds": round(dt, 2),
+                "sample": head + "; no whole oracle solve of that column is recorded to scale them by",
+                "extrapolated": True}
+    return {"value": r.inner_iters_total / n_full / dt, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "seconds": round(dt, 2), "extrapolated": True, "sample_fraction": r.inner_iters_total / n_full,
             "sample": head + f", scaled by the {n_full} inner iterations of a whole oracle solve of that column: "
-                             f"column solves per second"}
+                             f"column solves per second", "cpu_model": cpu_model()}
 
 
 # ------------------------------------------------------------------ reference arm (the oracle)
 
 def run_reference(args, ws, rank):
-    """The oracle, as it stands, on this arm's workload: each step is one
-    bounded sample (cpu_baseline*)."""
+    """The oracle, as it stands (its all-core build on the machine's host cores),
+    on this arm's workload: each step is one bounded sample (cpu_baseline*).
+    ms_per_step is the sample's real duration; value is the solves/s the
+    sample extrapolates to when the sample is part of a solve."""
     if rank != 0:
         return
     if args.workload == "batch64":
@@ -332,87 +383,294 @@ def run_reference(args, ws, rank):
         sample, desc = (lambda: cpu_baseline_shifted(fam)), SHIFTED_WORKLOAD
     else:
         p, desc = single_system(args.workload)
-        sample = lambda: cpu_baseline(p, args.mcg)  # noqa: E731
-    vals = []
+        sample = lambda: cpu_baseline_one(p, args.mcg, threads=True, sample_iters=4 * CPU_SAMPLE_ITERS)  # noqa: E731
+    vals, secs = [], []
+    cb = None
     for i in range(args.warmup + args.steps):
         cb = sample()
         if i >= args.warmup:
             vals.append(cb["value"])
+            secs.append(cb["seconds"])
     v = None if any(x is None for x in vals) else statistics.mean(vals)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": (1000.0 / v) if v else None,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * statistics.mean(secs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": desc, "inner_prec": args.mcg, "outer_tol": OUTER_TOL, "inner_tol": INNER_TOL,
-                       "parallelism": "rank 0 only (CPU oracle)"},
-            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": cb["sample"]},
+                       "parallelism": f"rank 0 only (CPU oracle, {cb['cores']} threads)"},
+            "value_extrapolated": bool(cb.get("extrapolated")),
+            "value_basis": ("each step is a sample of part of a solve; value scales it to whole solves by the "
+                            "oracle's recorded iteration count, ms_per_step is the sample's real duration")
+            if cb.get("extrapolated") else "each step is whole solves; value = solves / time",
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": cb["cores"], "kind": "oracle",
+                             "sample": cb["sample"], "cpu_model": cpu_model()},
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 # ------------------------------------------------------------------ our arm
 
-def run_batch64(args, ws, rank, local):
-    """64 independent uneven 2D shifted Laplacians solved as one batch; a step is
-    one batched solve of all 64 systems."""
+def gpu_setup(local):
     import torch
 
-    from gen import batch64_lap2d
     from paper_1805_12417_gb300 import build as _b
     _b.build()
     import paper_1805_12417_gb300 as m
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(dev)
-    ps = batch64_lap2d()
+    return torch, m, dev, torch.cuda.current_stream(dev)
+
+
+def timed_steps(torch, step, steps, warmup, stream, dev, ws, clock_index=None):
+    """Run `warmup` untimed steps, then time exactly `steps` steps with CUDA
+    events on `stream`, bracketed by a barrier and a device synchronize on
+    both sides.  Returns (max-over-ranks ms, list of step results, clocks)."""
+    for _ in range(warmup):
+        step()
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ck = Clocks(clock_index) if clock_index is not None else None
+    if ck:
+        ck.__enter__()
+    e0.record(stream)
+    res = [step() for _ in range(steps)]
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(ws)
+    if ck:
+        ck.__exit__(None, None, None)
+    return max_over_ranks(e0.elapsed_time(e1), ws, dev), res, (ck.summary() if ck else None)
+
+
+def inner_bytes(cfg, n, nnz, k, w, mcg):
+    """Algorithmic bytes of one inner CG iteration's two kernels (step a, step
+    b) for the launch configuration `cfg`: each streamed operand once, each
+    gathered vector entry counted once per row (it is reused from L2)."""
+    ib = cfg["index_bytes"]
+    var = cfg["step_a_variant"]
+    jac = n * w if mcg == "jacobi" else 0
+    a_mat = nnz * (w + ib) + k * n * w  # A values + column indices, V_hat
+    if var == 8:  # one kernel: r, q, p, z read and r, z, p, q written for the own rows
+        return a_mat + 8 * n * w, 0
+    if 9 <= var <= 13:  # one gather: p, r (and M_cg^-1) read, q written | p, q, z, r (M_cg^-1) read, z, r, p written
+        return a_mat + 3 * n * w + jac, 7 * n * w + jac
+    # two gathers: s, p (and M_cg^-1) read, q, p' written | p', q, z, r (M_cg^-1) read, z, r (s) written
+    b = 6 * n * w + (2 * jac if mcg == "jacobi" else 0) + (2 * n * w + k * n * w if mcg == "smw" else 0)
+    return a_mat + 4 * n * w + jac, b
+
+
+def step_a_flops(cfg, n, nnz, k, mcg):
+    """FP64 floating-point operations of one step-a launch (an FMA counts 2):
+    the SpMV, the two low-rank products (V c and V^T M_cg^{-1} A p) and the
+    row's dot-product terms; the two-gather variants also rebuild p' = s + beta p
+    at every gathered entry and for the own row."""
+    var = cfg["step_a_variant"]
+    base = 2 * nnz + 4 * k * n
+    if 9 <= var <= 13:
+        return base + 6 * n + (3 * n if mcg == "jacobi" else 0)
+    if var == 8:
+        return base + 2 * nnz * 2 + 14 * n
+    return base + 2 * nnz + 4 * n + (n if mcg == "jacobi" else 0)
+
+
+def measure_single(torch, m, p, dev, stream, ws, local, rank, steps, warmup, mcg="identity", clocks=True,
+                   e2e=True, kernel_timing=True, cpu=False):
+    """Mixed-precision and FP64 solves of one system: throughput, iteration
+    counts, errors (against x* and between the two precisions), the inner
+    kernels' standalone and in-situ times with their algorithmic GB/s, and
+    (optionally) the end-to-end rate with host buffers and the CPU baseline."""
+    b_dev = torch.from_numpy(p.b).to(dev)
+    x_dev = torch.zeros(p.n, dtype=torch.float64, device=dev)
+    code = {"identity": m.MCG_IDENTITY, "jacobi": m.MCG_JACOBI, "smw": m.MCG_SMW}[mcg]
+    solvers = {prec: m.Solver.from_problem(p, precision=prec, inner_prec=code, stream=stream.cuda_stream,
+                                           validate=False)
+               for prec in (m.MIXED_FP32, m.FP64)}
+    res, xs = {}, {}
+    n, nnz, k = p.n, p.nnz, p.k
+    peak, peak_kind = measured_peak_gbs()
+    for name, prec in (("mixed", m.MIXED_FP32), ("fp64", m.FP64)):
+        s = solvers[prec]
+
+        def step():
+            x_dev.zero_()
+            return s.solve(b_dev, x_dev, outer_tol=OUTER_TOL, inner_tol=INNER_TOL)[1]
+        ms, infos, ck = timed_steps(torch, step, steps, warmup if name == "mixed" else max(1, warmup), stream, dev,
+                                    ws, clock_index=local if (clocks and rank == 0 and name == "mixed") else None)
+        ok = sum(1 for i in infos if i.status == m.OK and i.true_relres <= OUTER_TOL)
+        ok = sum_over_ranks(ok, ws, dev)
+        xh = x_dev.cpu().numpy()
+        xs[name] = xh
+        rr = float(np.linalg.norm(p.b - p.scipy() @ xh) / np.linalg.norm(p.b))
+        cfg = m.launch_config(s.h)
+        w = 4 if prec == m.MIXED_FP32 else 8
+        r = {"value": ok / (ms / 1000.0), "unit": "solves/s", "ms_per_step": ms / steps, "steps": steps,
+             "outer_iters": infos[-1].outer_iters, "inner_iters_total": infos[-1].inner_iters_total,
+             "restarts": infos[-1].restarts, "true_relres": infos[-1].true_relres, "true_relres_host_fp64": rr,
+             "rel_err_vs_xstar": float(np.linalg.norm(xh - p.xstar) / np.linalg.norm(p.xstar)),
+             "launches_per_solve": infos[-1].kernel_launches, "launch_config": cfg}
+        if ck is not None:
+            r["clocks"] = ck
+        if kernel_timing:
+            ta, tb = m.time_inner_kernels(s.h, 50)
+            t_it = m.time_inner_graph(s.h, 512)
+            ba, bb = inner_bytes(cfg, n, nnz, k, w, mcg)
+            # in-situ step a: the in-loop iteration time split in the ratio of the standalone times
+            ta_in = t_it * ta / (ta + tb) if (ta + tb) > 0 else t_it
+            r["kernels"] = {"step_a_kernel": step_a_kernel_name(cfg, "float" if w == 4 else "double"),
+                            "step_a_ms_standalone": ta, "step_b_ms_standalone": tb, "iteration_ms_in_situ": t_it,
+                            "step_a_ms_in_situ": ta_in, "step_a_bytes": ba, "step_b_bytes": bb,
+                            "iteration_gbs_in_situ": (ba + bb) / (t_it * 1e-3) / 1e9,
+                            "step_a_gbs_in_situ": ba / (ta_in * 1e-3) / 1e9,
+                            "step_a_gbs_standalone": ba / (ta * 1e-3) / 1e9,
+                            "step_b_gbs_standalone": bb / (max(tb, 1e-6) * 1e-3) / 1e9 if bb else None,
+                            "step_a_frac_in_situ": round(ba / (ta_in * 1e-3) / 1e9 / peak, 4),
+                            "iteration_frac_in_situ": round((ba + bb) / (t_it * 1e-3) / 1e9 / peak, 4),
+                            "step_a_fp64_flops": step_a_flops(cfg, n, nnz, k, mcg) if w == 8 else None}
+        res[name] = r
+    res["mixed_vs_fp64_speedup"] = res["mixed"]["value"] / res["fp64"]["value"] if res["fp64"]["value"] else None
+    res["mixed_rel_err_vs_fp64"] = float(np.linalg.norm(xs["mixed"] - xs["fp64"]) / np.linalg.norm(xs["fp64"]))
+    res["peak_gbs"] = peak
+    res["peak_kind"] = peak_kind
+    if e2e:
+        # end to end through the C ABI with pinned host buffers (copies inside the call)
+        b_h = torch.from_numpy(p.b.copy()).pin_memory()
+        x_h = torch.zeros(p.n, dtype=torch.float64).pin_memory()
+        sm_ = solvers[m.MIXED_FP32]
+        x_h.zero_()
+        sm_.solve(b_h, x_h, outer_tol=OUTER_TOL, inner_tol=INNER_TOL)
+        barrier(ws)
+        t0 = time.perf_counter()
+        ok_e2e = 0
+        for _ in range(steps):
+            x_h.zero_()
+            _, info = sm_.solve(b_h, x_h, outer_tol=OUTER_TOL, inner_tol=INNER_TOL)
+            ok_e2e += int(info.status == m.OK and info.true_relres <= OUTER_TOL)
+        t_e2e = max_over_ranks(time.perf_counter() - t0, ws, dev)
+        ok_e2e = sum_over_ranks(ok_e2e, ws, dev)
+        res["e2e"] = {"value": ok_e2e / t_e2e, "unit": "solves/s", "h2d_bytes_per_step": 2 * n * 8,
+                      "d2h_bytes_per_step": n * 8}
+    for s_ in solvers.values():
+        s_.close()
+    if cpu and rank == 0 and ws == 1:
+        res["cpu_baseline"] = cpu_baseline(p, mcg)
+    return res
+
+
+def measure_batch(torch, m, ps, dev, stream, ws, local, rank, steps, warmup, clocks=False, e2e=False):
+    """64 independent uneven systems solved as one batch (a step = one batched
+    solve of all systems), mixed and FP64."""
     B = np.concatenate([p.b for p in ps])
     Bd = torch.from_numpy(B).to(dev)
     Xd = torch.zeros_like(Bd)
     out = {}
     for name, prec in (("mixed", m.MIXED_FP32), ("fp64", m.FP64)):
         with m.Batch(ps, precision=prec, validate=False, stream=stream.cuda_stream) as bt:
-            for _ in range(args.warmup):
+            def step():
                 Xd.zero_()
-                bt.solve(Bd, Xd, outer_tol=OUTER_TOL, inner_tol=INNER_TOL)
-            barrier(ws)
-            torch.cuda.synchronize(dev)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            ck = Clocks(local) if (rank == 0 and name == "mixed") else None
-            if ck:
-                ck.__enter__()
-            e0.record(stream)
-            ok, infos = 0, None
-            for _ in range(args.steps):
-                Xd.zero_()
-                _, st, infos = bt.solve(Bd, Xd, outer_tol=OUTER_TOL, inner_tol=INNER_TOL)
-                ok += sum(1 for i in infos if i.status == m.OK and i.true_relres <= OUTER_TOL)
-            e1.record(stream)
-            torch.cuda.synchronize(dev)
-            barrier(ws)
-            if ck:
-                ck.__exit__(None, None, None)
-            ms = max_over_ranks(e0.elapsed_time(e1), ws, dev)
+                return bt.solve(Bd, Xd, outer_tol=OUTER_TOL, inner_tol=INNER_TOL)[2]
+            ms, res, ck = timed_steps(torch, step, steps, warmup, stream, dev, ws,
+                                      clock_index=local if (clocks and rank == 0 and name == "mixed") else None)
+            ok = sum(sum(1 for i in infos if i.status == m.OK and i.true_relres <= OUTER_TOL) for infos in res)
             ok = sum_over_ranks(ok, ws, dev)
+            infos = res[-1]
             w = 4 if prec == m.MIXED_FP32 else 8
             # algorithmic bytes of the inner iterations actually run (both CG kernels)
             byts = sum(i.inner_iters_total * (p.nnz * (w + 4) + 10 * p.n * w + 2 * p.k * p.n * w)
                        for i, p in zip(infos, ps))
-            out[name] = {"value": ok / (ms / 1000.0), "ms_per_step": ms / args.steps,
-                         "inner_gbs": byts / (ms / args.steps * 1e-3) / 1e9, "launches": infos[0].kernel_launches,
+            out[name] = {"value": ok / (ms / 1000.0), "unit": "solves/s", "ms_per_step": ms / steps, "steps": steps,
+                         "inner_gbs": byts / (ms / steps * 1e-3) / 1e9, "launches": infos[0].kernel_launches,
                          "inner_iters_max": max(i.inner_iters_total for i in infos),
                          "outer_iters_max": max(i.outer_iters for i in infos),
-                         "clocks": ck.summary() if ck else None}
-            if name == "mixed":
+                         "max_true_relres": max(i.true_relres for i in infos)}
+            if ck is not None:
+                out[name]["clocks"] = ck
+            if name == "mixed" and e2e:
                 b_h = torch.from_numpy(B.copy()).pin_memory()
                 x_h = torch.zeros(len(B), dtype=torch.float64).pin_memory()
                 t0 = time.perf_counter()
                 ok_e2e = 0
-                for _ in range(args.steps):
+                for _ in range(steps):
                     x_h.zero_()
                     _, st, inf = bt.solve(b_h, x_h, outer_tol=OUTER_TOL, inner_tol=INNER_TOL)
                     ok_e2e += sum(1 for i in inf if i.status == m.OK and i.true_relres <= OUTER_TOL)
                 out["e2e"] = {"value": ok_e2e / (time.perf_counter() - t0), "unit": "solves/s",
                               "h2d_bytes_per_step": 2 * len(B) * 8, "d2h_bytes_per_step": len(B) * 8}
+    out["mixed_vs_fp64_speedup"] = out["mixed"]["value"] / out["fp64"]["value"]
+    return out
+
+
+def loop_single_systems(torch, m, systems, dev, stream, precision, warmup=1):
+    """The baseline a batched engine must beat: the single-system solver run
+    in a loop over the same systems, one handle per system (created outside
+    the timed region), every solve from x0 = 0.  `systems` is a list of
+    (Problem, list of right-hand sides); returns solves/s and the wall time."""
+    handles = []
+    for p, rhs in systems:
+        handles.append((m.Solver.from_problem(p, precision=precision, stream=stream.cuda_stream, validate=False),
+                        [torch.from_numpy(np.ascontiguousarray(b)).to(dev) for b in rhs], p.n))
+    xs = {n: torch.zeros(n, dtype=torch.float64, device=dev) for _, _, n in handles}
+    for _ in range(warmup):
+        s, bs, n = handles[0]
+        xs[n].zero_()
+        s.solve(bs[0], xs[n], outer_tol=OUTER_TOL, inner_tol=INNER_TOL)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ok = total = 0
+    for s, bs, n in handles:
+        for b in bs:
+            xs[n].zero_()
+            info = s.solve(b, xs[n], outer_tol=OUTER_TOL, inner_tol=INNER_TOL)[1]
+            ok += int(info.status == m.OK and info.true_relres <= OUTER_TOL)
+            total += 1
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    for s, _, _ in handles:
+        s.close()
+    return {"value": ok / (ms / 1000.0), "unit": "solves/s", "ms_per_step": ms, "solves": total, "ok": ok}
+
+
+def measure_shifted(torch, m, fam, dev, stream, ws, local, rank, precision, steps=1, warmup=0, clocks=False):
+    """One right-hand-side block of a shifted family (a step = one solve of all
+    its columns) in one precision."""
+    Bd = torch.from_numpy(fam.B).to(dev)
+    Xd = torch.zeros_like(Bd)
+    n, nc = fam.n, fam.ncols
+    with m.Shifted(fam, precision=precision, stream=stream.cuda_stream) as sh:
+        def step():
+            Xd.zero_()
+            return sh.solve(Bd, Xd, outer_tol=OUTER_TOL, inner_tol=INNER_TOL)[2]
+        ms, res, ck = timed_steps(torch, step, steps, warmup, stream, dev, ws,
+                                  clock_index=local if (clocks and rank == 0) else None)
+    infos = res[-1]
+    ok = sum(sum(1 for i in inf if i.status == m.OK and i.true_relres <= OUTER_TOL) for inf in res)
+    ok = sum_over_ranks(ok, ws, dev)
+    w = 4 if precision == m.MIXED_FP32 else 8
+    iters = max(i.inner_iters_total for i in infos)  # lock-step block iterations
+    ncp = 32 if nc <= 32 else 64
+    kv = fam.V.shape[1]
+    byts = iters * (fam.nnz * (w + 4) + 10 * n * ncp * w + 2 * n * kv * w)
+    xh = Xd.cpu().numpy()
+    err = max(float(np.linalg.norm(xh[:, c] - fam.xstar[:, c]) / np.linalg.norm(fam.xstar[:, c])) for c in range(nc))
+    out = {"value": ok / (ms / 1000.0), "unit": "solves/s", "ms_per_step": ms / steps, "steps": steps,
+           "columns": nc, "inner_gbs": byts / (ms / steps * 1e-3) / 1e9, "launches": infos[0].kernel_launches,
+           "inner_iters_max": iters, "inner_iters_per_column": [i.inner_iters_total for i in infos],
+           "outer_iters_max": max(i.outer_iters for i in infos),
+           "max_true_relres": max(i.true_relres for i in infos), "max_rel_err_vs_xstar": err}
+    if ck is not None:
+        out["clocks"] = ck
+    return out, xh
+
+
+def run_batch64(args, ws, rank, local):
+    """64 independent uneven 2D shifted Laplacians solved as one batch; a step is
+    one batched solve of all 64 systems."""
+    torch, m, dev, stream = gpu_setup(local)
+    from gen import batch64_lap2d
+    ps = batch64_lap2d()
+    out = measure_batch(torch, m, ps, dev, stream, ws, local, rank, args.steps, args.warmup, clocks=True, e2e=True)
     if rank == 0:
         peak, kind = measured_peak_gbs()
         mx = out["mixed"]
@@ -420,100 +678,102 @@ def run_batch64(args, ws, rank, local):
                 "warmup": args.warmup, "ms_per_step": mx["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner CG + f64 outer MINRES",
                 "data": "synthetic",
-                "config": {"workload": BATCH_WORKLOAD,
-                           "systems": len(ps), "rows": int(len(B)), "outer_tol": OUTER_TOL, "inner_tol": INNER_TOL,
-                           "l2": "inputs larger than L2", "parallelism": "replicas" if ws > 1 else "single GPU"},
+                "config": {"workload": BATCH_WORKLOAD, "systems": len(ps), "rows": int(sum(p.n for p in ps)),
+                           "outer_tol": OUTER_TOL, "inner_tol": INNER_TOL, "l2": "inputs larger than L2",
+                           "parallelism": "replicas" if ws > 1 else "single GPU"},
                 "roofline": {"kernel": "whole inner loop (batched step a + step b)", "bound": "hbm",
                              "achieved": round(mx["inner_gbs"], 1), "peak": peak, "unit": "GB/s",
                              "frac": round(mx["inner_gbs"] / peak, 4), "traffic": None,
                              "peak_kind": f"{kind} copy bandwidth"},
-                "fp64": out["fp64"], "mixed": mx, "mixed_vs_fp64_speedup": mx["value"] / out["fp64"]["value"],
-                "e2e": out["e2e"], "gpu_launches": int(mx["launches"] * args.steps), "clocks": mx["clocks"],
+                "fp64": out["fp64"], "mixed": mx, "mixed_vs_fp64_speedup": out["mixed_vs_fp64_speedup"],
+                "e2e": out["e2e"], "gpu_launches": int(mx["launches"] * args.steps), "clocks": mx.get("clocks"),
                 "cpu_baseline": cpu_baseline_batch(ps) if (ws == 1 and not args.no_cpu_baseline) else None}
         print(json.dumps(line), flush=True)
 
 
 def run_shifted64(args, ws, rank, local):
     """16 shifts x 4 right-hand sides of the 160^3 Laplacian solved as one
-    right-hand-side block; a step is one solve of all 64 columns."""
-    import torch
-
+    right-hand-side block; a step is one solve of all 64 columns (FP64: one
+    step, it takes minutes)."""
+    torch, m, dev, stream = gpu_setup(local)
     from gen import shifted_lap3d_160
-    from paper_1805_12417_gb300 import build as _b
-    _b.build()
-    import paper_1805_12417_gb300 as m
-
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(dev)
     fam = shifted_lap3d_160()
-    Bd = torch.from_numpy(fam.B).to(dev)
-    Xd = torch.zeros_like(Bd)
-    out = {}
-    n, nc = fam.n, fam.ncols
-    for name, prec, steps, warm in (("mixed", m.MIXED_FP32, args.steps, args.warmup), ("fp64", m.FP64, 1, 1)):
-        with m.Shifted(fam, precision=prec, stream=stream.cuda_stream) as sh:
-            for _ in range(warm):
-                Xd.zero_()
-                sh.solve(Bd, Xd, outer_tol=OUTER_TOL, inner_tol=INNER_TOL)
-            barrier(ws)
-            torch.cuda.synchronize(dev)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            ck = Clocks(local) if (rank == 0 and name == "mixed") else None
-            if ck:
-                ck.__enter__()
-            e0.record(stream)
-            ok, infos = 0, None
-            for _ in range(steps):
-                Xd.zero_()
-                _, st, infos = sh.solve(Bd, Xd, outer_tol=OUTER_TOL, inner_tol=INNER_TOL)
-                ok += sum(1 for i in infos if i.status == m.OK and i.true_relres <= OUTER_TOL)
-            e1.record(stream)
-            torch.cuda.synchronize(dev)
-            barrier(ws)
-            if ck:
-                ck.__exit__(None, None, None)
-            ms = max_over_ranks(e0.elapsed_time(e1), ws, dev)
-            ok = sum_over_ranks(ok, ws, dev)
-            w = 4 if prec == m.MIXED_FP32 else 8
-            iters = max(i.inner_iters_total for i in infos)  # lock-step block iterations
-            byts = iters * (fam.nnz * (w + 4) + 10 * n * 64 * w + 2 * n * 32 * w)
-            xh = Xd.cpu().numpy()
-            err = max(float(np.linalg.norm(xh[:, c] - fam.xstar[:, c]) / np.linalg.norm(fam.xstar[:, c]))
-                      for c in range(nc))
-            out[name] = {"value": ok / (ms / 1000.0), "ms_per_step": ms / steps, "steps": steps,
-                         "inner_gbs": byts / (ms / steps * 1e-3) / 1e9, "launches": infos[0].kernel_launches,
-                         "inner_iters_max": iters, "outer_iters_max": max(i.outer_iters for i in infos),
-                         "max_rel_err_vs_xstar": err, "clocks": ck.summary() if ck else None}
-            if name == "mixed":
-                b_h = torch.from_numpy(fam.B.copy()).pin_memory()
-                x_h = torch.zeros(fam.B.shape, dtype=torch.float64).pin_memory()
-                t0 = time.perf_counter()
-                ok_e2e = 0
-                for _ in range(steps):
-                    x_h.zero_()
-                    _, st, inf = sh.solve(b_h, x_h, outer_tol=OUTER_TOL, inner_tol=INNER_TOL)
-                    ok_e2e += sum(1 for i in inf if i.status == m.OK and i.true_relres <= OUTER_TOL)
-                out["e2e"] = {"value": ok_e2e / (time.perf_counter() - t0), "unit": "solves/s",
-                              "h2d_bytes_per_step": 2 * n * nc * 8, "d2h_bytes_per_step": n * nc * 8}
+    mx, _ = measure_shifted(torch, m, fam, dev, stream, ws, local, rank, m.MIXED_FP32, args.steps, args.warmup,
+                            clocks=True)
+    f64, _ = measure_shifted(torch, m, fam, dev, stream, ws, local, rank, m.FP64, 1, 0)
     if rank == 0:
         peak, kind = measured_peak_gbs()
-        mx = out["mixed"]
         line = {"metric": METRIC, "value": mx["value"], "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": mx["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner CG + f64 outer MINRES",
                 "data": "synthetic",
-                "config": {"workload": SHIFTED_WORKLOAD,
-                           "columns": nc, "outer_tol": OUTER_TOL, "inner_tol": INNER_TOL,
-                           "l2": "inputs larger than L2", "parallelism": "replicas" if ws > 1 else "single GPU"},
+                "config": {"workload": SHIFTED_WORKLOAD, "columns": fam.ncols, "outer_tol": OUTER_TOL,
+                           "inner_tol": INNER_TOL, "l2": "inputs larger than L2",
+                           "parallelism": "replicas" if ws > 1 else "single GPU"},
                 "roofline": {"kernel": "whole inner loop (block step a + step b)", "bound": "hbm",
                              "achieved": round(mx["inner_gbs"], 1), "peak": peak, "unit": "GB/s",
                              "frac": round(mx["inner_gbs"] / peak, 4), "traffic": None,
                              "peak_kind": f"{kind} copy bandwidth"},
-                "fp64": out["fp64"], "mixed": mx, "mixed_vs_fp64_speedup": mx["value"] / out["fp64"]["value"],
-                "e2e": out["e2e"], "gpu_launches": int(mx["launches"] * args.steps), "clocks": mx["clocks"],
+                "fp64": f64, "mixed": mx, "mixed_vs_fp64_speedup": mx["value"] / f64["value"],
+                "gpu_launches": int(mx["launches"] * args.steps), "clocks": mx.get("clocks"),
                 "cpu_baseline": cpu_baseline_shifted(fam) if (ws == 1 and not args.no_cpu_baseline) else None}
         print(json.dumps(line), flush=True)
+
+
+def fp64_roofline(m, single):
+    """Second roofline entry: the FP64 step a against the measured FP64 FMA
+    throughput of this GPU (the kernel is FP64-pipe bound, not HBM bound)."""
+    f = single["fp64"].get("kernels")
+    if not f:
+        return None
+    try:
+        peak_tf, _ = m.fp64_fma_peak()
+    except Exception:  # noqa: BLE001 - a diagnostic; the line still prints
+        return None
+    ach = f["step_a_fp64_flops"] / (f["step_a_ms_in_situ"] * 1e-3) / 1e12
+    return {"kernel": f["step_a_kernel"], "bound": "fp64", "achieved": round(ach, 4), "peak": round(peak_tf, 4),
+            "unit": "TFLOP/s", "frac": round(ach / peak_tf, 4), "flops_per_launch": f["step_a_fp64_flops"],
+            "avg_ms": round(f["step_a_ms_in_situ"], 5), "hbm_gbs": round(f["step_a_gbs_in_situ"], 1),
+            "peak_kind": "measured FP64 FMA throughput (mrcg_fp64_fma_peak: independent FMA chains, CUDA events)"}
+
+
+def workloads_block(args, torch, m, dev, stream, ws, local, rank):
+    """The other configurations the targets are stated on, measured in the
+    same run: the saddle-point system (mixed and FP64), the 160^3 shifted
+    family (mixed on all 64 columns; mixed and FP64 on the columns of shifts
+    0-3 for a like-for-like ratio) and the 64-system batch, each next to the
+    single-system solver run in a loop over the same systems."""
+    want = set(args.workloads.split(",")) if args.workloads else set()
+    out = {}
+    if "saddle" in want:
+        from gen import saddle_96_b20x64
+        p = saddle_96_b20x64()
+        r = measure_single(torch, m, p, dev, stream, ws, local, rank, steps=min(args.steps, 5), warmup=1,
+                           clocks=True, e2e=False)
+        out["saddle"] = {"workload": single_system("saddle")[1], **r}
+    if "batch64" in want:
+        from gen import batch64_lap2d
+        ps = batch64_lap2d()
+        r = measure_batch(torch, m, ps, dev, stream, ws, local, rank, steps=1, warmup=1, clocks=True)
+        loop = loop_single_systems(torch, m, [(p, [p.b]) for p in ps], dev, stream, m.MIXED_FP32)
+        r["loop_single_system_mixed"] = loop
+        r["batch_vs_loop"] = r["mixed"]["value"] / loop["value"] if loop["value"] else None
+        out["batch64"] = {"workload": BATCH_WORKLOAD, **r}
+    if "shifted64" in want:
+        from gen import shifted_lap3d_160
+        fam = shifted_lap3d_160()
+        mx, _ = measure_shifted(torch, m, fam, dev, stream, ws, local, rank, m.MIXED_FP32, 1, 0, clocks=True)
+        sub = fam.subfamily(list(range(4)))
+        mx_sub, _ = measure_shifted(torch, m, sub, dev, stream, ws, local, rank, m.MIXED_FP32, 1, 0)
+        f64_sub, _ = measure_shifted(torch, m, sub, dev, stream, ws, local, rank, m.FP64, 1, 0)
+        cols = [(fam.column_problem(4 * j), [fam.B[:, 4 * j + r] for r in range(fam.nrhs)])
+                for j in range(len(fam.sigma))]
+        loop = loop_single_systems(torch, m, cols, dev, stream, m.MIXED_FP32)
+        out["shifted64"] = {"workload": SHIFTED_WORKLOAD, "mixed": mx, "shifts_0_3": {
+            "mixed": mx_sub, "fp64": f64_sub, "mixed_vs_fp64_speedup": mx_sub["value"] / f64_sub["value"]},
+            "loop_single_system_mixed": loop,
+            "block_vs_loop": mx["value"] / loop["value"] if loop["value"] else None}
+    return out
 
 
 def main():
@@ -530,156 +790,51 @@ def main():
     if args.workload == "shifted64":
         run_shifted64(args, ws, rank, local)
         return
-    import torch
-
-    from paper_1805_12417_gb300 import build as _b
-    _b.build()
-    import paper_1805_12417_gb300 as m
-
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(dev)
+    torch, m, dev, stream = gpu_setup(local)
     p, workload = single_system(args.workload)
-    b_dev = torch.from_numpy(p.b).to(dev)
-    x_dev = torch.zeros(p.n, dtype=torch.float64, device=dev)
-    mcg = {"identity": m.MCG_IDENTITY, "jacobi": m.MCG_JACOBI, "smw": m.MCG_SMW}[args.mcg]
-    solvers = {prec: m.Solver.from_problem(p, precision=prec, inner_prec=mcg, stream=stream.cuda_stream,
-                                           validate=False)
-               for prec in (m.MIXED_FP32, m.FP64)}
-
-    def run(prec, steps, warmup, clocks=False):
-        s = solvers[prec]
-        for _ in range(warmup):
-            x_dev.zero_()
-            s.solve(b_dev, x_dev, outer_tol=OUTER_TOL, inner_tol=INNER_TOL)
-        barrier(ws)
-        torch.cuda.synchronize(dev)
-        infos = []
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ck = Clocks(local) if clocks else None
-        if ck:
-            ck.__enter__()
-        e0.record(stream)
-        for _ in range(steps):
-            x_dev.zero_()
-            _, info = s.solve(b_dev, x_dev, outer_tol=OUTER_TOL, inner_tol=INNER_TOL)
-            infos.append(info)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        barrier(ws)
-        if ck:
-            ck.__exit__(None, None, None)
-        ok = sum(1 for i in infos if i.status == m.OK and i.true_relres <= OUTER_TOL)
-        ms, ok, v = replica_throughput(e0.elapsed_time(e1), ok, ws, dev)
-        return ms, ok, v, infos, (ck.summary() if ck else None)
-
-    # mixed precision (headline) and plain FP64
-    ms_mx, ok_mx, value, inf_mx, clocks = run(m.MIXED_FP32, args.steps, args.warmup, clocks=(rank == 0))
-    ms_64, ok_64, fp64_value, inf_64, _ = run(m.FP64, args.steps, max(1, args.warmup))
-
-    # errors against x* (FP64 check on the host)
-    x_last = x_dev.cpu().numpy()
-    err64 = float(np.linalg.norm(x_last - p.xstar) / np.linalg.norm(p.xstar))
-    x_dev.zero_()
-    solvers[m.MIXED_FP32].solve(b_dev, x_dev, outer_tol=OUTER_TOL, inner_tol=INNER_TOL)
-    xm = x_dev.cpu().numpy()
-    errmx = float(np.linalg.norm(xm - p.xstar) / np.linalg.norm(p.xstar))
-    rr_mx = float(np.linalg.norm(p.b - p.scipy() @ xm) / np.linalg.norm(p.b))
-
-    # end to end through the C ABI with pinned host buffers (copies inside the call)
-    b_h = torch.from_numpy(p.b.copy()).pin_memory()
-    x_h = torch.zeros(p.n, dtype=torch.float64).pin_memory()
-    sm = solvers[m.MIXED_FP32]
-    x_h.zero_()
-    sm.solve(b_h, x_h, outer_tol=OUTER_TOL, inner_tol=INNER_TOL)
-    barrier(ws)
-    t0 = time.perf_counter()
-    ok_e2e = 0
-    for _ in range(args.steps):
-        x_h.zero_()
-        _, info = sm.solve(b_h, x_h, outer_tol=OUTER_TOL, inner_tol=INNER_TOL)
-        ok_e2e += int(info.status == m.OK and info.true_relres <= OUTER_TOL)
-    t_e2e = time.perf_counter() - t0
-    t_e2e = max_over_ranks(t_e2e, ws, dev)
-    ok_e2e = sum_over_ranks(ok_e2e, ws, dev)
-
-    # dominant kernel: inner-CG step a (SpMV + low-rank term + direction update + dot)
-    ta_mx, tb_mx = m.time_inner_kernels(solvers[m.MIXED_FP32].h, 50)
-    ta_64, tb_64 = m.time_inner_kernels(solvers[m.FP64].h, 50)
-    n, nnz, k = p.n, p.nnz, p.k
-
-    ib = m.launch_config(solvers[m.MIXED_FP32].h)["index_bytes"]
-
-    fused_of = {4: m.launch_config(solvers[m.MIXED_FP32].h)["step_a_variant"] == 8,
-                8: m.launch_config(solvers[m.FP64].h)["step_a_variant"] == 8}
-
-    def bytes_a(w):  # A values + column indices, s and p_old read, V read, q and p_new written
-        if fused_of[w]:  # one-kernel iteration: r, q, p, z read and r, z, p, q written for the own rows
-            return nnz * (w + ib) + k * n * w + 8 * n * w
-        return nnz * (w + ib) + 2 * n * w + k * n * w + 2 * n * w + (n * w if args.mcg == "jacobi" else 0)
-
-    def bytes_b(w):  # p, q, z, r read; z, r written (V^T s by recurrence: no V pass)
-        if fused_of[w]:
-            return 0
-        if args.mcg == "jacobi":  # + M_cg^{-1} read, s written
-            return 8 * n * w
-        if args.mcg == "smw":  # + diag(A)^{-1} and V read, s written
-            return 8 * n * w + k * n * w
-        return 6 * n * w
-
-    peak, peak_kind = measured_peak_gbs()
-    ach_a = bytes_a(4) / (ta_mx * 1e-3) / 1e9
-    kname = step_a_kernel_name(m.launch_config(solvers[m.MIXED_FP32].h))
-    roof = {"kernel": kname, "bound": "hbm", "achieved": round(ach_a, 1), "peak": peak,
-            "unit": "GB/s", "frac": round(ach_a / peak, 4), "traffic": recorded_traffic(kname),
-            "peak_kind": f"{peak_kind} copy bandwidth (burst: kernel timed alone)",
-            "bytes_per_launch": bytes_a(4), "avg_ms": round(ta_mx, 5)}
-
-    kernels = {
-        "mixed": {"step_a_ms": ta_mx, "step_b_ms": tb_mx, "step_a_gbs": bytes_a(4) / (ta_mx * 1e-3) / 1e9,
-                  "step_b_gbs": bytes_b(4) / (max(tb_mx, 1e-6) * 1e-3) / 1e9},
-        "fp64": {"step_a_ms": ta_64, "step_b_ms": tb_64, "step_a_gbs": bytes_a(8) / (ta_64 * 1e-3) / 1e9,
-                 "step_b_gbs": bytes_b(8) / (max(tb_64, 1e-6) * 1e-3) / 1e9},
-    }
-    launches = sum(i.kernel_launches for i in inf_mx)
-
-    cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(p, args.mcg)
-
+    single = measure_single(torch, m, p, dev, stream, ws, local, rank, args.steps, args.warmup, mcg=args.mcg,
+                            cpu=not args.no_cpu_baseline)
+    mx, f64 = single["mixed"], single["fp64"]
+    ka = mx["kernels"]
+    peak, peak_kind = single["peak_gbs"], single["peak_kind"]
+    roof = {"kernel": ka["step_a_kernel"], "bound": "hbm", "achieved": round(ka["step_a_gbs_in_situ"], 1),
+            "peak": peak, "unit": "GB/s", "frac": ka["step_a_frac_in_situ"],
+            "traffic": recorded_traffic(ka["step_a_kernel"]),
+            "peak_kind": f"{peak_kind} copy bandwidth (burst)",
+            "bytes_per_launch": ka["step_a_bytes"], "avg_ms": round(ka["step_a_ms_in_situ"], 5),
+            "avg_ms_standalone": round(ka["step_a_ms_standalone"], 5),
+            "timing": "in situ: the solver's own inner loop timed with CUDA events over 512 iterations "
+                      "(difference of two fixed-count inner solves), split between step a and step b in "
+                      "the ratio of their standalone event-timed averages",
+            "achieved_standalone": round(ka["step_a_gbs_standalone"], 1),
+            "iteration_frac_in_situ": ka["iteration_frac_in_situ"]}
+    roof64 = fp64_roofline(m, single) if rank == 0 else None
+    wl = workloads_block(args, torch, m, dev, stream, ws, local, rank) if ws == 1 else {}
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_mx / args.steps, "higher_is_better": True, "scaling": "weak",
+            "metric": METRIC, "value": mx["value"], "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": mx["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 inner CG + f64 outer MINRES", "data": "synthetic",
-            "config": {"workload": workload, "n": n, "nnz": nnz, "k": k, "outer_tol": OUTER_TOL,
-                       "inner_tol": INNER_TOL, "inner_prec": args.mcg, "precision": "mixed: FP32 inner CG, FP64 outer MINRES",
-                       "l2": f"inputs larger than L2 (FP32 A {nnz * 8 / 1e6:.0f} MB + V {k * n * 4 / 1e6:.0f} MB "
-                             "+ vectors per inner iteration)",
+            "config": {"workload": workload, "n": p.n, "nnz": p.nnz, "k": p.k, "outer_tol": OUTER_TOL,
+                       "inner_tol": INNER_TOL, "inner_prec": args.mcg,
+                       "precision": "mixed: FP32 inner CG, FP64 outer MINRES",
+                       "l2": f"inputs larger than L2 (FP32 A {p.nnz * 8 / 1e6:.0f} MB + V "
+                             f"{p.k * p.n * 4 / 1e6:.0f} MB + vectors per inner iteration)",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "roofline": roof,
-            "launch_config": {"mixed": m.launch_config(solvers[m.MIXED_FP32].h),
-                              "fp64": m.launch_config(solvers[m.FP64].h)},
-            "spmv_hbm_gbs": {"mixed_step_a": round(kernels["mixed"]["step_a_gbs"], 1),
-                             "fp64_step_a": round(kernels["fp64"]["step_a_gbs"], 1), "peak": peak},
-            "kernels": {kk: {a: round(b, 5) for a, b in v.items()} for kk, v in kernels.items()},
-            "fp64": {"value": fp64_value, "unit": "solves/s", "ms_per_step": ms_64 / args.steps,
-                     "outer_iters": inf_64[-1].outer_iters, "inner_iters_total": inf_64[-1].inner_iters_total,
-                     "true_relres": inf_64[-1].true_relres, "rel_err_vs_xstar": err64},
-            "mixed": {"outer_iters": inf_mx[-1].outer_iters, "inner_iters_total": inf_mx[-1].inner_iters_total,
-                      "restarts": inf_mx[-1].restarts, "true_relres": inf_mx[-1].true_relres,
-                      "true_relres_host_fp64": rr_mx, "rel_err_vs_xstar": errmx},
-            "mixed_vs_fp64_speedup": value / fp64_value if fp64_value > 0 else None,
-            "e2e": {"value": ok_e2e / t_e2e, "unit": "solves/s", "h2d_bytes_per_step": 2 * n * 8,
-                    "d2h_bytes_per_step": n * 8},
-            "gpu_launches": int(launches),
-            "launches_per_solve": round(launches / max(1, len(inf_mx)), 1),
-            "clocks": clocks,
-            "cpu_baseline": cpu,
+            "roofline_fp64": roof64,
+            "fp64": {k: v for k, v in f64.items()},
+            "mixed": {k: v for k, v in mx.items() if k != "clocks"},
+            "mixed_vs_fp64_speedup": single["mixed_vs_fp64_speedup"],
+            "mixed_rel_err_vs_fp64": single["mixed_rel_err_vs_fp64"],
+            "e2e": single["e2e"],
+            "gpu_launches": int(mx["launches_per_solve"] * args.steps),
+            "launches_per_solve": mx["launches_per_solve"],
+            "clocks": mx.get("clocks"),
+            "cpu_baseline": single.get("cpu_baseline"),
+            "workloads": wl,
         }
         print(json.dumps(line), flush=True)
-    for s in solvers.values():
-        s.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -319,6 +319,49 @@ mrcg_status mrcg_mmr_apply_noalloc(int64_t n, const int64_t* rowptr, const int32
                                    int32_t k, const double* V, const double* lambda, const double* u, double* out,
                                    void* stream);
 
+/* ---- Setup stage 2: the negative eigenpairs that define M_mr ----
+ *
+ * The paper's scheme computes the k negative eigenvalues of A and an
+ * approximate basis of their invariant subspace once, before the solves
+ * (Sec. 2, stage two of the three-stage summary; the experiments use a
+ * Krylov eigensolver, Sec. 4), and amortises that cost over many solves.
+ * mrcg_negative_eigenpairs does this on the GPU with the library's own block
+ * SpMV: Chebyshev-filtered subspace iteration on a block of `block` vectors
+ * (FP64), Rayleigh-Ritz between filters, until every Ritz value below zero
+ * has a residual ||A v - lambda v||_2 <= tol * ||A||_gersh (the Gershgorin
+ * bound of the spectral radius) and the first nonnegative Ritz value of the
+ * block has settled to sqrt(tol) * ||A||_gersh.  Its output is ready for
+ * mrcg_create_args (V column-major, lambda ascending, all < 0). */
+typedef struct {
+  int32_t negative_found;      /* negative Ritz values in the block at exit */
+  int32_t rayleigh_ritz_steps;
+  int64_t block_spmvs;         /* products A X with the n x block matrix X */
+  double max_residual;         /* max ||A v - lambda v||_2 over the negative pairs at exit */
+  double spectrum_lo;          /* Gershgorin bounds of the spectrum of A */
+  double spectrum_hi;
+  double seconds;              /* wall time of the call */
+  int32_t status;              /* mrcg_status of the call */
+} mrcg_eig_info;
+
+/* CSR A as for mrcg_create_args (host or device arrays, full symmetric
+ * storage).  block: 2..64 vectors, more than the number of negative
+ * eigenvalues (a guard of 8 or more speeds convergence).  tol > 0 (1e-11 gives
+ * subspaces that pass mrcg_solver_create's validation with a wide margin).
+ * max_spmv: cap on block SpMVs.  seed: the start block's counter-based hash.
+ * Outputs: *k (the number of negative eigenvalues found), V (capacity n x
+ * block doubles, column-major; the first k columns written, orthonormal) and
+ * lambda (capacity block; the first k written, ascending), host or device.
+ * Allocates its own device work space (about 4 n x 64 doubles at most) on the
+ * current device and frees it before returning.  info may be NULL.
+ * Errors: MRCG_ERR_INVALID (bad sizes or CSR), MRCG_ERR_NONFINITE,
+ * MRCG_ERR_MAXITER (not converged within max_spmv: most often the block holds
+ * no nonnegative Ritz value, i.e. `block` is too small for A's negative
+ * eigenvalues; info->negative_found says how many it saw), MRCG_ERR_BREAKDOWN
+ * (the block lost rank), MRCG_ERR_OOM, MRCG_ERR_CUDA. */
+mrcg_status mrcg_negative_eigenpairs(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val,
+                                     int32_t block, double tol, int64_t max_spmv, uint64_t seed, int32_t* k,
+                                     double* V, double* lambda, mrcg_eig_info* info);
+
 /* Release every device and host resource of the handle (NULL is a no-op). */
 void mrcg_solver_destroy(mrcg_handle h);
 

@@ -242,6 +242,21 @@ def minres(sys: System, b, prec, x0=None, outer_tol=1e-10, max_outer=200, max_in
     return _result(x, info, hr, he)
 
 
+def negative_eigenpairs_dense(rowptr, colind, val):
+    """Setup stage 2 by its definition (Sec. 2): every eigenpair of the
+    symmetric A with a negative eigenvalue, from a dense symmetric
+    eigendecomposition (numpy.linalg.eigh; small n only).  Returns (V n x k,
+    lam[k] ascending, all eigenvalues)."""
+    n = len(rowptr) - 1
+    A = np.zeros((n, n))
+    for i in range(n):
+        for p in range(int(rowptr[i]), int(rowptr[i + 1])):
+            A[i, int(colind[p])] += float(val[p])
+    w, Q = np.linalg.eigh(0.5 * (A + A.T))
+    k = int(np.sum(w < 0.0))
+    return Q[:, :k].copy(), w[:k].copy(), w
+
+
 def abs_2x2(a, b, c):
     """Sec. 1 2x2 replacement.  Returns (block[2,2], (l1, l2), (cs, sn))."""
     out = np.zeros(3); eig = np.zeros(2); rot = np.zeros(2)

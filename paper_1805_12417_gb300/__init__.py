@@ -39,6 +39,12 @@ class Info(C.Structure):
                 ("status", C.c_int32)]
 
 
+class EigInfo(C.Structure):
+    _fields_ = [("negative_found", C.c_int32), ("rayleigh_ritz_steps", C.c_int32), ("block_spmvs", C.c_int64),
+                ("max_residual", C.c_double), ("spectrum_lo", C.c_double), ("spectrum_hi", C.c_double),
+                ("seconds", C.c_double), ("status", C.c_int32)]
+
+
 _lib = None
 
 
@@ -69,6 +75,9 @@ def lib() -> C.CDLL:
         L.mrcg_time_inner_graph.restype = C.c_int
         L.mrcg_fp64_fma_peak.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.mrcg_fp64_fma_peak.restype = C.c_int
+        L.mrcg_negative_eigenpairs.argtypes = [C.c_int64, P, P, P, C.c_int32, C.c_double, C.c_int64, C.c_uint64,
+                                               C.POINTER(C.c_int32), P, P, C.POINTER(EigInfo)]
+        L.mrcg_negative_eigenpairs.restype = C.c_int
         L.mrcg_batch_create.argtypes = [C.c_int32, C.POINTER(CreateArgs), C.POINTER(C.c_void_p)]
         L.mrcg_batch_create.restype = C.c_int
         L.mrcg_batched_solve.argtypes = [P, P, P, C.c_double, C.c_double, C.c_int64, C.POINTER(Info)]
@@ -261,6 +270,28 @@ def fp64_fma_peak():
     if st != OK:
         raise MrcgError(st, "mrcg_fp64_fma_peak")
     return float(tf.value), float(ms.value)
+
+
+def negative_eigenpairs(n, rowptr, colind, val, block, tol=1e-11, max_spmv=400000, seed=1):
+    """mrcg_negative_eigenpairs: the negative eigenpairs of the CSR matrix A
+    (setup stage 2).  Returns (V n x k, lam[k] ascending, info dict); raises
+    MrcgError on failure (info is attached to the error as .info)."""
+    _check_dtype(rowptr, np.int64, "rowptr"); _check_dtype(colind, np.int32, "colind")
+    _check_dtype(val, np.float64, "val")
+    V = np.zeros(int(n) * int(block))
+    lam = np.zeros(int(block))
+    k = C.c_int32(0)
+    info = EigInfo()
+    rp, k1 = _ptr(rowptr); ci, k2 = _ptr(colind); va, k3 = _ptr(val)
+    st = lib().mrcg_negative_eigenpairs(int(n), rp, ci, va, int(block), float(tol), int(max_spmv), int(seed),
+                                        C.byref(k), V.ctypes.data, lam.ctypes.data, C.byref(info))
+    d = {f: getattr(info, f) for f, _ in EigInfo._fields_}
+    if st != OK:
+        err = MrcgError(st, "mrcg_negative_eigenpairs")
+        err.info = d
+        raise err
+    kk = int(k.value)
+    return V[: int(n) * kk].reshape(kk, int(n)).T.copy(), lam[:kk].copy(), d
 
 
 class Solver:

@@ -875,7 +875,9 @@ mrcg_status mrcg_time_inner_graph(mrcg_handle h, int32_t iters, double* ms_per_i
   CK(cudaEventCreate(&e1));
   // one inner solve of exactly `n_it` iterations (tolerance 1e-300: only the
   // budget stops it), bracketed by events on the handle's stream
-  auto timed = [&](long long n_it, float* ms) -> mrcg_status {
+  // returns the iterations the solve ran (it stops at the budget unless the
+  // recursion itself ends, e.g. a residual that reaches exactly zero)
+  auto timed = [&](long long n_it, float* ms, long long* ran) -> mrcg_status {
     reset_state(h, 1e-300, n_it);
     h->h_init->cg.vin = h->v[0];
     h->h_init->cg.zout = h->zraw;
@@ -886,19 +888,24 @@ mrcg_status mrcg_time_inner_graph(mrcg_handle h, int32_t iters, double* ms_per_i
     CK(cudaEventSynchronize(e1));
     CK(cudaEventElapsedTime(ms, e0, e1));
     ST(read_state(h));
-    if (h->h_st->cg.iters != n_it) return MRCG_ERR_BREAKDOWN;
+    *ran = h->h_st->cg.iters;
+    if (getenv("MRCG_DEBUG"))
+      fprintf(stderr, "mrcg time_inner_graph: budget %lld ran %lld done %d in %.3f ms\n", n_it, *ran,
+              h->h_st->cg.done, (double)*ms);
     return MRCG_OK;
   };
   const long long base = 2LL * h->unroll;
   float t_short = 0.f, t_long = 0.f, unused = 0.f;
-  mrcg_status st = timed(base, &unused);  // warm-up
+  long long r0 = 0, r1 = 0, r2 = 0;
+  mrcg_status st = timed(base, &unused, &r0);  // warm-up
   // the difference of two solves cancels the per-solve kernels (norm, init, finish)
-  if (st == MRCG_OK) st = timed(base, &t_short);
-  if (st == MRCG_OK) st = timed(base + iters, &t_long);
+  if (st == MRCG_OK) st = timed(base, &t_short, &r1);
+  if (st == MRCG_OK) st = timed(base + iters, &t_long, &r2);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != MRCG_OK) return st;
-  *ms_per_iter = (double)(t_long - t_short) / (double)iters;
+  if (r2 - r1 < iters / 2) return MRCG_ERR_BREAKDOWN;  // the recursion stopped early: no steady state to time
+  *ms_per_iter = (double)(t_long - t_short) / (double)(r2 - r1);
   return MRCG_OK;
 }
 

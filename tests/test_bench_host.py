@@ -70,7 +70,11 @@ def test_reference_arm_prints_the_contract_line():
     assert line["impl"] == "reference" and line["steps"] == 2 and line["warmup"] == 3
     assert line["value"] > 0 and line["unit"] == "solves/s" and line["higher_is_better"] is True
     assert line["config"]["workload"].startswith("lap2d_64x64_k4")
-    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    import oracle as O
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == O.threads_available()
+    # the whole 64 x 64 solve fits a step: nothing is extrapolated, and ms_per_step is the solve's real time
+    assert line["value_extrapolated"] is False
+    assert abs(line["ms_per_step"] - 1000.0 / line["value"]) <= 0.5 * line["ms_per_step"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
 
 
@@ -90,9 +94,12 @@ def test_cpu_baseline_scales_only_by_the_oracles_own_count(monkeypatch):
         lambda cls, q: cls(p.rowptr, p.colind, p.val, p.V, p.lam)))
     cb = bench.cpu_baseline(big)
     assert cb["value"] is None and "no whole oracle solve" in cb["sample"]
+    assert cb["serial"]["value"] is None
     monkeypatch.setattr(bench, "full_solve_inner_iters", lambda name, mcg="identity": 815)
     cb = bench.cpu_baseline(big)
     assert cb["value"] > 0 and "scaled by the 815 inner iterations" in cb["sample"]
+    assert cb["serial"]["value"] > 0 and cb["serial"]["cores"] == 1 and cb["extrapolated"] is True
+    assert cb["cores"] == O.threads_available() and cb["cpu_model"]
 
 
 def test_reference_arm_follows_the_inner_tolerance():

@@ -617,3 +617,23 @@ def test_saddle_krylov_eigensolver_matches_dense():
     assert np.allclose(lk, ld, atol=1e-12)
     assert np.linalg.norm(A @ Vk - Vk * lk, axis=0).max() < 1e-10
     assert np.linalg.svd(Vk.T @ Vd, compute_uv=False).min() > 1 - 1e-10
+
+
+
+# ---------------------------------------------------------------- setup stage 2: negative eigenpairs
+
+def test_dense_negative_eigenpairs_match_laplacian_spectrum_and_inertia():
+    """The dense stage-2 reference returns the analytic negative spectrum of a
+    shifted Laplacian (sine-mode eigenvalues) with an orthonormal basis of
+    A-invariant vectors, and Sylvester's count on a saddle system."""
+    p = shifted_laplacian_problem("eig_pin", (13, 11), 5, seed=3)
+    V, lam, w = O.negative_eigenpairs_dense(p.rowptr, p.colind, p.val)
+    assert len(lam) == p.k
+    assert np.allclose(lam, p.lam, rtol=0, atol=1e-12)
+    A = p.dense()
+    assert np.allclose(A @ V, V * lam, atol=1e-11)
+    assert np.allclose(V.T @ V, np.eye(p.k), atol=1e-12)
+    from gen import small_saddle
+    q = small_saddle()
+    V2, lam2, _ = O.negative_eigenpairs_dense(q.rowptr, q.colind, q.val)
+    assert len(lam2) == q.k  # nb constraint rows: Sylvester's law of inertia
