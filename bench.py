@@ -513,7 +513,10 @@ def measure_single(torch, m, p, dev, stream, ws, local, rank, steps, warmup, mcg
             r["clocks"] = ck
         if kernel_timing:
             ta, tb = m.time_inner_kernels(s.h, 50)
-            t_it = m.time_inner_graph(s.h, 512)
+            try:
+                t_it = m.time_inner_graph(s.h, 512)
+            except m.MrcgError:  # the recursion ended too early to time in situ: standalone sum
+                t_it = ta + tb
             ba, bb = inner_bytes(cfg, n, nnz, k, w, mcg)
             # in-situ step a: the in-loop iteration time split in the ratio of the standalone times
             ta_in = t_it * ta / (ta + tb) if (ta + tb) > 0 else t_it

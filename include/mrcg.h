@@ -85,12 +85,20 @@ typedef enum {
 typedef enum {
   MRCG_MCG_IDENTITY = 0, /* M_cg = I */
   MRCG_MCG_JACOBI = 1,   /* M_cg = diag(M_mr) */
-  MRCG_MCG_SMW = 2       /* MINRES-CG* (Sec. 2.1): M_cg^{-1} = Atilde^{-1} - 2 V_hat Lambda_hat^{-1} V_hat^T,
+  MRCG_MCG_SMW = 2,      /* MINRES-CG* (Sec. 2.1): M_cg^{-1} = Atilde^{-1} - 2 V_hat Lambda_hat^{-1} V_hat^T,
                             the Sherman-Morrison-Woodbury form of M_mr^{-1} with A^{-1} approximated by
                             Atilde^{-1} = diag(A)^{-1}.  Needs a nonzero diagonal in every row of A
                             (else MRCG_ERR_INVALID at create); positive definite when diag(A) > 0.
                             Costs one more pass over V_hat per inner iteration.  Single systems only
                             (mrcg_batch_create and mrcg_shifted_create reject it). */
+  MRCG_MCG_ILU0 = 3,     /* the incomplete LU factorisation ILU(0) of A (the experiments' inner preconditioner,
+                            Sec. 4) in block-Jacobi form: A's diagonal blocks of ilu_block consecutive rows are
+                            factored at create (couplings between blocks dropped; ilu_block >= n is plain
+                            ILU(0)) and each inner CG step solves with the factors, one warp per block, level by
+                            level.  Indefinite A gives an indefinite M_cg (Sec. 2 discusses CG with an indefinite
+                            preconditioner); a zero pivot is MRCG_ERR_BREAKDOWN at create.  Single systems only. */
+  MRCG_MCG_SMW_ILU0 = 4  /* MINRES-CG* (Sec. 2.1) with Atilde = those ILU(0) factors:
+                            M_cg^{-1} = (L U)^{-1} - 2 V_hat Lambda_hat^{-1} V_hat^T.  Single systems only. */
 } mrcg_inner_prec;
 
 typedef struct {
@@ -109,6 +117,9 @@ typedef struct {
   double restart_factor;  /* restart a MINRES cycle when relres_j > f * relres_{j-3}
                              (j >= 4 within the cycle); 0 selects 0.5, < 0 disables */
   void* stream;           /* cudaStream_t to order all work on; NULL = a stream of its own */
+  int32_t ilu_block;      /* MRCG_MCG_ILU0 / MRCG_MCG_SMW_ILU0: rows per diagonal block, a multiple of 32 up to
+                             16384 (8192 with MRCG_FP64); 0 selects 8192 (capped at the padded n) */
+  int32_t reserved;       /* set to 0 */
 } mrcg_create_args;
 
 typedef struct {
@@ -132,7 +143,8 @@ typedef struct {
  * FP32 copy of A and V_hat.
  * Errors: MRCG_ERR_INVALID (bad sizes, unsorted or out-of-range columns,
  * lambda >= 0, a V_hat that fails validation, a zero diagonal entry of A with
- * MRCG_MCG_SMW), MRCG_ERR_OOM, MRCG_ERR_CUDA. */
+ * MRCG_MCG_SMW, a bad ilu_block), MRCG_ERR_BREAKDOWN (a zero pivot in the
+ * ILU(0) factorisation), MRCG_ERR_OOM, MRCG_ERR_CUDA. */
 mrcg_status mrcg_solver_create(const mrcg_create_args* args, mrcg_handle* out);
 
 /* Solve A x = b by MINRES-CG (Algorithm 1).  On entry x holds x0, on exit the
@@ -180,12 +192,15 @@ mrcg_status mrcg_time_inner_kernels(mrcg_handle h, int32_t iters, double* ms);
 /* In-situ time of one inner CG iteration (Eq. 2) as it runs inside the
  * solver: the handle's own inner-CG graph (the device-side loop, or the
  * host-driven loop under MRCG_INNER_LOOP=host) is launched on a fixed
- * synthetic right-hand side for exactly 2U and 2U + iters iterations
- * (U = iterations per loop body), each bracketed by CUDA events on the
- * handle's stream, and *ms_per_iter receives the difference divided by iters
- * (the per-solve kernels cancel).  8 <= iters <= 65536.  Overwrites the
+ * synthetic right-hand side with no tolerance, for 2U and for 2U + iters
+ * iterations (U = iterations per loop body), each bracketed by CUDA events
+ * on the handle's stream, and *ms_per_iter receives the difference divided by
+ * the difference of the iterations run (the per-solve kernels cancel).  An
+ * FP32 recursion can end by itself once it reaches its rounding floor
+ * (p^T q <= 0); a first probe run finds where, and the long run then stops at
+ * three quarters of that count.  8 <= iters <= 65536.  Overwrites the
  * handle's work vectors (not its matrix).  Errors: MRCG_ERR_INVALID,
- * MRCG_ERR_BREAKDOWN (the solve stopped before the count), MRCG_ERR_CUDA. */
+ * MRCG_ERR_BREAKDOWN (fewer than 8 iterations to time), MRCG_ERR_CUDA. */
 mrcg_status mrcg_time_inner_graph(mrcg_handle h, int32_t iters, double* ms_per_iter);
 
 /* Measured FP64 fused-multiply-add throughput of the current device, in

@@ -22,7 +22,7 @@ _OUT = os.path.join(_HERE, "_build", "liboracle.so")
 _OUT_OMP = os.path.join(_HERE, "_build", "liboracle_omp.so")
 
 OK, ERR_INVALID, ERR_NOT_SPD, ERR_BREAKDOWN, ERR_MAXITER, ERR_NONFINITE = range(6)
-MCG_IDENTITY, MCG_JACOBI, MCG_SMW = 0, 1, 2
+MCG_IDENTITY, MCG_JACOBI, MCG_SMW, MCG_ILU0, MCG_SMW_ILU0 = 0, 1, 2, 3, 4
 STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "NOT_SPD", 3: "BREAKDOWN", 4: "MAXITER", 5: "NONFINITE"}
 
 
@@ -48,9 +48,14 @@ def build(force: bool = False) -> str:
     return _build_one(_OUT, [])
 
 
+class _Ilu(C.Structure):
+    _fields_ = [("n", C.c_int64), ("block", C.c_int64), ("lrow", C.c_void_p), ("urow", C.c_void_p),
+                ("lcol", C.c_void_p), ("ucol", C.c_void_p), ("lval", C.c_void_p), ("uval", C.c_void_p)]
+
+
 class _System(C.Structure):
     _fields_ = [("n", C.c_int64), ("rowptr", C.c_void_p), ("colind", C.c_void_p), ("val", C.c_void_p),
-                ("k", C.c_int32), ("V", C.c_void_p), ("lam", C.c_void_p)]
+                ("k", C.c_int32), ("V", C.c_void_p), ("lam", C.c_void_p), ("ilu", C.POINTER(_Ilu))]
 
 
 class _Info(C.Structure):
@@ -110,6 +115,12 @@ def _declare(L):
     L.orc_abs_2x2.argtypes = [C.c_double, C.c_double, C.c_double, P, P, P]
     L.orc_true_relres.argtypes = [C.POINTER(_System), P, P, P]
     L.orc_true_relres.restype = C.c_double
+    L.orc_ilu0_factor.argtypes = [C.POINTER(_System), C.c_int64, C.POINTER(_Ilu)]
+    L.orc_ilu0_factor.restype = C.c_int
+    L.orc_ilu0_free.argtypes = [C.POINTER(_Ilu)]
+    L.orc_ilu0_free.restype = None
+    L.orc_ilu0_apply.argtypes = [C.POINTER(_Ilu), P, P]
+    L.orc_ilu0_apply.restype = None
     return L
 
 
@@ -138,7 +149,58 @@ class System:
             self.Vc = np.ascontiguousarray(V.T)
             self.lam = _f64(lam)
         self._s = _System(self.n, self.rowptr.ctypes.data, self.colind.ctypes.data, self.val.ctypes.data,
-                          self.k, self.Vc.ctypes.data, self.lam.ctypes.data)
+                          self.k, self.Vc.ctypes.data, self.lam.ctypes.data, None)
+        self._ilu = None
+
+    def set_ilu0(self, block=None):
+        """Factor A by block-Jacobi ILU(0) (diagonal blocks of `block` rows; None:
+        one block) for the MCG_ILU0 / MCG_SMW_ILU0 inner preconditioners.
+        Returns the status (OK or ERR_BREAKDOWN on a zero pivot)."""
+        self.clear_ilu0()
+        f = _Ilu()
+        st = lib().orc_ilu0_factor(C.byref(self._s), int(block or self.n), C.byref(f))
+        if st == OK:
+            self._ilu = f
+            self._s.ilu = C.pointer(self._ilu)
+        return st
+
+    def clear_ilu0(self):
+        if self._ilu is not None:
+            self._s.ilu = None
+            lib().orc_ilu0_free(C.byref(self._ilu))
+            self._ilu = None
+
+    def __del__(self):
+        try:
+            self.clear_ilu0()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+    def ilu0_factors(self):
+        """(L, U) of the current factorisation as dense arrays (small n only):
+        L unit lower triangular, U upper triangular with its diagonal."""
+        f = self._ilu
+        n = self.n
+        L = np.eye(n)
+        U = np.zeros((n, n))
+        lrow = np.ctypeslib.as_array(C.cast(f.lrow, C.POINTER(C.c_int64)), shape=(n + 1,))
+        urow = np.ctypeslib.as_array(C.cast(f.urow, C.POINTER(C.c_int64)), shape=(n + 1,))
+        nl, nu = int(lrow[n]), int(urow[n])
+        lcol = np.ctypeslib.as_array(C.cast(f.lcol, C.POINTER(C.c_int32)), shape=(max(nl, 1),))
+        ucol = np.ctypeslib.as_array(C.cast(f.ucol, C.POINTER(C.c_int32)), shape=(max(nu, 1),))
+        lval = np.ctypeslib.as_array(C.cast(f.lval, C.POINTER(C.c_double)), shape=(max(nl, 1),))
+        uval = np.ctypeslib.as_array(C.cast(f.uval, C.POINTER(C.c_double)), shape=(max(nu, 1),))
+        for i in range(n):
+            for p in range(int(lrow[i]), int(lrow[i + 1])):
+                L[i, lcol[p]] = lval[p]
+            for p in range(int(urow[i]), int(urow[i + 1])):
+                U[i, ucol[p]] = uval[p]
+        return L, U
+
+    def ilu0_apply(self, r):
+        r = _f64(r); out = np.empty(self.n)
+        lib().orc_ilu0_apply(C.byref(self._ilu), r.ctypes.data, out.ctypes.data)
+        return out
 
     @classmethod
     def from_problem(cls, p):

@@ -108,10 +108,122 @@ static int diag_a_inverse(const orc_system* s, double* dainv) {
   return ORC_OK;
 }
 
+/* Sec. 4 (the experiments' inner preconditioner): ILU(0).  Row i of the
+ * working copy w (A's entries of row i inside its block) is reduced by the
+ * rows k < i it holds, in increasing k: w_ik <- w_ik / u_kk, then
+ * w_ij <- w_ij - w_ik u_kj for every j > k that is in row i's pattern.  The
+ * reduced row is split into L (j < i) and U (j >= i). */
+int orc_ilu0_factor(const orc_system* s, int64_t block, orc_ilu* f) {
+  const int64_t n = s->n;
+  memset(f, 0, sizeof(*f));
+  if (block < 1) return ORC_ERR_INVALID;
+  f->n = n;
+  f->block = block;
+  f->lrow = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+  f->urow = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+  const int64_t nnz = s->rowptr[n];
+  f->lcol = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nnz + 1));
+  f->ucol = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nnz + 1));
+  f->lval = (double*)malloc(sizeof(double) * (size_t)(nnz + 1));
+  f->uval = (double*)malloc(sizeof(double) * (size_t)(nnz + 1));
+  double* w = (double*)calloc((size_t)n, sizeof(double));       /* dense scatter of the current row */
+  int64_t* upos = (int64_t*)malloc(sizeof(int64_t) * (size_t)n); /* row k -> position of u_kk */
+  if (!f->lrow || !f->urow || !f->lcol || !f->ucol || !f->lval || !f->uval || !w || !upos) {
+    free(w); free(upos); orc_ilu0_free(f);
+    return ORC_ERR_INVALID;
+  }
+  int64_t nl = 0, nu = 0;
+  int rc = ORC_OK;
+  for (int64_t i = 0; i < n && rc == ORC_OK; ++i) {
+    const int64_t b0 = (i / block) * block, b1 = b0 + block < n ? b0 + block : n;
+    /* scatter row i's in-block entries */
+    for (int64_t p = s->rowptr[i]; p < s->rowptr[i + 1]; ++p) {
+      const int64_t j = s->colind[p];
+      if (j >= b0 && j < b1) w[j] = s->val[p];
+    }
+    /* eliminate with the rows k < i of the pattern, in increasing k */
+    for (int64_t p = s->rowptr[i]; p < s->rowptr[i + 1]; ++p) {
+      const int64_t kk = s->colind[p];
+      if (kk < b0 || kk >= i) continue;
+      const double piv = f->uval[upos[kk]];
+      const double lik = w[kk] / piv;
+      w[kk] = lik;
+      for (int64_t q = upos[kk] + 1; q < f->urow[kk + 1]; ++q) {
+        const int64_t j = f->ucol[q];
+        /* only positions of row i's pattern are kept (level 0 fill) */
+        int in_pattern = 0;
+        for (int64_t r = s->rowptr[i]; r < s->rowptr[i + 1]; ++r)
+          if (s->colind[r] == j) { in_pattern = 1; break; }
+        if (in_pattern) w[j] -= lik * f->uval[q];
+      }
+    }
+    /* gather: L (j < i), U (j >= i) */
+    f->lrow[i] = nl;
+    f->urow[i] = nu;
+    int have_diag = 0;
+    for (int64_t p = s->rowptr[i]; p < s->rowptr[i + 1]; ++p) {
+      const int64_t j = s->colind[p];
+      if (j < b0 || j >= b1) continue;
+      if (j < i) {
+        f->lcol[nl] = (int32_t)j;
+        f->lval[nl++] = w[j];
+      } else {
+        if (j == i) { upos[i] = nu; have_diag = 1; }
+        f->ucol[nu] = (int32_t)j;
+        f->uval[nu++] = w[j];
+      }
+      w[j] = 0.0;
+    }
+    if (!have_diag || f->uval[upos[i]] == 0.0 || !isfinite(f->uval[upos[i]])) rc = ORC_ERR_BREAKDOWN;
+    f->lrow[i + 1] = nl;
+    f->urow[i + 1] = nu;
+  }
+  free(w);
+  free(upos);
+  if (rc != ORC_OK) orc_ilu0_free(f);
+  return rc;
+}
+
+void orc_ilu0_free(orc_ilu* f) {
+  free(f->lrow); free(f->urow); free(f->lcol); free(f->ucol); free(f->lval); free(f->uval);
+  memset(f, 0, sizeof(*f));
+}
+
+void orc_ilu0_apply(const orc_ilu* f, const double* r, double* out) {
+  const int64_t n = f->n;
+  for (int64_t i = 0; i < n; ++i) { /* L y = r (unit diagonal) */
+    double acc = r[i];
+    for (int64_t p = f->lrow[i]; p < f->lrow[i + 1]; ++p) acc -= f->lval[p] * out[f->lcol[p]];
+    out[i] = acc;
+  }
+  for (int64_t i = n - 1; i >= 0; --i) { /* U x = y; u_ii is the row's first U entry */
+    double acc = out[i];
+    const int64_t p0 = f->urow[i];
+    for (int64_t p = p0 + 1; p < f->urow[i + 1]; ++p) acc -= f->uval[p] * out[f->ucol[p]];
+    out[i] = acc / f->uval[p0];
+  }
+}
+
+/* Sec. 2.1 with Atilde = the ILU(0) factors: (L U)^{-1} r - 2 V (Lambda^{-1} (V^T r)) */
+static void smw_ilu_apply(const orc_system* s, const double* r, double* out, double* t) {
+  const int64_t n = s->n;
+  for (int32_t j = 0; j < s->k; ++j) t[j] = dot(n, s->V + (int64_t)j * n, r);
+  for (int32_t j = 0; j < s->k; ++j) t[j] = -2.0 * t[j] / s->lam[j];
+  orc_ilu0_apply(s->ilu, r, out);
+  for (int64_t i = 0; i < n; ++i)
+    for (int32_t j = 0; j < s->k; ++j) out[i] += s->V[(int64_t)j * n + i] * t[j];
+}
+
 int orc_mcg_apply(const orc_system* s, int mcg, const double* r, double* out, double* work) {
   const int64_t n = s->n;
   double* d = work;
   double* t = work + n;
+  if (mcg == ORC_MCG_ILU0 || mcg == ORC_MCG_SMW_ILU0) {
+    if (!s->ilu) return ORC_ERR_INVALID;
+    if (mcg == ORC_MCG_ILU0) orc_ilu0_apply(s->ilu, r, out);
+    else smw_ilu_apply(s, r, out, t);
+    return ORC_OK;
+  }
   if (mcg == ORC_MCG_SMW) {
     const int rc = diag_a_inverse(s, d);
     if (rc != ORC_OK) return rc;
@@ -140,6 +252,8 @@ int orc_cg(const orc_system* s, int mcg, const double* y, double* z, double tol,
   double* dinv = work + 4 * n;
   double* t = work + 5 * n;
   *iters = 0;
+  const int fact = mcg == ORC_MCG_ILU0 || mcg == ORC_MCG_SMW_ILU0; /* M_cg^{-1} through the ILU(0) factors */
+  if (fact && !s->ilu) return ORC_ERR_INVALID;
   if (mcg == ORC_MCG_SMW) {
     const int rc = diag_a_inverse(s, dinv);
     if (rc != ORC_OK) return rc;
@@ -155,6 +269,8 @@ int orc_cg(const orc_system* s, int mcg, const double* y, double* z, double tol,
   }
   if (mcg == ORC_MCG_SMW) {
     smw_apply(s, dinv, r, sv, t);
+  } else if (fact) {
+    orc_mcg_apply(s, mcg, r, sv, dinv); /* dinv: scratch of n + k doubles here */
   } else {
     for (int64_t i = 0; i < n; ++i) sv[i] = dinv[i] * r[i];
   }
@@ -180,6 +296,8 @@ int orc_cg(const orc_system* s, int mcg, const double* y, double* z, double tol,
     if (rnorm <= tol * ynorm) return ORC_OK;
     if (mcg == ORC_MCG_SMW) {
       smw_apply(s, dinv, r, sv, t);
+    } else if (fact) {
+      orc_mcg_apply(s, mcg, r, sv, dinv);
     } else {
       ORC_FOR
       for (int64_t i = 0; i < n; ++i) sv[i] = dinv[i] * r[i];

@@ -26,9 +26,22 @@ enum {
   ORC_ERR_NONFINITE = 5
 };
 
-/* inner preconditioner M_cg: identity; Jacobi with diag(M_mr); or the
- * MINRES-CG* preconditioner of Sec. 2.1, M_cg^{-1} = diag(A)^{-1} - 2 V Lambda^{-1} V^T */
-enum { ORC_MCG_IDENTITY = 0, ORC_MCG_JACOBI = 1, ORC_MCG_SMW = 2 };
+/* inner preconditioner M_cg: identity; Jacobi with diag(M_mr); the
+ * MINRES-CG* preconditioner of Sec. 2.1, M_cg^{-1} = diag(A)^{-1} - 2 V Lambda^{-1} V^T;
+ * the incomplete factorisation ILU(0) of A (Sec. 4), block-Jacobi: factored on
+ * the diagonal blocks of `block` consecutive rows; or MINRES-CG* with that
+ * factorisation as Atilde: M_cg^{-1} = (L U)^{-1} - 2 V Lambda^{-1} V^T */
+enum { ORC_MCG_IDENTITY = 0, ORC_MCG_JACOBI = 1, ORC_MCG_SMW = 2, ORC_MCG_ILU0 = 3, ORC_MCG_SMW_ILU0 = 4 };
+
+/* ILU(0) factors: L strictly lower (unit diagonal implied) and U upper with
+ * its diagonal, both on the pattern of A restricted to the diagonal blocks
+ * (CSR, column-sorted). */
+typedef struct orc_ilu {
+  int64_t n, block;
+  int64_t *lrow, *urow;
+  int32_t *lcol, *ucol;
+  double *lval, *uval;
+} orc_ilu;
 
 typedef struct {
   int64_t n;
@@ -38,7 +51,17 @@ typedef struct {
   int32_t k;
   const double* V;   /* n x k column-major */
   const double* lam; /* k eigenvalues (negative) */
+  const orc_ilu* ilu; /* factors for ORC_MCG_ILU0 / ORC_MCG_SMW_ILU0, else NULL */
 } orc_system;
+
+/* ILU(0) of A on its diagonal blocks of `block` rows (block >= n: the whole
+ * matrix): Gaussian elimination in row order keeping only the positions of
+ * A's pattern inside the block (Saad, Iterative Methods, Alg. 10.4).
+ * ORC_ERR_BREAKDOWN on a zero or non-finite pivot.  Free with orc_ilu0_free. */
+int orc_ilu0_factor(const orc_system* s, int64_t block, orc_ilu* out);
+void orc_ilu0_free(orc_ilu* f);
+/* out = U^{-1} (L^{-1} r): forward then backward substitution */
+void orc_ilu0_apply(const orc_ilu* f, const double* r, double* out);
 
 /* y = A x (the products with A that Alg. 1 takes). */
 void orc_csr_spmv(const orc_system* s, const double* x, double* y);

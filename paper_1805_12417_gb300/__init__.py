@@ -22,14 +22,15 @@ LIB_PATH = os.path.join(_HERE, "libmrcg.so")
 
 OK, ERR_INVALID, ERR_NOT_SPD, ERR_BREAKDOWN, ERR_MAXITER, ERR_NONFINITE, ERR_CUDA, ERR_OOM = range(8)
 FP64, MIXED_FP32 = 0, 1
-MCG_IDENTITY, MCG_JACOBI, MCG_SMW = 0, 1, 2
+MCG_IDENTITY, MCG_JACOBI, MCG_SMW, MCG_ILU0, MCG_SMW_ILU0 = 0, 1, 2, 3, 4
 
 
 class CreateArgs(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("rowptr", C.c_void_p), ("colind", C.c_void_p),
                 ("val", C.c_void_p), ("k", C.c_int32), ("V", C.c_void_p), ("lambda_", C.c_void_p),
                 ("precision", C.c_int32), ("inner_prec", C.c_int32), ("validate", C.c_int32),
-                ("max_outer", C.c_int32), ("restart_factor", C.c_double), ("stream", C.c_void_p)]
+                ("max_outer", C.c_int32), ("restart_factor", C.c_double), ("stream", C.c_void_p),
+                ("ilu_block", C.c_int32), ("reserved", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -143,7 +144,7 @@ class MrcgError(RuntimeError):
 
 
 def solver_create(n, rowptr, colind, val, V=None, lam=None, precision=FP64, inner_prec=MCG_IDENTITY,
-                  validate=True, max_outer=0, restart_factor=0.0, stream=None) -> int:
+                  validate=True, max_outer=0, restart_factor=0.0, stream=None, ilu_block=0) -> int:
     """mrcg_solver_create.  V is n x k (row index = unknown); it is passed
     column-major.  Returns the opaque handle (int)."""
     _check_dtype(rowptr, np.int64, "rowptr"); _check_dtype(colind, np.int32, "colind")
@@ -164,7 +165,7 @@ def solver_create(n, rowptr, colind, val, V=None, lam=None, precision=FP64, inne
     rp, k1 = _ptr(rowptr); ci, k2 = _ptr(colind); va, k3 = _ptr(val)
     keep += [k1, k2, k3]
     a = CreateArgs(int(n), int(rowptr[-1]), rp, ci, va, k, Vp, lamp, int(precision), int(inner_prec),
-                   1 if validate else 0, int(max_outer), float(restart_factor), stream)
+                   1 if validate else 0, int(max_outer), float(restart_factor), stream, int(ilu_block), 0)
     h = C.c_void_p()
     st = lib().mrcg_solver_create(C.byref(a), C.byref(h))
     if st != OK:
@@ -358,7 +359,7 @@ def _create_args(n, rowptr, colind, val, V, lam, precision, inner_prec, validate
     rp, k1 = _ptr(rowptr); ci, k2 = _ptr(colind); va, k3 = _ptr(val)
     keep += [k1, k2, k3]
     return CreateArgs(int(n), int(rowptr[-1]), rp, ci, va, k, Vp, lamp, int(precision), int(inner_prec),
-                      1 if validate else 0, int(max_outer), float(restart_factor), stream)
+                      1 if validate else 0, int(max_outer), float(restart_factor), stream, 0, 0)
 
 
 def batch_create(problems, precision=FP64, inner_prec=MCG_IDENTITY, validate=True, max_outer=0,

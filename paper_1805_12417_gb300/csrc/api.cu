@@ -56,6 +56,7 @@ struct mrcg_solver {
   // inner-precision vectors
   void *iz = nullptr, *ir = nullptr, *is = nullptr, *ip0 = nullptr, *ip1 = nullptr, *iq = nullptr;
   void *ir2 = nullptr, *iq2 = nullptr;  // one-kernel iteration (M_cg = I): second r and q buffers
+  int64_t ilu_levels = 0;              // ILU(0) M_cg: forward + backward levels over all blocks
 
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -378,6 +379,67 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
     cudaFree(d64);
     h->d_dsmw = q;
   }
+  // ---- block-Jacobi ILU(0) M_cg: host factorisation with level scheduling, device copy
+  IluArgs ilu;
+  if (h->mcg == MRCG_MCG_ILU0 || h->mcg == MRCG_MCG_SMW_ILU0) {
+    const int cap = h->fp32 ? kIluMaxBlock : kIluMaxBlock / 2;  // a block's values in shared memory
+    int bs = a->ilu_block > 0 ? a->ilu_block : 8192;
+    if (bs % 32 != 0 || bs > cap) return MRCG_ERR_INVALID;
+    bs = (int)std::min<int64_t>(bs, n_pad);
+    IluHost fh;
+    ST(ilu0_build(n, n_pad, rp, ci, va, bs, fh));
+    if (fh.fent.back() < 0 || fh.bent.back() < 0) return MRCG_ERR_INVALID;  // entry offsets beyond int32
+    auto up_i32 = [&](const std::vector<int32_t>& v, const int32_t** dst) -> mrcg_status {
+      int32_t* d = nullptr;
+      ST(dalloc(h, &d, v.size()));
+      CK(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+      *dst = d;
+      return MRCG_OK;
+    };
+    auto up_u16 = [&](const std::vector<uint16_t>& v, const uint16_t** dst) -> mrcg_status {
+      uint16_t* d = nullptr;
+      ST(dalloc(h, &d, v.size()));
+      if (!v.empty()) CK(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, h->stream));
+      *dst = d;
+      return MRCG_OK;
+    };
+    auto up_val = [&](const std::vector<double>& v, const void** dst) -> mrcg_status {
+      if (h->fp32) {
+        std::vector<float> f(v.begin(), v.end());
+        float* d = nullptr;
+        ST(dalloc(h, &d, f.size()));
+        if (!f.empty()) CK(cudaMemcpyAsync(d, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+        CK(cudaStreamSynchronize(h->stream));  // f is a temporary
+        *dst = d;
+      } else {
+        double* d = nullptr;
+        ST(dalloc(h, &d, v.size()));
+        if (!v.empty()) CK(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        *dst = d;
+      }
+      return MRCG_OK;
+    };
+    ST(up_i32(fh.fblk, &ilu.fblk));
+    ST(up_i32(fh.flvl, &ilu.flvl));
+    ST(up_i32(fh.frow, &ilu.frow));
+    ST(up_i32(fh.fent, &ilu.fent));
+    ST(up_u16(fh.fcol, &ilu.fcol));
+    ST(up_val(fh.fval, &ilu.fval));
+    ST(up_i32(fh.bblk, &ilu.bblk));
+    ST(up_i32(fh.blvl, &ilu.blvl));
+    ST(up_i32(fh.brow, &ilu.brow));
+    ST(up_i32(fh.bent, &ilu.bent));
+    ST(up_u16(fh.bcol, &ilu.bcol));
+    ST(up_val(fh.bval, &ilu.bval));
+    ST(up_val(fh.bdinv, &ilu.bdinv));
+    CK(cudaStreamSynchronize(h->stream));  // the host vectors go out of scope
+    ilu.nblk = fh.nblk;
+    ilu.bs = fh.bs;
+    const size_t per_warp = (size_t)bs * (h->fp32 ? sizeof(float) : sizeof(double));
+    ilu.wpc = (int)std::max<size_t>(1, std::min<size_t>(kThreads / 32, (size_t)(200 * 1024) / per_warp));
+    ilu.smw = h->mcg == MRCG_MCG_SMW_ILU0 ? 1 : 0;
+    h->ilu_levels = fh.levels_f + fh.levels_b;
+  }
   CK(cudaStreamSynchronize(h->stream));
   cudaFree(t_rp);
   cudaFree(t_ci);
@@ -416,6 +478,7 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
   g.k = a->k;
   g.dinv = h->d_dinv;
   g.dsmw = h->d_dsmw;
+  g.ilu = ilu;
   if (a->k > 0) {
     ST(dalloc(h, &h->d_gram, (size_t)a->k * a->k));
     CK(launch_gram(g, h->stream, h->d_gram));
@@ -711,7 +774,7 @@ mrcg_status solve_impl(mrcg_solver* h, const double* ub, double* ux, double oute
     info->prec_calls = h->h_st->out.prec_calls;
     // per inner solve: norm, init (two passes for MINRES-CG*), finish; per body
     // of the while loop: U iterations of one or two kernels, then the control kernel
-    const long long per_graph = 3 + (h->mcg == MRCG_MCG_SMW ? 1 : 0);
+    const long long per_graph = 3 + (h->mcg == MRCG_MCG_SMW || h->mcg == MRCG_MCG_ILU0 || h->mcg == MRCG_MCG_SMW_ILU0 ? 1 : 0);
     const long long per_body = (h->spec.var_a == 8 ? 1LL : 2LL) * h->unroll + 1;
     info->kernel_launches = launches + per_graph * graphs + h->h_st->out.bodies * per_body;
     info->true_relres = relres;
@@ -744,8 +807,7 @@ mrcg_status mrcg_solver_create(const mrcg_create_args* a, mrcg_handle* out) {
   *out = nullptr;
   if (a->n < 1 || a->n > (int64_t)0x7fffff00 || a->nnz < 0 || a->k < 0 || a->k > kMaxK) return MRCG_ERR_INVALID;
   if (a->precision != MRCG_FP64 && a->precision != MRCG_MIXED_FP32) return MRCG_ERR_INVALID;
-  if (a->inner_prec != MRCG_MCG_IDENTITY && a->inner_prec != MRCG_MCG_JACOBI && a->inner_prec != MRCG_MCG_SMW)
-    return MRCG_ERR_INVALID;
+  if (a->inner_prec < MRCG_MCG_IDENTITY || a->inner_prec > MRCG_MCG_SMW_ILU0) return MRCG_ERR_INVALID;
   if (!a->rowptr || (a->nnz > 0 && (!a->colind || !a->val))) return MRCG_ERR_INVALID;
   if (a->k > 0 && (!a->V || !a->lambda)) return MRCG_ERR_INVALID;
   if (std::isnan(a->restart_factor)) return MRCG_ERR_INVALID;
@@ -897,14 +959,19 @@ mrcg_status mrcg_time_inner_graph(mrcg_handle h, int32_t iters, double* ms_per_i
   const long long base = 2LL * h->unroll;
   float t_short = 0.f, t_long = 0.f, unused = 0.f;
   long long r0 = 0, r1 = 0, r2 = 0;
-  mrcg_status st = timed(base, &unused, &r0);  // warm-up
+  // warm-up and probe: with no tolerance to stop it, an FP32 recursion that
+  // has reached its rounding floor can end on its own (p^T q <= 0); the long
+  // run then keeps to three quarters of the iterations the probe reached
+  mrcg_status st = timed(base + iters, &unused, &r0);
+  long long n_long = base + iters;
+  if (st == MRCG_OK && r0 < n_long) n_long = std::max(base + 8, r0 * 3 / 4);
   // the difference of two solves cancels the per-solve kernels (norm, init, finish)
   if (st == MRCG_OK) st = timed(base, &t_short, &r1);
-  if (st == MRCG_OK) st = timed(base + iters, &t_long, &r2);
+  if (st == MRCG_OK) st = timed(n_long, &t_long, &r2);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != MRCG_OK) return st;
-  if (r2 - r1 < iters / 2) return MRCG_ERR_BREAKDOWN;  // the recursion stopped early: no steady state to time
+  if (r2 - r1 < 8) return MRCG_ERR_BREAKDOWN;  // the recursion stops too early: no steady state to time
   *ms_per_iter = (double)(t_long - t_short) / (double)(r2 - r1);
   return MRCG_OK;
 }

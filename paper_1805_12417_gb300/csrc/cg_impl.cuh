@@ -423,6 +423,145 @@ __global__ void __launch_bounds__(kThreads) cg_step_b_smw_kernel(CgArgs<T> a) {
   }
 }
 
+// ------------------------------------------------------------------ step b with the block-Jacobi ILU(0) M_cg
+//
+// The inner preconditioner of the paper's experiments (Sec. 4) is an
+// incomplete LU factorisation of A; here its block-Jacobi form (ilu.cu): the
+// factors of A's diagonal blocks of bs consecutive rows.  One warp owns a
+// block: it applies the CG updates z += alpha p', r -= alpha q to the block's
+// rows, solves L U s = r by a forward and a backward sweep over the block's
+// levels with the block's values of r / s in shared memory (a warp barrier
+// between levels), and stores s with the partials r^T s, r^T r and
+// V^T (L U)^{-1} r.  V^T s is then direct (no recurrence): with M_cg^{-1} not
+// diagonal, step a cannot form its share row by row.  With f.smw (MINRES-CG*,
+// Sec. 2.1, Atilde = L U) s = (L U)^{-1} r + V e, e = -2 Lambda^{-1} V^T r,
+// with V^T r by its recurrence and V^T s = V^T (L U)^{-1} r + (V^T V) e as in
+// the diag(A) form.  init = 1: the first residual (alpha = 0) and start_cg.
+// Launched with kThreads threads per CTA; warps 0 .. f.wpc-1 own blocks
+// blockIdx.x * f.wpc + warp, the others only join the reduction.
+template <typename T, int KB>
+__global__ void __launch_bounds__(kThreads) cg_step_b_ilu_kernel(CgArgs<T> a, IluArgs f, int init) {
+  constexpr int KS = KB > 0 ? KB : 1;
+  extern __shared__ __align__(16) unsigned char ilu_smem[];
+  CgState& S = a.st->cg;
+  if (!init && S.done != kRunning) return;
+  const T alpha = init ? (T)0 : alpha_of(S, T(0));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ double vr_new[KS];
+  __shared__ T es[KS];
+  if (f.smw) {
+    if ((int)threadIdx.x < KS)
+      vr_new[threadIdx.x] = ((int)threadIdx.x < a.k)
+                                ? (init ? S.vr[threadIdx.x] : S.vr[threadIdx.x] - S.alpha * S.vq[threadIdx.x])
+                                : 0.0;
+    __syncthreads();
+    smw_coeffs<T, KS>(S, vr_new, a.k, es);
+  }
+  T rs = 0, rr = 0;
+  T wd[KS];
+#pragma unroll
+  for (int l = 0; l < KS; ++l) wd[l] = 0;
+  const int blk = blockIdx.x * f.wpc + warp;
+  if (warp < f.wpc && blk < f.nblk) {
+    T* x = reinterpret_cast<T*>(ilu_smem) + (size_t)warp * f.bs;
+    const int64_t b0 = (int64_t)blk * f.bs;
+    const int m = (int)min((int64_t)f.bs, a.n_pad - b0);
+    // CG updates of the block's rows; x = r, the right-hand side of the solve
+    for (int r = lane; r < m; r += 32) {
+      const int64_t i = b0 + r;
+      T rv = a.r[i];
+      if (!init) {
+        a.z[i] = a.z[i] + alpha * a.p_new[i];
+        rv -= alpha * a.q[i];
+        a.r[i] = rv;
+      }
+      x[r] = rv;
+    }
+    __syncwarp();
+    const T* fval = reinterpret_cast<const T*>(f.fval);
+    for (int lv = f.fblk[blk]; lv < f.fblk[blk + 1]; ++lv) {  // L y = r (unit diagonal)
+      for (int pos = f.flvl[lv] + lane; pos < f.flvl[lv + 1]; pos += 32) {
+        const int row = f.frow[pos];
+        T acc = x[row];
+        for (int e = f.fent[pos]; e < f.fent[pos + 1]; ++e) acc -= fval[e] * x[f.fcol[e]];
+        x[row] = acc;
+      }
+      __syncwarp();
+    }
+    const T* bval = reinterpret_cast<const T*>(f.bval);
+    const T* bdinv = reinterpret_cast<const T*>(f.bdinv);
+    for (int lv = f.bblk[blk]; lv < f.bblk[blk + 1]; ++lv) {  // U s = y
+      for (int pos = f.blvl[lv] + lane; pos < f.blvl[lv + 1]; pos += 32) {
+        const int row = f.brow[pos];
+        T acc = x[row];
+        for (int e = f.bent[pos]; e < f.bent[pos + 1]; ++e) acc -= bval[e] * x[f.bcol[e]];
+        x[row] = acc * bdinv[pos];
+      }
+      __syncwarp();
+    }
+    for (int r = lane; r < m; r += 32) {  // each lane rereads the residual rows it wrote itself
+      const int64_t i = b0 + r;
+      const T rv = a.r[i];
+      const T xr = x[r];
+      T sv = xr;
+#pragma unroll
+      for (int l = 0; l < KB; ++l)
+        if (l < a.k) {
+          const T v = a.V[(size_t)l * a.n_pad + i];
+          wd[l] += v * xr;
+          if (f.smw) sv += v * es[l];
+        }
+      a.s[i] = sv;
+      rs += rv * sv;
+      rr += rv * rv;
+    }
+  }
+  T acc[KB + 2];
+  pack_slots<T, KB>(acc, rs, wd, rr, a.k, true);
+  const int nv = a.k + 2;
+  block_partials_t<T, KB + 2>(acc, nv, a.partials);
+  if (last_block_after_partials(&a.st->ticket)) {
+    __shared__ double tot[KB + 2];
+    __shared__ double ed[KS];
+    final_sums(a.partials, nv, tot);
+    if (f.smw) {
+      if ((int)threadIdx.x < a.k) {
+        S.vr[threadIdx.x] = vr_new[threadIdx.x];
+        ed[threadIdx.x] = 4.0 * vr_new[threadIdx.x] / S.lam2[threadIdx.x];
+      }
+      __syncthreads();
+      smw_u(S, a.gram, tot, a.k, ed);
+    } else if ((int)threadIdx.x < a.k) {
+      S.u[threadIdx.x] = tot[threadIdx.x + 1];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const double rho_new = tot[0], rnorm = sqrt(tot[a.k + 1]);
+      if (init) {
+        start_cg(S, a.k, S.vnorm, rho_new, rnorm);
+      } else {
+        S.iters += 1;
+        if (!isfinite(rho_new) || !isfinite(rnorm)) {
+          S.done = kNonFinite;
+        } else if (rnorm <= S.tol_abs) {
+          S.done = kConverged;
+        } else if (S.iters >= S.maxit) {
+          S.done = kMaxIter;
+        } else if (rho_new == 0.0) {
+          S.done = kBreakdown;
+        } else {
+          const double beta = rho_new / S.rho;
+          S.beta = beta;
+          S.beta32 = (float)beta;
+          S.rho = rho_new;
+          for (int l = 0; l < a.k; ++l) S.t[l] = S.u[l] + beta * S.t[l];
+          publish_c(S, a.k);
+        }
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------ step a
 
 // The entries of one slice row, 8 at a time: all value / index loads of a
@@ -1832,7 +1971,7 @@ void make_args(const InnerGraphSpec& spec, CgArgs<T> (&a)[2]) {
     x.gram = spec.gram;
     x.z = reinterpret_cast<T*>(spec.z);
     x.r = reinterpret_cast<T*>(spec.r);
-    x.s = (spec.dinv || spec.dsmw) ? reinterpret_cast<T*>(spec.s) : reinterpret_cast<T*>(spec.r);
+    x.s = (spec.dinv || spec.dsmw || spec.ilu.nblk > 0) ? reinterpret_cast<T*>(spec.s) : reinterpret_cast<T*>(spec.r);
     x.q = reinterpret_cast<T*>(spec.q);
     x.p_old = reinterpret_cast<T*>(par == 0 ? spec.p0 : spec.p1);
     x.p_new = reinterpret_cast<T*>(par == 0 ? spec.p1 : spec.p0);
@@ -1909,8 +2048,25 @@ const void* step_b_fn(const InnerGraphSpec& spec) {
   return spec.dsmw ? (const void*)cg_step_b_smw_kernel<T, KB> : (const void*)cg_step_b_kernel<T, KB>;
 }
 
+// the ILU step b: grid, dynamic shared memory (one block's values per owning warp)
+inline int ilu_grid(const InnerGraphSpec& spec) { return (spec.ilu.nblk + spec.ilu.wpc - 1) / spec.ilu.wpc; }
+template <typename T>
+unsigned ilu_smem(const InnerGraphSpec& spec) {
+  return (unsigned)((size_t)spec.ilu.wpc * spec.ilu.bs * sizeof(T));
+}
+
 template <typename T, int KB>
 void launch_b(const InnerGraphSpec& spec, cudaStream_t stream, CgArgs<T>& a) {
+  if (spec.ilu.nblk > 0) {
+    cudaFuncSetAttribute((const void*)cg_step_b_ilu_kernel<T, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)ilu_smem<T>(spec));
+    IluArgs f = spec.ilu;
+    int init = 0;
+    void* args[] = {&a, &f, &init};
+    cudaLaunchKernel((const void*)cg_step_b_ilu_kernel<T, KB>, dim3(ilu_grid(spec)), dim3(kThreads), args,
+                     ilu_smem<T>(spec), stream);
+    return;
+  }
   void* args[] = {&a};
   cudaLaunchKernel(step_b_fn<T, KB>(spec), dim3(spec.grid_stream_b), dim3(kThreads), args, 0, stream);
 }
@@ -1918,6 +2074,17 @@ void launch_b(const InnerGraphSpec& spec, cudaStream_t stream, CgArgs<T>& a) {
 // the first residual and its preconditioned form (two passes for the MINRES-CG* M_cg)
 template <typename T, int KB>
 void launch_init(const InnerGraphSpec& spec, cudaStream_t stream, CgArgs<T>& a) {
+  if (spec.ilu.nblk > 0) {
+    cudaFuncSetAttribute((const void*)cg_step_b_ilu_kernel<T, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)ilu_smem<T>(spec));
+    cg_init_smw_vr_kernel<T, KB><<<spec.grid_stream, kThreads, 0, stream>>>(a);
+    IluArgs f = spec.ilu;
+    int init = 1;
+    void* args[] = {&a, &f, &init};
+    cudaLaunchKernel((const void*)cg_step_b_ilu_kernel<T, KB>, dim3(ilu_grid(spec)), dim3(kThreads), args,
+                     ilu_smem<T>(spec), stream);
+    return;
+  }
   if (spec.dsmw) {
     cg_init_smw_vr_kernel<T, KB><<<spec.grid_stream, kThreads, 0, stream>>>(a);
     cg_init_smw_kernel<T, KB><<<spec.grid_stream, kThreads, 0, stream>>>(a);
@@ -1938,6 +2105,12 @@ cudaError_t build_graph_t(const InnerGraphSpec& spec, cudaGraph_t* out_graph) {
   int64_t n_pad = spec.A.n_pad;
   const T* zc = reinterpret_cast<const T*>(spec.z);
   const unsigned smem_a = step_a_smem<T, KB>(spec);
+  IluArgs ilu_f = spec.ilu;
+  int ilu_init1 = 1, ilu_init0 = 0;
+  const unsigned smem_ilu = spec.ilu.nblk > 0 ? ilu_smem<T>(spec) : 0;
+  if (spec.ilu.nblk > 0)
+    cudaFuncSetAttribute((const void*)cg_step_b_ilu_kernel<T, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem_ilu);
 
   cudaGraphNode_t n_norm, n_init, n_loop, n_fin;
   void* norm_args[] = {&st, &partials, &n_pad};
@@ -1945,7 +2118,16 @@ cudaError_t build_graph_t(const InnerGraphSpec& spec, cudaGraph_t* out_graph) {
     goto fail;
   {
     void* init_args[] = {&a[0]};
-    if (spec.dsmw) {
+    if (spec.ilu.nblk > 0) {
+      cudaGraphNode_t n_vr;
+      void* ilu_args[] = {&a[0], &ilu_f, &ilu_init1};
+      if ((e = add_kernel(g, &n_vr, &n_norm, 1, (const void*)cg_init_smw_vr_kernel<T, KB>, spec.grid_stream,
+                          kThreads, init_args)))
+        goto fail;
+      if ((e = add_kernel(g, &n_init, &n_vr, 1, (const void*)cg_step_b_ilu_kernel<T, KB>, ilu_grid(spec), kThreads,
+                          ilu_args, smem_ilu)))
+        goto fail;
+    } else if (spec.dsmw) {
       cudaGraphNode_t n_vr;
       if ((e = add_kernel(g, &n_vr, &n_norm, 1, (const void*)cg_init_smw_vr_kernel<T, KB>, spec.grid_stream,
                           kThreads, init_args)))
@@ -1979,9 +2161,15 @@ cudaError_t build_graph_t(const InnerGraphSpec& spec, cudaGraph_t* out_graph) {
         prev = na;
         continue;
       }
-      if ((e = add_kernel(body, &nb, &na, 1, step_b_fn<T, KB>(spec), spec.grid_stream_b, kThreads,
-                          aa)))
+      if (spec.ilu.nblk > 0) {
+        void* ba[] = {&a[it & 1], &ilu_f, &ilu_init0};
+        if ((e = add_kernel(body, &nb, &na, 1, (const void*)cg_step_b_ilu_kernel<T, KB>, ilu_grid(spec), kThreads,
+                            ba, smem_ilu)))
+          goto fail;
+      } else if ((e = add_kernel(body, &nb, &na, 1, step_b_fn<T, KB>(spec), spec.grid_stream_b, kThreads,
+                                 aa))) {
         goto fail;
+      }
       prev = nb;
     }
     cudaGraphNode_t nc;

@@ -45,8 +45,8 @@ void inner_occupancy(const InnerGraphSpec& s, int* spmv_blocks_per_sm, int* stre
   *spmv_blocks_per_sm = 1;
   *stream_blocks_per_sm = 1;
   if ((is_staged_variant(s.var_a) && staged_smem_bytes(s) == 0) ||
-      (s.var_a == 8 && (s.dinv || s.dsmw || !s.r2 || !s.q2)) ||  // the one-kernel iteration needs M_cg = I
-      (is_pg_variant(s.var_a) && s.dsmw)) {  // variants 9-11: M_cg = I or Jacobi
+      (s.var_a == 8 && (s.dinv || s.dsmw || s.ilu.nblk > 0 || !s.r2 || !s.q2)) ||  // one kernel: M_cg = I only
+      (is_pg_variant(s.var_a) && (s.dsmw || s.ilu.nblk > 0))) {  // variants 9-13: M_cg = I or Jacobi
     *spmv_blocks_per_sm = 0;
     return;
   }

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "ilu.h"
 
 namespace mrcg {
 
@@ -37,6 +38,7 @@ struct InnerGraphSpec {
                  // 9 / 10: staged as 5 / 6 and 11: plain, all three with one gather per
                  // matrix entry (p explicit, beta by expansion in step a; M_cg = I or Jacobi);
                  // 12 / 13: 9 / 10 with each warp's gathers issued one tile ahead)
+  IluArgs ilu;               // block-Jacobi ILU(0) M_cg (ilu.nblk > 0): step b solves with the factors
   int64_t tile_entries = 0;  // most SELL entries in one tile of 8 slices (sizes the staged variant's buffers)
   int stages = 3;            // staged variant: shared-memory stages per block
   bool stall_test = false;   // test hook: the staged producer issues only the first tile

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from gen import (batch64_lap2d, lap2d_64_k4, dense_to_csr, laplacian_csr, laplacian_smallest_eigs,
+from gen import (batch64_lap2d, lap2d_64_k4, dense_to_csr, laplacian_csr, laplacian_smallest_eigs, random_sparse_symmetric,
                  random_indefinite_dense, shifted_family, shifted_laplacian_problem)
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -637,3 +637,117 @@ def test_dense_negative_eigenpairs_match_laplacian_spectrum_and_inertia():
     q = small_saddle()
     V2, lam2, _ = O.negative_eigenpairs_dense(q.rowptr, q.colind, q.val)
     assert len(lam2) == q.k  # nb constraint rows: Sylvester's law of inertia
+
+
+# ---------------------------------------------------------------- ILU(0) inner preconditioner (Sec. 4)
+
+def _dense(rp, ci, va):
+    n = len(rp) - 1
+    A = np.zeros((n, n))
+    for i in range(n):
+        A[i, ci[rp[i]:rp[i + 1]]] = va[rp[i]:rp[i + 1]]
+    return A
+
+
+def test_ilu0_of_a_tridiagonal_matrix_is_its_exact_lu():
+    """Tridiagonal A (indefinite, nonzero pivots): ILU(0) has no fill to drop,
+    so L U = A and the preconditioner is A^{-1}."""
+    rp, ci, va = laplacian_csr((31,), sigma=0.37)
+    A = _dense(rp, ci, va)
+    s = O.System(rp, ci, va)
+    assert s.set_ilu0() == O.OK
+    L, U = s.ilu0_factors()
+    assert np.allclose(L @ U, A, atol=1e-13)
+    r = np.random.default_rng(1).standard_normal(31)
+    assert np.allclose(s.ilu0_apply(r), np.linalg.solve(A, r), atol=1e-10)
+
+
+def test_ilu0_matches_a_on_its_pattern_and_solves_triangularly():
+    """General sparse pattern: L is unit lower and U upper triangular on A's
+    pattern, (L U)_ij = a_ij wherever a_ij is stored (the defining property of
+    ILU(0)), fill outside the pattern is dropped, and the preconditioner is the
+    two triangular solves (scipy's solve_triangular)."""
+    from scipy.linalg import solve_triangular
+    rp, ci, va = random_sparse_symmetric(60, 5, density_rows=(2, 9), diag_shift=6.0, empty_rows=0)
+    A = _dense(rp, ci, va)
+    pattern = A != 0
+    s = O.System(rp, ci, va)
+    assert s.set_ilu0() == O.OK
+    L, U = s.ilu0_factors()
+    assert np.allclose(np.diag(L), 1.0) and np.allclose(np.triu(L, 1), 0) and np.allclose(np.tril(U, -1), 0)
+    assert not np.any((L - np.eye(60) != 0) & ~pattern) and not np.any((U != 0) & ~pattern)
+    LU = L @ U
+    assert np.allclose(LU[pattern], A[pattern], atol=1e-12)
+    assert np.abs(LU[~pattern]).max() > 1e-3  # fill was dropped, so L U is not A
+    r = np.random.default_rng(2).standard_normal(60)
+    ref = solve_triangular(U, solve_triangular(L, r, lower=True, unit_diagonal=True), lower=False)
+    assert np.allclose(s.ilu0_apply(r), ref, atol=1e-12)
+
+
+def test_block_jacobi_ilu0_factors_each_diagonal_block():
+    """Blocks of b rows: M = L U is block diagonal, and each block is the
+    ILU(0) of A's diagonal block factored on its own (couplings between
+    blocks dropped)."""
+    rp, ci, va = laplacian_csr((7, 6), sigma=0.5)
+    A = _dense(rp, ci, va)
+    n, b = 42, 8
+    s = O.System(rp, ci, va)
+    assert s.set_ilu0(b) == O.OK
+    L, U = s.ilu0_factors()
+    M = L @ U
+    for i0 in range(0, n, b):
+        i1 = min(i0 + b, n)
+        Ab = A[i0:i1, i0:i1]
+        sb = O.System(*dense_to_csr(Ab))
+        assert sb.set_ilu0() == O.OK
+        Lb, Ub = sb.ilu0_factors()
+        assert np.allclose(M[i0:i1, i0:i1], Lb @ Ub, atol=1e-13)
+        M[i0:i1, i0:i1] = 0.0
+    assert np.allclose(M, 0.0)
+
+
+def test_ilu0_zero_pivot_is_a_breakdown():
+    A = np.array([[0.0, 1.0], [1.0, 2.0]])
+    s = O.System(*dense_to_csr(A))
+    assert s.set_ilu0() == O.ERR_BREAKDOWN
+
+
+@pytest.mark.parametrize("mcg", [O.MCG_ILU0, O.MCG_SMW_ILU0], ids=["ilu0", "smw_ilu0"])
+def test_ilu_cg_iterates_are_galerkin(mcg):
+    """CG on M_mr with P = M_cg^{-1} (ILU(0), or the MINRES-CG* form with
+    Atilde = ILU(0)): iterates are the M_mr-energy best points of
+    K_m(P M_mr, P y) -- P is symmetric here because A is (U = D L^T)."""
+    A, Vn, lam, d, Q, s0 = dense_system(30, 3, 31)
+    A = A + 0.0  # dense symmetric, every pivot nonzero for this seed
+    rp, ci, va = dense_to_csr(A)
+    s = O.System(rp, ci, va, Vn, lam)
+    assert s.set_ilu0() == O.OK
+    M = dense_op(s.mmr_apply, 30)
+    P = dense_op(lambda r: s.mcg_apply(r, mcg)[0], 30)
+    assert np.allclose(P, P.T, atol=1e-9 * np.abs(P).max())
+    y = np.random.default_rng(3).standard_normal(30)
+    for m_it in range(1, 6):
+        z, it, st = s.cg(y, 1e-300, m_it, mcg)
+        assert it == m_it
+        vecs = [P @ y]
+        for _ in range(m_it - 1):
+            vecs.append(P @ (M @ vecs[-1]))
+        K, _ = np.linalg.qr(np.column_stack(vecs))
+        zg = K @ np.linalg.solve(K.T @ M @ K, K.T @ y)
+        assert np.allclose(z, zg, rtol=0, atol=1e-8 * np.linalg.norm(zg))
+
+
+def test_ilu0_cuts_inner_iterations_on_a_laplacian():
+    """On a shifted 2D Laplacian the ILU(0) inner preconditioner (one block)
+    needs fewer CG iterations than M_cg = I to the same tolerance, and
+    MINRES-CG with it reaches x*."""
+    p = shifted_laplacian_problem("ilu_lap", (30, 29), 5, seed=7)
+    s = O.System.from_problem(p)
+    assert s.set_ilu0() == O.OK
+    y = np.random.default_rng(4).standard_normal(p.n)
+    _, it_id, st_id = s.cg(y, 1e-6, 10000, O.MCG_IDENTITY)
+    _, it_ilu, st_ilu = s.cg(y, 1e-6, 10000, O.MCG_ILU0)
+    assert st_id == st_ilu == O.OK and it_ilu < it_id
+    r = O.minres_cg(s, p.b, outer_tol=1e-12, inner_tol=1e-3, mcg=O.MCG_ILU0)
+    assert r.status == O.OK
+    assert np.linalg.norm(r.x - p.xstar) / np.linalg.norm(p.xstar) <= 1e-8
