@@ -569,6 +569,8 @@ def measure_batch(torch, m, ps, dev, stream, ws, local, rank, steps, warmup, clo
     out = {}
     for name, prec in (("mixed", m.MIXED_FP32), ("fp64", m.FP64)):
         with m.Batch(ps, precision=prec, validate=False, stream=stream.cuda_stream) as bt:
+            shape = m.batch_launch_config(bt.h)
+
             def step():
                 Xd.zero_()
                 return bt.solve(Bd, Xd, outer_tol=OUTER_TOL, inner_tol=INNER_TOL)[2]
@@ -585,7 +587,7 @@ def measure_batch(torch, m, ps, dev, stream, ws, local, rank, steps, warmup, clo
                          "inner_gbs": byts / (ms / steps * 1e-3) / 1e9, "launches": infos[0].kernel_launches,
                          "inner_iters_max": max(i.inner_iters_total for i in infos),
                          "outer_iters_max": max(i.outer_iters for i in infos),
-                         "max_true_relres": max(i.true_relres for i in infos)}
+                         "max_true_relres": max(i.true_relres for i in infos), "launch_config": shape}
             if ck is not None:
                 out[name]["clocks"] = ck
             if name == "mixed" and e2e:
@@ -642,6 +644,8 @@ def measure_shifted(torch, m, fam, dev, stream, ws, local, rank, precision, step
     Xd = torch.zeros_like(Bd)
     n, nc = fam.n, fam.ncols
     with m.Shifted(fam, precision=precision, stream=stream.cuda_stream) as sh:
+        shape = m.shifted_launch_config(sh.h)
+
         def step():
             Xd.zero_()
             return sh.solve(Bd, Xd, outer_tol=OUTER_TOL, inner_tol=INNER_TOL)[2]
@@ -661,7 +665,8 @@ def measure_shifted(torch, m, fam, dev, stream, ws, local, rank, precision, step
            "columns": nc, "inner_gbs": byts / (ms / steps * 1e-3) / 1e9, "launches": infos[0].kernel_launches,
            "inner_iters_max": iters, "inner_iters_per_column": [i.inner_iters_total for i in infos],
            "outer_iters_max": max(i.outer_iters for i in infos),
-           "max_true_relres": max(i.true_relres for i in infos), "max_rel_err_vs_xstar": err}
+           "max_true_relres": max(i.true_relres for i in infos), "max_rel_err_vs_xstar": err,
+           "launch_config": shape}
     if ck is not None:
         out["clocks"] = ck
     return out, xh

@@ -332,11 +332,13 @@ class ShiftedFamily:
 
     def subfamily(self, shifts) -> "ShiftedFamily":
         """The family restricted to the listed shifts (their columns, in order;
-        L, V and lamL shared)."""
+        L shared, V and lamL cut to the largest k_j kept)."""
         shifts = [int(j) for j in shifts]
         cols = [j * self.nrhs + r for j in shifts for r in range(self.nrhs)]
+        kmax = max(int(self.k[j]) for j in shifts)  # V and lamL trimmed to the widest shift kept
         return ShiftedFamily(f"{self.name}_shifts{'_'.join(map(str, shifts))}", self.dims, self.n, self.rowptr,
-                             self.colind, self.val, self.V, self.lamL, self.sigma[shifts].copy(),
+                             self.colind, self.val, np.ascontiguousarray(self.V[:, :kmax]), self.lamL[:kmax].copy(),
+                             self.sigma[shifts].copy(),
                              self.k[shifts].copy(), self.nrhs, np.ascontiguousarray(self.B[:, cols]),
                              np.ascontiguousarray(self.xstar[:, cols]))
 

@@ -27,8 +27,12 @@
  *
  * Environment variables, read when a handle is created (none is needed; the
  * defaults are the tuned path):
- *  - MRCG_AUTOTUNE=0      skip the launch-shape autotuner of mrcg_solver_create
- *                         (it runs for n_pad >= 4096) and keep the default shape.
+ *  - MRCG_AUTOTUNE=0      skip the launch-shape autotuners and keep the default
+ *                         shapes (mrcg_solver_create tunes for n_pad >= 4096,
+ *                         mrcg_batch_create for 2^20 rows or more,
+ *                         mrcg_shifted_create for n x columns >= 2^22);
+ *                         MRCG_AUTOTUNE=2 tunes batches and shifted families of
+ *                         any size.
  *  - MRCG_SHAPE_F32 / MRCG_SHAPE_F64 = "variant,stages,grid_a,grid_b"
  *                         replay a shape reported by mrcg_launch_config (for
  *                         profilers, whose slowed launches mislead the tuner);
@@ -265,6 +269,13 @@ mrcg_status mrcg_batched_solve(mrcg_batch_handle h, const double* B, double* X, 
 /* Number of systems in the batch (0 for NULL). */
 int32_t mrcg_batch_size(mrcg_batch_handle h);
 
+/* Launch shape of the batch engine, chosen at create by timing calibration
+ * solves on the batch itself (unless MRCG_AUTOTUNE=0, or the batch holds
+ * fewer than 2^20 rows): cfg[0] rows per chunk (the unit one block reduces
+ * and a converged system skips: 1024, 2048, 4096 or 8192), cfg[1] step-a
+ * grid, cfg[2] step-b grid, cfg[3] chunks.  cfg must hold 4 values. */
+mrcg_status mrcg_batch_launch_config(mrcg_batch_handle h, int32_t* cfg);
+
 /* Release a batch (NULL is a no-op). */
 void mrcg_batch_destroy(mrcg_batch_handle h);
 
@@ -301,6 +312,15 @@ mrcg_status mrcg_shifted_solve(mrcg_shifted_handle h, const double* B, double* X
 
 /* Number of columns (nshift * nrhs_per_shift; 0 for NULL). */
 int32_t mrcg_shifted_columns(mrcg_shifted_handle h);
+
+/* Launch shape of the shifted-family engine, chosen at create by timing
+ * calibration solves on the handle's own matrix (unless MRCG_AUTOTUNE=0, or
+ * the blocks hold fewer than 2^22 values): cfg[0] row-kernel grid (blocks),
+ * cfg[1] blocks per SM (0: the occupancy limit, untuned), cfg[2] 1 when the
+ * SpMV takes four rows of at most 8 entries per warp (ELL-8), 0 for one row
+ * per warp (CSR), cfg[3] V_hat width bucket (8, 16, 24, 32), cfg[4] padded
+ * columns (32 or 64).  cfg must hold 5 values. */
+mrcg_status mrcg_shifted_launch_config(mrcg_shifted_handle h, int32_t* cfg);
 
 /* Release a shifted-family handle (NULL is a no-op). */
 void mrcg_shifted_destroy(mrcg_shifted_handle h);

@@ -85,6 +85,8 @@ def lib() -> C.CDLL:
         L.mrcg_batched_solve.restype = C.c_int
         L.mrcg_batch_size.argtypes = [P]
         L.mrcg_batch_size.restype = C.c_int32
+        L.mrcg_batch_launch_config.argtypes = [P, P]
+        L.mrcg_batch_launch_config.restype = C.c_int
         L.mrcg_batch_destroy.argtypes = [P]
         L.mrcg_batch_destroy.restype = None
         L.mrcg_shifted_create.argtypes = [C.POINTER(CreateArgs), C.c_int32, P, P, C.c_int32,
@@ -94,6 +96,8 @@ def lib() -> C.CDLL:
         L.mrcg_shifted_solve.restype = C.c_int
         L.mrcg_shifted_columns.argtypes = [P]
         L.mrcg_shifted_columns.restype = C.c_int32
+        L.mrcg_shifted_launch_config.argtypes = [P, P]
+        L.mrcg_shifted_launch_config.restype = C.c_int
         L.mrcg_shifted_destroy.argtypes = [P]
         L.mrcg_shifted_destroy.restype = None
         L.mrcg_solver_destroy.argtypes = [P]
@@ -395,6 +399,15 @@ def batched_solve(h, B, X, outer_tol=1e-10, inner_tol=1e-3, max_iters=0, history
     return st, out
 
 
+def batch_launch_config(h):
+    """mrcg_batch_launch_config: the autotuned launch shape of a batch handle."""
+    cfg = np.zeros(4, dtype=np.int32)
+    st = lib().mrcg_batch_launch_config(h, cfg.ctypes.data)
+    if st != OK:
+        raise MrcgError(st, "mrcg_batch_launch_config")
+    return {"chunk_rows": int(cfg[0]), "step_a_grid": int(cfg[1]), "step_b_grid": int(cfg[2]), "chunks": int(cfg[3])}
+
+
 class Batch:
     """Owning wrapper of one batch handle; vectors are concatenated in system order."""
 
@@ -466,6 +479,16 @@ def shifted_solve(h, B, X, outer_tol=1e-10, inner_tol=1e-3, max_iters=0, history
     out = [SolveInfo(f.status, f.outer_iters, f.restarts, f.inner_iters_total, f.prec_calls, f.kernel_launches,
                      f.true_relres, f.solve_ms, hists[i][: f.history_len].copy()) for i, f in enumerate(infos)]
     return st, out
+
+
+def shifted_launch_config(h):
+    """mrcg_shifted_launch_config: the autotuned launch shape of a shifted-family handle."""
+    cfg = np.zeros(5, dtype=np.int32)
+    st = lib().mrcg_shifted_launch_config(h, cfg.ctypes.data)
+    if st != OK:
+        raise MrcgError(st, "mrcg_shifted_launch_config")
+    return {"grid": int(cfg[0]), "blocks_per_sm": int(cfg[1]), "ell8": int(cfg[2]), "v_width": int(cfg[3]),
+            "padded_columns": int(cfg[4])}
 
 
 class Shifted:

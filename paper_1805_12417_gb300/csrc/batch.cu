@@ -34,7 +34,8 @@
 namespace mrcg {
 namespace batch {
 
-constexpr int kChunkRows = 4096;
+constexpr int kChunkRows = 4096;  // default rows per chunk
+constexpr int kChunkMin = 1024;   // smallest chunk height the autotuner tries
 constexpr int kMaxSystems = 4096;
 
 struct SysDesc {
@@ -896,6 +897,8 @@ struct mrcg_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int grid = 1, grid_b = 1, unroll = 4;
+  int chunk_rows = 0, nc_cap = 0;  // rows per chunk (autotuned), chunk capacity of the device arrays
+  int occ_a = 1, occ_b = 1;        // occupancy limits of step a / step b (blocks per SM)
   bool host_loop = false;  // MRCG_INNER_LOOP=host: inner loop driven from the host (for profilers)
   GraphSpec gs;
   std::vector<void*> allocs;
@@ -949,6 +952,120 @@ mrcg_status fetch(const T* src, size_t count, std::vector<T>& dst) {
   return MRCG_OK;
 }
 
+// cut every system into chunks of at most `rows` rows (never straddling two
+// systems); chunk0 / nchunks of each system follow
+void make_chunks(mrcg_batch* h, int rows) {
+  h->chunk_rows = rows;
+  h->h_chunks.clear();
+  int chunk0 = 0;
+  for (int i = 0; i < (int)h->h_sys.size(); ++i) {
+    SysDesc& sd = h->h_sys[i];
+    sd.chunk0 = chunk0;
+    sd.nchunks = (int)((sd.n_pad + rows - 1) / rows);
+    for (int c = 0; c < sd.nchunks; ++c) {
+      Chunk ch = {};
+      ch.row0 = sd.row0 + (int64_t)c * rows;
+      ch.row1 = std::min<int64_t>(sd.row0 + sd.n_pad, ch.row0 + rows);
+      ch.sys = i;
+      h->h_chunks.push_back(ch);
+    }
+    chunk0 += sd.nchunks;
+  }
+  h->nc = chunk0;
+}
+
+mrcg_status upload_chunks(mrcg_batch* h) {
+  BCK(cudaMemcpyAsync(h->d_sys, h->h_sys.data(), h->h_sys.size() * sizeof(SysDesc), cudaMemcpyHostToDevice,
+                      h->stream));
+  BCK(cudaMemcpyAsync(h->d_chunks, h->h_chunks.data(), h->nc * sizeof(Chunk), cudaMemcpyHostToDevice, h->stream));
+  BCK(cudaStreamSynchronize(h->stream));  // the host vectors may change next
+  return MRCG_OK;
+}
+
+mrcg_status batched_solve_impl(mrcg_batch* h, const double* B, double* X, double outer_tol, double inner_tol,
+                               int64_t max_iters, mrcg_info* infos, int64_t* launches_out);
+
+__global__ void b_pattern_kernel(double* v, int64_t count) {
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < count; i += (int64_t)gridDim.x * kThreads)
+    v[i] = 1.0 + 0.125 * (double)(i % 7) - 0.0625 * (double)(i % 5);
+}
+
+// host time of one calibration solve: each system's first inner solve runs
+// exactly `iters` iterations (tolerance 1e-300, budget iters) on a fixed
+// right-hand side, then every system stops (iteration budget)
+mrcg_status b_calib(mrcg_batch* h, long long iters, double* ms) {
+  b_pattern_kernel<<<256, kThreads, 0, h->stream>>>(h->zn, h->n_total);
+  BCK(cudaGetLastError());
+  BCK(cudaStreamSynchronize(h->stream));
+  const auto t0 = std::chrono::steady_clock::now();
+  const mrcg_status st = batched_solve_impl(h, h->zn, h->w0, 0.0, 1e-300, iters, nullptr, nullptr);
+  *ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return (st == MRCG_OK || st == MRCG_ERR_MAXITER) ? MRCG_OK : st;
+}
+
+mrcg_status b_rebuild(mrcg_batch* h, int nsm, int rows, int bps_a, int bps_b) {
+  make_chunks(h, rows);
+  BST(upload_chunks(h));
+  h->grid = std::max(1, std::min(h->nc, nsm * bps_a));
+  h->grid_b = std::max(1, std::min(h->nc, nsm * bps_b));
+  h->gs.nc = h->nc;
+  h->gs.grid = h->grid;
+  h->gs.grid_b = h->grid_b;
+  if (h->exec) cudaGraphExecDestroy(h->exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  h->exec = nullptr;
+  h->graph = nullptr;
+  BCK(build_graph_any(h->gs, &h->graph));
+  BCK(cudaGraphInstantiate(&h->exec, h->graph, 0));
+  return MRCG_OK;
+}
+
+// Launch-shape autotuner of the batch engine: rows per chunk (the unit a
+// block reduces and a converged system skips) and blocks per SM of step a,
+// then blocks per SM of step b, each candidate timed by the difference of two
+// calibration solves (8 and 40 inner iterations per system)
+mrcg_status batch_autotune(mrcg_batch* h, int nsm) {
+  auto per_iter = [&](double* out) -> mrcg_status {
+    double t1 = 0.0, t2 = 0.0;
+    BST(b_calib(h, 8, &t1));
+    BST(b_calib(h, 40, &t2));
+    *out = (t2 - t1) / 32.0;
+    return MRCG_OK;
+  };
+  double best = 1e300;
+  int best_rows = kChunkRows, best_a = h->occ_a, best_b = h->occ_b;
+  for (int rows : {1024, 2048, 4096, 8192}) {
+    for (int bps = 1; bps <= h->occ_a; ++bps) {
+      BST(b_rebuild(h, nsm, rows, bps, h->occ_b));
+      double t = 0.0;
+      BST(per_iter(&t));
+      if (getenv("MRCG_DEBUG"))
+        fprintf(stderr, "mrcg batch autotune: chunk %d rows, step a %d blocks/SM: %.4f ms per iteration\n", rows,
+                bps, t);
+      if (t < best) {
+        best = t;
+        best_rows = rows;
+        best_a = bps;
+      }
+    }
+  }
+  for (int bps = 1; bps <= h->occ_b; ++bps) {
+    if (bps == h->occ_b) continue;  // timed above
+    BST(b_rebuild(h, nsm, best_rows, best_a, bps));
+    double t = 0.0;
+    BST(per_iter(&t));
+    if (getenv("MRCG_DEBUG"))
+      fprintf(stderr, "mrcg batch autotune: step b %d blocks/SM: %.4f ms per iteration\n", bps, t);
+    if (t < best) {
+      best = t;
+      best_b = bps;
+    }
+  }
+  BST(b_rebuild(h, nsm, best_rows, best_a, best_b));
+  BCK(cudaStreamSynchronize(h->stream));
+  return MRCG_OK;
+}
+
 mrcg_status batch_create_impl(int32_t nsys, const mrcg_create_args* args, mrcg_batch* h) {
   h->nsys = nsys;
   h->fp32 = args[0].precision == MRCG_MIXED_FP32;
@@ -967,7 +1084,7 @@ mrcg_status batch_create_impl(int32_t nsys, const mrcg_create_args* args, mrcg_b
   std::vector<std::vector<double>> vas(nsys), Vs(nsys), lams(nsys);
   h->lam2.assign((size_t)nsys * kMaxK, 0.0);
   int64_t row0 = 0, voff = 0, slices = 0;
-  int chunk0 = 0;
+
   for (int i = 0; i < nsys; ++i) {
     const mrcg_create_args& a = args[i];
     if (a.n < 1 || a.nnz < 0 || a.k < 0 || a.k > kMaxK || !a.rowptr || (a.nnz > 0 && (!a.colind || !a.val)) ||
@@ -1001,25 +1118,18 @@ mrcg_status batch_create_impl(int32_t nsys, const mrcg_create_args* args, mrcg_b
     sd.slice0 = slices;
     sd.voff = voff;
     sd.k = a.k;
-    sd.chunk0 = chunk0;
-    sd.nchunks = (int)((sd.n_pad + kChunkRows - 1) / kChunkRows);
-    for (int c = 0; c < sd.nchunks; ++c) {
-      Chunk ch = {};
-      ch.row0 = row0 + (int64_t)c * kChunkRows;
-      ch.row1 = std::min<int64_t>(row0 + sd.n_pad, ch.row0 + kChunkRows);
-      ch.sys = i;
-      h->h_chunks.push_back(ch);
-    }
     h->h_sys.push_back(sd);
     row0 += sd.n_pad;
     slices += sd.n_pad / kSlice;
     voff += sd.n_pad * a.k;
-    chunk0 += sd.nchunks;
     h->kmax = std::max(h->kmax, a.k);
   }
   if (row0 > (int64_t)0x7fffff00) return MRCG_ERR_INVALID;
   h->n_total = row0;
-  h->nc = chunk0;
+  // chunk capacity: the smallest chunk height the autotuner tries
+  h->nc_cap = 0;
+  for (const SysDesc& sd : h->h_sys) h->nc_cap += (int)((sd.n_pad + kChunkMin - 1) / kChunkMin);
+  make_chunks(h, kChunkRows);
   h->kb = h->kmax == 0 ? 0 : h->kmax <= 8 ? 8 : h->kmax <= 16 ? 16 : 32;
   // ---- block-diagonal SELL-32 with global columns
   const int64_t nslices = slices;
@@ -1130,13 +1240,12 @@ mrcg_status batch_create_impl(int32_t nsys, const mrcg_create_args* args, mrcg_b
     *p = q;
   }
   BST(balloc(h, &h->d_sys, (size_t)nsys));
-  BST(balloc(h, &h->d_chunks, (size_t)h->nc));
+  BST(balloc(h, &h->d_chunks, (size_t)h->nc_cap));
   BST(balloc(h, &h->d_st, (size_t)nsys));
-  BST(balloc(h, &h->d_partials, (size_t)kMaxNV * h->nc));
+  BST(balloc(h, &h->d_partials, (size_t)kMaxNV * h->nc_cap));
   BST(balloc(h, &h->d_modes, (size_t)nsys));
   BST(balloc(h, &h->d_ctl, 3));
-  BCK(cudaMemcpyAsync(h->d_sys, h->h_sys.data(), nsys * sizeof(SysDesc), cudaMemcpyHostToDevice, h->stream));
-  BCK(cudaMemcpyAsync(h->d_chunks, h->h_chunks.data(), h->nc * sizeof(Chunk), cudaMemcpyHostToDevice, h->stream));
+  BST(upload_chunks(h));
   BCK(cudaMemsetAsync(h->d_st, 0, nsys * sizeof(DevState), h->stream));
   BCK(cudaMallocHost(&h->h_st, nsys * sizeof(DevState)));
   BCK(cudaMallocHost(&h->h_init, nsys * sizeof(DevState)));
@@ -1146,6 +1255,8 @@ mrcg_status batch_create_impl(int32_t nsys, const mrcg_create_args* args, mrcg_b
   BCK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
   int occ_b = 1;
   const int occ = occupancy(h->fp32, h->kb, &occ_b);
+  h->occ_a = occ;
+  h->occ_b = occ_b;
   h->grid = std::max(1, std::min(h->nc, nsm * occ));
   h->grid_b = std::max(1, std::min(h->nc, nsm * occ_b));
   if (const char* u = getenv("MRCG_UNROLL")) h->unroll = std::max(2, atoi(u) & ~1);
@@ -1176,6 +1287,9 @@ mrcg_status batch_create_impl(int32_t nsys, const mrcg_create_args* args, mrcg_b
   BCK(build_graph_any(gs, &h->graph));
   BCK(cudaGraphInstantiate(&h->exec, h->graph, 0));
   BCK(cudaStreamSynchronize(h->stream));
+  const char* at = getenv("MRCG_AUTOTUNE");
+  // MRCG_AUTOTUNE=2 tunes whatever the size (tests)
+  if ((!at || atoi(at) != 0) && (h->n_total >= (1 << 20) || (at && atoi(at) == 2))) BST(batch_autotune(h, nsm));
   return MRCG_OK;
 }
 
@@ -1416,6 +1530,15 @@ mrcg_status mrcg_batched_solve(mrcg_batch_handle h, const double* B, double* X, 
 }
 
 int32_t mrcg_batch_size(mrcg_batch_handle h) { return h ? h->nsys : 0; }
+
+mrcg_status mrcg_batch_launch_config(mrcg_batch_handle h, int32_t* cfg) {
+  if (!h || !cfg) return MRCG_ERR_INVALID;
+  cfg[0] = h->chunk_rows;
+  cfg[1] = h->grid;
+  cfg[2] = h->grid_b;
+  cfg[3] = h->nc;
+  return MRCG_OK;
+}
 
 void mrcg_batch_destroy(mrcg_batch_handle h) {
   if (h) batch_destroy_impl(h);

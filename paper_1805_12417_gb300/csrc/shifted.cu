@@ -1059,6 +1059,8 @@ struct mrcg_shifted {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int grid = 1, unroll = 4;
+  int grid_bps = 0;        // row-kernel blocks per SM chosen by the autotuner (0: the occupancy limit)
+  bool use_ell = true;     // ELL-8 row path (four rows per warp) when L allows it; else one row per warp (CSR)
   bool host_loop = false;  // MRCG_INNER_LOOP=host: inner loop driven from the host (for profilers)
   GSpec gs = {};
   std::vector<void*> allocs;
@@ -1124,7 +1126,7 @@ SArgs<T> sargs(mrcg_shifted* h) {
   a.rowptr = h->d_rowptr;
   a.colind = h->d_col;
   a.val = reinterpret_cast<const T*>(sizeof(T) == 4 ? (const void*)h->d_val32 : (const void*)h->d_val64);
-  a.ell_col = h->d_ell_col;
+  a.ell_col = h->use_ell ? h->d_ell_col : nullptr;
   a.ell_val = reinterpret_cast<const T*>(sizeof(T) == 4 ? (const void*)h->d_ell32 : (const void*)h->d_ell64);
   a.V = reinterpret_cast<const T*>(sizeof(T) == 4 ? (const void*)h->d_V32 : (const void*)h->d_V64);
   a.sigma = h->d_sigma;
@@ -1141,7 +1143,8 @@ SArgs<T> sargs(mrcg_shifted* h) {
 
 template <typename T, int NM, int KV>
 mrcg_status build_t(mrcg_shifted* h, int nsm) {
-  h->grid = std::max(1, nsm * occupancy_t<T, NM, KV>());
+  const int occ = occupancy_t<T, NM, KV>();
+  h->grid = std::max(1, nsm * (h->grid_bps > 0 ? std::min(h->grid_bps, occ) : occ));
   GSpec gs = {};
   gs.st = h->d_st;
   gs.kcol = h->d_kcol;
@@ -1163,22 +1166,115 @@ cudaError_t run_host_t(mrcg_shifted* h) {
   return run_host<T, NM, KV>(h->gs, sargs<T>(h), h->stream);
 }
 
-cudaError_t run_host_any(mrcg_shifted* h) {
-  if (h->fp32) {
-    if (h->nm == 1) return h->kv == 8 ? run_host_t<float, 1, 8>(h) : run_host_t<float, 1, 32>(h);
-    return h->kv == 8 ? run_host_t<float, 2, 8>(h) : run_host_t<float, 2, 32>(h);
-  }
-  if (h->nm == 1) return h->kv == 8 ? run_host_t<double, 1, 8>(h) : run_host_t<double, 1, 32>(h);
-  return h->kv == 8 ? run_host_t<double, 2, 8>(h) : run_host_t<double, 2, 32>(h);
+// dispatch on (precision, column groups NM, V_hat width bucket KV) of the handle
+#define SH_DISPATCH(F, ...)                                                                 \
+  do {                                                                                      \
+    if (h->fp32) {                                                                          \
+      if (h->nm == 1) {                                                                     \
+        switch (h->kv) {                                                                    \
+          case 8: return F<float, 1, 8>(__VA_ARGS__);                                        \
+          case 16: return F<float, 1, 16>(__VA_ARGS__);                                      \
+          case 24: return F<float, 1, 24>(__VA_ARGS__);                                      \
+          default: return F<float, 1, 32>(__VA_ARGS__);                                      \
+        }                                                                                   \
+      }                                                                                     \
+      switch (h->kv) {                                                                      \
+        case 8: return F<float, 2, 8>(__VA_ARGS__);                                          \
+        case 16: return F<float, 2, 16>(__VA_ARGS__);                                        \
+        case 24: return F<float, 2, 24>(__VA_ARGS__);                                        \
+        default: return F<float, 2, 32>(__VA_ARGS__);                                        \
+      }                                                                                     \
+    }                                                                                       \
+    if (h->nm == 1) {                                                                       \
+      switch (h->kv) {                                                                      \
+        case 8: return F<double, 1, 8>(__VA_ARGS__);                                         \
+        case 16: return F<double, 1, 16>(__VA_ARGS__);                                       \
+        case 24: return F<double, 1, 24>(__VA_ARGS__);                                       \
+        default: return F<double, 1, 32>(__VA_ARGS__);                                       \
+      }                                                                                     \
+    }                                                                                       \
+    switch (h->kv) {                                                                        \
+      case 8: return F<double, 2, 8>(__VA_ARGS__);                                           \
+      case 16: return F<double, 2, 16>(__VA_ARGS__);                                         \
+      case 24: return F<double, 2, 24>(__VA_ARGS__);                                         \
+      default: return F<double, 2, 32>(__VA_ARGS__);                                         \
+    }                                                                                       \
+  } while (0)
+
+cudaError_t run_host_any(mrcg_shifted* h) { SH_DISPATCH(run_host_t, h); }
+
+mrcg_status build_any(mrcg_shifted* h, int nsm) { SH_DISPATCH(build_t, h, nsm); }
+
+template <typename T, int NM, int KV>
+int occupancy_h(mrcg_shifted*) {
+  return occupancy_t<T, NM, KV>();
+}
+int occupancy_any(mrcg_shifted* h) { SH_DISPATCH(occupancy_h, h); }
+
+mrcg_status shifted_solve_impl(mrcg_shifted* h, const double* B, double* X, double outer_tol, double inner_tol,
+                               int64_t max_iters, mrcg_info* infos);
+
+__global__ void sh_pattern_kernel(double* v, int64_t count) {
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < count; i += (int64_t)gridDim.x * kThreads)
+    v[i] = 1.0 + 0.125 * (double)(i % 7) - 0.0625 * (double)(i % 5);
 }
 
-mrcg_status build_any(mrcg_shifted* h, int nsm) {
-  if (h->fp32) {
-    if (h->nm == 1) return h->kv == 8 ? build_t<float, 1, 8>(h, nsm) : build_t<float, 1, 32>(h, nsm);
-    return h->kv == 8 ? build_t<float, 2, 8>(h, nsm) : build_t<float, 2, 32>(h, nsm);
+// host time of one calibration solve: every column's first inner solve runs
+// exactly `iters` lock-step iterations (tolerance 1e-300, budget iters) on a
+// fixed block, then the solve stops (iteration budget)
+mrcg_status calib_time(mrcg_shifted* h, long long iters, double* ms) {
+  const int64_t cnt = h->n * (int64_t)h->ncp;
+  sh_pattern_kernel<<<256, kThreads, 0, h->stream>>>(h->zn, cnt);
+  SCK(cudaGetLastError());
+  SCK(cudaStreamSynchronize(h->stream));
+  const auto t0 = std::chrono::steady_clock::now();
+  const mrcg_status st = shifted_solve_impl(h, h->zn, h->w0, 0.0, 1e-300, iters, nullptr);
+  *ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return (st == MRCG_OK || st == MRCG_ERR_MAXITER) ? MRCG_OK : st;
+}
+
+mrcg_status rebuild(mrcg_shifted* h, int nsm) {
+  if (h->exec) cudaGraphExecDestroy(h->exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  h->exec = nullptr;
+  h->graph = nullptr;
+  SST(build_any(h, nsm));
+  SCK(cudaGraphInstantiate(&h->exec, h->graph, 0));
+  return MRCG_OK;
+}
+
+// Launch-shape autotuner of the lock-step engine: blocks per SM of the row
+// kernels (1 .. occupancy limit) and, when L has an ELL-8 copy, four rows per
+// warp (ELL-8) against one row per warp (CSR); each candidate is timed by the
+// difference of two calibration solves (8 and 40 lock-step iterations)
+mrcg_status shifted_autotune(mrcg_shifted* h, int nsm) {
+  const int occ = occupancy_any(h);
+  double best = 1e300;
+  int best_bps = 0;
+  bool best_ell = h->use_ell;
+  for (int ell = h->d_ell_col ? 1 : 0; ell >= 0; --ell) {
+    for (int bps = 1; bps <= occ; ++bps) {
+      h->grid_bps = bps;
+      h->use_ell = ell != 0;
+      SST(rebuild(h, nsm));
+      double t1 = 0.0, t2 = 0.0;
+      SST(calib_time(h, 8, &t1));
+      SST(calib_time(h, 40, &t2));
+      const double per = (t2 - t1) / 32.0;
+      if (getenv("MRCG_DEBUG"))
+        fprintf(stderr, "mrcg shifted autotune: ell %d bps %d: %.4f ms per lock-step iteration\n", ell, bps, per);
+      if (per < best) {
+        best = per;
+        best_bps = bps;
+        best_ell = ell != 0;
+      }
+    }
   }
-  if (h->nm == 1) return h->kv == 8 ? build_t<double, 1, 8>(h, nsm) : build_t<double, 1, 32>(h, nsm);
-  return h->kv == 8 ? build_t<double, 2, 8>(h, nsm) : build_t<double, 2, 32>(h, nsm);
+  h->grid_bps = best_bps;
+  h->use_ell = best_ell;
+  SST(rebuild(h, nsm));
+  SCK(cudaStreamSynchronize(h->stream));
+  return MRCG_OK;
 }
 
 mrcg_status shifted_create_impl(const mrcg_create_args* L, int32_t nshift, const double* sigma,
@@ -1191,7 +1287,7 @@ mrcg_status shifted_create_impl(const mrcg_create_args* L, int32_t nshift, const
   h->ncp = h->nc <= 32 ? 32 : 64;
   h->nm = h->ncp / 32;
   h->kmax = L->k;
-  h->kv = L->k <= 8 ? 8 : 32;
+  h->kv = L->k <= 8 ? 8 : L->k <= 16 ? 16 : L->k <= 24 ? 24 : 32;  // width bucket of the row-major V_hat
   h->fp32 = L->precision == MRCG_MIXED_FP32;
   h->max_outer = L->max_outer > 0 ? L->max_outer : 200;
   h->restart_factor = L->restart_factor == 0.0 ? 0.5 : L->restart_factor;
@@ -1311,6 +1407,10 @@ mrcg_status shifted_create_impl(const mrcg_create_args* L, int32_t nshift, const
   if (h->grid > nsm * 8) return MRCG_ERR_INVALID;
   SCK(cudaGraphInstantiate(&h->exec, h->graph, 0));
   SCK(cudaStreamSynchronize(h->stream));
+  const char* at = getenv("MRCG_AUTOTUNE");
+  // MRCG_AUTOTUNE=2 tunes whatever the size (tests)
+  if ((!at || atoi(at) != 0) && (n * (int64_t)h->ncp >= (int64_t)1 << 22 || (at && atoi(at) == 2)))
+    SST(shifted_autotune(h, nsm));
   return MRCG_OK;
 }
 
@@ -1337,7 +1437,7 @@ OArgs soargs(mrcg_shifted* h) {
   a.rowptr = h->d_rowptr;
   a.colind = h->d_col;
   a.val = h->d_val64;
-  a.ell_col = h->d_ell_col;
+  a.ell_col = h->use_ell ? h->d_ell_col : nullptr;
   a.ell_val = h->d_ell64;
   a.sigma = h->d_sigma;
   a.x = h->x;
@@ -1583,6 +1683,16 @@ mrcg_status mrcg_shifted_solve(mrcg_shifted_handle h, const double* B, double* X
 }
 
 int32_t mrcg_shifted_columns(mrcg_shifted_handle h) { return h ? h->nc : 0; }
+
+mrcg_status mrcg_shifted_launch_config(mrcg_shifted_handle h, int32_t* cfg) {
+  if (!h || !cfg) return MRCG_ERR_INVALID;
+  cfg[0] = h->grid;
+  cfg[1] = h->grid_bps;
+  cfg[2] = (h->use_ell && h->d_ell_col) ? 1 : 0;
+  cfg[3] = h->kv;
+  cfg[4] = h->ncp;
+  return MRCG_OK;
+}
 
 void mrcg_shifted_destroy(mrcg_shifted_handle h) {
   if (h) shifted_destroy_impl(h);

@@ -148,3 +148,22 @@ def test_batch64_lap2d_mixed():
     for p, x in zip(ps, xs):
         A = O.System(p.rowptr, p.colind, p.val)
         assert A.true_relres(p.b, x) <= 1e-10
+
+
+def test_batch_autotuned_shape_solves_like_the_default(monkeypatch):
+    """The batch autotuner (forced with MRCG_AUTOTUNE=2) picks the chunk height
+    and the grids by timing calibration solves; the solutions match the
+    default shape's to the FP64 tolerance."""
+    from gen import shifted_laplacian_problem
+    ps = [shifted_laplacian_problem(f"bt{i}", (37 + 9 * i, 31 + 4 * i), 2 + i, seed=60 + i) for i in range(5)]
+    B = np.concatenate([p.b for p in ps])
+    out = {}
+    for mode in ("0", "2"):
+        monkeypatch.setenv("MRCG_AUTOTUNE", mode)
+        with m.Batch(ps) as bt:
+            cfg = m.batch_launch_config(bt.h)
+            X, st, infos = bt.solve(B.copy(), outer_tol=1e-12)
+        assert st == m.OK
+        out[mode] = (X, cfg)
+    assert out["0"][1]["chunk_rows"] == 4096 and out["2"][1]["chunk_rows"] in (1024, 2048, 4096, 8192)
+    assert np.linalg.norm(out["0"][0] - out["2"][0]) <= 1e-8 * np.linalg.norm(out["0"][0])

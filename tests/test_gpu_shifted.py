@@ -166,3 +166,22 @@ def shift_condition(fam, j):
     gap = min(abs(ev[kj - 1] - fam.sigma[j]), abs(ev[kj] - fam.sigma[j]))
     lam_max = 4.0 * len(fam.dims)
     return (lam_max - fam.sigma[j]) / gap
+
+
+def test_shifted_autotuned_shape_solves_like_the_default(fam, monkeypatch):
+    """The autotuner (forced with MRCG_AUTOTUNE=2 at this small size) picks a
+    grid and the ELL-8 or CSR row path by timing calibration solves; the
+    solution is the same to the FP64 tolerance as with the default shape."""
+    out = {}
+    for mode in ("0", "2"):
+        monkeypatch.setenv("MRCG_AUTOTUNE", mode)
+        with m.Shifted(fam) as sh:
+            cfg = m.shifted_launch_config(sh.h)
+            X, st, infos = sh.solve(fam.B.copy(), outer_tol=1e-12)
+        assert st == m.OK
+        out[mode] = (X, cfg)
+    assert out["0"][1]["blocks_per_sm"] == 0 and out["2"][1]["blocks_per_sm"] >= 1
+    assert out["2"][1]["ell8"] in (0, 1) and out["2"][1]["v_width"] in (8, 16, 24, 32)
+    for c in range(fam.ncols):
+        a, b = out["0"][0][:, c], out["2"][0][:, c]
+        assert np.linalg.norm(a - b) <= 1e-8 * np.linalg.norm(a)
