@@ -27,3 +27,4 @@ from .problems import (  # noqa: F401
     WORKLOADS,
 )
 from .saddle import saddle_96_b20x64, saddle_problem, small_saddle  # noqa: F401,E402
+from .brake import BrakeSystem, brake_64, brake_system, small_brake  # noqa: F401,E402

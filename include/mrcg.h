@@ -397,6 +397,85 @@ mrcg_status mrcg_negative_eigenpairs(int64_t n, const int64_t* rowptr, const int
                                      int32_t block, double tol, int64_t max_spmv, uint64_t seed, int32_t* k,
                                      double* V, double* lambda, mrcg_eig_info* info);
 
+/* ---- Complex shifted systems of the disk-brake application (Sec. 3) ----
+ *
+ * For a quadratic pencil lambda^2 Mass + lambda D + K (Mass: lumped, i.e.
+ * diagonal, positive; K, D general sparse) with companion linearisation
+ * A = [[0, I], [-K, -D]], B = [[I, 0], [0, Mass]], solve
+ *     (gamma B - A) (x + i y) = f + i g        (x, y, f, g of length 2n)
+ * through the double-size real system of Sec. 3 with its preconditioner M
+ * built from the symmetric positive definite stiffness KE (K without its
+ * general part) and no damping: flexible GMRES on the real system, M applied
+ * by its block LU, the Schur complement S = S1 S2 (Sec. 3), S2 solved by
+ * flexible GMRES preconditioned with its block lower triangular part, whose
+ * diagonal solves are with KE - |gamma|^2 Mass: the symmetric indefinite
+ * inner level, solved by this library's MINRES-CG.  That inner matrix depends
+ * on |gamma| only, so one handle serves every gamma of the same modulus (the
+ * reuse Sec. 3 points out): its negative eigenpairs are given or computed once
+ * at create by mrcg_negative_eigenpairs. */
+typedef struct mrcg_complex* mrcg_complex_handle; /* opaque */
+
+typedef struct {
+  int64_t n;                                  /* mechanical unknowns (the real system has 4n) */
+  const int64_t* ke_rowptr;                   /* KE: symmetric positive definite stiffness, CSR (its diagonal stored) */
+  const int32_t* ke_colind;
+  const double* ke_val;
+  const int64_t* k_rowptr;                    /* K (K_Omega of Sec. 3): general sparse, CSR */
+  const int32_t* k_colind;
+  const double* k_val;
+  const int64_t* d_rowptr;                    /* D (D_Omega): general sparse, CSR */
+  const int32_t* d_colind;
+  const double* d_val;
+  const double* mass;                         /* [n] lumped mass, all > 0 */
+  double gamma_abs;                           /* |gamma| > 0 */
+  int32_t k;                                  /* negative eigenpairs of KE - |gamma|^2 Mass given in V, lambda
+                                                 (0 <= k <= 32), or -1: computed at create */
+  const double* V;                            /* [n*k] column-major, orthonormal */
+  const double* lambda;                       /* [k], all < 0 */
+  int32_t eig_block;                          /* k = -1: block size of the eigensolver (0 selects 32) */
+  int32_t precision;                          /* mrcg_precision of the inner CG */
+  int32_t inner_prec;                         /* mrcg_inner_prec of the inner CG */
+  int32_t reserved;                           /* set to 0 */
+  void* stream;                               /* cudaStream_t, or NULL for a stream of its own */
+} mrcg_complex_args;
+
+typedef struct {
+  int32_t outer_iters;       /* flexible GMRES iterations on the real-equivalent system */
+  int32_t s2_iters_total;    /* flexible GMRES iterations on S2, over all applications of M */
+  int64_t inner_solves;      /* MINRES-CG solves of the inner level */
+  int64_t inner_cg_iters;    /* CG iterations inside them */
+  double true_relres;        /* ||f + i g - C (x + i y)|| / ||f + i g|| at exit */
+  double solve_ms;
+  int32_t status;
+} mrcg_complex_info;
+
+/* Copies every input (host or device arrays).  Errors: MRCG_ERR_INVALID (sizes,
+ * CSR, a mass entry <= 0, a KE row without its diagonal, k > 32), the errors of
+ * mrcg_negative_eigenpairs and mrcg_solver_create for the inner level,
+ * MRCG_ERR_OOM, MRCG_ERR_CUDA. */
+mrcg_status mrcg_complex_create(const mrcg_complex_args* args, mrcg_complex_handle* out);
+
+/* Negative eigenvalues of the handle's inner-level matrix (-1 for NULL). */
+int32_t mrcg_complex_negative_count(mrcg_complex_handle h);
+
+/* Solve for one shift gamma = gamma_re + i gamma_im with |gamma| equal to the
+ * handle's (relative 1e-10) and gamma_im > 0, from x + i y = 0.  f, g (inputs)
+ * and x, y (outputs) hold 2n values each, host or device.  Outer flexible
+ * GMRES(restart) to the relative residual tol (at most max_iters iterations,
+ * restart <= 120); each application of M solves S2 by one cycle of flexible
+ * GMRES to s2_tol (at most s2_max <= 120 iterations); each inner-level solve is
+ * MINRES-CG to the true relative residual inner_tol with inner CG tolerance
+ * cg_tol.  Allocates its work space (about (restart + 2) 4n + (s2_max + 2) 2n
+ * doubles) for the call.  Returns MRCG_OK, MRCG_ERR_MAXITER (info valid, x, y
+ * the last iterate), MRCG_ERR_INVALID, or an inner-level failure. */
+mrcg_status mrcg_complex_solve(mrcg_complex_handle h, double gamma_re, double gamma_im, const double* f,
+                               const double* g, double* x, double* y, double tol, int32_t restart,
+                               int32_t max_iters, double s2_tol, int32_t s2_max, double inner_tol, double cg_tol,
+                               mrcg_complex_info* info);
+
+/* Release the handle and its inner-level solver (NULL is a no-op). */
+void mrcg_complex_destroy(mrcg_complex_handle h);
+
 /* Release every device and host resource of the handle (NULL is a no-op). */
 void mrcg_solver_destroy(mrcg_handle h);
 

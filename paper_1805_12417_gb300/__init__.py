@@ -46,6 +46,21 @@ class EigInfo(C.Structure):
                 ("seconds", C.c_double), ("status", C.c_int32)]
 
 
+class ComplexArgs(C.Structure):
+    _fields_ = [("n", C.c_int64), ("ke_rowptr", C.c_void_p), ("ke_colind", C.c_void_p), ("ke_val", C.c_void_p),
+                ("k_rowptr", C.c_void_p), ("k_colind", C.c_void_p), ("k_val", C.c_void_p),
+                ("d_rowptr", C.c_void_p), ("d_colind", C.c_void_p), ("d_val", C.c_void_p),
+                ("mass", C.c_void_p), ("gamma_abs", C.c_double), ("k", C.c_int32), ("V", C.c_void_p),
+                ("lambda_", C.c_void_p), ("eig_block", C.c_int32), ("precision", C.c_int32),
+                ("inner_prec", C.c_int32), ("reserved", C.c_int32), ("stream", C.c_void_p)]
+
+
+class ComplexInfo(C.Structure):
+    _fields_ = [("outer_iters", C.c_int32), ("s2_iters_total", C.c_int32), ("inner_solves", C.c_int64),
+                ("inner_cg_iters", C.c_int64), ("true_relres", C.c_double), ("solve_ms", C.c_double),
+                ("status", C.c_int32)]
+
+
 _lib = None
 
 
@@ -79,6 +94,15 @@ def lib() -> C.CDLL:
         L.mrcg_negative_eigenpairs.argtypes = [C.c_int64, P, P, P, C.c_int32, C.c_double, C.c_int64, C.c_uint64,
                                                C.POINTER(C.c_int32), P, P, C.POINTER(EigInfo)]
         L.mrcg_negative_eigenpairs.restype = C.c_int
+        L.mrcg_complex_create.argtypes = [C.POINTER(ComplexArgs), C.POINTER(C.c_void_p)]
+        L.mrcg_complex_create.restype = C.c_int
+        L.mrcg_complex_negative_count.argtypes = [P]
+        L.mrcg_complex_negative_count.restype = C.c_int32
+        L.mrcg_complex_solve.argtypes = [P, C.c_double, C.c_double, P, P, P, P, C.c_double, C.c_int32, C.c_int32,
+                                         C.c_double, C.c_int32, C.c_double, C.c_double, C.POINTER(ComplexInfo)]
+        L.mrcg_complex_solve.restype = C.c_int
+        L.mrcg_complex_destroy.argtypes = [P]
+        L.mrcg_complex_destroy.restype = None
         L.mrcg_batch_create.argtypes = [C.c_int32, C.POINTER(CreateArgs), C.POINTER(C.c_void_p)]
         L.mrcg_batch_create.restype = C.c_int
         L.mrcg_batched_solve.argtypes = [P, P, P, C.c_double, C.c_double, C.c_int64, C.POINTER(Info)]
@@ -508,6 +532,80 @@ class Shifted:
     def close(self):
         if getattr(self, "h", None):
             lib().mrcg_shifted_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class ComplexShifted:
+    """Owning wrapper of a complex-shift handle (Sec. 3): built from a system
+    object with n, KE, K, D (scipy CSR), mass and gamma (its modulus fixes the
+    inner level); V, lam (n x k, k) are used when given, else the eigenpairs
+    are computed at create."""
+
+    def __init__(self, sysobj, precision=FP64, inner_prec=MCG_IDENTITY, V=None, lam=None, eig_block=0,
+                 stream=None):
+        self.n = int(sysobj.n)
+        keep = []
+
+        def csr(M):
+            M = M.tocsr()
+            M.sort_indices()
+            arrs = (np.ascontiguousarray(M.indptr, dtype=np.int64), np.ascontiguousarray(M.indices, dtype=np.int32),
+                    np.ascontiguousarray(M.data, dtype=np.float64))
+            keep.extend(arrs)
+            return [a.ctypes.data for a in arrs]
+        ke, kk, dd = csr(sysobj.KE), csr(sysobj.K), csr(sysobj.D)
+        mass = np.ascontiguousarray(sysobj.mass, dtype=np.float64)
+        keep.append(mass)
+        k, Vp, lamp = -1, None, None
+        if V is not None:
+            Vc = np.ascontiguousarray(np.asarray(V, dtype=np.float64).reshape(self.n, -1).T)
+            lam = np.ascontiguousarray(lam, dtype=np.float64)
+            keep += [Vc, lam]
+            k, Vp, lamp = Vc.shape[0], Vc.ctypes.data, lam.ctypes.data
+        a = ComplexArgs(self.n, *ke, *kk, *dd, mass.ctypes.data, float(abs(sysobj.gamma)), k, Vp, lamp,
+                        int(eig_block), int(precision), int(inner_prec), 0, stream)
+        h = C.c_void_p()
+        st = lib().mrcg_complex_create(C.byref(a), C.byref(h))
+        if st != OK:
+            raise MrcgError(st, "mrcg_complex_create")
+        self.h = h.value
+
+    @property
+    def negative_count(self):
+        return int(lib().mrcg_complex_negative_count(self.h))
+
+    def solve(self, gamma, f, g, tol=1e-10, restart=40, max_iters=200, s2_tol=1e-6, s2_max=60, inner_tol=1e-8,
+              cg_tol=1e-3):
+        """x + i y with (gamma B - A)(x + i y) = f + i g.  Returns (x, y, status, info dict)."""
+        _check_dtype(f, np.float64, "f"); _check_dtype(g, np.float64, "g")
+        if isinstance(f, np.ndarray):
+            x = np.zeros(2 * self.n); y = np.zeros(2 * self.n)
+        else:
+            x = f.new_zeros(2 * self.n); y = f.new_zeros(2 * self.n)
+        info = ComplexInfo()
+        fp, kf = _ptr(f); gp, kg = _ptr(g); xp, kx = _ptr(x); yp, ky = _ptr(y)
+        st = lib().mrcg_complex_solve(self.h, float(gamma.real), float(gamma.imag), fp, gp, xp, yp, float(tol),
+                                      int(restart), int(max_iters), float(s2_tol), int(s2_max), float(inner_tol),
+                                      float(cg_tol), C.byref(info))
+        if st in (ERR_INVALID, ERR_CUDA, ERR_OOM):
+            raise MrcgError(st, "mrcg_complex_solve")
+        return x, y, st, {f_: getattr(info, f_) for f_, _ in ComplexInfo._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mrcg_complex_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmrcg.so")
-SOURCES = ["api.cu", "batch.cu", "cg_f32.cu", "cg_f64.cu", "cg_kernels.cu", "diag.cu", "eig.cu", "ilu.cu", "minres_kernels.cu", "noalloc.cu",
+SOURCES = ["api.cu", "batch.cu", "complex.cu", "cg_f32.cu", "cg_f64.cu", "cg_kernels.cu", "diag.cu", "eig.cu", "ilu.cu", "minres_kernels.cu", "noalloc.cu",
            "shifted.cu"]
 HEADERS = ["cg_impl.cuh", "common.cuh", "ilu.h", "kernels.h", "trace.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

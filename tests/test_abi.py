@@ -71,7 +71,9 @@ def _c_struct_fields(name):
     return fields
 
 
-@pytest.mark.parametrize("cname,pyname", [("mrcg_create_args", "CreateArgs"), ("mrcg_info", "Info")])
+@pytest.mark.parametrize("cname,pyname", [("mrcg_create_args", "CreateArgs"), ("mrcg_info", "Info"),
+                                          ("mrcg_eig_info", "EigInfo"), ("mrcg_complex_args", "ComplexArgs"),
+                                          ("mrcg_complex_info", "ComplexInfo")])
 def test_binding_struct_layout_matches_header(cname, pyname):
     import paper_1805_12417_gb300 as m
     cf = _c_struct_fields(cname)
