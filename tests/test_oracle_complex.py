@@ -4,9 +4,9 @@ The section's algebra is checked on a small synthetic disk-brake stand-in:
 the real-equivalent system reproduces the complex solution; the block LU of
 the preconditioner M is exact; the Schur complement factors as S = S1 S2;
 S2t is S2 without its (1, 2) block and its diagonal block is
--(1/gamma_i)(KE - |gamma|^2 Mass); and the preconditioner application by the
-block LU with Richardson steps on S2 (preconditioned by S2t) converges to
-M^{-1} r, one step being within the size of the dropped block.
+-(1/gamma_i)(KE - |gamma|^2 Mass), whose inertia is the generator's k; the
+block-LU application equals M^{-1} r; and S2t preconditions S2 well inside
+GMRES, while the plain splitting iteration with S2t diverges.
 """
 import numpy as np
 
