@@ -175,6 +175,8 @@ def step_a_kernel_name(cfg, prec="float"):
         return f"cg_step_a_pg_staged_kernel<{prec}, {kb}, {mb}, {pipe}>"
     if var == 11:
         return f"cg_step_a_pg_kernel<{prec}, {kb}>"
+    if var in (14, 15):
+        return f"cg_step_a_pg2_kernel<{prec}, {kb}, {2 if var == 14 else 1}>"
     if var == 8:
         return f"cg_step_a_staged_kernel<{prec}, {kb}, 3, 0, 1>"
     if var >= 5:
@@ -453,7 +455,7 @@ def inner_bytes(cfg, n, nnz, k, w, mcg):
     a_mat = nnz * (w + ib) + k * n * w  # A values + column indices, V_hat
     if var == 8:  # one kernel: r, q, p, z read and r, z, p, q written for the own rows
         return a_mat + 8 * n * w, 0
-    if 9 <= var <= 13:  # one gather: p, r (and M_cg^-1) read, q written | p, q, z, r (M_cg^-1) read, z, r, p written
+    if 9 <= var <= 15:  # one gather: p, r (and M_cg^-1) read, q written | p, q, z, r (M_cg^-1) read, z, r, p written
         return a_mat + 3 * n * w + jac, 7 * n * w + jac
     # two gathers: s, p (and M_cg^-1) read, q, p' written | p', q, z, r (M_cg^-1) read, z, r (s) written
     b = 6 * n * w + (2 * jac if mcg == "jacobi" else 0) + (2 * n * w + k * n * w if mcg == "smw" else 0)
@@ -467,7 +469,7 @@ def step_a_flops(cfg, n, nnz, k, mcg):
     at every gathered entry and for the own row."""
     var = cfg["step_a_variant"]
     base = 2 * nnz + 4 * k * n
-    if 9 <= var <= 13:
+    if 9 <= var <= 15:
         return base + 6 * n + (3 * n if mcg == "jacobi" else 0)
     if var == 8:
         return base + 2 * nnz * 2 + 14 * n

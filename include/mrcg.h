@@ -37,10 +37,14 @@
  *                         replay a shape reported by mrcg_launch_config (for
  *                         profilers, whose slowed launches mislead the tuner);
  *                         ignored when the shape does not fit the matrix.
- *  - MRCG_VAR_A (0-11), MRCG_STAGES (2-8), MRCG_BPSM_A, MRCG_BPSM_B
+ *  - MRCG_VAR_A (0-15), MRCG_STAGES (2-8), MRCG_BPSM_A, MRCG_BPSM_B
  *                         fix the step-a variant, its pipeline depth and the
  *                         blocks per SM of the two inner kernels; any of them
  *                         turns the autotuner off.
+ *  - MRCG_PDL=0           plain graph edges between the inner kernels (by default
+ *                         step-a variants 14 and 15 and their step b are joined by
+ *                         programmatic edges: a kernel starts streaming its static
+ *                         operands while its predecessor finishes).
  *  - MRCG_IDX16=0         keep 32-bit column indices in the inner kernels
  *                         (16-bit deltas are used whenever |col - row| <= 32767).
  *  - MRCG_UNROLL=U        inner iterations per convergence check (even, >= 2).
@@ -51,7 +55,7 @@
  *  - MRCG_DEBUG           print failed CUDA calls and the tuner's choice to
  *                         stderr.
  *  - MRCG_TEST_STALL=1    test hook: the producer warp of the staged step-a
- *                         kernels (variants 5-10) stops after the first tile, the
+ *                         kernels (variants 5-10, 12-15) stops after the first tile, the
  *                         consumers' bounded waits give up and the call returns
  *                         MRCG_ERR_CUDA; the context stays usable.
  */
@@ -225,14 +229,17 @@ mrcg_status mrcg_fp64_fma_peak(double* tflops, double* ms);
  * capped for 2 / 4 blocks per SM, 7: as 5 with each warp's gathers issued
  * one tile ahead, 8: the whole CG iteration in one staged kernel, with the
  * residual norm by expansion and no step b; M_cg = I only; 9 / 10: staged as
- * 5 with registers capped for 2 / 3 blocks per SM and 11: plain loads, all
- * three gathering only p (one load per matrix entry) with beta formed by
- * expansion in step a and p = s + beta p done by their own step b; M_cg = I
- * or Jacobi), cfg[1] step-a grid (blocks), cfg[2] step-b grid,
+ * 5 with registers capped for 2 / 3 blocks per SM, 11: plain loads,
+ * 12 / 13: 9 / 10 with each warp's gathers issued one tile ahead, 14 / 15:
+ * tiles of 16 slices with two adjacent slices per consumer warp, registers
+ * capped for 2 / 1 blocks per SM; variants 9-15 gather only p (one load per
+ * matrix entry) with beta formed by expansion in step a and p = s + beta p
+ * done by their own step b; M_cg = I or Jacobi),
+ * cfg[1] step-a grid (blocks), cfg[2] step-b grid,
  * cfg[3] CG iterations per body of the device loop, cfg[4] k bucket of the
  * kernels (0, 8, 12, 16, 24 or 32), cfg[5] bytes per column index read by the
  * inner kernels (2: 16-bit col - row deltas, used when every delta fits; 4),
- * cfg[6] shared-memory stages of variants 5 to 10 (0 for the others).
+ * cfg[6] shared-memory stages of variants 5-10 and 12-15 (0 for the others).
  * cfg must hold 7 values. */
 mrcg_status mrcg_launch_config(mrcg_handle h, int32_t* cfg);
 

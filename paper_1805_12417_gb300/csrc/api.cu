@@ -498,13 +498,17 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
   // after the first tile, so its bounded waits run out and the solve reports
   // MRCG_ERR_CUDA (the GPU context stays usable)
   if (const char* e = getenv("MRCG_TEST_STALL")) g.stall_test = atoi(e) != 0;
-  // SELL entries of the largest tile of 8 slices (the staged step a's buffers)
+  if (const char* e = getenv("MRCG_PDL")) g.pdl = atoi(e) != 0;
+  // SELL entries of the largest tile of 8 (16) slices (the staged step a's buffers)
   for (int64_t s0 = 0; s0 < nslices; s0 += 8) g.tile_entries = std::max(g.tile_entries, sp[std::min(s0 + 8, nslices)] - sp[s0]);
+  for (int64_t s0 = 0; s0 < nslices; s0 += 16)
+    g.tile_entries16 = std::max(g.tile_entries16, sp[std::min(s0 + 16, nslices)] - sp[s0]);
   if (const char* e = getenv("MRCG_STAGES")) g.stages = std::max(2, std::min(8, atoi(e)));
-  const int64_t ntiles = (nslices + 7) / 8;
-  // step-a grid of a variant at bp blocks per SM (the staged variant is persistent over tiles)
+  const int64_t ntiles = (nslices + 7) / 8, ntiles16 = (nslices + 15) / 16;
+  // step-a grid of a variant at bp blocks per SM (the staged variants are persistent over tiles)
   auto grid_a = [&](const InnerGraphSpec& t, int bp) {
-    return is_staged_variant(t.var_a) ? clamp_grid(ntiles, bp) : clamp_grid(want_spmv, bp);
+    if (!is_staged_variant(t.var_a)) return clamp_grid(want_spmv, bp);
+    return clamp_grid(tile_slices(t.var_a) == 16 ? ntiles16 : ntiles, bp);
   };
   if (const char* va = getenv("MRCG_VAR_A")) g.var_a = std::min(kNumStepAVariants - 1, std::max(0, atoi(va)));
   int occ_a = 1, occ_b = 1;
@@ -614,7 +618,7 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
     InnerGraphSpec classic = g, onegather = g;
     double t_classic = 1e30, t_onegather = 1e30;
     ST(tune_family({0, 1, 2, 3, 4, 5, 6, 7}, &classic, &t_classic));
-    ST(tune_family({9, 10, 11, 12, 13}, &onegather, &t_onegather));
+    ST(tune_family({9, 10, 11, 12, 13, 14, 15}, &onegather, &t_onegather));
     InnerGraphSpec bestg = t_onegather < t_classic ? onegather : classic;
     const double best_pair = std::min(t_classic, t_onegather);
     // the one-kernel iteration (variant 8, M_cg = I) competes with the best

@@ -775,13 +775,14 @@ constexpr int kTileRows = kTileSlices * kSlice;
 constexpr int kStagedThreads = kThreads + 32;    // consumer warps + one producer warp
 constexpr int kMaxStages = 8;
 
-template <typename T, bool FUSED>
+template <typename T, bool FUSED, int TSL = kTileSlices>
 __device__ __forceinline__ void issue_tile(const CgArgs<T>& a, unsigned char* b, uint64_t* bar, int64_t t, int64_t e0,
                                            int64_t e1, uint64_t stream_pol) {
+  constexpr int TR = TSL * kSlice;  // rows of a tile
   const bool jac = !FUSED && a.dinv != nullptr;
   const int ib = a.col16 ? 2 : 4;
   const char* idx = a.col16 ? (const char*)a.col16 : (const char*)a.col;
-  const int64_t s0 = t * kTileSlices, s1 = min(s0 + kTileSlices, a.nslices);
+  const int64_t s0 = t * TSL, s1 = min(s0 + TSL, a.nslices);
   const int64_t row0 = s0 * kSlice;
   const uint32_t rb = (uint32_t)((s1 - s0) * kSlice * (int64_t)sizeof(T));
   const uint32_t ne = (uint32_t)(e1 - e0);
@@ -793,7 +794,7 @@ __device__ __forceinline__ void issue_tile(const CgArgs<T>& a, unsigned char* b,
     bulk_g2s_hint(b + a.off_col, idx + e0 * ib, ne * (uint32_t)ib, bar, stream_pol);
   }
   for (int l = 0; l < a.k; ++l)
-    bulk_g2s_hint(b + a.off_v + (size_t)l * kTileRows * sizeof(T), a.V + (size_t)l * a.n_pad + row0, rb, bar,
+    bulk_g2s_hint(b + a.off_v + (size_t)l * TR * sizeof(T), a.V + (size_t)l * a.n_pad + row0, rb, bar,
                   stream_pol);
   if constexpr (FUSED) {
     bulk_g2s(b + a.off_s, a.r + row0, rb, bar);
@@ -811,7 +812,7 @@ __device__ __forceinline__ void issue_tile(const CgArgs<T>& a, unsigned char* b,
 // consumer warp has left it (tile offsets fetched one tile ahead), then waits
 // (bounded) until no copy it issued is still writing this block's shared
 // memory.  Tile i of this block is tile blockIdx.x + i * gridDim.x.
-template <typename T, bool FUSED>
+template <typename T, bool FUSED, int TSL = kTileSlices>
 __device__ __forceinline__ void stage_producer(const CgArgs<T>& a, unsigned char* stage_mem, uint64_t* full,
                                                uint64_t* empty, int* stalled, int64_t ntl, int nst) {
   const int64_t G = gridDim.x;
@@ -819,8 +820,8 @@ __device__ __forceinline__ void stage_producer(const CgArgs<T>& a, unsigned char
   int64_t issued = 0;
   int64_t e0 = 0, e1 = 0;
   if (ntl > 0) {
-    e0 = a.slice_ptr[(int64_t)blockIdx.x * kTileSlices];
-    e1 = a.slice_ptr[min((int64_t)(blockIdx.x + 1) * kTileSlices, a.nslices)];
+    e0 = a.slice_ptr[(int64_t)blockIdx.x * TSL];
+    e1 = a.slice_ptr[min((int64_t)(blockIdx.x + 1) * TSL, a.nslices)];
   }
   // stage st of tile i = i mod nst, and the parity of its use (i / nst) & 1,
   // kept incrementally (no integer division in the loop)
@@ -832,11 +833,11 @@ __device__ __forceinline__ void stage_producer(const CgArgs<T>& a, unsigned char
     if (i >= nst && !mbar_wait_or_abort(&empty[st], ph ^ 1u, stalled)) break;
     const int64_t c0 = e0, c1 = e1;
     if (i + 1 < ntl) {
-      e0 = a.slice_ptr[(t + G) * kTileSlices];
-      e1 = a.slice_ptr[min((t + G + 1) * kTileSlices, a.nslices)];
+      e0 = a.slice_ptr[(t + G) * TSL];
+      e1 = a.slice_ptr[min((t + G + 1) * TSL, a.nslices)];
     }
     fence_proxy_async_smem();
-    issue_tile<T, FUSED>(a, stage_mem + (size_t)st * a.stage_bytes, &full[st], t, c0, c1, stream_pol);
+    issue_tile<T, FUSED, TSL>(a, stage_mem + (size_t)st * a.stage_bytes, &full[st], t, c0, c1, stream_pol);
     ++issued;
     if (++st == nst) {
       st = 0;
@@ -1631,6 +1632,263 @@ __global__ void __launch_bounds__(kStagedThreads, MB) cg_step_a_pg_staged_kernel
   pg_reduce<T, KB, kStagedThreads / 32>(a, S, pq, sq, qdq, wq, cl);
 }
 
+// Variants 14 / 15: the one-gather step a on tiles of 16 slices (512 rows),
+// each consumer warp taking two adjacent slices of every tile.  A warp's
+// per-tile work (the stage wait and release, the tile offsets) is shared by
+// two slices, the gathers of both slices are in flight together, and the
+// coefficients c stay in registers.  Registers capped for MB = 2 / 1 blocks
+// per SM (FP32 with two stages of about 46 KB; FP64, or deeper rings).
+
+// A p of two slice rows (entries in groups of 8, the 16 gathers of a group in
+// flight before the products; missing entries contribute 0 * 0)
+template <typename T, typename I>
+__device__ __forceinline__ void pg_row_pair(const T* va, const I* ca, int rowa, int wa, const T* vb, const I* cb,
+                                            int rowb, int wb, bool delta, const T* __restrict__ pv, T& apa, T& apb) {
+  const int w = wa > wb ? wa : wb;
+  for (int j0 = 0; j0 < w; j0 += 8) {
+    T xa[8], xb[8];
+    int ja[8], jb[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const bool ia = j0 + j < wa, ib = j0 + j < wb;
+      xa[j] = ia ? va[(j0 + j) * kSlice] : (T)0;
+      ja[j] = ia ? (delta ? rowa : 0) + (int)ca[(j0 + j) * kSlice] : rowa;
+      xb[j] = ib ? vb[(j0 + j) * kSlice] : (T)0;
+      jb[j] = ib ? (delta ? rowb : 0) + (int)cb[(j0 + j) * kSlice] : rowb;
+    }
+    T ga[8], gb[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      ga[j] = (j0 + j < wa) ? __ldg(pv + ja[j]) : (T)0;
+      gb[j] = (j0 + j < wb) ? __ldg(pv + jb[j]) : (T)0;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      apa += xa[j] * ga[j];
+      apb += xb[j] * gb[j];
+    }
+  }
+}
+
+// Producer of variants 14 / 15.  A stage is filled in two parts: the static
+// operands (A's values and indices, V_hat's rows, the Jacobi diagonal), which
+// no kernel of the iteration writes, and the Krylov vectors of the own rows
+// (s, p).  The static parts of the first stages are issued before the grid
+// dependency wait, so behind a programmatic edge they stream in while the
+// previous step b still runs.
+template <typename T, int TSL>
+__device__ __forceinline__ void pg2_issue_static(const CgArgs<T>& a, unsigned char* b, uint64_t* bar, int64_t t,
+                                                 int64_t e0, int64_t e1, uint64_t pol) {
+  constexpr int TR = TSL * kSlice;
+  const int ib = a.col16 ? 2 : 4;
+  const char* idx = a.col16 ? (const char*)a.col16 : (const char*)a.col;
+  const int64_t s0 = t * TSL, s1 = min(s0 + TSL, a.nslices);
+  const int64_t row0 = s0 * kSlice;
+  const uint32_t rb = (uint32_t)((s1 - s0) * kSlice * (int64_t)sizeof(T));
+  const uint32_t ne = (uint32_t)(e1 - e0);
+  const bool jac = a.dinv != nullptr;
+  mbar_arrive_expect_tx(bar, ne * (uint32_t)(sizeof(T) + ib) + (uint32_t)(a.k + 2 + (jac ? 1 : 0)) * rb);
+  if (ne > 0) {
+    bulk_g2s_hint(b, a.val + e0, ne * (uint32_t)sizeof(T), bar, pol);
+    bulk_g2s_hint(b + a.off_col, idx + e0 * ib, ne * (uint32_t)ib, bar, pol);
+  }
+  for (int l = 0; l < a.k; ++l)
+    bulk_g2s_hint(b + a.off_v + (size_t)l * TR * sizeof(T), a.V + (size_t)l * a.n_pad + row0, rb, bar, pol);
+  if (jac) bulk_g2s(b + a.off_d, a.dinv + row0, rb, bar);
+}
+
+template <typename T, int TSL>
+__device__ __forceinline__ void pg2_issue_vectors(const CgArgs<T>& a, unsigned char* b, uint64_t* bar, int64_t t) {
+  const int64_t s0 = t * TSL, s1 = min(s0 + TSL, a.nslices);
+  const int64_t row0 = s0 * kSlice;
+  const uint32_t rb = (uint32_t)((s1 - s0) * kSlice * (int64_t)sizeof(T));
+  bulk_g2s(b + a.off_s, a.s + row0, rb, bar);
+  bulk_g2s(b + a.off_p, a.p_old + row0, rb, bar);
+}
+
+// returns false when the solve is no longer running (the block then leaves
+// once its copies have landed)
+template <typename T, int TSL>
+__device__ __forceinline__ void pg2_producer(const CgArgs<T>& a, unsigned char* stage_mem, uint64_t* full,
+                                             uint64_t* empty, int* stalled, int64_t ntl, int nst, bool run) {
+  const int64_t G = gridDim.x;
+  const uint64_t pol = l2_evict_first_policy();
+  const int64_t pre = min(ntl, (int64_t)(a.stall_test ? 1 : nst));  // stages whose static part is in flight
+  // the vectors of the prefetched stages (every thread has passed the grid dependency wait)
+  for (int64_t i = 0; i < pre; ++i) {
+    fence_proxy_async_smem();
+    pg2_issue_vectors<T, TSL>(a, stage_mem + (size_t)i * a.stage_bytes, &full[i], blockIdx.x + i * G);
+  }
+  int64_t issued = pre;
+  if (run) {
+    int st = (int)(pre % nst);
+    uint32_t ph = (uint32_t)((pre / nst) & 1);
+    int64_t t = blockIdx.x + pre * G;
+    int64_t e0 = 0, e1 = 0;
+    if (pre < ntl) {
+      e0 = a.slice_ptr[t * TSL];
+      e1 = a.slice_ptr[min((t + 1) * TSL, a.nslices)];
+    }
+    for (int64_t i = pre; i < ntl; ++i, t += G) {
+      if (a.stall_test) break;
+      if (!mbar_wait_or_abort(&empty[st], ph ^ 1u, stalled)) break;
+      const int64_t c0 = e0, c1 = e1;
+      if (i + 1 < ntl) {
+        e0 = a.slice_ptr[(t + G) * TSL];
+        e1 = a.slice_ptr[min((t + G + 1) * TSL, a.nslices)];
+      }
+      fence_proxy_async_smem();
+      unsigned char* b = stage_mem + (size_t)st * a.stage_bytes;
+      pg2_issue_static<T, TSL>(a, b, &full[st], t, c0, c1, pol);
+      pg2_issue_vectors<T, TSL>(a, b, &full[st], t);
+      ++issued;
+      if (++st == nst) {
+        st = 0;
+        ph ^= 1u;
+      }
+    }
+  }
+  for (int64_t j = issued > nst ? issued - nst : 0; j < issued; ++j)
+    mbar_wait(&full[j % nst], (uint32_t)((j / nst) & 1));
+}
+
+template <typename T, int KB, int MB>
+__global__ void __launch_bounds__(kStagedThreads, MB) cg_step_a_pg2_kernel(CgArgs<T> a) {
+  constexpr int KS = KB > 0 ? KB : 1;
+  constexpr int TSL = 2 * kTileSlices;  // slices of a tile
+  constexpr int TR = TSL * kSlice;      // rows of a tile
+  extern __shared__ __align__(128) unsigned char stage_mem[];
+  __shared__ __align__(8) uint64_t full[kMaxStages];
+  __shared__ __align__(8) uint64_t empty[kMaxStages];
+  __shared__ int stalled;
+  __shared__ T cls[KS];
+  CgState& S = a.st->cg;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool jac = a.dinv != nullptr;
+  const int nst = a.stages;
+  const int64_t ntiles = (a.nslices + TSL - 1) / TSL;
+  const int64_t ntl = (int64_t)blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t G = gridDim.x;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < nst; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], kTileSlices);
+    }
+    stalled = 0;
+    mbar_init_fence();
+  }
+  __syncthreads();
+  if (warp == kTileSlices && lane == 0) {  // static operands of the first stages
+    const uint64_t pol = l2_evict_first_policy();
+    const int64_t pre = min(ntl, (int64_t)(a.stall_test ? 1 : nst));
+    for (int64_t i = 0; i < pre; ++i) {
+      const int64_t t = blockIdx.x + i * G;
+      pg2_issue_static<T, TSL>(a, stage_mem + (size_t)i * a.stage_bytes, &full[i], t, a.slice_ptr[t * TSL],
+                               a.slice_ptr[min((t + 1) * TSL, a.nslices)], pol);
+    }
+  }
+  grid_dependency_wait();  // the previous step b's p, s and scalars are visible from here on
+  const bool run = S.done == kRunning;
+  if (!run) {  // the producer lets its copies land before the block leaves
+    if (warp == kTileSlices && lane == 0) pg2_producer<T, TSL>(a, stage_mem, full, empty, &stalled, ntl, nst, false);
+    return;
+  }
+  if (threadIdx.x < KS) cls[threadIdx.x] = ((int)threadIdx.x < a.k) ? c_of(S, threadIdx.x, T(0)) : (T)0;
+  __syncthreads();
+  T cl[KS];
+#pragma unroll
+  for (int l = 0; l < KS; ++l) cl[l] = cls[l];
+  T pq = 0, sq = 0, qdq = 0;
+  T wq[KS];
+#pragma unroll
+  for (int l = 0; l < KS; ++l) wq[l] = 0;
+  if (warp == kTileSlices) {
+    if (lane == 0) pg2_producer<T, TSL>(a, stage_mem, full, empty, &stalled, ntl, nst, true);
+  } else {
+    const T* __restrict__ pv = a.p_old;
+    const bool d16 = a.col16 != nullptr;
+    // entry offsets of the tile and of this warp's slices 2 warp, 2 warp + 1
+    // (one tile ahead); a slice past the end has no entries
+    int64_t c_t0 = 0, c_a0 = 0, c_a1 = 0, c_b1 = 0;
+    auto fetch = [&](int64_t tt) {
+      const int64_t sa = tt * TSL + 2 * warp;
+      c_t0 = a.slice_ptr[tt * TSL];
+      c_a0 = a.slice_ptr[min(sa, a.nslices)];
+      c_a1 = a.slice_ptr[min(sa + 1, a.nslices)];
+      c_b1 = a.slice_ptr[min(sa + 2, a.nslices)];
+    };
+    if (ntl > 0) fetch(blockIdx.x);
+    int st = 0;
+    uint32_t ph = 0;
+    int64_t t = blockIdx.x;
+    for (int64_t i = 0; i < ntl; ++i, t += G) {
+      const int64_t t0 = c_t0, a0 = c_a0, a1 = c_a1, b1 = c_b1;
+      if (i + 1 < ntl) fetch(t + G);
+      if (!mbar_wait_or_abort(&full[st], ph, &stalled)) break;
+      const int64_t sla = t * TSL + 2 * warp;
+      if (sla < a.nslices) {
+        const unsigned char* b = stage_mem + (size_t)st * a.stage_bytes;
+        const bool has_b = sla + 1 < a.nslices;
+        const int wa = (int)((a1 - a0) >> 5), wb = (int)((b1 - a1) >> 5);
+        const int offa = (int)(a0 - t0) + lane, offb = (int)(a1 - t0) + lane;
+        const int ra = 2 * warp * kSlice + lane, rb = ra + kSlice;  // rows within the tile
+        const int rowa = (int)(sla * kSlice) + lane, rowb = rowa + kSlice;
+        const T* vals = reinterpret_cast<const T*>(b);
+        const T* ps = reinterpret_cast<const T*>(b + a.off_p);
+        const T* rs = reinterpret_cast<const T*>(b + a.off_s);
+        const T* ds = reinterpret_cast<const T*>(b + a.off_d);
+        const T* vt = reinterpret_cast<const T*>(b + a.off_v);
+        T apa = 0, apb = 0;
+        if (d16) {
+          const int16_t* cc = reinterpret_cast<const int16_t*>(b + a.off_col);
+          pg_row_pair<T, int16_t>(vals + offa, cc + offa, rowa, wa, vals + offb, cc + offb, rowb, wb, true, pv, apa,
+                                  apb);
+        } else {
+          const int32_t* cc = reinterpret_cast<const int32_t*>(b + a.off_col);
+          pg_row_pair<T, int32_t>(vals + offa, cc + offa, rowa, wa, vals + offb, cc + offb, rowb, wb, false, pv, apa,
+                                  apb);
+        }
+        const T pa = ps[ra], rva = rs[ra];
+        const T pb = has_b ? ps[rb] : (T)0, rvb = has_b ? rs[rb] : (T)0;
+        const T da = jac ? ds[ra] : (T)1;
+        const T db = (jac && has_b) ? ds[rb] : (T)1;
+        const T apsa = jac ? da * apa : apa;  // (M_cg^{-1} A p)_row
+        const T apsb = has_b ? (jac ? db * apb : apb) : (T)0;
+        T qa = apa, qb = apb;
+#pragma unroll
+        for (int l = 0; l < KB; ++l)
+          if (l < a.k) {
+            const T v1 = vt[l * TR + ra];
+            const T v2 = has_b ? vt[l * TR + rb] : (T)0;
+            qa += v1 * cl[l];
+            qb += v2 * cl[l];
+            wq[l] += v1 * apsa;
+            wq[l] += v2 * apsb;
+          }
+        a.q[rowa] = qa;
+        pq += pa * qa;
+        sq += (jac ? da * rva : rva) * qa;
+        qdq += jac ? da * qa * qa : qa * qa;
+        if (has_b) {
+          a.q[rowb] = qb;
+          pq += pb * qb;
+          sq += (jac ? db * rvb : rvb) * qb;
+          qdq += jac ? db * qb * qb : qb * qb;
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[st]);
+      if (++st == nst) {
+        st = 0;
+        ph ^= 1u;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && stalled) *(volatile int*)&S.done = kStall;
+  pg_reduce<T, KB, kStagedThreads / 32>(a, S, pq, sq, qdq, wq, cls);
+}
+
 // Variant 11: the same arithmetic with plain loads, one warp per SELL slice,
 // grid-stride (matrices whose tiles do not fit two shared-memory stages);
 // registers capped for 4 blocks per SM in FP32, 2 in FP64 (no spills)
@@ -1674,6 +1932,7 @@ template <typename T, int KB>
 __global__ void __launch_bounds__(kThreads) cg_step_b_pg_kernel(CgArgs<T> a) {
   constexpr int W = V16<T>::W;
   CgState& S = a.st->cg;
+  grid_dependency_wait();  // step a's alpha, beta, q (launched early behind a programmatic edge)
   if (S.done != kRunning) return;
   const T alpha = alpha_of(S, T(0));
   const T beta = beta_of(S, T(0));
@@ -1921,21 +2180,23 @@ struct StageGeo {
 
 StageGeo stage_geo(const InnerGraphSpec& spec) {
   auto up = [](int64_t x) { return (x + 127) / 128 * 128; };
-  const int64_t w = spec.fp32 ? 4 : 8, ib = spec.A.col16 ? 2 : 4, E = spec.tile_entries;
+  const int64_t w = spec.fp32 ? 4 : 8, ib = spec.A.col16 ? 2 : 4;
+  const int64_t TR = (int64_t)tile_slices(spec.var_a) * kSlice;  // rows of the variant's tile
+  const int64_t E = tile_slices(spec.var_a) == 16 ? spec.tile_entries16 : spec.tile_entries;
   StageGeo g;
   int64_t o = up(E * w);
   g.off_col = (int)o;
   o += up(E * ib);
   g.off_v = (int)o;
-  o += (int64_t)spec.k * kTileRows * w;
+  o += (int64_t)spec.k * TR * w;
   g.off_s = (int)o;
-  o += kTileRows * w;
+  o += TR * w;
   g.off_p = (int)o;
-  o += kTileRows * w;
+  o += TR * w;
   g.off_d = (int)o;
-  if (spec.dinv || spec.var_a == 8) o += kTileRows * w;  // M_cg^{-1} (Jacobi) or q_{i-1} (one-kernel iteration)
+  if (spec.dinv || spec.var_a == 8) o += TR * w;  // M_cg^{-1} (Jacobi) or q_{i-1} (one-kernel iteration)
   g.off_z = (int)o;
-  if (spec.var_a == 8) o += kTileRows * w;  // z (one-kernel iteration)
+  if (spec.var_a == 8) o += TR * w;  // z (one-kernel iteration)
   g.bytes = o > (1 << 30) ? (1 << 30) : (int)o;
   return g;
 }
@@ -2011,6 +2272,8 @@ const void* step_a_fn(int var) {
     case 11: return (const void*)cg_step_a_pg_kernel<T, KB>;
     case 12: return (const void*)cg_step_a_pg_staged_kernel<T, KB, 2, true>;
     case 13: return (const void*)cg_step_a_pg_staged_kernel<T, KB, 3, true>;
+    case 14: return (const void*)cg_step_a_pg2_kernel<T, KB, 2>;
+    case 15: return (const void*)cg_step_a_pg2_kernel<T, KB, 1>;
     case 1: return (const void*)cg_step_a_kernel<T, KB, 1>;
     case 2: return (const void*)cg_step_a_kernel<T, KB, 2>;
     case 3: return (const void*)cg_step_a_kernel<T, KB, 3>;
@@ -2151,9 +2414,28 @@ cudaError_t build_graph_t(const InnerGraphSpec& spec, cudaGraph_t* out_graph) {
     if ((e = cudaGraphAddNode(&n_loop, g, &n_init, nullptr, 1, &cp))) goto fail;
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     cudaGraphNode_t prev = nullptr;
+    // variants 14 / 15 with the one-gather step b: programmatic edges (the
+    // successor may start once every block of its predecessor has started; it
+    // waits for the predecessor's results with grid_dependency_wait), so a
+    // step a streams its static operands while the previous step b finishes
+    const bool pdl = spec.pdl && (spec.var_a == 14 || spec.var_a == 15) && spec.ilu.nblk == 0 && !spec.dsmw;
+    cudaGraphEdgeData ed = {};
+    ed.from_port = cudaGraphKernelNodePortLaunchCompletion;
+    ed.type = cudaGraphDependencyTypeProgrammatic;
     for (int it = 0; it < spec.unroll; ++it) {
       void* aa[] = {&a[it & 1]};
       cudaGraphNode_t na, nb;
+      if (pdl) {
+        if ((e = add_kernel(body, &na, nullptr, 0, step_a_fn<T, KB>(spec.var_a), spec.grid_spmv,
+                            step_a_block(spec), aa, smem_a)))
+          goto fail;
+        if (prev && (e = cudaGraphAddDependencies(body, &prev, &na, &ed, 1))) goto fail;
+        if ((e = add_kernel(body, &nb, nullptr, 0, step_b_fn<T, KB>(spec), spec.grid_stream_b, kThreads, aa)))
+          goto fail;
+        if ((e = cudaGraphAddDependencies(body, &na, &nb, &ed, 1))) goto fail;
+        prev = nb;
+        continue;
+      }
       if ((e = add_kernel(body, &na, prev ? &prev : nullptr, prev ? 1 : 0, step_a_fn<T, KB>(spec.var_a),
                           spec.grid_spmv, step_a_block(spec), aa, smem_a)))
         goto fail;

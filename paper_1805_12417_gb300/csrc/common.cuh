@@ -308,6 +308,12 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 // make mbarrier initialisation visible to the copy engine
 __device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
+// Programmatic dependent launch: a kernel launched behind a programmatic
+// graph edge may start while its predecessor still runs; it waits here (all
+// of the predecessor's blocks finished, their memory visible) before reading
+// anything the predecessor writes.  Without such an edge this returns at once.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // order this thread's earlier shared-memory accesses before later bulk copies into shared memory
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 

@@ -39,16 +39,20 @@ struct InnerGraphSpec {
                  // matrix entry (p explicit, beta by expansion in step a; M_cg = I or Jacobi);
                  // 12 / 13: 9 / 10 with each warp's gathers issued one tile ahead)
   IluArgs ilu;               // block-Jacobi ILU(0) M_cg (ilu.nblk > 0): step b solves with the factors
-  int64_t tile_entries = 0;  // most SELL entries in one tile of 8 slices (sizes the staged variant's buffers)
+  int64_t tile_entries = 0;    // most SELL entries in one tile of 8 slices (sizes the staged variants' buffers)
+  int64_t tile_entries16 = 0;  // the same for tiles of 16 slices (variants 14, 15)
+  bool pdl = true;             // programmatic edges between the inner kernels of variants 14, 15 (MRCG_PDL=0: off)
   int stages = 3;            // staged variant: shared-memory stages per block
   bool stall_test = false;   // test hook: the staged producer issues only the first tile
 };
 
 // step-a variants whose operands are staged in shared memory by bulk copies
-inline bool is_staged_variant(int var) { return (var >= 5 && var <= 10) || var == 12 || var == 13; }
+inline bool is_staged_variant(int var) { return (var >= 5 && var <= 10) || (var >= 12 && var <= 15); }
 // step-a variants 9-13: one gather per matrix entry, p kept explicit (their own step b)
-inline bool is_pg_variant(int var) { return var >= 9 && var <= 13; }
-constexpr int kNumStepAVariants = 14;
+inline bool is_pg_variant(int var) { return var >= 9 && var <= 15; }
+// slices of a staged variant's tile (variants 14, 15: two per consumer warp)
+inline int tile_slices(int var) { return var == 14 || var == 15 ? 16 : 8; }
+constexpr int kNumStepAVariants = 16;
 
 cudaError_t build_inner_graph(const InnerGraphSpec& spec, cudaGraph_t* graph);
 // the same inner solve with the loop driven from the host (profiling mode)

@@ -42,7 +42,7 @@ def main(argv=None):
                          "inner loop driven from the host (MRCG_INNER_LOOP=host), so a profiler sees their kernels")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--iters", type=int, default=3)
-    ap.add_argument("--var-a", type=int, default=None, help="step-a kernel variant (0-8)")
+    ap.add_argument("--var-a", type=int, default=None, help="step-a kernel variant (0-15)")
     ap.add_argument("--bpsm-a", type=int, default=None, help="step-a blocks per SM")
     ap.add_argument("--bpsm-b", type=int, default=None, help="step-b blocks per SM")
     a = ap.parse_args(argv)

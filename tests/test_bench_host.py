@@ -24,6 +24,8 @@ import bench  # noqa: E402
     (11, "cg_step_a_pg_kernel<float, 12>"),
     (12, "cg_step_a_pg_staged_kernel<float, 12, 2, 1>"),
     (13, "cg_step_a_pg_staged_kernel<float, 12, 3, 1>"),
+    (14, "cg_step_a_pg2_kernel<float, 12, 2>"),
+    (15, "cg_step_a_pg2_kernel<float, 12, 1>"),
 ])
 def test_kernel_name_per_variant(var, name):
     assert bench.step_a_kernel_name({"step_a_variant": var, "k_bucket": 12}) == name

@@ -25,9 +25,9 @@ if not torch.cuda.is_available():  # pragma: no cover - collected on CPU hosts t
 import paper_1805_12417_gb300 as m  # noqa: E402
 
 
-@pytest.mark.parametrize("var", [5, 7], ids=["staged", "pipelined"])
+@pytest.mark.parametrize("var", [5, 7, 14], ids=["staged", "pipelined", "twoslice"])
 def test_stalled_copies_report_an_error_and_leave_the_context_usable(var, monkeypatch):
-    p = small_3d()  # 6 tiles of 8 slices: every block has a second tile to wait for
+    p = small_3d()  # 6 tiles of 8 slices (3 of 16): block 0 has a second tile to wait for
     y = np.random.default_rng(2).standard_normal(p.n)
     monkeypatch.setenv("MRCG_VAR_A", str(var))
     monkeypatch.setenv("MRCG_STAGES", "2")

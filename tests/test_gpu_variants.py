@@ -34,15 +34,16 @@ import paper_1805_12417_gb300 as m  # noqa: E402
 DEV = torch.device("cuda:0")
 
 SHAPES = [(0, None), (1, None), (2, None), (3, None), (4, None), (5, 2), (5, 3), (5, 4), (6, 2), (6, 3), (7, 2),
-          (7, 3), (9, 2), (9, 3), (10, 2), (10, 4), (11, None), (12, 2), (12, 3), (13, 3)]
+          (7, 3), (9, 2), (9, 3), (10, 2), (10, 4), (11, None), (12, 2), (12, 3), (13, 3), (14, 2), (14, 3),
+          (15, 2), (15, 3)]
 SHAPE_IDS = ["v0", "v1", "v2", "v3", "v4", "staged2", "staged3", "staged4", "staged4bpsm_2", "staged4bpsm_3",
              "pipelined2", "pipelined3", "onegather_staged2", "onegather_staged3", "onegather_staged3bpsm_2",
              "onegather_staged3bpsm_4", "onegather_plain", "onegather_pipelined2", "onegather_pipelined3",
-             "onegather_pipelined3bpsm"]
+             "onegather_pipelined3bpsm", "twoslice2", "twoslice3", "twoslice_1bpsm2", "twoslice_1bpsm3"]
 
 
 def is_staged(var):
-    return 5 <= var <= 10 or var in (12, 13)
+    return 5 <= var <= 10 or 12 <= var <= 15
 
 
 @pytest.fixture
@@ -67,7 +68,8 @@ def _check_cfg(g, var, stages, idx_bytes=None):
         assert cfg["index_bytes"] == idx_bytes
 
 
-def _inner_vs_oracle(p, prec, mcg, tol, seed, var, stages, idx_bytes=None, V=None, lam=None, sysargs=None):
+def _inner_vs_oracle(p, prec, mcg, tol, seed, var, stages, idx_bytes=None, V=None, lam=None, sysargs=None,
+                     expect_var=None):
     s = O.System(*sysargs, V, lam) if sysargs is not None else O.System.from_problem(p)
     n = sysargs[0].shape[0] - 1 if sysargs is not None else p.n
     y = np.random.default_rng(seed).standard_normal(n)
@@ -78,7 +80,7 @@ def _inner_vs_oracle(p, prec, mcg, tol, seed, var, stages, idx_bytes=None, V=Non
     else:
         g = m.Solver.from_problem(p, precision=prec, inner_prec=mcg)
     with g:
-        _check_cfg(g, var, stages, idx_bytes)
+        _check_cfg(g, var if expect_var is None else expect_var, stages, idx_bytes)
         z, st, it = g.inner_solve(y, inner_tol=tol)
     assert st == m.OK
     if prec == m.FP64:
@@ -99,12 +101,15 @@ def test_inner_variants_small_3d(shape_env, var, stages, prec, mcg):
 
 @pytest.mark.parametrize("k", [0, 1, 10, 13, 17, 32])
 @pytest.mark.parametrize("var,stages", [(1, None), (3, None), (5, 2), (6, 2), (7, 2), (9, 2), (10, 2), (11, None),
-                                       (12, 2), (13, 2)],
+                                       (12, 2), (13, 2), (14, 2), (15, 2)],
                          ids=["v1", "v3", "staged2", "staged4bpsm", "pipelined2", "onegather_staged2",
                               "onegather_staged3bpsm", "onegather_plain", "onegather_pipelined2",
-                              "onegather_pipelined3bpsm"])
+                              "onegather_pipelined3bpsm", "twoslice2", "twoslice_1bpsm2"])
 def test_inner_variants_k_buckets(shape_env, k, var, stages):
-    """Every k bucket of the kernels (FP64 stages of k = 32 hold 86 KB, so two fit a block)."""
+    """Every k bucket of the kernels (FP64 stages of k = 32 hold 86 KB on tiles
+    of 8 slices, so two fit a block; on tiles of 16 slices FP64 stages of
+    k >= 17 exceed half the block's shared memory and the solver falls back to
+    variant 0, with the same answers)."""
     p = shifted_laplacian_problem("t", (13, 11, 9), max(k, 1), seed=k) if k else None
     shape_env(var, stages)
     if p is None:
@@ -112,7 +117,8 @@ def test_inner_variants_k_buckets(shape_env, k, var, stages):
         rp, ci, va = laplacian_csr((13, 11, 9), sigma=-0.5)  # SPD: M_mr = A
         _inner_vs_oracle(None, m.FP64, m.MCG_IDENTITY, 1e-8, 1, var, stages, sysargs=(rp, ci, va))
         return
-    _inner_vs_oracle(p, m.FP64, m.MCG_IDENTITY, 1e-8, k, var, stages)
+    fp64_var = 0 if var in (14, 15) and k >= 17 else None
+    _inner_vs_oracle(p, m.FP64, m.MCG_IDENTITY, 1e-8, k, var, stages, expect_var=fp64_var)
     _inner_vs_oracle(p, m.MIXED_FP32, m.MCG_IDENTITY, 1e-4, k, var, stages)
 
 
@@ -154,10 +160,10 @@ def test_staged_falls_back_when_stages_do_not_fit(shape_env, var):
 
 
 @pytest.mark.parametrize("var,stages", [(0, None), (5, 3), (6, 2), (7, 3), (9, 3), (10, 2), (11, None), (12, 3),
-                                       (13, 2)],
+                                       (13, 2), (14, 2), (15, 2)],
                          ids=["v0", "staged3", "staged4bpsm", "pipelined3", "onegather_staged3",
                               "onegather_staged3bpsm", "onegather_plain", "onegather_pipelined3",
-                              "onegather_pipelined3bpsm"])
+                              "onegather_pipelined3bpsm", "twoslice2", "twoslice_1bpsm2"])
 def test_variants_full_solve_small(shape_env, var, stages):
     """A whole MINRES-CG solve on every step-a path agrees with the oracle's."""
     shape_env(var, stages)
@@ -252,11 +258,11 @@ def test_one_kernel_iteration_full_solves(shape_env):
 
 
 
-# ---------------------------------------------------------------- variants 9-11: one gather per matrix entry
+# ---------------------------------------------------------------- variants 9-15: one gather per matrix entry
 
 def test_one_gather_falls_back_with_smw(shape_env):
-    """Variants 9-13 cover M_cg = I and Jacobi; the MINRES-CG* M_cg keeps its own kernels."""
-    for var in (9, 11, 12):
+    """Variants 9-15 cover M_cg = I and Jacobi; the MINRES-CG* M_cg keeps its own kernels."""
+    for var in (9, 11, 12, 14):
         shape_env(var, 2)
         with m.Solver.from_problem(small_3d(), inner_prec=m.MCG_SMW) as g:
             assert m.launch_config(g.h)["step_a_variant"] == 0
@@ -279,13 +285,15 @@ def test_one_gather_budget_returns_mth_iterate(shape_env, prec):
             assert np.linalg.norm(z - zr) <= bar * np.linalg.norm(zr)
 
 
-def test_one_gather_full_size_mixed(shape_env):
-    """128^3 shifted Laplacian, mixed precision, one-gather staged step a: the
-    FP64 true residual reaches the benchmark tolerance and x matches x*."""
-    shape_env(9, 2)
+@pytest.mark.parametrize("var", [9, 14], ids=["onegather", "twoslice"])
+def test_one_gather_full_size_mixed(shape_env, var):
+    """128^3 shifted Laplacian, mixed precision, one-gather staged step a (8-
+    and 16-slice tiles): the FP64 true residual reaches the benchmark tolerance
+    and x matches x*."""
+    shape_env(var, 2)
     p = lap3d_128_k10()
     with m.Solver.from_problem(p, precision=m.MIXED_FP32) as g:
-        _check_cfg(g, 9, 2)
+        _check_cfg(g, var, 2)
         x = torch.zeros(p.n, dtype=torch.float64, device=DEV)
         _, info = g.solve(torch.from_numpy(p.b).to(DEV), x, outer_tol=1e-10, inner_tol=1e-3)
     x = x.cpu().numpy()
@@ -296,7 +304,8 @@ def test_one_gather_full_size_mixed(shape_env):
 
 # ---------------------------------------------------------------- a CG step that removes almost all of the residual
 
-@pytest.mark.parametrize("var,stages", [(8, 2), (9, 2), (12, 3)], ids=["one_kernel", "onegather", "onegather_pipelined"])
+@pytest.mark.parametrize("var,stages", [(8, 2), (9, 2), (12, 3), (14, 2)],
+                         ids=["one_kernel", "onegather", "onegather_pipelined", "twoslice"])
 @pytest.mark.parametrize("prec", [m.FP64, m.MIXED_FP32], ids=["fp64", "mixed"])
 def test_sharp_single_step_reduction(shape_env, var, stages, prec):
     """A = diag(2 + 1e-3 u): the first CG step cuts ||r|| by about 1e-4, so the
