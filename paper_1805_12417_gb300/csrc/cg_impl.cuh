@@ -1381,7 +1381,24 @@ __device__ __forceinline__ void pg_reduce(const CgArgs<T>& a, CgState& S, T pq, 
       const int e = threadIdx.x + j * NT;
       greg[j] = (e < kk) ? __ldcg(a.gram + e) : 0.0;
     }
+    // the state the tail updates, loaded before the partial sums so that its
+    // round trips overlap theirs: direction l's V^T s, V^T p and 2|lambda_l|
+    // by thread l, rho and the status by thread 0
+    const int l = threadIdx.x;
+    double u_l = 0.0, t_l = 0.0, lam_l = 0.0, rho = 0.0;
+    int running = 0;
+    if (l < a.k) {
+      u_l = S.u[l];
+      t_l = S.t[l];
+      lam_l = S.lam2[l];
+    }
+    if (l == 0) {
+      rho = S.rho;
+      running = *(volatile int*)&S.done == kRunning;
+    }
     __shared__ double tot[KB + 3];
+    __shared__ double ab[2];
+    __shared__ int go;
     final_sums(a.partials, a.k + 3, tot);
 #pragma unroll
     for (int j = 0; j < GPT; ++j) {
@@ -1389,42 +1406,52 @@ __device__ __forceinline__ void pg_reduce(const CgArgs<T>& a, CgState& S, T pq, 
       if (e < kk) gs[e] = greg[j];
     }
     __syncthreads();
-    const int l = threadIdx.x;
+    double vq = 0.0;
     if (l < a.k) {  // V^T M_cg^{-1} q = V^T M_cg^{-1} A p + G c
-      double g = tot[l + 3];
+      vq = tot[l + 3];
 #pragma unroll 8
       for (int m = 0; m < KB; ++m)
-        if (m < a.k) g += gs[m * a.k + l] * (double)cl[m];
-      S.vq[l] = g;
+        if (m < a.k) vq += gs[m * a.k + l] * (double)cl[m];
+      S.vq[l] = vq;
     }
-    __syncthreads();
-    if (threadIdx.x == 0 && *(volatile int*)&S.done == kRunning) {
-      const double kappa = tot[0], rho = S.rho;
-      S.kappa = kappa;
-      if (!isfinite(kappa)) {
-        S.done = kNonFinite;
-      } else if (kappa <= 0.0) {
-        S.done = kNotSpd;
-      } else {
-        const double alpha = rho / kappa;
-        const double rho_e = rho - 2.0 * alpha * tot[1] + alpha * alpha * tot[2];
-        // below its rounding floor the expansion is noise around a true
-        // rho_{i+1} << rho_i: beta is then ~0 either way (>= 0 is kept)
-        const double beta = (rho_e > 0.0 ? rho_e : 0.0) / rho;
-        if (!isfinite(rho_e)) {
+    if (l == 0) {
+      go = 0;
+      if (running) {
+        const double kappa = tot[0];
+        S.kappa = kappa;
+        if (!isfinite(kappa)) {
           S.done = kNonFinite;
+        } else if (kappa <= 0.0) {
+          S.done = kNotSpd;
         } else {
-          S.alpha = alpha;
-          S.alpha32 = (float)alpha;
-          S.beta = beta;
-          S.beta32 = (float)beta;
-          for (int m = 0; m < a.k; ++m) {
-            S.u[m] -= alpha * S.vq[m];
-            S.t[m] = S.u[m] + beta * S.t[m];
+          const double alpha = rho / kappa;
+          const double rho_e = rho - 2.0 * alpha * tot[1] + alpha * alpha * tot[2];
+          // below its rounding floor the expansion is noise around a true
+          // rho_{i+1} << rho_i: beta is then ~0 either way (>= 0 is kept)
+          const double beta = (rho_e > 0.0 ? rho_e : 0.0) / rho;
+          if (!isfinite(rho_e)) {
+            S.done = kNonFinite;
+          } else {
+            S.alpha = alpha;
+            S.alpha32 = (float)alpha;
+            S.beta = beta;
+            S.beta32 = (float)beta;
+            ab[0] = alpha;
+            ab[1] = beta;
+            go = 1;
           }
-          publish_c(S, a.k);
         }
       }
+    }
+    __syncthreads();
+    if (go && l < a.k) {  // the recurrences of V^T s and V^T p, and c = 2|Lambda| V^T p, one direction per thread
+      u_l -= ab[0] * vq;
+      t_l = u_l + ab[1] * t_l;
+      S.u[l] = u_l;
+      S.t[l] = t_l;
+      const double c = lam_l * t_l;
+      S.c[l] = c;
+      S.c32[l] = (float)c;
     }
   }
 }
@@ -1979,15 +2006,22 @@ __global__ void __launch_bounds__(kThreads) cg_step_b_pg_kernel(CgArgs<T> a) {
   block_partials_t<T, 2>(acc, nv, a.partials);
   if (last_block_after_partials(&a.st->ticket)) {
     __shared__ double tot[2];
+    double tol_abs = 0.0;
+    long long iters = 0, maxit = 0;
+    if (threadIdx.x == 0) {  // loaded before the partial sums (overlapping round trips)
+      tol_abs = S.tol_abs;
+      iters = S.iters + 1;
+      maxit = S.maxit;
+    }
     final_sums(a.partials, nv, tot);
     if (threadIdx.x == 0) {
       const double rho_new = tot[0], rnorm = sqrt(jac ? tot[1] : tot[0]);
-      S.iters += 1;
+      S.iters = iters;
       if (!isfinite(rho_new) || !isfinite(rnorm)) {
         S.done = kNonFinite;
-      } else if (rnorm <= S.tol_abs) {
+      } else if (rnorm <= tol_abs) {
         S.done = kConverged;
-      } else if (S.iters >= S.maxit) {
+      } else if (iters >= maxit) {
         S.done = kMaxIter;
       } else if (rho_new <= 0.0) {
         S.done = kBreakdown;

@@ -208,15 +208,44 @@ __device__ __forceinline__ bool last_block_after_partials(unsigned int* ticket) 
 
 // Sum the partials of nv values over all blocks in a fixed order
 // (deterministic).  Result in out[0..nv) (shared memory), valid after return.
+// Every thread takes part, so the last block's reduction costs one round trip
+// to L2 rather than one per value a warp handles: value i is summed by a group
+// of g = blockDim / nv threads, thread j of the group over the partials j,
+// j + g, j + 2g, ... (16 loads in flight at a time), and one warp per value
+// combines its group's sums (strided lane sums, then a butterfly).
+constexpr int kFinalSumsThreads = 320;  // threads beyond this count only wait
 __device__ __forceinline__ void final_sums(const double* partials, int nv, double* out) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int i = warp; i < nv; i += (int)(blockDim.x >> 5)) {
+  __shared__ double fs[kFinalSumsThreads];
+  const int nt = min((int)blockDim.x, kFinalSumsThreads) & ~31;
+  const int G = (int)gridDim.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = max(1, nt / max(1, nv));  // threads per value
+  const int nvr = nt / g;                 // values per round
+  for (int i0 = 0; i0 < nv; i0 += nvr) {
+    const int i = i0 + tid / g, j = tid - (tid / g) * g;
     double s = 0.0;
-    s = lane_sum8(partials + (size_t)i * gridDim.x, (int)gridDim.x, lane);
-    s = warp_sum(s);
-    if (lane == 0) out[i] = s;
+    if (tid < nvr * g && i < nv) {
+      const double* x = partials + (size_t)i * G;
+      for (int b0 = j; b0 < G; b0 += 16 * g) {
+        double v[16];
+#pragma unroll
+        for (int m = 0; m < 16; ++m) v[m] = b0 + m * g < G ? __ldcg(x + b0 + m * g) : 0.0;
+#pragma unroll
+        for (int w = 8; w > 0; w >>= 1)
+#pragma unroll
+          for (int m = 0; m < w; ++m) v[m] += v[m + w];
+        s += v[0];
+      }
+    }
+    if (tid < nt) fs[tid] = s;
+    __syncthreads();
+    for (int v = warp; v < nvr && i0 + v < nv; v += nt >> 5) {
+      double t = 0.0;
+      for (int q = lane; q < g; q += 32) t += fs[v * g + q];
+      t = warp_sum(t);
+      if (lane == 0) out[i0 + v] = t;
+    }
+    __syncthreads();
   }
-  __syncthreads();
 }
 
 __device__ __forceinline__ bool finite(double x) { return isfinite(x); }
