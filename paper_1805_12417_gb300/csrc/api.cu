@@ -349,7 +349,7 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
     CK(cudaMemsetAsync(q, 0, (size_t)n_pad * esz, h->stream));
     *p = q;
   }
-  ST(dalloc(h, &h->d_partials, (size_t)kMaxNV * kMaxBlocks));
+  ST(dalloc(h, &h->d_partials, (size_t)(kMaxNV + 2) * kMaxBlocks));  // + step b's partials of the one-gather family
   ST(dalloc(h, &h->d_st, 1));
   CK(cudaMemsetAsync(h->d_st, 0, sizeof(DevState), h->stream));
   CK(cudaMallocHost(&h->h_st, sizeof(DevState)));

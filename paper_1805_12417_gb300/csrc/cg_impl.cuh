@@ -58,6 +58,10 @@ struct CgArgs {
   // staged step a: ring of shared-memory stages (bytes; region offsets inside a stage)
   int stages, stage_bytes, off_col, off_v, off_s, off_p, off_d, off_z;
   int stall_test;  // test hook: the producer stops after the first tile (waits then run out)
+  // one-gather family: step b's partials (step a's are `partials`), the grids
+  // that wrote them, and the parity of the iteration this launch belongs to
+  double* partials_b;
+  int grid_a, grid_b, par;
   // one-kernel iteration: r and q ping-pong (r = r_{i-1} read, r_new written; q = q_i written, q_old read)
   T* r_new;
   T* q_old;
@@ -115,6 +119,9 @@ __device__ __forceinline__ void start_cg(CgState& S, int k, double vn, double rh
     S.ctl_limit = (int)(lim < 0x7fffffffLL ? lim : 0x7fffffffLL);
   }
   S.done = kRunning;
+  S.rho_s[0] = rho;
+  S.it_s[0] = 0;
+  S.bp_s[0] = S.bp_s[1] = 0;
   if (!isfinite(vn) || !isfinite(rho)) {
     S.done = kNonFinite;
   } else if (vn == 0.0 || rnorm == 0.0) {
@@ -1355,105 +1362,166 @@ __device__ __forceinline__ T pg_row(const T* vp, const I* cp, int row, bool delt
   return acc;
 }
 
-// Reduction of step a (variants 9-11) and its last block: alpha from the
-// fresh rho, beta from the expansion, and the recurrences of V^T s, V^T p
-// and c = 2|Lambda| V^T p for the next step a.
+// Reductions of the one-gather iteration (variants 9-15).  No last block:
+// every block of a kernel finishes its predecessor's reduction itself (the
+// partials are visible once the predecessor has completed) and all blocks
+// take the same decisions from the same sums; block 0 alone writes the state
+// (into slots its own kernel does not read; see CgState).
+//
+// pg_begin, step a of iteration j (all threads, after the grid dependency
+// wait): for j >= 1 the sums r^T s (and r^T r) of step b of iteration j - 1:
+// rho_j, the iteration count j, and the stopping test on the fresh values.
+// Returns false (in every block) when the solve is over.
+template <typename T>
+__device__ __forceinline__ bool pg_begin(const CgArgs<T>& a, CgState& S) {
+  __shared__ int go;
+  __shared__ double tot[2];
+  if (threadIdx.x == 0) go = *(volatile int*)&S.done == kRunning ? 1 : 0;
+  __syncthreads();
+  if (!go) return false;
+  const int P = a.par;
+  if (!S.bp_s[P]) return true;  // iteration 0: rho_0 comes from the init kernel
+  const bool jac = a.dinv != nullptr;
+  long long it = 0, maxit = 0;
+  double tol = 0.0;
+  if (threadIdx.x == 0) {
+    it = S.it_s[P ^ 1] + 1;
+    maxit = S.maxit;
+    tol = S.tol_abs;
+  }
+  final_sums_g(a.partials_b, a.grid_b, jac ? 2 : 1, tot);
+  if (threadIdx.x == 0) {
+    const double rho = tot[0], rnorm = sqrt(jac ? tot[1] : tot[0]);
+    int st = kRunning;
+    if (!isfinite(rho) || !isfinite(rnorm)) st = kNonFinite;
+    else if (rnorm <= tol) st = kConverged;
+    else if (it >= maxit) st = kMaxIter;
+    else if (rho <= 0.0) st = kBreakdown;
+    if (blockIdx.x == 0) {
+      S.it_s[P] = it;
+      S.iters = it;
+      if (st == kRunning) {
+        S.rho_s[P] = rho;
+        S.rho = rho;
+      } else {
+        S.done = st;
+      }
+    }
+    go = st == kRunning ? 1 : 0;
+  }
+  __syncthreads();
+  return go != 0;
+}
+
+// pg_end, step a: this block's partials p^T q, s^T q, q^T M_cg^{-1} q and
+// V^T M_cg^{-1} A p (finished by step b).
 template <typename T, int KB, int NW>
-__device__ __forceinline__ void pg_reduce(const CgArgs<T>& a, CgState& S, T pq, T sq, T qdq,
-                                          const T (&wq)[KB > 0 ? KB : 1], const T* cl) {
-  constexpr int KS = KB > 0 ? KB : 1;
+__device__ __forceinline__ void pg_end(const CgArgs<T>& a, T pq, T sq, T qdq, const T (&wq)[KB > 0 ? KB : 1]) {
   T part[KB + 3];
   part[0] = pq;
   part[1] = sq;
   part[2] = qdq;
 #pragma unroll
   for (int l = 0; l < KB; ++l) part[l + 3] = wq[l];
-  block_partials_t<T, KB + 3, NW>(part, a.k + 3, a.partials);
-  if (last_block_after_partials(&a.st->ticket)) {
-    constexpr int KK = KS * KS;
-    constexpr int NT = NW * 32;
-    constexpr int GPT = (KK + NT - 1) / NT;
-    __shared__ double gs[KK];
-    double greg[GPT];
-    const int kk = a.k * a.k;
+  block_partials_t<T, KB + 3, NW, false>(part, a.k + 3, a.partials);
+}
+
+// pg_b_begin, step b of iteration j (all threads, after the grid dependency
+// wait): step a's sums give kappa = p^T q, alpha = rho_j / kappa and beta from
+// the expansion rho_j - 2 alpha s^T q + alpha^2 q^T M_cg^{-1} q; block 0 also
+// advances V^T s, V^T p and c = 2|Lambda| V^T p with
+// V^T M_cg^{-1} q = V^T M_cg^{-1} A p + G c (G = V^T M_cg^{-1} V, c the
+// coefficients step a applied).  Returns false when the solve is over.
+template <typename T, int KB>
+__device__ __forceinline__ bool pg_b_begin(const CgArgs<T>& a, CgState& S, T& alpha_t, T& beta_t) {
+  constexpr int KS = KB > 0 ? KB : 1;
+  constexpr int KK = KS * KS;
+  constexpr int GPT = (KK + kThreads - 1) / kThreads;
+  __shared__ int go;
+  __shared__ double ab[2];
+  __shared__ double tot[KB + 3];
+  __shared__ double gs[KK];
+  __shared__ double cs[KS];
+  if (threadIdx.x == 0) go = *(volatile int*)&S.done == kRunning ? 1 : 0;
+  __syncthreads();
+  if (!go) return false;
+  const int P = a.par, l = threadIdx.x, k = a.k;
+  const bool b0 = blockIdx.x == 0;
+  double rho = 0.0, u_l = 0.0, t_l = 0.0, lam_l = 0.0;
+  double greg[GPT];
+  if (l == 0) rho = S.rho_s[P];
+  if (b0) {  // loaded before the sums, so that the round trips overlap
 #pragma unroll
     for (int j = 0; j < GPT; ++j) {
-      const int e = threadIdx.x + j * NT;
-      greg[j] = (e < kk) ? __ldcg(a.gram + e) : 0.0;
+      const int e = l + j * kThreads;
+      greg[j] = (e < k * k) ? __ldcg(a.gram + e) : 0.0;
     }
-    // the state the tail updates, loaded before the partial sums so that its
-    // round trips overlap theirs: direction l's V^T s, V^T p and 2|lambda_l|
-    // by thread l, rho and the status by thread 0
-    const int l = threadIdx.x;
-    double u_l = 0.0, t_l = 0.0, lam_l = 0.0, rho = 0.0;
-    int running = 0;
-    if (l < a.k) {
+    if (l < k) {
       u_l = S.u[l];
       t_l = S.t[l];
       lam_l = S.lam2[l];
-    }
-    if (l == 0) {
-      rho = S.rho;
-      running = *(volatile int*)&S.done == kRunning;
-    }
-    __shared__ double tot[KB + 3];
-    __shared__ double ab[2];
-    __shared__ int go;
-    final_sums(a.partials, a.k + 3, tot);
-#pragma unroll
-    for (int j = 0; j < GPT; ++j) {
-      const int e = threadIdx.x + j * NT;
-      if (e < kk) gs[e] = greg[j];
-    }
-    __syncthreads();
-    double vq = 0.0;
-    if (l < a.k) {  // V^T M_cg^{-1} q = V^T M_cg^{-1} A p + G c
-      vq = tot[l + 3];
-#pragma unroll 8
-      for (int m = 0; m < KB; ++m)
-        if (m < a.k) vq += gs[m * a.k + l] * (double)cl[m];
-      S.vq[l] = vq;
-    }
-    if (l == 0) {
-      go = 0;
-      if (running) {
-        const double kappa = tot[0];
-        S.kappa = kappa;
-        if (!isfinite(kappa)) {
-          S.done = kNonFinite;
-        } else if (kappa <= 0.0) {
-          S.done = kNotSpd;
-        } else {
-          const double alpha = rho / kappa;
-          const double rho_e = rho - 2.0 * alpha * tot[1] + alpha * alpha * tot[2];
-          // below its rounding floor the expansion is noise around a true
-          // rho_{i+1} << rho_i: beta is then ~0 either way (>= 0 is kept)
-          const double beta = (rho_e > 0.0 ? rho_e : 0.0) / rho;
-          if (!isfinite(rho_e)) {
-            S.done = kNonFinite;
-          } else {
-            S.alpha = alpha;
-            S.alpha32 = (float)alpha;
-            S.beta = beta;
-            S.beta32 = (float)beta;
-            ab[0] = alpha;
-            ab[1] = beta;
-            go = 1;
-          }
-        }
-      }
-    }
-    __syncthreads();
-    if (go && l < a.k) {  // the recurrences of V^T s and V^T p, and c = 2|Lambda| V^T p, one direction per thread
-      u_l -= ab[0] * vq;
-      t_l = u_l + ab[1] * t_l;
-      S.u[l] = u_l;
-      S.t[l] = t_l;
-      const double c = lam_l * t_l;
-      S.c[l] = c;
-      S.c32[l] = (float)c;
+      cs[l] = (double)c_of(S, l, T(0));
     }
   }
+  final_sums_g(a.partials, a.grid_a, k + 3, tot);
+  if (l == 0) {
+    int st = kRunning;
+    double alpha = 0.0, beta = 0.0;
+    const double kappa = tot[0];
+    if (!isfinite(kappa)) {
+      st = kNonFinite;
+    } else if (kappa <= 0.0) {
+      st = kNotSpd;
+    } else {
+      alpha = rho / kappa;
+      const double rho_e = rho - 2.0 * alpha * tot[1] + alpha * alpha * tot[2];
+      // below its rounding floor the expansion is noise around a true
+      // rho_{i+1} << rho_i: beta is then ~0 either way (>= 0 is kept)
+      beta = (rho_e > 0.0 ? rho_e : 0.0) / rho;
+      if (!isfinite(rho_e)) st = kNonFinite;
+    }
+    if (b0) {
+      S.kappa = kappa;
+      if (st == kRunning) {
+        S.alpha = alpha;
+        S.alpha32 = (float)alpha;
+        S.beta = beta;
+        S.beta32 = (float)beta;
+        S.bp_s[P ^ 1] = 1;
+      } else {
+        S.done = st;
+      }
+    }
+    ab[0] = alpha;
+    ab[1] = beta;
+    go = st == kRunning ? 1 : 0;
+  }
+  if (b0) {
+#pragma unroll
+    for (int j = 0; j < GPT; ++j) {
+      const int e = l + j * kThreads;
+      if (e < k * k) gs[e] = greg[j];
+    }
+  }
+  __syncthreads();
+  if (!go) return false;
+  if (b0 && l < k) {
+    double vq = tot[l + 3];
+#pragma unroll 8
+    for (int m = 0; m < KB; ++m)
+      if (m < k) vq += gs[m * k + l] * cs[m];
+    S.vq[l] = vq;
+    u_l -= ab[0] * vq;
+    t_l = u_l + ab[1] * t_l;
+    S.u[l] = u_l;
+    S.t[l] = t_l;
+    const double c = lam_l * t_l;
+    S.c[l] = c;
+    S.c32[l] = (float)c;
+  }
+  alpha_t = (T)ab[0];
+  beta_t = (T)ab[1];
+  return true;
 }
 
 // per-row part of step a (variants 9-11): q = A p + V c and the row's terms of the partials
@@ -1490,7 +1558,8 @@ __global__ void __launch_bounds__(kStagedThreads, MB) cg_step_a_pg_staged_kernel
   __shared__ int stalled;
   __shared__ T cl[KS];
   CgState& S = a.st->cg;
-  if (S.done != kRunning) return;
+  grid_dependency_wait();
+  if (!pg_begin(a, S)) return;
   if (threadIdx.x < KS) cl[threadIdx.x] = ((int)threadIdx.x < a.k) ? c_of(S, threadIdx.x, T(0)) : (T)0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool jac = a.dinv != nullptr;
@@ -1656,7 +1725,7 @@ __global__ void __launch_bounds__(kStagedThreads, MB) cg_step_a_pg_staged_kernel
   }
   __syncthreads();
   if (threadIdx.x == 0 && stalled) *(volatile int*)&S.done = kStall;
-  pg_reduce<T, KB, kStagedThreads / 32>(a, S, pq, sq, qdq, wq, cl);
+  pg_end<T, KB, kStagedThreads / 32>(a, pq, sq, qdq, wq);
 }
 
 // Variants 14 / 15: the one-gather step a on tiles of 16 slices (512 rows),
@@ -1814,8 +1883,8 @@ __global__ void __launch_bounds__(kStagedThreads, MB) cg_step_a_pg2_kernel(CgArg
                                a.slice_ptr[min((t + 1) * TSL, a.nslices)], pol);
     }
   }
-  grid_dependency_wait();  // the previous step b's p, s and scalars are visible from here on
-  const bool run = S.done == kRunning;
+  grid_dependency_wait();  // the previous step b's p, s and partials are visible from here on
+  const bool run = pg_begin(a, S);
   if (!run) {  // the producer lets its copies land before the block leaves
     if (warp == kTileSlices && lane == 0) pg2_producer<T, TSL>(a, stage_mem, full, empty, &stalled, ntl, nst, false);
     return;
@@ -1913,7 +1982,7 @@ __global__ void __launch_bounds__(kStagedThreads, MB) cg_step_a_pg2_kernel(CgArg
   }
   __syncthreads();
   if (threadIdx.x == 0 && stalled) *(volatile int*)&S.done = kStall;
-  pg_reduce<T, KB, kStagedThreads / 32>(a, S, pq, sq, qdq, wq, cls);
+  pg_end<T, KB, kStagedThreads / 32>(a, pq, sq, qdq, wq);
 }
 
 // Variant 11: the same arithmetic with plain loads, one warp per SELL slice,
@@ -1923,7 +1992,8 @@ template <typename T, int KB>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? 2 : 4) cg_step_a_pg_kernel(CgArgs<T> a) {
   constexpr int KS = KB > 0 ? KB : 1;
   CgState& S = a.st->cg;
-  if (S.done != kRunning) return;
+  grid_dependency_wait();
+  if (!pg_begin(a, S)) return;
   __shared__ T cl[KS];
   if (threadIdx.x < KS) cl[threadIdx.x] = ((int)threadIdx.x < a.k) ? c_of(S, threadIdx.x, T(0)) : (T)0;
   __syncthreads();
@@ -1950,7 +2020,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? 2 : 4) cg_step_a_pg
     for (int l = 0; l < KS; ++l) vv[l] = (l < a.k) ? ld_stream(a.V + (size_t)l * a.n_pad + row) : (T)0;
     pg_row_update<T, KB, 1>(a, row, ap, pr, rr, d, jac, vv, cl, pq, sq, qdq, wq);
   }
-  pg_reduce<T, KB, kThreads / 32>(a, S, pq, sq, qdq, wq, cl);
+  pg_end<T, KB, kThreads / 32>(a, pq, sq, qdq, wq);
 }
 
 // step b of variants 9-11: z += alpha p, r -= alpha q, s = M_cg^{-1} r,
@@ -1959,10 +2029,9 @@ template <typename T, int KB>
 __global__ void __launch_bounds__(kThreads) cg_step_b_pg_kernel(CgArgs<T> a) {
   constexpr int W = V16<T>::W;
   CgState& S = a.st->cg;
-  grid_dependency_wait();  // step a's alpha, beta, q (launched early behind a programmatic edge)
-  if (S.done != kRunning) return;
-  const T alpha = alpha_of(S, T(0));
-  const T beta = beta_of(S, T(0));
+  grid_dependency_wait();  // step a's q and partials (launched early behind a programmatic edge)
+  T alpha, beta;
+  if (!pg_b_begin<T, KB>(a, S, alpha, beta)) return;
   const bool jac = a.dinv != nullptr;
   T rs = 0, rr = 0;
   const int64_t nvec = a.n_pad / W;
@@ -2002,34 +2071,7 @@ __global__ void __launch_bounds__(kThreads) cg_step_b_pg_kernel(CgArgs<T> a) {
     }
   }
   T acc[2] = {rs, rr};
-  const int nv = jac ? 2 : 1;
-  block_partials_t<T, 2>(acc, nv, a.partials);
-  if (last_block_after_partials(&a.st->ticket)) {
-    __shared__ double tot[2];
-    double tol_abs = 0.0;
-    long long iters = 0, maxit = 0;
-    if (threadIdx.x == 0) {  // loaded before the partial sums (overlapping round trips)
-      tol_abs = S.tol_abs;
-      iters = S.iters + 1;
-      maxit = S.maxit;
-    }
-    final_sums(a.partials, nv, tot);
-    if (threadIdx.x == 0) {
-      const double rho_new = tot[0], rnorm = sqrt(jac ? tot[1] : tot[0]);
-      S.iters = iters;
-      if (!isfinite(rho_new) || !isfinite(rnorm)) {
-        S.done = kNonFinite;
-      } else if (rnorm <= tol_abs) {
-        S.done = kConverged;
-      } else if (iters >= maxit) {
-        S.done = kMaxIter;
-      } else if (rho_new <= 0.0) {
-        S.done = kBreakdown;
-      } else {
-        S.rho = rho_new;
-      }
-    }
-  }
+  block_partials_t<T, 2, kThreads / 32, false>(acc, jac ? 2 : 1, a.partials_b);  // finished by the next step a
 }
 
 // G = V^T M_cg^{-1} V (k x k, both triangles) from the kernels' own V and
@@ -2253,6 +2295,10 @@ void make_args(const InnerGraphSpec& spec, CgArgs<T> (&a)[2]) {
     x.off_z = geo.off_z;
     x.st = spec.st;
     x.partials = spec.partials;
+    x.partials_b = spec.partials + (size_t)kMaxNV * kMaxBlocks;  // allocated (kMaxNV + 2) x kMaxBlocks
+    x.grid_a = spec.grid_spmv;
+    x.grid_b = spec.grid_stream_b;
+    x.par = par;
     x.slice_ptr = spec.A.slice_ptr;
     x.col = spec.A.col;
     x.col16 = spec.A.col16;

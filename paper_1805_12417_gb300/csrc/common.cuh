@@ -68,6 +68,15 @@ struct CgState {
   int fused_pending;
   int pad_f;
   const void* p_last;
+  // one-gather iteration (variants 9-15): each kernel finishes the reduction
+  // of its predecessor in every block (no last block).  Slots by the parity of
+  // the iteration, so that a kernel never writes a slot its own blocks read:
+  // rho_s[j & 1] = rho_j, it_s[j & 1] = j (iterations done when step a of
+  // iteration j starts), bp_s[j & 1] = 1 once step b of iteration j - 1 left
+  // its partials for step a of iteration j to finish.
+  double rho_s[2];
+  long long it_s[2];
+  int bp_s[2];
 };
 
 struct OuterState {
@@ -113,7 +122,9 @@ __device__ __forceinline__ T warp_sum(T v) {
 // Block reduction of NV per-thread values in the threads' own precision T
 // (FP32 in the mixed-precision kernels: no FP64 pipe work), stored as this
 // block's FP64 partials, value-major: partials[i * gridDim.x + blockIdx.x].
-template <typename T, int NV, int NW = kThreads / 32>
+// FENCE = false: the partials are read only by a later kernel (the kernel
+// boundary makes them visible), so no block draws a ticket after them.
+template <typename T, int NV, int NW = kThreads / 32, bool FENCE = true>
 __device__ __forceinline__ void block_partials_t(T (&v)[NV], int nv, double* partials) {
   __shared__ T smt[NW][NV > 0 ? NV : 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -131,7 +142,7 @@ __device__ __forceinline__ void block_partials_t(T (&v)[NV], int nv, double* par
 #pragma unroll
     for (int w = 0; w < NW; ++w) s += smt[w][threadIdx.x];
     partials[threadIdx.x * gridDim.x + blockIdx.x] = (double)s;
-    __threadfence();  // the partial is visible before this block draws its ticket
+    if (FENCE) __threadfence();  // the partial is visible before this block draws its ticket
   }
 }
 
@@ -213,11 +224,13 @@ __device__ __forceinline__ bool last_block_after_partials(unsigned int* ticket) 
 // of g = blockDim / nv threads, thread j of the group over the partials j,
 // j + g, j + 2g, ... (16 loads in flight at a time), and one warp per value
 // combines its group's sums (strided lane sums, then a butterfly).
+// G: the grid that wrote the partials (this grid for a last block; the
+// previous kernel's when a kernel finishes its predecessor's reduction).
 constexpr int kFinalSumsThreads = 320;  // threads beyond this count only wait
-__device__ __forceinline__ void final_sums(const double* partials, int nv, double* out) {
+__device__ __forceinline__ void final_sums_g(const double* partials, int G, int nv, double* out) {
   __shared__ double fs[kFinalSumsThreads];
   const int nt = min((int)blockDim.x, kFinalSumsThreads) & ~31;
-  const int G = (int)gridDim.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int g = max(1, nt / max(1, nv));  // threads per value
   const int nvr = nt / g;                 // values per round
   for (int i0 = 0; i0 < nv; i0 += nvr) {
@@ -246,6 +259,10 @@ __device__ __forceinline__ void final_sums(const double* partials, int nv, doubl
     }
     __syncthreads();
   }
+}
+
+__device__ __forceinline__ void final_sums(const double* partials, int nv, double* out) {
+  final_sums_g(partials, (int)gridDim.x, nv, out);
 }
 
 __device__ __forceinline__ bool finite(double x) { return isfinite(x); }

@@ -28,7 +28,7 @@ import paper_1805_12417_gb300 as m  # noqa: E402
 
 MIB = 1 << 20
 SLICE = 32           # SELL slice height
-PARTIAL_SLOTS = (32 + 4) * 2048  # per-block reduction partials (FP64)
+PARTIAL_SLOTS = (32 + 6) * 2048  # per-block reduction partials (FP64), step b's own two rows included
 
 
 @pytest.fixture(scope="module")
@@ -46,7 +46,7 @@ def _accounted(p, fp32, mcg):
     width = np.pad(width, (0, n_pad - n))
     total = int(width.reshape(nsl, SLICE).max(axis=1).sum()) * SLICE
     esz = 4 if fp32 else 8
-    pad = 16  # every allocation carries 16 guard bytes
+    pad = 0  # allocations are exact
     large = [total * 4 + pad, total * 8 + pad, (total + 1) * 2 + pad, n_pad * k * 8 + pad]
     if fp32:
         large += [total * 4 + pad, n_pad * k * 4 + pad]
