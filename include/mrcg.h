@@ -41,10 +41,11 @@
  *                         fix the step-a variant, its pipeline depth and the
  *                         blocks per SM of the two inner kernels; any of them
  *                         turns the autotuner off.
- *  - MRCG_PDL=0           plain graph edges between the inner kernels (by default
- *                         step-a variants 14 and 15 and their step b are joined by
- *                         programmatic edges: a kernel starts streaming its static
- *                         operands while its predecessor finishes).
+ *  - MRCG_PDL=0..3        graph edges between the inner kernels of step-a
+ *                         variants 14 and 15 (0: plain; 1: programmatic both ways;
+ *                         2, the default: programmatic from step b to the next
+ *                         step a, which streams its static operands while step b
+ *                         finishes; 3: programmatic from step a to step b).
  *  - MRCG_IDX16=0         keep 32-bit column indices in the inner kernels
  *                         (16-bit deltas are used whenever |col - row| <= 32767).
  *  - MRCG_UNROLL=U        inner iterations per convergence check (even, >= 2).

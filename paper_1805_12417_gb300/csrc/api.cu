@@ -349,7 +349,7 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
     CK(cudaMemsetAsync(q, 0, (size_t)n_pad * esz, h->stream));
     *p = q;
   }
-  ST(dalloc(h, &h->d_partials, (size_t)(kMaxNV + 2) * kMaxBlocks));  // + step b's partials of the one-gather family
+  ST(dalloc(h, &h->d_partials, (size_t)(2 * kMaxNV + 2) * kMaxBlocks));  // one-gather family: two parities + step b
   ST(dalloc(h, &h->d_st, 1));
   CK(cudaMemsetAsync(h->d_st, 0, sizeof(DevState), h->stream));
   CK(cudaMallocHost(&h->h_st, sizeof(DevState)));
@@ -498,7 +498,7 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
   // after the first tile, so its bounded waits run out and the solve reports
   // MRCG_ERR_CUDA (the GPU context stays usable)
   if (const char* e = getenv("MRCG_TEST_STALL")) g.stall_test = atoi(e) != 0;
-  if (const char* e = getenv("MRCG_PDL")) g.pdl = atoi(e) != 0;
+  if (const char* e = getenv("MRCG_PDL")) g.pdl = std::max(0, std::min(3, atoi(e)));
   // SELL entries of the largest tile of 8 (16) slices (the staged step a's buffers)
   for (int64_t s0 = 0; s0 < nslices; s0 += 8) g.tile_entries = std::max(g.tile_entries, sp[std::min(s0 + 8, nslices)] - sp[s0]);
   for (int64_t s0 = 0; s0 < nslices; s0 += 16)
@@ -585,8 +585,22 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
             bps.push_back(occ_v + 1);
             bps.push_back(2 * occ_v);
           }
+          // grids: bp blocks per SM, and for the staged kernels the smallest grid
+          // with the same tiles per block (every block then takes as many
+          // tiles, none idles while the last ones finish)
+          std::vector<int> grids;
           for (int bp : bps) {
-            t.grid_spmv = grid_a(t, bp);
+            const int gr = grid_a(t, bp);
+            grids.push_back(gr);
+            if (is_staged_variant(var)) {
+              const int64_t tiles = tile_slices(var) == 16 ? ntiles16 : ntiles;
+              const int64_t per = (tiles + gr - 1) / gr;
+              const int bal = (int)((tiles + per - 1) / per);
+              if (bal != gr) grids.push_back(bal);
+            }
+          }
+          for (int gr : grids) {
+            t.grid_spmv = gr;
             ST(time_spec(t));
             if (ms[0] < best) {
               best = ms[0];

@@ -61,6 +61,7 @@ struct CgArgs {
   // one-gather family: step b's partials (step a's are `partials`), the grids
   // that wrote them, and the parity of the iteration this launch belongs to
   double* partials_b;
+  const double* partials_o;  // step a's partials of the other parity (the previous iteration's)
   int grid_a, grid_b, par;
   // one-kernel iteration: r and q ping-pong (r = r_{i-1} read, r_new written; q = q_i written, q_old read)
   T* r_new;
@@ -131,6 +132,11 @@ __device__ __forceinline__ void start_cg(CgState& S, int k, double vn, double rh
   }
   for (int l = 0; l < k; ++l) S.t[l] = S.u[l];
   publish_c(S, k);
+  for (int l = 0; l < k; ++l) {  // iteration 0 of the one-gather family
+    S.u_s[0][l] = S.u[l];
+    S.t_s[0][l] = S.t[l];
+    S.c_s[0][l] = S.c[l];
+  }
 }
 
 template <typename T, int KB>
@@ -1372,44 +1378,103 @@ __device__ __forceinline__ T pg_row(const T* vp, const I* cp, int row, bool delt
 // wait): for j >= 1 the sums r^T s (and r^T r) of step b of iteration j - 1:
 // rho_j, the iteration count j, and the stopping test on the fresh values.
 // Returns false (in every block) when the solve is over.
-template <typename T>
-__device__ __forceinline__ bool pg_begin(const CgArgs<T>& a, CgState& S) {
+template <typename T, int KB, int NT = 0>
+__device__ __forceinline__ bool pg_begin(const CgArgs<T>& a, CgState& S, T* cls) {
+  constexpr int KS = KB > 0 ? KB : 1;
+  constexpr int KK = KS * KS;
+  constexpr int GPT = (KK + kThreads - 1) / kThreads;
   __shared__ int go;
-  __shared__ double tot[2];
-  if (threadIdx.x == 0) go = *(volatile int*)&S.done == kRunning ? 1 : 0;
-  __syncthreads();
-  if (!go) return false;
-  const int P = a.par;
-  if (!S.bp_s[P]) return true;  // iteration 0: rho_0 comes from the init kernel
+  __shared__ double tot[KB + 2];
+  __shared__ double gs[KK];
+  __shared__ double cprev[KS];
+  const int P = a.par, l = threadIdx.x, k = a.k;
   const bool jac = a.dinv != nullptr;
+  const int nb = jac ? 2 : 1;
+  // one round of loads: the status and the slots, step b's partials (rho_j)
+  // and the previous step a's projections, whether or not they are pending
+  // (iteration 0 takes its slot from the init kernel and uses neither)
+  // (no load depends on another: both slots are read, the pending flag picks one)
+  const int running = *(volatile int*)&S.done == kRunning;
+  const int pending = S.bp_s[P];
+  const double alpha = S.alpha, beta = S.beta;
   long long it = 0, maxit = 0;
-  double tol = 0.0;
-  if (threadIdx.x == 0) {
+  double tol = 0.0, u_l = 0.0, t_l = 0.0, lam_l = 0.0, c_l = 0.0, u_o = 0.0, t_o = 0.0, c_o = 0.0;
+  double greg[GPT];
+  if (l == 0) {
     it = S.it_s[P ^ 1] + 1;
     maxit = S.maxit;
     tol = S.tol_abs;
   }
-  final_sums_g(a.partials_b, a.grid_b, jac ? 2 : 1, tot);
-  if (threadIdx.x == 0) {
-    const double rho = tot[0], rnorm = sqrt(jac ? tot[1] : tot[0]);
-    int st = kRunning;
-    if (!isfinite(rho) || !isfinite(rnorm)) st = kNonFinite;
-    else if (rnorm <= tol) st = kConverged;
-    else if (it >= maxit) st = kMaxIter;
-    else if (rho <= 0.0) st = kBreakdown;
-    if (blockIdx.x == 0) {
-      S.it_s[P] = it;
-      S.iters = it;
-      if (st == kRunning) {
-        S.rho_s[P] = rho;
-        S.rho = rho;
-      } else {
-        S.done = st;
+  if (l < k) {
+    u_l = S.u_s[P][l];
+    t_l = S.t_s[P][l];
+    c_l = S.c_s[P][l];
+    u_o = S.u_s[P ^ 1][l];
+    t_o = S.t_s[P ^ 1][l];
+    c_o = S.c_s[P ^ 1][l];
+    lam_l = S.lam2[l];
+  }
+#pragma unroll
+  for (int j = 0; j < GPT; ++j) {
+    const int e = l + j * kThreads;
+    greg[j] = e < k * k ? __ldcg(a.gram + e) : 0.0;
+  }
+  if (pending) {  // iteration j - 1's slot
+    u_l = u_o;
+    t_l = t_o;
+    c_l = c_o;
+  }
+  if (l < k) cprev[l] = (double)(T)c_l;  // the coefficient the previous step a applied
+  final_sums_2<NT>(a.partials_b, a.grid_b, nb, a.partials_o + (size_t)3 * a.grid_a, a.grid_a, k, tot);
+#pragma unroll
+  for (int j = 0; j < GPT; ++j) {
+    const int e = l + j * kThreads;
+    if (e < k * k) gs[e] = greg[j];
+  }
+  if (l == 0) {
+    int st = running ? kRunning : kConverged;  // (an earlier status stands; only its "not running" is used here)
+    if (running && pending) {
+      const double rho = tot[0], rnorm = sqrt(jac ? tot[1] : tot[0]);
+      if (!isfinite(rho) || !isfinite(rnorm)) st = kNonFinite;
+      else if (rnorm <= tol) st = kConverged;
+      else if (it >= maxit) st = kMaxIter;
+      else if (rho <= 0.0) st = kBreakdown;
+      if (blockIdx.x == 0) {
+        S.it_s[P] = it;
+        S.iters = it;
+        if (st == kRunning) {
+          S.rho_s[P] = rho;
+          S.rho = rho;
+        } else {
+          S.done = st;
+        }
       }
     }
     go = st == kRunning ? 1 : 0;
   }
-  __syncthreads();
+  group_sync<NT>();
+  if (l < KS) {
+    double c = c_l;
+    if (pending && l < k) {
+      // iteration j - 1's recurrences: V^T M_cg^{-1} q = V^T M_cg^{-1} A p + G c,
+      // V^T s -= alpha V^T M_cg^{-1} q, V^T p = V^T s + beta V^T p, c = 2|lambda| V^T p
+      double vq = tot[nb + l];
+#pragma unroll 8
+      for (int m = 0; m < KB; ++m)
+        if (m < k) vq += gs[m * k + l] * cprev[m];
+      u_l -= alpha * vq;
+      t_l = u_l + beta * t_l;
+      c = lam_l * t_l;
+      if (blockIdx.x == 0 && running) {
+        S.vq[l] = vq;
+        S.u_s[P][l] = u_l;
+        S.t_s[P][l] = t_l;
+        S.c_s[P][l] = c;
+      }
+    }
+    cls[l] = l < k ? (T)c : (T)0;
+  }
+  group_sync<NT>();
   return go != 0;
 }
 
@@ -1434,41 +1499,24 @@ __device__ __forceinline__ void pg_end(const CgArgs<T>& a, T pq, T sq, T qdq, co
 // coefficients step a applied).  Returns false when the solve is over.
 template <typename T, int KB>
 __device__ __forceinline__ bool pg_b_begin(const CgArgs<T>& a, CgState& S, T& alpha_t, T& beta_t) {
-  constexpr int KS = KB > 0 ? KB : 1;
-  constexpr int KK = KS * KS;
-  constexpr int GPT = (KK + kThreads - 1) / kThreads;
   __shared__ int go;
   __shared__ double ab[2];
-  __shared__ double tot[KB + 3];
-  __shared__ double gs[KK];
-  __shared__ double cs[KS];
-  if (threadIdx.x == 0) go = *(volatile int*)&S.done == kRunning ? 1 : 0;
-  __syncthreads();
-  if (!go) return false;
-  const int P = a.par, l = threadIdx.x, k = a.k;
-  const bool b0 = blockIdx.x == 0;
-  double rho = 0.0, u_l = 0.0, t_l = 0.0, lam_l = 0.0;
-  double greg[GPT];
-  if (l == 0) rho = S.rho_s[P];
-  if (b0) {  // loaded before the sums, so that the round trips overlap
-#pragma unroll
-    for (int j = 0; j < GPT; ++j) {
-      const int e = l + j * kThreads;
-      greg[j] = (e < k * k) ? __ldcg(a.gram + e) : 0.0;
-    }
-    if (l < k) {
-      u_l = S.u[l];
-      t_l = S.t[l];
-      lam_l = S.lam2[l];
-      cs[l] = (double)c_of(S, l, T(0));
-    }
+  __shared__ double tot[3];
+  const int P = a.par;
+  double rho = 0.0;
+  int running = 0;
+  if (threadIdx.x == 0) {  // one round of loads: these and step a's sums
+    running = *(volatile int*)&S.done == kRunning;
+    rho = S.rho_s[P];
   }
-  final_sums_g(a.partials, a.grid_a, k + 3, tot);
-  if (l == 0) {
+  final_sums_g(a.partials, a.grid_a, 3, tot);
+  if (threadIdx.x == 0) {
     int st = kRunning;
     double alpha = 0.0, beta = 0.0;
     const double kappa = tot[0];
-    if (!isfinite(kappa)) {
+    if (!running) {
+      st = kConverged;  // over already (its status stands)
+    } else if (!isfinite(kappa)) {
       st = kNonFinite;
     } else if (kappa <= 0.0) {
       st = kNotSpd;
@@ -1480,7 +1528,7 @@ __device__ __forceinline__ bool pg_b_begin(const CgArgs<T>& a, CgState& S, T& al
       beta = (rho_e > 0.0 ? rho_e : 0.0) / rho;
       if (!isfinite(rho_e)) st = kNonFinite;
     }
-    if (b0) {
+    if (blockIdx.x == 0 && running) {
       S.kappa = kappa;
       if (st == kRunning) {
         S.alpha = alpha;
@@ -1496,29 +1544,8 @@ __device__ __forceinline__ bool pg_b_begin(const CgArgs<T>& a, CgState& S, T& al
     ab[1] = beta;
     go = st == kRunning ? 1 : 0;
   }
-  if (b0) {
-#pragma unroll
-    for (int j = 0; j < GPT; ++j) {
-      const int e = l + j * kThreads;
-      if (e < k * k) gs[e] = greg[j];
-    }
-  }
   __syncthreads();
   if (!go) return false;
-  if (b0 && l < k) {
-    double vq = tot[l + 3];
-#pragma unroll 8
-    for (int m = 0; m < KB; ++m)
-      if (m < k) vq += gs[m * k + l] * cs[m];
-    S.vq[l] = vq;
-    u_l -= ab[0] * vq;
-    t_l = u_l + ab[1] * t_l;
-    S.u[l] = u_l;
-    S.t[l] = t_l;
-    const double c = lam_l * t_l;
-    S.c[l] = c;
-    S.c32[l] = (float)c;
-  }
   alpha_t = (T)ab[0];
   beta_t = (T)ab[1];
   return true;
@@ -1559,8 +1586,7 @@ __global__ void __launch_bounds__(kStagedThreads, MB) cg_step_a_pg_staged_kernel
   __shared__ T cl[KS];
   CgState& S = a.st->cg;
   grid_dependency_wait();
-  if (!pg_begin(a, S)) return;
-  if (threadIdx.x < KS) cl[threadIdx.x] = ((int)threadIdx.x < a.k) ? c_of(S, threadIdx.x, T(0)) : (T)0;
+  if (!pg_begin<T, KB>(a, S, cl)) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool jac = a.dinv != nullptr;
   const int nst = a.stages;
@@ -1793,6 +1819,40 @@ __device__ __forceinline__ void pg2_issue_static(const CgArgs<T>& a, unsigned ch
   if (jac) bulk_g2s(b + a.off_d, a.dinv + row0, rb, bar);
 }
 
+// The same copies spread over the producer warp's lanes (the kernel's
+// prologue, where a single lane's issue loop would hold the whole block at
+// the begin phase's barrier): lane 0 arms the barrier with the tile's bytes,
+// then lane c issues copy c (A's values, its indices, V_hat column c - 2, the
+// Jacobi diagonal).
+template <typename T, int TSL>
+__device__ __forceinline__ void pg2_issue_static_warp(const CgArgs<T>& a, unsigned char* b, uint64_t* bar, int64_t t,
+                                                      int64_t e0, int64_t e1, uint64_t pol, int lane) {
+  constexpr int TR = TSL * kSlice;
+  const int ib = a.col16 ? 2 : 4;
+  const char* idx = a.col16 ? (const char*)a.col16 : (const char*)a.col;
+  const int64_t s0 = t * TSL, s1 = min(s0 + TSL, a.nslices);
+  const int64_t row0 = s0 * kSlice;
+  const uint32_t rb = (uint32_t)((s1 - s0) * kSlice * (int64_t)sizeof(T));
+  const uint32_t ne = (uint32_t)(e1 - e0);
+  const bool jac = a.dinv != nullptr;
+  if (lane == 0)
+    mbar_arrive_expect_tx(bar, ne * (uint32_t)(sizeof(T) + ib) + (uint32_t)(a.k + 2 + (jac ? 1 : 0)) * rb);
+  __syncwarp();
+  const int nc = 2 + a.k + (jac ? 1 : 0);
+  for (int c = lane; c < nc; c += 32) {
+    if (c == 0) {
+      if (ne > 0) bulk_g2s_hint(b, a.val + e0, ne * (uint32_t)sizeof(T), bar, pol);
+    } else if (c == 1) {
+      if (ne > 0) bulk_g2s_hint(b + a.off_col, idx + e0 * ib, ne * (uint32_t)ib, bar, pol);
+    } else if (c < 2 + a.k) {
+      const int l = c - 2;
+      bulk_g2s_hint(b + a.off_v + (size_t)l * TR * sizeof(T), a.V + (size_t)l * a.n_pad + row0, rb, bar, pol);
+    } else {
+      bulk_g2s(b + a.off_d, a.dinv + row0, rb, bar);
+    }
+  }
+}
+
 template <typename T, int TSL>
 __device__ __forceinline__ void pg2_issue_vectors(const CgArgs<T>& a, unsigned char* b, uint64_t* bar, int64_t t) {
   const int64_t s0 = t * TSL, s1 = min(s0 + TSL, a.nslices);
@@ -1802,19 +1862,14 @@ __device__ __forceinline__ void pg2_issue_vectors(const CgArgs<T>& a, unsigned c
   bulk_g2s(b + a.off_p, a.p_old + row0, rb, bar);
 }
 
-// returns false when the solve is no longer running (the block then leaves
-// once its copies have landed)
+// The stages before `pre` were issued whole by the kernel's prologue; with
+// run == false the producer only waits until their copies have landed.
 template <typename T, int TSL>
 __device__ __forceinline__ void pg2_producer(const CgArgs<T>& a, unsigned char* stage_mem, uint64_t* full,
                                              uint64_t* empty, int* stalled, int64_t ntl, int nst, bool run) {
   const int64_t G = gridDim.x;
   const uint64_t pol = l2_evict_first_policy();
-  const int64_t pre = min(ntl, (int64_t)(a.stall_test ? 1 : nst));  // stages whose static part is in flight
-  // the vectors of the prefetched stages (every thread has passed the grid dependency wait)
-  for (int64_t i = 0; i < pre; ++i) {
-    fence_proxy_async_smem();
-    pg2_issue_vectors<T, TSL>(a, stage_mem + (size_t)i * a.stage_bytes, &full[i], blockIdx.x + i * G);
-  }
+  const int64_t pre = min(ntl, (int64_t)(a.stall_test ? 1 : nst));  // stages issued before the loop
   int64_t issued = pre;
   if (run) {
     int st = (int)(pre % nst);
@@ -1858,6 +1913,7 @@ __global__ void __launch_bounds__(kStagedThreads, MB) cg_step_a_pg2_kernel(CgArg
   __shared__ __align__(8) uint64_t empty[kMaxStages];
   __shared__ int stalled;
   __shared__ T cls[KS];
+  __shared__ int run_flag;
   CgState& S = a.st->cg;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool jac = a.dinv != nullptr;
@@ -1874,23 +1930,55 @@ __global__ void __launch_bounds__(kStagedThreads, MB) cg_step_a_pg2_kernel(CgArg
     mbar_init_fence();
   }
   __syncthreads();
-  if (warp == kTileSlices && lane == 0) {  // static operands of the first stages
+  if (warp == kTileSlices) {  // static operands of the first stages, issued by the whole producer warp
     const uint64_t pol = l2_evict_first_policy();
     const int64_t pre = min(ntl, (int64_t)(a.stall_test ? 1 : nst));
-    for (int64_t i = 0; i < pre; ++i) {
+    int64_t e0[kMaxStages], e1[kMaxStages];  // their entry ranges, all loads in flight together
+#pragma unroll
+    for (int i = 0; i < kMaxStages; ++i) {
       const int64_t t = blockIdx.x + i * G;
-      pg2_issue_static<T, TSL>(a, stage_mem + (size_t)i * a.stage_bytes, &full[i], t, a.slice_ptr[t * TSL],
-                               a.slice_ptr[min((t + 1) * TSL, a.nslices)], pol);
+      e0[i] = i < pre ? a.slice_ptr[t * TSL] : 0;
+      e1[i] = i < pre ? a.slice_ptr[min((t + 1) * TSL, a.nslices)] : 0;
     }
+#pragma unroll
+    for (int i = 0; i < kMaxStages; ++i)
+      if (i < pre)
+        pg2_issue_static_warp<T, TSL>(a, stage_mem + (size_t)i * a.stage_bytes, &full[i], blockIdx.x + i * G, e0[i],
+                                      e1[i], pol, lane);
   }
-  grid_dependency_wait();  // the previous step b's p, s and partials are visible from here on
-  const bool run = pg_begin(a, S);
+  // entry offsets of the tile and of a consumer warp's slices 2 warp,
+  // 2 warp + 1 (fetched one tile ahead; the first before the dependency
+  // wait, as the matrix is static); a slice past the end has no entries
+  int64_t c_t0 = 0, c_a0 = 0, c_a1 = 0, c_b1 = 0;
+  auto fetch = [&](int64_t tt) {
+    const int64_t sa = tt * TSL + 2 * warp;
+    c_t0 = a.slice_ptr[tt * TSL];
+    c_a0 = a.slice_ptr[min(sa, a.nslices)];
+    c_a1 = a.slice_ptr[min(sa + 1, a.nslices)];
+    c_b1 = a.slice_ptr[min(sa + 2, a.nslices)];
+  };
+  if (warp < kTileSlices && ntl > 0) fetch(blockIdx.x);
+  grid_dependency_wait();  // the previous step b's p, s, c and partials are visible from here on
+  // The consumer warps run the begin phase among themselves (named barrier
+  // 1), so that the producer, whose bulk copies can block while the memory
+  // system drains the first stages, does not hold them; the producer learns
+  // the outcome at barrier 2, where the consumers only arrive.
+  bool run;
+  if (warp == kTileSlices) {  // the Krylov vectors of those stages, lane i issuing stage i's
+    const int64_t pre = min(ntl, (int64_t)(a.stall_test ? 1 : nst));
+    if (lane < pre)
+      pg2_issue_vectors<T, TSL>(a, stage_mem + (size_t)lane * a.stage_bytes, &full[lane], blockIdx.x + lane * G);
+    asm volatile("bar.sync 2, %0;" ::"n"(kStagedThreads) : "memory");
+    run = run_flag != 0;
+  } else {
+    run = pg_begin<T, KB, kThreads>(a, S, cls);
+    if (threadIdx.x == 0) run_flag = run ? 1 : 0;
+    asm volatile("bar.arrive 2, %0;" ::"n"(kStagedThreads) : "memory");
+  }
   if (!run) {  // the producer lets its copies land before the block leaves
     if (warp == kTileSlices && lane == 0) pg2_producer<T, TSL>(a, stage_mem, full, empty, &stalled, ntl, nst, false);
     return;
   }
-  if (threadIdx.x < KS) cls[threadIdx.x] = ((int)threadIdx.x < a.k) ? c_of(S, threadIdx.x, T(0)) : (T)0;
-  __syncthreads();
   T cl[KS];
 #pragma unroll
   for (int l = 0; l < KS; ++l) cl[l] = cls[l];
@@ -1903,17 +1991,6 @@ __global__ void __launch_bounds__(kStagedThreads, MB) cg_step_a_pg2_kernel(CgArg
   } else {
     const T* __restrict__ pv = a.p_old;
     const bool d16 = a.col16 != nullptr;
-    // entry offsets of the tile and of this warp's slices 2 warp, 2 warp + 1
-    // (one tile ahead); a slice past the end has no entries
-    int64_t c_t0 = 0, c_a0 = 0, c_a1 = 0, c_b1 = 0;
-    auto fetch = [&](int64_t tt) {
-      const int64_t sa = tt * TSL + 2 * warp;
-      c_t0 = a.slice_ptr[tt * TSL];
-      c_a0 = a.slice_ptr[min(sa, a.nslices)];
-      c_a1 = a.slice_ptr[min(sa + 1, a.nslices)];
-      c_b1 = a.slice_ptr[min(sa + 2, a.nslices)];
-    };
-    if (ntl > 0) fetch(blockIdx.x);
     int st = 0;
     uint32_t ph = 0;
     int64_t t = blockIdx.x;
@@ -1993,10 +2070,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? 2 : 4) cg_step_a_pg
   constexpr int KS = KB > 0 ? KB : 1;
   CgState& S = a.st->cg;
   grid_dependency_wait();
-  if (!pg_begin(a, S)) return;
   __shared__ T cl[KS];
-  if (threadIdx.x < KS) cl[threadIdx.x] = ((int)threadIdx.x < a.k) ? c_of(S, threadIdx.x, T(0)) : (T)0;
-  __syncthreads();
+  if (!pg_begin<T, KB>(a, S, cl)) return;
   const T* __restrict__ pv = a.p_old;
   const int lane = threadIdx.x & 31;
   const int64_t warp0 = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
@@ -2294,8 +2369,12 @@ void make_args(const InnerGraphSpec& spec, CgArgs<T> (&a)[2]) {
     x.off_d = geo.off_d;
     x.off_z = geo.off_z;
     x.st = spec.st;
-    x.partials = spec.partials;
-    x.partials_b = spec.partials + (size_t)kMaxNV * kMaxBlocks;  // allocated (kMaxNV + 2) x kMaxBlocks
+    // rows of kMaxBlocks: [0, kMaxNV) and [kMaxNV, 2 kMaxNV) step a's partials by
+    // the parity of the iteration (a step a reads the other parity's while its
+    // own blocks write theirs), then two rows of step b's
+    x.partials = spec.partials + (size_t)par * kMaxNV * kMaxBlocks;
+    x.partials_o = spec.partials + (size_t)(par ^ 1) * kMaxNV * kMaxBlocks;
+    x.partials_b = spec.partials + (size_t)2 * kMaxNV * kMaxBlocks;
     x.grid_a = spec.grid_spmv;
     x.grid_b = spec.grid_stream_b;
     x.par = par;
@@ -2498,10 +2577,15 @@ cudaError_t build_graph_t(const InnerGraphSpec& spec, cudaGraph_t* out_graph) {
     // successor may start once every block of its predecessor has started; it
     // waits for the predecessor's results with grid_dependency_wait), so a
     // step a streams its static operands while the previous step b finishes
-    const bool pdl = spec.pdl && (spec.var_a == 14 || spec.var_a == 15) && spec.ilu.nblk == 0 && !spec.dsmw;
-    cudaGraphEdgeData ed = {};
+    const bool pdl = spec.pdl != 0 && (spec.var_a == 14 || spec.var_a == 15) && spec.ilu.nblk == 0 && !spec.dsmw;
+    cudaGraphEdgeData ed = {}, ed_plain = {};
     ed.from_port = cudaGraphKernelNodePortLaunchCompletion;
     ed.type = cudaGraphDependencyTypeProgrammatic;
+    // pdl 1: both edges programmatic; 2 (default): only step b -> step a, whose
+    // static prefetch then overlaps step b's tail (an early step b slowed its
+    // own streaming, measured); 3: only step a -> step b
+    const cudaGraphEdgeData& e_ba = (spec.pdl == 1 || spec.pdl == 2) ? ed : ed_plain;
+    const cudaGraphEdgeData& e_ab = (spec.pdl == 1 || spec.pdl == 3) ? ed : ed_plain;
     for (int it = 0; it < spec.unroll; ++it) {
       void* aa[] = {&a[it & 1]};
       cudaGraphNode_t na, nb;
@@ -2509,10 +2593,10 @@ cudaError_t build_graph_t(const InnerGraphSpec& spec, cudaGraph_t* out_graph) {
         if ((e = add_kernel(body, &na, nullptr, 0, step_a_fn<T, KB>(spec.var_a), spec.grid_spmv,
                             step_a_block(spec), aa, smem_a)))
           goto fail;
-        if (prev && (e = cudaGraphAddDependencies(body, &prev, &na, &ed, 1))) goto fail;
+        if (prev && (e = cudaGraphAddDependencies(body, &prev, &na, &e_ba, 1))) goto fail;
         if ((e = add_kernel(body, &nb, nullptr, 0, step_b_fn<T, KB>(spec), spec.grid_stream_b, kThreads, aa)))
           goto fail;
-        if ((e = cudaGraphAddDependencies(body, &na, &nb, &ed, 1))) goto fail;
+        if ((e = cudaGraphAddDependencies(body, &na, &nb, &e_ab, 1))) goto fail;
         prev = nb;
         continue;
       }

@@ -77,6 +77,11 @@ struct CgState {
   double rho_s[2];
   long long it_s[2];
   int bp_s[2];
+  // V^T s, V^T p and c = 2|Lambda| V^T p of the one-gather iteration, slot
+  // j & 1 holding their values for iteration j (advanced by step a)
+  double u_s[2][kMaxK];
+  double t_s[2][kMaxK];
+  double c_s[2][kMaxK];
 };
 
 struct OuterState {
@@ -227,9 +232,20 @@ __device__ __forceinline__ bool last_block_after_partials(unsigned int* ticket) 
 // G: the grid that wrote the partials (this grid for a last block; the
 // previous kernel's when a kernel finishes its predecessor's reduction).
 constexpr int kFinalSumsThreads = 320;  // threads beyond this count only wait
-__device__ __forceinline__ void final_sums_g(const double* partials, int G, int nv, double* out) {
+// NT > 0: only the block's first NT threads take part (named barrier 1);
+// the others must not call.
+template <int NT>
+__device__ __forceinline__ void group_sync() {
+  if (NT == 0) __syncthreads();
+  else asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+}
+
+template <int NT = 0>
+__device__ __forceinline__ void final_sums_2(const double* pa, int ga, int na, const double* pb, int gb, int nb,
+                                             double* out) {
   __shared__ double fs[kFinalSumsThreads];
-  const int nt = min((int)blockDim.x, kFinalSumsThreads) & ~31;
+  const int nv = na + nb;
+  const int nt = (NT > 0 ? NT : min((int)blockDim.x, kFinalSumsThreads)) & ~31;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int g = max(1, nt / max(1, nv));  // threads per value
   const int nvr = nt / g;                 // values per round
@@ -237,7 +253,8 @@ __device__ __forceinline__ void final_sums_g(const double* partials, int G, int 
     const int i = i0 + tid / g, j = tid - (tid / g) * g;
     double s = 0.0;
     if (tid < nvr * g && i < nv) {
-      const double* x = partials + (size_t)i * G;
+      const int G = i < na ? ga : gb;
+      const double* x = i < na ? pa + (size_t)i * ga : pb + (size_t)(i - na) * gb;
       for (int b0 = j; b0 < G; b0 += 16 * g) {
         double v[16];
 #pragma unroll
@@ -250,15 +267,20 @@ __device__ __forceinline__ void final_sums_g(const double* partials, int G, int 
       }
     }
     if (tid < nt) fs[tid] = s;
-    __syncthreads();
+    group_sync<NT>();
     for (int v = warp; v < nvr && i0 + v < nv; v += nt >> 5) {
       double t = 0.0;
       for (int q = lane; q < g; q += 32) t += fs[v * g + q];
       t = warp_sum(t);
       if (lane == 0) out[i0 + v] = t;
     }
-    __syncthreads();
+    group_sync<NT>();
   }
+}
+
+// the na values of one grid's partials
+__device__ __forceinline__ void final_sums_g(const double* partials, int G, int nv, double* out) {
+  final_sums_2(partials, G, nv, nullptr, 1, 0, out);
 }
 
 __device__ __forceinline__ void final_sums(const double* partials, int nv, double* out) {

@@ -41,7 +41,7 @@ struct InnerGraphSpec {
   IluArgs ilu;               // block-Jacobi ILU(0) M_cg (ilu.nblk > 0): step b solves with the factors
   int64_t tile_entries = 0;    // most SELL entries in one tile of 8 slices (sizes the staged variants' buffers)
   int64_t tile_entries16 = 0;  // the same for tiles of 16 slices (variants 14, 15)
-  bool pdl = true;             // programmatic edges between the inner kernels of variants 14, 15 (MRCG_PDL=0: off)
+  int pdl = 2;                 // programmatic edges between the inner kernels of variants 14, 15 (MRCG_PDL)
   int stages = 3;            // staged variant: shared-memory stages per block
   bool stall_test = false;   // test hook: the staged producer issues only the first tile
 };

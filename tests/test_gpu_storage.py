@@ -28,7 +28,7 @@ import paper_1805_12417_gb300 as m  # noqa: E402
 
 MIB = 1 << 20
 SLICE = 32           # SELL slice height
-PARTIAL_SLOTS = (32 + 6) * 2048  # per-block reduction partials (FP64), step b's own two rows included
+PARTIAL_SLOTS = (2 * (32 + 4) + 2) * 2048  # per-block reduction partials (FP64): step a's by parity, step b's
 
 
 @pytest.fixture(scope="module")
