@@ -59,9 +59,11 @@ def parse():
     ap.add_argument("--workloads", default="saddle,shifted64,batch64",
                     help="comma-separated extra workloads measured after the headline and reported in the same "
                          "line under 'workloads' (saddle, shifted64, batch64; empty for none)")
-    ap.add_argument("--mcg", choices=["identity", "jacobi", "smw"], default="identity",
+    ap.add_argument("--mcg", choices=["identity", "jacobi", "smw", "ilu0", "smw_ilu0"], default="identity",
                     help="inner preconditioner of the single-system workloads: identity (default), Jacobi on "
-                         "M_mr, or smw, the MINRES-CG* form diag(A)^-1 - 2 V Lambda^-1 V^T (Sec. 2.1)")
+                         "M_mr, smw, the MINRES-CG* form diag(A)^-1 - 2 V Lambda^-1 V^T (Sec. 2.1), ilu0, block-Jacobi "
+                         "ILU(0) of A on blocks of 8,192 rows (Sec. 4), or smw_ilu0, MINRES-CG* with that ILU(0) as "
+                         "Atilde")
     return ap.parse_args()
 
 
@@ -165,6 +167,7 @@ class Clocks:
 
 KERNEL_SOURCES = ["paper_1805_12417_gb300/csrc/cg_impl.cuh", "paper_1805_12417_gb300/csrc/common.cuh"]
 TRAFFIC_RECORDS = "profiles/traffic.json"
+ILU_BLOCK = 8192  # rows per diagonal block of the block-Jacobi ILU(0) inner preconditioner
 
 
 def step_a_kernel_name(cfg, prec="float"):
@@ -282,8 +285,11 @@ def cpu_baseline_one(p, mcg="identity", threads=False, sample_iters=CPU_SAMPLE_I
     one full solve by the oracle's own recorded count (value None when none is
     recorded)."""
     import oracle as O
-    code = {"identity": O.MCG_IDENTITY, "jacobi": O.MCG_JACOBI, "smw": O.MCG_SMW}[mcg]
+    code = {"identity": O.MCG_IDENTITY, "jacobi": O.MCG_JACOBI, "smw": O.MCG_SMW, "ilu0": O.MCG_ILU0,
+            "smw_ilu0": O.MCG_SMW_ILU0}[mcg]
     s = O.System.from_problem(p)
+    if mcg in ("ilu0", "smw_ilu0"):
+        s.set_ilu0(ILU_BLOCK)
     cores = _cores(threads)
     build = f"all-core OpenMP build, {cores} threads" if threads else "serial build"
     if p.n <= 100_000:
@@ -458,7 +464,9 @@ def inner_bytes(cfg, n, nnz, k, w, mcg):
     if 9 <= var <= 15:  # one gather: p, r (and M_cg^-1) read, q written | p, q, z, r (M_cg^-1) read, z, r, p written
         return a_mat + 3 * n * w + jac, 7 * n * w + jac
     # two gathers: s, p (and M_cg^-1) read, q, p' written | p', q, z, r (M_cg^-1) read, z, r (s) written
-    b = 6 * n * w + (2 * jac if mcg == "jacobi" else 0) + (2 * n * w + k * n * w if mcg == "smw" else 0)
+    b = 6 * n * w + (2 * jac if mcg == "jacobi" else 0) + (2 * n * w + k * n * w if mcg in ("smw", "smw_ilu0") else 0)
+    if mcg in ("ilu0", "smw_ilu0"):  # the factors (at most nnz entries of value and 16-bit column), pivots, offsets
+        b += nnz * (w + 2) + n * (w + 8)
     return a_mat + 4 * n * w + jac, b
 
 
@@ -484,9 +492,11 @@ def measure_single(torch, m, p, dev, stream, ws, local, rank, steps, warmup, mcg
     (optionally) the end-to-end rate with host buffers and the CPU baseline."""
     b_dev = torch.from_numpy(p.b).to(dev)
     x_dev = torch.zeros(p.n, dtype=torch.float64, device=dev)
-    code = {"identity": m.MCG_IDENTITY, "jacobi": m.MCG_JACOBI, "smw": m.MCG_SMW}[mcg]
+    code = {"identity": m.MCG_IDENTITY, "jacobi": m.MCG_JACOBI, "smw": m.MCG_SMW, "ilu0": m.MCG_ILU0,
+            "smw_ilu0": m.MCG_SMW_ILU0}[mcg]
+    extra = {"ilu_block": ILU_BLOCK} if mcg in ("ilu0", "smw_ilu0") else {}
     solvers = {prec: m.Solver.from_problem(p, precision=prec, inner_prec=code, stream=stream.cuda_stream,
-                                           validate=False)
+                                           validate=False, **extra)
                for prec in (m.MIXED_FP32, m.FP64)}
     res, xs = {}, {}
     n, nnz, k = p.n, p.nnz, p.k
