@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--inner-tol", type=float, default=INNER_TOL,
                     help="relative recursive-residual tolerance of every inner CG solve (default 1e-3); the CPU "
                          "baseline of a sampled workload is scaled only by a count recorded at the same tolerance")
+    ap.add_argument("--ilu-block", type=int, default=None,
+                    help="rows per diagonal block of the ILU(0) inner preconditioners (default: the library's)")
     ap.add_argument("--workloads", default="saddle,shifted64,batch64",
                     help="comma-separated extra workloads measured after the headline and reported in the same "
                          "line under 'workloads' (saddle, shifted64, batch64; empty for none)")
@@ -167,7 +169,7 @@ class Clocks:
 
 KERNEL_SOURCES = ["paper_1805_12417_gb300/csrc/cg_impl.cuh", "paper_1805_12417_gb300/csrc/common.cuh"]
 TRAFFIC_RECORDS = "profiles/traffic.json"
-ILU_BLOCK = 8192  # rows per diagonal block of the block-Jacobi ILU(0) inner preconditioner
+ILU_BLOCK = 1024  # rows per diagonal block of the block-Jacobi ILU(0) inner preconditioner (--ilu-block)
 
 
 def step_a_kernel_name(cfg, prec="float"):
@@ -797,9 +799,11 @@ def workloads_block(args, torch, m, dev, stream, ws, local, rank):
 
 
 def main():
-    global INNER_TOL
+    global INNER_TOL, ILU_BLOCK
     args = parse()
     INNER_TOL = args.inner_tol
+    if args.ilu_block:
+        ILU_BLOCK = args.ilu_block
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, ws, rank)

@@ -46,6 +46,9 @@
  *                         2, the default: programmatic from step b to the next
  *                         step a, which streams its static operands while step b
  *                         finishes; 3: programmatic from step a to step b).
+ *  - MRCG_ILU_STAGE=0/1   ILU(0) sweeps read the factors from global memory (0)
+ *                         or from per-block images copied into shared memory
+ *                         (1); default: images in mixed precision, global in FP64.
  *  - MRCG_IDX16=0         keep 32-bit column indices in the inner kernels
  *                         (16-bit deltas are used whenever |col - row| <= 32767).
  *  - MRCG_UNROLL=U        inner iterations per convergence check (even, >= 2).
@@ -127,7 +130,7 @@ typedef struct {
                              (j >= 4 within the cycle); 0 selects 0.5, < 0 disables */
   void* stream;           /* cudaStream_t to order all work on; NULL = a stream of its own */
   int32_t ilu_block;      /* MRCG_MCG_ILU0 / MRCG_MCG_SMW_ILU0: rows per diagonal block, a multiple of 32 up to
-                             16384 (8192 with MRCG_FP64); 0 selects 8192 (capped at the padded n) */
+                             16384 (8192 with MRCG_FP64); 0 selects 1024 (capped at the padded n) */
   int32_t reserved;       /* set to 0 */
 } mrcg_create_args;
 

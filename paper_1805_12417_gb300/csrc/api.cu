@@ -383,7 +383,7 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
   IluArgs ilu;
   if (h->mcg == MRCG_MCG_ILU0 || h->mcg == MRCG_MCG_SMW_ILU0) {
     const int cap = h->fp32 ? kIluMaxBlock : kIluMaxBlock / 2;  // a block's values in shared memory
-    int bs = a->ilu_block > 0 ? a->ilu_block : 8192;
+    int bs = a->ilu_block > 0 ? a->ilu_block : 1024;  // 1024: 8 x-lines of a 128^3 grid, fastest per solve measured
     if (bs % 32 != 0 || bs > cap) return MRCG_ERR_INVALID;
     bs = (int)std::min<int64_t>(bs, n_pad);
     IluHost fh;
@@ -435,8 +435,35 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
     CK(cudaStreamSynchronize(h->stream));  // the host vectors go out of scope
     ilu.nblk = fh.nblk;
     ilu.bs = fh.bs;
-    const size_t per_warp = (size_t)bs * (h->fp32 ? sizeof(float) : sizeof(double));
-    ilu.wpc = (int)std::max<size_t>(1, std::min<size_t>(kThreads / 32, (size_t)(200 * 1024) / per_warp));
+    const size_t esz = h->fp32 ? sizeof(float) : sizeof(double);
+    size_t per_warp = (size_t)bs * esz;  // the block's values
+    // staged sweeps (FP32): each block's sweep data as one image a warp copies
+    // into shared memory next to its values, when an image of every block
+    // fits beside them (MRCG_ILU_STAGE=0: off, 1: also in FP64).  In FP64 the
+    // images are twice the size and the lost occupancy outweighed the shorter
+    // sweeps (measured at 128^3, blocks of 1024 and 2048 rows)
+    const char* stg = getenv("MRCG_ILU_STAGE");
+    if (stg ? atoi(stg) != 0 : h->fp32) {
+      std::vector<unsigned char> img;
+      std::vector<int64_t> img_off;
+      int img_max = 0;
+      if (ilu0_images(fh, esz, img, img_off, &img_max) && per_warp + (size_t)img_max <= (size_t)200 * 1024) {
+        unsigned char* d_img = nullptr;
+        int64_t* d_off = nullptr;
+        ST(dalloc(h, &d_img, img.size()));
+        ST(dalloc(h, &d_off, img_off.size()));
+        CK(cudaMemcpyAsync(d_img, img.data(), img.size(), cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemcpyAsync(d_off, img_off.data(), img_off.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
+                           h->stream));
+        CK(cudaStreamSynchronize(h->stream));  // the host vectors go out of scope
+        ilu.img = d_img;
+        ilu.img_off = d_off;
+        ilu.img_bytes = img_max;
+        per_warp += (size_t)img_max;
+      }
+    }
+    // blocks (warps) per CTA: two CTAs' worth of shared memory fit an SM
+    ilu.wpc = (int)std::max<size_t>(1, std::min<size_t>(kThreads / 32, (size_t)(110 * 1024) / per_warp));
     ilu.smw = h->mcg == MRCG_MCG_SMW_ILU0 ? 1 : 0;
     h->ilu_levels = fh.levels_f + fh.levels_b;
   }

@@ -436,6 +436,13 @@ __global__ void __launch_bounds__(kThreads) cg_step_b_smw_kernel(CgArgs<T> a) {
   }
 }
 
+// shared memory of one warp of the ILU(0) step b: the block's values, then the
+// largest sweep image (when staged)
+template <typename T>
+__host__ __device__ inline size_t ilu_warp_bytes(const IluArgs& f) {
+  return (size_t)f.bs * sizeof(T) + (size_t)f.img_bytes;
+}
+
 // ------------------------------------------------------------------ step b with the block-Jacobi ILU(0) M_cg
 //
 // The inner preconditioner of the paper's experiments (Sec. 4) is an
@@ -476,57 +483,121 @@ __global__ void __launch_bounds__(kThreads) cg_step_b_ilu_kernel(CgArgs<T> a, Il
   for (int l = 0; l < KS; ++l) wd[l] = 0;
   const int blk = blockIdx.x * f.wpc + warp;
   if (warp < f.wpc && blk < f.nblk) {
-    T* x = reinterpret_cast<T*>(ilu_smem) + (size_t)warp * f.bs;
+    unsigned char* wmem = ilu_smem + (size_t)warp * ilu_warp_bytes<T>(f);
+    T* x = reinterpret_cast<T*>(wmem);
     const int64_t b0 = (int64_t)blk * f.bs;
     const int m = (int)min((int64_t)f.bs, a.n_pad - b0);
     // CG updates of the block's rows; x = r, the right-hand side of the solve
-    for (int r = lane; r < m; r += 32) {
-      const int64_t i = b0 + r;
-      T rv = a.r[i];
-      if (!init) {
-        a.z[i] = a.z[i] + alpha * a.p_new[i];
-        rv -= alpha * a.q[i];
-        a.r[i] = rv;
+    // (eight rows per lane in flight: one warp streams the whole block)
+    constexpr int UR = 8;
+    for (int r0 = lane; r0 < m; r0 += 32 * UR) {
+      T rv[UR], zv[UR], pw[UR], qv[UR];
+#pragma unroll
+      for (int u = 0; u < UR; ++u) {
+        const int r = r0 + 32 * u;
+        if (r < m) {
+          const int64_t i = b0 + r;
+          rv[u] = a.r[i];
+          if (!init) {
+            zv[u] = a.z[i];
+            pw[u] = a.p_new[i];
+            qv[u] = a.q[i];
+          }
+        }
       }
-      x[r] = rv;
+#pragma unroll
+      for (int u = 0; u < UR; ++u) {
+        const int r = r0 + 32 * u;
+        if (r < m) {
+          const int64_t i = b0 + r;
+          if (!init) {
+            a.z[i] = zv[u] + alpha * pw[u];
+            rv[u] -= alpha * qv[u];
+            a.r[i] = rv[u];
+          }
+          x[r] = rv[u];
+        }
+      }
     }
     __syncwarp();
-    const T* fval = reinterpret_cast<const T*>(f.fval);
-    for (int lv = f.fblk[blk]; lv < f.fblk[blk + 1]; ++lv) {  // L y = r (unit diagonal)
-      for (int pos = f.flvl[lv] + lane; pos < f.flvl[lv + 1]; pos += 32) {
-        const int row = f.frow[pos];
-        T acc = x[row];
-        for (int e = f.fent[pos]; e < f.fent[pos + 1]; ++e) acc -= fval[e] * x[f.fcol[e]];
-        x[row] = acc;
-      }
-      __syncwarp();
-    }
-    const T* bval = reinterpret_cast<const T*>(f.bval);
-    const T* bdinv = reinterpret_cast<const T*>(f.bdinv);
-    for (int lv = f.bblk[blk]; lv < f.bblk[blk + 1]; ++lv) {  // U s = y
-      for (int pos = f.blvl[lv] + lane; pos < f.blvl[lv + 1]; pos += 32) {
-        const int row = f.brow[pos];
-        T acc = x[row];
-        for (int e = f.bent[pos]; e < f.bent[pos + 1]; ++e) acc -= bval[e] * x[f.bcol[e]];
-        x[row] = acc * bdinv[pos];
-      }
-      __syncwarp();
-    }
-    for (int r = lane; r < m; r += 32) {  // each lane rereads the residual rows it wrote itself
-      const int64_t i = b0 + r;
-      const T rv = a.r[i];
-      const T xr = x[r];
-      T sv = xr;
-#pragma unroll
-      for (int l = 0; l < KB; ++l)
-        if (l < a.k) {
-          const T v = a.V[(size_t)l * a.n_pad + i];
-          wd[l] += v * xr;
-          if (f.smw) sv += v * es[l];
+    if (f.img_bytes > 0) {  // sweeps from this block's images, copied into shared memory
+      unsigned char* im = wmem + (size_t)f.bs * sizeof(T);
+      for (int back = 0; back < 2; ++back) {
+        const uint4* src = reinterpret_cast<const uint4*>(f.img + f.img_off[2 * (int64_t)blk + back]);
+        const int4 hdr = __ldg(reinterpret_cast<const int4*>(src));
+        const IluImage g = ilu_image_layout(hdr.x, hdr.y, hdr.z, (int)sizeof(T), back != 0);
+        uint4* dst = reinterpret_cast<uint4*>(im);
+        for (int c = lane; c < g.bytes / 16; c += 32) dst[c] = __ldg(src + c);
+        __syncwarp();
+        const uint16_t* lv = reinterpret_cast<const uint16_t*>(im + g.lv);
+        const uint16_t* rw = reinterpret_cast<const uint16_t*>(im + g.rows);
+        const uint16_t* en = reinterpret_cast<const uint16_t*>(im + g.ent);
+        const uint16_t* cl = reinterpret_cast<const uint16_t*>(im + g.cols);
+        const T* vl = reinterpret_cast<const T*>(im + g.vals);
+        const T* di = reinterpret_cast<const T*>(im + g.dinv);
+        for (int l = 0; l < hdr.y; ++l) {  // L y = r (unit diagonal), then U s = y
+          for (int pos = lv[l] + lane; pos < lv[l + 1]; pos += 32) {
+            const int row = rw[pos];
+            T acc = x[row];
+            for (int e = en[pos]; e < en[pos + 1]; ++e) acc -= vl[e] * x[cl[e]];
+            x[row] = back ? acc * di[pos] : acc;
+          }
+          __syncwarp();
         }
-      a.s[i] = sv;
-      rs += rv * sv;
-      rr += rv * rv;
+      }
+    } else {
+      const T* fval = reinterpret_cast<const T*>(f.fval);
+      for (int lv = f.fblk[blk]; lv < f.fblk[blk + 1]; ++lv) {  // L y = r (unit diagonal)
+        for (int pos = f.flvl[lv] + lane; pos < f.flvl[lv + 1]; pos += 32) {
+          const int row = f.frow[pos];
+          T acc = x[row];
+          for (int e = f.fent[pos]; e < f.fent[pos + 1]; ++e) acc -= fval[e] * x[f.fcol[e]];
+          x[row] = acc;
+        }
+        __syncwarp();
+      }
+      const T* bval = reinterpret_cast<const T*>(f.bval);
+      const T* bdinv = reinterpret_cast<const T*>(f.bdinv);
+      for (int lv = f.bblk[blk]; lv < f.bblk[blk + 1]; ++lv) {  // U s = y
+        for (int pos = f.blvl[lv] + lane; pos < f.blvl[lv + 1]; pos += 32) {
+          const int row = f.brow[pos];
+          T acc = x[row];
+          for (int e = f.bent[pos]; e < f.bent[pos + 1]; ++e) acc -= bval[e] * x[f.bcol[e]];
+          x[row] = acc * bdinv[pos];
+        }
+        __syncwarp();
+      }
+    }
+    // s, its V_hat projections and the dot products (each lane rereads the
+    // residual rows it wrote itself; UV rows per lane in flight)
+    constexpr int UV = KB <= 12 ? 4 : (KB <= 24 ? 2 : 1);
+    for (int r0 = lane; r0 < m; r0 += 32 * UV) {
+      T rv[UV], vv[UV][KS];
+#pragma unroll
+      for (int u = 0; u < UV; ++u) {
+        const int r = r0 + 32 * u;
+        const int64_t i = b0 + (r < m ? r : 0);
+        rv[u] = r < m ? a.r[i] : (T)0;
+#pragma unroll
+        for (int l = 0; l < KB; ++l) vv[u][l] = (r < m && l < a.k) ? a.V[(size_t)l * a.n_pad + i] : (T)0;
+      }
+#pragma unroll
+      for (int u = 0; u < UV; ++u) {
+        const int r = r0 + 32 * u;
+        if (r < m) {
+          const T xr = x[r];
+          T sv = xr;
+#pragma unroll
+          for (int l = 0; l < KB; ++l)
+            if (l < a.k) {
+              wd[l] += vv[u][l] * xr;
+              if (f.smw) sv += vv[u][l] * es[l];
+            }
+          a.s[b0 + r] = sv;
+          rs += rv[u] * sv;
+          rr += rv[u] * rv[u];
+        }
+      }
     }
   }
   T acc[KB + 2];
@@ -2474,7 +2545,7 @@ const void* step_b_fn(const InnerGraphSpec& spec) {
 inline int ilu_grid(const InnerGraphSpec& spec) { return (spec.ilu.nblk + spec.ilu.wpc - 1) / spec.ilu.wpc; }
 template <typename T>
 unsigned ilu_smem(const InnerGraphSpec& spec) {
-  return (unsigned)((size_t)spec.ilu.wpc * spec.ilu.bs * sizeof(T));
+  return (unsigned)((size_t)spec.ilu.wpc * ilu_warp_bytes<T>(spec.ilu));
 }
 
 template <typename T, int KB>

@@ -20,6 +20,7 @@
 // order, so each sweep streams them once.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "ilu.h"
@@ -155,6 +156,58 @@ mrcg_status ilu0_build(int64_t n, int64_t n_pad, const std::vector<int64_t>& rp,
   out.levels_f = (int64_t)out.flvl.size() - 1;
   out.levels_b = (int64_t)out.blvl.size() - 1;
   return MRCG_OK;
+}
+
+bool ilu0_images(const IluHost& fh, size_t esz, std::vector<unsigned char>& img, std::vector<int64_t>& off,
+                 int* max_bytes) {
+  img.clear();
+  off.assign(2 * (size_t)fh.nblk, 0);
+  *max_bytes = 0;
+  for (int b = 0; b < fh.nblk; ++b) {
+    for (int back = 0; back < 2; ++back) {
+      const std::vector<int32_t>& blk = back ? fh.bblk : fh.fblk;
+      const std::vector<int32_t>& lvl = back ? fh.blvl : fh.flvl;
+      const std::vector<int32_t>& row = back ? fh.brow : fh.frow;
+      const std::vector<int32_t>& ent = back ? fh.bent : fh.fent;
+      const std::vector<uint16_t>& col = back ? fh.bcol : fh.fcol;
+      const std::vector<double>& val = back ? fh.bval : fh.fval;
+      const int L0 = blk[b], L1 = blk[b + 1], nlev = L1 - L0;
+      const int64_t P0 = lvl[L0], P1 = lvl[L1];
+      const int m = (int)(P1 - P0);
+      const int64_t E0 = ent[P0], E1 = ent[P1];
+      if (E1 - E0 > 65535 || m > 65535) return false;
+      const int ne = (int)(E1 - E0);
+      const IluImage g = ilu_image_layout(m, nlev, ne, (int)esz, back != 0);
+      const size_t o = img.size();
+      off[2 * (size_t)b + back] = (int64_t)o;
+      img.resize(o + g.bytes, 0);
+      unsigned char* p = img.data() + o;
+      const int32_t hdr[4] = {m, nlev, ne, 0};
+      std::memcpy(p, hdr, sizeof(hdr));
+      uint16_t* lv = reinterpret_cast<uint16_t*>(p + g.lv);
+      for (int l = 0; l <= nlev; ++l) lv[l] = (uint16_t)(lvl[L0 + l] - P0);
+      uint16_t* rw = reinterpret_cast<uint16_t*>(p + g.rows);
+      uint16_t* en = reinterpret_cast<uint16_t*>(p + g.ent);
+      for (int i = 0; i < m; ++i) {
+        rw[i] = (uint16_t)row[P0 + i];
+        en[i] = (uint16_t)(ent[P0 + i] - E0);
+      }
+      en[m] = (uint16_t)ne;
+      uint16_t* cl = reinterpret_cast<uint16_t*>(p + g.cols);
+      for (int e = 0; e < ne; ++e) cl[e] = col[E0 + e];
+      for (int e = 0; e < ne; ++e) {
+        if (esz == 4) reinterpret_cast<float*>(p + g.vals)[e] = (float)val[E0 + e];
+        else reinterpret_cast<double*>(p + g.vals)[e] = val[E0 + e];
+      }
+      if (back)
+        for (int i = 0; i < m; ++i) {
+          if (esz == 4) reinterpret_cast<float*>(p + g.dinv)[i] = (float)fh.bdinv[P0 + i];
+          else reinterpret_cast<double*>(p + g.dinv)[i] = fh.bdinv[P0 + i];
+        }
+      *max_bytes = std::max(*max_bytes, g.bytes);
+    }
+  }
+  return true;
 }
 
 }  // namespace mrcg

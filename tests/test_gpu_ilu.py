@@ -122,3 +122,22 @@ def test_full_size_mixed_solve_with_ilu():
     assert info.inner_iters_total < 2184  # M_cg = I needs 2184 at this tolerance
     print(f"ILU(0) 8192-row blocks at 128^3: outer {info.outer_iters}, inner {info.inner_iters_total}, "
           f"{info.solve_ms:.1f} ms")
+
+
+@pytest.mark.parametrize("block", [64, 2048])
+@pytest.mark.parametrize("mcg", [m.MCG_ILU0, m.MCG_SMW_ILU0], ids=["ilu0", "smw_ilu0"])
+@pytest.mark.parametrize("prec", [m.FP64, m.MIXED_FP32], ids=["fp64", "mixed"])
+def test_staged_sweeps_equal_global_sweeps(block, mcg, prec, monkeypatch):
+    """The sweeps from the per-block images copied into shared memory do the
+    same operations in the same order as the sweeps from global memory:
+    bitwise the same inner solve (and the oracle's within its bar)."""
+    p = small_3d()
+    y = np.random.default_rng(block + 1).standard_normal(p.n)
+    out = []
+    for stage in ("1", "0"):
+        monkeypatch.setenv("MRCG_ILU_STAGE", stage)
+        with m.Solver.from_problem(p, precision=prec, inner_prec=mcg, ilu_block=block) as g:
+            out.append(g.inner_solve(y, inner_tol=1e-8 if prec == m.FP64 else 1e-4))
+    (z1, st1, it1), (z0, st0, it0) = out
+    assert st1 == st0 == m.OK and it1 == it0
+    assert np.array_equal(z1, z0)
