@@ -45,6 +45,9 @@ def main(argv=None):
     ap.add_argument("--var-a", type=int, default=None, help="step-a kernel variant (0-15)")
     ap.add_argument("--bpsm-a", type=int, default=None, help="step-a blocks per SM")
     ap.add_argument("--bpsm-b", type=int, default=None, help="step-b blocks per SM")
+    ap.add_argument("--mcg", default="identity", choices=["identity", "jacobi", "smw", "ilu0", "smw_ilu0"],
+                    help="inner preconditioner M_cg of the single-system workloads")
+    ap.add_argument("--ilu-block", type=int, default=0, help="ILU(0) block rows (0: the library default)")
     a = ap.parse_args(argv)
     # read by the library when the solver is created
     for key, val in (("MRCG_VAR_A", a.var_a), ("MRCG_BPSM_A", a.bpsm_a), ("MRCG_BPSM_B", a.bpsm_b)):
@@ -73,10 +76,12 @@ def main(argv=None):
                           "inner_iters": int(sum(i.inner_iters_total for i in infos))}))
         return
     p = workload(a.workload)
-    with m.Solver.from_problem(p, precision=prec, validate=False) as s:
+    mcg = {"identity": m.MCG_IDENTITY, "jacobi": m.MCG_JACOBI, "smw": m.MCG_SMW, "ilu0": m.MCG_ILU0,
+           "smw_ilu0": m.MCG_SMW_ILU0}[a.mcg]
+    with m.Solver.from_problem(p, precision=prec, validate=False, inner_prec=mcg, ilu_block=a.ilu_block) as s:
         ta, tb = m.time_inner_kernels(s.h, a.iters)
         cfg = m.launch_config(s.h)
-    print(json.dumps({"workload": p.name, "precision": a.precision, "iters": a.iters, "step_a_ms": ta,
+    print(json.dumps({"workload": p.name, "precision": a.precision, "mcg": a.mcg, "iters": a.iters, "step_a_ms": ta,
                       "step_b_ms": tb, "launch_config": cfg}))
 
 
