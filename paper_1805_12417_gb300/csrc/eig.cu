@@ -45,13 +45,6 @@ struct Csr {
 };
 
 // Y = ca * (A X) + cx * X + cp * P   (P may be null when cp == 0)
-//
-// A warp takes 4 consecutive rows per trip.  When the 4 rows hold at most 32
-// entries and none more than 8 (stencil rows), one coalesced load brings all
-// their values and columns, and the gathers of two rows (one row of a 64-wide
-// block) are all in flight together; other groups take each row's entries 32
-// at a time.  Every
-// row sums its entries in CSR order, so both forms give the same bits.
 template <int NM>
 __global__ void __launch_bounds__(kThreads) eig_cheb_kernel(Csr A, const double* __restrict__ X,
                                                            const double* __restrict__ P, double* __restrict__ Y,
@@ -59,95 +52,30 @@ __global__ void __launch_bounds__(kThreads) eig_cheb_kernel(Csr A, const double*
   constexpr int MP = 32 * NM;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
-  for (int64_t r0 = ((int64_t)blockIdx.x * (kThreads / 32) + warp) * 4; r0 < A.n; r0 += nwarps * 4) {
-    const int nr = (int)min((int64_t)4, A.n - r0);
-    const int64_t rp = lane <= nr ? A.rowptr[r0 + lane] : 0;
-    const int64_t nxt = __shfl_sync(0xffffffffu, rp, min(lane + 1, 31));
-    const int len_l = lane < nr ? (int)(nxt - rp) : 0;
-    const int64_t g0 = __shfl_sync(0xffffffffu, rp, 0);
-    const int tot = (int)(__shfl_sync(0xffffffffu, rp, nr) - g0);
-    const bool fast = tot <= 32 && __all_sync(0xffffffffu, len_l <= 8);
-    // own rows of X (and P) for the 4 rows: independent of the entries
-    double xo[4][NM], po[4][NM];
+  for (int64_t row = (int64_t)blockIdx.x * (kThreads / 32) + warp; row < A.n; row += nwarps) {
+    const int64_t e0 = A.rowptr[row];
+    const int nnz = (int)(A.rowptr[row + 1] - e0);
+    double acc[NM];
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+    for (int g = 0; g < NM; ++g) acc[g] = 0.0;
+    for (int base = 0; base < nnz; base += 32) {
+      const bool has = lane + base < nnz;
+      const double my_val = has ? A.val[e0 + base + lane] : 0.0;
+      const int my_col = has ? A.col[e0 + base + lane] : 0;
+      const int cnt = min(32, nnz - base);
+      for (int j = 0; j < cnt; ++j) {
+        const double av = __shfl_sync(0xffffffffu, my_val, j);
+        const int64_t cj = (int64_t)__shfl_sync(0xffffffffu, my_col, j) * MP + lane;
 #pragma unroll
-      for (int g = 0; g < NM; ++g) {
-        const int64_t idx = (r0 + q) * MP + 32 * g + lane;
-        xo[q][g] = q < nr ? X[idx] : 0.0;
-        po[q][g] = (q < nr && cp != 0.0) ? P[idx] : 0.0;
-      }
-    double acc[4][NM];
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int g = 0; g < NM; ++g) acc[q][g] = 0.0;
-    if (fast) {
-      const double my_val = lane < tot ? A.val[g0 + lane] : 0.0;
-      const int my_col = lane < tot ? A.col[g0 + lane] : 0;
-      constexpr int U = NM == 1 ? 2 : 1;  // rows whose gathers are in flight together
-#pragma unroll
-      for (int h = 0; h < 4; h += U) {
-        double gx[U][8][NM];
-        int len[U], st[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int q = h + u;
-          st[u] = (int)(__shfl_sync(0xffffffffu, rp, q) - g0);
-          len[u] = __shfl_sync(0xffffffffu, len_l, q);
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int64_t cj = (int64_t)__shfl_sync(0xffffffffu, my_col, (st[u] + j) & 31) * MP + lane;
-#pragma unroll
-            for (int g = 0; g < NM; ++g) gx[u][j][g] = j < len[u] ? __ldg(X + cj + 32 * g) : 0.0;
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const double av = __shfl_sync(0xffffffffu, my_val, (st[u] + j) & 31);
-            if (j < len[u])
-#pragma unroll
-              for (int g = 0; g < NM; ++g) acc[h + u][g] = fma(av, gx[u][j][g], acc[h + u][g]);
-          }
-      }
-    } else {
-      for (int q = 0; q < nr; ++q) {
-        const int64_t e0 = __shfl_sync(0xffffffffu, rp, q);
-        const int nnz = __shfl_sync(0xffffffffu, len_l, q);
-        double a[NM];
-#pragma unroll
-        for (int g = 0; g < NM; ++g) a[g] = 0.0;
-        for (int base = 0; base < nnz; base += 32) {
-          const bool has = lane + base < nnz;
-          const double my_val = has ? A.val[e0 + base + lane] : 0.0;
-          const int my_col = has ? A.col[e0 + base + lane] : 0;
-          const int cnt = min(32, nnz - base);
-          for (int j = 0; j < cnt; ++j) {
-            const double av = __shfl_sync(0xffffffffu, my_val, j);
-            const int64_t cj = (int64_t)__shfl_sync(0xffffffffu, my_col, j) * MP + lane;
-#pragma unroll
-            for (int g = 0; g < NM; ++g) a[g] = fma(av, __ldg(X + cj + 32 * g), a[g]);
-          }
-        }
-        // q is warp-uniform: select the accumulator row without dynamic indexing
-#pragma unroll
-        for (int qq = 0; qq < 4; ++qq)
-          if (qq == q)
-#pragma unroll
-            for (int g = 0; g < NM; ++g) acc[qq][g] = a[g];
+        for (int g = 0; g < NM; ++g) acc[g] = fma(av, __ldg(X + cj + 32 * g), acc[g]);
       }
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (q >= nr) break;
-#pragma unroll
-      for (int g = 0; g < NM; ++g) {
-        double y = ca * acc[q][g] + cx * xo[q][g];
-        if (cp != 0.0) y += cp * po[q][g];
-        Y[(r0 + q) * MP + 32 * g + lane] = y;
-      }
+    for (int g = 0; g < NM; ++g) {
+      const int64_t idx = row * MP + lane + 32 * g;
+      double y = ca * acc[g] + cx * X[idx];
+      if (cp != 0.0) y += cp * P[idx];
+      Y[idx] = y;
     }
   }
 }

@@ -184,15 +184,12 @@ __global__ void __launch_bounds__(kThreads) sh_step_a_kernel(SArgs<T> a) {
                    ? (T)(sizeof(T) == 4 ? (double)a.st[c].cg.c32[l] : a.st[c].cg.c[l])
                    : (T)0;
   }
-  // lanes of columns whose inner solve is not running neither load nor store
-  // their vectors: a sector whose columns have all stopped is not fetched
   T beta[NM], sig[NM];
-  bool on[NM];
 #pragma unroll
   for (int m = 0; m < NM; ++m) {
     const int c = (threadIdx.x & 31) + 32 * m;
-    on[m] = c < a.nc && in_round(a.st[c]) && a.st[c].cg.done == kRunning;
-    beta[m] = on[m] ? (T)(sizeof(T) == 4 ? (double)a.st[c].cg.beta32 : a.st[c].cg.beta) : (T)0;
+    const bool on = c < a.nc && in_round(a.st[c]) && a.st[c].cg.done == kRunning;
+    beta[m] = on ? (T)(sizeof(T) == 4 ? (double)a.st[c].cg.beta32 : a.st[c].cg.beta) : (T)0;
     sig[m] = (T)a.sigma[c];
   }
   __syncthreads();
@@ -219,8 +216,8 @@ __global__ void __launch_bounds__(kThreads) sh_step_a_kernel(SArgs<T> a) {
 #pragma unroll
         for (int m = 0; m < NM; ++m) {
           const int64_t idx = row * a.ncp + lane + 32 * m;
-          srow[q][m] = (ok && on[m]) ? sv[idx] : (T)0;
-          prow[q][m] = (ok && on[m]) ? po[idx] : (T)0;
+          srow[q][m] = ok ? sv[idx] : (T)0;
+          prow[q][m] = ok ? po[idx] : (T)0;
         }
       }
 #pragma unroll
@@ -234,8 +231,8 @@ __global__ void __launch_bounds__(kThreads) sh_step_a_kernel(SArgs<T> a) {
           const int64_t cj = (int64_t)__shfl_sync(0xffffffffu, my_col, q * 8 + j) * a.ncp + lane;
 #pragma unroll
           for (int m = 0; m < NM; ++m) {
-            gs[j][m] = on[m] ? __ldg(sv + cj + 32 * m) : (T)0;
-            gp[j][m] = on[m] ? __ldg(po + cj + 32 * m) : (T)0;
+            gs[j][m] = __ldg(sv + cj + 32 * m);
+            gp[j][m] = __ldg(po + cj + 32 * m);
           }
         }
         T acc[NM], pn[NM];
@@ -256,10 +253,8 @@ __global__ void __launch_bounds__(kThreads) sh_step_a_kernel(SArgs<T> a) {
 #pragma unroll
         for (int m = 0; m < NM; ++m) {
           const int64_t idx = row * a.ncp + lane + 32 * m;
-          if (on[m]) {
-            a.q[idx] = acc[m];
-            a.p_new[idx] = pn[m];
-          }
+          a.q[idx] = acc[m];
+          a.p_new[idx] = pn[m];
           dot[0][m] += pn[m] * acc[m];
         }
       }
@@ -274,8 +269,8 @@ __global__ void __launch_bounds__(kThreads) sh_step_a_kernel(SArgs<T> a) {
 #pragma unroll
     for (int m = 0; m < NM; ++m) {
       const int64_t idx = row * a.ncp + lane + 32 * m;
-      srow[m] = on[m] ? sv[idx] : (T)0;
-      prow[m] = on[m] ? po[idx] : (T)0;
+      srow[m] = sv[idx];
+      prow[m] = po[idx];
     }
     const int64_t e0 = a.rowptr[row];
     const int nnz = (int)(a.rowptr[row + 1] - e0);
@@ -294,8 +289,8 @@ __global__ void __launch_bounds__(kThreads) sh_step_a_kernel(SArgs<T> a) {
         const int64_t cj = (int64_t)__shfl_sync(0xffffffffu, my_col, j) * a.ncp + lane;
 #pragma unroll
         for (int m = 0; m < NM; ++m) {
-          gs[j][m] = (j < nnz && on[m]) ? __ldg(sv + cj + 32 * m) : (T)0;
-          gp[j][m] = (j < nnz && on[m]) ? __ldg(po + cj + 32 * m) : (T)0;
+          gs[j][m] = (j < nnz) ? __ldg(sv + cj + 32 * m) : (T)0;
+          gp[j][m] = (j < nnz) ? __ldg(po + cj + 32 * m) : (T)0;
         }
       }
 #pragma unroll
@@ -313,7 +308,7 @@ __global__ void __launch_bounds__(kThreads) sh_step_a_kernel(SArgs<T> a) {
           const int64_t cj = (int64_t)__shfl_sync(0xffffffffu, my_col, j) * a.ncp + lane;
 #pragma unroll
           for (int m = 0; m < NM; ++m)
-            if (on[m]) acc[m] += av * (__ldg(sv + cj + 32 * m) + beta[m] * __ldg(po + cj + 32 * m));
+            acc[m] += av * (__ldg(sv + cj + 32 * m) + beta[m] * __ldg(po + cj + 32 * m));
         }
       }
     }
@@ -332,10 +327,8 @@ __global__ void __launch_bounds__(kThreads) sh_step_a_kernel(SArgs<T> a) {
 #pragma unroll
     for (int m = 0; m < NM; ++m) {
       const int64_t idx = row * a.ncp + lane + 32 * m;
-      if (on[m]) {
-        a.q[idx] = acc[m];
-        a.p_new[idx] = pn[m];
-      }
+      a.q[idx] = acc[m];
+      a.p_new[idx] = pn[m];
       dot[0][m] += pn[m] * acc[m];
     }
   }
@@ -346,14 +339,12 @@ template <typename T, int NM, int KV>
 __global__ void __launch_bounds__(kThreads) sh_step_b_kernel(SArgs<T> a) {
   __shared__ T sm[(KV + 1) * NM * 32];
   T alpha[NM];
-  bool on[NM];
 #pragma unroll
   for (int m = 0; m < NM; ++m) {
     const int c = (threadIdx.x & 31) + 32 * m;
-    on[m] = c < a.nc && in_round(a.st[c]) && a.st[c].cg.done == kRunning;
-    // finished or idle columns keep z and r, and their lanes skip the loads
-    // and stores (their partial sums are zero and not read)
-    alpha[m] = on[m] ? (T)(sizeof(T) == 4 ? (double)a.st[c].cg.alpha32 : a.st[c].cg.alpha) : (T)0;
+    const bool on = c < a.nc && in_round(a.st[c]) && a.st[c].cg.done == kRunning;
+    // finished or idle columns keep z and r: alpha = 0
+    alpha[m] = on ? (T)(sizeof(T) == 4 ? (double)a.st[c].cg.alpha32 : a.st[c].cg.alpha) : (T)0;
   }
   T acc[KV + 1][NM];
 #pragma unroll
@@ -374,11 +365,10 @@ __global__ void __launch_bounds__(kThreads) sh_step_b_kernel(SArgs<T> a) {
 #pragma unroll
       for (int m = 0; m < NM; ++m) {
         const int64_t idx = rows[h] * a.ncp + lane + 32 * m;
-        const bool ld = ok && on[m];
-        pn[h][m] = ld ? a.p_new[idx] : (T)0;
-        qv[h][m] = ld ? a.q[idx] : (T)0;
-        zv[h][m] = ld ? a.z[idx] : (T)0;
-        rv[h][m] = ld ? a.r[idx] : (T)0;
+        pn[h][m] = ok ? a.p_new[idx] : (T)0;
+        qv[h][m] = ok ? a.q[idx] : (T)0;
+        zv[h][m] = ok ? a.z[idx] : (T)0;
+        rv[h][m] = ok ? a.r[idx] : (T)0;
       }
     }
 #pragma unroll
@@ -387,11 +377,9 @@ __global__ void __launch_bounds__(kThreads) sh_step_b_kernel(SArgs<T> a) {
 #pragma unroll
       for (int m = 0; m < NM; ++m) {
         const int64_t idx = rows[h] * a.ncp + lane + 32 * m;
+        a.z[idx] = zv[h][m] + alpha[m] * pn[h][m];
         rv[h][m] = rv[h][m] - alpha[m] * qv[h][m];
-        if (on[m]) {
-          a.z[idx] = zv[h][m] + alpha[m] * pn[h][m];
-          a.r[idx] = rv[h][m];
-        }
+        a.r[idx] = rv[h][m];
         acc[0][m] += rv[h][m] * rv[h][m];
       }
 #pragma unroll
