@@ -147,8 +147,11 @@ __global__ void __launch_bounds__(kThreads) b_vnorm_kernel(DevState* st, const S
   }
 }
 
+// CTAs per SM the V_hat-width buckets are compiled for (register budgets)
+constexpr int b_min_blocks(int kb) { return kb >= 24 ? 2 : kb >= 16 ? 3 : 4; }
+
 template <typename T, int KB>
-__global__ void __launch_bounds__(kThreads, KB >= 32 ? 2 : 4) b_init_kernel(BArgs<T> a) {
+__global__ void __launch_bounds__(kThreads, b_min_blocks(KB)) b_init_kernel(BArgs<T> a) {
   constexpr int W = V16<T>::W;
   constexpr int KS = KB > 0 ? KB : 1;
   const bool jac = a.dinv != nullptr;
@@ -225,7 +228,7 @@ __global__ void __launch_bounds__(kThreads, KB >= 32 ? 2 : 4) b_init_kernel(BArg
 }
 
 template <typename T, int KB>
-__global__ void __launch_bounds__(kThreads, 4) b_step_a_kernel(BArgs<T> a) {
+__global__ void __launch_bounds__(kThreads, KB >= 24 ? 3 : 4) b_step_a_kernel(BArgs<T> a) {
   constexpr int KS = KB > 0 ? KB : 1;
   __shared__ T cl[KS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -302,7 +305,7 @@ __global__ void __launch_bounds__(kThreads, 4) b_step_a_kernel(BArgs<T> a) {
 }
 
 template <typename T, int KB>
-__global__ void __launch_bounds__(kThreads, KB >= 32 ? 2 : 4) b_step_b_kernel(BArgs<T> a) {
+__global__ void __launch_bounds__(kThreads, b_min_blocks(KB)) b_step_b_kernel(BArgs<T> a) {
   constexpr int W = V16<T>::W;
   constexpr int KS = KB > 0 ? KB : 1;
   const bool jac = a.dinv != nullptr;
@@ -810,11 +813,13 @@ cudaError_t run_host_any(const GraphSpec& gs, cudaStream_t stream) {
     if (gs.kb == 0) return run_host<float, 0>(gs, stream);
     if (gs.kb == 8) return run_host<float, 8>(gs, stream);
     if (gs.kb == 16) return run_host<float, 16>(gs, stream);
+    if (gs.kb == 24) return run_host<float, 24>(gs, stream);
     return run_host<float, 32>(gs, stream);
   }
   if (gs.kb == 0) return run_host<double, 0>(gs, stream);
   if (gs.kb == 8) return run_host<double, 8>(gs, stream);
   if (gs.kb == 16) return run_host<double, 16>(gs, stream);
+  if (gs.kb == 24) return run_host<double, 24>(gs, stream);
   return run_host<double, 32>(gs, stream);
 }
 
@@ -823,11 +828,13 @@ cudaError_t build_graph_any(const GraphSpec& gs, cudaGraph_t* out) {
     if (gs.kb == 0) return build_graph<float, 0>(gs, out);
     if (gs.kb == 8) return build_graph<float, 8>(gs, out);
     if (gs.kb == 16) return build_graph<float, 16>(gs, out);
+    if (gs.kb == 24) return build_graph<float, 24>(gs, out);
     return build_graph<float, 32>(gs, out);
   }
   if (gs.kb == 0) return build_graph<double, 0>(gs, out);
   if (gs.kb == 8) return build_graph<double, 8>(gs, out);
   if (gs.kb == 16) return build_graph<double, 16>(gs, out);
+  if (gs.kb == 24) return build_graph<double, 24>(gs, out);
   return build_graph<double, 32>(gs, out);
 }
 
@@ -839,17 +846,21 @@ int occupancy(bool fp32, int kb, int* occ_b) {
   if (fp32) {
     fa = kb == 0 ? (const void*)b_step_a_kernel<float, 0>
        : kb == 8 ? (const void*)b_step_a_kernel<float, 8>
-       : kb == 16 ? (const void*)b_step_a_kernel<float, 16> : (const void*)b_step_a_kernel<float, 32>;
+       : kb == 16 ? (const void*)b_step_a_kernel<float, 16>
+       : kb == 24 ? (const void*)b_step_a_kernel<float, 24> : (const void*)b_step_a_kernel<float, 32>;
     fb = kb == 0 ? (const void*)b_step_b_kernel<float, 0>
        : kb == 8 ? (const void*)b_step_b_kernel<float, 8>
-       : kb == 16 ? (const void*)b_step_b_kernel<float, 16> : (const void*)b_step_b_kernel<float, 32>;
+       : kb == 16 ? (const void*)b_step_b_kernel<float, 16>
+       : kb == 24 ? (const void*)b_step_b_kernel<float, 24> : (const void*)b_step_b_kernel<float, 32>;
   } else {
     fa = kb == 0 ? (const void*)b_step_a_kernel<double, 0>
        : kb == 8 ? (const void*)b_step_a_kernel<double, 8>
-       : kb == 16 ? (const void*)b_step_a_kernel<double, 16> : (const void*)b_step_a_kernel<double, 32>;
+       : kb == 16 ? (const void*)b_step_a_kernel<double, 16>
+       : kb == 24 ? (const void*)b_step_a_kernel<double, 24> : (const void*)b_step_a_kernel<double, 32>;
     fb = kb == 0 ? (const void*)b_step_b_kernel<double, 0>
        : kb == 8 ? (const void*)b_step_b_kernel<double, 8>
-       : kb == 16 ? (const void*)b_step_b_kernel<double, 16> : (const void*)b_step_b_kernel<double, 32>;
+       : kb == 16 ? (const void*)b_step_b_kernel<double, 16>
+       : kb == 24 ? (const void*)b_step_b_kernel<double, 24> : (const void*)b_step_b_kernel<double, 32>;
   }
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, fa, kThreads, 0);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fb, kThreads, 0);
@@ -1130,7 +1141,7 @@ mrcg_status batch_create_impl(int32_t nsys, const mrcg_create_args* args, mrcg_b
   h->nc_cap = 0;
   for (const SysDesc& sd : h->h_sys) h->nc_cap += (int)((sd.n_pad + kChunkMin - 1) / kChunkMin);
   make_chunks(h, kChunkRows);
-  h->kb = h->kmax == 0 ? 0 : h->kmax <= 8 ? 8 : h->kmax <= 16 ? 16 : 32;
+  h->kb = h->kmax == 0 ? 0 : h->kmax <= 8 ? 8 : h->kmax <= 16 ? 16 : h->kmax <= 24 ? 24 : 32;
   // ---- block-diagonal SELL-32 with global columns
   const int64_t nslices = slices;
   std::vector<int64_t> sp((size_t)nslices + 1, 0);

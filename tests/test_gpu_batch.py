@@ -67,6 +67,30 @@ def test_batch_fp64_matches_oracle(mcg, device):
         assert len(inf.relres_history) == inf.outer_iters
 
 
+@pytest.mark.parametrize("kmax", [5, 12, 20, 28], ids=["kb8", "kb16", "kb24", "kb32"])
+@pytest.mark.parametrize("prec", [m.FP64, m.MIXED_FP32], ids=["fp64", "mixed"])
+def test_batch_each_v_width_bucket_matches_oracle(kmax, prec):
+    """The batch kernels are compiled for V_hat widths of 8, 16, 24 and 32
+    columns and the batch's largest k picks one: a batch per bucket (its
+    largest system on a rectangle, whose low Laplacian eigenvalues are simple)
+    against the oracle, system by system."""
+    ps = [shifted_laplacian_problem("w0", (33, 29), 2, seed=11),
+          shifted_laplacian_problem("w1", (61, 47), kmax, seed=12),
+          _P((19, 23), 13)]
+    assert ps[1].k == kmax
+    B = np.concatenate([p.b for p in ps])
+    tol = 1e-12 if prec == m.FP64 else 1e-10
+    with m.Batch(ps, precision=prec) as bt:
+        X, st, infos = bt.solve(B.copy(), outer_tol=tol)
+        xs = bt.split(X)
+    assert st == m.OK
+    for p, x, inf in zip(ps, xs, infos):
+        ref = _oracle(p, 1e-12)
+        A = O.System(p.rowptr, p.colind, p.val)
+        assert inf.status == m.OK and A.true_relres(p.b, x) <= tol
+        assert np.linalg.norm(x - ref.x) <= (1e-8 if prec == m.FP64 else 1e-6) * np.linalg.norm(ref.x)
+
+
 def test_batch_matches_single_system_solver():
     ps = _small_batch()[:4]
     B = np.concatenate([p.b for p in ps])
