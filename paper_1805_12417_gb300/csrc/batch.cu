@@ -348,15 +348,27 @@ __global__ void __launch_bounds__(kThreads, b_min_blocks(KB)) b_step_b_kernel(BA
       }
 #pragma unroll
       for (int e = 0; e < W; ++e) rs += rv[e] * s[e];
+      // V_hat^T s: the columns in groups of 8, each group's loads issued
+      // together before its FMAs (k is uniform over the block)
       const int64_t li = i - sd.row0;
 #pragma unroll
-      for (int l = 0; l < KB; ++l)
-        if (l < sd.k) {
-          T vv[W];
-          ld16_stream(a.V + sd.voff + (size_t)l * sd.n_pad + li, vv);
+      for (int l0 = 0; l0 < KB; l0 += 8) {
+        if (l0 >= sd.k) break;
+        T vv[8][W];
 #pragma unroll
-          for (int e = 0; e < W; ++e) u[l] += vv[e] * s[e];
+        for (int j = 0; j < 8; ++j) {
+          if (l0 + j < sd.k) {
+            ld16_stream(a.V + sd.voff + (size_t)(l0 + j) * sd.n_pad + li, vv[j]);
+          } else {
+#pragma unroll
+            for (int e = 0; e < W; ++e) vv[j][e] = 0;
+          }
         }
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+          for (int e = 0; e < W; ++e) u[l0 + j] += vv[j][e] * s[e];
+      }
     }
     T acc[KB + 2];
     pack_slots<T, KB>(acc, rs, u, rr, sd.k, jac);
