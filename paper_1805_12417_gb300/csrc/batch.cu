@@ -149,6 +149,8 @@ __global__ void __launch_bounds__(kThreads) b_vnorm_kernel(DevState* st, const S
 
 // CTAs per SM the V_hat-width buckets are compiled for (register budgets)
 constexpr int b_min_blocks(int kb) { return kb >= 24 ? 2 : kb >= 16 ? 3 : 4; }
+template <typename T>
+constexpr int b_min_blocks_a(int kb) { return kb >= 24 ? 3 : 4; }
 
 template <typename T, int KB>
 __global__ void __launch_bounds__(kThreads, b_min_blocks(KB)) b_init_kernel(BArgs<T> a) {
@@ -228,7 +230,7 @@ __global__ void __launch_bounds__(kThreads, b_min_blocks(KB)) b_init_kernel(BArg
 }
 
 template <typename T, int KB>
-__global__ void __launch_bounds__(kThreads, KB >= 24 ? 3 : 4) b_step_a_kernel(BArgs<T> a) {
+__global__ void __launch_bounds__(kThreads, b_min_blocks_a<T>(KB)) b_step_a_kernel(BArgs<T> a) {
   constexpr int KS = KB > 0 ? KB : 1;
   __shared__ T cl[KS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -245,45 +247,58 @@ __global__ void __launch_bounds__(kThreads, KB >= 24 ? 3 : 4) b_step_a_kernel(BA
     const T* __restrict__ sv = a.s;
     const T* __restrict__ po = a.p_old;
     T dot = 0;
-    for (int64_t sl = ch.row0 / kSlice + warp; sl < ch.row1 / kSlice; sl += kThreads / 32) {
-      const int64_t row = sl * kSlice + lane;
-      const int64_t li = row - sd.row0;
-      T vrow[KS];
+    constexpr int NW = kThreads / 32;
+    const int64_t s_end = ch.row1 / kSlice;
+    for (int64_t g0 = ch.row0 / kSlice + warp; g0 < s_end; g0 += 32 * NW) {
+      // FP32: the slice pointers of the warp's next (up to) 32 slices in one
+      // round trip, lane t holding those of slice g0 + t * NW (FP64 keeps the
+      // per-slice loads: the two registers would spill at its register budget)
+      constexpr bool PF = sizeof(T) == 4;
+      const int64_t my_sl = g0 + (int64_t)lane * NW;
+      const int64_t my_b = (PF && my_sl < s_end) ? a.slice_ptr[my_sl] : 0;
+      const int my_w = (PF && my_sl < s_end) ? (int)((a.slice_ptr[my_sl + 1] - my_b) >> 5) : 0;
+      const int cnt = (int)min((int64_t)32, (s_end - g0 + NW - 1) / NW);
+      for (int t = 0; t < cnt; ++t) {
+        const int64_t sl = g0 + (int64_t)t * NW;
+        const int64_t row = sl * kSlice + lane;
+        const int64_t li = row - sd.row0;
+        T vrow[KS];
 #pragma unroll
-      for (int l = 0; l < KS; ++l)
-        vrow[l] = (l < sd.k) ? __ldcs(a.V + sd.voff + (size_t)l * sd.n_pad + li) : (T)0;
-      const T srow = sv[row], prow = po[row];
-      const int64_t base = a.slice_ptr[sl];
-      const int w = (int)((a.slice_ptr[sl + 1] - base) >> 5);
-      const T* vp = a.val + base + lane;
-      const int32_t* cp = a.col + base + lane;
-      T acc = 0;
-      if (w <= 8) {
-        T av[8];
-        int cc[8];
+        for (int l = 0; l < KS; ++l)
+          vrow[l] = (l < sd.k) ? __ldcs(a.V + sd.voff + (size_t)l * sd.n_pad + li) : (T)0;
+        const T srow = sv[row], prow = po[row];
+        const int64_t base = PF ? __shfl_sync(0xffffffffu, my_b, t) : a.slice_ptr[sl];
+        const int w = PF ? __shfl_sync(0xffffffffu, my_w, t) : (int)((a.slice_ptr[sl + 1] - base) >> 5);
+        const T* vp = a.val + base + lane;
+        const int32_t* cp = a.col + base + lane;
+        T acc = 0;
+        if (w <= 8) {
+          T av[8];
+          int cc[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          av[j] = (j < w) ? __ldcs(vp + (size_t)j * kSlice) : (T)0;
-          cc[j] = (j < w) ? __ldcs(cp + (size_t)j * kSlice) : 0;
-        }
+          for (int j = 0; j < 8; ++j) {
+            av[j] = (j < w) ? __ldcs(vp + (size_t)j * kSlice) : (T)0;
+            cc[j] = (j < w) ? __ldcs(cp + (size_t)j * kSlice) : 0;
+          }
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-          if (j < w) acc += av[j] * (__ldg(sv + cc[j]) + beta * __ldg(po + cc[j]));
-      } else {
+          for (int j = 0; j < 8; ++j)
+            if (j < w) acc += av[j] * (__ldg(sv + cc[j]) + beta * __ldg(po + cc[j]));
+        } else {
 #pragma unroll 4
-        for (int j = 0; j < w; ++j) {
-          const T av = __ldcs(vp + (size_t)j * kSlice);
-          const int cj = __ldcs(cp + (size_t)j * kSlice);
-          acc += av * (__ldg(sv + cj) + beta * __ldg(po + cj));
+          for (int j = 0; j < w; ++j) {
+            const T av = __ldcs(vp + (size_t)j * kSlice);
+            const int cj = __ldcs(cp + (size_t)j * kSlice);
+            acc += av * (__ldg(sv + cj) + beta * __ldg(po + cj));
+          }
         }
-      }
-      const T pn = srow + beta * prow;
+        const T pn = srow + beta * prow;
 #pragma unroll
-      for (int l = 0; l < KB; ++l)
-        if (l < sd.k) acc += vrow[l] * cl[l];
-      a.q[row] = acc;
-      a.p_new[row] = pn;
-      dot += pn * acc;
+        for (int l = 0; l < KB; ++l)
+          if (l < sd.k) acc += vrow[l] * cl[l];
+        a.q[row] = acc;
+        a.p_new[row] = pn;
+        dot += pn * acc;
+      }
     }
     T part[1] = {dot};
     chunk_partials<T, 1>(part, 1, a.partials, a.nchunks, c);
