@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-bf16", action="store_true",
+                    help="skip the extra measurement of the mixed solver with V_hat rounded to BF16 "
+                         "(MRCG_MIXED_BF16M), reported beside the headline under 'mixed_bf16m'")
     ap.add_argument("--workload", choices=["lap3d_128", "lap2d_64", "lap3d_128_near", "saddle", "batch64",
                                            "shifted64"],
                     default="lap3d_128",
@@ -458,14 +461,15 @@ def timed_steps(torch, step, steps, warmup, stream, dev, ws, clock_index=None):
     return max_over_ranks(e0.elapsed_time(e1), ws, dev), res, (ck.summary() if ck else None)
 
 
-def inner_bytes(cfg, n, nnz, k, w, mcg):
+def inner_bytes(cfg, n, nnz, k, w, mcg, vw=None):
     """Algorithmic bytes of one inner CG iteration's two kernels (step a, step
     b) for the launch configuration `cfg`: each streamed operand once, each
-    gathered vector entry counted once per row (it is reused from L2)."""
+    gathered vector entry counted once per row (it is reused from L2).  `vw`:
+    bytes per V_hat value streamed by step a (2 when variant 14 streams BF16)."""
     ib = cfg["index_bytes"]
     var = cfg["step_a_variant"]
     jac = n * w if mcg == "jacobi" else 0
-    a_mat = nnz * (w + ib) + k * n * w  # A values + column indices, V_hat
+    a_mat = nnz * (w + ib) + k * n * (vw or w)  # A values + column indices, V_hat
     if var == 8:  # one kernel: r, q, p, z read and r, z, p, q written for the own rows
         return a_mat + 8 * n * w, 0
     if 9 <= var <= 15:  # one gather: p, r (and M_cg^-1) read, q written | p, q, z, r (M_cg^-1) read, z, r, p written
@@ -492,7 +496,7 @@ def step_a_flops(cfg, n, nnz, k, mcg):
 
 
 def measure_single(torch, m, p, dev, stream, ws, local, rank, steps, warmup, mcg="identity", clocks=True,
-                   e2e=True, kernel_timing=True, cpu=False):
+                   e2e=True, kernel_timing=True, cpu=False, bf16=False):
     """Mixed-precision and FP64 solves of one system: throughput, iteration
     counts, errors (against x* and between the two precisions), the inner
     kernels' standalone and in-situ times with their algorithmic GB/s, and
@@ -504,11 +508,12 @@ def measure_single(torch, m, p, dev, stream, ws, local, rank, steps, warmup, mcg
     extra = {"ilu_block": ILU_BLOCK} if mcg in ("ilu0", "smw_ilu0") else {}
     solvers = {prec: m.Solver.from_problem(p, precision=prec, inner_prec=code, stream=stream.cuda_stream,
                                            validate=False, **extra)
-               for prec in (m.MIXED_FP32, m.FP64)}
+               for prec in ((m.MIXED_FP32, m.FP64) + ((m.MIXED_BF16M,) if bf16 else ()))}
     res, xs = {}, {}
     n, nnz, k = p.n, p.nnz, p.k
     peak, peak_kind = measured_peak_gbs()
-    for name, prec in (("mixed", m.MIXED_FP32), ("fp64", m.FP64)):
+    runs = (("mixed", m.MIXED_FP32), ("fp64", m.FP64)) + ((("mixed_bf16m", m.MIXED_BF16M),) if bf16 else ())
+    for name, prec in runs:
         s = solvers[prec]
 
         def step():
@@ -522,7 +527,8 @@ def measure_single(torch, m, p, dev, stream, ws, local, rank, steps, warmup, mcg
         xs[name] = xh
         rr = float(np.linalg.norm(p.b - p.scipy() @ xh) / np.linalg.norm(p.b))
         cfg = m.launch_config(s.h)
-        w = 4 if prec == m.MIXED_FP32 else 8
+        w = 8 if prec == m.FP64 else 4
+        vw = 2 if (prec == m.MIXED_BF16M and cfg["step_a_variant"] == 14) else None
         r = {"value": ok / (ms / 1000.0), "unit": "solves/s", "ms_per_step": ms / steps, "steps": steps,
              "outer_iters": infos[-1].outer_iters, "inner_iters_total": infos[-1].inner_iters_total,
              "restarts": infos[-1].restarts, "true_relres": infos[-1].true_relres, "true_relres_host_fp64": rr,
@@ -536,7 +542,7 @@ def measure_single(torch, m, p, dev, stream, ws, local, rank, steps, warmup, mcg
                 t_it = m.time_inner_graph(s.h, 512)
             except m.MrcgError:  # the recursion ended too early to time in situ: standalone sum
                 t_it = ta + tb
-            ba, bb = inner_bytes(cfg, n, nnz, k, w, mcg)
+            ba, bb = inner_bytes(cfg, n, nnz, k, w, mcg, vw)
             # in-situ step a: the in-loop iteration time split in the ratio of the standalone times
             ta_in = t_it * ta / (ta + tb) if (ta + tb) > 0 else t_it
             r["kernels"] = {"step_a_kernel": step_a_kernel_name(cfg, "float" if w == 4 else "double"),
@@ -883,7 +889,7 @@ def main():
     torch, m, dev, stream = gpu_setup(local)
     p, workload = single_system(args.workload)
     single = measure_single(torch, m, p, dev, stream, ws, local, rank, args.steps, args.warmup, mcg=args.mcg,
-                            cpu=not args.no_cpu_baseline)
+                            cpu=not args.no_cpu_baseline, bf16=not args.no_bf16)
     mx, f64 = single["mixed"], single["fp64"]
     ka = mx["kernels"]
     peak, peak_kind = single["peak_gbs"], single["peak_kind"]
@@ -916,6 +922,9 @@ def main():
             "fp64": {k: v for k, v in f64.items()},
             "mixed": {k: v for k, v in mx.items() if k != "clocks"},
             "mixed_vs_fp64_speedup": single["mixed_vs_fp64_speedup"],
+            "mixed_bf16m": single.get("mixed_bf16m"),
+            "mixed_bf16m_vs_mixed": (single["mixed_bf16m"]["value"] / mx["value"]
+                                     if single.get("mixed_bf16m") and mx["value"] else None),
             "mixed_rel_err_vs_fp64": single["mixed_rel_err_vs_fp64"],
             "e2e": single["e2e"],
             "gpu_launches": int(mx["launches_per_solve"] * args.steps),

@@ -89,8 +89,15 @@ typedef enum {
 /* Arithmetic of the inner CG.  The outer MINRES (Lanczos vectors, Givens
  * rotations, residual norms, true-residual check) is always FP64. */
 typedef enum {
-  MRCG_FP64 = 0,       /* inner CG in FP64 */
-  MRCG_MIXED_FP32 = 1  /* inner CG with FP32 copies of A, V_hat and FP32 vectors */
+  MRCG_FP64 = 0,        /* inner CG in FP64 */
+  MRCG_MIXED_FP32 = 1,  /* inner CG with FP32 copies of A, V_hat and FP32 vectors */
+  MRCG_MIXED_BF16M = 2  /* MRCG_MIXED_FP32 with V_hat's values rounded to BF16 (round to nearest even
+                         * from their FP32 values): every inner kernel computes with the same rounded
+                         * V_hat, so M_mr of Eq. 5 is built on it, and the one-gather step a on 16-slice
+                         * tiles streams it as BF16 (half of V_hat's bytes).  A stays FP32: its shifted
+                         * diagonal is not a BF16 number.  Single-system handles (and the inner
+                         * level of complex handles); batch and shifted-family handles return
+                         * MRCG_ERR_INVALID for it. */
 } mrcg_precision;
 
 /* Inner preconditioner M_cg of Algorithm 1 (the solves with M_cg inside each CG step). */

@@ -21,7 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmrcg.so")
 
 OK, ERR_INVALID, ERR_NOT_SPD, ERR_BREAKDOWN, ERR_MAXITER, ERR_NONFINITE, ERR_CUDA, ERR_OOM = range(8)
-FP64, MIXED_FP32 = 0, 1
+FP64, MIXED_FP32, MIXED_BF16M = 0, 1, 2
 MCG_IDENTITY, MCG_JACOBI, MCG_SMW, MCG_ILU0, MCG_SMW_ILU0 = 0, 1, 2, 3, 4
 
 

@@ -41,6 +41,8 @@ struct mrcg_solver {
   float* d_val32 = nullptr;
   double* d_V64 = nullptr;
   float* d_V32 = nullptr;
+  uint16_t* d_Vbf = nullptr;  // MRCG_MIXED_BF16M: V_hat's BF16 values (the bits of d_V32's upper halves)
+  bool bf16v = false;
   void* d_dinv = nullptr;
   void* d_dsmw = nullptr;    // MINRES-CG* M_cg: 1 / diag(A) in the inner precision
   double* d_gram = nullptr;  // k x k V^T M_cg^{-1} V of the inner kernels' V
@@ -214,12 +216,28 @@ mrcg_status validate_subspace(const mrcg_create_args* a, const std::vector<int64
   return MRCG_OK;
 }
 
+// BF16 of a finite FP32 value: its upper 16 bits after rounding the lower 16
+// to nearest, ties to even (BF16 is FP32 with a 7-bit fraction)
+inline uint16_t float_to_bf16_bits(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+inline float bf16_bits_to_float(uint16_t b) {
+  const uint32_t u = (uint32_t)b << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
 mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
   const int64_t n = a->n;
   h->n = n;
   h->nnz = a->nnz;
   h->k = a->k;
-  h->fp32 = a->precision == MRCG_MIXED_FP32;
+  h->fp32 = a->precision == MRCG_MIXED_FP32 || a->precision == MRCG_MIXED_BF16M;
+  h->bf16v = a->precision == MRCG_MIXED_BF16M;
   h->mcg = a->inner_prec;
   h->max_outer = a->max_outer > 0 ? a->max_outer : 200;
   h->restart_factor = a->restart_factor == 0.0 ? 0.5 : a->restart_factor;
@@ -259,6 +277,11 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
   for (double x : V)
     if (!std::isfinite(x)) return MRCG_ERR_NONFINITE;
   if (a->validate && a->k > 0) ST(validate_subspace(a, rp, ci, va, V, lam));
+  // MRCG_MIXED_BF16M: V_hat rounded to BF16 (after the validation of the given
+  // pairs), so that every kernel, the Jacobi diagonal and MINRES-CG*'s terms
+  // all use one V_hat
+  if (h->bf16v)
+    for (double& x : V) x = (double)bf16_bits_to_float(float_to_bf16_bits((float)x));
   // MINRES-CG* M_cg: Atilde = diag(A) of Sec. 2.1, every diagonal entry nonzero
   std::vector<double> dd;
   if (h->mcg == MRCG_MCG_SMW) {
@@ -331,6 +354,15 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
   if (h->fp32) {
     ST(dalloc(h, &h->d_V32, vcount));
     LK(launch_to_f32(h->stream, h->d_V64, h->d_V32, (int64_t)vcount));
+  }
+  if (h->bf16v && a->k > 0) {
+    std::vector<uint16_t> vb(vcount, 0);
+    for (int j = 0; j < a->k; ++j)
+      for (int64_t i = 0; i < n; ++i)
+        vb[(size_t)j * n_pad + i] = float_to_bf16_bits((float)V[(size_t)j * n + i]);
+    ST(dalloc(h, &h->d_Vbf, vcount));
+    CK(cudaMemcpyAsync(h->d_Vbf, vb.data(), vcount * sizeof(uint16_t), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));  // vb goes out of scope
   }
 
   // ---- vectors
@@ -502,6 +534,7 @@ mrcg_status create_impl(const mrcg_create_args* a, mrcg_solver* h) {
   g.partials = h->d_partials;
   g.A = h->A;
   g.V = h->fp32 ? (const void*)h->d_V32 : (const void*)h->d_V64;
+  g.Vbf = h->d_Vbf;
   g.k = a->k;
   g.dinv = h->d_dinv;
   g.dsmw = h->d_dsmw;
@@ -851,7 +884,8 @@ mrcg_status mrcg_solver_create(const mrcg_create_args* a, mrcg_handle* out) {
   if (!a || !out) return MRCG_ERR_INVALID;
   *out = nullptr;
   if (a->n < 1 || a->n > (int64_t)0x7fffff00 || a->nnz < 0 || a->k < 0 || a->k > kMaxK) return MRCG_ERR_INVALID;
-  if (a->precision != MRCG_FP64 && a->precision != MRCG_MIXED_FP32) return MRCG_ERR_INVALID;
+  if (a->precision != MRCG_FP64 && a->precision != MRCG_MIXED_FP32 && a->precision != MRCG_MIXED_BF16M)
+    return MRCG_ERR_INVALID;
   if (a->inner_prec < MRCG_MCG_IDENTITY || a->inner_prec > MRCG_MCG_SMW_ILU0) return MRCG_ERR_INVALID;
   if (!a->rowptr || (a->nnz > 0 && (!a->colind || !a->val))) return MRCG_ERR_INVALID;
   if (a->k > 0 && (!a->V || !a->lambda)) return MRCG_ERR_INVALID;

@@ -1130,6 +1130,7 @@ mrcg_status batch_create_impl(int32_t nsys, const mrcg_create_args* args, mrcg_b
       return MRCG_ERR_INVALID;
     if (a.precision != args[0].precision || a.inner_prec != args[0].inner_prec) return MRCG_ERR_INVALID;
     if (a.inner_prec != MRCG_MCG_IDENTITY && a.inner_prec != MRCG_MCG_JACOBI) return MRCG_ERR_INVALID;
+    if (a.precision != MRCG_FP64 && a.precision != MRCG_MIXED_FP32) return MRCG_ERR_INVALID;
     BST(fetch(a.rowptr, (size_t)a.n + 1, rps[i]));
     BST(fetch(a.colind, (size_t)a.nnz, cis[i]));
     BST(fetch(a.val, (size_t)a.nnz, vas[i]));

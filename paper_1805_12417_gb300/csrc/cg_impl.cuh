@@ -48,6 +48,7 @@ struct CgArgs {
   int64_t nslices, n_pad;
   // low-rank term
   const T* V;  // n_pad x k column-major
+  const uint16_t* Vbf;  // the same values as BF16 bits, streamed by variant 14 (else null)
   int k;
   // Jacobi: dinv != nullptr, s is a separate vector; identity: s == r
   const T* dinv;
@@ -1880,13 +1881,20 @@ __device__ __forceinline__ void pg2_issue_static(const CgArgs<T>& a, unsigned ch
   const uint32_t rb = (uint32_t)((s1 - s0) * kSlice * (int64_t)sizeof(T));
   const uint32_t ne = (uint32_t)(e1 - e0);
   const bool jac = a.dinv != nullptr;
-  mbar_arrive_expect_tx(bar, ne * (uint32_t)(sizeof(T) + ib) + (uint32_t)(a.k + 2 + (jac ? 1 : 0)) * rb);
+  const bool vbf = a.Vbf != nullptr;
+  const uint32_t rbv = vbf ? rb / (uint32_t)(sizeof(T) / 2) : rb;  // bytes of one V_hat column's rows
+  mbar_arrive_expect_tx(bar, ne * (uint32_t)(sizeof(T) + ib) + (uint32_t)(2 + (jac ? 1 : 0)) * rb +
+                                 (uint32_t)a.k * rbv);
   if (ne > 0) {
     bulk_g2s_hint(b, a.val + e0, ne * (uint32_t)sizeof(T), bar, pol);
     bulk_g2s_hint(b + a.off_col, idx + e0 * ib, ne * (uint32_t)ib, bar, pol);
   }
-  for (int l = 0; l < a.k; ++l)
-    bulk_g2s_hint(b + a.off_v + (size_t)l * TR * sizeof(T), a.V + (size_t)l * a.n_pad + row0, rb, bar, pol);
+  for (int l = 0; l < a.k; ++l) {
+    if (vbf)
+      bulk_g2s_hint(b + a.off_v + (size_t)l * TR * 2, a.Vbf + (size_t)l * a.n_pad + row0, rbv, bar, pol);
+    else
+      bulk_g2s_hint(b + a.off_v + (size_t)l * TR * sizeof(T), a.V + (size_t)l * a.n_pad + row0, rb, bar, pol);
+  }
   if (jac) bulk_g2s(b + a.off_d, a.dinv + row0, rb, bar);
 }
 
@@ -1906,8 +1914,11 @@ __device__ __forceinline__ void pg2_issue_static_warp(const CgArgs<T>& a, unsign
   const uint32_t rb = (uint32_t)((s1 - s0) * kSlice * (int64_t)sizeof(T));
   const uint32_t ne = (uint32_t)(e1 - e0);
   const bool jac = a.dinv != nullptr;
+  const bool vbf = a.Vbf != nullptr;
+  const uint32_t rbv = vbf ? rb / (uint32_t)(sizeof(T) / 2) : rb;  // bytes of one V_hat column's rows
   if (lane == 0)
-    mbar_arrive_expect_tx(bar, ne * (uint32_t)(sizeof(T) + ib) + (uint32_t)(a.k + 2 + (jac ? 1 : 0)) * rb);
+    mbar_arrive_expect_tx(bar, ne * (uint32_t)(sizeof(T) + ib) + (uint32_t)(2 + (jac ? 1 : 0)) * rb +
+                                   (uint32_t)a.k * rbv);
   __syncwarp();
   const int nc = 2 + a.k + (jac ? 1 : 0);
   for (int c = lane; c < nc; c += 32) {
@@ -1917,7 +1928,10 @@ __device__ __forceinline__ void pg2_issue_static_warp(const CgArgs<T>& a, unsign
       if (ne > 0) bulk_g2s_hint(b + a.off_col, idx + e0 * ib, ne * (uint32_t)ib, bar, pol);
     } else if (c < 2 + a.k) {
       const int l = c - 2;
-      bulk_g2s_hint(b + a.off_v + (size_t)l * TR * sizeof(T), a.V + (size_t)l * a.n_pad + row0, rb, bar, pol);
+      if (vbf)
+        bulk_g2s_hint(b + a.off_v + (size_t)l * TR * 2, a.Vbf + (size_t)l * a.n_pad + row0, rbv, bar, pol);
+      else
+        bulk_g2s_hint(b + a.off_v + (size_t)l * TR * sizeof(T), a.V + (size_t)l * a.n_pad + row0, rb, bar, pol);
     } else {
       bulk_g2s(b + a.off_d, a.dinv + row0, rb, bar);
     }
@@ -2062,6 +2076,7 @@ __global__ void __launch_bounds__(kStagedThreads, MB) cg_step_a_pg2_kernel(CgArg
   } else {
     const T* __restrict__ pv = a.p_old;
     const bool d16 = a.col16 != nullptr;
+    const bool vbf = a.Vbf != nullptr;
     int st = 0;
     uint32_t ph = 0;
     int64_t t = blockIdx.x;
@@ -2099,16 +2114,30 @@ __global__ void __launch_bounds__(kStagedThreads, MB) cg_step_a_pg2_kernel(CgArg
         const T apsa = jac ? da * apa : apa;  // (M_cg^{-1} A p)_row
         const T apsb = has_b ? (jac ? db * apb : apb) : (T)0;
         T qa = apa, qb = apb;
+        if (vbf) {  // V_hat's rows as BF16: the FP32 value is the BF16 bits shifted up
+          const uint16_t* vh = reinterpret_cast<const uint16_t*>(b + a.off_v);
 #pragma unroll
-        for (int l = 0; l < KB; ++l)
-          if (l < a.k) {
-            const T v1 = vt[l * TR + ra];
-            const T v2 = has_b ? vt[l * TR + rb] : (T)0;
-            qa += v1 * cl[l];
-            qb += v2 * cl[l];
-            wq[l] += v1 * apsa;
-            wq[l] += v2 * apsb;
-          }
+          for (int l = 0; l < KB; ++l)
+            if (l < a.k) {
+              const T v1 = (T)__uint_as_float((uint32_t)vh[l * TR + ra] << 16);
+              const T v2 = has_b ? (T)__uint_as_float((uint32_t)vh[l * TR + rb] << 16) : (T)0;
+              qa += v1 * cl[l];
+              qb += v2 * cl[l];
+              wq[l] += v1 * apsa;
+              wq[l] += v2 * apsb;
+            }
+        } else {
+#pragma unroll
+          for (int l = 0; l < KB; ++l)
+            if (l < a.k) {
+              const T v1 = vt[l * TR + ra];
+              const T v2 = has_b ? vt[l * TR + rb] : (T)0;
+              qa += v1 * cl[l];
+              qb += v2 * cl[l];
+              wq[l] += v1 * apsa;
+              wq[l] += v2 * apsb;
+            }
+        }
         a.q[rowa] = qa;
         pq += pa * qa;
         sq += (jac ? da * rva : rva) * qa;
@@ -2400,6 +2429,9 @@ struct StageGeo {
   int off_col, off_v, off_s, off_p, off_d, off_z, bytes;
 };
 
+// V_hat streamed as BF16: FP32 one-gather step a on 16-slice tiles (variant 14)
+inline bool bf16_stream(const InnerGraphSpec& spec) { return spec.Vbf != nullptr && spec.fp32 && spec.var_a == 14; }
+
 StageGeo stage_geo(const InnerGraphSpec& spec) {
   auto up = [](int64_t x) { return (x + 127) / 128 * 128; };
   const int64_t w = spec.fp32 ? 4 : 8, ib = spec.A.col16 ? 2 : 4;
@@ -2410,7 +2442,7 @@ StageGeo stage_geo(const InnerGraphSpec& spec) {
   g.off_col = (int)o;
   o += up(E * ib);
   g.off_v = (int)o;
-  o += (int64_t)spec.k * TR * w;
+  o += up((int64_t)spec.k * TR * (bf16_stream(spec) ? 2 : w));
   g.off_s = (int)o;
   o += TR * w;
   g.off_p = (int)o;
@@ -2456,6 +2488,7 @@ void make_args(const InnerGraphSpec& spec, CgArgs<T> (&a)[2]) {
     x.nslices = spec.A.nslices;
     x.n_pad = spec.A.n_pad;
     x.V = reinterpret_cast<const T*>(spec.V);
+    x.Vbf = bf16_stream(spec) ? reinterpret_cast<const uint16_t*>(spec.Vbf) : nullptr;
     x.k = spec.k;
     x.dinv = reinterpret_cast<const T*>(spec.dinv);
     x.dsmw = reinterpret_cast<const T*>(spec.dsmw);

@@ -16,6 +16,7 @@ struct InnerGraphSpec {
   double* partials = nullptr;
   Sell A;
   const void* V = nullptr;     // n_pad x k, inner precision
+  const void* Vbf = nullptr;   // MRCG_MIXED_BF16M: V's BF16 values (uint16 bits), n_pad x k
   int k = 0;
   const void* dinv = nullptr;  // Jacobi: 1 / diag(M_mr) (inner precision) or nullptr
   const void* dsmw = nullptr;  // MINRES-CG* M_cg: 1 / diag(A) (inner precision; dinv is then nullptr)
