@@ -112,3 +112,17 @@ def test_reference_arm_follows_the_inner_tolerance():
                          text=True, timeout=600, check=True).stdout.strip().splitlines()
     line = json.loads(out[-1])
     assert line["config"]["inner_tol"] == 1e-2 and line["value"] > 0
+
+
+def test_inner_bytes_of_the_one_gather_iteration():
+    """Step a of the one-gather iteration streams A (values and 16-bit deltas),
+    V_hat and three vectors; step b seven vectors.  With V_hat in BF16 only
+    V_hat's term halves."""
+    n, nnz, k = 1000, 6800, 10
+    cfg = {"step_a_variant": 14, "index_bytes": 2}
+    a, b = bench.inner_bytes(cfg, n, nnz, k, 4, "identity")
+    assert a == nnz * (4 + 2) + k * n * 4 + 3 * n * 4 and b == 7 * n * 4
+    a16, b16 = bench.inner_bytes(cfg, n, nnz, k, 4, "identity", vw=2)
+    assert a - a16 == k * n * 2 and b16 == b
+    a64, _ = bench.inner_bytes({"step_a_variant": 9, "index_bytes": 4}, n, nnz, k, 8, "jacobi")
+    assert a64 == nnz * 12 + k * n * 8 + 3 * n * 8 + n * 8
