@@ -49,6 +49,9 @@
  *  - MRCG_ILU_STAGE=0/1   ILU(0) sweeps read the factors from global memory (0)
  *                         or from per-block images copied into shared memory
  *                         (1); default: images in mixed precision, global in FP64.
+ *  - MRCG_EIG_FP32=0      mrcg_negative_eigenpairs filters in FP64 throughout
+ *                         (default: FP32 filter steps until the lowest Ritz
+ *                         pairs reach 1e-5 of the spectral radius bound).
  *  - MRCG_IDX16=0         keep 32-bit column indices in the inner kernels
  *                         (16-bit deltas are used whenever |col - row| <= 32767).
  *  - MRCG_UNROLL=U        inner iterations per convergence check (even, >= 2).
@@ -379,8 +382,10 @@ mrcg_status mrcg_mmr_apply_noalloc(int64_t n, const int64_t* rowptr, const int32
  * (Sec. 2, stage two of the three-stage summary; the experiments use a
  * Krylov eigensolver, Sec. 4), and amortises that cost over many solves.
  * mrcg_negative_eigenpairs does this on the GPU with the library's own block
- * SpMV: Chebyshev-filtered subspace iteration on a block of `block` vectors
- * (FP64), Rayleigh-Ritz between filters, until every Ritz value below zero
+ * SpMV: Chebyshev-filtered subspace iteration on a block of `block` vectors,
+ * Rayleigh-Ritz (FP64) between filters; the filter steps run in FP32 while
+ * the lowest Ritz pairs' residuals exceed 1e-5 ||A||_gersh and in FP64 from
+ * then on (MRCG_EIG_FP32=0: FP64 throughout), until every Ritz value below zero
  * has a residual ||A v - lambda v||_2 <= tol * ||A||_gersh (the Gershgorin
  * bound of the spectral radius) and the first nonnegative Ritz value of the
  * block has settled to sqrt(tol) * ||A||_gersh.  Its output is ready for

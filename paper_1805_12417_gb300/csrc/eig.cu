@@ -16,8 +16,11 @@
 //      else filter X <- p_d(A) X with the degree-d Chebyshev polynomial that
 //      damps [theta_m, hi] and grows below it (scaled at theta_1 so nothing
 //      overflows), and orthonormalise X again (Cholesky QR, twice).
-// All block arithmetic is FP64; the m x m eigenproblems and Cholesky
-// factorisations run on the host (m <= 64).
+// The filter runs in FP32 (A's values and the blocks rounded) while the
+// lowest Ritz pairs are far from converged, then in FP64 to the end
+// (MRCG_EIG_FP32=0: FP64 throughout); Rayleigh-Ritz, the orthonormalisation
+// and the residuals are always FP64, on FP64 blocks.  The m x m
+// eigenproblems and Cholesky factorisations run on the host (m <= 64).
 //
 // Layout: blocks are row-major n x MP (MP = 32 or 64 >= m, padding columns
 // zero), so one warp owns a row and lane j (+ 32 g) owns column j (+ 32 g).
@@ -36,35 +39,43 @@ namespace mrcg {
 namespace eig {
 
 constexpr int kGramBlocks = 608;
+// relative Ritz residual below which an FP32 filter step cannot help: its rounding
+// noise, about the FP32 epsilon per step over up to 64 steps, is of that size
+constexpr double kF32Floor = 1e-5;
+// natural log of the largest growth an FP32 filter may apply (FP32 overflows near 3.4e38)
+constexpr double kF32Growth = 60.0;
 
-struct Csr {
+template <typename T>
+struct CsrT {
   int64_t n;
   const int64_t* rowptr;
   const int32_t* col;
-  const double* val;
+  const T* val;
 };
+using Csr = CsrT<double>;
 
-// Y = ca * (A X) + cx * X + cp * P   (P may be null when cp == 0)
-template <int NM>
-__global__ void __launch_bounds__(kThreads) eig_cheb_kernel(Csr A, const double* __restrict__ X,
-                                                           const double* __restrict__ P, double* __restrict__ Y,
-                                                           double ca, double cx, double cp) {
+// Y = ca * (A X) + cx * X + cp * P   (P may be null when cp == 0): one warp
+// per row (the FP64 step is bound by the FP64 pipe, not by its gathers)
+template <typename T, int NM>
+__global__ void __launch_bounds__(kThreads) eig_cheb_kernel(CsrT<T> A, const T* __restrict__ X,
+                                                           const T* __restrict__ P, T* __restrict__ Y, T ca, T cx,
+                                                           T cp) {
   constexpr int MP = 32 * NM;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
   for (int64_t row = (int64_t)blockIdx.x * (kThreads / 32) + warp; row < A.n; row += nwarps) {
     const int64_t e0 = A.rowptr[row];
     const int nnz = (int)(A.rowptr[row + 1] - e0);
-    double acc[NM];
+    T acc[NM];
 #pragma unroll
-    for (int g = 0; g < NM; ++g) acc[g] = 0.0;
+    for (int g = 0; g < NM; ++g) acc[g] = 0;
     for (int base = 0; base < nnz; base += 32) {
       const bool has = lane + base < nnz;
-      const double my_val = has ? A.val[e0 + base + lane] : 0.0;
+      const T my_val = has ? A.val[e0 + base + lane] : (T)0;
       const int my_col = has ? A.col[e0 + base + lane] : 0;
       const int cnt = min(32, nnz - base);
       for (int j = 0; j < cnt; ++j) {
-        const double av = __shfl_sync(0xffffffffu, my_val, j);
+        const T av = __shfl_sync(0xffffffffu, my_val, j);
         const int64_t cj = (int64_t)__shfl_sync(0xffffffffu, my_col, j) * MP + lane;
 #pragma unroll
         for (int g = 0; g < NM; ++g) acc[g] = fma(av, __ldg(X + cj + 32 * g), acc[g]);
@@ -73,11 +84,129 @@ __global__ void __launch_bounds__(kThreads) eig_cheb_kernel(Csr A, const double*
 #pragma unroll
     for (int g = 0; g < NM; ++g) {
       const int64_t idx = row * MP + lane + 32 * g;
-      double y = ca * acc[g] + cx * X[idx];
-      if (cp != 0.0) y += cp * P[idx];
+      T y = ca * acc[g] + cx * X[idx];
+      if (cp != (T)0) y += cp * P[idx];
       Y[idx] = y;
     }
   }
+}
+
+// The FP32 filter step.  Its arithmetic is light, so it is bound by the
+// latency of its gathers: a warp takes 4 consecutive rows per trip; when they
+// hold at most 32 entries and none more than 8 (stencil rows), one coalesced
+// load brings all their values and columns and the gathers of two rows (one
+// row of a 64-wide block) are in flight together; other groups take each
+// row's entries 32 at a time.  Each row sums its entries in CSR order.
+template <int NM>
+__global__ void __launch_bounds__(kThreads) eig_cheb32_kernel(CsrT<float> A, const float* __restrict__ X,
+                                                             const float* __restrict__ P, float* __restrict__ Y,
+                                                             float ca, float cx, float cp) {
+  constexpr int MP = 32 * NM;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+  for (int64_t r0 = ((int64_t)blockIdx.x * (kThreads / 32) + warp) * 4; r0 < A.n; r0 += nwarps * 4) {
+    const int nr = (int)min((int64_t)4, A.n - r0);
+    const int64_t rp = lane <= nr ? A.rowptr[r0 + lane] : 0;
+    const int64_t nxt = __shfl_sync(0xffffffffu, rp, min(lane + 1, 31));
+    const int len_l = lane < nr ? (int)(nxt - rp) : 0;
+    const int64_t g0 = __shfl_sync(0xffffffffu, rp, 0);
+    const int tot = (int)(__shfl_sync(0xffffffffu, rp, nr) - g0);
+    const bool fast = tot <= 32 && __all_sync(0xffffffffu, len_l <= 8);
+    // own rows of X (and P) for the 4 rows: independent of the entries
+    float xo[4][NM], po[4][NM];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int g = 0; g < NM; ++g) {
+        const int64_t idx = (r0 + q) * MP + 32 * g + lane;
+        xo[q][g] = q < nr ? X[idx] : 0.0f;
+        po[q][g] = (q < nr && cp != 0.0f) ? P[idx] : 0.0f;
+      }
+    float acc[4][NM];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int g = 0; g < NM; ++g) acc[q][g] = 0.0f;
+    if (fast) {
+      const float my_val = lane < tot ? A.val[g0 + lane] : 0.0f;
+      const int my_col = lane < tot ? A.col[g0 + lane] : 0;
+      constexpr int U = NM == 1 ? 2 : 1;  // rows whose gathers are in flight together
+#pragma unroll
+      for (int h = 0; h < 4; h += U) {
+        float gx[U][8][NM];
+        int len[U], st[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int q = h + u;
+          st[u] = (int)(__shfl_sync(0xffffffffu, rp, q) - g0);
+          len[u] = __shfl_sync(0xffffffffu, len_l, q);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int64_t cj = (int64_t)__shfl_sync(0xffffffffu, my_col, (st[u] + j) & 31) * MP + lane;
+#pragma unroll
+            for (int g = 0; g < NM; ++g) gx[u][j][g] = j < len[u] ? __ldg(X + cj + 32 * g) : 0.0f;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const float av = __shfl_sync(0xffffffffu, my_val, (st[u] + j) & 31);
+            if (j < len[u])
+#pragma unroll
+              for (int g = 0; g < NM; ++g) acc[h + u][g] = fma(av, gx[u][j][g], acc[h + u][g]);
+          }
+      }
+    } else {
+      for (int q = 0; q < nr; ++q) {
+        const int64_t e0 = __shfl_sync(0xffffffffu, rp, q);
+        const int nnz = __shfl_sync(0xffffffffu, len_l, q);
+        float a[NM];
+#pragma unroll
+        for (int g = 0; g < NM; ++g) a[g] = 0.0f;
+        for (int base = 0; base < nnz; base += 32) {
+          const bool has = lane + base < nnz;
+          const float my_val = has ? A.val[e0 + base + lane] : 0.0f;
+          const int my_col = has ? A.col[e0 + base + lane] : 0;
+          const int cnt = min(32, nnz - base);
+          for (int j = 0; j < cnt; ++j) {
+            const float av = __shfl_sync(0xffffffffu, my_val, j);
+            const int64_t cj = (int64_t)__shfl_sync(0xffffffffu, my_col, j) * MP + lane;
+#pragma unroll
+            for (int g = 0; g < NM; ++g) a[g] = fma(av, __ldg(X + cj + 32 * g), a[g]);
+          }
+        }
+        // q is warp-uniform: select the accumulator row without dynamic indexing
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq)
+          if (qq == q)
+#pragma unroll
+            for (int g = 0; g < NM; ++g) acc[qq][g] = a[g];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (q >= nr) break;
+#pragma unroll
+      for (int g = 0; g < NM; ++g) {
+        float y = ca * acc[q][g] + cx * xo[q][g];
+        if (cp != 0.0f) y += cp * po[q][g];
+        Y[(r0 + q) * MP + 32 * g + lane] = y;
+      }
+    }
+  }
+}
+
+// y = x rounded to FP32 / widened to FP64, count elements
+__global__ void __launch_bounds__(kThreads) eig_to_f32_kernel(const double* __restrict__ x, float* __restrict__ y,
+                                                             int64_t count) {
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < count; i += (int64_t)gridDim.x * kThreads)
+    y[i] = (float)x[i];
+}
+__global__ void __launch_bounds__(kThreads) eig_to_f64_kernel(const float* __restrict__ x, double* __restrict__ y,
+                                                             int64_t count) {
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < count; i += (int64_t)gridDim.x * kThreads)
+    y[i] = (double)x[i];
 }
 
 // block partials of G[jg*32 + j][lg*32 + l] = sum_rows X[row][jg*32 + j] * Y[row][lg*32 + l]
@@ -310,6 +439,10 @@ struct Ctx {
   Csr A{};
   double *X = nullptr, *Y = nullptr, *Z = nullptr, *W = nullptr, *Qd = nullptr, *partials = nullptr, *small = nullptr,
          *theta = nullptr;
+  // FP32 filter steps (the early ones): A's values and three blocks in FP32
+  bool mixed = false;
+  CsrT<float> Af{};
+  float *Xf = nullptr, *Yf = nullptr, *Zf = nullptr;
   std::vector<void*> allocs;
   long long spmv_blocks = 0;
 };
@@ -338,8 +471,19 @@ mrcg_status ealloc(Ctx& c, T** p, size_t count) {
 
 // Y = ca A X + cx X + cp P
 mrcg_status cheb(Ctx& c, const double* X, const double* P, double* Y, double ca, double cx, double cp) {
-  if (c.nm == 1) eig_cheb_kernel<1><<<c.grid, kThreads, 0, c.s>>>(c.A, X, P, Y, ca, cx, cp);
-  else eig_cheb_kernel<2><<<c.grid, kThreads, 0, c.s>>>(c.A, X, P, Y, ca, cx, cp);
+  if (c.nm == 1) eig_cheb_kernel<double, 1><<<c.grid, kThreads, 0, c.s>>>(c.A, X, P, Y, ca, cx, cp);
+  else eig_cheb_kernel<double, 2><<<c.grid, kThreads, 0, c.s>>>(c.A, X, P, Y, ca, cx, cp);
+  ECK(cudaGetLastError());
+  ++c.spmv_blocks;
+  return MRCG_OK;
+}
+
+// the same step in FP32 (coefficients rounded to FP32)
+mrcg_status cheb32(Ctx& c, const float* X, const float* P, float* Y, double ca, double cx, double cp) {
+  if (c.nm == 1)
+    eig_cheb32_kernel<1><<<c.grid, kThreads, 0, c.s>>>(c.Af, X, P, Y, (float)ca, (float)cx, (float)cp);
+  else
+    eig_cheb32_kernel<2><<<c.grid, kThreads, 0, c.s>>>(c.Af, X, P, Y, (float)ca, (float)cx, (float)cp);
   ECK(cudaGetLastError());
   ++c.spmv_blocks;
   return MRCG_OK;
@@ -431,10 +575,31 @@ mrcg_status rayleigh_ritz(Ctx& c, std::vector<double>& theta, std::vector<double
 
 // X <- p_d(A) X: the Chebyshev polynomial of degree d on [a, b] (|p| <= 1 there
 // after scaling), scaled so that p_d(a0) = 1 (a0 < a, the lowest Ritz value)
-mrcg_status filter(Ctx& c, int d, double a, double b, double a0) {
+mrcg_status filter(Ctx& c, int d, double a, double b, double a0, bool f32) {
   const double e = 0.5 * (b - a), ctr = 0.5 * (b + a);
   double sigma = e / (ctr - a0);
   const double tau = 2.0 / sigma;
+  if (f32) {
+    // the same recurrence on FP32 copies; the result is widened back into X
+    const int64_t cnt = c.n * c.mp;
+    float *x = c.Xf, *y = c.Yf, *z = c.Zf;
+    eig_to_f32_kernel<<<c.grid, kThreads, 0, c.s>>>(c.X, x, cnt);
+    ECK(cudaGetLastError());
+    mrcg_status st = cheb32(c, x, nullptr, y, sigma / e, -ctr * sigma / e, 0.0);
+    if (st != MRCG_OK) return st;
+    for (int i = 2; i <= d; ++i) {
+      const double sn = 1.0 / (tau - sigma);
+      if ((st = cheb32(c, y, x, z, 2.0 * sn / e, -2.0 * ctr * sn / e, -sigma * sn)) != MRCG_OK) return st;
+      float* t = x;
+      x = y;
+      y = z;
+      z = t;
+      sigma = sn;
+    }
+    eig_to_f64_kernel<<<c.grid, kThreads, 0, c.s>>>(y, c.X, cnt);
+    ECK(cudaGetLastError());
+    return MRCG_OK;
+  }
   // Y = (A X - ctr X) sigma / e
   mrcg_status st = cheb(c, c.X, nullptr, c.Y, sigma / e, -ctr * sigma / e, 0.0);
   if (st != MRCG_OK) return st;
@@ -515,6 +680,19 @@ mrcg_status run(Ctx& c, const std::vector<int64_t>& rp, const std::vector<int32_
   if ((st = ealloc(c, &c.partials, (size_t)32 * 32 * c.nblk_gram)) != MRCG_OK) return st;
   if ((st = ealloc(c, &c.small, (size_t)32 * 32)) != MRCG_OK) return st;
   if ((st = ealloc(c, &c.theta, (size_t)c.mp)) != MRCG_OK) return st;
+  {
+    const char* e = getenv("MRCG_EIG_FP32");
+    c.mixed = !(e && atoi(e) == 0);
+  }
+  if (c.mixed) {
+    float* d_vaf = nullptr;
+    if ((st = ealloc(c, &d_vaf, va.size())) != MRCG_OK) return st;
+    for (float** p : {&c.Xf, &c.Yf, &c.Zf})
+      if ((st = ealloc(c, p, blk)) != MRCG_OK) return st;
+    if (!va.empty()) eig_to_f32_kernel<<<c.grid, kThreads, 0, c.s>>>(d_va, d_vaf, (int64_t)va.size());
+    ECK(cudaGetLastError());
+    c.Af = {n, d_rp, d_ci, d_vaf};
+  }
   if (c.nm == 1) eig_random_kernel<1><<<c.grid, kThreads, 0, c.s>>>(n, c.m, seed, c.X);
   else eig_random_kernel<2><<<c.grid, kThreads, 0, c.s>>>(n, c.m, seed, c.X);
   ECK(cudaGetLastError());
@@ -523,6 +701,7 @@ mrcg_status run(Ctx& c, const std::vector<int64_t>& rp, const std::vector<int32_
   std::vector<double> theta, res;
   int degree = 8;
   int rr_steps = 0;
+  bool f32 = c.mixed;  // FP32 filters until the leading Ritz pairs reach FP32's floor, then FP64 to the end
   bool converged = false;
   int kneg = 0;
   double maxres = 0.0;
@@ -552,7 +731,28 @@ mrcg_status run(Ctx& c, const std::vector<int64_t>& rp, const std::vector<int32_
     const double b = hi + 1e-12 * anorm;
     const double a = std::min(theta[c.m - 1], b - 1e-6 * anorm);
     const double a0 = std::min(theta[0], a - 1e-9 * anorm);
-    if ((st = filter(c, degree, a, b, a0)) != MRCG_OK) return st;
+    if (f32) {
+      double lead = 0.0;  // the residuals of the negative Ritz pairs (at least the lowest pair)
+      for (int j = 0; j < std::max(kneg, 1); ++j) lead = std::max(lead, res[j]);
+      if (!(lead > kF32Floor * anorm)) {
+        // the FP64 steps start again from a low degree: a degree-64 filter on
+        // a block whose wanted pairs are already this close makes the block
+        // too ill-conditioned for the Cholesky QR that follows
+        f32 = false;
+        degree = 8;
+      }
+    }
+    // an FP32 filter must not overflow: below a0 the scaled polynomial grows
+    // like exp(d (acosh t(lambda) - acosh t(a0))), largest at the Gershgorin
+    // bound lo; beyond about 1e26 this filter runs in FP64
+    bool use32 = f32;
+    if (use32) {
+      const double e = 0.5 * (b - a), ctr = 0.5 * (b + a);
+      auto ach = [](double t) { return t <= 1.0 ? 0.0 : std::log(t + std::sqrt(t * t - 1.0)); };
+      const double growth = degree * (ach((ctr - std::min(lo, a0)) / e) - ach((ctr - a0) / e));
+      use32 = std::isfinite(growth) && growth < kF32Growth;
+    }
+    if ((st = filter(c, degree, a, b, a0, use32)) != MRCG_OK) return st;
     if ((st = orthonormalise(c)) != MRCG_OK) return st;
     degree = std::min(degree * 2, 64);
   }

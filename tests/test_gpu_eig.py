@@ -136,3 +136,32 @@ def test_full_size_saddle_eigenpairs():
     rr = O.System.from_problem(q).true_relres(q.b, x.cpu().numpy())
     assert rr <= 1e-10
     print(f"eig saddle: {info['block_spmvs']} block SpMVs, {info['seconds']:.2f} s")
+
+
+@pytest.mark.parametrize("name", ["laplacian", "dense", "saddle"])
+def test_fp32_filter_steps_reach_the_fp64_result(name, monkeypatch):
+    """The filter's early FP32 steps (the default) and FP64 throughout
+    (MRCG_EIG_FP32=0) give the same pairs to the tolerance: the FP32 steps only
+    bring the block near the subspace, FP64 steps and FP64 Rayleigh-Ritz finish.
+    Covers the stencil path (4 rows per warp), dense rows and a saddle matrix."""
+    if name == "laplacian":
+        p = shifted_laplacian_problem("eig32", (23, 21, 19), 7, seed=4)
+        rp, ci, va, n, block = p.rowptr, p.colind, p.val, p.n, 16
+    elif name == "dense":
+        D = random_indefinite_dense(500, 6, seed=9)[0]
+        rp, ci, va = dense_to_csr(D)
+        n, block = 500, 16
+    else:
+        q = small_saddle()
+        rp, ci, va, n, block = q.rowptr, q.colind, q.val, q.n, 24
+    out = {}
+    for mode in ("1", "0"):
+        monkeypatch.setenv("MRCG_EIG_FP32", mode)
+        out[mode] = m.negative_eigenpairs(n, rp, ci, va, block, tol=1e-12)
+    (V1, l1, i1), (V0, l0, i0) = out["1"], out["0"]
+    assert len(l1) == len(l0) > 0
+    anorm = max(abs(i0["spectrum_lo"]), abs(i0["spectrum_hi"]))
+    assert np.allclose(l1, l0, rtol=0, atol=1e-10 * anorm)
+    _check_pairs(rp, ci, va, V1, l1, 1e-11 * anorm)
+    assert _projector_gap(V1, V0) <= 1e-7
+    print(f"{name}: FP32 filter {i1['block_spmvs']} block SpMVs, FP64 only {i0['block_spmvs']}")
